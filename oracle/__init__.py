@@ -1,0 +1,218 @@
+"""CPU oracle for the windowed fragment kMC (arXiv:2004.09081).
+
+TEST INFRASTRUCTURE ONLY: the test-suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only users.  The product path never
+imports this package.  The oracle is plain serial C (``fkmc_oracle.c``),
+compiled with ``-O2 -ffp-contract=off`` so that each floating-point operation is
+one IEEE round-to-nearest operation, in source order.  It shares nothing with
+the CUDA library.
+
+Functions follow the paper: rates (Sec. II.A Eq. RateCnst1, Sec. III ESP term),
+event selection (Eq. eventSelection), clock (Eq. TimeStep), fragment-local
+selection (Sec. II.B Eq. AtomP), D from tracked trajectories (Sec. III).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fkmc_oracle.c")
+_LIB = os.path.join(_HERE, "libfkmc_oracle.so")
+
+SP_O, SP_H, SP_V = 0, 1, 2
+PLAIN, MIXED = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library next to its source (gcc, C99)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-std=gnu99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+             "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        P, u64, i64, i32, u32, d = C.c_void_p, C.c_uint64, C.c_int64, C.c_int32, C.c_uint32, C.c_double
+        sig = {
+            "orc_philox4x64": (None, [P, P, P]),
+            "orc_neglog64": (d, [u64]),
+            "orc_neglog32": (C.c_float, [u64]),
+            "orc_neighbour_table": (None, [P]),
+            "orc_feistel": (u64, [u64, u64, u64, u32]),
+            "orc_colour_perm": (None, [u64, u32, u64, P]),
+            "orc_create": (P, [C.c_int] * 6 + [i64, i64, u64, u32, C.c_int]),
+            "orc_destroy": (None, [P]),
+            "orc_rate_table": (C.c_int, [d] * 8 + [C.c_int, P, P, P, P]),
+            "orc_set_rates": (C.c_int, [P] + [d] * 8 + [C.c_int, d, C.c_int]),
+            "orc_run": (C.c_int, [P, u64]),
+            "orc_bkl_run": (C.c_int, [P, d, u64, P]),
+            "orc_get_occ": (None, [P, P]),
+            "orc_set_occ_records": (None, [P, P]),
+            "orc_n_records": (i64, [P]),
+            "orc_get_records": (i64, [P, P, i64]),
+            "orc_get_tracer": (None, [P, P]),
+            "orc_get_counters": (None, [P, P, P]),
+            "orc_get_params": (None, [P, P, P, P]),
+            "orc_moments": (C.c_int, [P, C.c_int, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+# ---------------------------------------------------------------- primitives
+def philox4x64(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.zeros(4, np.uint64)
+    lib().orc_philox4x64(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def neglog64(x: int) -> float:
+    return lib().orc_neglog64(int(x))
+
+
+def neglog32(x: int) -> float:
+    return lib().orc_neglog32(int(x))
+
+
+def neighbour_table() -> np.ndarray:
+    """int32 [3 types][8 neighbours][t2, dcx, dcy, dcz, dx, dy, dz]."""
+    out = np.zeros((3, 8, 7), np.int32)
+    lib().orc_neighbour_table(_ptr(out))
+    return out
+
+
+def feistel(i: int, nsite: int, seed: int, replica: int = 0) -> int:
+    return int(lib().orc_feistel(i, nsite, seed, replica))
+
+
+def colour_perm(seed: int, replica: int, w: int) -> np.ndarray:
+    out = np.zeros(8, np.int32)
+    lib().orc_colour_perm(seed, replica, w, _ptr(out))
+    return out
+
+
+def rate_table(Ea_O, Ea_H, A, q_O, q_H, T, Ez, a_ang, cap_v=64):
+    k64 = np.zeros(6, np.float64)
+    k32 = np.zeros(6, np.float32)
+    q = np.zeros(6, np.uint64)
+    F = C.c_int32(0)
+    rc = lib().orc_rate_table(Ea_O, Ea_H, A, q_O, q_H, T, Ez, a_ang, cap_v, _ptr(k64), _ptr(k32),
+                              _ptr(q), C.byref(F))
+    if rc:
+        raise ValueError("bad rate parameters")
+    return k64, k32, q, F.value
+
+
+# ---------------------------------------------------------------- lattice
+class Lattice:
+    """One replica held by the oracle.  ``nf`` = fragments per dimension."""
+
+    def __init__(self, cells, nf, n_vac, n_H, seed=0, replica=0, tracer=False):
+        self.L = tuple(int(c) for c in cells)
+        self.nf = tuple(int(f) for f in nf)
+        self.nsite = 3 * self.L[0] * self.L[1] * self.L[2]
+        self._h = lib().orc_create(*self.L, *self.nf, int(n_vac), int(n_H), int(seed), int(replica),
+                                   int(bool(tracer)))
+        if not self._h:
+            raise ValueError("invalid lattice / partition / composition")
+        self.tracer = bool(tracer)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().orc_destroy(h)
+            self._h = None
+
+    def set_rates(self, Ea_O, Ea_H, T, A=1e13, q_O=2.0, q_H=1.0, Ez=0.0, a_ang=3.905, cap_v=64,
+                  n_tau=1.0, precision=PLAIN):
+        rc = lib().orc_set_rates(self._h, Ea_O, Ea_H, A, q_O, q_H, T, Ez, a_ang, cap_v, n_tau,
+                                 precision)
+        if rc:
+            raise ValueError("bad rate parameters")
+        self.a_ang = a_ang
+
+    def run(self, windows: int):
+        if lib().orc_run(self._h, int(windows)):
+            raise RuntimeError("rates not set")
+
+    def bkl_run(self, t_end: float, stream: int = 0) -> float:
+        t = C.c_double(0)
+        if lib().orc_bkl_run(self._h, float(t_end), int(stream), C.byref(t)):
+            raise RuntimeError("rates not set")
+        return t.value
+
+    def occupancy(self) -> np.ndarray:
+        out = np.zeros(self.nsite, np.uint8)
+        lib().orc_get_occ(self._h, _ptr(out))
+        return out
+
+    def set_occupancy(self, occ: np.ndarray):
+        occ = np.ascontiguousarray(occ, dtype=np.uint8)
+        assert occ.size == self.nsite
+        lib().orc_set_occ_records(self._h, _ptr(occ))
+
+    def records(self) -> np.ndarray:
+        n = lib().orc_n_records(self._h)
+        out = np.zeros((max(n, 1), 6), np.int64)
+        k = lib().orc_get_records(self._h, _ptr(out), n)
+        return out[:k]
+
+    def tracer_field(self) -> np.ndarray:
+        out = np.zeros((self.nsite, 3), np.int32)
+        lib().orc_get_tracer(self._h, _ptr(out))
+        return out
+
+    def counters(self):
+        c = np.zeros(3, np.uint64)
+        cs = C.c_double(0)
+        lib().orc_get_counters(self._h, _ptr(c), C.byref(cs))
+        return {"window": int(c[0]), "hops": int(c[1]), "handoffs": int(c[2]),
+                "clock_sum": cs.value}
+
+    def params(self):
+        tau, th = C.c_double(0), C.c_double(0)
+        F = C.c_int32(0)
+        lib().orc_get_params(self._h, C.byref(tau), C.byref(th), C.byref(F))
+        return {"tau": tau.value, "theta_tau": th.value, "F": F.value}
+
+    def moments(self, species=SP_V) -> np.ndarray:
+        out = np.zeros(7, np.int64)
+        if lib().orc_moments(self._h, int(species), _ptr(out)):
+            raise RuntimeError("tracer field not enabled")
+        return out
+
+    def diffusion(self, species=SP_V, t=None):
+        """D (m^2/s): MSD/(6t) from tracked displacements (Sec. III), plus the
+        per-axis D_x = <dx^2>/(2t) and the mean z displacement."""
+        m = self.moments(species)
+        if t is None:
+            t = self.counters()["window"] * self.params()["tau"]
+        n = max(int(m[0]), 1)
+        h = 0.5 * self.a_ang * 1e-10
+        msd = m[4:7].astype(np.float64) / n * h * h
+        mean = m[1:4].astype(np.float64) / n * h
+        return {"D": msd.sum() / (6 * t), "D_axes": msd / (2 * t), "mean": mean, "t": t, "n": n}
