@@ -1,0 +1,410 @@
+#!/usr/bin/env python3
+"""Benchmark of the fragment-kMC hot path (arXiv:2004.09081) on GB300.
+
+Workload (default): 256 uneven BaTiO(3-x)H_x replicas (16^3..48^3 cells,
+x ~ U[0,0.3], vacancies ~ U[0.1,1]%, T ~ U[300,1000] K, barriers 0.70/0.35 eV)
+in one batch, mixed precision.  One step = `--windows` synchronisation
+windows over the whole batch (8 colour phases each: rates, BKL selection,
+exchange, hand-off) followed by the batch-wide displacement-moment reduction
+that D comes from.  The lattice state stays resident; L2 is flushed (256 MiB
+write) between timed steps.
+
+Prints one JSON line.  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "hops/s on 1 GB300 (batched mixed vs plain FP64) at D within 1%; HBM roofline frac"
+UNIT = "hops/s"
+B_ALG_PER_HOP = 160  # algorithmic bytes per hop at 32-byte sector granularity
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--windows", type=int, default=64, help="windows per step")
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison leg")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return p.parse_args()
+
+
+def dist_setup(want_cuda: bool):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if want_cuda else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(v: float, ws: int, device) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(v: float, ws: int, device) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                                       "-i", str(gpu_index), "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                smax.append(float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def make_batch(fk, wl, seed, precision, replicas=None):
+    reps = wl.replicas if replicas is None else [wl.replicas[i] for i in replicas]
+    b = fk.Batch([(*r.cells, r.a) for r in reps], [(r.n_vac, r.n_H) for r in reps], seed, edge=wl.edge,
+                 precision=precision)
+    b.set_barriers([r.Ea_O for r in reps], [r.Ea_H for r in reps], [r.T for r in reps],
+                   field_z=[r.field_z for r in reps])
+    return b
+
+
+def D_from_moments(m, t, a):
+    """D = <|d|^2>/(6t) (m^2/s) from the integer moments of one replica."""
+    h = 0.5 * a * 1e-10
+    return (m[4] + m[5] + m[6]) / max(m[0], 1) * h * h / (6 * t)
+
+
+def cpu_oracle_rate(wl, seed, windows, budget_s, replicas=None):
+    """Time the CPU oracle (one core, as written) on replicas of the workload
+    until the budget is spent; returns (hops/s, hops, seconds, replicas done)."""
+    import oracle
+    oracle.build()
+    order = list(range(len(wl.replicas))) if replicas is None else list(replicas)
+    hops, secs, done = 0, 0.0, 0
+    info_cap = None
+    for r in order:
+        rep = wl.replicas[r]
+        nf = rep.nfrag or tuple(_nfrag(c, wl.edge) for c in rep.cells)
+        if info_cap is None:
+            info_cap = _auto_cap(wl)
+        L = oracle.Lattice(rep.cells, nf, rep.n_vac, rep.n_H, seed=seed, replica=r)
+        L.set_rates(rep.Ea_O, rep.Ea_H, rep.T, Ez=rep.field_z, a_ang=rep.a, cap_v=info_cap,
+                    precision=wl.precision)
+        t0 = time.perf_counter()
+        L.run(windows)
+        secs += time.perf_counter() - t0
+        hops += L.counters()["hops"]
+        done += 1
+        if secs >= budget_s:
+            break
+    return hops / secs if secs > 0 else 0.0, hops, secs, done
+
+
+def _nfrag(L, edge):
+    nf = 2 * int(math.floor(L / (2.0 * edge) + 0.5))
+    if nf < 2:
+        nf = 2 if L >= 4 else 1
+    while nf > 1 and L // nf < 2:
+        nf -= 2
+    return max(nf, 1)
+
+
+def _auto_cap(wl):
+    worst = 0.0
+    for r in wl.replicas:
+        nf = r.nfrag or tuple(_nfrag(c, wl.edge) for c in r.cells)
+        worst = max(worst, r.n_vac / (nf[0] * nf[1] * nf[2]))
+    cap = int(math.ceil(worst + 10.0 * math.sqrt(worst + 1.0) + 8.0))
+    cap = ((cap + 7) // 8) * 8
+    return min(256, max(8, cap))
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def load_traffic(kernel_tag):
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    return d.get(kernel_tag)
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    from paper_2004_09081_gb300 import workloads
+    ws, rank, _ = dist_setup(False)
+    if rank != 0:
+        return
+    wl = workloads.batched_batio3(args.seed)
+    nrep = len(wl.replicas)
+    per_step_budget = 8.0
+    times, hops_all, reps_done = [], 0, 0
+    cursor = 0
+    for k in range(args.warmup + args.steps):
+        sample = [(cursor + i) % nrep for i in range(nrep)]
+        rate, hops, secs, done = cpu_oracle_rate(wl, args.seed, args.windows, per_step_budget, sample)
+        cursor = (cursor + done) % nrep
+        if k >= args.warmup:
+            times.append(secs)
+            hops_all += hops
+            reps_done += done
+    total = sum(times)
+    value = hops_all / total if total > 0 else 0.0
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+u64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "replicas": nrep, "windows_per_step": args.windows,
+                   "precision": "mixed"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{reps_done} replica runs of {args.windows} windows each over "
+                                   f"{args.steps} steps (~{per_step_budget:.0f} s of serial C per step)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    ws, rank, local = dist_setup(True)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2004_09081_gb300 import fkmc, workloads
+    fkmc.load()
+    seed = args.seed + rank  # each rank simulates its own independent batch (weak scaling)
+    wl = workloads.batched_batio3(seed)
+    nrep = len(wl.replicas)
+    W = args.windows
+    stream = torch.cuda.current_stream()
+
+    b = make_batch(fkmc, wl, seed, fkmc.FKMC_MIXED)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        s = b.run(W)
+        b.moments_all()
+        return s
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    hops = 0
+    kernel_ms = 0.0
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        ev[k][0].record(stream)
+        s = step()
+        ev[k][1].record(stream)
+        hops += s.hops
+        kernel_ms += s.gpu_ms
+    torch.cuda.synchronize()
+    barrier(ws)
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(c) for a, c in ev]
+    t_dev = sum(step_ms) / 1e3
+    t_max = allreduce_max(t_dev, ws, dev)
+    hops_all = allreduce_sum(float(hops), ws, dev)
+    value = hops_all / t_max
+    launches = args.steps * (8 * W + 1)
+
+    # roofline of the dominant kernel (the colour-phase kernel)
+    peak, peak_kind = load_peaks()
+    n_launch = args.steps * 8 * W
+    avg_launch_s = kernel_ms / 1e3 / n_launch
+    bytes_per_launch = hops / n_launch * B_ALG_PER_HOP
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    traffic = load_traffic("k_phase_mixed_batched")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": f"{peak_kind} hbm_gbs",
+                "kernel": "k_phase<mixed>", "bytes_per_hop": B_ALG_PER_HOP,
+                "hops_per_launch": hops / n_launch, "avg_launch_us": avg_launch_s * 1e6}
+
+    extra = {}
+    if rank == 0:
+        # end to end through the public API: host state blob -> GPU, run, moments -> host
+        nbytes = fkmc.kmc_state_bytes(b.h)
+        host = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+        fkmc.kmc_download_state(b.h, host.data_ptr(), nbytes)
+        e2e_steps = max(3, min(args.steps, 5))
+        e2e_hops = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            fkmc.kmc_upload_state(b.h, host.data_ptr(), nbytes)
+            e2e_hops += b.run(W).hops
+            m = b.moments_all()
+        e2e_t = time.perf_counter() - t0
+        extra["e2e"] = {"value": e2e_hops / e2e_t, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                        "d2h_bytes_per_step": int(m.nbytes), "steps": e2e_steps}
+
+        if not args.no_plain:
+            # accuracy: mixed vs plain FP64 from the same initial state, same draws
+            Wacc = 4 * W
+            bm = make_batch(fkmc, wl, seed, fkmc.FKMC_MIXED)
+            bp = make_batch(fkmc, wl, seed, fkmc.FKMC_PLAIN)
+            hm, hp = bm.run(Wacc).hops, bp.run(Wacc).hops
+            mm, mp = bm.moments_all(), bp.moments_all()
+            rel = []
+            for r in range(nrep):
+                tr = bp.info(r).window * bp.info(r).tau
+                Dm = D_from_moments(mm[r], tr, wl.replicas[r].a)
+                Dp = D_from_moments(mp[r], tr, wl.replicas[r].a)
+                if Dp > 0:
+                    rel.append(abs(Dm - Dp) / Dp)
+            agg_m = float(mm[:, 4:7].sum()) / float(mm[:, 0].sum())
+            agg_p = float(mp[:, 4:7].sum()) / float(mp[:, 0].sum())
+            same = sum(int(np.array_equal(mm[r], mp[r])) for r in range(nrep))
+            bm.close()
+            bp.close()
+            # plain FP64, replicas one at a time (the comparison form)
+            p_hops, p_ms = 0, 0.0
+            t0 = time.perf_counter()
+            for r in range(nrep):
+                b1 = make_batch(fkmc, wl, seed, fkmc.FKMC_PLAIN, replicas=[r])
+                # keep replica identity: batch of one keyed as replica 0 draws its own stream;
+                # throughput comparison only
+                s1 = b1.run(W)
+                p_hops += s1.hops
+                p_ms += s1.gpu_ms
+                b1.close()
+            p_wall = time.perf_counter() - t0
+            plain_rate = p_hops / (p_ms / 1e3)
+            # plain FP64 in one batch, for the split between batching and precision
+            bpb = make_batch(fkmc, wl, seed, fkmc.FKMC_PLAIN)
+            bpb.run(2)
+            spb = bpb.run(W)
+            bpb.close()
+            extra["plain_fp64"] = {
+                "one_at_a_time": {"value": plain_rate, "unit": UNIT, "hops": p_hops,
+                                  "kernel_s": p_ms / 1e3, "wall_s": p_wall},
+                "batched": {"value": spb.hops / (spb.gpu_ms / 1e3), "unit": UNIT},
+                "mixed_over_plain_one_at_a_time": value / plain_rate if plain_rate else None,
+                "mixed_over_plain_batched": (value / (spb.hops / (spb.gpu_ms / 1e3))) if spb.hops else None,
+            }
+            extra["D_mixed_vs_plain"] = {
+                "windows": Wacc, "hops_mixed": hm, "hops_plain": hp,
+                "aggregate_msd_rel_err": abs(agg_m - agg_p) / agg_p,
+                "per_replica_rel_err_median": float(np.median(rel)) if rel else None,
+                "per_replica_rel_err_max": float(np.max(rel)) if rel else None,
+                "replicas_bit_identical": same, "replicas": nrep,
+            }
+        if not args.no_cpu:
+            rate, ch, cs, cd = cpu_oracle_rate(wl, seed, W, 12.0)
+            extra["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                     "sample": f"first {cd} replicas of the batch, {W} windows each, "
+                                               f"serial C oracle ({ch} hops in {cs:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64+f32+f64", "data": "synthetic",
+            "config": {"workload": wl.name, "replicas": nrep, "windows_per_step": W,
+                       "precision": "mixed (fp32 rates -> u64 fixed point, fp32 variate, fp64 clock)",
+                       "n_tau": 1.0, "edge": wl.edge, "l2": "flushed between timed steps (256 MiB write)",
+                       "schedule": "one launch per colour phase", "seed": args.seed},
+            "roofline": roofline,
+            "clocks": clk,
+            "gpu_launches": launches,
+            "hops_per_step": hops / args.steps,
+            "wall_s": wall,
+        }
+        line.update(extra)
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

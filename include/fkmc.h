@@ -1,0 +1,235 @@
+/*
+ * fkmc.h -- C ABI of the GB300 fragment kinetic Monte Carlo library.
+ *
+ * Method: H. Nakata, "Development of a fragment kinetic Monte Carlo method for
+ * efficient prediction of ionic diffusion in perovskite crystals",
+ * arXiv:2004.09081.  O vacancies (V) and hydride ions (H-) hop on the O
+ * sublattice of a cubic ABO3 perovskite (Fig. 2: O at the three face centres
+ * of a cell of edge a, 8 O-O neighbours at a/sqrt2).  Hop rates follow
+ * Eq. (RateCnst1), k = A exp(-Ea/(kB T)), with the electrostatic shift of
+ * Sec. III; events are selected by cumulative rate, Eq. (eventSelection), and
+ * each fragment keeps its own residence-time clock, Eq. (TimeStep).  Fragments
+ * select independently because, once the clock is shared, an event's
+ * probability depends only on the rates it competes with (Sec. II.B,
+ * Eq. (AtomP)).
+ *
+ * Execution model: the lattice is cut into spatial fragments (an even number
+ * per dimension, or one); fragments are coloured by the parity of their
+ * indices (8 colours).  A synchronisation window of length tau runs the 8
+ * colours in a per-window random order; in a colour phase every fragment of
+ * that colour runs BKL on its own vacancies until its next event would pass
+ * tau.  Concurrent fragments never touch the same site.  A vacancy that hops
+ * out of its fragment is handed to the owner of its new site and moves again
+ * when that fragment's colour next runs.  Global time after window w is
+ * (w+1) tau.
+ *
+ * Conventions for every entry point:
+ *   - Return value: FKMC_OK (0) or a negative FKMC_E* code; kmc_last_error()
+ *     returns a thread-local message for the last failure.  Nothing aborts.
+ *   - Host pointers are read or written only during the call; the library
+ *     keeps no reference to them.  Device memory belongs to the batch (taken
+ *     from the caller's allocator callback if given, else cudaMalloc) and is
+ *     released by kmc_destroy().
+ *   - All GPU work goes to the stream in kmc_opts.stream (NULL = legacy
+ *     default stream).  kmc_run() and the read/write calls are synchronous on
+ *     return.
+ *   - Units: temperatures K, energies eV, fields V/m, lengths Angstrom in
+ *     inputs; D in m^2/s, time in s in outputs.  Displacements are integers
+ *     in units of a/2.
+ */
+#ifndef FKMC_ABI_H_
+#define FKMC_ABI_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FKMC_OK 0
+#define FKMC_EINVAL (-1)    /* bad argument: sizes, partition, composition, replica index */
+#define FKMC_ENOMEM (-2)    /* allocator returned NULL */
+#define FKMC_ECUDA (-3)     /* a CUDA runtime call failed (message has the CUDA error) */
+#define FKMC_ETIMEOUT (-4)  /* a device-side wait or the per-phase event bound (2^24) ran out */
+#define FKMC_EOVERFLOW (-5) /* a fragment received more vacancies than its slot capacity */
+#define FKMC_ESTATE (-6)    /* call out of order (e.g. kmc_run before kmc_set_barriers) */
+
+/* species codes (2 bits per site on the device) */
+#define FKMC_O 0
+#define FKMC_H 1
+#define FKMC_V 2
+
+/* arithmetic forms */
+#define FKMC_PLAIN 0 /* FP64 rates, FP64 prefix sums, FP64 clock */
+#define FKMC_MIXED 1 /* FP32 rates quantised to u64 fixed point, exact integer sums, FP32 variate + FP64 clock */
+
+typedef struct {
+    int32_t nx, ny, nz; /* cells per dimension, each >= 1 and <= 65535 */
+    double a_angstrom;  /* cubic lattice constant */
+} kmc_cells;
+
+typedef struct {
+    int64_t n_vac; /* O vacancies placed at creation */
+    int64_t n_H;   /* H- ions placed at creation (on O sites) */
+} kmc_composition;
+
+typedef struct {
+    double Ea_O_eV;   /* barrier of the O <-> V exchange */
+    double Ea_H_eV;   /* barrier of the H- <-> V exchange */
+    double prefactor; /* A of Eq. (RateCnst1), 1/s (the paper uses 1e13) */
+    double q_O;       /* charge carried with the vacancy in an O exchange, units of e (+2) */
+    double q_H;       /* same for an H- exchange (+1) */
+} kmc_barrier_table;
+
+typedef void* (*kmc_alloc_fn)(void* ctx, size_t bytes);
+typedef void (*kmc_free_fn)(void* ctx, void* ptr);
+
+typedef struct {
+    int32_t edge;       /* target fragment edge in cells (used where nfrag[d] == 0); default 4 */
+    int32_t nfrag[3];   /* fragments per dimension: 1 or even with every edge >= 2; 0 = from edge */
+    int32_t precision;  /* FKMC_PLAIN or FKMC_MIXED */
+    int32_t tracer;     /* nonzero: also track every ion's displacement (12 bytes per site) */
+    int32_t cap_v;      /* vacancy slots per fragment, 8..256; 0 = sized from the composition */
+    double n_tau;       /* window length tau = n_tau / (8 k_fast), 0 < n_tau <= 64; default 1 */
+    void* stream;       /* cudaStream_t for all work */
+    kmc_alloc_fn alloc; /* optional device allocator; NULL = cudaMalloc */
+    kmc_free_fn free;
+    void* alloc_ctx;
+    int32_t schedule;   /* 0 = one launch per colour phase; 1 = persistent ordered-queue kernel */
+    int32_t reserved[7];
+} kmc_opts;
+
+typedef struct {
+    uint64_t hops;     /* executed (non-null) exchanges, summed over replicas */
+    uint64_t handoffs; /* exchanges that moved a vacancy into another fragment */
+    uint64_t windows;  /* windows run by this call */
+    double gpu_ms;     /* device time of the call's kernels (CUDA events) */
+} kmc_run_stats;
+
+typedef struct {
+    int32_t nfrag[3];   /* fragments per dimension */
+    int32_t cap_v;      /* vacancy slots per fragment */
+    int32_t F;          /* fixed-point fraction bits of the mixed form */
+    int32_t precision;
+    double tau;         /* window length, s */
+    double theta_tau;   /* window length in units of 1/k32max (mixed clock) */
+    double k64[6];      /* FP64 rate table, index 3*h + dz + 1 (h: 0 = O, 1 = H) */
+    uint64_t q[6];      /* fixed-point table of the mixed form */
+    uint64_t window;    /* windows completed */
+    uint64_t hops;      /* exchanges executed so far */
+    uint64_t handoffs;
+    int64_t nsite;      /* 3 nx ny nz */
+    int64_t n_vac, n_H;
+} kmc_replica_info;
+
+typedef struct kmc_batch kmc_batch;
+
+/* Fill *opts with the defaults listed above. */
+void kmc_default_opts(kmc_opts* opts);
+
+/* Create n independent replicas (lattices of possibly different sizes and
+ * compositions) in one batch; replica r uses cells[r], comp[r] and draws its
+ * random numbers from Philox4x64-10 keyed by (seed, r).  The initial state
+ * places comp[r].n_vac vacancies and then comp[r].n_H hydride ions at the
+ * images of 0, 1, 2, ... under a keyed bijection of the site indices (a
+ * 4-round Feistel network with cycle walking); vacancy i gets id i.  The
+ * paper gives no placement rule; this one gives exact counts and uniformly
+ * random positions.
+ * Errors: FKMC_EINVAL for n < 1, bad cells/partition/composition or opts;
+ * FKMC_ENOMEM / FKMC_ECUDA; FKMC_EOVERFLOW if a fragment starts with more
+ * vacancies than cap_v.  On error *out is NULL and nothing is leaked. */
+int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* comp,
+                     uint64_t seed, const kmc_opts* opts, kmc_batch** out);
+
+/* kmc_create_batch with n = 1. */
+int kmc_create_lattice(const kmc_cells* cells, const kmc_composition* comp, uint64_t seed,
+                       const kmc_opts* opts, kmc_batch** out);
+
+/* Rate tables of every replica, Eq. (RateCnst1) with the ESP shift of Sec. III:
+ *   k[h][dz] = A exp(-(Ea_h + dU/2) / (kB T)),  dU = -q_h E_z dz a/2,
+ * dz in {-1,0,+1} the vacancy's z step in units of a/2 (in-plane hops have
+ * dz = 0).  tables, T_K and field_z_Vpm each hold n entries (field may be
+ * NULL = 0).  Computed on the host in FP64; the mixed form stores
+ * k32 = fp32(k64) and q = rint(k32/k32max 2^F), F = 63 - ceil(log2(8 cap_v)).
+ * Sets tau = n_tau / (8 k_fast), k_fast the largest rate of the species
+ * present.  Errors: FKMC_EINVAL for T <= 0 or non-finite inputs. */
+int kmc_set_barriers(kmc_batch* b, const kmc_barrier_table* tables, const double* T_K,
+                     const double* field_z_Vpm);
+
+/* Run `windows` synchronisation windows on every replica.  Synchronous.
+ * Errors: FKMC_ESTATE before kmc_set_barriers; FKMC_EOVERFLOW if a hand-off
+ * found its target fragment full (the state is then invalid);
+ * FKMC_ETIMEOUT if a device wait gave up; FKMC_ECUDA. */
+int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats);
+
+/* Exact integer moments of the displacements of one species of replica r:
+ * out = {count, sum dx, sum dy, sum dz, sum dx^2, sum dy^2, sum dz^2}, units
+ * a/2 and (a/2)^2.  FKMC_V sums the vacancy records; FKMC_O / FKMC_H sum the
+ * tracer field over the sites holding that species (FKMC_ESTATE without
+ * tracer).  Computed by a reduction kernel into a small scratch buffer. */
+int kmc_read_moments(kmc_batch* b, int32_t r, int32_t species, int64_t out[7]);
+
+/* Vacancy moments of every replica in one reduction launch: out[7 r + k] as
+ * in kmc_read_moments; n_out must be 7 x the number of replicas. */
+int kmc_read_moments_all(kmc_batch* b, int64_t* out, size_t n_out);
+
+/* Mean squared displacement per axis (m^2), mean displacement per axis (m)
+ * and the simulated time t = windows * tau (s) of one species (Sec. III:
+ * D from tracked trajectories). */
+int kmc_read_msd(kmc_batch* b, int32_t r, int32_t species, double msd_xyz[3],
+                 double mean_xyz[3], double* t_s);
+
+/* D_axis = <d_axis^2>/(2t), D = MSD/(6t) (m^2/s), and the drift velocity
+ * v_z = <dz>/t (m/s) of one species. */
+int kmc_read_D(kmc_batch* b, int32_t r, int32_t species, double D_xyz[3], double* D,
+               double* v_drift_z);
+
+/* Occupancy of replica r, one species code per site, site index
+ * ((t nz + z) ny + y) nx + x with t the site type (0: a/2 x, 1: a/2 y,
+ * 2: a/2 z from the cell corner).  n must equal 3 nx ny nz. */
+int kmc_read_state(kmc_batch* b, int32_t r, uint8_t* host_occ, size_t n);
+
+/* Replace the state of replica r: occupancy as given (codes 0..2), one record
+ * per vacancy with zero displacement and id = rank in site order, tracer
+ * field cleared, window counter kept.  Errors: FKMC_EINVAL for bad codes,
+ * FKMC_EOVERFLOW if a fragment would exceed cap_v. */
+int kmc_write_state(kmc_batch* b, int32_t r, const uint8_t* host_occ, size_t n);
+
+/* Vacancy records of replica r as rows {fragment, site, dx, dy, dz, id},
+ * fragments ascending and sites ascending inside a fragment.  *n_rows gets
+ * the number of records; at most max_rows rows are written. */
+int kmc_read_records(kmc_batch* b, int32_t r, int64_t* rows, int64_t max_rows, int64_t* n_rows);
+
+/* Tracer displacements of replica r, 3 int32 per site (FKMC_ESTATE without tracer). */
+int kmc_read_tracer(kmc_batch* b, int32_t r, int32_t* host_disp, size_t n_sites);
+
+/* Packed device state of the whole batch (occupancy planes, vacancy records,
+ * counts) as one opaque blob, for end-to-end transfers: kmc_state_bytes gives
+ * its size; kmc_download_state / kmc_upload_state copy it to / from host
+ * memory (pinned memory gives full copy bandwidth). */
+int kmc_state_bytes(kmc_batch* b, size_t* bytes);
+int kmc_download_state(kmc_batch* b, void* host, size_t bytes);
+int kmc_upload_state(kmc_batch* b, const void* host, size_t bytes);
+
+int kmc_get_replica_info(kmc_batch* b, int32_t r, kmc_replica_info* out);
+int32_t kmc_num_replicas(const kmc_batch* b);
+
+/* Host-only: the rate table of kmc_set_barriers for one parameter set. */
+int kmc_rate_table(const kmc_barrier_table* t, double T_K, double field_z_Vpm, double a_angstrom,
+                   int32_t cap_v, double k64[6], float k32[6], uint64_t q[6], int32_t* F);
+
+/* Host-only: the 8 neighbours of each site type as rows {t2, dcx, dcy, dcz,
+ * dx, dy, dz} (24 rows of int32): neighbour cell offset and displacement in
+ * units of a/2, ascending in (dx, dy, dz). */
+void kmc_neighbour_table(int32_t out[168]);
+
+int kmc_destroy(kmc_batch* b);
+
+const char* kmc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

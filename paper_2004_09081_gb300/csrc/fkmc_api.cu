@@ -1,0 +1,712 @@
+// fkmc_api.cu -- host side of the C ABI declared in include/fkmc.h:
+// validation, partition of the lattice into fragments, device buffers,
+// rate tables (Eq. RateCnst1 of arXiv:2004.09081 with the ESP shift of
+// Sec. III), the window loop and the read-outs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fkmc.h"
+#include "fkmc_kernels.h"
+
+using namespace fkmc;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(FKMC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+const double KB_EV = 8.617333262e-5;  // Boltzmann constant, eV/K (R of Eq. RateCnst1)
+
+// Neighbour table built from the geometry: a site of type t sits at a/2 e_t
+// from its cell corner; its 8 nearest O neighbours are at a/2 (s_t e_t + s_u e_u)
+// for the two other axes u and signs s_t, s_u = +-1.  The neighbour has type u
+// and lies in the cell offset (d + e_t - e_u)/2.  Listed in ascending (dx,dy,dz).
+void build_nb_table(NbEntry tab[3][8])
+{
+    for (int t = 0; t < 3; ++t) {
+        struct Row { int d[3]; int u; };
+        std::vector<Row> rows;
+        for (int u = 0; u < 3; ++u) {
+            if (u == t) continue;
+            for (int st = -1; st <= 1; st += 2)
+                for (int su = -1; su <= 1; su += 2) {
+                    Row r{};
+                    r.d[t] = st;
+                    r.d[u] = su;
+                    r.u = u;
+                    rows.push_back(r);
+                }
+        }
+        std::sort(rows.begin(), rows.end(), [](const Row& a, const Row& b) {
+            return std::lexicographical_compare(a.d, a.d + 3, b.d, b.d + 3);
+        });
+        for (int n = 0; n < 8; ++n) {
+            NbEntry& e = tab[t][n];
+            e.t2 = (int8_t)rows[n].u;
+            for (int k = 0; k < 3; ++k) {
+                e.d[k] = (int8_t)rows[n].d[k];
+                e.dc[k] = (int8_t)((rows[n].d[k] + (k == t) - (k == rows[n].u)) / 2);
+            }
+            e.pad = 0;
+        }
+    }
+}
+
+int partition_count(int L, int edge)
+{
+    int nf = 2 * (int)std::floor((double)L / (2.0 * edge) + 0.5);
+    if (nf < 2) nf = L >= 4 ? 2 : 1;
+    while (nf > 1 && L / nf < 2) nf -= 2;
+    if (nf < 1) nf = 1;
+    return nf;
+}
+
+bool partition_ok(int L, int nf)
+{
+    if (nf < 1 || nf > L) return false;
+    if (nf == 1) return true;
+    return (nf % 2 == 0) && (L / nf >= 2);
+}
+
+int ceil_log2(int64_t v)
+{
+    int lg = 0;
+    while (((int64_t)1 << lg) < v) ++lg;
+    return lg;
+}
+
+}  // namespace
+
+struct kmc_batch {
+    int n = 0;
+    kmc_opts opts{};
+    cudaStream_t st = nullptr;
+    int cap = 0;
+    std::vector<RepDesc> desc;
+    std::vector<int64_t> n_vac, n_H;
+    std::vector<int> b_bits;
+    std::vector<double> a_ang;
+    std::vector<unsigned long long> stats_host;  // hops, handoffs per replica
+    int64_t nfrag_total = 0, occ_words = 0, nsite_total = 0, total_items = 0;
+    bool rates_set = false;
+    // device buffers
+    uint32_t* occ = nullptr;
+    VacRec* recs = nullptr;
+    int32_t* counts = nullptr;
+    int32_t* tracer = nullptr;
+    RepDesc* d_desc = nullptr;
+    unsigned long long* stats = nullptr;
+    uint32_t* status = nullptr;
+    unsigned long long* scratch = nullptr;  // 7 moments
+    unsigned long long* scratch_all = nullptr;  // 7 moments per replica
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<void*> owned;
+
+    void* dalloc(size_t bytes)
+    {
+        bytes = (bytes + 255) & ~(size_t)255;
+        if (bytes == 0) bytes = 256;
+        void* p = nullptr;
+        if (opts.alloc) {
+            p = opts.alloc(opts.alloc_ctx, bytes);
+        } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        if (p) owned.push_back(p);
+        return p;
+    }
+
+    void release()
+    {
+        for (void* p : owned) {
+            if (opts.alloc) {
+                if (opts.free) opts.free(opts.alloc_ctx, p);
+            } else {
+                cudaFree(p);
+            }
+        }
+        owned.clear();
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        ev0 = ev1 = nullptr;
+    }
+};
+
+namespace {
+
+int check_status(kmc_batch* b)
+{
+    uint32_t s = 0;
+    CK(cudaMemcpyAsync(&s, b->status, sizeof s, cudaMemcpyDeviceToHost, b->st), "status copy");
+    CK(cudaStreamSynchronize(b->st), "synchronize");
+    if (s & STATUS_OVERFLOW)
+        return fail(FKMC_EOVERFLOW, "a fragment received more vacancies than cap_v slots");
+    if (s & STATUS_TIMEOUT) return fail(FKMC_ETIMEOUT, "a device-side wait ran out of time");
+    if (s & STATUS_EVENT_LIMIT)
+        return fail(FKMC_ETIMEOUT, "a fragment reached the per-phase event limit (window too long)");
+    return FKMC_OK;
+}
+
+int upload_desc(kmc_batch* b)
+{
+    CK(cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(RepDesc) * b->n, cudaMemcpyHostToDevice, b->st),
+       "descriptor upload");
+    CK(cudaStreamSynchronize(b->st), "synchronize");
+    return FKMC_OK;
+}
+
+int rate_table_impl(const kmc_barrier_table* t, double T_K, double Ez, double a_ang, int cap_v,
+                    double k64[6], float k32[6], uint64_t q[6], int32_t* F_out)
+{
+    if (!t || !(T_K > 0.0) || !std::isfinite(T_K) || !std::isfinite(Ez) || !(a_ang > 0.0) ||
+        !std::isfinite(t->Ea_O_eV) || !std::isfinite(t->Ea_H_eV) || !(t->prefactor > 0.0) ||
+        !std::isfinite(t->q_O) || !std::isfinite(t->q_H) || cap_v < 1)
+        return fail(FKMC_EINVAL, "rate table: T must be > 0, inputs finite, prefactor > 0");
+    const double Ea[2] = {t->Ea_O_eV, t->Ea_H_eV};
+    const double qc[2] = {t->q_O, t->q_H};
+    const double half_a_m = 0.5 * a_ang * 1e-10;
+    for (int h = 0; h < 2; ++h)
+        for (int dz = -1; dz <= 1; ++dz) {
+            // Eq. (RateCnst1) with the vacancy's z step dz a/2 shifting the barrier by dU/2
+            const double dz_m = (double)dz * half_a_m;
+            const double dU = -(qc[h] * Ez) * dz_m;
+            const double barrier = Ea[h] + 0.5 * dU;
+            k64[3 * h + dz + 1] = t->prefactor * std::exp(-(barrier / (KB_EV * T_K)));
+        }
+    float kmax = 0.0f;
+    for (int i = 0; i < 6; ++i) {
+        k32[i] = (float)k64[i];
+        kmax = std::max(kmax, k32[i]);
+    }
+    if (!(kmax > 0.0f) || !std::isfinite(kmax))
+        return fail(FKMC_EINVAL, "rate table: rates underflow or overflow in fp32");
+    const int F = 63 - ceil_log2(8 * (int64_t)cap_v);
+    for (int i = 0; i < 6; ++i) q[i] = (uint64_t)std::llrint(std::ldexp((double)k32[i] / (double)kmax, F));
+    *F_out = F;
+    return FKMC_OK;
+}
+
+bool valid_replica(const kmc_batch* b, int32_t r) { return b && r >= 0 && r < b->n; }
+
+}  // namespace
+
+extern "C" {
+
+const char* kmc_last_error(void) { return g_err.c_str(); }
+
+void kmc_default_opts(kmc_opts* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->edge = 4;
+    o->precision = FKMC_PLAIN;
+    o->n_tau = 1.0;
+}
+
+void kmc_neighbour_table(int32_t out[168])
+{
+    NbEntry tab[3][8];
+    build_nb_table(tab);
+    for (int t = 0; t < 3; ++t)
+        for (int n = 0; n < 8; ++n) {
+            int32_t* o = out + (t * 8 + n) * 7;
+            o[0] = tab[t][n].t2;
+            for (int k = 0; k < 3; ++k) {
+                o[1 + k] = tab[t][n].dc[k];
+                o[4 + k] = tab[t][n].d[k];
+            }
+        }
+}
+
+int kmc_rate_table(const kmc_barrier_table* t, double T_K, double field_z_Vpm, double a_angstrom,
+                   int32_t cap_v, double k64[6], float k32[6], uint64_t q[6], int32_t* F)
+{
+    if (!k64 || !k32 || !q || !F) return fail(FKMC_EINVAL, "null output");
+    return rate_table_impl(t, T_K, field_z_Vpm, a_angstrom, cap_v, k64, k32, q, F);
+}
+
+int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* comp, uint64_t seed,
+                     const kmc_opts* opts_in, kmc_batch** out)
+{
+    if (!out) return fail(FKMC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || !cells || !comp) return fail(FKMC_EINVAL, "need n >= 1 replicas with cells and composition");
+    kmc_opts o;
+    kmc_default_opts(&o);
+    if (opts_in) o = *opts_in;
+    if (o.edge <= 0) o.edge = 4;
+    if (!(o.n_tau > 0.0) || !(o.n_tau <= 64.0)) return fail(FKMC_EINVAL, "n_tau must be in (0, 64]");
+    if (o.precision != FKMC_PLAIN && o.precision != FKMC_MIXED) return fail(FKMC_EINVAL, "bad precision");
+    if (o.cap_v != 0 && (o.cap_v < 8 || o.cap_v > 256 || o.cap_v % 8))
+        return fail(FKMC_EINVAL, "cap_v must be 0 or a multiple of 8 in [8, 256]");
+    if (o.schedule != 0) return fail(FKMC_EINVAL, "schedule must be 0");
+
+    kmc_batch* b = new kmc_batch();
+    b->n = n;
+    b->opts = o;
+    b->st = (cudaStream_t)o.stream;
+    b->desc.resize(n);
+    b->n_vac.resize(n);
+    b->n_H.resize(n);
+    b->b_bits.resize(n);
+    b->a_ang.resize(n);
+    b->stats_host.assign(2 * (size_t)n, 0ull);
+    double worst_mean = 0.0;
+    for (int r = 0; r < n; ++r) {
+        const kmc_cells& c = cells[r];
+        const int L[3] = {c.nx, c.ny, c.nz};
+        RepDesc& D = b->desc[r];
+        std::memset(&D, 0, sizeof D);
+        for (int d = 0; d < 3; ++d) {
+            if (L[d] < 1 || L[d] > 65535) {
+                delete b;
+                return fail(FKMC_EINVAL, "cells per dimension must be in [1, 65535]");
+            }
+            D.L[d] = L[d];
+            D.nf[d] = o.nfrag[d] > 0 ? o.nfrag[d] : partition_count(L[d], o.edge);
+            if (!partition_ok(L[d], D.nf[d])) {
+                delete b;
+                return fail(FKMC_EINVAL, "fragments per dimension must be 1, or even with every edge >= 2");
+            }
+            D.base[d] = L[d] / D.nf[d];
+            D.rem[d] = L[d] % D.nf[d];
+        }
+        if (!(c.a_angstrom > 0.0)) {
+            delete b;
+            return fail(FKMC_EINVAL, "lattice constant must be > 0");
+        }
+        D.nsite = 3 * (int64_t)L[0] * L[1] * L[2];
+        if (comp[r].n_vac < 0 || comp[r].n_H < 0 || comp[r].n_vac + comp[r].n_H > D.nsite ||
+            comp[r].n_vac > 0xffffffffll) {
+            delete b;
+            return fail(FKMC_EINVAL, "composition does not fit the lattice");
+        }
+        b->n_vac[r] = comp[r].n_vac;
+        b->n_H[r] = comp[r].n_H;
+        b->a_ang[r] = c.a_angstrom;
+        D.replica = (uint32_t)r;
+        D.seed = seed;
+        D.row_words = (int32_t)(((L[0] + 63) / 64) * 4);  // 16 sites per word, rows padded to 16 bytes
+        D.items = ((D.nf[0] + 1) / 2) * ((D.nf[1] + 1) / 2) * ((D.nf[2] + 1) / 2);
+        D.items_off = b->total_items;
+        b->total_items += D.items;
+        const int64_t nfrag = (int64_t)D.nf[0] * D.nf[1] * D.nf[2];
+        D.frag_base = b->nfrag_total;
+        b->nfrag_total += nfrag;
+        D.occ_word_off = b->occ_words;
+        b->occ_words += 3 * (int64_t)L[2] * L[1] * D.row_words;
+        D.site_off = b->nsite_total;
+        b->nsite_total += D.nsite;
+        int bb = 1;
+        while (((int64_t)1 << (2 * bb)) < D.nsite) ++bb;
+        b->b_bits[r] = bb;
+        worst_mean = std::max(worst_mean, (double)comp[r].n_vac / (double)nfrag);
+    }
+    if (o.cap_v == 0) {
+        int cap = (int)std::ceil(worst_mean + 10.0 * std::sqrt(worst_mean + 1.0) + 8.0);
+        cap = ((cap + 7) / 8) * 8;
+        b->cap = std::min(256, std::max(8, cap));
+    } else {
+        b->cap = o.cap_v;
+    }
+    b->opts.cap_v = b->cap;
+
+    b->occ = (uint32_t*)b->dalloc(sizeof(uint32_t) * b->occ_words);
+    b->recs = (VacRec*)b->dalloc(sizeof(VacRec) * b->nfrag_total * b->cap);
+    b->counts = (int32_t*)b->dalloc(sizeof(int32_t) * b->nfrag_total);
+    if (o.tracer) b->tracer = (int32_t*)b->dalloc(sizeof(int32_t) * 3 * b->nsite_total);
+    b->d_desc = (RepDesc*)b->dalloc(sizeof(RepDesc) * n);
+    b->stats = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * 2 * n);
+    b->status = (uint32_t*)b->dalloc(sizeof(uint32_t));
+    b->scratch = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * 8);
+    b->scratch_all = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * 7 * n);
+    if (!b->occ || !b->recs || !b->counts || (o.tracer && !b->tracer) || !b->d_desc || !b->stats ||
+        !b->status || !b->scratch || !b->scratch_all) {
+        b->release();
+        delete b;
+        return fail(FKMC_ENOMEM, "device allocation failed");
+    }
+    int rc = FKMC_OK;
+    auto step = [&](cudaError_t e, const char* what) {
+        if (rc == FKMC_OK && e != cudaSuccess) rc = cuda_fail(e, what);
+    };
+    NbEntry tab[3][8];
+    build_nb_table(tab);
+    step(upload_neighbours(&tab[0][0]), "neighbour table upload");
+    step(phase_prepare(b->cap), "kernel attributes");
+    step(cudaEventCreate(&b->ev0), "event");
+    step(cudaEventCreate(&b->ev1), "event");
+    step(cudaMemsetAsync(b->occ, 0, sizeof(uint32_t) * b->occ_words, b->st), "memset");
+    step(cudaMemsetAsync(b->counts, 0, sizeof(int32_t) * b->nfrag_total, b->st), "memset");
+    if (o.tracer) step(cudaMemsetAsync(b->tracer, 0, sizeof(int32_t) * 3 * b->nsite_total, b->st), "memset");
+    step(cudaMemsetAsync(b->stats, 0, sizeof(unsigned long long) * 2 * n, b->st), "memset");
+    step(cudaMemsetAsync(b->status, 0, sizeof(uint32_t), b->st), "memset");
+    for (int r = 0; r < n && rc == FKMC_OK; ++r)
+        step(launch_init(b->desc[r], b->b_bits[r], b->n_vac[r], b->n_vac[r] + b->n_H[r], b->occ, b->recs,
+                         b->counts, b->cap, b->status, b->st),
+             "init kernel");
+    if (rc == FKMC_OK) rc = upload_desc(b);
+    if (rc == FKMC_OK) rc = check_status(b);
+    if (rc != FKMC_OK) {
+        std::string keep = g_err;
+        b->release();
+        delete b;
+        g_err = keep;
+        return rc;
+    }
+    *out = b;
+    return FKMC_OK;
+}
+
+int kmc_create_lattice(const kmc_cells* cells, const kmc_composition* comp, uint64_t seed,
+                       const kmc_opts* opts, kmc_batch** out)
+{
+    return kmc_create_batch(1, cells, comp, seed, opts, out);
+}
+
+int kmc_set_barriers(kmc_batch* b, const kmc_barrier_table* tables, const double* T_K,
+                     const double* field_z_Vpm)
+{
+    if (!b || !tables || !T_K) return fail(FKMC_EINVAL, "null argument");
+    std::vector<RepDesc> nd = b->desc;
+    for (int r = 0; r < b->n; ++r) {
+        RepDesc& D = nd[r];
+        float k32[6];
+        int32_t F;
+        const double Ez = field_z_Vpm ? field_z_Vpm[r] : 0.0;
+        int rc = rate_table_impl(&tables[r], T_K[r], Ez, b->a_ang[r], b->cap, D.k64, k32, D.q, &F);
+        if (rc) return rc;
+        double kmax = 0.0;
+        float kmax32 = 0.0f;
+        for (int i = 0; i < 6; ++i) {
+            if ((i < 3 || b->n_H[r] > 0) && D.k64[i] > kmax) kmax = D.k64[i];
+            kmax32 = std::max(kmax32, k32[i]);
+        }
+        D.F = F;
+        D.two_pow_F = std::ldexp(1.0, F);
+        D.tau = b->opts.n_tau / (8.0 * kmax);
+        D.theta_tau = D.tau * (double)kmax32;
+    }
+    b->desc = nd;
+    int rc = upload_desc(b);
+    if (rc) return rc;
+    b->rates_set = true;
+    return FKMC_OK;
+}
+
+int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
+{
+    if (!b) return fail(FKMC_EINVAL, "null batch");
+    if (!b->rates_set) return fail(FKMC_ESTATE, "kmc_set_barriers must come before kmc_run");
+    std::vector<unsigned long long> before = b->stats_host;
+    CK(cudaEventRecord(b->ev0, b->st), "event record");
+    for (uint64_t wk = 0; wk < windows; ++wk)
+        for (int p = 0; p < 8; ++p)
+            CK(launch_phase(b->opts.precision, b->d_desc, b->n, b->total_items, p, wk, b->occ, b->recs,
+                            b->counts, b->tracer, b->stats, b->status, b->cap, b->st),
+               "phase kernel");
+    CK(cudaEventRecord(b->ev1, b->st), "event record");
+    for (int r = 0; r < b->n; ++r) b->desc[r].window += windows;
+    int rc = upload_desc(b);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(b->stats_host.data(), b->stats, sizeof(unsigned long long) * 2 * b->n,
+                       cudaMemcpyDeviceToHost, b->st),
+       "stats copy");
+    rc = check_status(b);
+    if (stats) {
+        std::memset(stats, 0, sizeof *stats);
+        for (int r = 0; r < b->n; ++r) {
+            stats->hops += b->stats_host[2 * r] - before[2 * r];
+            stats->handoffs += b->stats_host[2 * r + 1] - before[2 * r + 1];
+        }
+        stats->windows = windows;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+        stats->gpu_ms = ms;
+    }
+    return rc;
+}
+
+int kmc_read_moments(kmc_batch* b, int32_t r, int32_t species, int64_t out[7])
+{
+    if (!valid_replica(b, r) || !out) return fail(FKMC_EINVAL, "bad replica or output");
+    if (species != FKMC_O && species != FKMC_H && species != FKMC_V) return fail(FKMC_EINVAL, "bad species");
+    if (species != FKMC_V && !b->tracer) return fail(FKMC_ESTATE, "ion moments need tracer mode");
+    CK(launch_moments(b->desc[r], species, b->occ, b->recs, b->counts, b->tracer, b->cap, b->scratch, b->st),
+       "moments kernel");
+    unsigned long long h[7];
+    CK(cudaMemcpyAsync(h, b->scratch, sizeof h, cudaMemcpyDeviceToHost, b->st), "moments copy");
+    CK(cudaStreamSynchronize(b->st), "synchronize");
+    for (int k = 0; k < 7; ++k) out[k] = (int64_t)h[k];
+    return FKMC_OK;
+}
+
+int kmc_read_moments_all(kmc_batch* b, int64_t* out, size_t n_out)
+{
+    if (!b || !out) return fail(FKMC_EINVAL, "null argument");
+    if (n_out != 7 * (size_t)b->n) return fail(FKMC_EINVAL, "n_out must be 7 x replicas");
+    CK(launch_moments_all(b->d_desc, b->n, b->recs, b->counts, b->nfrag_total, b->cap, b->scratch_all, b->st),
+       "moments kernel");
+    CK(cudaMemcpyAsync(out, b->scratch_all, sizeof(int64_t) * n_out, cudaMemcpyDeviceToHost, b->st),
+       "moments copy");
+    CK(cudaStreamSynchronize(b->st), "synchronize");
+    return FKMC_OK;
+}
+
+int kmc_read_msd(kmc_batch* b, int32_t r, int32_t species, double msd_xyz[3], double mean_xyz[3],
+                 double* t_s)
+{
+    int64_t m[7];
+    int rc = kmc_read_moments(b, r, species, m);
+    if (rc) return rc;
+    const double h = 0.5 * b->a_ang[r] * 1e-10;
+    const double n = m[0] > 0 ? (double)m[0] : 1.0;
+    for (int k = 0; k < 3; ++k) {
+        if (msd_xyz) msd_xyz[k] = (double)m[4 + k] / n * h * h;
+        if (mean_xyz) mean_xyz[k] = (double)m[1 + k] / n * h;
+    }
+    if (t_s) *t_s = (double)b->desc[r].window * b->desc[r].tau;
+    return FKMC_OK;
+}
+
+int kmc_read_D(kmc_batch* b, int32_t r, int32_t species, double D_xyz[3], double* D, double* v_drift_z)
+{
+    double msd[3], mean[3], t;
+    int rc = kmc_read_msd(b, r, species, msd, mean, &t);
+    if (rc) return rc;
+    if (!(t > 0.0)) return fail(FKMC_ESTATE, "no simulated time yet");
+    for (int k = 0; k < 3; ++k)
+        if (D_xyz) D_xyz[k] = msd[k] / (2.0 * t);
+    if (D) *D = (msd[0] + msd[1] + msd[2]) / (6.0 * t);
+    if (v_drift_z) *v_drift_z = mean[2] / t;
+    return FKMC_OK;
+}
+
+int kmc_read_state(kmc_batch* b, int32_t r, uint8_t* host_occ, size_t n)
+{
+    if (!valid_replica(b, r) || !host_occ) return fail(FKMC_EINVAL, "bad replica or output");
+    const RepDesc& D = b->desc[r];
+    if ((int64_t)n != D.nsite) return fail(FKMC_EINVAL, "n must equal 3 nx ny nz");
+    const int64_t words = 3 * (int64_t)D.L[2] * D.L[1] * D.row_words;
+    std::vector<uint32_t> w(words);
+    CK(cudaMemcpyAsync(w.data(), b->occ + D.occ_word_off, sizeof(uint32_t) * words, cudaMemcpyDeviceToHost,
+                       b->st),
+       "state copy");
+    CK(cudaStreamSynchronize(b->st), "synchronize");
+    int64_t s = 0;
+    for (int t = 0; t < 3; ++t)
+        for (int z = 0; z < D.L[2]; ++z)
+            for (int y = 0; y < D.L[1]; ++y) {
+                const uint32_t* row = w.data() + (((int64_t)t * D.L[2] + z) * D.L[1] + y) * D.row_words;
+                for (int x = 0; x < D.L[0]; ++x) host_occ[s++] = (uint8_t)((row[x >> 4] >> ((x & 15) * 2)) & 3u);
+            }
+    return FKMC_OK;
+}
+
+int kmc_write_state(kmc_batch* b, int32_t r, const uint8_t* host_occ, size_t n)
+{
+    if (!valid_replica(b, r) || !host_occ) return fail(FKMC_EINVAL, "bad replica or input");
+    const RepDesc& D = b->desc[r];
+    if ((int64_t)n != D.nsite) return fail(FKMC_EINVAL, "n must equal 3 nx ny nz");
+    const int64_t words = 3 * (int64_t)D.L[2] * D.L[1] * D.row_words;
+    const int64_t nfrag = (int64_t)D.nf[0] * D.nf[1] * D.nf[2];
+    std::vector<uint32_t> w(words, 0u);
+    std::vector<int32_t> cnt(nfrag, 0);
+    std::vector<VacRec> rec((size_t)nfrag * b->cap);
+    int64_t s = 0, nv = 0, nh = 0;
+    for (int t = 0; t < 3; ++t)
+        for (int z = 0; z < D.L[2]; ++z)
+            for (int y = 0; y < D.L[1]; ++y) {
+                uint32_t* row = w.data() + (((int64_t)t * D.L[2] + z) * D.L[1] + y) * D.row_words;
+                for (int x = 0; x < D.L[0]; ++x, ++s) {
+                    const uint8_t c = host_occ[s];
+                    if (c > 2) return fail(FKMC_EINVAL, "species codes must be 0, 1 or 2");
+                    row[x >> 4] |= (uint32_t)c << ((x & 15) * 2);
+                    if (c == FKMC_H) ++nh;
+                    if (c != FKMC_V) continue;
+                    int f[3];
+                    const int cc[3] = {x, y, z};
+                    for (int d = 0; d < 3; ++d) {
+                        const int big = D.rem[d] * (D.base[d] + 1);
+                        f[d] = cc[d] < big ? cc[d] / (D.base[d] + 1) : D.rem[d] + (cc[d] - big) / D.base[d];
+                    }
+                    const int64_t g = ((int64_t)f[2] * D.nf[1] + f[1]) * D.nf[0] + f[0];
+                    if (cnt[g] >= b->cap) return fail(FKMC_EOVERFLOW, "a fragment would exceed cap_v vacancies");
+                    VacRec& v = rec[g * b->cap + cnt[g]++];
+                    v.key = ((uint64_t)t << 48) | ((uint64_t)z << 32) | ((uint64_t)y << 16) | (uint64_t)x;
+                    v.d[0] = v.d[1] = v.d[2] = 0;
+                    v.id = (uint32_t)nv++;
+                }
+            }
+    CK(cudaMemcpyAsync(b->occ + D.occ_word_off, w.data(), sizeof(uint32_t) * words, cudaMemcpyHostToDevice,
+                       b->st),
+       "state upload");
+    CK(cudaMemcpyAsync(b->counts + D.frag_base, cnt.data(), sizeof(int32_t) * nfrag, cudaMemcpyHostToDevice,
+                       b->st),
+       "count upload");
+    CK(cudaMemcpyAsync(b->recs + D.frag_base * b->cap, rec.data(), sizeof(VacRec) * rec.size(),
+                       cudaMemcpyHostToDevice, b->st),
+       "record upload");
+    if (b->tracer)
+        CK(cudaMemsetAsync(b->tracer + 3 * D.site_off, 0, sizeof(int32_t) * 3 * D.nsite, b->st), "memset");
+    CK(cudaStreamSynchronize(b->st), "synchronize");
+    b->n_vac[r] = nv;
+    b->n_H[r] = nh;
+    return FKMC_OK;
+}
+
+int kmc_read_records(kmc_batch* b, int32_t r, int64_t* rows, int64_t max_rows, int64_t* n_rows)
+{
+    if (!valid_replica(b, r) || (!rows && max_rows > 0)) return fail(FKMC_EINVAL, "bad replica or output");
+    const RepDesc& D = b->desc[r];
+    const int64_t nfrag = (int64_t)D.nf[0] * D.nf[1] * D.nf[2];
+    std::vector<int32_t> cnt(nfrag);
+    std::vector<VacRec> rec((size_t)nfrag * b->cap);
+    CK(cudaMemcpyAsync(cnt.data(), b->counts + D.frag_base, sizeof(int32_t) * nfrag, cudaMemcpyDeviceToHost,
+                       b->st),
+       "count copy");
+    CK(cudaMemcpyAsync(rec.data(), b->recs + D.frag_base * b->cap, sizeof(VacRec) * rec.size(),
+                       cudaMemcpyDeviceToHost, b->st),
+       "record copy");
+    CK(cudaStreamSynchronize(b->st), "synchronize");
+    int64_t k = 0, total = 0;
+    for (int64_t f = 0; f < nfrag; ++f) {
+        const int c = std::min(cnt[f], b->cap);
+        total += c;
+        std::vector<std::pair<int64_t, int>> lst;
+        for (int m = 0; m < c; ++m) {
+            const VacRec& v = rec[f * b->cap + m];
+            const int64_t x = v.key & 0xffff, y = (v.key >> 16) & 0xffff, z = (v.key >> 32) & 0xffff,
+                          t = (int64_t)(v.key >> 48);
+            lst.push_back({((t * D.L[2] + z) * D.L[1] + y) * D.L[0] + x, m});
+        }
+        std::sort(lst.begin(), lst.end());
+        for (auto& pr : lst) {
+            if (k >= max_rows) break;
+            const VacRec& v = rec[f * b->cap + pr.second];
+            int64_t* o = rows + 6 * k++;
+            o[0] = f;
+            o[1] = pr.first;
+            o[2] = v.d[0];
+            o[3] = v.d[1];
+            o[4] = v.d[2];
+            o[5] = v.id;
+        }
+    }
+    if (n_rows) *n_rows = total;
+    return FKMC_OK;
+}
+
+int kmc_read_tracer(kmc_batch* b, int32_t r, int32_t* host_disp, size_t n_sites)
+{
+    if (!valid_replica(b, r) || !host_disp) return fail(FKMC_EINVAL, "bad replica or output");
+    if (!b->tracer) return fail(FKMC_ESTATE, "tracer mode is off");
+    const RepDesc& D = b->desc[r];
+    if ((int64_t)n_sites != D.nsite) return fail(FKMC_EINVAL, "n_sites must equal 3 nx ny nz");
+    CK(cudaMemcpyAsync(host_disp, b->tracer + 3 * D.site_off, sizeof(int32_t) * 3 * D.nsite,
+                       cudaMemcpyDeviceToHost, b->st),
+       "tracer copy");
+    CK(cudaStreamSynchronize(b->st), "synchronize");
+    return FKMC_OK;
+}
+
+int kmc_state_bytes(kmc_batch* b, size_t* bytes)
+{
+    if (!b || !bytes) return fail(FKMC_EINVAL, "null argument");
+    *bytes = sizeof(uint32_t) * b->occ_words + sizeof(VacRec) * b->nfrag_total * b->cap +
+             sizeof(int32_t) * b->nfrag_total;
+    return FKMC_OK;
+}
+
+int kmc_download_state(kmc_batch* b, void* host, size_t bytes)
+{
+    size_t need = 0;
+    int rc = kmc_state_bytes(b, &need);
+    if (rc) return rc;
+    if (!host || bytes != need) return fail(FKMC_EINVAL, "buffer size must equal kmc_state_bytes");
+    char* h = (char*)host;
+    const size_t a = sizeof(uint32_t) * b->occ_words, c = sizeof(VacRec) * b->nfrag_total * b->cap;
+    CK(cudaMemcpyAsync(h, b->occ, a, cudaMemcpyDeviceToHost, b->st), "state copy");
+    CK(cudaMemcpyAsync(h + a, b->recs, c, cudaMemcpyDeviceToHost, b->st), "state copy");
+    CK(cudaMemcpyAsync(h + a + c, b->counts, sizeof(int32_t) * b->nfrag_total, cudaMemcpyDeviceToHost, b->st),
+       "state copy");
+    CK(cudaStreamSynchronize(b->st), "synchronize");
+    return FKMC_OK;
+}
+
+int kmc_upload_state(kmc_batch* b, const void* host, size_t bytes)
+{
+    size_t need = 0;
+    int rc = kmc_state_bytes(b, &need);
+    if (rc) return rc;
+    if (!host || bytes != need) return fail(FKMC_EINVAL, "buffer size must equal kmc_state_bytes");
+    const char* h = (const char*)host;
+    const size_t a = sizeof(uint32_t) * b->occ_words, c = sizeof(VacRec) * b->nfrag_total * b->cap;
+    CK(cudaMemcpyAsync(b->occ, h, a, cudaMemcpyHostToDevice, b->st), "state upload");
+    CK(cudaMemcpyAsync(b->recs, h + a, c, cudaMemcpyHostToDevice, b->st), "state upload");
+    CK(cudaMemcpyAsync(b->counts, h + a + c, sizeof(int32_t) * b->nfrag_total, cudaMemcpyHostToDevice, b->st),
+       "state upload");
+    CK(cudaStreamSynchronize(b->st), "synchronize");
+    return FKMC_OK;
+}
+
+int kmc_get_replica_info(kmc_batch* b, int32_t r, kmc_replica_info* out)
+{
+    if (!valid_replica(b, r) || !out) return fail(FKMC_EINVAL, "bad replica or output");
+    const RepDesc& D = b->desc[r];
+    std::memset(out, 0, sizeof *out);
+    for (int d = 0; d < 3; ++d) out->nfrag[d] = D.nf[d];
+    out->cap_v = b->cap;
+    out->F = D.F;
+    out->precision = b->opts.precision;
+    out->tau = D.tau;
+    out->theta_tau = D.theta_tau;
+    for (int i = 0; i < 6; ++i) {
+        out->k64[i] = D.k64[i];
+        out->q[i] = D.q[i];
+    }
+    out->window = D.window;
+    out->hops = b->stats_host[2 * r];
+    out->handoffs = b->stats_host[2 * r + 1];
+    out->nsite = D.nsite;
+    out->n_vac = b->n_vac[r];
+    out->n_H = b->n_H[r];
+    return FKMC_OK;
+}
+
+int32_t kmc_num_replicas(const kmc_batch* b) { return b ? b->n : 0; }
+
+int kmc_destroy(kmc_batch* b)
+{
+    if (!b) return FKMC_OK;
+    if (b->st) cudaStreamSynchronize(b->st);
+    else cudaDeviceSynchronize();
+    b->release();
+    delete b;
+    return FKMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,193 @@
+// fkmc_device.cuh -- device-side definitions of the fragment kMC library:
+// replica descriptors, Philox4x64-10, the two series logarithms that feed
+// the residence-time clock (Eq. TimeStep of arXiv:2004.09081), the O-sublattice
+// geometry and the fragment partition.
+//
+// Every floating-point operation in this file is written as an explicit
+// round-to-nearest intrinsic (__dadd_rn, __fmul_rn, ...) so that no
+// multiply-add is fused and each result is one IEEE operation in the order
+// written.
+#pragma once
+#include <cstdint>
+
+namespace fkmc {
+
+constexpr int SP_O = 0, SP_H = 1, SP_V = 2;
+constexpr uint32_t PURPOSE_INIT = 1u, PURPOSE_PERM = 2u, PURPOSE_HOP = 3u;
+constexpr uint32_t STATUS_OVERFLOW = 1u, STATUS_TIMEOUT = 2u, STATUS_EVENT_LIMIT = 4u;
+// Hard bound on the events one fragment may execute in one colour phase
+// (about 2.5e5 x the expected count at n_tau <= 64); reaching it ends the
+// phase and reports an error instead of running on.
+constexpr uint64_t MAX_EVENTS_PER_PHASE = 1ull << 24;
+
+// One vacancy record: site key (t<<48 | z<<32 | y<<16 | x, so that key order
+// is linear site order), unwrapped displacement in units of a/2, id.
+struct __align__(8) VacRec {
+    uint64_t key;
+    int32_t d[3];
+    uint32_t id;
+};
+static_assert(sizeof(VacRec) == 24, "record layout");
+
+// Per-replica descriptor (device copy is read-only inside kernels).
+struct RepDesc {
+    int32_t L[3];          // cells per dimension
+    int32_t nf[3];         // fragments per dimension (1 or even)
+    int32_t base[3];       // L / nf
+    int32_t rem[3];        // L % nf: the first `rem` fragments are one cell longer
+    int32_t row_words;     // 32-bit words per occupancy row (16 sites per word)
+    int32_t F;             // fixed-point fraction bits (mixed form)
+    int32_t items;         // work items per colour phase = prod ceil(nf/2)
+    uint32_t replica;
+    int64_t items_off;     // prefix of `items` over replicas
+    int64_t frag_base;     // first fragment of this replica in batch-wide arrays
+    int64_t occ_word_off;  // first occupancy word of this replica
+    int64_t site_off;      // first site of this replica (tracer field)
+    int64_t nsite;
+    uint64_t seed;
+    uint64_t window;       // windows completed before the current run
+    double k64[6];         // FP64 rate table, index 3*h + dz + 1
+    uint64_t q[6];         // fixed-point rate table
+    double tau;            // window length (s), plain clock
+    double theta_tau;      // window length in units of 1/k32max, mixed clock
+    double two_pow_F;      // 2^F, exact
+};
+
+// ---------------------------------------------------------------- Philox
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the
+// multiply S-box on words 0 and 2 with the two published multipliers, Weyl
+// key increments (golden ratio, sqrt(3)-1) between rounds.
+struct U64x4 {
+    uint64_t x[4];
+};
+
+__device__ __forceinline__ U64x4 philox4x64(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                             uint64_t k0, uint64_t k1)
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+        const uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+        const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += W0; k1 += W1;
+    }
+    U64x4 o;
+    o.x[0] = c0; o.x[1] = c1; o.x[2] = c2; o.x[3] = c3;
+    return o;
+}
+
+__device__ __forceinline__ uint64_t key_word(uint32_t replica, uint32_t purpose)
+{
+    return ((uint64_t)replica << 8) | purpose;
+}
+
+// ---------------------------------------------------------------- logs
+// -ln u from the atanh series ln m = 2 (s + s^3/3 + s^5/5 + ...),
+// s = (m-1)/(m+1), m in [sqrt(1/2), sqrt(2)) (Abramowitz & Stegun 4.1.27),
+// with u = m 2^e.
+
+// FP64 form: u = (2 floor(x/2^12) + 1) 2^-53, exactly representable in (0,1).
+__device__ __forceinline__ double neglog64(uint64_t x)
+{
+    const double u = __dmul_rn(__ull2double_rn(2ull * (x >> 12) + 1ull), 0x1p-53);
+    const uint64_t bits = (uint64_t)__double_as_longlong(u);
+    int e = (int)((bits >> 52) & 0x7ffull) - 1022;
+    double m = __longlong_as_double((long long)((bits & 0x000fffffffffffffull) | 0x3fe0000000000000ull));
+    if (m < 0.70710678118654752440) {
+        m = __dmul_rn(m, 2.0);
+        e -= 1;
+    }
+    const double s = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
+    const double s2 = __dmul_rn(s, s);
+    double p = 2.0 / 21.0;
+    p = __dadd_rn(2.0 / 19.0, __dmul_rn(s2, p));
+    p = __dadd_rn(2.0 / 17.0, __dmul_rn(s2, p));
+    p = __dadd_rn(2.0 / 15.0, __dmul_rn(s2, p));
+    p = __dadd_rn(2.0 / 13.0, __dmul_rn(s2, p));
+    p = __dadd_rn(2.0 / 11.0, __dmul_rn(s2, p));
+    p = __dadd_rn(2.0 / 9.0, __dmul_rn(s2, p));
+    p = __dadd_rn(2.0 / 7.0, __dmul_rn(s2, p));
+    p = __dadd_rn(2.0 / 5.0, __dmul_rn(s2, p));
+    p = __dadd_rn(2.0 / 3.0, __dmul_rn(s2, p));
+    p = __dadd_rn(2.0, __dmul_rn(s2, p));
+    const double lnm = __dmul_rn(s, p);
+    const double ln_u = __dadd_rn(__dmul_rn(__int2double_rn(e), 0.69314718055994530942), lnm);
+    return -ln_u;
+}
+
+// FP32 form over the full 64-bit range: the leading one of (x|1) gives the
+// binary exponent, the next 22 bits and a forced midpoint bit the mantissa.
+__device__ __forceinline__ float neglog32(uint64_t x)
+{
+    x |= 1ull;
+    const int lz = __clzll((long long)x);
+    const int p = 63 - lz;
+    const uint64_t nx = x << lz;
+    const uint32_t mant = (uint32_t)(nx >> 40) | 1u;
+    float m = __fmul_rn(__uint2float_rn(mant), 0x1p-23f);
+    int e = p - 64;
+    if (m > 1.41421356f) {
+        m = __fmul_rn(m, 0.5f);
+        e += 1;
+    }
+    const float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    const float s2 = __fmul_rn(s, s);
+    float q = 2.0f / 9.0f;
+    q = __fadd_rn(2.0f / 7.0f, __fmul_rn(s2, q));
+    q = __fadd_rn(2.0f / 5.0f, __fmul_rn(s2, q));
+    q = __fadd_rn(2.0f / 3.0f, __fmul_rn(s2, q));
+    q = __fadd_rn(2.0f, __fmul_rn(s2, q));
+    const float lnm = __fmul_rn(s, q);
+    const float ln_u = __fadd_rn(__fmul_rn(__int2float_rn(e), 0.693147182f), lnm);
+    return -ln_u;
+}
+
+// ---------------------------------------------------------------- geometry
+// Neighbour table in constant memory, filled by the host at load time:
+// for site type t and neighbour n (ascending (dx,dy,dz)): packed
+// {t2, dcx, dcy, dcz, dx, dy, dz} as signed bytes in two words.
+struct NbEntry {
+    int8_t t2, dc[3], d[3], pad;
+};
+
+__device__ __forceinline__ int wrapc(int c, int L)
+{
+    return c < 0 ? c + L : (c >= L ? c - L : c);
+}
+
+__device__ __forceinline__ int frag_start(int i, int base, int rem)
+{
+    return i * base + min(i, rem);
+}
+
+__device__ __forceinline__ int frag_of(int c, int base, int rem)
+{
+    const int big = rem * (base + 1);
+    return c < big ? c / (base + 1) : rem + (c - big) / base;
+}
+
+__device__ __forceinline__ uint64_t make_key(int t, int x, int y, int z)
+{
+    return ((uint64_t)t << 48) | ((uint64_t)z << 32) | ((uint64_t)y << 16) | (uint64_t)x;
+}
+
+__device__ __forceinline__ void split_key(uint64_t k, int& t, int& x, int& y, int& z)
+{
+    x = (int)(k & 0xffff);
+    y = (int)((k >> 16) & 0xffff);
+    z = (int)((k >> 32) & 0xffff);
+    t = (int)(k >> 48);
+}
+
+// word index (within the batch occupancy array) and bit shift of a site
+__device__ __forceinline__ int64_t occ_word(const RepDesc& D, int t, int x, int y, int z)
+{
+    return D.occ_word_off + (((int64_t)t * D.L[2] + z) * D.L[1] + y) * D.row_words + (x >> 4);
+}
+
+__device__ __forceinline__ int occ_shift(int x) { return (x & 15) * 2; }
+
+}  // namespace fkmc

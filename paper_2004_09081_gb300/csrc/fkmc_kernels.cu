@@ -1,0 +1,585 @@
+// fkmc_kernels.cu -- sm_103a kernels of the fragment kMC library.
+//
+//   k_init       placement of vacancies and H- (keyed Feistel bijection)
+//   k_phase      one colour phase: every fragment of the phase's colour runs
+//                BKL on its own vacancies until its next event would pass the
+//                window length (arXiv:2004.09081 Sec. II.A Eqs. RateCnst1,
+//                eventSelection, TimeStep; fragment-local selection Sec. II.B
+//                Eq. AtomP).  One warp per fragment.
+//   k_moments_*  exact integer displacement moments (Sec. III: D from tracked
+//                trajectories).
+#include <cuda_runtime.h>
+
+#include "fkmc_device.cuh"
+#include "fkmc_kernels.h"
+
+namespace fkmc {
+
+__constant__ NbEntry c_nb[3][8];
+
+// ------------------------------------------------------------------ init
+__global__ void k_init(RepDesc D, int b_bits, int64_t n_vac, int64_t n_total, uint32_t* occ,
+                       VacRec* recs, int32_t* counts, int cap, uint32_t* status)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_total) return;
+    const uint64_t mask = (1ull << b_bits) - 1ull;
+    const uint64_t k0 = D.seed, k1 = key_word(D.replica, PURPOSE_INIT);
+    uint64_t v = (uint64_t)i;
+    do {
+        uint64_t Lh = v >> b_bits, Rh = v & mask;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const U64x4 o = philox4x64(Rh, (uint64_t)k, 0, 0, k0, k1);
+            const uint64_t nr = Lh ^ (o.x[0] & mask);
+            Lh = Rh;
+            Rh = nr;
+        }
+        v = (Lh << b_bits) | Rh;
+    } while (v >= (uint64_t)D.nsite);
+    const int x = (int)(v % D.L[0]);
+    const int y = (int)((v / D.L[0]) % D.L[1]);
+    const int z = (int)((v / ((uint64_t)D.L[0] * D.L[1])) % D.L[2]);
+    const int t = (int)(v / ((uint64_t)D.L[0] * D.L[1] * D.L[2]));
+    const uint32_t code = i < n_vac ? (uint32_t)SP_V : (uint32_t)SP_H;
+    atomicOr(occ + occ_word(D, t, x, y, z), code << occ_shift(x));
+    if (i < n_vac) {
+        const int fx = frag_of(x, D.base[0], D.rem[0]);
+        const int fy = frag_of(y, D.base[1], D.rem[1]);
+        const int fz = frag_of(z, D.base[2], D.rem[2]);
+        const int64_t g = D.frag_base + ((int64_t)fz * D.nf[1] + fy) * D.nf[0] + fx;
+        const int slot = atomicAdd(counts + g, 1);
+        if (slot < cap) {
+            VacRec r;
+            r.key = make_key(t, x, y, z);
+            r.d[0] = r.d[1] = r.d[2] = 0;
+            r.id = (uint32_t)i;
+            recs[g * cap + slot] = r;
+        } else {
+            atomicOr(status, STATUS_OVERFLOW);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ phase
+template <int PREC>
+struct Arith;
+
+// FP64 plain form: rates are doubles, prefix sums in the canonical order.
+template <>
+struct Arith<0> {
+    using V = double;
+    static __device__ __forceinline__ V zero() { return 0.0; }
+    static __device__ __forceinline__ V add(V a, V b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ V rate(const RepDesc& D, int ty) { return ty < 0 ? 0.0 : D.k64[ty]; }
+    static __device__ __forceinline__ V shfl_up(V v, int off) { return __shfl_up_sync(0xffffffffu, v, off); }
+    static __device__ __forceinline__ V shfl(V v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+    static __device__ __forceinline__ bool pos(V v) { return v > 0.0; }
+};
+
+// Mixed form: u64 fixed-point rates, exact integer sums.
+template <>
+struct Arith<1> {
+    using V = unsigned long long;
+    static __device__ __forceinline__ V zero() { return 0ull; }
+    static __device__ __forceinline__ V add(V a, V b) { return a + b; }
+    static __device__ __forceinline__ V rate(const RepDesc& D, int ty) { return ty < 0 ? 0ull : (V)D.q[ty]; }
+    static __device__ __forceinline__ V shfl_up(V v, int off) { return __shfl_up_sync(0xffffffffu, v, off); }
+    static __device__ __forceinline__ V shfl(V v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+    static __device__ __forceinline__ bool pos(V v) { return v != 0ull; }
+};
+
+// Inclusive Kogge-Stone scan over the 32 lanes (strides 1,2,4,8,16), the
+// canonical order of the plain form's partial sums.
+template <int PREC>
+__device__ __forceinline__ typename Arith<PREC>::V warp_scan(typename Arith<PREC>::V v, int lane)
+{
+    using A = Arith<PREC>;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const typename A::V t = A::shfl_up(v, off);
+        if (lane >= off) v = A::add(v, t);
+    }
+    return v;
+}
+
+// Colour processed in `phase` of window w: Fisher-Yates shuffle of 0..7 with
+// j = mulhi(y_k, i+1), y_0..y_7 = Philox blocks (w,0) and (w,1).
+__device__ __forceinline__ int colour_of_phase(uint64_t seed, uint32_t replica, uint64_t w, int phase,
+                                               int lane)
+{
+    const U64x4 blk = philox4x64(w, (uint64_t)(lane & 1), 0, 0, seed, key_word(replica, PURPOSE_PERM));
+    uint32_t perm = 0x76543210u;  // nibble i holds perm[i]
+#pragma unroll
+    for (int i = 7; i >= 1; --i) {
+        const int k = 7 - i;
+        const uint64_t mine = blk.x[k & 3];
+        const uint64_t y = __shfl_sync(0xffffffffu, mine, k >> 2);
+        const int j = (int)__umul64hi(y, (uint64_t)(i + 1));
+        const uint32_t pi = (perm >> (4 * i)) & 15u, pj = (perm >> (4 * j)) & 15u;
+        perm &= ~((15u << (4 * i)) | (15u << (4 * j)));
+        perm |= (pj << (4 * i)) | (pi << (4 * j));
+    }
+    return (int)((perm >> (4 * phase)) & 15u);
+}
+
+struct WarpSmem {
+    VacRec* rec;     // [cap] records as loaded (slot data lives here)
+    uint16_t* order; // [cap] slot m -> index into rec
+    int8_t* types;   // [8*cap] rate type of event e, -1 = no event
+    uint8_t* alive;  // [cap]
+};
+
+__device__ __forceinline__ WarpSmem carve(unsigned char* base, int cap)
+{
+    WarpSmem s;
+    s.rec = reinterpret_cast<VacRec*>(base);
+    s.order = reinterpret_cast<uint16_t*>(base + 24 * cap);
+    s.types = reinterpret_cast<int8_t*>(base + 26 * cap);
+    s.alive = reinterpret_cast<uint8_t*>(base + 34 * cap);
+    return s;
+}
+
+__host__ __device__ inline size_t warp_smem_bytes(int cap) { return (size_t)((35 * cap + 15) / 16) * 16; }
+
+// Rate types of every event of the fragment, read from the occupancy words
+// in L2 (ld.global.cg, so that this warp's own exchanges are seen).
+__device__ __forceinline__ void compute_types(const RepDesc& D, const uint32_t* occ, const WarpSmem& S,
+                                              int nslots, int nch, int lane)
+{
+    for (int c = 0; c < nch; ++c) {
+        const int e = c * 32 + lane;
+        const int m = e >> 3, n = e & 7;
+        int ty = -1;
+        if (m < nslots && S.alive[m]) {
+            int t, x, y, z;
+            split_key(S.rec[S.order[m]].key, t, x, y, z);
+            const NbEntry nb = c_nb[t][n];
+            const int jx = wrapc(x + nb.dc[0], D.L[0]);
+            const int jy = wrapc(y + nb.dc[1], D.L[1]);
+            const int jz = wrapc(z + nb.dc[2], D.L[2]);
+            const uint32_t w = __ldcg(occ + occ_word(D, nb.t2, jx, jy, jz));
+            const int code = (int)((w >> occ_shift(jx)) & 3u);
+            ty = code == SP_V ? -1 : code * 3 + nb.d[2] + 1;
+        }
+        S.types[e] = (int8_t)ty;
+    }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(128) k_phase(const RepDesc* __restrict__ descs, int nrep,
+                                               int64_t total_items, int phase, uint64_t wk,
+                                               uint32_t* occ, VacRec* recs, int32_t* counts,
+                                               int32_t* tracer, unsigned long long* stats,
+                                               uint32_t* status, int cap)
+{
+    using A = Arith<PREC>;
+    using V = typename A::V;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    if (item >= total_items) return;
+
+    // replica of this item
+    int lo = 0, hi = nrep - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (descs[mid].items_off <= item) lo = mid; else hi = mid - 1;
+    }
+    const RepDesc& D = descs[lo];
+    const int64_t local = item - D.items_off;
+    const uint64_t w = D.window + wk;
+    const int colour = colour_of_phase(D.seed, D.replica, w, phase, lane);
+
+    // fragment of the colour class
+    int cnt[3], bit[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        bit[d] = (colour >> d) & 1;
+        cnt[d] = D.nf[d] == 1 ? (bit[d] == 0 ? 1 : 0) : D.nf[d] / 2;
+    }
+    if (local >= (int64_t)cnt[0] * cnt[1] * cnt[2]) return;
+    int f[3];
+    f[0] = (int)(local % cnt[0]);
+    f[1] = (int)((local / cnt[0]) % cnt[1]);
+    f[2] = (int)(local / ((int64_t)cnt[0] * cnt[1]));
+    int lo_c[3], hi_c[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        f[d] = D.nf[d] == 1 ? 0 : 2 * f[d] + bit[d];
+        lo_c[d] = frag_start(f[d], D.base[d], D.rem[d]);
+        hi_c[d] = frag_start(f[d] + 1, D.base[d], D.rem[d]);
+    }
+    const int64_t fid = ((int64_t)f[2] * D.nf[1] + f[1]) * D.nf[0] + f[0];
+    const int64_t g = D.frag_base + fid;
+
+    int nv = counts[g];
+    if (nv == 0) return;
+    if (nv > cap) {
+        if (lane == 0) atomicOr(status, STATUS_OVERFLOW);
+        nv = cap;
+    }
+    WarpSmem S = carve(smem + warp_smem_bytes(cap) * wib, cap);
+
+    // slots: the fragment's records in ascending site order
+    for (int k = lane; k < nv; k += 32) S.rec[k] = recs[g * cap + k];
+    __syncwarp();
+    for (int k = lane; k < nv; k += 32) {
+        const uint64_t mk = S.rec[k].key;
+        int rank = 0;
+        for (int o = 0; o < nv; ++o) rank += S.rec[o].key < mk;
+        S.order[rank] = (uint16_t)k;
+        S.alive[rank] = 1;
+    }
+    __syncwarp();
+    const int nslots = nv;
+    const int nch = (nslots + 3) >> 2;  // 32 events per chunk
+    compute_types(D, occ, S, nslots, nch, lane);
+    __syncwarp();
+
+    const uint64_t hop_k1 = key_word(D.replica, PURPOSE_HOP);
+    // draws for events [64*batch, 64*batch+64): lane l holds Philox block 32*batch + l
+    uint64_t batch = ~0ull;
+    uint64_t xs_even = 0, xs_odd = 0;
+    double Ed_even = 0.0, Ed_odd = 0.0;
+    float Ef_even = 0.f, Ef_odd = 0.f;
+
+    double clock = 0.0;
+    uint64_t i = 0;
+    uint32_t nhand = 0;
+    for (;;) {
+        // totals: canonical scan over chunks with a running carry
+        V carry = A::zero();
+        V Plast = A::zero();
+        for (int c = 0; c < nch; ++c) {
+            const V v = A::rate(D, S.types[c * 32 + lane]);
+            const V p = A::add(carry, warp_scan<PREC>(v, lane));
+            carry = A::shfl(p, 31);
+            Plast = p;
+        }
+        const V total = carry;
+        if (!A::pos(total)) break;
+        if (i >= MAX_EVENTS_PER_PHASE) {
+            if (lane == 0) atomicOr(status, STATUS_EVENT_LIMIT);
+            break;
+        }
+
+        if ((i >> 6) != batch) {
+            batch = i >> 6;
+            const U64x4 blk = philox4x64(g - D.frag_base, w, 32 * batch + lane, 0, D.seed, hop_k1);
+            xs_even = blk.x[1];
+            xs_odd = blk.x[3];
+            if constexpr (PREC == 0) {
+                Ed_even = neglog64(blk.x[0]);
+                Ed_odd = neglog64(blk.x[2]);
+            } else {
+                Ef_even = neglog32(blk.x[0]);
+                Ef_odd = neglog32(blk.x[2]);
+            }
+        }
+        const int src = (int)((i >> 1) & 31);
+        const bool odd = (i & 1) != 0;
+        const uint64_t xs = __shfl_sync(0xffffffffu, odd ? xs_odd : xs_even, src);
+
+        double dclock;
+        int e_sel = -1;
+        if constexpr (PREC == 0) {
+            const double R = (double)total;
+            const double E = __shfl_sync(0xffffffffu, odd ? Ed_odd : Ed_even, src);
+            const double dt = __ddiv_rn(E, R);
+            if (__dadd_rn(clock, dt) > D.tau) break;
+            dclock = dt;
+            const double target = __dmul_rn(__dmul_rn(__ull2double_rn(xs >> 11), 0x1p-53), R);
+            // first event with a nonzero rate whose prefix exceeds the target
+            double cc = 0.0;
+            for (int c = 0; c < nch; ++c) {
+                double p;
+                const double v = Arith<0>::rate(D, S.types[c * 32 + lane]);
+                if (nch == 1) {
+                    p = (double)Plast;
+                } else {
+                    p = __dadd_rn(cc, warp_scan<0>(v, lane));
+                    cc = __shfl_sync(0xffffffffu, p, 31);
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, v > 0.0 && p > target);
+                if (bal) {
+                    e_sel = c * 32 + __ffs(bal) - 1;
+                    break;
+                }
+            }
+            if (e_sel < 0) {  // rounding left no prefix above the target: last nonzero event
+                for (int c = nch - 1; c >= 0 && e_sel < 0; --c) {
+                    const unsigned bal =
+                        __ballot_sync(0xffffffffu, Arith<0>::rate(D, S.types[c * 32 + lane]) > 0.0);
+                    if (bal) e_sel = c * 32 + 31 - __clz(bal);
+                }
+            }
+        } else {
+            const unsigned long long Sq = (unsigned long long)total;
+            const float E = __shfl_sync(0xffffffffu, odd ? Ef_odd : Ef_even, src);
+            const float ratio = __fdiv_rn(E, __ull2float_rn(Sq));
+            const double dth = __dmul_rn((double)ratio, D.two_pow_F);
+            if (__dadd_rn(clock, dth) > D.theta_tau) break;
+            dclock = dth;
+            const unsigned long long target = __umul64hi(xs, Sq);
+            unsigned long long cc = 0ull;
+            for (int c = 0; c < nch; ++c) {
+                const unsigned long long v = Arith<1>::rate(D, S.types[c * 32 + lane]);
+                unsigned long long p;
+                if (nch == 1) {
+                    p = (unsigned long long)Plast;
+                } else {
+                    p = cc + warp_scan<1>(v, lane);
+                    cc = __shfl_sync(0xffffffffu, p, 31);
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, p > target);
+                if (bal) {
+                    e_sel = c * 32 + __ffs(bal) - 1;
+                    break;
+                }
+            }
+        }
+
+        // apply the exchange (lane 0 writes; the rest of the warp waits)
+        if (lane == 0) {
+            const int m = e_sel >> 3, n = e_sel & 7;
+            VacRec& r = S.rec[S.order[m]];
+            int t, x, y, z;
+            split_key(r.key, t, x, y, z);
+            const NbEntry nb = c_nb[t][n];
+            const int jx = wrapc(x + nb.dc[0], D.L[0]);
+            const int jy = wrapc(y + nb.dc[1], D.L[1]);
+            const int jz = wrapc(z + nb.dc[2], D.L[2]);
+            const uint32_t ion = (uint32_t)(S.types[e_sel] / 3);
+            atomicXor(occ + occ_word(D, t, x, y, z), ((uint32_t)SP_V ^ ion) << occ_shift(x));
+            atomicXor(occ + occ_word(D, nb.t2, jx, jy, jz), (ion ^ (uint32_t)SP_V) << occ_shift(jx));
+            r.d[0] += nb.d[0];
+            r.d[1] += nb.d[1];
+            r.d[2] += nb.d[2];
+            if (tracer) {
+                const int64_t s_lin = (((int64_t)t * D.L[2] + z) * D.L[1] + y) * D.L[0] + x;
+                const int64_t j_lin = (((int64_t)nb.t2 * D.L[2] + jz) * D.L[1] + jy) * D.L[0] + jx;
+                int32_t* ts = tracer + 3 * (D.site_off + s_lin);
+                int32_t* tj = tracer + 3 * (D.site_off + j_lin);
+                ts[0] = tj[0] - nb.d[0];
+                ts[1] = tj[1] - nb.d[1];
+                ts[2] = tj[2] - nb.d[2];
+                tj[0] = tj[1] = tj[2] = 0;
+            }
+            r.key = make_key(nb.t2, jx, jy, jz);
+            const bool owned = jx >= lo_c[0] && jx < hi_c[0] && jy >= lo_c[1] && jy < hi_c[1] &&
+                               jz >= lo_c[2] && jz < hi_c[2];
+            if (!owned) {
+                const int gx = frag_of(jx, D.base[0], D.rem[0]);
+                const int gy = frag_of(jy, D.base[1], D.rem[1]);
+                const int gz = frag_of(jz, D.base[2], D.rem[2]);
+                const int64_t g2 = D.frag_base + ((int64_t)gz * D.nf[1] + gy) * D.nf[0] + gx;
+                const int slot = atomicAdd(counts + g2, 1);
+                if (slot < cap) recs[g2 * cap + slot] = r;
+                else atomicOr(status, STATUS_OVERFLOW);
+                S.alive[m] = 0;
+                ++nhand;
+            }
+            __threadfence_block();
+        }
+        __syncwarp();
+        clock = __dadd_rn(clock, dclock);
+        ++i;
+        compute_types(D, occ, S, nslots, nch, lane);
+        __syncwarp();
+    }
+
+    // surviving records stay with the fragment
+    int base_pos = 0;
+    for (int c = 0; c * 32 < nslots; ++c) {
+        const int m = c * 32 + lane;
+        const bool keep = m < nslots && S.alive[m];
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) recs[g * cap + base_pos + __popc(bal & ((1u << lane) - 1u))] = S.rec[S.order[m]];
+        base_pos += __popc(bal);
+    }
+    if (lane == 0) {
+        counts[g] = base_pos;
+        if (i) atomicAdd(stats + 2 * lo, (unsigned long long)i);
+        if (nhand) atomicAdd(stats + 2 * lo + 1, (unsigned long long)nhand);
+    }
+}
+
+// ------------------------------------------------------------------ moments
+// Vacancy records: out += {count, sum d, sum d^2} (two's-complement u64 atomics).
+__global__ void k_moments_vac(const VacRec* recs, const int32_t* counts, int64_t frag0, int64_t nfrag,
+                              int cap, unsigned long long* out)
+{
+    __shared__ unsigned long long acc[7];
+    if (threadIdx.x < 7) acc[threadIdx.x] = 0ull;
+    __syncthreads();
+    unsigned long long a[7] = {0, 0, 0, 0, 0, 0, 0};
+    const int64_t total = nfrag * cap;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t f = k / cap;
+        const int s = (int)(k % cap);
+        if (s < counts[frag0 + f]) {
+            const VacRec r = recs[(frag0 + f) * cap + s];
+            a[0] += 1ull;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                a[1 + d] += (unsigned long long)(long long)r.d[d];
+                a[4 + d] += (unsigned long long)((long long)r.d[d] * r.d[d]);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        unsigned long long v = a[q];
+        for (int off = 16; off; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(acc + q, v);
+    }
+    __syncthreads();
+    if (threadIdx.x < 7 && acc[threadIdx.x]) atomicAdd(out + threadIdx.x, acc[threadIdx.x]);
+}
+
+// Vacancy moments of every replica of the batch in one launch: one thread per
+// fragment slot, replica found from the fragment index; out[7 r + q].
+__global__ void k_moments_vac_all(const RepDesc* __restrict__ descs, int nrep, const VacRec* recs,
+                                  const int32_t* counts, int64_t nfrag_total, int cap,
+                                  unsigned long long* out)
+{
+    const int64_t total = nfrag_total * cap;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t f = k / cap;
+        const int s = (int)(k % cap);
+        if (s >= counts[f]) continue;
+        int lo = 0, hi = nrep - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (descs[mid].frag_base <= f) lo = mid; else hi = mid - 1;
+        }
+        const VacRec r = recs[f * cap + s];
+        unsigned long long* o = out + 7 * (int64_t)lo;
+        atomicAdd(o, 1ull);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (r.d[d]) {
+                atomicAdd(o + 1 + d, (unsigned long long)(long long)r.d[d]);
+                atomicAdd(o + 4 + d, (unsigned long long)((long long)r.d[d] * r.d[d]));
+            }
+        }
+    }
+}
+
+// Tracer field over the sites holding `species`.
+__global__ void k_moments_ion(RepDesc D, const uint32_t* occ, const int32_t* tracer, int species,
+                              unsigned long long* out)
+{
+    __shared__ unsigned long long acc[7];
+    if (threadIdx.x < 7) acc[threadIdx.x] = 0ull;
+    __syncthreads();
+    unsigned long long a[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < D.nsite;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(s % D.L[0]);
+        const int64_t rest = s / D.L[0];
+        const int y = (int)(rest % D.L[1]);
+        const int z = (int)((rest / D.L[1]) % D.L[2]);
+        const int t = (int)(rest / ((int64_t)D.L[1] * D.L[2]));
+        const uint32_t wv = occ[occ_word(D, t, x, y, z)];
+        if ((int)((wv >> occ_shift(x)) & 3u) != species) continue;
+        const int32_t* d = tracer + 3 * (D.site_off + s);
+        a[0] += 1ull;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            a[1 + k] += (unsigned long long)(long long)d[k];
+            a[4 + k] += (unsigned long long)((long long)d[k] * d[k]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        unsigned long long v = a[q];
+        for (int off = 16; off; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(acc + q, v);
+    }
+    __syncthreads();
+    if (threadIdx.x < 7 && acc[threadIdx.x]) atomicAdd(out + threadIdx.x, acc[threadIdx.x]);
+}
+
+// ------------------------------------------------------------------ launchers
+cudaError_t upload_neighbours(const NbEntry* host)
+{
+    return cudaMemcpyToSymbol(c_nb, host, sizeof(NbEntry) * 24);
+}
+
+cudaError_t launch_init(const RepDesc& D, int b_bits, int64_t n_vac, int64_t n_total, uint32_t* occ,
+                        VacRec* recs, int32_t* counts, int cap, uint32_t* status, cudaStream_t st)
+{
+    if (n_total <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int64_t blocks = (n_total + threads - 1) / threads;
+    k_init<<<(unsigned)blocks, threads, 0, st>>>(D, b_bits, n_vac, n_total, occ, recs, counts, cap,
+                                                 status);
+    return cudaGetLastError();
+}
+
+size_t phase_smem_bytes(int cap) { return warp_smem_bytes(cap) * 4; }
+
+cudaError_t phase_prepare(int cap)
+{
+    const int bytes = (int)phase_smem_bytes(cap);
+    cudaError_t e = cudaFuncSetAttribute(k_phase<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_phase<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+cudaError_t launch_phase(int prec, const RepDesc* d_descs, int nrep, int64_t total_items, int phase,
+                         uint64_t wk, uint32_t* occ, VacRec* recs, int32_t* counts, int32_t* tracer,
+                         unsigned long long* stats, uint32_t* status, int cap, cudaStream_t st)
+{
+    if (total_items <= 0) return cudaSuccess;
+    const int warps = 4;
+    const int64_t blocks = (total_items + warps - 1) / warps;
+    const size_t smem = phase_smem_bytes(cap);
+    if (prec == 0)
+        k_phase<0><<<(unsigned)blocks, 32 * warps, smem, st>>>(d_descs, nrep, total_items, phase, wk, occ,
+                                                               recs, counts, tracer, stats, status, cap);
+    else
+        k_phase<1><<<(unsigned)blocks, 32 * warps, smem, st>>>(d_descs, nrep, total_items, phase, wk, occ,
+                                                               recs, counts, tracer, stats, status, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const RepDesc& D, int species, const uint32_t* occ, const VacRec* recs,
+                           const int32_t* counts, const int32_t* tracer, int cap,
+                           unsigned long long* out, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, 7 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    const int threads = 256;
+    if (species == SP_V) {
+        const int64_t nfrag = (int64_t)D.nf[0] * D.nf[1] * D.nf[2];
+        int64_t blocks = (nfrag * cap + threads - 1) / threads;
+        if (blocks > 4096) blocks = 4096;
+        k_moments_vac<<<(unsigned)blocks, threads, 0, st>>>(recs, counts, D.frag_base, nfrag, cap, out);
+    } else {
+        int64_t blocks = (D.nsite + threads - 1) / threads;
+        if (blocks > 4096) blocks = 4096;
+        k_moments_ion<<<(unsigned)blocks, threads, 0, st>>>(D, occ, tracer, species, out);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments_all(const RepDesc* d_descs, int nrep, const VacRec* recs, const int32_t* counts,
+                               int64_t nfrag_total, int cap, unsigned long long* out, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, 7 * sizeof(unsigned long long) * nrep, st);
+    if (e != cudaSuccess) return e;
+    const int threads = 256;
+    int64_t blocks = (nfrag_total * cap + threads - 1) / threads;
+    if (blocks > 8 * 152) blocks = 8 * 152;
+    if (blocks < 1) blocks = 1;
+    k_moments_vac_all<<<(unsigned)blocks, threads, 0, st>>>(d_descs, nrep, recs, counts, nfrag_total, cap, out);
+    return cudaGetLastError();
+}
+
+}  // namespace fkmc

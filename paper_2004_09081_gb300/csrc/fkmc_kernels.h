@@ -1,0 +1,24 @@
+// fkmc_kernels.h -- host-side launchers of the kernels in fkmc_kernels.cu.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "fkmc_device.cuh"
+
+namespace fkmc {
+
+cudaError_t upload_neighbours(const NbEntry* host24);
+cudaError_t launch_init(const RepDesc& D, int b_bits, int64_t n_vac, int64_t n_total, uint32_t* occ,
+                        VacRec* recs, int32_t* counts, int cap, uint32_t* status, cudaStream_t st);
+size_t phase_smem_bytes(int cap);
+cudaError_t phase_prepare(int cap);
+cudaError_t launch_phase(int prec, const RepDesc* d_descs, int nrep, int64_t total_items, int phase,
+                         uint64_t wk, uint32_t* occ, VacRec* recs, int32_t* counts, int32_t* tracer,
+                         unsigned long long* stats, uint32_t* status, int cap, cudaStream_t st);
+cudaError_t launch_moments(const RepDesc& D, int species, const uint32_t* occ, const VacRec* recs,
+                           const int32_t* counts, const int32_t* tracer, int cap,
+                           unsigned long long* out, cudaStream_t st);
+
+cudaError_t launch_moments_all(const RepDesc* d_descs, int nrep, const VacRec* recs, const int32_t* counts,
+                               int64_t nfrag_total, int cap, unsigned long long* out, cudaStream_t st);
+
+}  // namespace fkmc

@@ -1,0 +1,101 @@
+"""Seeded synthetic workloads (input generators only; no kMC arithmetic).
+
+The paper's experiments use no public dataset; every input here is synthetic
+with the shapes of the paper's systems (Sec. Computational details):
+perovskite O sublattice, a = 3.905 A (SrTiO3) or 4.01 A (BaTiO3, from the
+641.6 nm / 1600-cell model of Sec. III), O-vacancy barriers 0.6 / 0.7 eV,
+A = 1e13 1/s.  Replica parameters of the batched workload are drawn from
+numpy's Philox generator keyed by the seed.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+A_SRTIO3 = 3.905
+A_BATIO3 = 4.01
+
+
+@dataclass
+class Replica:
+    cells: tuple
+    a: float
+    n_vac: int
+    n_H: int
+    T: float
+    Ea_O: float
+    Ea_H: float
+    field_z: float = 0.0
+    nfrag: tuple | None = None
+
+
+@dataclass
+class Workload:
+    name: str
+    replicas: list
+    edge: int = 4
+    precision: int = 0
+    tracer: bool = False
+    windows: int = 1
+    notes: dict = field(default_factory=dict)
+
+
+def round_half_up(v: float) -> int:
+    return int(np.floor(v + 0.5))
+
+
+def small_srtio3(seed: int = 0) -> Workload:
+    """8^3 cells SrTiO3 (1536 O sites), 15 vacancies, no H, 2^3 fragments of
+    4^3 cells, Ea 0.60 eV, 800 K, plain FP64; ~1e5 hops = 6700 windows."""
+    r = Replica((8, 8, 8), A_SRTIO3, 15, 0, 800.0, 0.60, 0.60, nfrag=(2, 2, 2))
+    return Workload("srtio3_8c_15v", [r], precision=0, windows=6700)
+
+
+def srtio3_h_sweep(seed: int = 0) -> Workload:
+    """SrTiO(3-x)H_x, 32^3 cells, x = 0.1 (3277 H), 0.5% vacancies (492),
+    8^3 fragments of 4^3 cells, barriers 0.60 / 0.30 eV, T = 300..700 K."""
+    cells = (32, 32, 32)
+    nsite = 3 * 32**3
+    reps = [Replica(cells, A_SRTIO3, round_half_up(0.005 * nsite), round_half_up(0.1 * 32**3), T,
+                    0.60, 0.30, nfrag=(8, 8, 8)) for T in (300.0, 400.0, 500.0, 600.0, 700.0)]
+    return Workload("srtio3h_32c_Tsweep", reps, precision=0, tracer=True, windows=200)
+
+
+def batched_batio3(seed: int = 0, n: int = 256) -> Workload:
+    """256 uneven BaTiO(3-x)H_x replicas: edge L ~ U{16..48} cells, x ~ U[0, 0.3],
+    vacancies ~ U[0.1, 1]% of O sites, T ~ U[300, 1000] K, barriers 0.70 / 0.35 eV,
+    mixed precision, one batch."""
+    g = np.random.Generator(np.random.Philox(key=np.array([seed, 0x0C0F16], np.uint64)))
+    reps = []
+    for _ in range(n):
+        L = int(g.integers(16, 49))
+        x = float(g.uniform(0.0, 0.3))
+        fv = float(g.uniform(0.001, 0.01))
+        T = float(g.uniform(300.0, 1000.0))
+        nsite = 3 * L**3
+        reps.append(Replica((L, L, L), A_BATIO3, max(1, round_half_up(fv * nsite)),
+                            round_half_up(x * L**3), T, 0.70, 0.35))
+    return Workload("batio3h_256rep_16to48c", reps, edge=4, precision=1, windows=64)
+
+
+def bulk_batio3(seed: int = 0) -> Workload:
+    """BaTiO(3-x)H_x bulk: 128^3 cells (6.29M O sites), x = 0.05, 0.3% vacancies,
+    16^3 fragments of 8^3 cells, 400 K, barriers 0.70 / 0.35 eV."""
+    cells = (128, 128, 128)
+    nsite = 3 * 128**3
+    r = Replica(cells, A_BATIO3, round_half_up(0.003 * nsite), round_half_up(0.05 * 128**3), 400.0,
+                0.70, 0.35, nfrag=(16, 16, 16))
+    return Workload("batio3h_128c", [r], precision=1, windows=10)
+
+
+def um_batio3_bias(seed: int = 0, L: int = 2500) -> Workload:
+    """um-scale BaTiO3 under bias: L^3 cells, 0.1% vacancies (charge +2), uniform
+    field 1e7 V/m along z, Ea 0.70 eV, 400 K, fragments of 8^3 cells."""
+    nsite = 3 * L**3
+    r = Replica((L, L, L), A_BATIO3, round_half_up(0.001 * nsite), 0, 400.0, 0.70, 0.70, field_z=1e7)
+    return Workload(f"batio3_{L}c_bias", [r], edge=8, precision=1, windows=4)
+
+
+ALL = {"small": small_srtio3, "sweep": srtio3_h_sweep, "batched": batched_batio3,
+       "bulk": bulk_batio3, "um": um_batio3_bias}

@@ -1,0 +1,204 @@
+"""GPU path vs the CPU oracle through the C ABI.
+
+The plain (FP64) and mixed (FP32 + u64 fixed point) forms must reproduce the
+oracle's lattice bit for bit: occupancy, vacancy records (site, displacement,
+id), tracer field and hop counts.  Both sides draw the same Philox streams and
+take every floating-point decision with the same IEEE operations, so there is
+nothing to tolerate.  Cases span several fragments per colour, several
+32-event chunks per fragment, uneven and single-fragment partitions, batches
+of uneven replicas, edge cases, and the full-size batched workload on sampled
+replicas.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fk():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2004_09081_gb300 import fkmc
+    fkmc.load()
+    return fkmc
+
+
+def run_pair(fk, orc, cells, nf, nv, nh, seed, windows, prec, tracer=True, T=800.0, Ea=(0.6, 0.3),
+             Ez=0.0, a=3.905, cap=64, n_tau=1.0, chunks=1):
+    b = fk.Batch([(*cells, a)], [(nv, nh)], seed, nfrag=nf, precision=prec, tracer=tracer, cap_v=cap,
+                 n_tau=n_tau)
+    b.set_barriers(Ea[0], Ea[1], T, field_z=Ez)
+    ref = orc.Lattice(cells, nf, nv, nh, seed=seed, tracer=tracer)
+    ref.set_rates(Ea[0], Ea[1], T, Ez=Ez, a_ang=a, cap_v=cap, n_tau=n_tau, precision=prec)
+    # initial state
+    assert np.array_equal(b.state(), ref.occupancy())
+    assert np.array_equal(b.records(), ref.records())
+    per = max(1, windows // chunks)
+    done = 0
+    while done < windows:
+        w = min(per, windows - done)
+        b.run(w)
+        ref.run(w)
+        done += w
+        assert np.array_equal(b.state(), ref.occupancy()), f"occupancy differs after {done} windows"
+        assert np.array_equal(b.records(), ref.records()), f"records differ after {done} windows"
+        if tracer:
+            assert np.array_equal(b.tracer_field(), ref.tracer_field())
+        info, c = b.info(), ref.counters()
+        assert (info.hops, info.handoffs, info.window) == (c["hops"], c["handoffs"], c["window"])
+    return b, ref
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_small_srtio3_bit_exact(fk, orc, prec):
+    """8^3 cells, 15 V, 2^3 fragments of 4^3 (one fragment per colour)."""
+    b, ref = run_pair(fk, orc, (8, 8, 8), (2, 2, 2), 15, 0, 0, 600, prec, tracer=False, Ea=(0.6, 0.6),
+                      chunks=3)
+    assert ref.counters()["hops"] > 5000
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_hydride_tracer_field_bit_exact(fk, orc, prec):
+    run_pair(fk, orc, (8, 8, 12), (2, 2, 4), 30, 150, 3, 150, prec, T=700.0, Ez=3e7, chunks=2)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_many_vacancies_per_fragment(fk, orc, prec):
+    """One fragment holding 100 vacancies: 25 chunks of 32 events, multi-pass
+    scan and selection, periodic self-wrap."""
+    run_pair(fk, orc, (8, 8, 8), (1, 1, 1), 100, 200, 7, 60, prec, cap=128, chunks=2)
+
+
+@pytest.mark.parametrize("nf", [(2, 4, 2), (1, 2, 4), (4, 1, 1)])
+def test_uneven_partitions(fk, orc, nf):
+    run_pair(fk, orc, (10, 12, 9), nf, 25, 60, 11, 120, 0, Ez=-2e7)
+
+
+def test_srtio3_h_32c_plain(fk, orc):
+    """32^3 cells, 492 V, 3277 H, 8^3 fragments (the T-sweep lattice at 500 K)."""
+    run_pair(fk, orc, (32, 32, 32), (8, 8, 8), 492, 3277, 0, 30, 0, T=500.0, chunks=2)
+
+
+def test_batch_of_uneven_replicas(fk, orc):
+    """Replica r of a batch equals the oracle lattice keyed by (seed, r)."""
+    cells = [(8, 8, 8), (12, 10, 8), (16, 16, 16), (9, 9, 9), (6, 8, 10)]
+    comps = [(15, 0), (20, 40), (60, 300), (3, 10), (12, 30)]
+    Ts = [800.0, 650.0, 500.0, 900.0, 1000.0]
+    for prec in (0, 1):
+        b = fk.Batch([(*c, 4.01) for c in cells], comps, 21, edge=4, precision=prec, tracer=True, cap_v=64)
+        b.set_barriers(0.7, 0.35, Ts, field_z=[0, 1e7, 0, -1e7, 0])
+        b.run(40)
+        for r, (c, (nv, nh), T) in enumerate(zip(cells, comps, Ts)):
+            info = b.info(r)
+            ref = orc.Lattice(c, tuple(info.nfrag), nv, nh, seed=21, replica=r, tracer=True)
+            ref.set_rates(0.7, 0.35, T, Ez=[0, 1e7, 0, -1e7, 0][r], a_ang=4.01, cap_v=64, precision=prec)
+            ref.run(40)
+            assert np.array_equal(b.state(r), ref.occupancy()), r
+            assert np.array_equal(b.records(r), ref.records()), r
+            assert np.array_equal(b.tracer_field(r), ref.tracer_field()), r
+            assert info.hops == ref.counters()["hops"]
+            for sp in (0, 1, 2):
+                assert np.array_equal(b.moments(r, sp), ref.moments(sp))
+
+
+def test_D_matches_oracle(fk, orc):
+    b, ref = run_pair(fk, orc, (12, 12, 12), (2, 2, 2), 20, 80, 5, 200, 1, T=900.0, Ez=1e7)
+    for sp in (0, 1, 2):
+        Dx, D, v = b.D(0, sp)
+        d = ref.diffusion(sp)
+        assert D == pytest.approx(d["D"], rel=1e-12)
+        assert np.allclose(Dx, d["D_axes"], rtol=1e-12)
+        assert v == pytest.approx(d["mean"][2] / d["t"], rel=1e-12, abs=1e-30)
+
+
+def test_edge_cases(fk, orc):
+    # no vacancies: nothing moves, no hops
+    b, _ = run_pair(fk, orc, (4, 4, 4), (2, 2, 2), 0, 10, 1, 5, 0)
+    assert b.info().hops == 0
+    # every site a vacancy: no ion to exchange with
+    b, _ = run_pair(fk, orc, (2, 2, 2), (1, 1, 1), 24, 0, 1, 5, 1, tracer=False)
+    assert b.info().hops == 0
+    # a single vacancy on the smallest lattice, and degenerate 1-cell dimensions
+    run_pair(fk, orc, (2, 2, 2), (1, 1, 1), 1, 3, 2, 300, 0)
+    run_pair(fk, orc, (1, 2, 3), (1, 1, 1), 2, 3, 2, 200, 1)
+    run_pair(fk, orc, (1, 1, 1), (1, 1, 1), 1, 1, 2, 200, 0)
+
+
+def test_explicit_state(fk, orc):
+    """kmc_write_state: one vacancy at a chosen site next to an H."""
+    cells, nf = (6, 6, 6), (2, 2, 2)
+    occ = np.zeros(3 * 216, np.uint8)
+    occ[5] = 2
+    occ[216 + 5] = 1
+    occ[400] = 2
+    b = fk.Batch([(*cells, 3.905)], [(0, 0)], 4, nfrag=nf, tracer=True, cap_v=16)
+    b.write_state(occ)
+    b.set_barriers(0.6, 0.3, 700.0)
+    ref = orc.Lattice(cells, nf, 0, 0, seed=4, tracer=True)
+    ref.set_occupancy(occ)
+    ref.set_rates(0.6, 0.3, 700.0, cap_v=16)
+    assert np.array_equal(b.records(), ref.records())
+    b.run(100)
+    ref.run(100)
+    assert np.array_equal(b.state(), ref.occupancy())
+    assert np.array_equal(b.records(), ref.records())
+
+
+def test_errors(fk):
+    with pytest.raises(fk.KmcError) as e:
+        fk.Batch([(8, 8, 8, 3.9)], [(0, 0)], 0, nfrag=(3, 2, 2))
+    assert e.value.code == fk.FKMC_EINVAL
+    with pytest.raises(fk.KmcError) as e:
+        fk.Batch([(4, 4, 4, 3.9)], [(150, 0)], 0, nfrag=(2, 2, 2), cap_v=8)
+    assert e.value.code == fk.FKMC_EOVERFLOW
+    b = fk.Batch([(4, 4, 4, 3.9)], [(1, 0)], 0)
+    with pytest.raises(fk.KmcError) as e:
+        b.run(1)
+    assert e.value.code == fk.FKMC_ESTATE
+    with pytest.raises(fk.KmcError) as e:
+        b.moments(0, fk.FKMC_O)
+    assert e.value.code == fk.FKMC_ESTATE
+
+
+def test_state_blob_roundtrip(fk):
+    import torch
+    b = fk.Batch([(8, 8, 8, 3.9), (6, 6, 6, 3.9)], [(10, 20), (5, 5)], 3)
+    b.set_barriers(0.6, 0.3, 800.0)
+    n = fk.kmc_state_bytes(b.h)
+    host = torch.empty(n, dtype=torch.uint8).pin_memory()
+    fk.kmc_download_state(b.h, host.data_ptr(), n)
+    s0 = [b.state(0), b.state(1)]
+    b.run(30)
+    assert not np.array_equal(b.state(0), s0[0])
+    fk.kmc_upload_state(b.h, host.data_ptr(), n)
+    assert np.array_equal(b.state(0), s0[0]) and np.array_equal(b.state(1), s0[1])
+
+
+def test_batched_workload_full_size_sampled(fk, orc):
+    """The 256-replica batched workload in the benchmark's configuration:
+    conservation on every replica, full bit-exact comparison on a sample."""
+    from paper_2004_09081_gb300 import workloads
+    wl = workloads.batched_batio3(0)
+    reps = wl.replicas
+    b = fk.Batch([(*r.cells, r.a) for r in reps], [(r.n_vac, r.n_H) for r in reps], 0, edge=wl.edge,
+                 precision=wl.precision)
+    b.set_barriers([r.Ea_O for r in reps], [r.Ea_H for r in reps], [r.T for r in reps])
+    W = 8
+    b.run(W)
+    for r in range(len(reps)):
+        m = b.moments(r, 2)
+        assert m[0] == reps[r].n_vac
+    cap = b.info(0).cap_v
+    for r in (0, 1, 97, 200, 255):
+        rep = reps[r]
+        info = b.info(r)
+        ref = orc.Lattice(rep.cells, tuple(info.nfrag), rep.n_vac, rep.n_H, seed=0, replica=r)
+        ref.set_rates(rep.Ea_O, rep.Ea_H, rep.T, a_ang=rep.a, cap_v=cap, precision=wl.precision)
+        ref.run(W)
+        occ = b.state(r)
+        assert np.array_equal(np.bincount(occ, minlength=3)[1:], [rep.n_H, rep.n_vac])
+        assert np.array_equal(occ, ref.occupancy()), r
+        assert np.array_equal(b.records(r), ref.records()), r
+        assert info.hops == ref.counters()["hops"]
