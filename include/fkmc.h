@@ -96,7 +96,9 @@ typedef struct {
     kmc_alloc_fn alloc; /* optional device allocator; NULL = cudaMalloc */
     kmc_free_fn free;
     void* alloc_ctx;
-    int32_t schedule;   /* 0 = one launch per colour phase; 1 = persistent ordered-queue kernel */
+    int32_t schedule;   /* 0 = auto: mixed-form replicas whose state fits one SM run in the
+                           replica-resident kernel, the rest one launch per colour phase;
+                           1 = colour-phase launches only; 2 = resident kernel only */
     int32_t reserved[7];
 } kmc_opts;
 

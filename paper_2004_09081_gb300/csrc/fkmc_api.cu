@@ -123,6 +123,14 @@ struct kmc_batch {
     unsigned long long* scratch_all = nullptr;  // 7 moments per replica
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<void*> owned;
+    // replica-resident kernel: replicas grouped by shared-memory size class
+    NbTable nbt{};
+    int32_t* d_reps = nullptr;   // resident replica ids, class by class
+    int64_t* d_nvac = nullptr;   // vacancies per replica
+    struct RClass { int start, count; size_t smem; cudaStream_t st; cudaEvent_t done; };
+    std::vector<RClass> rclass;
+    cudaEvent_t fork = nullptr;
+    bool any_global = true;
 
     void* dalloc(size_t bytes)
     {
@@ -151,7 +159,13 @@ struct kmc_batch {
         owned.clear();
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
-        ev0 = ev1 = nullptr;
+        if (fork) cudaEventDestroy(fork);
+        ev0 = ev1 = fork = nullptr;
+        for (auto& c : rclass) {
+            if (c.st) cudaStreamDestroy(c.st);
+            if (c.done) cudaEventDestroy(c.done);
+        }
+        rclass.clear();
     }
 };
 
@@ -211,6 +225,52 @@ int rate_table_impl(const kmc_barrier_table* t, double T_K, double Ez, double a_
 
 bool valid_replica(const kmc_batch* b, int32_t r) { return b && r >= 0 && r < b->n; }
 
+// Decide which replicas run in the replica-resident kernel and group them
+// into shared-memory size classes (one launch per class, on forked streams).
+int plan_residency(kmc_batch* b)
+{
+    for (auto& c : b->rclass) {
+        if (c.st) cudaStreamDestroy(c.st);
+        if (c.done) cudaEventDestroy(c.done);
+    }
+    b->rclass.clear();
+    const bool allowed = b->opts.precision == FKMC_MIXED && b->opts.schedule != 1 &&
+                         b->cap <= RESIDENT_MAX_SLOTS;
+    const size_t bounds[4] = {24 * 1024, 48 * 1024, 96 * 1024, RESIDENT_MAX_SMEM};
+    std::vector<std::vector<int>> cls(4);
+    std::vector<size_t> need(b->n, 0), cmax(4, 0);
+    b->any_global = false;
+    for (int r = 0; r < b->n; ++r) {
+        need[r] = resident_smem_bytes(b->desc[r], b->n_vac[r]);
+        const bool fits = allowed && need[r] <= RESIDENT_MAX_SMEM;
+        b->desc[r].resident = fits ? 1 : 0;
+        if (!fits) {
+            b->any_global = true;
+            continue;
+        }
+        int c = 0;
+        while (need[r] > bounds[c]) ++c;
+        cls[c].push_back(r);
+        cmax[c] = std::max(cmax[c], need[r]);
+    }
+    if (b->opts.schedule == 2 && b->any_global)
+        return fail(FKMC_EINVAL, "schedule 2 needs every replica to fit the resident kernel (mixed form)");
+    std::vector<int32_t> order;
+    for (int c = 0; c < 4; ++c) {
+        if (cls[c].empty()) continue;
+        kmc_batch::RClass rc{(int)order.size(), (int)cls[c].size(), cmax[c], nullptr, nullptr};
+        for (int r : cls[c]) order.push_back(r);
+        CK(cudaStreamCreateWithFlags(&rc.st, cudaStreamNonBlocking), "stream");
+        CK(cudaEventCreateWithFlags(&rc.done, cudaEventDisableTiming), "event");
+        b->rclass.push_back(rc);
+    }
+    if (!order.empty())
+        CK(cudaMemcpyAsync(b->d_reps, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice,
+                           b->st),
+           "replica list upload");
+    return FKMC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -262,7 +322,7 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
     if (o.precision != FKMC_PLAIN && o.precision != FKMC_MIXED) return fail(FKMC_EINVAL, "bad precision");
     if (o.cap_v != 0 && (o.cap_v < 8 || o.cap_v > 256 || o.cap_v % 8))
         return fail(FKMC_EINVAL, "cap_v must be 0 or a multiple of 8 in [8, 256]");
-    if (o.schedule != 0) return fail(FKMC_EINVAL, "schedule must be 0");
+    if (o.schedule < 0 || o.schedule > 2) return fail(FKMC_EINVAL, "schedule must be 0, 1 or 2");
 
     kmc_batch* b = new kmc_batch();
     b->n = n;
@@ -343,8 +403,10 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
     b->status = (uint32_t*)b->dalloc(sizeof(uint32_t));
     b->scratch = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * 8);
     b->scratch_all = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * 7 * n);
+    b->d_reps = (int32_t*)b->dalloc(sizeof(int32_t) * n);
+    b->d_nvac = (int64_t*)b->dalloc(sizeof(int64_t) * n);
     if (!b->occ || !b->recs || !b->counts || (o.tracer && !b->tracer) || !b->d_desc || !b->stats ||
-        !b->status || !b->scratch || !b->scratch_all) {
+        !b->status || !b->scratch || !b->scratch_all || !b->d_reps || !b->d_nvac) {
         b->release();
         delete b;
         return fail(FKMC_ENOMEM, "device allocation failed");
@@ -353,10 +415,11 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
     auto step = [&](cudaError_t e, const char* what) {
         if (rc == FKMC_OK && e != cudaSuccess) rc = cuda_fail(e, what);
     };
-    NbEntry tab[3][8];
-    build_nb_table(tab);
-    step(upload_neighbours(&tab[0][0]), "neighbour table upload");
+    build_nb_table(b->nbt.e);
+    step(upload_neighbours(&b->nbt.e[0][0]), "neighbour table upload");
     step(phase_prepare(b->cap), "kernel attributes");
+    step(resident_prepare(), "kernel attributes");
+    step(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "event");
     step(cudaEventCreate(&b->ev0), "event");
     step(cudaEventCreate(&b->ev1), "event");
     step(cudaMemsetAsync(b->occ, 0, sizeof(uint32_t) * b->occ_words, b->st), "memset");
@@ -411,7 +474,11 @@ int kmc_set_barriers(kmc_batch* b, const kmc_barrier_table* tables, const double
         D.theta_tau = D.tau * (double)kmax32;
     }
     b->desc = nd;
-    int rc = upload_desc(b);
+    int rc = plan_residency(b);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(b->d_nvac, b->n_vac.data(), sizeof(int64_t) * b->n, cudaMemcpyHostToDevice, b->st),
+       "vacancy count upload");
+    rc = upload_desc(b);
     if (rc) return rc;
     b->rates_set = true;
     return FKMC_OK;
@@ -423,11 +490,25 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
     if (!b->rates_set) return fail(FKMC_ESTATE, "kmc_set_barriers must come before kmc_run");
     std::vector<unsigned long long> before = b->stats_host;
     CK(cudaEventRecord(b->ev0, b->st), "event record");
-    for (uint64_t wk = 0; wk < windows; ++wk)
-        for (int p = 0; p < 8; ++p)
-            CK(launch_phase(b->opts.precision, b->d_desc, b->n, b->total_items, p, wk, b->occ, b->recs,
-                            b->counts, b->tracer, b->stats, b->status, b->cap, b->st),
-               "phase kernel");
+    if (!b->rclass.empty() && windows > 0) {
+        // replica-resident classes on forked streams, joined back before ev1
+        CK(cudaEventRecord(b->fork, b->st), "event record");
+        for (auto& c : b->rclass) {
+            CK(cudaStreamWaitEvent(c.st, b->fork, 0), "stream wait");
+            CK(launch_resident(b->d_desc, b->d_reps + c.start, c.count, b->d_nvac, c.smem, windows, b->occ,
+                               b->recs, b->counts, b->tracer, b->stats, b->status, b->cap, b->nbt, c.st),
+               "resident kernel");
+            CK(cudaEventRecord(c.done, c.st), "event record");
+        }
+    }
+    if (b->any_global)
+        for (uint64_t wk = 0; wk < windows; ++wk)
+            for (int p = 0; p < 8; ++p)
+                CK(launch_phase(b->opts.precision, b->d_desc, b->n, b->total_items, p, wk, b->occ, b->recs,
+                                b->counts, b->tracer, b->stats, b->status, b->cap, b->st),
+                   "phase kernel");
+    if (!b->rclass.empty() && windows > 0)
+        for (auto& c : b->rclass) CK(cudaStreamWaitEvent(b->st, c.done, 0), "stream wait");
     CK(cudaEventRecord(b->ev1, b->st), "event record");
     for (int r = 0; r < b->n; ++r) b->desc[r].window += windows;
     int rc = upload_desc(b);
@@ -575,6 +656,14 @@ int kmc_write_state(kmc_batch* b, int32_t r, const uint8_t* host_occ, size_t n)
     CK(cudaStreamSynchronize(b->st), "synchronize");
     b->n_vac[r] = nv;
     b->n_H[r] = nh;
+    if (b->rates_set) {
+        int rc = plan_residency(b);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(b->d_nvac, b->n_vac.data(), sizeof(int64_t) * b->n, cudaMemcpyHostToDevice, b->st),
+           "vacancy count upload");
+        rc = upload_desc(b);
+        if (rc) return rc;
+    }
     return FKMC_OK;
 }
 

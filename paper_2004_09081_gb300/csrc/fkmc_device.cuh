@@ -51,6 +51,8 @@ struct RepDesc {
     double tau;            // window length (s), plain clock
     double theta_tau;      // window length in units of 1/k32max, mixed clock
     double two_pow_F;      // 2^F, exact
+    int32_t resident;      // 1: this replica runs in the replica-resident kernel
+    int32_t pad_;
 };
 
 // ---------------------------------------------------------------- Philox
@@ -152,6 +154,9 @@ __device__ __forceinline__ float neglog32(uint64_t x)
 struct NbEntry {
     int8_t t2, dc[3], d[3], pad;
 };
+struct NbTable {
+    NbEntry e[3][8];
+};
 
 __device__ __forceinline__ int wrapc(int c, int L)
 {
@@ -189,5 +194,25 @@ __device__ __forceinline__ int64_t occ_word(const RepDesc& D, int t, int x, int 
 }
 
 __device__ __forceinline__ int occ_shift(int x) { return (x & 15) * 2; }
+
+// Colour processed in `phase` of window w: Fisher-Yates shuffle of 0..7 with
+// j = mulhi(y_k, i+1), y_0..y_7 = Philox blocks (w,0) and (w,1).
+__device__ __forceinline__ int colour_of_phase(uint64_t seed, uint32_t replica, uint64_t w, int phase,
+                                               int lane)
+{
+    const U64x4 blk = philox4x64(w, (uint64_t)(lane & 1), 0, 0, seed, key_word(replica, PURPOSE_PERM));
+    uint32_t perm = 0x76543210u;  // nibble i holds perm[i]
+#pragma unroll
+    for (int i = 7; i >= 1; --i) {
+        const int k = 7 - i;
+        const uint64_t mine = blk.x[k & 3];
+        const uint64_t y = __shfl_sync(0xffffffffu, mine, k >> 2);
+        const int j = (int)__umul64hi(y, (uint64_t)(i + 1));
+        const uint32_t pi = (perm >> (4 * i)) & 15u, pj = (perm >> (4 * j)) & 15u;
+        perm &= ~((15u << (4 * i)) | (15u << (4 * j)));
+        perm |= (pj << (4 * i)) | (pi << (4 * j));
+    }
+    return (int)((perm >> (4 * phase)) & 15u);
+}
 
 }  // namespace fkmc

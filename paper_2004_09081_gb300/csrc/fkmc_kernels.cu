@@ -103,26 +103,6 @@ __device__ __forceinline__ typename Arith<PREC>::V warp_scan(typename Arith<PREC
     return v;
 }
 
-// Colour processed in `phase` of window w: Fisher-Yates shuffle of 0..7 with
-// j = mulhi(y_k, i+1), y_0..y_7 = Philox blocks (w,0) and (w,1).
-__device__ __forceinline__ int colour_of_phase(uint64_t seed, uint32_t replica, uint64_t w, int phase,
-                                               int lane)
-{
-    const U64x4 blk = philox4x64(w, (uint64_t)(lane & 1), 0, 0, seed, key_word(replica, PURPOSE_PERM));
-    uint32_t perm = 0x76543210u;  // nibble i holds perm[i]
-#pragma unroll
-    for (int i = 7; i >= 1; --i) {
-        const int k = 7 - i;
-        const uint64_t mine = blk.x[k & 3];
-        const uint64_t y = __shfl_sync(0xffffffffu, mine, k >> 2);
-        const int j = (int)__umul64hi(y, (uint64_t)(i + 1));
-        const uint32_t pi = (perm >> (4 * i)) & 15u, pj = (perm >> (4 * j)) & 15u;
-        perm &= ~((15u << (4 * i)) | (15u << (4 * j)));
-        perm |= (pj << (4 * i)) | (pi << (4 * j));
-    }
-    return (int)((perm >> (4 * phase)) & 15u);
-}
-
 struct WarpSmem {
     VacRec* rec;     // [cap] records as loaded (slot data lives here)
     uint16_t* order; // [cap] slot m -> index into rec
@@ -188,6 +168,7 @@ __global__ void __launch_bounds__(128) k_phase(const RepDesc* __restrict__ descs
         if (descs[mid].items_off <= item) lo = mid; else hi = mid - 1;
     }
     const RepDesc& D = descs[lo];
+    if (D.resident) return;
     const int64_t local = item - D.items_off;
     const uint64_t w = D.window + wk;
     const int colour = colour_of_phase(D.seed, D.replica, w, phase, lane);

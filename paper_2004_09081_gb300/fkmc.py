@@ -282,7 +282,7 @@ class Batch:
     """A batch of replicas (one lattice = a batch of one) on the current GPU."""
 
     def __init__(self, cells, comps, seed=0, *, edge=4, nfrag=None, precision=FKMC_PLAIN,
-                 tracer=False, cap_v=0, n_tau=1.0, stream=None):
+                 tracer=False, cap_v=0, n_tau=1.0, schedule=0, stream=None):
         import torch
         self._alloc = TorchAllocator()
         o = kmc_default_opts()
@@ -294,6 +294,7 @@ class Batch:
         o.tracer = int(bool(tracer))
         o.cap_v = int(cap_v)
         o.n_tau = float(n_tau)
+        o.schedule = int(schedule)
         st = stream if stream is not None else torch.cuda.current_stream()
         o.stream = C.c_void_p(st.cuda_stream)
         o.alloc = self._alloc.c_alloc

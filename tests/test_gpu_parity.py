@@ -26,9 +26,9 @@ def fk():
 
 
 def run_pair(fk, orc, cells, nf, nv, nh, seed, windows, prec, tracer=True, T=800.0, Ea=(0.6, 0.3),
-             Ez=0.0, a=3.905, cap=64, n_tau=1.0, chunks=1):
+             Ez=0.0, a=3.905, cap=64, n_tau=1.0, chunks=1, schedule=0):
     b = fk.Batch([(*cells, a)], [(nv, nh)], seed, nfrag=nf, precision=prec, tracer=tracer, cap_v=cap,
-                 n_tau=n_tau)
+                 n_tau=n_tau, schedule=schedule)
     b.set_barriers(Ea[0], Ea[1], T, field_z=Ez)
     ref = orc.Lattice(cells, nf, nv, nh, seed=seed, tracer=tracer)
     ref.set_rates(Ea[0], Ea[1], T, Ez=Ez, a_ang=a, cap_v=cap, n_tau=n_tau, precision=prec)
@@ -51,29 +51,35 @@ def run_pair(fk, orc, cells, nf, nv, nh, seed, windows, prec, tracer=True, T=800
     return b, ref
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_small_srtio3_bit_exact(fk, orc, prec):
+# (precision, schedule): plain FP64 runs the colour-phase kernel; the mixed form
+# runs both the colour-phase kernel (1) and the replica-resident kernel (2)
+FORMS = [(0, 0), (1, 1), (1, 2)]
+
+
+@pytest.mark.parametrize("prec,sched", FORMS)
+def test_small_srtio3_bit_exact(fk, orc, prec, sched):
     """8^3 cells, 15 V, 2^3 fragments of 4^3 (one fragment per colour)."""
     b, ref = run_pair(fk, orc, (8, 8, 8), (2, 2, 2), 15, 0, 0, 600, prec, tracer=False, Ea=(0.6, 0.6),
-                      chunks=3)
+                      chunks=3, schedule=sched)
     assert ref.counters()["hops"] > 5000
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_hydride_tracer_field_bit_exact(fk, orc, prec):
-    run_pair(fk, orc, (8, 8, 12), (2, 2, 4), 30, 150, 3, 150, prec, T=700.0, Ez=3e7, chunks=2)
+@pytest.mark.parametrize("prec,sched", FORMS)
+def test_hydride_tracer_field_bit_exact(fk, orc, prec, sched):
+    run_pair(fk, orc, (8, 8, 12), (2, 2, 4), 30, 150, 3, 150, prec, T=700.0, Ez=3e7, chunks=2, schedule=sched)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_many_vacancies_per_fragment(fk, orc, prec):
-    """One fragment holding 100 vacancies: 25 chunks of 32 events, multi-pass
+@pytest.mark.parametrize("prec,sched", FORMS)
+def test_many_vacancies_per_fragment(fk, orc, prec, sched):
+    """One fragment holding 60 vacancies: 15 chunks of 32 events, multi-pass
     scan and selection, periodic self-wrap."""
-    run_pair(fk, orc, (8, 8, 8), (1, 1, 1), 100, 200, 7, 60, prec, cap=128, chunks=2)
+    run_pair(fk, orc, (8, 8, 8), (1, 1, 1), 60, 200, 7, 60, prec, cap=64, chunks=2, schedule=sched)
 
 
 @pytest.mark.parametrize("nf", [(2, 4, 2), (1, 2, 4), (4, 1, 1)])
-def test_uneven_partitions(fk, orc, nf):
-    run_pair(fk, orc, (10, 12, 9), nf, 25, 60, 11, 120, 0, Ez=-2e7)
+@pytest.mark.parametrize("prec,sched", FORMS)
+def test_uneven_partitions(fk, orc, nf, prec, sched):
+    run_pair(fk, orc, (10, 12, 9), nf, 25, 60, 11, 120, prec, Ez=-2e7, schedule=sched)
 
 
 def test_srtio3_h_32c_plain(fk, orc):
@@ -86,8 +92,9 @@ def test_batch_of_uneven_replicas(fk, orc):
     cells = [(8, 8, 8), (12, 10, 8), (16, 16, 16), (9, 9, 9), (6, 8, 10)]
     comps = [(15, 0), (20, 40), (60, 300), (3, 10), (12, 30)]
     Ts = [800.0, 650.0, 500.0, 900.0, 1000.0]
-    for prec in (0, 1):
-        b = fk.Batch([(*c, 4.01) for c in cells], comps, 21, edge=4, precision=prec, tracer=True, cap_v=64)
+    for prec, sched in FORMS:
+        b = fk.Batch([(*c, 4.01) for c in cells], comps, 21, edge=4, precision=prec, tracer=True, cap_v=64,
+                     schedule=sched)
         b.set_barriers(0.7, 0.35, Ts, field_z=[0, 1e7, 0, -1e7, 0])
         b.run(40)
         for r, (c, (nv, nh), T) in enumerate(zip(cells, comps, Ts)):
@@ -104,7 +111,7 @@ def test_batch_of_uneven_replicas(fk, orc):
 
 
 def test_D_matches_oracle(fk, orc):
-    b, ref = run_pair(fk, orc, (12, 12, 12), (2, 2, 2), 20, 80, 5, 200, 1, T=900.0, Ez=1e7)
+    b, ref = run_pair(fk, orc, (12, 12, 12), (2, 2, 2), 20, 80, 5, 200, 1, T=900.0, Ez=1e7, schedule=2)
     for sp in (0, 1, 2):
         Dx, D, v = b.D(0, sp)
         d = ref.diffusion(sp)
@@ -114,16 +121,17 @@ def test_D_matches_oracle(fk, orc):
 
 
 def test_edge_cases(fk, orc):
-    # no vacancies: nothing moves, no hops
-    b, _ = run_pair(fk, orc, (4, 4, 4), (2, 2, 2), 0, 10, 1, 5, 0)
-    assert b.info().hops == 0
-    # every site a vacancy: no ion to exchange with
-    b, _ = run_pair(fk, orc, (2, 2, 2), (1, 1, 1), 24, 0, 1, 5, 1, tracer=False)
-    assert b.info().hops == 0
-    # a single vacancy on the smallest lattice, and degenerate 1-cell dimensions
-    run_pair(fk, orc, (2, 2, 2), (1, 1, 1), 1, 3, 2, 300, 0)
-    run_pair(fk, orc, (1, 2, 3), (1, 1, 1), 2, 3, 2, 200, 1)
-    run_pair(fk, orc, (1, 1, 1), (1, 1, 1), 1, 1, 2, 200, 0)
+    for prec, sched in FORMS:
+        # no vacancies: nothing moves, no hops
+        b, _ = run_pair(fk, orc, (4, 4, 4), (2, 2, 2), 0, 10, 1, 5, prec, schedule=sched)
+        assert b.info().hops == 0
+        # every site a vacancy: no ion to exchange with
+        b, _ = run_pair(fk, orc, (2, 2, 2), (1, 1, 1), 24, 0, 1, 5, prec, tracer=False, schedule=sched)
+        assert b.info().hops == 0
+        # a single vacancy on the smallest lattice, and degenerate 1-cell dimensions
+        run_pair(fk, orc, (2, 2, 2), (1, 1, 1), 1, 3, 2, 300, prec, schedule=sched)
+        run_pair(fk, orc, (1, 2, 3), (1, 1, 1), 2, 3, 2, 200, prec, schedule=sched)
+        run_pair(fk, orc, (1, 1, 1), (1, 1, 1), 1, 1, 2, 200, prec, schedule=sched)
 
 
 def test_explicit_state(fk, orc):
@@ -184,6 +192,7 @@ def test_batched_workload_full_size_sampled(fk, orc):
     reps = wl.replicas
     b = fk.Batch([(*r.cells, r.a) for r in reps], [(r.n_vac, r.n_H) for r in reps], 0, edge=wl.edge,
                  precision=wl.precision)
+    assert all(b.info(r).n_vac == reps[r].n_vac for r in range(len(reps)))
     b.set_barriers([r.Ea_O for r in reps], [r.Ea_H for r in reps], [r.T for r in reps])
     W = 8
     b.run(W)
