@@ -5,13 +5,24 @@
 // (cp.async.bulk + mbarrier), its vacancy records are unpacked into
 // shared-memory arrays linked per fragment, and the CTA runs every window and
 // colour phase with __syncthreads() between phases -- no grid-wide
-// synchronisation, because replicas are independent.  Inside a phase one
-// thread runs one fragment's BKL (arXiv:2004.09081 Sec. II.A Eqs.
-// RateCnst1, eventSelection, TimeStep; fragment-local selection Sec. II.B
-// Eq. AtomP).  Selection uses exact u64 fixed-point sums, so the result is
-// identical to the warp kernel and to the oracle's mixed form.  At the end the
-// occupancy goes back to global memory with a TMA bulk store and the records
-// go back to the per-fragment lists.
+// synchronisation, because replicas are independent.  The fragment BKL is
+// that of arXiv:2004.09081 Sec. II.A (Eqs. RateCnst1, eventSelection,
+// TimeStep) with fragment-local selection (Sec. II.B, Eq. AtomP); selection
+// uses exact u64 fixed-point sums, so results are identical to the
+// colour-phase kernel and to the oracle's mixed form.
+//
+// Each colour phase has two passes:
+//   screen  one thread per fragment of the colour.  A fragment whose
+//           neighbourhood did not change since its last visit keeps its exact
+//           event total S; with the first draw of the phase, E/S > window
+//           proves that nothing happens, and the fragment is skipped.
+//           Everything else goes to a compact list.
+//   run     one group of 8 lanes per listed fragment (lane q evaluates
+//           neighbour direction q of every vacancy): exact total, clock,
+//           selection by group scan, exchange, hand-off, and "dirty" marks on
+//           every fragment whose box or halo holds one of the two changed sites.
+// At the end the occupancy goes back with a TMA bulk store and the records go
+// back to the per-fragment lists.
 #include <cuda_runtime.h>
 
 #include "fkmc_device.cuh"
@@ -83,8 +94,23 @@ __device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t by
                  : "memory");
 }
 
-constexpr uint32_t BULK_CHUNK = 32768;  // bytes per bulk copy instruction
-constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s bound on any device-side wait
+constexpr uint32_t BULK_CHUNK = 32768;        // bytes per bulk copy instruction
+constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s bound on any device-side wait
+
+// compact site key in shared memory: t<<30 | z<<20 | y<<10 | x (cells < 1024),
+// ordered like the linear site index
+__device__ __forceinline__ uint32_t key32(int t, int x, int y, int z)
+{
+    return ((uint32_t)t << 30) | ((uint32_t)z << 20) | ((uint32_t)y << 10) | (uint32_t)x;
+}
+
+__device__ __forceinline__ void split32(uint32_t k, int& t, int& x, int& y, int& z)
+{
+    x = (int)(k & 1023u);
+    y = (int)((k >> 10) & 1023u);
+    z = (int)((k >> 20) & 1023u);
+    t = (int)(k >> 30);
+}
 
 struct Shared {
     RepDesc D;
@@ -92,9 +118,119 @@ struct Shared {
     uint64_t bar;
     int perm[8];
     int nv_count;
+    int nact;
     unsigned long long hops, hand;
     int abort;
 };
+
+struct Layout {
+    uint32_t* occ;
+    uint32_t* key;
+    int32_t* d;
+    uint32_t* id;
+    int16_t* next;
+    int32_t* head;
+    unsigned long long* S;
+    uint8_t* dirty;
+    int32_t* act;
+};
+
+
+__host__ __device__ inline size_t layout_bytes(int64_t words, int64_t nv, int64_t nfrag, int64_t ncls,
+                                               size_t* off /* 9 offsets or null */)
+{
+    size_t o[9];
+    size_t b = 0;
+    o[0] = b; b += (size_t)words * 4; b = (b + 15) & ~(size_t)15;   // occupancy (bulk-copied)
+    o[6] = b; b += (size_t)nfrag * 8; b = (b + 15) & ~(size_t)15;   // cached totals
+    o[1] = b; b += (size_t)nv * 4;                                    // keys
+    o[2] = b; b += (size_t)nv * 12;                                   // displacements
+    o[3] = b; b += (size_t)nv * 4;                                    // ids
+    o[8] = b; b += (size_t)ncls * 4;                                  // screened list
+    o[5] = b; b += (size_t)nfrag * 4;                                 // list heads
+    o[4] = b; b += (size_t)nv * 2;                                    // next links
+    o[7] = b; b += (size_t)nfrag;                                     // dirty flags
+    b = (b + 127) & ~(size_t)127;
+    if (off)
+        for (int k = 0; k < 9; ++k) off[k] = o[k];
+    return b;
+}
+
+__device__ __forceinline__ Layout carve(unsigned char* dyn, int64_t words, int64_t nv, int64_t nfrag, int64_t ncls)
+{
+    size_t o[9];
+    layout_bytes(words, nv, nfrag, ncls, o);
+    Layout L;
+    L.occ = reinterpret_cast<uint32_t*>(dyn + o[0]);
+    L.key = reinterpret_cast<uint32_t*>(dyn + o[1]);
+    L.d = reinterpret_cast<int32_t*>(dyn + o[2]);
+    L.id = reinterpret_cast<uint32_t*>(dyn + o[3]);
+    L.next = reinterpret_cast<int16_t*>(dyn + o[4]);
+    L.head = reinterpret_cast<int32_t*>(dyn + o[5]);
+    L.S = reinterpret_cast<unsigned long long*>(dyn + o[6]);
+    L.dirty = reinterpret_cast<uint8_t*>(dyn + o[7]);
+    L.act = reinterpret_cast<int32_t*>(dyn + o[8]);
+    return L;
+}
+
+// word and shift in the replica's occupancy of neighbour q of the site (t,x,y,z)
+struct NbSite {
+    int t2, jx, jy, jz;
+};
+
+__device__ __forceinline__ NbSite nb_site(const Shared& sh, int t, int x, int y, int z, int q)
+{
+    const NbEntry nb = sh.nb[t][q];
+    NbSite s;
+    s.t2 = nb.t2;
+    s.jx = wrapc(x + nb.dc[0], sh.D.L[0]);
+    s.jy = wrapc(y + nb.dc[1], sh.D.L[1]);
+    s.jz = wrapc(z + nb.dc[2], sh.D.L[2]);
+    return s;
+}
+
+__device__ __forceinline__ int site_code(const Shared& sh, const uint32_t* occ, int t, int x, int y, int z)
+{
+    const RepDesc& D = sh.D;
+    const uint32_t w = occ[((t * D.L[2] + z) * D.L[1] + y) * D.row_words + (x >> 4)];
+    return (int)((w >> occ_shift(x)) & 3u);
+}
+
+// fixed-point rate of the exchange of the vacancy at key k with neighbour q
+__device__ __forceinline__ unsigned long long event_rate(const Shared& sh, const uint32_t* occ, uint32_t k,
+                                                         int q, int* code_out)
+{
+    int t, x, y, z;
+    split32(k, t, x, y, z);
+    const NbSite s = nb_site(sh, t, x, y, z, q);
+    const int code = site_code(sh, occ, s.t2, s.jx, s.jy, s.jz);
+    if (code_out) *code_out = code;
+    return code == SP_V ? 0ull : (unsigned long long)sh.D.q[code * 3 + sh.nb[t][q].d[2] + 1];
+}
+
+// mark every fragment other than `self` whose box or one-cell halo holds cell (x,y,z)
+__device__ __forceinline__ void mark_dirty(const RepDesc& D, uint8_t* dirty, int x, int y, int z, int self)
+{
+    const int c[3] = {x, y, z};
+    int cand[3][3], nc[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int o = frag_of(c[d], D.base[d], D.rem[d]);
+        nc[d] = 0;
+        cand[d][nc[d]++] = o;
+        if (D.nf[d] > 1) {
+            if (c[d] == frag_start(o, D.base[d], D.rem[d])) cand[d][nc[d]++] = o == 0 ? D.nf[d] - 1 : o - 1;
+            if (c[d] == frag_start(o + 1, D.base[d], D.rem[d]) - 1)
+                cand[d][nc[d]++] = o == D.nf[d] - 1 ? 0 : o + 1;
+        }
+    }
+    for (int a = 0; a < nc[2]; ++a)
+        for (int b = 0; b < nc[1]; ++b)
+            for (int e = 0; e < nc[0]; ++e) {
+                const int f = (cand[2][a] * D.nf[1] + cand[1][b]) * D.nf[0] + cand[0][e];
+                if (f != self) dirty[f] = 1;
+            }
+}
 
 }  // namespace
 
@@ -102,10 +238,10 @@ size_t resident_smem_bytes(const RepDesc& D, int64_t n_vac)
 {
     const int64_t words = 3 * (int64_t)D.L[2] * D.L[1] * D.row_words;
     const int64_t nfrag = (int64_t)D.nf[0] * D.nf[1] * D.nf[2];
-    size_t b = (size_t)words * 4;                 // occupancy
-    b += (size_t)n_vac * (8 + 12 + 4 + 4);        // key, d[3], id, next
-    b += (size_t)nfrag * 4;                       // list heads
-    return (b + 127) & ~(size_t)127;
+    const int64_t ncls = (int64_t)((D.nf[0] + 1) / 2) * ((D.nf[1] + 1) / 2) * ((D.nf[2] + 1) / 2);
+    if (D.L[0] > 1024 || D.L[1] > 1024 || D.L[2] > 1024 || n_vac > 32767 || nfrag > 32767)
+        return ~(size_t)0;  // compact keys and 16-bit links need these bounds
+    return layout_bytes(words, n_vac, nfrag, ncls, nullptr);
 }
 
 __global__ void __launch_bounds__(256) k_resident(const RepDesc* __restrict__ descs,
@@ -132,13 +268,9 @@ __global__ void __launch_bounds__(256) k_resident(const RepDesc* __restrict__ de
     __syncthreads();
     const RepDesc& D = sh.D;
     const int64_t words = 3 * (int64_t)D.L[2] * D.L[1] * D.row_words;
-    const int64_t nfrag = (int64_t)D.nf[0] * D.nf[1] * D.nf[2];
-    uint32_t* occ_s = reinterpret_cast<uint32_t*>(dyn);
-    uint64_t* key_s = reinterpret_cast<uint64_t*>(dyn + ((words * 4 + 15) & ~15ll));
-    int32_t* d_s = reinterpret_cast<int32_t*>(key_s + n_vac);
-    uint32_t* id_s = reinterpret_cast<uint32_t*>(d_s + 3 * n_vac);
-    int32_t* next_s = reinterpret_cast<int32_t*>(id_s + n_vac);
-    int32_t* head_s = next_s + n_vac;
+    const int nfrag = D.nf[0] * D.nf[1] * D.nf[2];
+    const int ncls_max = ((D.nf[0] + 1) / 2) * ((D.nf[1] + 1) / 2) * ((D.nf[2] + 1) / 2);
+    const Layout S = carve(dyn, words, n_vac, nfrag, ncls_max);
 
     // ---- stage in: occupancy by TMA bulk copies, records by plain loads
     const uint32_t occ_bytes = (uint32_t)(words * 4);
@@ -148,10 +280,10 @@ __global__ void __launch_bounds__(256) k_resident(const RepDesc* __restrict__ de
         const char* src = reinterpret_cast<const char*>(occ + D.occ_word_off);
         for (uint32_t off = 0; off < occ_bytes; off += BULK_CHUNK) {
             const uint32_t n = min(BULK_CHUNK, occ_bytes - off);
-            bulk_g2s(dyn + off, src + off, n, &sh.bar);
+            bulk_g2s(S.occ + off / 4, src + off, n, &sh.bar);
         }
     }
-    for (int64_t f = tid; f < nfrag; f += blockDim.x) {
+    for (int f = tid; f < nfrag; f += blockDim.x) {
         const int64_t g = D.frag_base + f;
         const int c = counts[g];
         int head = -1;
@@ -162,16 +294,20 @@ __global__ void __launch_bounds__(256) k_resident(const RepDesc* __restrict__ de
                 break;
             }
             const VacRec rr = recs[g * cap + k];
-            key_s[v] = rr.key;
-            d_s[3 * v] = rr.d[0];
-            d_s[3 * v + 1] = rr.d[1];
-            d_s[3 * v + 2] = rr.d[2];
-            id_s[v] = rr.id;
-            next_s[v] = head;
+            int t, x, y, z;
+            split_key(rr.key, t, x, y, z);
+            S.key[v] = key32(t, x, y, z);
+            S.d[3 * v] = rr.d[0];
+            S.d[3 * v + 1] = rr.d[1];
+            S.d[3 * v + 2] = rr.d[2];
+            S.id[v] = rr.id;
+            S.next[v] = (int16_t)head;
             head = v;
         }
         if (c > cap) atomicOr(status, STATUS_OVERFLOW);
-        head_s[f] = head;
+        S.head[f] = head;
+        S.dirty[f] = 1;
+        S.S[f] = 0ull;
     }
     __syncthreads();  // the barrier init is visible to every thread from here on
     if (!mbar_wait_bounded(&sh.bar, 0, WAIT_NS)) {
@@ -185,8 +321,12 @@ __global__ void __launch_bounds__(256) k_resident(const RepDesc* __restrict__ de
     if (sh.abort) return;
 
     const uint64_t hop_k1 = key_word(D.replica, PURPOSE_HOP);
+    const int lane = tid & 31;
+    const int q = lane & 7;                       // neighbour direction of this lane
+    const int grp = tid >> 3;                     // 8-lane group id in the CTA
+    const int ngrp = blockDim.x >> 3;
+    const unsigned gmask = 0xffu << (lane & 24);  // lanes of this group
     unsigned long long my_hops = 0, my_hand = 0;
-    uint16_t sl[RESIDENT_MAX_SLOTS];  // slot -> vacancy index (bit 15: slot dead)
 
     for (uint64_t wk = 0; wk < windows; ++wk) {
         const uint64_t w = D.window + wk;
@@ -204,61 +344,80 @@ __global__ void __launch_bounds__(256) k_resident(const RepDesc* __restrict__ de
                 cnt[d] = D.nf[d] == 1 ? (bit[d] == 0 ? 1 : 0) : D.nf[d] / 2;
             }
             const int ncls = cnt[0] * cnt[1] * cnt[2];
+            if (tid == 0) sh.nact = 0;
+            __syncthreads();
+            // ---- screen: one thread per fragment of the colour
             for (int l = tid; l < ncls; l += blockDim.x) {
-                int f[3], lo_c[3], hi_c[3];
-                f[0] = l % cnt[0];
-                f[1] = (l / cnt[0]) % cnt[1];
-                f[2] = l / (cnt[0] * cnt[1]);
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    f[d] = D.nf[d] == 1 ? 0 : 2 * f[d] + bit[d];
-                    lo_c[d] = frag_start(f[d], D.base[d], D.rem[d]);
-                    hi_c[d] = frag_start(f[d] + 1, D.base[d], D.rem[d]);
+                int f0 = l % cnt[0], f1 = (l / cnt[0]) % cnt[1], f2 = l / (cnt[0] * cnt[1]);
+                f0 = D.nf[0] == 1 ? 0 : 2 * f0 + bit[0];
+                f1 = D.nf[1] == 1 ? 0 : 2 * f1 + bit[1];
+                f2 = D.nf[2] == 1 ? 0 : 2 * f2 + bit[2];
+                const int fid = (f2 * D.nf[1] + f1) * D.nf[0] + f0;
+                if (S.head[fid] < 0) continue;
+                bool active = S.dirty[fid] != 0;
+                if (!active) {
+                    const unsigned long long tot = S.S[fid];
+                    if (tot == 0ull) continue;
+                    const U64x4 blk = philox4x64((uint64_t)fid, w, 0, 0, D.seed, hop_k1);
+                    const float ratio = __fdiv_rn(neglog32(blk.x[0]), __ull2float_rn(tot));
+                    const double dth = __dmul_rn((double)ratio, D.two_pow_F);
+                    active = !(__dadd_rn(0.0, dth) > D.theta_tau);
                 }
-                const int fid = (f[2] * D.nf[1] + f[1]) * D.nf[0] + f[0];
-                // slots: the fragment's vacancies in ascending site order
-                int n = 0;
-                for (int v = head_s[fid]; v >= 0; v = next_s[v]) {
-                    if (n >= cap || n >= RESIDENT_MAX_SLOTS) {
-                        atomicOr(status, STATUS_OVERFLOW);
-                        break;
+                if (active) S.act[atomicAdd(&sh.nact, 1)] = fid;
+            }
+            __syncthreads();
+            // ---- run: one 8-lane group per listed fragment
+            const int nact = sh.nact;
+            for (int a = grp; a < nact; a += ngrp) {
+                const int fid = S.act[a];
+                const int fz = fid / (D.nf[0] * D.nf[1]);
+                const int fy = (fid / D.nf[0]) % D.nf[1];
+                const int fx = fid % D.nf[0];
+                const int lo0 = frag_start(fx, D.base[0], D.rem[0]), hi0 = frag_start(fx + 1, D.base[0], D.rem[0]);
+                const int lo1 = frag_start(fy, D.base[1], D.rem[1]), hi1 = frag_start(fy + 1, D.base[1], D.rem[1]);
+                const int lo2 = frag_start(fz, D.base[2], D.rem[2]), hi2 = frag_start(fz + 1, D.base[2], D.rem[2]);
+                // slots in ascending site order: sort the fragment's list in place
+                if (q == 0) {
+                    int sorted = -1;
+                    int64_t n = 0;
+                    for (int v = S.head[fid]; v >= 0;) {
+                        const int nx = S.next[v];
+                        const uint32_t k = S.key[v];
+                        if (sorted < 0 || S.key[sorted] > k) {
+                            S.next[v] = (int16_t)sorted;
+                            sorted = v;
+                        } else {
+                            int pv = sorted;
+                            while (S.next[pv] >= 0 && S.key[S.next[pv]] < k) pv = S.next[pv];
+                            S.next[v] = S.next[pv];
+                            S.next[pv] = (int16_t)v;
+                        }
+                        v = nx;
+                        if (++n > n_vac) {  // a list longer than the vacancy count is corrupt
+                            atomicOr(status, STATUS_OVERFLOW);
+                            break;
+                        }
                     }
-                    const uint64_t k = key_s[v];
-                    int m = n++;
-                    while (m > 0 && key_s[sl[m - 1]] > k) {
-                        sl[m] = sl[m - 1];
-                        --m;
-                    }
-                    sl[m] = (uint16_t)v;
+                    S.head[fid] = sorted;
                 }
-                if (n == 0) continue;
+                __syncwarp(gmask);
 
                 double clock = 0.0;
                 uint64_t i = 0, blk_id = ~0ull;
                 U64x4 blk;
                 blk.x[0] = blk.x[1] = blk.x[2] = blk.x[3] = 0;
+                unsigned long long tot = 0;
                 for (;;) {
-                    // exact fixed-point total of the fragment's events
-                    unsigned long long S = 0;
-                    for (int m = 0; m < n; ++m) {
-                        if (sl[m] & 0x8000u) continue;
-                        int t, x, y, z;
-                        split_key(key_s[sl[m]], t, x, y, z);
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const NbEntry nb = sh.nb[t][q];
-                            const int jx = wrapc(x + nb.dc[0], D.L[0]);
-                            const int jy = wrapc(y + nb.dc[1], D.L[1]);
-                            const int jz = wrapc(z + nb.dc[2], D.L[2]);
-                            const uint32_t wd =
-                                occ_s[(((int64_t)nb.t2 * D.L[2] + jz) * D.L[1] + jy) * D.row_words + (jx >> 4)];
-                            const int code = (int)((wd >> occ_shift(jx)) & 3u);
-                            if (code != SP_V) S += D.q[code * 3 + nb.d[2] + 1];
-                        }
-                    }
-                    if (S == 0) break;
+                    // exact total: lane q sums direction q over the vacancies, then a group reduction
+                    unsigned long long part = 0;
+                    for (int v = S.head[fid]; v >= 0; v = S.next[v]) part += event_rate(sh, S.occ, S.key[v], q, nullptr);
+                    part += __shfl_xor_sync(gmask, part, 1, 8);
+                    part += __shfl_xor_sync(gmask, part, 2, 8);
+                    part += __shfl_xor_sync(gmask, part, 4, 8);
+                    tot = part;
+                    if (tot == 0ull) break;
                     if (i >= MAX_EVENTS_PER_PHASE) {
-                        atomicOr(status, STATUS_EVENT_LIMIT);
+                        if (q == 0) atomicOr(status, STATUS_EVENT_LIMIT);
                         break;
                     }
                     if ((i >> 1) != blk_id) {
@@ -267,85 +426,93 @@ __global__ void __launch_bounds__(256) k_resident(const RepDesc* __restrict__ de
                     }
                     const uint64_t xt = (i & 1) ? blk.x[2] : blk.x[0];
                     const uint64_t xs = (i & 1) ? blk.x[3] : blk.x[1];
-                    const float E = neglog32(xt);
-                    const float ratio = __fdiv_rn(E, __ull2float_rn(S));
+                    const float ratio = __fdiv_rn(neglog32(xt), __ull2float_rn(tot));
                     const double dth = __dmul_rn((double)ratio, D.two_pow_F);
                     if (__dadd_rn(clock, dth) > D.theta_tau) break;
-                    const unsigned long long target = __umul64hi(xs, S);
-                    // first event whose running sum exceeds the target
+                    const unsigned long long target = __umul64hi(xs, tot);
+                    // first event (slot order, then direction) whose running sum exceeds the target
                     unsigned long long P = 0;
-                    int sm_ = -1, sq = -1, ion = 0;
-                    for (int m = 0; m < n && sm_ < 0; ++m) {
-                        if (sl[m] & 0x8000u) continue;
+                    int sel_v = -1, sel_prev = -1, sel_q = 0, sel_code = 0, prev = -1;
+                    for (int v = S.head[fid]; v >= 0; prev = v, v = S.next[v]) {
+                        int code;
+                        const unsigned long long rt = event_rate(sh, S.occ, S.key[v], q, &code);
+                        unsigned long long inc = rt;
+#pragma unroll
+                        for (int off = 1; off < 8; off <<= 1) {
+                            const unsigned long long t2 = __shfl_up_sync(gmask, inc, off, 8);
+                            if (q >= off) inc += t2;
+                        }
+                        const unsigned long long tv = __shfl_sync(gmask, inc, 7, 8);
+                        if (P + tv > target) {
+                            const unsigned bal = __ballot_sync(gmask, P + inc > target) >> (lane & 24);
+                            sel_q = __ffs(bal) - 1;
+                            sel_code = __shfl_sync(gmask, code, sel_q, 8);
+                            sel_v = v;
+                            sel_prev = prev;
+                            break;
+                        }
+                        P += tv;
+                    }
+                    if (sel_v < 0) {  // cannot happen: the target lies below the total
+                        if (q == 0) atomicOr(status, STATUS_OVERFLOW);
+                        break;
+                    }
+                    // apply the exchange (lane 0 of the group)
+                    if (q == 0) {
+                        const int v = sel_v;
                         int t, x, y, z;
-                        split_key(key_s[sl[m]], t, x, y, z);
-                        for (int q = 0; q < 8; ++q) {
-                            const NbEntry nb = sh.nb[t][q];
-                            const int jx = wrapc(x + nb.dc[0], D.L[0]);
-                            const int jy = wrapc(y + nb.dc[1], D.L[1]);
-                            const int jz = wrapc(z + nb.dc[2], D.L[2]);
-                            const uint32_t wd =
-                                occ_s[(((int64_t)nb.t2 * D.L[2] + jz) * D.L[1] + jy) * D.row_words + (jx >> 4)];
-                            const int code = (int)((wd >> occ_shift(jx)) & 3u);
-                            if (code == SP_V) continue;
-                            P += D.q[code * 3 + nb.d[2] + 1];
-                            if (P > target) {
-                                sm_ = m;
-                                sq = q;
-                                ion = code;
-                                break;
-                            }
+                        split32(S.key[v], t, x, y, z);
+                        const NbEntry nb = sh.nb[t][sel_q];
+                        const NbSite j = nb_site(sh, t, x, y, z, sel_q);
+                        const uint32_t ion = (uint32_t)sel_code;
+                        atomicXor(S.occ + ((t * D.L[2] + z) * D.L[1] + y) * D.row_words + (x >> 4),
+                                  ((uint32_t)SP_V ^ ion) << occ_shift(x));
+                        atomicXor(S.occ + ((j.t2 * D.L[2] + j.jz) * D.L[1] + j.jy) * D.row_words + (j.jx >> 4),
+                                  (ion ^ (uint32_t)SP_V) << occ_shift(j.jx));
+                        S.d[3 * v] += nb.d[0];
+                        S.d[3 * v + 1] += nb.d[1];
+                        S.d[3 * v + 2] += nb.d[2];
+                        if (tracer) {
+                            const int64_t s_lin = (((int64_t)t * D.L[2] + z) * D.L[1] + y) * D.L[0] + x;
+                            const int64_t j_lin = (((int64_t)j.t2 * D.L[2] + j.jz) * D.L[1] + j.jy) * D.L[0] + j.jx;
+                            int32_t* ts = tracer + 3 * (D.site_off + s_lin);
+                            int32_t* tj = tracer + 3 * (D.site_off + j_lin);
+                            ts[0] = tj[0] - nb.d[0];
+                            ts[1] = tj[1] - nb.d[1];
+                            ts[2] = tj[2] - nb.d[2];
+                            tj[0] = tj[1] = tj[2] = 0;
+                        }
+                        S.key[v] = key32(j.t2, j.jx, j.jy, j.jz);
+                        mark_dirty(D, S.dirty, x, y, z, fid);
+                        mark_dirty(D, S.dirty, j.jx, j.jy, j.jz, fid);
+                        const bool owned = j.jx >= lo0 && j.jx < hi0 && j.jy >= lo1 && j.jy < hi1 &&
+                                           j.jz >= lo2 && j.jz < hi2;
+                        if (!owned) {
+                            // leaves the fragment: unlink here (a zero-rate slot does not
+                            // change which event the running sums select), push to the owner
+                            const int nxt = S.next[v];
+                            if (sel_prev < 0) S.head[fid] = nxt;
+                            else S.next[sel_prev] = (int16_t)nxt;
+                            const int gx = frag_of(j.jx, D.base[0], D.rem[0]);
+                            const int gy = frag_of(j.jy, D.base[1], D.rem[1]);
+                            const int gz = frag_of(j.jz, D.base[2], D.rem[2]);
+                            const int g2 = (gz * D.nf[1] + gy) * D.nf[0] + gx;
+                            // lock-free push: g2 does not run in this phase, so its list only
+                            // receives pushes; links are read after the phase barrier
+                            S.next[v] = (int16_t)atomicExch(S.head + g2, v);
+                            ++my_hand;
                         }
                     }
-                    // apply the exchange
-                    const int v = sl[sm_];
-                    int t, x, y, z;
-                    split_key(key_s[v], t, x, y, z);
-                    const NbEntry nb = sh.nb[t][sq];
-                    const int jx = wrapc(x + nb.dc[0], D.L[0]);
-                    const int jy = wrapc(y + nb.dc[1], D.L[1]);
-                    const int jz = wrapc(z + nb.dc[2], D.L[2]);
-                    atomicXor(occ_s + (((int64_t)t * D.L[2] + z) * D.L[1] + y) * D.row_words + (x >> 4),
-                              ((uint32_t)SP_V ^ (uint32_t)ion) << occ_shift(x));
-                    atomicXor(occ_s + (((int64_t)nb.t2 * D.L[2] + jz) * D.L[1] + jy) * D.row_words + (jx >> 4),
-                              ((uint32_t)ion ^ (uint32_t)SP_V) << occ_shift(jx));
-                    d_s[3 * v] += nb.d[0];
-                    d_s[3 * v + 1] += nb.d[1];
-                    d_s[3 * v + 2] += nb.d[2];
-                    if (tracer) {
-                        const int64_t s_lin = (((int64_t)t * D.L[2] + z) * D.L[1] + y) * D.L[0] + x;
-                        const int64_t j_lin = (((int64_t)nb.t2 * D.L[2] + jz) * D.L[1] + jy) * D.L[0] + jx;
-                        int32_t* ts = tracer + 3 * (D.site_off + s_lin);
-                        int32_t* tj = tracer + 3 * (D.site_off + j_lin);
-                        ts[0] = tj[0] - nb.d[0];
-                        ts[1] = tj[1] - nb.d[1];
-                        ts[2] = tj[2] - nb.d[2];
-                        tj[0] = tj[1] = tj[2] = 0;
-                    }
-                    key_s[v] = make_key(nb.t2, jx, jy, jz);
-                    const bool owned = jx >= lo_c[0] && jx < hi_c[0] && jy >= lo_c[1] && jy < hi_c[1] &&
-                                       jz >= lo_c[2] && jz < hi_c[2];
-                    if (!owned) {
-                        const int gx = frag_of(jx, D.base[0], D.rem[0]);
-                        const int gy = frag_of(jy, D.base[1], D.rem[1]);
-                        const int gz = frag_of(jz, D.base[2], D.rem[2]);
-                        const int g2 = (gz * D.nf[1] + gy) * D.nf[0] + gx;
-                        next_s[v] = atomicExch(head_s + g2, v);
-                        sl[sm_] |= 0x8000u;
-                        ++my_hand;
-                    }
+                    __syncwarp(gmask);
                     clock = __dadd_rn(clock, dth);
                     ++i;
                 }
-                my_hops += i;
-                // surviving vacancies stay linked to this fragment
-                int head = -1;
-                for (int m = 0; m < n; ++m) {
-                    if (sl[m] & 0x8000u) continue;
-                    next_s[sl[m]] = head;
-                    head = sl[m];
+                if (q == 0) {
+                    S.S[fid] = tot;
+                    S.dirty[fid] = 0;
+                    my_hops += i;
                 }
-                head_s[fid] = head;
+                __syncwarp(gmask);
             }
             __syncthreads();
         }
@@ -357,24 +524,26 @@ __global__ void __launch_bounds__(256) k_resident(const RepDesc* __restrict__ de
         char* dst = reinterpret_cast<char*>(occ + D.occ_word_off);
         for (uint32_t off = 0; off < occ_bytes; off += BULK_CHUNK) {
             const uint32_t nb = min(BULK_CHUNK, occ_bytes - off);
-            bulk_s2g(dst + off, dyn + off, nb);
+            bulk_s2g(dst + off, S.occ + off / 4, nb);
         }
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
     }
-    for (int64_t f = tid; f < nfrag; f += blockDim.x) {
+    for (int f = tid; f < nfrag; f += blockDim.x) {
         const int64_t g = D.frag_base + f;
         int k = 0;
-        for (int v = head_s[f]; v >= 0; v = next_s[v], ++k) {
+        for (int v = S.head[f]; v >= 0; v = S.next[v], ++k) {
             if (k >= cap) {
                 atomicOr(status, STATUS_OVERFLOW);
                 break;
             }
+            int t, x, y, z;
+            split32(S.key[v], t, x, y, z);
             VacRec rr;
-            rr.key = key_s[v];
-            rr.d[0] = d_s[3 * v];
-            rr.d[1] = d_s[3 * v + 1];
-            rr.d[2] = d_s[3 * v + 2];
-            rr.id = id_s[v];
+            rr.key = make_key(t, x, y, z);
+            rr.d[0] = S.d[3 * v];
+            rr.d[1] = S.d[3 * v + 1];
+            rr.d[2] = S.d[3 * v + 2];
+            rr.id = S.id[v];
             recs[g * cap + k] = rr;
         }
         counts[g] = k;
