@@ -127,7 +127,7 @@ struct kmc_batch {
     NbTable nbt{};
     int32_t* d_reps = nullptr;   // resident replica ids, class by class
     int64_t* d_nvac = nullptr;   // vacancies per replica
-    struct RClass { int start, count; size_t smem; cudaStream_t st; cudaEvent_t done; };
+    struct RClass { int start, count; size_t smem; int threads; cudaStream_t st; cudaEvent_t done; };
     std::vector<RClass> rclass;
     cudaEvent_t fork = nullptr;
     bool any_global = true;
@@ -238,27 +238,30 @@ int plan_residency(kmc_batch* b)
                          b->cap <= RESIDENT_MAX_SLOTS;
     const size_t bounds[4] = {24 * 1024, 48 * 1024, 96 * 1024, RESIDENT_MAX_SMEM};
     std::vector<std::vector<int>> cls(4);
-    std::vector<size_t> need(b->n, 0), cmax(4, 0);
+    std::vector<size_t> cmax(4, 0);
     b->any_global = false;
     for (int r = 0; r < b->n; ++r) {
-        need[r] = resident_smem_bytes(b->desc[r], b->n_vac[r]);
-        const bool fits = allowed && need[r] <= RESIDENT_MAX_SMEM;
-        b->desc[r].resident = fits ? 1 : 0;
-        if (!fits) {
+        int c = -1;
+        size_t need = 0;
+        for (int k = 0; k < 4 && allowed && c < 0; ++k) {
+            need = resident_smem_bytes(b->desc[r], b->n_vac[r], b->cap, resident_threads_for(bounds[k]));
+            if (need <= bounds[k]) c = k;
+        }
+        b->desc[r].resident = c >= 0 ? 1 : 0;
+        if (c < 0) {
             b->any_global = true;
             continue;
         }
-        int c = 0;
-        while (need[r] > bounds[c]) ++c;
         cls[c].push_back(r);
-        cmax[c] = std::max(cmax[c], need[r]);
+        cmax[c] = std::max(cmax[c], need);
     }
     if (b->opts.schedule == 2 && b->any_global)
         return fail(FKMC_EINVAL, "schedule 2 needs every replica to fit the resident kernel (mixed form)");
     std::vector<int32_t> order;
     for (int c = 0; c < 4; ++c) {
         if (cls[c].empty()) continue;
-        kmc_batch::RClass rc{(int)order.size(), (int)cls[c].size(), cmax[c], nullptr, nullptr};
+        kmc_batch::RClass rc{(int)order.size(), (int)cls[c].size(), cmax[c], resident_threads_for(bounds[c]),
+                             nullptr, nullptr};
         for (int r : cls[c]) order.push_back(r);
         CK(cudaStreamCreateWithFlags(&rc.st, cudaStreamNonBlocking), "stream");
         CK(cudaEventCreateWithFlags(&rc.done, cudaEventDisableTiming), "event");
@@ -495,8 +498,8 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
         CK(cudaEventRecord(b->fork, b->st), "event record");
         for (auto& c : b->rclass) {
             CK(cudaStreamWaitEvent(c.st, b->fork, 0), "stream wait");
-            CK(launch_resident(b->d_desc, b->d_reps + c.start, c.count, b->d_nvac, c.smem, windows, b->occ,
-                               b->recs, b->counts, b->tracer, b->stats, b->status, b->cap, b->nbt, c.st),
+            CK(launch_resident(b->d_desc, b->d_reps + c.start, c.count, b->d_nvac, c.smem, c.threads, windows,
+                               b->occ, b->recs, b->counts, b->tracer, b->stats, b->status, b->cap, b->nbt, c.st),
                "resident kernel");
             CK(cudaEventRecord(c.done, c.st), "event record");
         }

@@ -17,10 +17,11 @@
 //           event total S; with the first draw of the phase, E/S > window
 //           proves that nothing happens, and the fragment is skipped.
 //           Everything else goes to a compact list.
-//   run     one group of 8 lanes per listed fragment (lane q evaluates
-//           neighbour direction q of every vacancy): exact total, clock,
-//           selection by group scan, exchange, hand-off, and "dirty" marks on
-//           every fragment whose box or halo holds one of the two changed sites.
+//   run     one warp per listed fragment (lane = 4 slots x 8 directions per
+//           32-event chunk; the warp draws 64 events' random numbers at once):
+//           exact total, clock, selection by warp scan, exchange, hand-off,
+//           and "dirty" marks on the owners of every vacancy next to one of the
+//           two changed sites -- exactly the fragments whose total changed.
 // At the end the occupancy goes back with a TMA bulk store and the records go
 // back to the per-fragment lists.
 #include <cuda_runtime.h>
@@ -133,13 +134,15 @@ struct Layout {
     unsigned long long* S;
     uint8_t* dirty;
     int32_t* act;
+    int16_t* wslot;   // per warp: vacancy index of each slot (-1: handed off)
+    int8_t* wtype;    // per warp: rate type of each event (-1: none)
 };
 
 
-__host__ __device__ inline size_t layout_bytes(int64_t words, int64_t nv, int64_t nfrag, int64_t ncls,
-                                               size_t* off /* 9 offsets or null */)
+__host__ __device__ inline size_t layout_bytes(int64_t words, int64_t nv, int64_t nfrag, int64_t ncls, int cap,
+                                               int nwarps, size_t* off /* 11 offsets or null */)
 {
-    size_t o[9];
+    size_t o[11];
     size_t b = 0;
     o[0] = b; b += (size_t)words * 4; b = (b + 15) & ~(size_t)15;   // occupancy (bulk-copied)
     o[6] = b; b += (size_t)nfrag * 8; b = (b + 15) & ~(size_t)15;   // cached totals
@@ -149,17 +152,20 @@ __host__ __device__ inline size_t layout_bytes(int64_t words, int64_t nv, int64_
     o[8] = b; b += (size_t)ncls * 4;                                  // screened list
     o[5] = b; b += (size_t)nfrag * 4;                                 // list heads
     o[4] = b; b += (size_t)nv * 2;                                    // next links
+    o[9] = b; b += (size_t)nwarps * cap * 2;                         // per-warp slots
     o[7] = b; b += (size_t)nfrag;                                     // dirty flags
+    o[10] = b; b += (size_t)nwarps * cap * 8;                        // per-warp event types
     b = (b + 127) & ~(size_t)127;
     if (off)
-        for (int k = 0; k < 9; ++k) off[k] = o[k];
+        for (int k = 0; k < 11; ++k) off[k] = o[k];
     return b;
 }
 
-__device__ __forceinline__ Layout carve(unsigned char* dyn, int64_t words, int64_t nv, int64_t nfrag, int64_t ncls)
+__device__ __forceinline__ Layout carve(unsigned char* dyn, int64_t words, int64_t nv, int64_t nfrag, int64_t ncls,
+                                        int cap, int nwarps)
 {
-    size_t o[9];
-    layout_bytes(words, nv, nfrag, ncls, o);
+    size_t o[11];
+    layout_bytes(words, nv, nfrag, ncls, cap, nwarps, o);
     Layout L;
     L.occ = reinterpret_cast<uint32_t*>(dyn + o[0]);
     L.key = reinterpret_cast<uint32_t*>(dyn + o[1]);
@@ -170,6 +176,8 @@ __device__ __forceinline__ Layout carve(unsigned char* dyn, int64_t words, int64
     L.S = reinterpret_cast<unsigned long long*>(dyn + o[6]);
     L.dirty = reinterpret_cast<uint8_t*>(dyn + o[7]);
     L.act = reinterpret_cast<int32_t*>(dyn + o[8]);
+    L.wslot = reinterpret_cast<int16_t*>(dyn + o[9]);
+    L.wtype = reinterpret_cast<int8_t*>(dyn + o[10]);
     return L;
 }
 
@@ -208,43 +216,33 @@ __device__ __forceinline__ unsigned long long event_rate(const Shared& sh, const
     return code == SP_V ? 0ull : (unsigned long long)sh.D.q[code * 3 + sh.nb[t][q].d[2] + 1];
 }
 
-// mark every fragment other than `self` whose box or one-cell halo holds cell (x,y,z)
-__device__ __forceinline__ void mark_dirty(const RepDesc& D, uint8_t* dirty, int x, int y, int z, int self)
+// owner fragment of cell (x,y,z)
+__device__ __forceinline__ int owner_of(const RepDesc& D, int x, int y, int z)
 {
-    const int c[3] = {x, y, z};
-    int cand[3][3], nc[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const int o = frag_of(c[d], D.base[d], D.rem[d]);
-        nc[d] = 0;
-        cand[d][nc[d]++] = o;
-        if (D.nf[d] > 1) {
-            if (c[d] == frag_start(o, D.base[d], D.rem[d])) cand[d][nc[d]++] = o == 0 ? D.nf[d] - 1 : o - 1;
-            if (c[d] == frag_start(o + 1, D.base[d], D.rem[d]) - 1)
-                cand[d][nc[d]++] = o == D.nf[d] - 1 ? 0 : o + 1;
-        }
-    }
-    for (int a = 0; a < nc[2]; ++a)
-        for (int b = 0; b < nc[1]; ++b)
-            for (int e = 0; e < nc[0]; ++e) {
-                const int f = (cand[2][a] * D.nf[1] + cand[1][b]) * D.nf[0] + cand[0][e];
-                if (f != self) dirty[f] = 1;
-            }
+    return (frag_of(z, D.base[2], D.rem[2]) * D.nf[1] + frag_of(y, D.base[1], D.rem[1])) * D.nf[0] +
+           frag_of(x, D.base[0], D.rem[0]);
+}
+
+// exact product 2^F * d for a positive normal double (exponent add)
+__device__ __forceinline__ double scale_pow2(double d, int F)
+{
+    return __longlong_as_double(__double_as_longlong(d) + ((long long)F << 52));
 }
 
 }  // namespace
 
-size_t resident_smem_bytes(const RepDesc& D, int64_t n_vac)
+size_t resident_smem_bytes(const RepDesc& D, int64_t n_vac, int cap, int threads)
 {
     const int64_t words = 3 * (int64_t)D.L[2] * D.L[1] * D.row_words;
     const int64_t nfrag = (int64_t)D.nf[0] * D.nf[1] * D.nf[2];
     const int64_t ncls = (int64_t)((D.nf[0] + 1) / 2) * ((D.nf[1] + 1) / 2) * ((D.nf[2] + 1) / 2);
     if (D.L[0] > 1024 || D.L[1] > 1024 || D.L[2] > 1024 || n_vac > 32767 || nfrag > 32767)
         return ~(size_t)0;  // compact keys and 16-bit links need these bounds
-    return layout_bytes(words, n_vac, nfrag, ncls, nullptr);
+    return layout_bytes(words, n_vac, nfrag, ncls, cap, threads / 32, nullptr);
 }
 
-__global__ void __launch_bounds__(256) k_resident(const RepDesc* __restrict__ descs,
+template <int NT>
+__global__ void __launch_bounds__(NT) k_resident(const RepDesc* __restrict__ descs,
                                                   const int32_t* __restrict__ reps,
                                                   const int64_t* __restrict__ nvac, uint64_t windows,
                                                   uint32_t* occ, VacRec* recs, int32_t* counts,
@@ -270,7 +268,7 @@ __global__ void __launch_bounds__(256) k_resident(const RepDesc* __restrict__ de
     const int64_t words = 3 * (int64_t)D.L[2] * D.L[1] * D.row_words;
     const int nfrag = D.nf[0] * D.nf[1] * D.nf[2];
     const int ncls_max = ((D.nf[0] + 1) / 2) * ((D.nf[1] + 1) / 2) * ((D.nf[2] + 1) / 2);
-    const Layout S = carve(dyn, words, n_vac, nfrag, ncls_max);
+    const Layout S = carve(dyn, words, n_vac, nfrag, ncls_max, cap, NT / 32);
 
     // ---- stage in: occupancy by TMA bulk copies, records by plain loads
     const uint32_t occ_bytes = (uint32_t)(words * 4);
@@ -322,10 +320,10 @@ __global__ void __launch_bounds__(256) k_resident(const RepDesc* __restrict__ de
 
     const uint64_t hop_k1 = key_word(D.replica, PURPOSE_HOP);
     const int lane = tid & 31;
-    const int q = lane & 7;                       // neighbour direction of this lane
-    const int grp = tid >> 3;                     // 8-lane group id in the CTA
-    const int ngrp = blockDim.x >> 3;
-    const unsigned gmask = 0xffu << (lane & 24);  // lanes of this group
+    const int warp = tid >> 5;
+    const unsigned FULL = 0xffffffffu;
+    int16_t* wslot = S.wslot + warp * cap;
+    int8_t* wtype = S.wtype + warp * cap * 8;
     unsigned long long my_hops = 0, my_hand = 0;
 
     for (uint64_t wk = 0; wk < windows; ++wk) {
@@ -360,15 +358,15 @@ __global__ void __launch_bounds__(256) k_resident(const RepDesc* __restrict__ de
                     if (tot == 0ull) continue;
                     const U64x4 blk = philox4x64((uint64_t)fid, w, 0, 0, D.seed, hop_k1);
                     const float ratio = __fdiv_rn(neglog32(blk.x[0]), __ull2float_rn(tot));
-                    const double dth = __dmul_rn((double)ratio, D.two_pow_F);
+                    const double dth = scale_pow2((double)ratio, D.F);
                     active = !(__dadd_rn(0.0, dth) > D.theta_tau);
                 }
                 if (active) S.act[atomicAdd(&sh.nact, 1)] = fid;
             }
             __syncthreads();
-            // ---- run: one 8-lane group per listed fragment
+            // ---- run: one warp per listed fragment
             const int nact = sh.nact;
-            for (int a = grp; a < nact; a += ngrp) {
+            for (int a = warp; a < nact; a += NT / 32) {
                 const int fid = S.act[a];
                 const int fz = fid / (D.nf[0] * D.nf[1]);
                 const int fy = (fid / D.nf[0]) % D.nf[1];
@@ -376,95 +374,111 @@ __global__ void __launch_bounds__(256) k_resident(const RepDesc* __restrict__ de
                 const int lo0 = frag_start(fx, D.base[0], D.rem[0]), hi0 = frag_start(fx + 1, D.base[0], D.rem[0]);
                 const int lo1 = frag_start(fy, D.base[1], D.rem[1]), hi1 = frag_start(fy + 1, D.base[1], D.rem[1]);
                 const int lo2 = frag_start(fz, D.base[2], D.rem[2]), hi2 = frag_start(fz + 1, D.base[2], D.rem[2]);
-                // slots in ascending site order: sort the fragment's list in place
-                if (q == 0) {
-                    int sorted = -1;
-                    int64_t n = 0;
-                    for (int v = S.head[fid]; v >= 0;) {
-                        const int nx = S.next[v];
-                        const uint32_t k = S.key[v];
-                        if (sorted < 0 || S.key[sorted] > k) {
-                            S.next[v] = (int16_t)sorted;
-                            sorted = v;
-                        } else {
-                            int pv = sorted;
-                            while (S.next[pv] >= 0 && S.key[S.next[pv]] < k) pv = S.next[pv];
-                            S.next[v] = S.next[pv];
-                            S.next[pv] = (int16_t)v;
-                        }
-                        v = nx;
-                        if (++n > n_vac) {  // a list longer than the vacancy count is corrupt
+                // slots: the fragment's vacancies in ascending site order
+                int n = 0;
+                if (lane == 0) {
+                    for (int v = S.head[fid]; v >= 0; v = S.next[v]) {
+                        if (n >= cap) {
                             atomicOr(status, STATUS_OVERFLOW);
                             break;
                         }
+                        const uint32_t k = S.key[v];
+                        int m = n++;
+                        while (m > 0 && S.key[wslot[m - 1]] > k) {
+                            wslot[m] = wslot[m - 1];
+                            --m;
+                        }
+                        wslot[m] = (int16_t)v;
                     }
-                    S.head[fid] = sorted;
                 }
-                __syncwarp(gmask);
+                n = __shfl_sync(FULL, n, 0);
+                __syncwarp();
+                const int nch = (n + 3) >> 2;
+                auto compute_types = [&]() {
+                    for (int c = 0; c < nch; ++c) {
+                        const int e = c * 32 + lane, m = e >> 3;
+                        int ty = -1;
+                        if (m < n && wslot[m] >= 0) {
+                            int code;
+                            const uint32_t k = S.key[wslot[m]];
+                            event_rate(sh, S.occ, k, e & 7, &code);
+                            ty = code == SP_V ? -1 : code * 3 + sh.nb[k >> 30][e & 7].d[2] + 1;
+                        }
+                        wtype[e] = (int8_t)ty;
+                    }
+                    __syncwarp();
+                };
+                compute_types();
 
                 double clock = 0.0;
-                uint64_t i = 0, blk_id = ~0ull;
-                U64x4 blk;
-                blk.x[0] = blk.x[1] = blk.x[2] = blk.x[3] = 0;
+                uint64_t i = 0, batch = ~0ull;
+                uint64_t xs_even = 0, xs_odd = 0;
+                float E_even = 0.f, E_odd = 0.f;
                 unsigned long long tot = 0;
                 for (;;) {
-                    // exact total: lane q sums direction q over the vacancies, then a group reduction
+                    // exact total of the fragment's events (order-free integer sum)
                     unsigned long long part = 0;
-                    for (int v = S.head[fid]; v >= 0; v = S.next[v]) part += event_rate(sh, S.occ, S.key[v], q, nullptr);
-                    part += __shfl_xor_sync(gmask, part, 1, 8);
-                    part += __shfl_xor_sync(gmask, part, 2, 8);
-                    part += __shfl_xor_sync(gmask, part, 4, 8);
+                    for (int c = 0; c < nch; ++c) {
+                        const int ty = wtype[c * 32 + lane];
+                        part += ty < 0 ? 0ull : (unsigned long long)D.q[ty];
+                    }
+#pragma unroll
+                    for (int off = 16; off; off >>= 1) part += __shfl_xor_sync(FULL, part, off);
                     tot = part;
                     if (tot == 0ull) break;
                     if (i >= MAX_EVENTS_PER_PHASE) {
-                        if (q == 0) atomicOr(status, STATUS_EVENT_LIMIT);
+                        if (lane == 0) atomicOr(status, STATUS_EVENT_LIMIT);
                         break;
                     }
-                    if ((i >> 1) != blk_id) {
-                        blk_id = i >> 1;
-                        blk = philox4x64((uint64_t)fid, w, blk_id, 0, D.seed, hop_k1);
+                    if ((i >> 6) != batch) {  // draws of events [64 batch, 64 batch + 64)
+                        batch = i >> 6;
+                        const U64x4 blk = philox4x64((uint64_t)fid, w, 32 * batch + lane, 0, D.seed, hop_k1);
+                        xs_even = blk.x[1];
+                        xs_odd = blk.x[3];
+                        E_even = neglog32(blk.x[0]);
+                        E_odd = neglog32(blk.x[2]);
                     }
-                    const uint64_t xt = (i & 1) ? blk.x[2] : blk.x[0];
-                    const uint64_t xs = (i & 1) ? blk.x[3] : blk.x[1];
-                    const float ratio = __fdiv_rn(neglog32(xt), __ull2float_rn(tot));
-                    const double dth = __dmul_rn((double)ratio, D.two_pow_F);
-                    if (__dadd_rn(clock, dth) > D.theta_tau) break;
+                    const int src = (int)((i >> 1) & 31);
+                    const bool odd = (i & 1) != 0;
+                    const uint64_t xs = __shfl_sync(FULL, odd ? xs_odd : xs_even, src);
+                    const float E = __shfl_sync(FULL, odd ? E_odd : E_even, src);
+                    const float ratio = __fdiv_rn(E, __ull2float_rn(tot));
+                    const double nclock = __dadd_rn(clock, scale_pow2((double)ratio, D.F));
+                    if (nclock > D.theta_tau) break;
                     const unsigned long long target = __umul64hi(xs, tot);
-                    // first event (slot order, then direction) whose running sum exceeds the target
-                    unsigned long long P = 0;
-                    int sel_v = -1, sel_prev = -1, sel_q = 0, sel_code = 0, prev = -1;
-                    for (int v = S.head[fid]; v >= 0; prev = v, v = S.next[v]) {
-                        int code;
-                        const unsigned long long rt = event_rate(sh, S.occ, S.key[v], q, &code);
-                        unsigned long long inc = rt;
+                    // first event whose running sum exceeds the target
+                    unsigned long long carry = 0;
+                    int e_sel = -1;
+                    for (int c = 0; c < nch; ++c) {
+                        const int ty = wtype[c * 32 + lane];
+                        unsigned long long inc = ty < 0 ? 0ull : (unsigned long long)D.q[ty];
 #pragma unroll
-                        for (int off = 1; off < 8; off <<= 1) {
-                            const unsigned long long t2 = __shfl_up_sync(gmask, inc, off, 8);
-                            if (q >= off) inc += t2;
+                        for (int off = 1; off < 32; off <<= 1) {
+                            const unsigned long long t2 = __shfl_up_sync(FULL, inc, off);
+                            if (lane >= off) inc += t2;
                         }
-                        const unsigned long long tv = __shfl_sync(gmask, inc, 7, 8);
-                        if (P + tv > target) {
-                            const unsigned bal = __ballot_sync(gmask, P + inc > target) >> (lane & 24);
-                            sel_q = __ffs(bal) - 1;
-                            sel_code = __shfl_sync(gmask, code, sel_q, 8);
-                            sel_v = v;
-                            sel_prev = prev;
+                        inc += carry;
+                        const unsigned bal = __ballot_sync(FULL, inc > target);
+                        if (bal) {
+                            e_sel = c * 32 + __ffs(bal) - 1;
                             break;
                         }
-                        P += tv;
+                        carry = __shfl_sync(FULL, inc, 31);
                     }
-                    if (sel_v < 0) {  // cannot happen: the target lies below the total
-                        if (q == 0) atomicOr(status, STATUS_OVERFLOW);
+                    if (e_sel < 0) {  // cannot happen: the target lies below the total
+                        if (lane == 0) atomicOr(status, STATUS_OVERFLOW);
                         break;
                     }
-                    // apply the exchange (lane 0 of the group)
-                    if (q == 0) {
-                        const int v = sel_v;
-                        int t, x, y, z;
-                        split32(S.key[v], t, x, y, z);
-                        const NbEntry nb = sh.nb[t][sel_q];
-                        const NbSite j = nb_site(sh, t, x, y, z, sel_q);
-                        const uint32_t ion = (uint32_t)sel_code;
+                    const int m = e_sel >> 3, qd = e_sel & 7;
+                    const int v = wslot[m];
+                    int t, x, y, z;
+                    split32(S.key[v], t, x, y, z);
+                    const NbEntry nb = sh.nb[t][qd];
+                    const NbSite j = nb_site(sh, t, x, y, z, qd);
+                    const bool owned = j.jx >= lo0 && j.jx < hi0 && j.jy >= lo1 && j.jy < hi1 && j.jz >= lo2 &&
+                                       j.jz < hi2;
+                    if (lane == 0) {  // apply the exchange
+                        const uint32_t ion = (uint32_t)(wtype[e_sel] / 3);
                         atomicXor(S.occ + ((t * D.L[2] + z) * D.L[1] + y) * D.row_words + (x >> 4),
                                   ((uint32_t)SP_V ^ ion) << occ_shift(x));
                         atomicXor(S.occ + ((j.t2 * D.L[2] + j.jz) * D.L[1] + j.jy) * D.row_words + (j.jx >> 4),
@@ -483,36 +497,48 @@ __global__ void __launch_bounds__(256) k_resident(const RepDesc* __restrict__ de
                             tj[0] = tj[1] = tj[2] = 0;
                         }
                         S.key[v] = key32(j.t2, j.jx, j.jy, j.jz);
-                        mark_dirty(D, S.dirty, x, y, z, fid);
-                        mark_dirty(D, S.dirty, j.jx, j.jy, j.jz, fid);
-                        const bool owned = j.jx >= lo0 && j.jx < hi0 && j.jy >= lo1 && j.jy < hi1 &&
-                                           j.jz >= lo2 && j.jz < hi2;
                         if (!owned) {
-                            // leaves the fragment: unlink here (a zero-rate slot does not
-                            // change which event the running sums select), push to the owner
-                            const int nxt = S.next[v];
-                            if (sel_prev < 0) S.head[fid] = nxt;
-                            else S.next[sel_prev] = (int16_t)nxt;
-                            const int gx = frag_of(j.jx, D.base[0], D.rem[0]);
-                            const int gy = frag_of(j.jy, D.base[1], D.rem[1]);
-                            const int gz = frag_of(j.jz, D.base[2], D.rem[2]);
-                            const int g2 = (gz * D.nf[1] + gy) * D.nf[0] + gx;
-                            // lock-free push: g2 does not run in this phase, so its list only
-                            // receives pushes; links are read after the phase barrier
+                            // leaves the fragment: its slot goes dead (zero rate), the record
+                            // is pushed onto the owner's list (the owner does not run in this
+                            // phase, so that list only receives pushes; links are read after
+                            // the phase barrier)
+                            wslot[m] = -1;
+                            const int g2 = owner_of(D, j.jx, j.jy, j.jz);
                             S.next[v] = (int16_t)atomicExch(S.head + g2, v);
                             ++my_hand;
                         }
                     }
-                    __syncwarp(gmask);
-                    clock = __dadd_rn(clock, dth);
+                    __syncwarp();
+                    // the fragments whose totals changed: owners of the vacancies next
+                    // to the two changed sites (lanes 0-7 look around s, 8-15 around j)
+                    if (lane < 16) {
+                        const int bt = lane < 8 ? t : j.t2;
+                        const int bx = lane < 8 ? x : j.jx, by = lane < 8 ? y : j.jy, bz = lane < 8 ? z : j.jz;
+                        const NbSite c = nb_site(sh, bt, bx, by, bz, lane & 7);
+                        if (site_code(sh, S.occ, c.t2, c.jx, c.jy, c.jz) == SP_V) {
+                            const int g = owner_of(D, c.jx, c.jy, c.jz);
+                            if (g != fid) S.dirty[g] = 1;
+                        }
+                    }
+                    compute_types();
+                    clock = nclock;
                     ++i;
                 }
-                if (q == 0) {
+                // surviving vacancies stay linked to this fragment, in slot order
+                if (lane == 0) {
+                    int head = -1;
+                    for (int m = n - 1; m >= 0; --m) {
+                        const int v = wslot[m];
+                        if (v < 0) continue;
+                        S.next[v] = (int16_t)head;
+                        head = v;
+                    }
+                    S.head[fid] = head;
                     S.S[fid] = tot;
                     S.dirty[fid] = 0;
                     my_hops += i;
                 }
-                __syncwarp(gmask);
+                __syncwarp();
             }
             __syncthreads();
         }
@@ -560,18 +586,34 @@ __global__ void __launch_bounds__(256) k_resident(const RepDesc* __restrict__ de
 
 cudaError_t resident_prepare()
 {
-    return cudaFuncSetAttribute(k_resident, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)RESIDENT_MAX_SMEM);
+    cudaError_t e = cudaSuccess;
+    for (auto fn : {k_resident<128>, k_resident<256>, k_resident<512>}) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RESIDENT_MAX_SMEM);
+        if (e != cudaSuccess) return e;
+    }
+    return e;
+}
+
+int resident_threads_for(size_t smem_class_bound)
+{
+    return smem_class_bound <= 48 * 1024 ? 128 : (smem_class_bound <= 96 * 1024 ? 256 : 512);
 }
 
 cudaError_t launch_resident(const RepDesc* d_descs, const int32_t* d_reps, int nreps, const int64_t* d_nvac,
-                            size_t smem, uint64_t windows, uint32_t* occ, VacRec* recs, int32_t* counts,
-                            int32_t* tracer, unsigned long long* stats, uint32_t* status, int cap,
-                            const NbTable& nbt, cudaStream_t st)
+                            size_t smem, int threads, uint64_t windows, uint32_t* occ, VacRec* recs,
+                            int32_t* counts, int32_t* tracer, unsigned long long* stats, uint32_t* status,
+                            int cap, const NbTable& nbt, cudaStream_t st)
 {
     if (nreps <= 0) return cudaSuccess;
-    k_resident<<<nreps, 256, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts, tracer, stats,
-                                         status, cap, nbt);
+    if (threads == 128)
+        k_resident<128><<<nreps, 128, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts, tracer,
+                                                  stats, status, cap, nbt);
+    else if (threads == 256)
+        k_resident<256><<<nreps, 256, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts, tracer,
+                                                  stats, status, cap, nbt);
+    else
+        k_resident<512><<<nreps, 512, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts, tracer,
+                                                  stats, status, cap, nbt);
     return cudaGetLastError();
 }
 
