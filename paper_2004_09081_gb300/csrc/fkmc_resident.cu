@@ -133,16 +133,19 @@ struct Layout {
     int32_t* head;
     unsigned long long* S;
     uint8_t* dirty;
-    int32_t* act;
+    int32_t* act;          // screened fragments
+    float* act_E;          // their first two exponential variates (events 0, 1)
+    uint64_t* act_xs;      // and selection words
+    uint16_t* frag_of_c;   // cell -> fragment index: x cells, then y, then z
     int16_t* wslot;   // per warp: vacancy index of each slot (-1: handed off)
     int8_t* wtype;    // per warp: rate type of each event (-1: none)
 };
 
 
 __host__ __device__ inline size_t layout_bytes(int64_t words, int64_t nv, int64_t nfrag, int64_t ncls, int cap,
-                                               int nwarps, size_t* off /* 11 offsets or null */)
+                                               int nwarps, int ltot, size_t* off /* 14 offsets or null */)
 {
-    size_t o[11];
+    size_t o[14];
     size_t b = 0;
     o[0] = b; b += (size_t)words * 4; b = (b + 15) & ~(size_t)15;   // occupancy (bulk-copied)
     o[6] = b; b += (size_t)nfrag * 8; b = (b + 15) & ~(size_t)15;   // cached totals
@@ -150,6 +153,10 @@ __host__ __device__ inline size_t layout_bytes(int64_t words, int64_t nv, int64_
     o[2] = b; b += (size_t)nv * 12;                                   // displacements
     o[3] = b; b += (size_t)nv * 4;                                    // ids
     o[8] = b; b += (size_t)ncls * 4;                                  // screened list
+    b = (b + 15) & ~(size_t)15;
+    o[11] = b; b += (size_t)ncls * 16;                                // screened: selection words
+    o[12] = b; b += (size_t)ncls * 8;                                 // screened: variates
+    o[13] = b; b += (size_t)ltot * 2;                                 // cell -> fragment tables
     o[5] = b; b += (size_t)nfrag * 4;                                 // list heads
     o[4] = b; b += (size_t)nv * 2;                                    // next links
     o[9] = b; b += (size_t)nwarps * cap * 2;                         // per-warp slots
@@ -157,15 +164,15 @@ __host__ __device__ inline size_t layout_bytes(int64_t words, int64_t nv, int64_
     o[10] = b; b += (size_t)nwarps * cap * 8;                        // per-warp event types
     b = (b + 127) & ~(size_t)127;
     if (off)
-        for (int k = 0; k < 11; ++k) off[k] = o[k];
+        for (int k = 0; k < 14; ++k) off[k] = o[k];
     return b;
 }
 
 __device__ __forceinline__ Layout carve(unsigned char* dyn, int64_t words, int64_t nv, int64_t nfrag, int64_t ncls,
-                                        int cap, int nwarps)
+                                        int cap, int nwarps, int ltot)
 {
-    size_t o[11];
-    layout_bytes(words, nv, nfrag, ncls, cap, nwarps, o);
+    size_t o[14];
+    layout_bytes(words, nv, nfrag, ncls, cap, nwarps, ltot, o);
     Layout L;
     L.occ = reinterpret_cast<uint32_t*>(dyn + o[0]);
     L.key = reinterpret_cast<uint32_t*>(dyn + o[1]);
@@ -176,6 +183,9 @@ __device__ __forceinline__ Layout carve(unsigned char* dyn, int64_t words, int64
     L.S = reinterpret_cast<unsigned long long*>(dyn + o[6]);
     L.dirty = reinterpret_cast<uint8_t*>(dyn + o[7]);
     L.act = reinterpret_cast<int32_t*>(dyn + o[8]);
+    L.act_xs = reinterpret_cast<uint64_t*>(dyn + o[11]);
+    L.act_E = reinterpret_cast<float*>(dyn + o[12]);
+    L.frag_of_c = reinterpret_cast<uint16_t*>(dyn + o[13]);
     L.wslot = reinterpret_cast<int16_t*>(dyn + o[9]);
     L.wtype = reinterpret_cast<int8_t*>(dyn + o[10]);
     return L;
@@ -216,11 +226,10 @@ __device__ __forceinline__ unsigned long long event_rate(const Shared& sh, const
     return code == SP_V ? 0ull : (unsigned long long)sh.D.q[code * 3 + sh.nb[t][q].d[2] + 1];
 }
 
-// owner fragment of cell (x,y,z)
-__device__ __forceinline__ int owner_of(const RepDesc& D, int x, int y, int z)
+// owner fragment of cell (x,y,z), from the per-dimension tables
+__device__ __forceinline__ int owner_of(const RepDesc& D, const uint16_t* fo, int x, int y, int z)
 {
-    return (frag_of(z, D.base[2], D.rem[2]) * D.nf[1] + frag_of(y, D.base[1], D.rem[1])) * D.nf[0] +
-           frag_of(x, D.base[0], D.rem[0]);
+    return (fo[D.L[0] + D.L[1] + z] * D.nf[1] + fo[D.L[0] + y]) * D.nf[0] + fo[x];
 }
 
 // exact product 2^F * d for a positive normal double (exponent add)
@@ -238,7 +247,7 @@ size_t resident_smem_bytes(const RepDesc& D, int64_t n_vac, int cap, int threads
     const int64_t ncls = (int64_t)((D.nf[0] + 1) / 2) * ((D.nf[1] + 1) / 2) * ((D.nf[2] + 1) / 2);
     if (D.L[0] > 1024 || D.L[1] > 1024 || D.L[2] > 1024 || n_vac > 32767 || nfrag > 32767)
         return ~(size_t)0;  // compact keys and 16-bit links need these bounds
-    return layout_bytes(words, n_vac, nfrag, ncls, cap, threads / 32, nullptr);
+    return layout_bytes(words, n_vac, nfrag, ncls, cap, threads / 32, D.L[0] + D.L[1] + D.L[2], nullptr);
 }
 
 template <int NT>
@@ -268,7 +277,7 @@ __global__ void __launch_bounds__(NT) k_resident(const RepDesc* __restrict__ des
     const int64_t words = 3 * (int64_t)D.L[2] * D.L[1] * D.row_words;
     const int nfrag = D.nf[0] * D.nf[1] * D.nf[2];
     const int ncls_max = ((D.nf[0] + 1) / 2) * ((D.nf[1] + 1) / 2) * ((D.nf[2] + 1) / 2);
-    const Layout S = carve(dyn, words, n_vac, nfrag, ncls_max, cap, NT / 32);
+    const Layout S = carve(dyn, words, n_vac, nfrag, ncls_max, cap, NT / 32, D.L[0] + D.L[1] + D.L[2]);
 
     // ---- stage in: occupancy by TMA bulk copies, records by plain loads
     const uint32_t occ_bytes = (uint32_t)(words * 4);
@@ -280,6 +289,11 @@ __global__ void __launch_bounds__(NT) k_resident(const RepDesc* __restrict__ des
             const uint32_t n = min(BULK_CHUNK, occ_bytes - off);
             bulk_g2s(S.occ + off / 4, src + off, n, &sh.bar);
         }
+    }
+    for (int k = tid; k < D.L[0] + D.L[1] + D.L[2]; k += blockDim.x) {
+        const int d = k < D.L[0] ? 0 : (k < D.L[0] + D.L[1] ? 1 : 2);
+        const int c = d == 0 ? k : (d == 1 ? k - D.L[0] : k - D.L[0] - D.L[1]);
+        S.frag_of_c[k] = (uint16_t)frag_of(c, D.base[d], D.rem[d]);
     }
     for (int f = tid; f < nfrag; f += blockDim.x) {
         const int64_t g = D.frag_base + f;
@@ -352,16 +366,24 @@ __global__ void __launch_bounds__(NT) k_resident(const RepDesc* __restrict__ des
                 f2 = D.nf[2] == 1 ? 0 : 2 * f2 + bit[2];
                 const int fid = (f2 * D.nf[1] + f1) * D.nf[0] + f0;
                 if (S.head[fid] < 0) continue;
-                bool active = S.dirty[fid] != 0;
+                const bool dirty = S.dirty[fid] != 0;
+                const unsigned long long tot = S.S[fid];
+                if (!dirty && tot == 0ull) continue;
+                const U64x4 blk = philox4x64((uint64_t)fid, w, 0, 0, D.seed, hop_k1);
+                const float E0 = neglog32(blk.x[0]);
+                bool active = dirty;
                 if (!active) {
-                    const unsigned long long tot = S.S[fid];
-                    if (tot == 0ull) continue;
-                    const U64x4 blk = philox4x64((uint64_t)fid, w, 0, 0, D.seed, hop_k1);
-                    const float ratio = __fdiv_rn(neglog32(blk.x[0]), __ull2float_rn(tot));
-                    const double dth = scale_pow2((double)ratio, D.F);
-                    active = !(__dadd_rn(0.0, dth) > D.theta_tau);
+                    const float ratio = __fdiv_rn(E0, __ull2float_rn(tot));
+                    active = !(__dadd_rn(0.0, scale_pow2((double)ratio, D.F)) > D.theta_tau);
                 }
-                if (active) S.act[atomicAdd(&sh.nact, 1)] = fid;
+                if (active) {
+                    const int a = atomicAdd(&sh.nact, 1);
+                    S.act[a] = fid;
+                    S.act_E[2 * a] = E0;
+                    S.act_E[2 * a + 1] = neglog32(blk.x[2]);
+                    S.act_xs[2 * a] = blk.x[1];
+                    S.act_xs[2 * a + 1] = blk.x[3];
+                }
             }
             __syncthreads();
             // ---- run: one warp per listed fragment
@@ -430,18 +452,28 @@ __global__ void __launch_bounds__(NT) k_resident(const RepDesc* __restrict__ des
                         if (lane == 0) atomicOr(status, STATUS_EVENT_LIMIT);
                         break;
                     }
-                    if ((i >> 6) != batch) {  // draws of events [64 batch, 64 batch + 64)
-                        batch = i >> 6;
-                        const U64x4 blk = philox4x64((uint64_t)fid, w, 32 * batch + lane, 0, D.seed, hop_k1);
-                        xs_even = blk.x[1];
-                        xs_odd = blk.x[3];
-                        E_even = neglog32(blk.x[0]);
-                        E_odd = neglog32(blk.x[2]);
+                    uint64_t xs;
+                    float E;
+                    if (i < 2) {  // block 0, drawn by the screen pass
+                        xs = S.act_xs[2 * a + (int)i];
+                        E = S.act_E[2 * a + (int)i];
+                    } else {
+                        // events [2 + 64 b, 66 + 64 b) come from blocks 1 + 32 b + lane
+                        const uint64_t k = i - 2;
+                        if ((k >> 6) != batch) {
+                            batch = k >> 6;
+                            const U64x4 blk =
+                                philox4x64((uint64_t)fid, w, 1 + 32 * batch + lane, 0, D.seed, hop_k1);
+                            xs_even = blk.x[1];
+                            xs_odd = blk.x[3];
+                            E_even = neglog32(blk.x[0]);
+                            E_odd = neglog32(blk.x[2]);
+                        }
+                        const int src = (int)((k >> 1) & 31);
+                        const bool odd = (k & 1) != 0;
+                        xs = __shfl_sync(FULL, odd ? xs_odd : xs_even, src);
+                        E = __shfl_sync(FULL, odd ? E_odd : E_even, src);
                     }
-                    const int src = (int)((i >> 1) & 31);
-                    const bool odd = (i & 1) != 0;
-                    const uint64_t xs = __shfl_sync(FULL, odd ? xs_odd : xs_even, src);
-                    const float E = __shfl_sync(FULL, odd ? E_odd : E_even, src);
                     const float ratio = __fdiv_rn(E, __ull2float_rn(tot));
                     const double nclock = __dadd_rn(clock, scale_pow2((double)ratio, D.F));
                     if (nclock > D.theta_tau) break;
@@ -503,7 +535,7 @@ __global__ void __launch_bounds__(NT) k_resident(const RepDesc* __restrict__ des
                             // phase, so that list only receives pushes; links are read after
                             // the phase barrier)
                             wslot[m] = -1;
-                            const int g2 = owner_of(D, j.jx, j.jy, j.jz);
+                            const int g2 = owner_of(D, S.frag_of_c, j.jx, j.jy, j.jz);
                             S.next[v] = (int16_t)atomicExch(S.head + g2, v);
                             ++my_hand;
                         }
@@ -516,7 +548,7 @@ __global__ void __launch_bounds__(NT) k_resident(const RepDesc* __restrict__ des
                         const int bx = lane < 8 ? x : j.jx, by = lane < 8 ? y : j.jy, bz = lane < 8 ? z : j.jz;
                         const NbSite c = nb_site(sh, bt, bx, by, bz, lane & 7);
                         if (site_code(sh, S.occ, c.t2, c.jx, c.jy, c.jz) == SP_V) {
-                            const int g = owner_of(D, c.jx, c.jy, c.jz);
+                            const int g = owner_of(D, S.frag_of_c, c.jx, c.jy, c.jz);
                             if (g != fid) S.dirty[g] = 1;
                         }
                     }
