@@ -145,27 +145,29 @@ struct Layout {
 __host__ __device__ inline size_t layout_bytes(int64_t words, int64_t nv, int64_t nfrag, int64_t ncls, int cap,
                                                int nwarps, int ltot, size_t* off /* 14 offsets or null */)
 {
-    size_t o[14];
+    // every array starts on a 16-byte boundary, whatever the sizes before it
+    const size_t sz[14] = {
+        (size_t)words * 4,         // 0 occupancy (bulk-copied)
+        (size_t)nv * 4,            // 1 keys
+        (size_t)nv * 12,           // 2 displacements
+        (size_t)nv * 4,            // 3 ids
+        (size_t)nv * 2,            // 4 next links
+        (size_t)nfrag * 4,         // 5 list heads
+        (size_t)nfrag * 8,         // 6 cached totals
+        (size_t)nfrag,             // 7 dirty flags
+        (size_t)ncls * 4,          // 8 screened list
+        (size_t)nwarps * cap * 2,  // 9 per-warp slots
+        (size_t)nwarps * cap * 8,  // 10 per-warp event types
+        (size_t)ncls * 16,         // 11 screened: selection words
+        (size_t)ncls * 8,          // 12 screened: variates
+        (size_t)ltot * 2,          // 13 cell -> fragment tables
+    };
     size_t b = 0;
-    o[0] = b; b += (size_t)words * 4; b = (b + 15) & ~(size_t)15;   // occupancy (bulk-copied)
-    o[6] = b; b += (size_t)nfrag * 8; b = (b + 15) & ~(size_t)15;   // cached totals
-    o[1] = b; b += (size_t)nv * 4;                                    // keys
-    o[2] = b; b += (size_t)nv * 12;                                   // displacements
-    o[3] = b; b += (size_t)nv * 4;                                    // ids
-    o[8] = b; b += (size_t)ncls * 4;                                  // screened list
-    b = (b + 15) & ~(size_t)15;
-    o[11] = b; b += (size_t)ncls * 16;                                // screened: selection words
-    o[12] = b; b += (size_t)ncls * 8;                                 // screened: variates
-    o[13] = b; b += (size_t)ltot * 2;                                 // cell -> fragment tables
-    o[5] = b; b += (size_t)nfrag * 4;                                 // list heads
-    o[4] = b; b += (size_t)nv * 2;                                    // next links
-    o[9] = b; b += (size_t)nwarps * cap * 2;                         // per-warp slots
-    o[7] = b; b += (size_t)nfrag;                                     // dirty flags
-    o[10] = b; b += (size_t)nwarps * cap * 8;                        // per-warp event types
-    b = (b + 127) & ~(size_t)127;
-    if (off)
-        for (int k = 0; k < 14; ++k) off[k] = o[k];
-    return b;
+    for (int k = 0; k < 14; ++k) {
+        if (off) off[k] = b;
+        b += (sz[k] + 15) & ~(size_t)15;
+    }
+    return (b + 127) & ~(size_t)127;
 }
 
 __device__ __forceinline__ Layout carve(unsigned char* dyn, int64_t words, int64_t nv, int64_t nfrag, int64_t ncls,
