@@ -107,6 +107,7 @@ typedef struct {
     uint64_t handoffs; /* exchanges that moved a vacancy into another fragment */
     uint64_t windows;  /* windows run by this call */
     double gpu_ms;     /* device time of the call's kernels (CUDA events) */
+    uint64_t launches; /* kernel launches made by the call */
 } kmc_run_stats;
 
 typedef struct {
@@ -225,6 +226,36 @@ int kmc_rate_table(const kmc_barrier_table* t, double T_K, double field_z_Vpm, d
  * dx, dy, dz} (24 rows of int32): neighbour cell offset and displacement in
  * units of a/2, ascending in (dx, dy, dz). */
 void kmc_neighbour_table(int32_t out[168]);
+
+/* Allocation-free variant of kmc_read_moments_all.  The paper has no
+ * counterpart: this is a service for callers that cannot allocate device
+ * memory -- a host framework that owns every device allocation through its
+ * own pool, a plugin that is handed fixed buffers, a serving loop whose memory
+ * is planned ahead.  The caller passes its own device buffers and gets the
+ * moments back; the library calls no cudaMalloc, cudaFree or allocating
+ * routine here.
+ *   d_records        device array of offsets[n_groups] x cap_v 24-byte records
+ *                    {u64 site key, int32 d[3], uint32 id} (the batch's layout),
+ *                    fragment-major; only the displacements d are read
+ *   d_counts         device int32[offsets[n_groups]]: slots in use per fragment
+ *   fragment_offsets host int64[n_groups + 1]: group g owns fragments
+ *                    [offsets[g], offsets[g+1]); offsets[0] = 0, non-decreasing
+ *   n_groups         1 .. FKMC_NOALLOC_MAX_GROUPS
+ *   out              host int64[7 n_groups], as in kmc_read_moments
+ *   stream           cudaStream_t (NULL = legacy default stream); synchronous
+ * Its only scratch (the offsets and the accumulators, about 256 KiB) is a
+ * static device array that every GPU loading the library holds until the
+ * process exits.  The first call on a device looks up that array's address
+ * (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.  All calls share the array and it keeps the last call's
+ * contents (the accumulators are cleared at the start of each call), so calls
+ * that overlap on the GPU -- on two streams, or from two threads -- race.
+ * Errors: FKMC_EINVAL for null pointers, n_groups outside [1, 4096], cap_v
+ * outside [1, 256] or bad offsets; FKMC_ECUDA. */
+#define FKMC_NOALLOC_MAX_GROUPS 4096
+int kmc_vacancy_moments_noalloc(const void* d_records, const int32_t* d_counts,
+                                const int64_t* fragment_offsets, int32_t n_groups, int32_t cap_v,
+                                int64_t* out, void* stream);
 
 int kmc_destroy(kmc_batch* b);
 

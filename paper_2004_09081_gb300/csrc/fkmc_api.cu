@@ -99,6 +99,14 @@ int ceil_log2(int64_t v)
 
 }  // namespace
 
+namespace fkmc {
+// error reporting shared with the other translation units of the library
+int set_error(int code, const char* msg)
+{
+    return fail(code, msg);
+}
+}  // namespace fkmc
+
 struct kmc_batch {
     int n = 0;
     kmc_opts opts{};
@@ -527,6 +535,7 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
             stats->handoffs += b->stats_host[2 * r + 1] - before[2 * r + 1];
         }
         stats->windows = windows;
+        stats->launches = (windows > 0 ? b->rclass.size() : 0) + (b->any_global ? 8 * windows : 0);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, b->ev0, b->ev1);
         stats->gpu_ms = ms;

@@ -6,6 +6,9 @@
 
 namespace fkmc {
 
+// sets the thread-local message of kmc_last_error() and returns `code`
+int set_error(int code, const char* msg);
+
 cudaError_t upload_neighbours(const NbEntry* host24);
 cudaError_t launch_init(const RepDesc& D, int b_bits, int64_t n_vac, int64_t n_total, uint32_t* occ,
                         VacRec* recs, int32_t* counts, int cap, uint32_t* status, cudaStream_t st);

@@ -53,7 +53,7 @@ class kmc_opts(C.Structure):
 
 class kmc_run_stats(C.Structure):
     _fields_ = [("hops", C.c_uint64), ("handoffs", C.c_uint64), ("windows", C.c_uint64),
-                ("gpu_ms", C.c_double)]
+                ("gpu_ms", C.c_double), ("launches", C.c_uint64)]
 
 
 class kmc_replica_info(C.Structure):
@@ -86,6 +86,7 @@ _SIGNATURES = {
     "kmc_num_replicas": (_I32, [_P]),
     "kmc_rate_table": (C.c_int, [_P, _D, _D, _D, _I32, _P, _P, _P, _P]),
     "kmc_neighbour_table": (None, [_P]),
+    "kmc_vacancy_moments_noalloc": (C.c_int, [_P, _P, _P, _I32, _I32, _P, _P]),
     "kmc_destroy": (C.c_int, [_P]),
     "kmc_last_error": (C.c_char_p, []),
 }
@@ -243,6 +244,21 @@ def kmc_neighbour_table() -> np.ndarray:
     out = np.zeros((3, 8, 7), np.int32)
     load().kmc_neighbour_table(_ptr(out))
     return out
+
+
+FKMC_NOALLOC_MAX_GROUPS = 4096
+
+
+def kmc_vacancy_moments_noalloc(records_ptr: int, counts_ptr: int, fragment_offsets, cap_v: int,
+                                stream_ptr: int = 0) -> np.ndarray:
+    """Moments per group from caller-owned device buffers; the library
+    allocates nothing for this call (scratch is a static device array)."""
+    off = np.ascontiguousarray(fragment_offsets, np.int64)
+    n = off.size - 1
+    out = np.zeros((max(n, 1), 7), np.int64)
+    _check(load().kmc_vacancy_moments_noalloc(C.c_void_p(records_ptr), C.c_void_p(counts_ptr), _ptr(off), n,
+                                               int(cap_v), _ptr(out), C.c_void_p(stream_ptr)))
+    return out[:n]
 
 
 def kmc_destroy(h):
