@@ -244,15 +244,19 @@ int plan_residency(kmc_batch* b)
     b->rclass.clear();
     const bool allowed = b->opts.precision == FKMC_MIXED && b->opts.schedule != 1 &&
                          b->cap <= RESIDENT_MAX_SLOTS;
-    const size_t bounds[4] = {24 * 1024, 48 * 1024, 96 * 1024, RESIDENT_MAX_SMEM};
-    std::vector<std::vector<int>> cls(4);
-    std::vector<size_t> cmax(4, 0);
+    // launch classes: (shared-memory bound, threads); a replica takes the first
+    // class its state fits, so small replicas pack several CTAs per SM and the
+    // largest get the most warps that still fit beside their state
+    const size_t bounds[5] = {24 * 1024, 48 * 1024, 96 * 1024, RESIDENT_MAX_SMEM, RESIDENT_MAX_SMEM};
+    const int threads[5] = {128, 128, 256, 1024, 512};
+    std::vector<std::vector<int>> cls(5);
+    std::vector<size_t> cmax(5, 0);
     b->any_global = false;
     for (int r = 0; r < b->n; ++r) {
         int c = -1;
         size_t need = 0;
-        for (int k = 0; k < 4 && allowed && c < 0; ++k) {
-            need = resident_smem_bytes(b->desc[r], b->n_vac[r], b->cap, resident_threads_for(bounds[k]));
+        for (int k = 0; k < 5 && allowed && c < 0; ++k) {
+            need = resident_smem_bytes(b->desc[r], b->n_vac[r], b->cap, threads[k]);
             if (need <= bounds[k]) c = k;
         }
         b->desc[r].resident = c >= 0 ? 1 : 0;
@@ -266,10 +270,9 @@ int plan_residency(kmc_batch* b)
     if (b->opts.schedule == 2 && b->any_global)
         return fail(FKMC_EINVAL, "schedule 2 needs every replica to fit the resident kernel (mixed form)");
     std::vector<int32_t> order;
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < 5; ++c) {
         if (cls[c].empty()) continue;
-        kmc_batch::RClass rc{(int)order.size(), (int)cls[c].size(), cmax[c], resident_threads_for(bounds[c]),
-                             nullptr, nullptr};
+        kmc_batch::RClass rc{(int)order.size(), (int)cls[c].size(), cmax[c], threads[c], nullptr, nullptr};
         for (int r : cls[c]) order.push_back(r);
         CK(cudaStreamCreateWithFlags(&rc.st, cudaStreamNonBlocking), "stream");
         CK(cudaEventCreateWithFlags(&rc.done, cudaEventDisableTiming), "event");

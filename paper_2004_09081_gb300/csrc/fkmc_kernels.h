@@ -28,7 +28,6 @@ cudaError_t launch_moments_all(const RepDesc* d_descs, int nrep, const VacRec* r
 constexpr int RESIDENT_MAX_SLOTS = 64;               // vacancies per fragment a thread can hold
 constexpr size_t RESIDENT_MAX_SMEM = 220 * 1024;     // dynamic shared memory per replica CTA
 size_t resident_smem_bytes(const RepDesc& D, int64_t n_vac, int cap, int threads);
-int resident_threads_for(size_t smem_class_bound);
 cudaError_t resident_prepare();
 cudaError_t launch_resident(const RepDesc* d_descs, const int32_t* d_reps, int nreps, const int64_t* d_nvac,
                             size_t smem, int threads, uint64_t windows, uint32_t* occ, VacRec* recs,

@@ -120,6 +120,7 @@ struct Shared {
     int perm[8];
     int nv_count;
     int nact;
+    int next_act;
     unsigned long long hops, hand;
     int abort;
 };
@@ -253,7 +254,7 @@ size_t resident_smem_bytes(const RepDesc& D, int64_t n_vac, int cap, int threads
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT) k_resident(const RepDesc* __restrict__ descs,
+__global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_resident(const RepDesc* __restrict__ descs,
                                                   const int32_t* __restrict__ reps,
                                                   const int64_t* __restrict__ nvac, uint64_t windows,
                                                   uint32_t* occ, VacRec* recs, int32_t* counts,
@@ -358,7 +359,10 @@ __global__ void __launch_bounds__(NT) k_resident(const RepDesc* __restrict__ des
                 cnt[d] = D.nf[d] == 1 ? (bit[d] == 0 ? 1 : 0) : D.nf[d] / 2;
             }
             const int ncls = cnt[0] * cnt[1] * cnt[2];
-            if (tid == 0) sh.nact = 0;
+            if (tid == 0) {
+                sh.nact = 0;
+                sh.next_act = 0;
+            }
             __syncthreads();
             // ---- screen: one thread per fragment of the colour
             for (int l = tid; l < ncls; l += blockDim.x) {
@@ -390,7 +394,12 @@ __global__ void __launch_bounds__(NT) k_resident(const RepDesc* __restrict__ des
             __syncthreads();
             // ---- run: one warp per listed fragment
             const int nact = sh.nact;
-            for (int a = warp; a < nact; a += NT / 32) {
+            for (;;) {
+                // warps take the screened fragments one at a time, as they become free
+                int a = 0;
+                if (lane == 0) a = atomicAdd(&sh.next_act, 1);
+                a = __shfl_sync(FULL, a, 0);
+                if (a >= nact) break;
                 const int fid = S.act[a];
                 const int fz = fid / (D.nf[0] * D.nf[1]);
                 const int fy = (fid / D.nf[0]) % D.nf[1];
@@ -621,16 +630,11 @@ __global__ void __launch_bounds__(NT) k_resident(const RepDesc* __restrict__ des
 cudaError_t resident_prepare()
 {
     cudaError_t e = cudaSuccess;
-    for (auto fn : {k_resident<128>, k_resident<256>, k_resident<512>}) {
+    for (auto fn : {k_resident<128>, k_resident<256>, k_resident<512>, k_resident<1024>}) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RESIDENT_MAX_SMEM);
         if (e != cudaSuccess) return e;
     }
     return e;
-}
-
-int resident_threads_for(size_t smem_class_bound)
-{
-    return smem_class_bound <= 48 * 1024 ? 128 : (smem_class_bound <= 96 * 1024 ? 256 : 512);
 }
 
 cudaError_t launch_resident(const RepDesc* d_descs, const int32_t* d_reps, int nreps, const int64_t* d_nvac,
@@ -645,6 +649,9 @@ cudaError_t launch_resident(const RepDesc* d_descs, const int32_t* d_reps, int n
     else if (threads == 256)
         k_resident<256><<<nreps, 256, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts, tracer,
                                                   stats, status, cap, nbt);
+    else if (threads == 1024)
+        k_resident<1024><<<nreps, 1024, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts, tracer,
+                                                    stats, status, cap, nbt);
     else
         k_resident<512><<<nreps, 512, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts, tracer,
                                                   stats, status, cap, nbt);

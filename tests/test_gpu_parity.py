@@ -200,7 +200,9 @@ def test_batched_workload_full_size_sampled(fk, orc):
         m = b.moments(r, 2)
         assert m[0] == reps[r].n_vac
     cap = b.info(0).cap_v
-    for r in (0, 1, 97, 200, 255):
+    # the largest replicas (1024- or 512-thread class) and a spread of others
+    largest = sorted(range(len(reps)), key=lambda r: -reps[r].n_vac)[:3]
+    for r in sorted(set(largest) | {0, 1, 97, 200, 255}):
         rep = reps[r]
         info = b.info(r)
         ref = orc.Lattice(rep.cells, tuple(info.nfrag), rep.n_vac, rep.n_H, seed=0, replica=r)
