@@ -39,10 +39,15 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--windows", type=int, default=64, help="windows per step")
+    p.add_argument("--windows", type=int, default=0, help="windows per step (0: the workload's default)")
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--workload", default="batched", choices=["batched", "sweep", "bulk", "um"],
+                   help="batched: 256 uneven replicas (the headline); sweep: SrTiO(3-x)H_x 32^3 at "
+                        "300..700 K; bulk: BaTiO(3-x)H_x 128^3; um: BaTiO3 L^3 under bias")
+    p.add_argument("--um-cells", type=int, default=2500, help="edge of the um-scale cube (cells)")
+    p.add_argument("--no-autotune", action="store_true", help="use the workload's default edge")
     return p.parse_args()
 
 
@@ -127,10 +132,12 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ helpers
-def make_batch(fk, wl, seed, precision, replicas=None):
+def make_batch(fk, wl, seed, precision, replicas=None, edge=None, tracer=None):
     reps = wl.replicas if replicas is None else [wl.replicas[i] for i in replicas]
-    b = fk.Batch([(*r.cells, r.a) for r in reps], [(r.n_vac, r.n_H) for r in reps], seed, edge=wl.edge,
-                 precision=precision)
+    nf = reps[0].nfrag if (len(reps) == 1 and reps[0].nfrag) else None
+    b = fk.Batch([(*r.cells, r.a) for r in reps], [(r.n_vac, r.n_H) for r in reps], seed,
+                 edge=wl.edge if edge is None else edge, nfrag=nf, precision=precision,
+                 tracer=wl.tracer if tracer is None else tracer)
     b.set_barriers([r.Ea_O for r in reps], [r.Ea_H for r in reps], [r.T for r in reps],
                    field_z=[r.field_z for r in reps])
     return b
@@ -196,16 +203,30 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+def kernel_source_hash() -> str:
+    """sha256 over the CUDA sources; a traffic figure taken on other sources is stale."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2004_09081_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
 def load_traffic(kernel_tag):
     """dram__bytes_read.sum + dram__bytes_write.sum per launch from the committed
-    ncu summary, or None."""
+    ncu summary, or None when absent or taken on different kernel sources."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
     e = d.get(kernel_tag)
-    return None if e is None else e.get("bytes_per_launch")
+    if e is None or e.get("source_sha256") != kernel_source_hash():
+        return None
+    return e.get("bytes_per_launch")
 
 
 # ------------------------------------------------------------------ reference arm
@@ -216,6 +237,7 @@ def run_reference(args):
         return
     wl = workloads.batched_batio3(args.seed)
     nrep = len(wl.replicas)
+    args.windows = args.windows or 64
     per_step_budget = 8.0
     times, hops_all, reps_done = [], 0, 0
     cursor = 0
@@ -245,6 +267,33 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
+def physics_report(fkmc, b, wl):
+    """The observables each workload is quoted with (Sec. Computational details):
+    D of V (and O, H- with tracer), drift and the Arrhenius fit of the T sweep."""
+    out = []
+    if len(wl.replicas) > 8:
+        return {"replicas": None, "note": "per-replica D in D_mixed_vs_plain; not listed for large batches"}
+    for r, rep in enumerate(wl.replicas):
+        row = {"T": rep.T, "cells": rep.cells[0], "n_vac": rep.n_vac, "n_H": rep.n_H}
+        Dx, D, v = b.D(r, fkmc.FKMC_V)
+        row.update({"D_V": D, "D_V_z": Dx[2], "D_V_xy": 0.5 * (Dx[0] + Dx[1]), "v_z_V": v})
+        if wl.tracer:
+            for sp, nm in ((fkmc.FKMC_O, "O"), (fkmc.FKMC_H, "H")):
+                if nm == "H" and rep.n_H == 0:
+                    continue
+                row["D_" + nm] = b.D(r, sp)[1]
+        out.append(row)
+    rep = {"replicas": out}
+    if wl.name.startswith("srtio3h_32c_Tsweep"):
+        kB = 8.617333262e-5
+        for nm in ("D_V", "D_O", "D_H"):
+            pts = [(1.0 / o["T"], math.log(o[nm])) for o in out if o.get(nm, 0) > 0]
+            if len(pts) >= 2:
+                x, y = np.array(pts).T
+                rep["Ea_apparent_" + nm[2:] + "_eV"] = float(-np.polyfit(x, y, 1)[0] * kB)
+    return rep
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -254,15 +303,29 @@ def main():
     ws, rank, local = dist_setup(True)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    from paper_2004_09081_gb300 import fkmc, workloads
+    from paper_2004_09081_gb300 import autotune, fkmc, workloads
     fkmc.load()
     seed = args.seed + rank  # each rank simulates its own independent batch (weak scaling)
-    wl = workloads.batched_batio3(seed)
+    makers = {"batched": workloads.batched_batio3, "sweep": workloads.srtio3_h_sweep,
+              "bulk": workloads.bulk_batio3, "um": lambda sd: workloads.um_batio3_bias(sd, args.um_cells)}
+    wl = makers[args.workload](seed)
     nrep = len(wl.replicas)
-    W = args.windows
+    default_windows = {"batched": 64, "sweep": 64, "bulk": 16, "um": 2}
+    W = args.windows if args.windows else default_windows[args.workload]
     stream = torch.cuda.current_stream()
+    reps = wl.replicas
+    precision = wl.precision
 
-    b = make_batch(fkmc, wl, seed, fkmc.FKMC_MIXED)
+    # K7: pick the fragment edge (batched workload; single lattices keep their stated partition)
+    edge, tuned = wl.edge, None
+    if args.workload == "batched" and not args.no_autotune:
+        best, res = autotune.autotune([(*r.cells, r.a) for r in reps], [(r.n_vac, r.n_H) for r in reps], seed,
+                                      [r.Ea_O for r in reps], [r.Ea_H for r in reps], [r.T for r in reps],
+                                      precision=precision)
+        edge = best["edge"]
+        tuned = [{"edge": c["edge"], "hops_per_s": h, "cap_v": cap} for c, h, cap in res]
+
+    b = make_batch(fkmc, wl, seed, precision, edge=edge)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def step():
@@ -282,6 +345,7 @@ def main():
     hops = 0
     kernel_ms = 0.0
     launches = 0
+    n_launch = 0
     wall0 = time.perf_counter()
     for k in range(args.steps):
         flush.fill_(k & 0xff)
@@ -291,6 +355,7 @@ def main():
         hops += s.hops
         kernel_ms += s.gpu_ms
         launches += s.launches + 1  # + the moment reduction
+        n_launch += s.launches
     torch.cuda.synchronize()
     barrier(ws)
     wall = time.perf_counter() - wall0
@@ -301,107 +366,128 @@ def main():
     hops_all = allreduce_sum(float(hops), ws, dev)
     value = hops_all / t_max
 
-    # roofline of the dominant kernel: the replica-resident window kernel (one
-    # launch per shared-memory size class, the classes run concurrently); the
-    # colour-phase kernel only runs replicas that do not fit one SM.
     peak, peak_kind = load_peaks()
-    n_launch = args.steps  # one concurrent set of class launches per kmc_run call
-    avg_launch_s = kernel_ms / 1e3 / n_launch
-    bytes_per_launch = hops / n_launch * B_ALG_PER_HOP
+    all_resident = n_launch <= args.steps * 5  # class launches only, no per-phase launches
+    if all_resident:
+        # the replica-resident kernel: one launch per shared-memory size class per call, the
+        # classes run concurrently, so a "launch" here is one call's concurrent set
+        units = args.steps
+        tag, kname = "k_resident_batched", "k_resident (replica-resident window kernel)"
+        note = ("lattice state lives in shared memory for the whole launch: DRAM traffic is the stage-in/out "
+                "of the state, not per hop; the kernel is bound by instruction issue and dependent latency "
+                "(see profiles/)")
+    else:
+        units = n_launch  # one launch per colour phase
+        tag = "k_phase_" + ("mixed_" if precision else "plain_") + args.workload
+        kname = "k_phase<%s> (colour-phase kernel)" % ("mixed" if precision else "plain")
+        note = ("one launch per colour phase; neighbour words read from L2/HBM with ld.global.cg; "
+                "algorithmic bytes = 160 B per hop at 32-byte sectors")
+    avg_launch_s = kernel_ms / 1e3 / units
+    bytes_per_launch = hops / units * B_ALG_PER_HOP
     achieved = bytes_per_launch / avg_launch_s / 1e9
-    traffic = load_traffic("k_resident_batched")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_kind": f"{peak_kind} hbm_gbs (of measured)",
-                "kernel": "k_resident (replica-resident window kernel)", "bytes_per_hop": B_ALG_PER_HOP,
-                "hops_per_launch": hops / n_launch, "avg_launch_us": avg_launch_s * 1e6,
-                "note": "lattice state lives in shared memory for the whole launch: DRAM traffic is the "
-                        "stage-in/out of the state, not per hop; the kernel is bound by instruction issue "
-                        "and dependent latency (see profiles/)"}
+                "traffic": load_traffic(tag), "peak_kind": f"{peak_kind} hbm_gbs",
+                "kernel": kname, "bytes_per_hop": B_ALG_PER_HOP, "hops_per_launch": hops / units,
+                "avg_launch_us": avg_launch_s * 1e6, "note": note}
 
     extra = {}
     if rank == 0:
+        extra["physics"] = physics_report(fkmc, b, wl)
         # end to end through the public API: host state blob -> GPU, run, moments -> host
         nbytes = fkmc.kmc_state_bytes(b.h)
-        host = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
-        fkmc.kmc_download_state(b.h, host.data_ptr(), nbytes)
-        e2e_steps = max(3, min(args.steps, 5))
-        e2e_hops = 0
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            fkmc.kmc_upload_state(b.h, host.data_ptr(), nbytes)
-            e2e_hops += b.run(W).hops
-            m = b.moments_all()
-        e2e_t = time.perf_counter() - t0
-        extra["e2e"] = {"value": e2e_hops / e2e_t, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-                        "d2h_bytes_per_step": int(m.nbytes), "steps": e2e_steps}
+        if nbytes <= (4 << 30):
+            host = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+            fkmc.kmc_download_state(b.h, host.data_ptr(), nbytes)
+            e2e_steps = max(3, min(args.steps, 5))
+            e2e_hops = 0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                fkmc.kmc_upload_state(b.h, host.data_ptr(), nbytes)
+                e2e_hops += b.run(W).hops
+                m = b.moments_all()
+            e2e_t = time.perf_counter() - t0
+            extra["e2e"] = {"value": e2e_hops / e2e_t, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                            "d2h_bytes_per_step": int(m.nbytes), "steps": e2e_steps}
+            del host
+        else:
+            extra["e2e"] = {"value": None, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": 0,
+                            "note": "state larger than 4 GiB: not re-uploaded every step"}
 
         if not args.no_plain:
             # accuracy: mixed vs plain FP64 from the same initial state, same draws
             Wacc = 4 * W
-            bm = make_batch(fkmc, wl, seed, fkmc.FKMC_MIXED)
-            bp = make_batch(fkmc, wl, seed, fkmc.FKMC_PLAIN)
+            bm = make_batch(fkmc, wl, seed, fkmc.FKMC_MIXED, edge=edge)
+            bp = make_batch(fkmc, wl, seed, fkmc.FKMC_PLAIN, edge=edge)
             hm, hp = bm.run(Wacc).hops, bp.run(Wacc).hops
             mm, mp = bm.moments_all(), bp.moments_all()
             rel = []
             for r in range(nrep):
                 tr = bp.info(r).window * bp.info(r).tau
-                Dm = D_from_moments(mm[r], tr, wl.replicas[r].a)
-                Dp = D_from_moments(mp[r], tr, wl.replicas[r].a)
+                Dm = D_from_moments(mm[r], tr, reps[r].a)
+                Dp = D_from_moments(mp[r], tr, reps[r].a)
                 if Dp > 0:
                     rel.append(abs(Dm - Dp) / Dp)
-            agg_m = float(mm[:, 4:7].sum()) / float(mm[:, 0].sum())
-            agg_p = float(mp[:, 4:7].sum()) / float(mp[:, 0].sum())
+            agg_m = float(mm[:, 4:7].sum()) / max(float(mm[:, 0].sum()), 1.0)
+            agg_p = float(mp[:, 4:7].sum()) / max(float(mp[:, 0].sum()), 1.0)
             same = sum(int(np.array_equal(mm[r], mp[r])) for r in range(nrep))
             bm.close()
             bp.close()
-            # plain FP64, replicas one at a time (the comparison form)
-            p_hops, p_ms = 0, 0.0
-            t0 = time.perf_counter()
-            for r in range(nrep):
-                b1 = make_batch(fkmc, wl, seed, fkmc.FKMC_PLAIN, replicas=[r])
-                # keep replica identity: batch of one keyed as replica 0 draws its own stream;
-                # throughput comparison only
-                s1 = b1.run(W)
-                p_hops += s1.hops
-                p_ms += s1.gpu_ms
-                b1.close()
-            p_wall = time.perf_counter() - t0
-            plain_rate = p_hops / (p_ms / 1e3)
-            # plain FP64 in one batch, for the split between batching and precision
-            bpb = make_batch(fkmc, wl, seed, fkmc.FKMC_PLAIN)
+            plain = {}
+            if nrep > 1:
+                # plain FP64, replicas one at a time (the comparison the method is quoted on)
+                p_hops, p_ms = 0, 0.0
+                t0 = time.perf_counter()
+                for r in range(nrep):
+                    # a batch of one is keyed as replica 0: its own stream, throughput comparison only
+                    b1 = make_batch(fkmc, wl, seed, fkmc.FKMC_PLAIN, replicas=[r], edge=edge)
+                    s1 = b1.run(W)
+                    p_hops += s1.hops
+                    p_ms += s1.gpu_ms
+                    b1.close()
+                plain["one_at_a_time"] = {"value": p_hops / (p_ms / 1e3), "unit": UNIT, "hops": p_hops,
+                                          "kernel_s": p_ms / 1e3, "wall_s": time.perf_counter() - t0}
+                plain["mixed_over_plain_one_at_a_time"] = value / plain["one_at_a_time"]["value"]
+            bpb = make_batch(fkmc, wl, seed, fkmc.FKMC_PLAIN, edge=edge)
             bpb.run(2)
             spb = bpb.run(W)
             bpb.close()
-            extra["plain_fp64"] = {
-                "one_at_a_time": {"value": plain_rate, "unit": UNIT, "hops": p_hops,
-                                  "kernel_s": p_ms / 1e3, "wall_s": p_wall},
-                "batched": {"value": spb.hops / (spb.gpu_ms / 1e3), "unit": UNIT},
-                "mixed_over_plain_one_at_a_time": value / plain_rate if plain_rate else None,
-                "mixed_over_plain_batched": (value / (spb.hops / (spb.gpu_ms / 1e3))) if spb.hops else None,
-            }
+            plain["batched"] = {"value": spb.hops / (spb.gpu_ms / 1e3), "unit": UNIT}
+            plain["mixed_over_plain_batched"] = value / plain["batched"]["value"] if spb.hops else None
+            extra["plain_fp64"] = plain
             extra["D_mixed_vs_plain"] = {
                 "windows": Wacc, "hops_mixed": hm, "hops_plain": hp,
-                "aggregate_msd_rel_err": abs(agg_m - agg_p) / agg_p,
+                "aggregate_msd_rel_err": abs(agg_m - agg_p) / agg_p if agg_p else None,
                 "per_replica_rel_err_median": float(np.median(rel)) if rel else None,
                 "per_replica_rel_err_max": float(np.max(rel)) if rel else None,
                 "replicas_bit_identical": same, "replicas": nrep,
             }
         if not args.no_cpu:
-            rate, ch, cs, cd = cpu_oracle_rate(wl, seed, W, 12.0)
-            extra["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                     "sample": f"first {cd} replicas of the batch, {W} windows each, "
-                                               f"serial C oracle ({ch} hops in {cs:.1f} s)"}
+            if args.workload == "um":
+                # the oracle holds one byte per site: time it on a 120^3 cube with the same
+                # density, field and temperature, and quote hops/s
+                small = workloads.um_batio3_bias(seed, 120)
+                rate, ch, cs, cd = cpu_oracle_rate(small, seed, 2, 12.0)
+                smp = f"120^3-cell cube with the same density, field and T, 2 windows ({ch} hops in {cs:.1f} s)"
+            else:
+                rate, ch, cs, cd = cpu_oracle_rate(wl, seed, min(W, 8) if nrep == 1 else W, 12.0)
+                smp = (f"first {cd} replicas, {W} windows each" if nrep > 1 else "the same lattice") + \
+                    f", serial C oracle ({ch} hops in {cs:.1f} s)"
+            extra["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": smp}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64+f32+f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64+f32+f64" if precision else "f64",
+            "data": "synthetic",
             "config": {"workload": wl.name, "replicas": nrep, "windows_per_step": W,
-                       "precision": "mixed (fp32 rates -> u64 fixed point, fp32 variate, fp64 clock)",
-                       "n_tau": 1.0, "edge": wl.edge, "l2": "flushed between timed steps (256 MiB write)",
-                       "schedule": "replica-resident kernel per shared-memory size class (auto)",
+                       "precision": ("mixed (fp32 rates -> u64 fixed point, fp32 variate, fp64 clock)"
+                                     if precision else "plain fp64"),
+                       "n_tau": 1.0, "edge": edge, "autotune": tuned,
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "schedule": ("replica-resident kernel per shared-memory size class" if all_resident
+                                    else "colour-phase kernel, one launch per phase"),
                        "seed": args.seed},
             "roofline": roofline,
             "clocks": clk,
