@@ -139,6 +139,14 @@ struct kmc_batch {
     std::vector<RClass> rclass;
     cudaEvent_t fork = nullptr;
     bool any_global = true;
+    // colour-phase path: per-window set-up, screen and run, captured once in a graph
+    unsigned long long* wctl = nullptr;  // [0] windows of this call so far, [1] current offset
+    uint32_t* perms = nullptr;           // colour order of every replica, this window
+    ActEntry* act = nullptr;             // screened fragments of a phase
+    int32_t* act_count = nullptr;        // per phase
+    int run_blocks = 0;
+    cudaStream_t cap_st = nullptr;
+    cudaGraphExec_t window_exec = nullptr;
 
     void* dalloc(size_t bytes)
     {
@@ -174,6 +182,10 @@ struct kmc_batch {
             if (c.done) cudaEventDestroy(c.done);
         }
         rclass.clear();
+        if (window_exec) cudaGraphExecDestroy(window_exec);
+        if (cap_st) cudaStreamDestroy(cap_st);
+        window_exec = nullptr;
+        cap_st = nullptr;
     }
 };
 
@@ -419,8 +431,13 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
     b->scratch_all = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * 7 * n);
     b->d_reps = (int32_t*)b->dalloc(sizeof(int32_t) * n);
     b->d_nvac = (int64_t*)b->dalloc(sizeof(int64_t) * n);
+    b->wctl = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * 2);
+    b->perms = (uint32_t*)b->dalloc(sizeof(uint32_t) * n);
+    b->act = (ActEntry*)b->dalloc(sizeof(ActEntry) * std::max<int64_t>(b->total_items, 1));
+    b->act_count = (int32_t*)b->dalloc(sizeof(int32_t) * 8);
     if (!b->occ || !b->recs || !b->counts || (o.tracer && !b->tracer) || !b->d_desc || !b->stats ||
-        !b->status || !b->scratch || !b->scratch_all || !b->d_reps || !b->d_nvac) {
+        !b->status || !b->scratch || !b->scratch_all || !b->d_reps || !b->d_nvac || !b->wctl || !b->perms ||
+        !b->act || !b->act_count) {
         b->release();
         delete b;
         return fail(FKMC_ENOMEM, "device allocation failed");
@@ -432,6 +449,7 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
     build_nb_table(b->nbt.e);
     step(upload_neighbours(&b->nbt.e[0][0]), "neighbour table upload");
     step(phase_prepare(b->cap), "kernel attributes");
+    step(run_pass_blocks(b->opts.precision, b->cap, &b->run_blocks), "occupancy query");
     step(resident_prepare(), "kernel attributes");
     step(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "event");
     step(cudaEventCreate(&b->ev0), "event");
@@ -515,12 +533,28 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
             CK(cudaEventRecord(c.done, c.st), "event record");
         }
     }
-    if (b->any_global)
-        for (uint64_t wk = 0; wk < windows; ++wk)
-            for (int p = 0; p < 8; ++p)
-                CK(launch_phase(b->opts.precision, b->d_desc, b->n, b->total_items, p, wk, b->occ, b->recs,
-                                b->counts, b->tracer, b->stats, b->status, b->cap, b->st),
-                   "phase kernel");
+    if (b->any_global && windows > 0) {
+        if (!b->window_exec) {
+            // capture one window (set-up + 8 x (screen, run)) once; every argument is fixed
+            CK(cudaStreamCreateWithFlags(&b->cap_st, cudaStreamNonBlocking), "stream");
+            cudaGraph_t graph = nullptr;
+            CK(cudaStreamBeginCapture(b->cap_st, cudaStreamCaptureModeThreadLocal), "graph capture");
+            cudaError_t le = launch_window(b->opts.precision, b->d_desc, b->n, b->total_items, b->wctl, b->perms,
+                                           b->act, b->act_count, b->occ, b->recs, b->counts, b->tracer,
+                                           b->stats, b->status, b->cap, b->run_blocks, b->cap_st);
+            cudaError_t ce = cudaStreamEndCapture(b->cap_st, &graph);
+            if (le != cudaSuccess) return cuda_fail(le, "window capture");
+            if (ce != cudaSuccess) return cuda_fail(ce, "window capture");
+            cudaError_t ie = cudaGraphInstantiate(&b->window_exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) {
+                b->window_exec = nullptr;
+                return cuda_fail(ie, "graph instantiate");
+            }
+        }
+        CK(cudaMemsetAsync(b->wctl, 0, sizeof(unsigned long long) * 2, b->st), "memset");
+        for (uint64_t wk = 0; wk < windows; ++wk) CK(cudaGraphLaunch(b->window_exec, b->st), "graph launch");
+    }
     if (!b->rclass.empty() && windows > 0)
         for (auto& c : b->rclass) CK(cudaStreamWaitEvent(b->st, c.done, 0), "stream wait");
     CK(cudaEventRecord(b->ev1, b->st), "event record");
@@ -538,7 +572,7 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
             stats->handoffs += b->stats_host[2 * r + 1] - before[2 * r + 1];
         }
         stats->windows = windows;
-        stats->launches = (windows > 0 ? b->rclass.size() : 0) + (b->any_global ? 8 * windows : 0);
+        stats->launches = (windows > 0 ? b->rclass.size() : 0) + (b->any_global ? 17 * windows : 0);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, b->ev0, b->ev1);
         stats->gpu_ms = ms;

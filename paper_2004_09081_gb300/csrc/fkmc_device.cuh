@@ -147,6 +147,35 @@ __device__ __forceinline__ float neglog32(uint64_t x)
     return -ln_u;
 }
 
+// A fragment that the screen pass of a colour phase keeps for the run pass,
+// with the first Philox block of its phase (events 0 and 1).
+struct ActEntry {
+    int32_t rep;        // replica index in the batch
+    int32_t pad;
+    int64_t fid;        // fragment index inside the replica
+    uint64_t xs[2];     // selection words of events 0, 1
+    uint64_t E[2];      // their exponential variates: fp64 bits (plain) or fp32 bits (mixed)
+};
+static_assert(sizeof(ActEntry) == 48, "active entry layout");
+
+// Colour order of window w as 8 nibbles (nibble p = colour of phase p):
+// Fisher-Yates shuffle of 0..7, j = mulhi(y_k, i+1), y_0..y_7 = Philox blocks (w,0), (w,1).
+__device__ __forceinline__ uint32_t colour_perm_packed(uint64_t seed, uint32_t replica, uint64_t w)
+{
+    const U64x4 b0 = philox4x64(w, 0, 0, 0, seed, key_word(replica, PURPOSE_PERM));
+    const U64x4 b1 = philox4x64(w, 1, 0, 0, seed, key_word(replica, PURPOSE_PERM));
+    const uint64_t y[8] = {b0.x[0], b0.x[1], b0.x[2], b0.x[3], b1.x[0], b1.x[1], b1.x[2], b1.x[3]};
+    uint32_t perm = 0x76543210u;
+#pragma unroll
+    for (int i = 7; i >= 1; --i) {
+        const int j = (int)__umul64hi(y[7 - i], (uint64_t)(i + 1));
+        const uint32_t pi = (perm >> (4 * i)) & 15u, pj = (perm >> (4 * j)) & 15u;
+        perm &= ~((15u << (4 * i)) | (15u << (4 * j)));
+        perm |= (pj << (4 * i)) | (pi << (4 * j));
+    }
+    return perm;
+}
+
 // ---------------------------------------------------------------- geometry
 // Neighbour table in constant memory, filled by the host at load time:
 // for site type t and neighbour n (ascending (dx,dy,dz)): packed

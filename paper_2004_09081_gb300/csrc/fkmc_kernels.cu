@@ -10,6 +10,8 @@
 //                trajectories).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "fkmc_device.cuh"
 #include "fkmc_kernels.h"
 
@@ -146,57 +148,123 @@ __device__ __forceinline__ void compute_types(const RepDesc& D, const uint32_t* 
     }
 }
 
+// Per-window set-up: colour order of every replica for this window, and the
+// screen counters of the 8 phases cleared.  wctl[0] counts the windows of the
+// current kmc_run call, wctl[1] holds the offset of the window being run.
+__global__ void k_window_setup(const RepDesc* __restrict__ descs, int nrep, unsigned long long* wctl,
+                               uint32_t* perms, int32_t* act_count)
+{
+    const uint64_t wk = wctl[0];
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrep; r += gridDim.x * blockDim.x)
+        perms[r] = colour_perm_packed(descs[r].seed, descs[r].replica, descs[r].window + wk);
+    if (blockIdx.x == 0 && threadIdx.x < 8) act_count[threadIdx.x] = 0;
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        wctl[1] = wk;
+        wctl[0] = wk + 1;
+    }
+}
+
+// Screen pass of a colour phase: one thread per fragment of the phase's colour
+// (every replica).  Fragments with vacancies go to the active list together
+// with their first Philox block, drawn here thirty-two fragments per warp
+// instead of once per fragment-warp.
 template <int PREC>
-__global__ void __launch_bounds__(128) k_phase(const RepDesc* __restrict__ descs, int nrep,
-                                               int64_t total_items, int phase, uint64_t wk,
-                                               uint32_t* occ, VacRec* recs, int32_t* counts,
-                                               int32_t* tracer, unsigned long long* stats,
-                                               uint32_t* status, int cap)
+__global__ void __launch_bounds__(256) k_screen(const RepDesc* __restrict__ descs, int nrep, int64_t total_items,
+                                                int phase, const unsigned long long* wctl,
+                                                const uint32_t* __restrict__ perms,
+                                                const int32_t* __restrict__ counts, ActEntry* act,
+                                                int32_t* act_count)
+{
+    const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool keep = false;
+    ActEntry e;
+    if (item < total_items) {
+        int lo = 0, hi = nrep - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (descs[mid].items_off <= item) lo = mid; else hi = mid - 1;
+        }
+        const RepDesc& D = descs[lo];
+        const int64_t local = item - D.items_off;
+        const int colour = (int)((perms[lo] >> (4 * phase)) & 15u);
+        int cnt[3], bit[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            bit[d] = (colour >> d) & 1;
+            cnt[d] = D.nf[d] == 1 ? (bit[d] == 0 ? 1 : 0) : D.nf[d] / 2;
+        }
+        if (!D.resident && local < (int64_t)cnt[0] * cnt[1] * cnt[2]) {
+            int f0 = (int)(local % cnt[0]);
+            int f1 = (int)((local / cnt[0]) % cnt[1]);
+            int f2 = (int)(local / ((int64_t)cnt[0] * cnt[1]));
+            f0 = D.nf[0] == 1 ? 0 : 2 * f0 + bit[0];
+            f1 = D.nf[1] == 1 ? 0 : 2 * f1 + bit[1];
+            f2 = D.nf[2] == 1 ? 0 : 2 * f2 + bit[2];
+            const int64_t fid = ((int64_t)f2 * D.nf[1] + f1) * D.nf[0] + f0;
+            if (counts[D.frag_base + fid] > 0) {
+                keep = true;
+                const uint64_t w = D.window + wctl[1];
+                const U64x4 blk = philox4x64((uint64_t)fid, w, 0, 0, D.seed, key_word(D.replica, PURPOSE_HOP));
+                e.rep = lo;
+                e.pad = 0;
+                e.fid = fid;
+                e.xs[0] = blk.x[1];
+                e.xs[1] = blk.x[3];
+                if constexpr (PREC == 0) {
+                    e.E[0] = (uint64_t)__double_as_longlong(neglog64(blk.x[0]));
+                    e.E[1] = (uint64_t)__double_as_longlong(neglog64(blk.x[2]));
+                } else {
+                    e.E[0] = (uint64_t)__float_as_uint(neglog32(blk.x[0]));
+                    e.E[1] = (uint64_t)__float_as_uint(neglog32(blk.x[2]));
+                }
+            }
+        }
+    }
+    // one atomic per warp for the slots of its kept fragments
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (!bal) return;
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == __ffs(bal) - 1) base = atomicAdd(act_count + phase, __popc(bal));
+    base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
+    if (keep) act[base + __popc(bal & ((1u << lane) - 1u))] = e;
+}
+
+// Run pass of a colour phase: one warp per screened fragment (grid-stride):
+// BKL on the fragment's vacancies until the next event would pass the window.
+template <int PREC>
+__global__ void __launch_bounds__(128) k_run(const RepDesc* __restrict__ descs, const ActEntry* __restrict__ act,
+                                             const int32_t* __restrict__ act_count, int phase,
+                                             const unsigned long long* wctl, uint32_t* occ, VacRec* recs,
+                                             int32_t* counts, int32_t* tracer, unsigned long long* stats,
+                                             uint32_t* status, int cap)
 {
     using A = Arith<PREC>;
     using V = typename A::V;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
-    if (item >= total_items) return;
-
-    // replica of this item
-    int lo = 0, hi = nrep - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (descs[mid].items_off <= item) lo = mid; else hi = mid - 1;
-    }
+    const int nact = act_count[phase];
+    const int nwarps_grid = gridDim.x * (blockDim.x >> 5);
+    for (int a = blockIdx.x * (blockDim.x >> 5) + wib; a < nact; a += nwarps_grid) {
+    const ActEntry ent = act[a];
+    const int lo = ent.rep;
     const RepDesc& D = descs[lo];
-    if (D.resident) return;
-    const int64_t local = item - D.items_off;
-    const uint64_t w = D.window + wk;
-    const int colour = colour_of_phase(D.seed, D.replica, w, phase, lane);
-
-    // fragment of the colour class
-    int cnt[3], bit[3];
+    const uint64_t w = D.window + wctl[1];
+    const int64_t fid = ent.fid;
+    int f[3], lo_c[3], hi_c[3];
+    f[0] = (int)(fid % D.nf[0]);
+    f[1] = (int)((fid / D.nf[0]) % D.nf[1]);
+    f[2] = (int)(fid / ((int64_t)D.nf[0] * D.nf[1]));
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        bit[d] = (colour >> d) & 1;
-        cnt[d] = D.nf[d] == 1 ? (bit[d] == 0 ? 1 : 0) : D.nf[d] / 2;
-    }
-    if (local >= (int64_t)cnt[0] * cnt[1] * cnt[2]) return;
-    int f[3];
-    f[0] = (int)(local % cnt[0]);
-    f[1] = (int)((local / cnt[0]) % cnt[1]);
-    f[2] = (int)(local / ((int64_t)cnt[0] * cnt[1]));
-    int lo_c[3], hi_c[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        f[d] = D.nf[d] == 1 ? 0 : 2 * f[d] + bit[d];
         lo_c[d] = frag_start(f[d], D.base[d], D.rem[d]);
         hi_c[d] = frag_start(f[d] + 1, D.base[d], D.rem[d]);
     }
-    const int64_t fid = ((int64_t)f[2] * D.nf[1] + f[1]) * D.nf[0] + f[0];
     const int64_t g = D.frag_base + fid;
 
     int nv = counts[g];
-    if (nv == 0) return;
     if (nv > cap) {
         if (lane == 0) atomicOr(status, STATUS_OVERFLOW);
         nv = cap;
@@ -246,29 +314,41 @@ __global__ void __launch_bounds__(128) k_phase(const RepDesc* __restrict__ descs
             break;
         }
 
-        if ((i >> 6) != batch) {
-            batch = i >> 6;
-            const U64x4 blk = philox4x64(g - D.frag_base, w, 32 * batch + lane, 0, D.seed, hop_k1);
-            xs_even = blk.x[1];
-            xs_odd = blk.x[3];
-            if constexpr (PREC == 0) {
-                Ed_even = neglog64(blk.x[0]);
-                Ed_odd = neglog64(blk.x[2]);
-            } else {
-                Ef_even = neglog32(blk.x[0]);
-                Ef_odd = neglog32(blk.x[2]);
+        uint64_t xs;
+        double Ed = 0.0;
+        float Ef = 0.f;
+        if (i < 2) {  // block 0, drawn by the screen pass
+            xs = ent.xs[i];
+            if constexpr (PREC == 0) Ed = __longlong_as_double((long long)ent.E[i]);
+            else Ef = __uint_as_float((uint32_t)ent.E[i]);
+        } else {
+            // events [2 + 64 b, 66 + 64 b): blocks 1 + 32 b + lane
+            const uint64_t k = i - 2;
+            if ((k >> 6) != batch) {
+                batch = k >> 6;
+                const U64x4 blk = philox4x64((uint64_t)fid, w, 1 + 32 * batch + lane, 0, D.seed, hop_k1);
+                xs_even = blk.x[1];
+                xs_odd = blk.x[3];
+                if constexpr (PREC == 0) {
+                    Ed_even = neglog64(blk.x[0]);
+                    Ed_odd = neglog64(blk.x[2]);
+                } else {
+                    Ef_even = neglog32(blk.x[0]);
+                    Ef_odd = neglog32(blk.x[2]);
+                }
             }
+            const int src = (int)((k >> 1) & 31);
+            const bool odd = (k & 1) != 0;
+            xs = __shfl_sync(0xffffffffu, odd ? xs_odd : xs_even, src);
+            if constexpr (PREC == 0) Ed = __shfl_sync(0xffffffffu, odd ? Ed_odd : Ed_even, src);
+            else Ef = __shfl_sync(0xffffffffu, odd ? Ef_odd : Ef_even, src);
         }
-        const int src = (int)((i >> 1) & 31);
-        const bool odd = (i & 1) != 0;
-        const uint64_t xs = __shfl_sync(0xffffffffu, odd ? xs_odd : xs_even, src);
 
         double dclock;
         int e_sel = -1;
         if constexpr (PREC == 0) {
             const double R = (double)total;
-            const double E = __shfl_sync(0xffffffffu, odd ? Ed_odd : Ed_even, src);
-            const double dt = __ddiv_rn(E, R);
+            const double dt = __ddiv_rn(Ed, R);
             if (__dadd_rn(clock, dt) > D.tau) break;
             dclock = dt;
             const double target = __dmul_rn(__dmul_rn(__ull2double_rn(xs >> 11), 0x1p-53), R);
@@ -298,8 +378,7 @@ __global__ void __launch_bounds__(128) k_phase(const RepDesc* __restrict__ descs
             }
         } else {
             const unsigned long long Sq = (unsigned long long)total;
-            const float E = __shfl_sync(0xffffffffu, odd ? Ef_odd : Ef_even, src);
-            const float ratio = __fdiv_rn(E, __ull2float_rn(Sq));
+            const float ratio = __fdiv_rn(Ef, __ull2float_rn(Sq));
             const double dth = __dmul_rn((double)ratio, D.two_pow_F);
             if (__dadd_rn(clock, dth) > D.theta_tau) break;
             dclock = dth;
@@ -384,6 +463,8 @@ __global__ void __launch_bounds__(128) k_phase(const RepDesc* __restrict__ descs
         counts[g] = base_pos;
         if (i) atomicAdd(stats + 2 * lo, (unsigned long long)i);
         if (nhand) atomicAdd(stats + 2 * lo + 1, (unsigned long long)nhand);
+    }
+    __syncwarp();  // the warp's shared memory is reused by its next fragment
     }
 }
 
@@ -508,25 +589,50 @@ size_t phase_smem_bytes(int cap) { return warp_smem_bytes(cap) * 4; }
 cudaError_t phase_prepare(int cap)
 {
     const int bytes = (int)phase_smem_bytes(cap);
-    cudaError_t e = cudaFuncSetAttribute(k_phase<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_run<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_phase<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return cudaFuncSetAttribute(k_run<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-cudaError_t launch_phase(int prec, const RepDesc* d_descs, int nrep, int64_t total_items, int phase,
-                         uint64_t wk, uint32_t* occ, VacRec* recs, int32_t* counts, int32_t* tracer,
-                         unsigned long long* stats, uint32_t* status, int cap, cudaStream_t st)
+// Blocks of the run pass: as many as fit on the GPU at once (it strides over
+// the screened fragments).
+cudaError_t run_pass_blocks(int prec, int cap, int* blocks)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = prec == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_run<0>, 128, phase_smem_bytes(cap))
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_run<1>, 128, phase_smem_bytes(cap));
+    *blocks = std::max(1, sms * std::max(per_sm, 1));
+    return e;
+}
+
+// One window of the colour-phase path: set-up, then screen and run for each of
+// the 8 phases.  Every argument is fixed for the batch (the window offset is
+// read from wctl on the device), so the sequence can be captured in a graph.
+cudaError_t launch_window(int prec, const RepDesc* d_descs, int nrep, int64_t total_items,
+                          unsigned long long* wctl, uint32_t* perms, ActEntry* act, int32_t* act_count,
+                          uint32_t* occ, VacRec* recs, int32_t* counts, int32_t* tracer,
+                          unsigned long long* stats, uint32_t* status, int cap, int run_blocks, cudaStream_t st)
 {
     if (total_items <= 0) return cudaSuccess;
-    const int warps = 4;
-    const int64_t blocks = (total_items + warps - 1) / warps;
+    k_window_setup<<<(nrep + 255) / 256, 256, 0, st>>>(d_descs, nrep, wctl, perms, act_count);
+    const int64_t sblocks = (total_items + 255) / 256;
     const size_t smem = phase_smem_bytes(cap);
-    if (prec == 0)
-        k_phase<0><<<(unsigned)blocks, 32 * warps, smem, st>>>(d_descs, nrep, total_items, phase, wk, occ,
-                                                               recs, counts, tracer, stats, status, cap);
-    else
-        k_phase<1><<<(unsigned)blocks, 32 * warps, smem, st>>>(d_descs, nrep, total_items, phase, wk, occ,
-                                                               recs, counts, tracer, stats, status, cap);
+    for (int p = 0; p < 8; ++p) {
+        if (prec == 0) {
+            k_screen<0><<<(unsigned)sblocks, 256, 0, st>>>(d_descs, nrep, total_items, p, wctl, perms, counts, act,
+                                                           act_count);
+            k_run<0><<<run_blocks, 128, smem, st>>>(d_descs, act, act_count, p, wctl, occ, recs, counts, tracer,
+                                                    stats, status, cap);
+        } else {
+            k_screen<1><<<(unsigned)sblocks, 256, 0, st>>>(d_descs, nrep, total_items, p, wctl, perms, counts, act,
+                                                           act_count);
+            k_run<1><<<run_blocks, 128, smem, st>>>(d_descs, act, act_count, p, wctl, occ, recs, counts, tracer,
+                                                    stats, status, cap);
+        }
+    }
     return cudaGetLastError();
 }
 

@@ -14,9 +14,11 @@ cudaError_t launch_init(const RepDesc& D, int b_bits, int64_t n_vac, int64_t n_t
                         VacRec* recs, int32_t* counts, int cap, uint32_t* status, cudaStream_t st);
 size_t phase_smem_bytes(int cap);
 cudaError_t phase_prepare(int cap);
-cudaError_t launch_phase(int prec, const RepDesc* d_descs, int nrep, int64_t total_items, int phase,
-                         uint64_t wk, uint32_t* occ, VacRec* recs, int32_t* counts, int32_t* tracer,
-                         unsigned long long* stats, uint32_t* status, int cap, cudaStream_t st);
+cudaError_t run_pass_blocks(int prec, int cap, int* blocks);
+cudaError_t launch_window(int prec, const RepDesc* d_descs, int nrep, int64_t total_items,
+                          unsigned long long* wctl, uint32_t* perms, ActEntry* act, int32_t* act_count,
+                          uint32_t* occ, VacRec* recs, int32_t* counts, int32_t* tracer,
+                          unsigned long long* stats, uint32_t* status, int cap, int run_blocks, cudaStream_t st);
 cudaError_t launch_moments(const RepDesc& D, int species, const uint32_t* occ, const VacRec* recs,
                            const int32_t* counts, const int32_t* tracer, int cap,
                            unsigned long long* out, cudaStream_t st);
