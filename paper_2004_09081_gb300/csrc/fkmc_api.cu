@@ -598,7 +598,9 @@ int kmc_read_moments_all(kmc_batch* b, int64_t* out, size_t n_out)
 {
     if (!b || !out) return fail(FKMC_EINVAL, "null argument");
     if (n_out != 7 * (size_t)b->n) return fail(FKMC_EINVAL, "n_out must be 7 x replicas");
-    CK(launch_moments_all(b->d_desc, b->n, b->recs, b->counts, b->nfrag_total, b->cap, b->scratch_all, b->st),
+    int64_t max_frag = 0;
+    for (const RepDesc& D : b->desc) max_frag = std::max<int64_t>(max_frag, (int64_t)D.nf[0] * D.nf[1] * D.nf[2]);
+    CK(launch_moments_all(b->d_desc, b->n, b->recs, b->counts, max_frag, b->cap, b->scratch_all, b->st),
        "moments kernel");
     CK(cudaMemcpyAsync(out, b->scratch_all, sizeof(int64_t) * n_out, cudaMemcpyDeviceToHost, b->st),
        "moments copy");

@@ -502,34 +502,47 @@ __global__ void k_moments_vac(const VacRec* recs, const int32_t* counts, int64_t
     if (threadIdx.x < 7 && acc[threadIdx.x]) atomicAdd(out + threadIdx.x, acc[threadIdx.x]);
 }
 
-// Vacancy moments of every replica of the batch in one launch: one thread per
-// fragment slot, replica found from the fragment index; out[7 r + q].
-__global__ void k_moments_vac_all(const RepDesc* __restrict__ descs, int nrep, const VacRec* recs,
-                                  const int32_t* counts, int64_t nfrag_total, int cap,
-                                  unsigned long long* out)
+// Vacancy moments of every replica of the batch in one launch: blockIdx.y is
+// the replica, blockIdx.x a chunk of its record slots; each block reduces in
+// registers and shared memory and adds its 7 sums to out[7 r + q] once.
+constexpr int MOM_THREADS = 256;
+constexpr int MOM_SLOTS_PER_THREAD = 16;
+
+__global__ void __launch_bounds__(MOM_THREADS) k_moments_vac_all(const RepDesc* __restrict__ descs,
+                                                                 const VacRec* recs, const int32_t* counts,
+                                                                 int cap, unsigned long long* out)
 {
-    const int64_t total = nfrag_total * cap;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t f = k / cap;
+    __shared__ unsigned long long acc[7];
+    const int r = blockIdx.y;
+    const RepDesc& D = descs[r];
+    const int64_t nfrag = (int64_t)D.nf[0] * D.nf[1] * D.nf[2];
+    const int64_t total = nfrag * cap;
+    const int64_t begin = (int64_t)blockIdx.x * MOM_THREADS * MOM_SLOTS_PER_THREAD;
+    if (begin >= total) return;  // block-uniform
+    if (threadIdx.x < 7) acc[threadIdx.x] = 0ull;
+    __syncthreads();
+    unsigned long long a[7] = {0, 0, 0, 0, 0, 0, 0};
+    const int64_t end = min(total, begin + (int64_t)MOM_THREADS * MOM_SLOTS_PER_THREAD);
+    for (int64_t k = begin + threadIdx.x; k < end; k += MOM_THREADS) {
+        const int64_t f = D.frag_base + k / cap;
         const int s = (int)(k % cap);
         if (s >= counts[f]) continue;
-        int lo = 0, hi = nrep - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (descs[mid].frag_base <= f) lo = mid; else hi = mid - 1;
-        }
-        const VacRec r = recs[f * cap + s];
-        unsigned long long* o = out + 7 * (int64_t)lo;
-        atomicAdd(o, 1ull);
+        const VacRec v = recs[f * cap + s];
+        a[0] += 1ull;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            if (r.d[d]) {
-                atomicAdd(o + 1 + d, (unsigned long long)(long long)r.d[d]);
-                atomicAdd(o + 4 + d, (unsigned long long)((long long)r.d[d] * r.d[d]));
-            }
+            a[1 + d] += (unsigned long long)(long long)v.d[d];
+            a[4 + d] += (unsigned long long)((long long)v.d[d] * v.d[d]);
         }
     }
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        unsigned long long v = a[q];
+        for (int off = 16; off; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(acc + q, v);
+    }
+    __syncthreads();
+    if (threadIdx.x < 7 && acc[threadIdx.x]) atomicAdd(out + 7 * (int64_t)r + threadIdx.x, acc[threadIdx.x]);
 }
 
 // Tracer field over the sites holding `species`.
@@ -657,15 +670,14 @@ cudaError_t launch_moments(const RepDesc& D, int species, const uint32_t* occ, c
 }
 
 cudaError_t launch_moments_all(const RepDesc* d_descs, int nrep, const VacRec* recs, const int32_t* counts,
-                               int64_t nfrag_total, int cap, unsigned long long* out, cudaStream_t st)
+                               int64_t max_frag_per_replica, int cap, unsigned long long* out, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(out, 0, 7 * sizeof(unsigned long long) * nrep, st);
     if (e != cudaSuccess) return e;
-    const int threads = 256;
-    int64_t blocks = (nfrag_total * cap + threads - 1) / threads;
-    if (blocks > 8 * 152) blocks = 8 * 152;
-    if (blocks < 1) blocks = 1;
-    k_moments_vac_all<<<(unsigned)blocks, threads, 0, st>>>(d_descs, nrep, recs, counts, nfrag_total, cap, out);
+    const int64_t per_block = (int64_t)MOM_THREADS * MOM_SLOTS_PER_THREAD;
+    const int64_t chunks = std::max<int64_t>(1, (max_frag_per_replica * cap + per_block - 1) / per_block);
+    dim3 grid((unsigned)chunks, (unsigned)nrep);
+    k_moments_vac_all<<<grid, MOM_THREADS, 0, st>>>(d_descs, recs, counts, cap, out);
     return cudaGetLastError();
 }
 

@@ -24,7 +24,7 @@ cudaError_t launch_moments(const RepDesc& D, int species, const uint32_t* occ, c
                            unsigned long long* out, cudaStream_t st);
 
 cudaError_t launch_moments_all(const RepDesc* d_descs, int nrep, const VacRec* recs, const int32_t* counts,
-                               int64_t nfrag_total, int cap, unsigned long long* out, cudaStream_t st);
+                               int64_t max_frag_per_replica, int cap, unsigned long long* out, cudaStream_t st);
 
 // replica-resident kernel (fkmc_resident.cu)
 constexpr int RESIDENT_MAX_SLOTS = 64;               // vacancies per fragment a thread can hold

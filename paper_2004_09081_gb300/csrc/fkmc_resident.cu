@@ -117,7 +117,7 @@ struct Shared {
     RepDesc D;
     NbEntry nb[3][8];
     uint64_t bar;
-    int perm[8];
+    uint32_t perms[64];  // colour orders of 64 consecutive windows (nibble p = colour of phase p)
     int nv_count;
     int nact;
     int next_act;
@@ -345,13 +345,13 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
 
     for (uint64_t wk = 0; wk < windows; ++wk) {
         const uint64_t w = D.window + wk;
-        if (tid < 32) {
-            const int c = colour_of_phase(D.seed, D.replica, w, tid & 7, tid);
-            if (tid < 8) sh.perm[tid] = c;
+        if ((wk & 63) == 0) {  // colour orders of the next 64 windows, one thread each
+            if (tid < 64 && wk + tid < windows) sh.perms[tid] = colour_perm_packed(D.seed, D.replica, w + tid);
+            __syncthreads();
         }
-        __syncthreads();
+        const uint32_t wperm = sh.perms[wk & 63];
         for (int p = 0; p < 8; ++p) {
-            const int colour = sh.perm[p];
+            const int colour = (int)((wperm >> (4 * p)) & 15u);
             int cnt[3], bit[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
