@@ -449,15 +449,40 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                 float E_even = 0.f, E_odd = 0.f;
                 unsigned long long tot = 0;
                 for (;;) {
-                    // exact total of the fragment's events (order-free integer sum)
-                    unsigned long long part = 0;
-                    for (int c = 0; c < nch; ++c) {
-                        const int ty = wtype[c * 32 + lane];
-                        part += ty < 0 ? 0ull : (unsigned long long)D.q[ty];
-                    }
+                    // exact total of the fragment's events (order-free integer sum).  Up to two
+                    // chunks (8 vacancies) one inclusive scan gives both the total and the
+                    // prefixes the selection needs; beyond that, a reduction now and scans later.
+                    unsigned long long inc0 = 0, inc1 = 0;
+                    if (nch <= 2) {
+                        const int t0 = wtype[lane];
+                        inc0 = t0 < 0 ? 0ull : (unsigned long long)D.q[t0];
 #pragma unroll
-                    for (int off = 16; off; off >>= 1) part += __shfl_xor_sync(FULL, part, off);
-                    tot = part;
+                        for (int off = 1; off < 32; off <<= 1) {
+                            const unsigned long long t2 = __shfl_up_sync(FULL, inc0, off);
+                            if (lane >= off) inc0 += t2;
+                        }
+                        tot = __shfl_sync(FULL, inc0, 31);
+                        if (nch == 2) {
+                            const int t1 = wtype[32 + lane];
+                            inc1 = t1 < 0 ? 0ull : (unsigned long long)D.q[t1];
+#pragma unroll
+                            for (int off = 1; off < 32; off <<= 1) {
+                                const unsigned long long t2 = __shfl_up_sync(FULL, inc1, off);
+                                if (lane >= off) inc1 += t2;
+                            }
+                            inc1 += tot;
+                            tot = __shfl_sync(FULL, inc1, 31);
+                        }
+                    } else {
+                        unsigned long long part = 0;
+                        for (int c = 0; c < nch; ++c) {
+                            const int ty = wtype[c * 32 + lane];
+                            part += ty < 0 ? 0ull : (unsigned long long)D.q[ty];
+                        }
+#pragma unroll
+                        for (int off = 16; off; off >>= 1) part += __shfl_xor_sync(FULL, part, off);
+                        tot = part;
+                    }
                     if (tot == 0ull) break;
                     if (i >= MAX_EVENTS_PER_PHASE) {
                         if (lane == 0) atomicOr(status, STATUS_EVENT_LIMIT);
@@ -490,23 +515,33 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                     if (nclock > D.theta_tau) break;
                     const unsigned long long target = __umul64hi(xs, tot);
                     // first event whose running sum exceeds the target
-                    unsigned long long carry = 0;
                     int e_sel = -1;
-                    for (int c = 0; c < nch; ++c) {
-                        const int ty = wtype[c * 32 + lane];
-                        unsigned long long inc = ty < 0 ? 0ull : (unsigned long long)D.q[ty];
-#pragma unroll
-                        for (int off = 1; off < 32; off <<= 1) {
-                            const unsigned long long t2 = __shfl_up_sync(FULL, inc, off);
-                            if (lane >= off) inc += t2;
-                        }
-                        inc += carry;
-                        const unsigned bal = __ballot_sync(FULL, inc > target);
+                    if (nch <= 2) {
+                        unsigned bal = __ballot_sync(FULL, inc0 > target);
                         if (bal) {
-                            e_sel = c * 32 + __ffs(bal) - 1;
-                            break;
+                            e_sel = __ffs(bal) - 1;
+                        } else {
+                            bal = __ballot_sync(FULL, inc1 > target);
+                            if (bal && nch == 2) e_sel = 32 + __ffs(bal) - 1;
                         }
-                        carry = __shfl_sync(FULL, inc, 31);
+                    } else {
+                        unsigned long long carry = 0;
+                        for (int c = 0; c < nch; ++c) {
+                            const int ty = wtype[c * 32 + lane];
+                            unsigned long long inc = ty < 0 ? 0ull : (unsigned long long)D.q[ty];
+#pragma unroll
+                            for (int off = 1; off < 32; off <<= 1) {
+                                const unsigned long long t2 = __shfl_up_sync(FULL, inc, off);
+                                if (lane >= off) inc += t2;
+                            }
+                            inc += carry;
+                            const unsigned bal = __ballot_sync(FULL, inc > target);
+                            if (bal) {
+                                e_sel = c * 32 + __ffs(bal) - 1;
+                                break;
+                            }
+                            carry = __shfl_sync(FULL, inc, 31);
+                        }
                     }
                     if (e_sel < 0) {  // cannot happen: the target lies below the total
                         if (lane == 0) atomicOr(status, STATUS_OVERFLOW);
