@@ -14,10 +14,9 @@
 // Each colour phase has two passes:
 //   screen  one thread per fragment of the colour.  A fragment whose
 //           neighbourhood did not change since its last visit keeps its exact
-//           event total S; with the clock variate E of its first event (drawn
-//           for every fragment at the start of the window, all in parallel),
-//           E/S > window proves that nothing happens, and the fragment is
-//           skipped.  Everything else goes to a compact list.
+//           event total S; with the first draw of the phase, E/S > window
+//           proves that nothing happens, and the fragment is skipped.
+//           Everything else goes to a compact list.
 //   run     one warp per listed fragment (lane = 4 slots x 8 directions per
 //           32-event chunk; the warp draws 64 events' random numbers at once):
 //           exact total, clock, selection by warp scan, exchange, hand-off,
@@ -136,7 +135,8 @@ struct Layout {
     unsigned long long* S;
     uint8_t* dirty;
     int32_t* act;          // screened fragments
-    float* E0;             // per fragment: clock variate of event 0 of the current window
+    float* act_E;          // their first two exponential variates (events 0, 1)
+    uint64_t* act_xs;      // and selection words
     uint16_t* frag_of_c;   // cell -> fragment index: x cells, then y, then z
     int16_t* wslot;   // per warp: vacancy index of each slot (-1: handed off)
     int8_t* wtype;    // per warp: rate type of each event (-1: none)
@@ -159,8 +159,8 @@ __host__ __device__ inline size_t layout_bytes(int64_t words, int64_t nv, int64_
         (size_t)ncls * 4,          // 8 screened list
         (size_t)nwarps * cap * 2,  // 9 per-warp slots
         (size_t)nwarps * cap * 8,  // 10 per-warp event types
-        (size_t)nfrag * 4,         // 11 first clock variate of each fragment, this window
-        0,                         // 12 (unused)
+        (size_t)ncls * 16,         // 11 screened: selection words
+        (size_t)ncls * 8,          // 12 screened: variates
         (size_t)ltot * 2,          // 13 cell -> fragment tables
     };
     size_t b = 0;
@@ -186,7 +186,8 @@ __device__ __forceinline__ Layout carve(unsigned char* dyn, int64_t words, int64
     L.S = reinterpret_cast<unsigned long long*>(dyn + o[6]);
     L.dirty = reinterpret_cast<uint8_t*>(dyn + o[7]);
     L.act = reinterpret_cast<int32_t*>(dyn + o[8]);
-    L.E0 = reinterpret_cast<float*>(dyn + o[11]);
+    L.act_xs = reinterpret_cast<uint64_t*>(dyn + o[11]);
+    L.act_E = reinterpret_cast<float*>(dyn + o[12]);
     L.frag_of_c = reinterpret_cast<uint16_t*>(dyn + o[13]);
     L.wslot = reinterpret_cast<int16_t*>(dyn + o[9]);
     L.wtype = reinterpret_cast<int8_t*>(dyn + o[10]);
@@ -349,12 +350,6 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
             __syncthreads();
         }
         const uint32_t wperm = sh.perms[wk & 63];
-        // event 0 of every fragment in this window: its clock variate, for the screens
-        for (int f = tid; f < nfrag; f += NT) {
-            const U64x4 blk = philox4x64((uint64_t)f, w, 0, 0, D.seed, hop_k1);
-            S.E0[f] = neglog32(blk.x[0]);
-        }
-        __syncthreads();
         for (int p = 0; p < 8; ++p) {
             const int colour = (int)((wperm >> (4 * p)) & 15u);
             int cnt[3], bit[3];
@@ -377,14 +372,24 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                 f2 = D.nf[2] == 1 ? 0 : 2 * f2 + bit[2];
                 const int fid = (f2 * D.nf[1] + f1) * D.nf[0] + f0;
                 if (S.head[fid] < 0) continue;
-                bool active = S.dirty[fid] != 0;
+                const bool dirty = S.dirty[fid] != 0;
+                const unsigned long long tot = S.S[fid];
+                if (!dirty && tot == 0ull) continue;
+                const U64x4 blk = philox4x64((uint64_t)fid, w, 0, 0, D.seed, hop_k1);
+                const float E0 = neglog32(blk.x[0]);
+                bool active = dirty;
                 if (!active) {
-                    const unsigned long long tot = S.S[fid];
-                    if (tot == 0ull) continue;
-                    const float ratio = __fdiv_rn(S.E0[fid], __ull2float_rn(tot));
+                    const float ratio = __fdiv_rn(E0, __ull2float_rn(tot));
                     active = !(__dadd_rn(0.0, scale_pow2((double)ratio, D.F)) > D.theta_tau);
                 }
-                if (active) S.act[atomicAdd(&sh.nact, 1)] = fid;
+                if (active) {
+                    const int a = atomicAdd(&sh.nact, 1);
+                    S.act[a] = fid;
+                    S.act_E[2 * a] = E0;
+                    S.act_E[2 * a + 1] = neglog32(blk.x[2]);
+                    S.act_xs[2 * a] = blk.x[1];
+                    S.act_xs[2 * a + 1] = blk.x[3];
+                }
             }
             __syncthreads();
             // ---- run: one warp per listed fragment
@@ -483,18 +488,28 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                         if (lane == 0) atomicOr(status, STATUS_EVENT_LIMIT);
                         break;
                     }
-                    if ((i >> 6) != batch) {  // draws of events [64 b, 64 b + 64): blocks 32 b + lane
-                        batch = i >> 6;
-                        const U64x4 blk = philox4x64((uint64_t)fid, w, 32 * batch + lane, 0, D.seed, hop_k1);
-                        xs_even = blk.x[1];
-                        xs_odd = blk.x[3];
-                        E_even = neglog32(blk.x[0]);
-                        E_odd = neglog32(blk.x[2]);
+                    uint64_t xs;
+                    float E;
+                    if (i < 2) {  // block 0, drawn by the screen pass
+                        xs = S.act_xs[2 * a + (int)i];
+                        E = S.act_E[2 * a + (int)i];
+                    } else {
+                        // events [2 + 64 b, 66 + 64 b) come from blocks 1 + 32 b + lane
+                        const uint64_t k = i - 2;
+                        if ((k >> 6) != batch) {
+                            batch = k >> 6;
+                            const U64x4 blk =
+                                philox4x64((uint64_t)fid, w, 1 + 32 * batch + lane, 0, D.seed, hop_k1);
+                            xs_even = blk.x[1];
+                            xs_odd = blk.x[3];
+                            E_even = neglog32(blk.x[0]);
+                            E_odd = neglog32(blk.x[2]);
+                        }
+                        const int src = (int)((k >> 1) & 31);
+                        const bool odd = (k & 1) != 0;
+                        xs = __shfl_sync(FULL, odd ? xs_odd : xs_even, src);
+                        E = __shfl_sync(FULL, odd ? E_odd : E_even, src);
                     }
-                    const int src = (int)((i >> 1) & 31);
-                    const bool odd = (i & 1) != 0;
-                    const uint64_t xs = __shfl_sync(FULL, odd ? xs_odd : xs_even, src);
-                    const float E = __shfl_sync(FULL, odd ? E_odd : E_even, src);
                     const float ratio = __fdiv_rn(E, __ull2float_rn(tot));
                     const double nclock = __dadd_rn(clock, scale_pow2((double)ratio, D.F));
                     if (nclock > D.theta_tau) break;
