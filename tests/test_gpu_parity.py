@@ -213,3 +213,36 @@ def test_batched_workload_full_size_sampled(fk, orc):
         assert np.array_equal(occ, ref.occupancy()), r
         assert np.array_equal(b.records(r), ref.records()), r
         assert info.hops == ref.counters()["hops"]
+
+
+def test_um_scale_full_size_properties(fk):
+    """The 2500^3-cell BaTiO3 lattice under bias (4.7e10 O sites) in the
+    benchmark's configuration.  Too large for the oracle, so it is held to
+    properties valid at any size: every vacancy conserved, about one exchange
+    per vacancy per window, and the drift velocity of the single-vacancy closed
+    form v_z = (8/3) a k0 sinh(qEa/4kT) (within the windowing error)."""
+    import math
+    import torch
+    from paper_2004_09081_gb300 import workloads
+    free, _ = torch.cuda.mem_get_info()
+    if free < 60 * 2**30:
+        pytest.skip("needs ~40 GB of free device memory")
+    wl = workloads.um_batio3_bias(0)
+    rep = wl.replicas[0]
+    b = fk.Batch([(*rep.cells, rep.a)], [(rep.n_vac, rep.n_H)], 0, edge=wl.edge, precision=wl.precision)
+    b.set_barriers(rep.Ea_O, rep.Ea_H, rep.T, field_z=rep.field_z)
+    s = b.run(2)
+    m = b.moments()
+    assert m[0] == rep.n_vac                      # every vacancy kept its record
+    assert s.hops > 0.5 * rep.n_vac               # about one exchange per vacancy per window
+    kB, q, a = 8.617333262e-5, 2.0, rep.a * 1e-10
+    k0 = 1e13 * math.exp(-rep.Ea_O / (kB * rep.T))
+    eps = q * rep.field_z * a / (4 * kB * rep.T)
+    v_exact = 8.0 / 3.0 * a * k0 * math.sinh(eps)
+    _, _, vz = b.D(0, fk.FKMC_V)
+    t = b.info().window * b.info().tau
+    h = 0.5 * a
+    var = (m[6] / m[0] - (m[3] / m[0]) ** 2) * h * h / t**2
+    se = math.sqrt(var / m[0])
+    assert abs(vz - v_exact) < 3 * se + 0.05 * v_exact, (vz, v_exact, se)
+    b.close()
