@@ -549,28 +549,21 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                     }
                     const int m = e_sel >> 3, qd = e_sel & 7;
                     const int v = wslot[m];
-                    const int ion = wtype[e_sel] / 3;
                     int t, x, y, z;
                     split32(S.key[v], t, x, y, z);
                     const NbEntry nb = sh.nb[t][qd];
                     const NbSite j = nb_site(sh, t, x, y, z, qd);
                     const bool owned = j.jx >= lo0 && j.jx < hi0 && j.jy >= lo1 && j.jy < hi1 && j.jz >= lo2 &&
                                        j.jz < hi2;
-                    const uint32_t ks = key32(t, x, y, z), kj = key32(j.t2, j.jx, j.jy, j.jz);
-                    // The exchange, split over lanes.  The species of the two changed
-                    // sites after it are known (s: the ion, j: the vacancy), so the dirty
-                    // marks and the new event types below read them from registers and
-                    // need not wait for the shared-memory writes of lanes 0-3.
-                    if (lane == 0) {
+                    if (lane == 0) {  // apply the exchange
+                        const uint32_t ion = (uint32_t)(wtype[e_sel] / 3);
                         atomicXor(S.occ + ((t * D.L[2] + z) * D.L[1] + y) * D.row_words + (x >> 4),
-                                  ((uint32_t)SP_V ^ (uint32_t)ion) << occ_shift(x));
+                                  ((uint32_t)SP_V ^ ion) << occ_shift(x));
                         atomicXor(S.occ + ((j.t2 * D.L[2] + j.jz) * D.L[1] + j.jy) * D.row_words + (j.jx >> 4),
-                                  ((uint32_t)ion ^ (uint32_t)SP_V) << occ_shift(j.jx));
-                    } else if (lane == 1) {
+                                  (ion ^ (uint32_t)SP_V) << occ_shift(j.jx));
                         S.d[3 * v] += nb.d[0];
                         S.d[3 * v + 1] += nb.d[1];
                         S.d[3 * v + 2] += nb.d[2];
-                    } else if (lane == 2) {
                         if (tracer) {
                             const int64_t s_lin = (((int64_t)t * D.L[2] + z) * D.L[1] + y) * D.L[0] + x;
                             const int64_t j_lin = (((int64_t)j.t2 * D.L[2] + j.jz) * D.L[1] + j.jy) * D.L[0] + j.jx;
@@ -581,8 +574,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                             ts[2] = tj[2] - nb.d[2];
                             tj[0] = tj[1] = tj[2] = 0;
                         }
-                    } else if (lane == 3) {
-                        S.key[v] = kj;
+                        S.key[v] = key32(j.t2, j.jx, j.jy, j.jz);
                         if (!owned) {
                             // leaves the fragment: its slot goes dead (zero rate), the record
                             // is pushed onto the owner's list (the owner does not run in this
@@ -591,41 +583,22 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                             wslot[m] = -1;
                             const int g2 = owner_of(D, S.frag_of_c, j.jx, j.jy, j.jz);
                             S.next[v] = (int16_t)atomicExch(S.head + g2, v);
+                            ++my_hand;
                         }
-                    } else if (lane >= 16) {
-                        // the fragments whose totals changed: owners of the vacancies next to
-                        // the two changed sites (lanes 16-23 look around s, 24-31 around j)
-                        const bool at_s = lane < 24;
-                        const NbSite c = at_s ? nb_site(sh, t, x, y, z, lane & 7)
-                                              : nb_site(sh, j.t2, j.jx, j.jy, j.jz, lane & 7);
-                        const uint32_t kc = key32(c.t2, c.jx, c.jy, c.jz);
-                        const int code = kc == ks ? ion : (kc == kj ? SP_V : site_code(sh, S.occ, c.t2, c.jx, c.jy, c.jz));
-                        if (code == SP_V) {
+                    }
+                    __syncwarp();
+                    // the fragments whose totals changed: owners of the vacancies next
+                    // to the two changed sites (lanes 0-7 look around s, 8-15 around j)
+                    if (lane < 16) {
+                        const int bt = lane < 8 ? t : j.t2;
+                        const int bx = lane < 8 ? x : j.jx, by = lane < 8 ? y : j.jy, bz = lane < 8 ? z : j.jz;
+                        const NbSite c = nb_site(sh, bt, bx, by, bz, lane & 7);
+                        if (site_code(sh, S.occ, c.t2, c.jx, c.jy, c.jz) == SP_V) {
                             const int g = owner_of(D, S.frag_of_c, c.jx, c.jy, c.jz);
                             if (g != fid) S.dirty[g] = 1;
                         }
                     }
-                    if (!owned && lane == 0) ++my_hand;
-                    // event types after the exchange (the moved vacancy now sits at j, or is gone)
-                    for (int c = 0; c < nch; ++c) {
-                        const int e = c * 32 + lane, mm = e >> 3, q = e & 7;
-                        int ty = -1;
-                        if (mm < n && !(mm == m && !owned)) {
-                            const int vv = wslot[mm];
-                            if (vv >= 0) {
-                                const uint32_t k = mm == m ? kj : S.key[vv];
-                                int tt, xx, yy, zz;
-                                split32(k, tt, xx, yy, zz);
-                                const NbSite cs = nb_site(sh, tt, xx, yy, zz, q);
-                                const uint32_t kc = key32(cs.t2, cs.jx, cs.jy, cs.jz);
-                                const int code =
-                                    kc == ks ? ion : (kc == kj ? SP_V : site_code(sh, S.occ, cs.t2, cs.jx, cs.jy, cs.jz));
-                                ty = code == SP_V ? -1 : code * 3 + sh.nb[tt][q].d[2] + 1;
-                            }
-                        }
-                        wtype[e] = (int8_t)ty;
-                    }
-                    __syncwarp();
+                    compute_types();
                     clock = nclock;
                     ++i;
                 }
