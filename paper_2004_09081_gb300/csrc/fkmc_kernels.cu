@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(256) k_screen(const RepDesc* __restrict__ desc
 // Run pass of a colour phase: one warp per screened fragment (grid-stride):
 // BKL on the fragment's vacancies until the next event would pass the window.
 template <int PREC>
-__global__ void __launch_bounds__(128) k_run(const RepDesc* __restrict__ descs, const ActEntry* __restrict__ act,
+__global__ void __launch_bounds__(128, 8) k_run(const RepDesc* __restrict__ descs, const ActEntry* __restrict__ act,
                                              const int32_t* __restrict__ act_count, int phase,
                                              const unsigned long long* wctl, uint32_t* occ, VacRec* recs,
                                              int32_t* counts, int32_t* tracer, unsigned long long* stats,
