@@ -135,10 +135,11 @@ struct kmc_batch {
     NbTable nbt{};
     int32_t* d_reps = nullptr;   // resident replica ids, class by class
     int64_t* d_nvac = nullptr;   // vacancies per replica
-    struct RClass { int start, count; size_t smem; int threads; cudaStream_t st; cudaEvent_t done; };
+    struct RClass { int start, count; size_t smem; int threads; int cluster; cudaStream_t st; cudaEvent_t done; };
     std::vector<RClass> rclass;
     cudaEvent_t fork = nullptr;
     bool any_global = true;
+    int cluster_top = 0;  // how many of the largest replicas run as 2-CTA clusters (kmc_opts)
     // colour-phase path: per-window set-up, screen and run, captured once in a graph
     unsigned long long* wctl = nullptr;  // [0] windows of this call so far, [1] current offset
     uint32_t* perms = nullptr;           // colour order of every replica, this window
@@ -258,11 +259,13 @@ int plan_residency(kmc_batch* b)
                          b->cap <= RESIDENT_MAX_SLOTS;
     // launch classes: (shared-memory bound, threads); a replica takes the first
     // class its state fits, so small replicas pack several CTAs per SM and the
-    // largest get the most warps that still fit beside their state
+    // largest get the most warps that still fit beside their state.  The
+    // `cluster_top` largest replicas of the 1024-thread class run as 2-CTA
+    // clusters (two SMs each), as long as the GPU has the SMs to spare.
     const size_t bounds[5] = {24 * 1024, 48 * 1024, 96 * 1024, RESIDENT_MAX_SMEM, RESIDENT_MAX_SMEM};
     const int threads[5] = {128, 128, 256, 1024, 512};
-    std::vector<std::vector<int>> cls(5);
-    std::vector<size_t> cmax(5, 0);
+    std::vector<std::vector<int>> cls(6);
+    std::vector<size_t> cmax(6, 0), need_of(b->n, 0);
     b->any_global = false;
     for (int r = 0; r < b->n; ++r) {
         int c = -1;
@@ -277,14 +280,27 @@ int plan_residency(kmc_batch* b)
             continue;
         }
         cls[c].push_back(r);
-        cmax[c] = std::max(cmax[c], need);
+        need_of[r] = need;
     }
+    // largest replicas (by vacancies, the work per phase) first in every class: the
+    // longest-running CTAs start earliest, which shortens the tail of the launch
+    for (int c = 0; c < 5; ++c)
+        std::sort(cls[c].begin(), cls[c].end(), [&](int a, int q) {
+            return b->n_vac[a] != b->n_vac[q] ? b->n_vac[a] > b->n_vac[q] : a < q;
+        });
+    // optionally the largest of the 1024-thread class run as 2-CTA clusters (class 5)
+    const int ntop = std::min<int>((int)cls[3].size(), b->cluster_top);
+    cls[5].assign(cls[3].begin(), cls[3].begin() + ntop);
+    cls[3].erase(cls[3].begin(), cls[3].begin() + ntop);
+    for (int c = 0; c < 6; ++c)
+        for (int r : cls[c]) cmax[c] = std::max(cmax[c], need_of[r]);
     if (b->opts.schedule == 2 && b->any_global)
         return fail(FKMC_EINVAL, "schedule 2 needs every replica to fit the resident kernel (mixed form)");
     std::vector<int32_t> order;
-    for (int c = 0; c < 5; ++c) {
+    for (int c = 0; c < 6; ++c) {
         if (cls[c].empty()) continue;
-        kmc_batch::RClass rc{(int)order.size(), (int)cls[c].size(), cmax[c], threads[c], nullptr, nullptr};
+        kmc_batch::RClass rc{(int)order.size(), (int)cls[c].size(), cmax[c], c == 5 ? 1024 : threads[c],
+                             c == 5 ? 2 : 1, nullptr, nullptr};
         for (int r : cls[c]) order.push_back(r);
         CK(cudaStreamCreateWithFlags(&rc.st, cudaStreamNonBlocking), "stream");
         CK(cudaEventCreateWithFlags(&rc.done, cudaEventDisableTiming), "event");
@@ -419,6 +435,7 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
         b->cap = o.cap_v;
     }
     b->opts.cap_v = b->cap;
+    b->cluster_top = std::max(0, o.cluster_top);
 
     b->occ = (uint32_t*)b->dalloc(sizeof(uint32_t) * b->occ_words);
     b->recs = (VacRec*)b->dalloc(sizeof(VacRec) * b->nfrag_total * b->cap);
@@ -527,8 +544,9 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
         CK(cudaEventRecord(b->fork, b->st), "event record");
         for (auto& c : b->rclass) {
             CK(cudaStreamWaitEvent(c.st, b->fork, 0), "stream wait");
-            CK(launch_resident(b->d_desc, b->d_reps + c.start, c.count, b->d_nvac, c.smem, c.threads, windows,
-                               b->occ, b->recs, b->counts, b->tracer, b->stats, b->status, b->cap, b->nbt, c.st),
+            CK(launch_resident(b->d_desc, b->d_reps + c.start, c.count, b->d_nvac, c.smem, c.threads, c.cluster,
+                               windows, b->occ, b->recs, b->counts, b->tracer, b->stats, b->status, b->cap, b->nbt,
+                               c.st),
                "resident kernel");
             CK(cudaEventRecord(c.done, c.st), "event record");
         }

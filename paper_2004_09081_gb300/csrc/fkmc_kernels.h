@@ -32,7 +32,7 @@ constexpr size_t RESIDENT_MAX_SMEM = 220 * 1024;     // dynamic shared memory pe
 size_t resident_smem_bytes(const RepDesc& D, int64_t n_vac, int cap, int threads);
 cudaError_t resident_prepare();
 cudaError_t launch_resident(const RepDesc* d_descs, const int32_t* d_reps, int nreps, const int64_t* d_nvac,
-                            size_t smem, int threads, uint64_t windows, uint32_t* occ, VacRec* recs,
+                            size_t smem, int threads, int cluster, uint64_t windows, uint32_t* occ, VacRec* recs,
                             int32_t* counts, int32_t* tracer, unsigned long long* stats, uint32_t* status,
                             int cap, const NbTable& nbt, cudaStream_t st);
 

@@ -95,6 +95,71 @@ __device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t by
                  : "memory");
 }
 
+// ---- thread-block cluster and distributed shared memory
+__device__ __forceinline__ uint32_t cluster_ctarank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// every thread of every CTA of the cluster; release / acquire of shared memory
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// address in CTA `peer`'s shared memory of the same variable as `p`
+__device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t peer)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(peer));
+    return r;
+}
+
+__device__ __forceinline__ void st_peer(uint32_t a, uint32_t v)
+{
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_peer(uint32_t a, int32_t v) { st_peer(a, (uint32_t)v); }
+__device__ __forceinline__ void st_peer16(uint32_t a, int16_t v)
+{
+    asm volatile("st.shared::cluster.u16 [%0], %1;" ::"r"(a), "h"((unsigned short)v) : "memory");
+}
+__device__ __forceinline__ void st_peer8(uint32_t a, uint8_t v)
+{
+    asm volatile("st.shared::cluster.u8 [%0], %1;" ::"r"(a), "h"((unsigned short)v) : "memory");
+}
+__device__ __forceinline__ void st_peer64(uint32_t a, unsigned long long v)
+{
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+__device__ __forceinline__ void red_peer_xor(uint32_t a, uint32_t v)
+{
+    asm volatile("red.shared::cluster.xor.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ int32_t atom_peer_exch(uint32_t a, int32_t v)
+{
+    int32_t o;
+    asm volatile("atom.shared::cluster.exch.b32 %0, [%1], %2;" : "=r"(o) : "r"(a), "r"(v) : "memory");
+    return o;
+}
+__device__ __forceinline__ uint4 ld_peer16(uint32_t a)
+{
+    uint4 v;
+    asm volatile("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(a)
+                 : "memory");
+    return v;
+}
+__device__ __forceinline__ int32_t ld_peer(uint32_t a)
+{
+    int32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+
 constexpr uint32_t BULK_CHUNK = 32768;        // bytes per bulk copy instruction
 constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s bound on any device-side wait
 
@@ -253,7 +318,12 @@ size_t resident_smem_bytes(const RepDesc& D, int64_t n_vac, int cap, int threads
     return layout_bytes(words, n_vac, nfrag, ncls, cap, threads / 32, D.L[0] + D.L[1] + D.L[2], nullptr);
 }
 
-template <int NT>
+// CL = CTAs per replica (a thread-block cluster).  With CL = 2 both CTAs hold
+// the whole replica; each screens and runs half of every colour's fragments,
+// and every write to the replica's state is made in both copies (the local one
+// and, through distributed shared memory, the peer's), so the copies stay
+// identical; reads are local.  Phases end with a cluster barrier.
+template <int NT, int CL>
 __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_resident(const RepDesc* __restrict__ descs,
                                                   const int32_t* __restrict__ reps,
                                                   const int64_t* __restrict__ nvac, uint64_t windows,
@@ -264,8 +334,10 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
     extern __shared__ __align__(128) unsigned char dyn[];
     __shared__ Shared sh;
     const int tid = threadIdx.x;
-    const int r = reps[blockIdx.x];
+    const int r = reps[blockIdx.x / CL];
     const int64_t n_vac = nvac[r];
+    const uint32_t rank = CL > 1 ? cluster_ctarank() : 0u;
+    const uint32_t peer = rank ^ 1u;
 
     if (tid == 0) {
         sh.D = descs[r];
@@ -282,9 +354,10 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
     const int ncls_max = ((D.nf[0] + 1) / 2) * ((D.nf[1] + 1) / 2) * ((D.nf[2] + 1) / 2);
     const Layout S = carve(dyn, words, n_vac, nfrag, ncls_max, cap, NT / 32, D.L[0] + D.L[1] + D.L[2]);
 
-    // ---- stage in: occupancy by TMA bulk copies, records by plain loads
+    // ---- stage in: occupancy by TMA bulk copies, records by plain loads (the
+    // first CTA of a cluster; the second copies its shared memory afterwards)
     const uint32_t occ_bytes = (uint32_t)(words * 4);
-    if (tid == 0) {
+    if (tid == 0 && rank == 0) {
         mbar_init(&sh.bar, 1);
         mbar_arrive_expect_tx(&sh.bar, occ_bytes);
         const char* src = reinterpret_cast<const char*>(occ + D.occ_word_off);
@@ -298,7 +371,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
         const int c = d == 0 ? k : (d == 1 ? k - D.L[0] : k - D.L[0] - D.L[1]);
         S.frag_of_c[k] = (uint16_t)frag_of(c, D.base[d], D.rem[d]);
     }
-    for (int f = tid; f < nfrag; f += blockDim.x) {
+    for (int f = tid; f < (rank == 0 ? nfrag : 0); f += blockDim.x) {
         const int64_t g = D.frag_base + f;
         const int c = counts[g];
         int head = -1;
@@ -325,7 +398,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
         S.S[f] = 0ull;
     }
     __syncthreads();  // the barrier init is visible to every thread from here on
-    if (!mbar_wait_bounded(&sh.bar, 0, WAIT_NS)) {
+    if (rank == 0 && !mbar_wait_bounded(&sh.bar, 0, WAIT_NS)) {
         if (tid == 0) {
             atomicOr(status, STATUS_TIMEOUT);
             sh.abort = 1;
@@ -333,6 +406,25 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
         mbar_wait_bounded(&sh.bar, 0, WAIT_NS);  // let copies in flight land before leaving
     }
     __syncthreads();
+    if constexpr (CL > 1) {
+        // every CTA of the cluster passes the same barriers: the decision to stop
+        // is read from the first CTA after the cluster barrier
+        cluster_sync();
+        if (rank != 0) {
+            if (tid == 0) sh.abort = ld_peer(peer_addr(&sh.abort, 0));
+            __syncthreads();
+            if (!sh.abort) {
+                const uint32_t base = peer_addr(dyn, 0);
+                const size_t bytes = layout_bytes(words, n_vac, nfrag, ncls_max, cap, NT / 32,
+                                                  D.L[0] + D.L[1] + D.L[2], nullptr);
+                for (size_t k = (size_t)tid * 16; k < bytes; k += (size_t)NT * 16) {
+                    const uint4 v = ld_peer16(base + (uint32_t)k);
+                    *reinterpret_cast<uint4*>(dyn + k) = v;
+                }
+            }
+        }
+        cluster_sync();  // the first CTA writes into the copy only after it is complete
+    }
     if (sh.abort) return;
 
     const uint64_t hop_k1 = key_word(D.replica, PURPOSE_HOP);
@@ -365,7 +457,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
             }
             __syncthreads();
             // ---- screen: one thread per fragment of the colour
-            for (int l = tid; l < ncls; l += blockDim.x) {
+            for (int l = tid * CL + (int)rank; l < ncls; l += NT * CL) {
                 int f0 = l % cnt[0], f1 = (l / cnt[0]) % cnt[1], f2 = l / (cnt[0] * cnt[1]);
                 f0 = D.nf[0] == 1 ? 0 : 2 * f0 + bit[0];
                 f1 = D.nf[1] == 1 ? 0 : 2 * f1 + bit[1];
@@ -557,13 +649,20 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                                        j.jz < hi2;
                     if (lane == 0) {  // apply the exchange
                         const uint32_t ion = (uint32_t)(wtype[e_sel] / 3);
-                        atomicXor(S.occ + ((t * D.L[2] + z) * D.L[1] + y) * D.row_words + (x >> 4),
-                                  ((uint32_t)SP_V ^ ion) << occ_shift(x));
-                        atomicXor(S.occ + ((j.t2 * D.L[2] + j.jz) * D.L[1] + j.jy) * D.row_words + (j.jx >> 4),
-                                  (ion ^ (uint32_t)SP_V) << occ_shift(j.jx));
+                        uint32_t* ws = S.occ + ((t * D.L[2] + z) * D.L[1] + y) * D.row_words + (x >> 4);
+                        uint32_t* wj = S.occ + ((j.t2 * D.L[2] + j.jz) * D.L[1] + j.jy) * D.row_words + (j.jx >> 4);
+                        const uint32_t ms = ((uint32_t)SP_V ^ ion) << occ_shift(x);
+                        const uint32_t mj = (ion ^ (uint32_t)SP_V) << occ_shift(j.jx);
+                        atomicXor(ws, ms);
+                        atomicXor(wj, mj);
                         S.d[3 * v] += nb.d[0];
                         S.d[3 * v + 1] += nb.d[1];
                         S.d[3 * v + 2] += nb.d[2];
+                        if constexpr (CL > 1) {
+                            red_peer_xor(peer_addr(ws, peer), ms);
+                            red_peer_xor(peer_addr(wj, peer), mj);
+                            for (int k = 0; k < 3; ++k) st_peer(peer_addr(S.d + 3 * v + k, peer), S.d[3 * v + k]);
+                        }
                         if (tracer) {
                             const int64_t s_lin = (((int64_t)t * D.L[2] + z) * D.L[1] + y) * D.L[0] + x;
                             const int64_t j_lin = (((int64_t)j.t2 * D.L[2] + j.jz) * D.L[1] + j.jy) * D.L[0] + j.jx;
@@ -575,6 +674,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                             tj[0] = tj[1] = tj[2] = 0;
                         }
                         S.key[v] = key32(j.t2, j.jx, j.jy, j.jz);
+                        if constexpr (CL > 1) st_peer(peer_addr(S.key + v, peer), S.key[v]);
                         if (!owned) {
                             // leaves the fragment: its slot goes dead (zero rate), the record
                             // is pushed onto the owner's list (the owner does not run in this
@@ -583,6 +683,9 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                             wslot[m] = -1;
                             const int g2 = owner_of(D, S.frag_of_c, j.jx, j.jy, j.jz);
                             S.next[v] = (int16_t)atomicExch(S.head + g2, v);
+                            if constexpr (CL > 1)
+                                st_peer16(peer_addr(S.next + v, peer),
+                                          (int16_t)atom_peer_exch(peer_addr(S.head + g2, peer), v));
                             ++my_hand;
                         }
                     }
@@ -595,7 +698,10 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                         const NbSite c = nb_site(sh, bt, bx, by, bz, lane & 7);
                         if (site_code(sh, S.occ, c.t2, c.jx, c.jy, c.jz) == SP_V) {
                             const int g = owner_of(D, S.frag_of_c, c.jx, c.jy, c.jz);
-                            if (g != fid) S.dirty[g] = 1;
+                            if (g != fid) {
+                                S.dirty[g] = 1;
+                                if constexpr (CL > 1) st_peer8(peer_addr(S.dirty + g, peer), 1);
+                            }
                         }
                     }
                     compute_types();
@@ -609,21 +715,28 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                         const int v = wslot[m];
                         if (v < 0) continue;
                         S.next[v] = (int16_t)head;
+                        if constexpr (CL > 1) st_peer16(peer_addr(S.next + v, peer), (int16_t)head);
                         head = v;
                     }
                     S.head[fid] = head;
                     S.S[fid] = tot;
                     S.dirty[fid] = 0;
+                    if constexpr (CL > 1) {
+                        st_peer(peer_addr(S.head + fid, peer), head);
+                        st_peer64(peer_addr(S.S + fid, peer), tot);
+                        st_peer8(peer_addr(S.dirty + fid, peer), 0);
+                    }
                     my_hops += i;
                 }
                 __syncwarp();
             }
-            __syncthreads();
+            if constexpr (CL > 1) cluster_sync();  // both copies hold every write of the phase
+            else __syncthreads();
         }
     }
 
-    // ---- stage out: occupancy by a TMA bulk store, records to the fragment lists
-    if (tid == 0) {
+    // ---- stage out (the first CTA of a cluster): occupancy by a TMA bulk store, records to the fragment lists
+    if (tid == 0 && rank == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         char* dst = reinterpret_cast<char*>(occ + D.occ_word_off);
         for (uint32_t off = 0; off < occ_bytes; off += BULK_CHUNK) {
@@ -632,7 +745,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
         }
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
     }
-    for (int f = tid; f < nfrag; f += blockDim.x) {
+    for (int f = tid; f < (rank == 0 ? nfrag : 0); f += blockDim.x) {
         const int64_t g = D.frag_base + f;
         int k = 0;
         for (int v = S.head[f]; v >= 0; v = S.next[v], ++k) {
@@ -658,14 +771,16 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
     if (tid == 0) {
         if (sh.hops) atomicAdd(stats + 2 * r, sh.hops);
         if (sh.hand) atomicAdd(stats + 2 * r + 1, sh.hand);
-        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        if (rank == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     }
+    if constexpr (CL > 1) cluster_sync();  // no CTA leaves while its peer may still address it
 }
 
 cudaError_t resident_prepare()
 {
     cudaError_t e = cudaSuccess;
-    for (auto fn : {k_resident<128>, k_resident<256>, k_resident<512>, k_resident<1024>}) {
+    for (auto fn : {k_resident<128, 1>, k_resident<256, 1>, k_resident<512, 1>, k_resident<1024, 1>,
+                    k_resident<1024, 2>}) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RESIDENT_MAX_SMEM);
         if (e != cudaSuccess) return e;
     }
@@ -673,23 +788,39 @@ cudaError_t resident_prepare()
 }
 
 cudaError_t launch_resident(const RepDesc* d_descs, const int32_t* d_reps, int nreps, const int64_t* d_nvac,
-                            size_t smem, int threads, uint64_t windows, uint32_t* occ, VacRec* recs,
+                            size_t smem, int threads, int cluster, uint64_t windows, uint32_t* occ, VacRec* recs,
                             int32_t* counts, int32_t* tracer, unsigned long long* stats, uint32_t* status,
                             int cap, const NbTable& nbt, cudaStream_t st)
 {
     if (nreps <= 0) return cudaSuccess;
+    if (cluster == 2 && threads == 1024) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2u * nreps);
+        cfg.blockDim = dim3(1024);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k_resident<1024, 2>, d_descs, d_reps, d_nvac, windows, occ, recs, counts,
+                                  tracer, stats, status, cap, nbt);
+    }
     if (threads == 128)
-        k_resident<128><<<nreps, 128, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts, tracer,
-                                                  stats, status, cap, nbt);
+        k_resident<128, 1><<<nreps, 128, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts, tracer,
+                                                     stats, status, cap, nbt);
     else if (threads == 256)
-        k_resident<256><<<nreps, 256, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts, tracer,
-                                                  stats, status, cap, nbt);
+        k_resident<256, 1><<<nreps, 256, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts, tracer,
+                                                     stats, status, cap, nbt);
     else if (threads == 1024)
-        k_resident<1024><<<nreps, 1024, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts, tracer,
-                                                    stats, status, cap, nbt);
+        k_resident<1024, 1><<<nreps, 1024, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts,
+                                                       tracer, stats, status, cap, nbt);
     else
-        k_resident<512><<<nreps, 512, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts, tracer,
-                                                  stats, status, cap, nbt);
+        k_resident<512, 1><<<nreps, 512, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts, tracer,
+                                                     stats, status, cap, nbt);
     return cudaGetLastError();
 }
 

@@ -246,3 +246,24 @@ def test_um_scale_full_size_properties(fk):
     se = math.sqrt(var / m[0])
     assert abs(vz - v_exact) < 3 * se + 0.05 * v_exact, (vz, v_exact, se)
     b.close()
+
+
+def test_cluster_pairs_bit_exact(fk, orc):
+    """Large replicas run as 2-CTA thread-block clusters (state mirrored through
+    distributed shared memory, half of each phase's fragments per CTA) give the
+    oracle's lattice bit for bit."""
+    cells = [(44, 44, 44), (40, 40, 42)]
+    comps = [(2300, 9000), (1900, 4000)]
+    Ts = [700.0, 900.0]
+    b = fk.Batch([(*c, 4.01) for c in cells], comps, 13, edge=4, precision=1, cap_v=32, schedule=2,
+                 cluster_top=2)
+    b.set_barriers(0.7, 0.35, Ts)
+    b.run(12)
+    for r, (c, (nv, nh), T) in enumerate(zip(cells, comps, Ts)):
+        info = b.info(r)
+        ref = orc.Lattice(c, tuple(info.nfrag), nv, nh, seed=13, replica=r)
+        ref.set_rates(0.7, 0.35, T, a_ang=4.01, cap_v=32, precision=1)
+        ref.run(12)
+        assert info.hops == ref.counters()["hops"] > 0
+        assert np.array_equal(b.state(r), ref.occupancy()), r
+        assert np.array_equal(b.records(r), ref.records()), r
