@@ -542,7 +542,9 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
     if (!b->rclass.empty() && windows > 0) {
         // replica-resident classes on forked streams, joined back before ev1
         CK(cudaEventRecord(b->fork, b->st), "event record");
-        for (auto& c : b->rclass) {
+        // largest classes first: their CTAs run longest and should take SMs first
+        for (auto it = b->rclass.rbegin(); it != b->rclass.rend(); ++it) {
+            auto& c = *it;
             CK(cudaStreamWaitEvent(c.st, b->fork, 0), "stream wait");
             CK(launch_resident(b->d_desc, b->d_reps + c.start, c.count, b->d_nvac, c.smem, c.threads, c.cluster,
                                windows, b->occ, b->recs, b->counts, b->tracer, b->stats, b->status, b->cap, b->nbt,
