@@ -99,11 +99,11 @@ typedef struct {
     int32_t schedule;   /* 0 = auto: mixed-form replicas whose state fits one SM run in the
                            replica-resident kernel, the rest one launch per colour phase;
                            1 = colour-phase launches only; 2 = resident kernel only */
-    int32_t cluster_top; /* resident kernel: the largest replicas of the 1024-thread class that
-                            run as 2-CTA thread-block clusters (each CTA holds the replica and
-                            takes half of every phase's fragments; writes are mirrored through
-                            distributed shared memory).  0 (default) = none: on the measured
-                            workloads one SM per replica is faster */
+    int32_t cluster_top; /* resident kernel: how many of the largest replicas of the 1024-thread
+                            class run as 2-CTA thread-block clusters (each CTA holds the replica
+                            and takes half of every phase's fragments; writes are mirrored
+                            through distributed shared memory).  -1 (default) = SMs / 8,
+                            0 = none */
     int32_t reserved[6];
 } kmc_opts;
 

@@ -326,6 +326,7 @@ void kmc_default_opts(kmc_opts* o)
     o->edge = 4;
     o->precision = FKMC_PLAIN;
     o->n_tau = 1.0;
+    o->cluster_top = -1;
 }
 
 void kmc_neighbour_table(int32_t out[168])
@@ -435,7 +436,16 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
         b->cap = o.cap_v;
     }
     b->opts.cap_v = b->cap;
-    b->cluster_top = std::max(0, o.cluster_top);
+    if (o.cluster_top >= 0) {
+        b->cluster_top = o.cluster_top;
+    } else {  // auto: the largest replicas take an extra SM each, about one SM in eight
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            b->cluster_top = sms / 8;
+        else
+            b->cluster_top = 0;
+    }
 
     b->occ = (uint32_t*)b->dalloc(sizeof(uint32_t) * b->occ_words);
     b->recs = (VacRec*)b->dalloc(sizeof(VacRec) * b->nfrag_total * b->cap);

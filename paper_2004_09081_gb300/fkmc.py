@@ -299,7 +299,7 @@ class Batch:
     """A batch of replicas (one lattice = a batch of one) on the current GPU."""
 
     def __init__(self, cells, comps, seed=0, *, edge=4, nfrag=None, precision=FKMC_PLAIN,
-                 tracer=False, cap_v=0, n_tau=1.0, schedule=0, cluster_top=0, stream=None):
+                 tracer=False, cap_v=0, n_tau=1.0, schedule=0, cluster_top=-1, stream=None):
         import torch
         self._alloc = TorchAllocator()
         o = kmc_default_opts()

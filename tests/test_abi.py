@@ -44,7 +44,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_defaults(lib):
     o = lib.kmc_default_opts()
-    assert o.edge == 4 and o.precision == 0 and o.n_tau == 1.0 and o.cap_v == 0
+    assert o.edge == 4 and o.precision == 0 and o.n_tau == 1.0 and o.cap_v == 0 and o.cluster_top == -1
 
 
 def test_neighbour_table_matches_oracle(lib, orc):
