@@ -380,11 +380,11 @@ def main():
                 "of the state, not per hop; the kernel is bound by instruction issue and dependent latency "
                 "(see profiles/)")
     else:
-        units = n_launch  # one launch per colour phase
+        units = args.steps * W * 8  # one colour phase = one screen and one run launch
         tag = "k_phase_" + ("mixed_" if precision else "plain_") + args.workload
         kname = "k_phase<%s> (colour-phase kernel)" % ("mixed" if precision else "plain")
-        note = ("one launch per colour phase; neighbour words read from L2/HBM with ld.global.cg; "
-                "algorithmic bytes = 160 B per hop at 32-byte sectors")
+        note = ("a launch here is one colour phase (screen + run pass); neighbour words read from L2/HBM "
+                "with ld.global.cg; algorithmic bytes = 160 B per hop at 32-byte sectors")
     avg_launch_s = kernel_ms / 1e3 / units
     bytes_per_launch = hops / units * B_ALG_PER_HOP
     achieved = bytes_per_launch / avg_launch_s / 1e9
