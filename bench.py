@@ -132,12 +132,12 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ helpers
-def make_batch(fk, wl, seed, precision, replicas=None, edge=None, tracer=None):
+def make_batch(fk, wl, seed, precision, replicas=None, edge=None, tracer=None, **opts):
     reps = wl.replicas if replicas is None else [wl.replicas[i] for i in replicas]
     nf = reps[0].nfrag if (len(reps) == 1 and reps[0].nfrag) else None
     b = fk.Batch([(*r.cells, r.a) for r in reps], [(r.n_vac, r.n_H) for r in reps], seed,
                  edge=wl.edge if edge is None else edge, nfrag=nf, precision=precision,
-                 tracer=wl.tracer if tracer is None else tracer)
+                 tracer=wl.tracer if tracer is None else tracer, **opts)
     b.set_barriers([r.Ea_O for r in reps], [r.Ea_H for r in reps], [r.T for r in reps],
                    field_z=[r.field_z for r in reps])
     return b
@@ -326,9 +326,12 @@ def main():
                                       [r.Ea_O for r in reps], [r.Ea_H for r in reps], [r.T for r in reps],
                                       precision=precision)
         edge = best["edge"]
-        tuned = [{"edge": c["edge"], "hops_per_s": h, "cap_v": cap} for c, h, cap in res]
+        tuned_opts = {"schedule": best["schedule"], "cluster_top": best["cluster_top"]}
+        tuned = [dict(c, hops_per_s=h, cap_v=cap) for c, h, cap in res]
+    else:
+        tuned_opts = {}
 
-    b = make_batch(fkmc, wl, seed, precision, edge=edge)
+    b = make_batch(fkmc, wl, seed, precision, edge=edge, **tuned_opts)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def step():
@@ -487,7 +490,7 @@ def main():
             "config": {"workload": wl.name, "replicas": nrep, "windows_per_step": W,
                        "precision": ("mixed (fp32 rates -> u64 fixed point, fp32 variate, fp64 clock)"
                                      if precision else "plain fp64"),
-                       "n_tau": 1.0, "edge": edge, "autotune": tuned,
+                       "n_tau": 1.0, "edge": edge, "launch_opts": tuned_opts, "autotune": tuned,
                        "l2": "flushed between timed steps (256 MiB write)",
                        "schedule": ("replica-resident kernel per shared-memory size class" if all_resident
                                     else "colour-phase kernel, one launch per phase"),
