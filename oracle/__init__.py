@@ -9,7 +9,9 @@ the CUDA library.
 
 Functions follow the paper: rates (Sec. II.A Eq. RateCnst1, Sec. III ESP term),
 event selection (Eq. eventSelection), clock (Eq. TimeStep), fragment-local
-selection (Sec. II.B Eq. AtomP), D from tracked trajectories (Sec. III).
+selection (Sec. II.B Eq. AtomP), D from tracked trajectories (Sec. III),
+site-energy interactions (Sec. "Oxygen vacancy diffusion with dopant and defect
+interaction", Table add01).
 """
 from __future__ import annotations
 
@@ -68,6 +70,13 @@ def lib():
             "orc_get_counters": (None, [P, P, P]),
             "orc_get_params": (None, [P, P, P, P]),
             "orc_moments": (C.c_int, [P, C.c_int, P]),
+            "orc_place_dopants": (None, [P, i64]),
+            "orc_set_dopants": (None, [P, P]),
+            "orc_get_dopants": (C.c_int, [P, P]),
+            "orc_set_site_energy": (C.c_int, [P, C.c_int, P, P, C.c_int, P, P]),
+            "orc_site_shells": (C.c_int, [P, C.c_int, P, C.c_int]),
+            "orc_site_energy": (i64, [P, i64, i64]),
+            "orc_event_rate": (d, [P, i64, C.c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -131,15 +140,51 @@ def rate_table(Ea_O, Ea_H, A, q_O, q_H, T, Ez, a_ang, cap_v=64):
 class Lattice:
     """One replica held by the oracle.  ``nf`` = fragments per dimension."""
 
-    def __init__(self, cells, nf, n_vac, n_H, seed=0, replica=0, tracer=False):
+    def __init__(self, cells, nf, n_vac, n_H, seed=0, replica=0, tracer=False, n_Fe=0):
         self.L = tuple(int(c) for c in cells)
         self.nf = tuple(int(f) for f in nf)
         self.nsite = 3 * self.L[0] * self.L[1] * self.L[2]
+        self.ncell = self.L[0] * self.L[1] * self.L[2]
         self._h = lib().orc_create(*self.L, *self.nf, int(n_vac), int(n_H), int(seed), int(replica),
                                    int(bool(tracer)))
         if not self._h:
             raise ValueError("invalid lattice / partition / composition")
         self.tracer = bool(tracer)
+        if n_Fe:
+            lib().orc_place_dopants(self._h, int(n_Fe))
+
+    # ---------------------------------------------- site-energy interactions
+    def set_site_energy(self, vv=(), fe=()):
+        """Shell energies: ``vv`` = [(d2, eV), ...] over O-O squared distances,
+        ``fe`` = [(d2, eV), ...] over O-B squared distances, d2 in (a/2)^2."""
+        vd = np.array([int(d) for d, _ in vv] or [0], np.int32)
+        ve = np.array([float(e) for _, e in vv] or [0.0], np.float64)
+        fd = np.array([int(d) for d, _ in fe] or [0], np.int32)
+        fv = np.array([float(e) for _, e in fe] or [0.0], np.float64)
+        rc = lib().orc_set_site_energy(self._h, len(vv), _ptr(vd), _ptr(ve), len(fe), _ptr(fd), _ptr(fv))
+        if rc:
+            raise ValueError("invalid site-energy shells for this lattice / partition / precision")
+
+    def shells(self, t: int) -> np.ndarray:
+        out = np.zeros((1024, 5), np.int32)
+        k = lib().orc_site_shells(self._h, int(t), _ptr(out), 1024)
+        return out[:k]
+
+    def site_energy(self, s: int, exclude: int = -1) -> int:
+        return int(lib().orc_site_energy(self._h, int(s), int(exclude)))
+
+    def event_rate(self, s: int, n: int) -> float:
+        return float(lib().orc_event_rate(self._h, int(s), int(n)))
+
+    def dopants(self) -> np.ndarray:
+        out = np.zeros(self.ncell, np.uint8)
+        lib().orc_get_dopants(self._h, _ptr(out))
+        return out
+
+    def set_dopants(self, cells: np.ndarray):
+        cells = np.ascontiguousarray(cells, dtype=np.uint8)
+        assert cells.size == self.ncell
+        lib().orc_set_dopants(self._h, _ptr(cells))
 
     def __del__(self):
         h = getattr(self, "_h", None)

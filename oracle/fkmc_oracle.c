@@ -23,6 +23,11 @@
  *   - fragment-local selection (p_i depends only on the
  *     rates inside the fragment once the clock is shared) Sec. II.B, Eq. (AtomP)
  *   - D from tracked trajectories                     Sec. III (per-atom tracking)
+ *   - site-energy interactions (vacancy-vacancy and vacancy-dopant pair
+ *     energies by coordination shell, barrier Ea + dE_site/2)
+ *                                                    Sec. "Oxygen vacancy diffusion
+ *                                                    with dopant and defect
+ *                                                    interaction", Table add01
  * The spatial fragments, checkerboard colour phases, synchronisation windows
  * and hand-off of boundary hops are the synchronous-sublattice reading of the
  * fragment scheme; every step is written out in fkmc_phase() below.
@@ -46,6 +51,7 @@
 #define PURPOSE_PERM 2u
 #define PURPOSE_HOP 3u
 #define PURPOSE_BKL 4u
+#define PURPOSE_DOPE 5u
 
 /* ------------------------------------------------------------------ */
 /* Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers:
@@ -242,6 +248,13 @@ typedef struct {
     int F;
     double tau, theta_tau, k32max;
     int rates_set;
+    double T;       /* temperature of the rate table (K) */
+    /* site-energy interactions (plain form only) */
+    int site_on;
+    uint8_t* fe;    /* dopant (Fe) on the B site of each cell, [z][y][x] */
+    int n_vv, n_fe; /* offsets to the O sites / B sites inside the energy shells */
+    struct { int t2; int dc[3]; int32_t e; } vv[3][512];
+    struct { int dc[3]; int32_t e; } feo[3][512];
     /* counters */
     uint64_t window;
     uint64_t hops;
@@ -395,6 +408,7 @@ void orc_destroy(orc_lattice* lat)
     free(lat->frag);
     free(lat->occ);
     free(lat->tdisp);
+    free(lat->fe);
     free(lat);
 }
 
@@ -454,12 +468,213 @@ int orc_set_rates(orc_lattice* lat, double Ea_O, double Ea_H, double A, double q
         if ((i < 3 || nH > 0) && lat->k64[i] > kmax) kmax = lat->k64[i];
         if (lat->k32[i] > kmax32) kmax32 = lat->k32[i];
     }
+    if (lat->site_on && precision != 0) return -1;
+    lat->T = T_K;
     lat->tau = n_tau / (8.0 * kmax);
     lat->k32max = (double)kmax32;
     lat->theta_tau = lat->tau * lat->k32max;
     lat->precision = precision;
     lat->rates_set = 1;
     return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Site-energy interactions (Sec. "Oxygen vacancy diffusion with dopant and
+ * defect interaction"): the energy of a vacancy at site s is
+ *   E_site(s) = sum over shells k of  N_VV,k(s) e_VV,k + N_VFe,k(s) e_VFe,k,
+ * N counting the other vacancies (O sites) and the dopants (B sites, one per
+ * cell at the cell corner) at the shell's distance from s.  A hop of the
+ * vacancy from s to j has barrier Ea + dU/2 + (E_site(j) - E_site(s))/2,
+ * E_site(j) counted without the moving vacancy itself (it is the energy
+ * change of the whole configuration, so detailed balance holds).
+ * Shells are named by their squared distance in units of (a/2)^2: O-O shells
+ * are even (2 = a/sqrt2, 4 = a, 6, 8, 10, ...), O-B shells odd (1 = a/2, 5,
+ * 9, 13, ...).  Energies are held as integers in units of 1e-4 eV
+ * (rint(e * 1e4)), so every energy difference is exact.
+ * The Boltzmann factor exp(-dE/(2 kB T)) of an energy difference of m units is
+ * evaluated as exp(-(512 m1) c) * exp(-m0 c), m = 512 m1 + m0 with
+ * 0 <= m0 < 512 and c = 1e-4 / (2 kB T); the rate is (k_table * first) *
+ * second, each product one IEEE rounding.                              */
+/* ------------------------------------------------------------------ */
+static int32_t energy_quanta(double eV) { return (int32_t)llrint(eV * 1e4); }
+
+void orc_place_dopants(orc_lattice* lat, int64_t n_fe)
+{
+    /* keyed bijection of the cell indices (same Feistel construction as the
+     * vacancy placement, its own key): cells f(0..n_fe-1) hold a dopant */
+    int64_t ncell = (int64_t)lat->L[0] * lat->L[1] * lat->L[2];
+    free(lat->fe);
+    lat->fe = (uint8_t*)calloc((size_t)ncell, 1);
+    int b = 1;
+    while (((uint64_t)1 << (2 * b)) < (uint64_t)ncell) b++;
+    uint64_t mask = ((uint64_t)1 << b) - 1;
+    uint64_t key[2];
+    key_for(lat->seed, lat->replica, PURPOSE_DOPE, key);
+    for (int64_t i = 0; i < n_fe && i < ncell; i++) {
+        uint64_t v = (uint64_t)i;
+        do {
+            uint64_t Lh = v >> b, Rh = v & mask;
+            for (int k = 0; k < 4; k++) {
+                uint64_t ctr[4] = {Rh, (uint64_t)k, 0, 0}, o[4];
+                orc_philox4x64(ctr, key, o);
+                uint64_t nl = Rh, nr = Lh ^ (o[0] & mask);
+                Lh = nl; Rh = nr;
+            }
+            v = (Lh << b) | Rh;
+        } while (v >= (uint64_t)ncell);
+        lat->fe[v] = 1;
+    }
+}
+
+void orc_set_dopants(orc_lattice* lat, const uint8_t* cells)
+{
+    int64_t ncell = (int64_t)lat->L[0] * lat->L[1] * lat->L[2];
+    free(lat->fe);
+    lat->fe = (uint8_t*)malloc((size_t)ncell);
+    for (int64_t c = 0; c < ncell; c++) lat->fe[c] = cells[c] ? 1 : 0;
+}
+
+int orc_get_dopants(const orc_lattice* lat, uint8_t* cells)
+{
+    int64_t ncell = (int64_t)lat->L[0] * lat->L[1] * lat->L[2];
+    if (lat->fe) memcpy(cells, lat->fe, (size_t)ncell);
+    else memset(cells, 0, (size_t)ncell);
+    return 0;
+}
+
+/* Shell offsets by exhaustive search over a box of cells: every O site (or B
+ * site) whose squared distance from a site of type t is one of the listed
+ * shells.  n = 0 turns the interactions off. */
+int orc_set_site_energy(orc_lattice* lat, int n_vv, const int32_t* vv_d2, const double* vv_eV,
+                        int n_fe, const int32_t* fe_d2, const double* fe_eV)
+{
+    if (n_vv < 0 || n_vv > 8 || n_fe < 0 || n_fe > 8) return -1;
+    if (n_vv == 0 && n_fe == 0) { lat->site_on = 0; lat->n_vv = lat->n_fe = 0; return 0; }
+    if (lat->rates_set && lat->precision != 0) return -1;
+    /* a shell distance beyond the search box is an error */
+    for (int q = 0; q < n_vv; q++) if (vv_d2[q] <= 0 || vv_d2[q] > 36) return -1;
+    for (int q = 0; q < n_fe; q++) if (fe_d2[q] <= 0 || fe_d2[q] > 36) return -1;
+    int reach_vv = 0, reach_all = 0;
+    int cnt_vv[3] = {0, 0, 0}, cnt_fe[3] = {0, 0, 0};
+    int hit_vv[8] = {0}, hit_fe[8] = {0};
+    for (int t = 0; t < 3; t++) {
+        for (int cz = -4; cz <= 4; cz++)
+            for (int cy = -4; cy <= 4; cy++)
+                for (int cx = -4; cx <= 4; cx++) {
+                    int c[3] = {cx, cy, cz};
+                    /* O sites of type t2 in cell n + c */
+                    for (int t2 = 0; t2 < 3; t2++) {
+                        int r2 = 0;
+                        for (int k = 0; k < 3; k++) {
+                            int d = 2 * c[k] + (k == t2) - (k == t);
+                            r2 += d * d;
+                        }
+                        for (int q = 0; q < n_vv; q++)
+                            if (vv_d2[q] == r2) {
+                                if (cnt_vv[t] == 512) return -1;
+                                hit_vv[q] = 1;
+                                lat->vv[t][cnt_vv[t]].t2 = t2;
+                                for (int k = 0; k < 3; k++) lat->vv[t][cnt_vv[t]].dc[k] = c[k];
+                                lat->vv[t][cnt_vv[t]].e = energy_quanta(vv_eV[q]);
+                                cnt_vv[t]++;
+                                for (int k = 0; k < 3; k++) {
+                                    int a = c[k] < 0 ? -c[k] : c[k];
+                                    if (a > reach_vv) reach_vv = a;
+                                    if (a > reach_all) reach_all = a;
+                                }
+                            }
+                    }
+                    /* the B site at the corner of cell n + c */
+                    int r2 = 0;
+                    for (int k = 0; k < 3; k++) {
+                        int d = 2 * c[k] - (k == t);
+                        r2 += d * d;
+                    }
+                    for (int q = 0; q < n_fe; q++)
+                        if (fe_d2[q] == r2) {
+                            if (cnt_fe[t] == 512) return -1;
+                            hit_fe[q] = 1;
+                            for (int k = 0; k < 3; k++) lat->feo[t][cnt_fe[t]].dc[k] = c[k];
+                            lat->feo[t][cnt_fe[t]].e = energy_quanta(fe_eV[q]);
+                            cnt_fe[t]++;
+                            for (int k = 0; k < 3; k++) {
+                                int a = c[k] < 0 ? -c[k] : c[k];
+                                if (a > reach_all) reach_all = a;
+                            }
+                        }
+                }
+    }
+    /* a shell distance that the lattice does not have is an error */
+    for (int q = 0; q < n_vv; q++) if (!hit_vv[q]) return -1;
+    for (int q = 0; q < n_fe; q++) if (!hit_fe[q]) return -1;
+    if (cnt_vv[0] != cnt_vv[1] || cnt_vv[0] != cnt_vv[2]) return -1;
+    for (int k = 0; k < 3; k++) {
+        /* every offset lands on a distinct site of the periodic lattice */
+        if (lat->L[k] < 2 * reach_all + 1) return -1;
+        /* same-colour fragments neither read nor write what the other reads:
+         * reads reach 1 + reach_vv cells out of a fragment, writes 1 cell */
+        if (lat->nf[k] > 1 && lat->L[k] / lat->nf[k] < 2 + reach_vv) return -1;
+    }
+    lat->n_vv = cnt_vv[0];
+    lat->n_fe = cnt_fe[0];
+    lat->site_on = 1;
+    if (!lat->fe) lat->fe = (uint8_t*)calloc((size_t)lat->L[0] * lat->L[1] * lat->L[2], 1);
+    return 0;
+}
+
+/* export of the shell offsets of site type t: rows {t2, dcx, dcy, dcz, e}
+ * (V-V, t2 = the O site type) then rows {-1, dcx, dcy, dcz, e} (V-Fe) */
+int orc_site_shells(const orc_lattice* lat, int t, int32_t* out, int max_rows)
+{
+    int k = 0;
+    for (int i = 0; i < lat->n_vv && k < max_rows; i++, k++) {
+        int32_t* o = out + 5 * k;
+        o[0] = lat->vv[t][i].t2;
+        for (int d = 0; d < 3; d++) o[1 + d] = lat->vv[t][i].dc[d];
+        o[4] = lat->vv[t][i].e;
+    }
+    for (int i = 0; i < lat->n_fe && k < max_rows; i++, k++) {
+        int32_t* o = out + 5 * k;
+        o[0] = -1;
+        for (int d = 0; d < 3; d++) o[1 + d] = lat->feo[t][i].dc[d];
+        o[4] = lat->feo[t][i].e;
+    }
+    return k;
+}
+
+/* E_site of site s in energy units, the site `exclude` counted as empty */
+int64_t orc_site_energy(const orc_lattice* lat, int64_t s, int64_t exclude)
+{
+    if (!lat->site_on) return 0;
+    int t, c[3];
+    site_coords(lat, s, &t, c);
+    int64_t E = 0;
+    for (int i = 0; i < lat->n_vv; i++) {
+        int64_t u = site_index(lat, lat->vv[t][i].t2, wrap(c[0] + lat->vv[t][i].dc[0], lat->L[0]),
+                               wrap(c[1] + lat->vv[t][i].dc[1], lat->L[1]),
+                               wrap(c[2] + lat->vv[t][i].dc[2], lat->L[2]));
+        if (u != exclude && lat->occ[u] == SP_V) E += lat->vv[t][i].e;
+    }
+    for (int i = 0; i < lat->n_fe; i++) {
+        int x = wrap(c[0] + lat->feo[t][i].dc[0], lat->L[0]);
+        int y = wrap(c[1] + lat->feo[t][i].dc[1], lat->L[1]);
+        int z = wrap(c[2] + lat->feo[t][i].dc[2], lat->L[2]);
+        if (lat->fe[((int64_t)z * lat->L[1] + y) * lat->L[0] + x]) E += lat->feo[t][i].e;
+    }
+    return E;
+}
+
+/* rate of the event (vacancy at s, ion at neighbour j) of table type ty */
+static double site_rate(const orc_lattice* lat, int64_t s, int64_t j, int ty)
+{
+    int64_t m = orc_site_energy(lat, j, s) - orc_site_energy(lat, s, -1);
+    int64_t m1 = m >= 0 ? m / 512 : -((-m + 511) / 512);
+    int64_t m0 = m - 512 * m1;
+    double c = 1e-4 / (2.0 * (KB_EV * lat->T));
+    double f1 = exp(-((double)(512 * m1) * c));
+    double f0 = exp(-((double)m0 * c));
+    double k = lat->k64[ty] * f1;
+    return k * f0;
 }
 
 /* rate type of the event "vacancy at s exchanges with neighbour n", or -1 */
@@ -472,6 +687,18 @@ static int event_type(const orc_lattice* lat, int64_t s, int n)
     if (sp == SP_V) return -1;
     return 3 * sp + NB[t][n].d[2] + 1;
 }
+
+/* FP64 rate of the event (s, n): the table rate, times the site-energy
+ * factor when the interactions are on; 0 when the neighbour is a vacancy */
+static double event_rate64(const orc_lattice* lat, int64_t s, int n)
+{
+    int ty = event_type(lat, s, n);
+    if (ty < 0) return 0.0;
+    if (!lat->site_on) return lat->k64[ty];
+    return site_rate(lat, s, neighbour_site(lat, s, n), ty);
+}
+
+double orc_event_rate(const orc_lattice* lat, int64_t s, int n) { return event_rate64(lat, s, n); }
 
 static int cmp_rec(const void* a, const void* b)
 {
@@ -523,12 +750,13 @@ static void fkmc_phase(orc_lattice* lat, int F, uint64_t w)
     uint64_t blk[4] = {0, 0, 0, 0};
     uint64_t blk_id = ~(uint64_t)0;
     for (;;) {
-        /* rates of every event of F, Eq. (RateCnst1) table lookups */
+        /* rates of every event of F, Eq. (RateCnst1) table lookups (times
+         * the site-energy factor when the interactions are on) */
         for (int m = 0; m < n; m++)
             for (int nb = 0; nb < 8; nb++) {
                 int e = 8 * m + nb;
                 int ty = alive[m] ? event_type(lat, slot[m].site, nb) : -1;
-                r64[e] = ty < 0 ? 0.0 : lat->k64[ty];
+                r64[e] = ty < 0 ? 0.0 : event_rate64(lat, slot[m].site, nb);
                 rq[e] = ty < 0 ? 0 : lat->q[ty];
             }
         /* draws of event i: Philox block (F, w, i/2); even i takes words 0,1 */
@@ -650,8 +878,7 @@ int orc_bkl_run(orc_lattice* lat, double t_end, uint64_t stream, double* t_out)
         double R = 0.0;
         for (int m = 0; m < n; m++)
             for (int nb = 0; nb < 8; nb++) {
-                int ty = event_type(lat, v[m].site, nb);
-                r[8 * m + nb] = ty < 0 ? 0.0 : lat->k64[ty];
+                r[8 * m + nb] = event_rate64(lat, v[m].site, nb);
                 R += r[8 * m + nb];
             }
         if (!(R > 0.0)) { t = t_end; break; }
