@@ -31,6 +31,9 @@ sys.path.insert(0, ROOT)
 METRIC = "hops/s on 1 GB300 (batched mixed vs plain FP64) at D within 1%; HBM roofline frac"
 UNIT = "hops/s"
 B_ALG_PER_HOP = 160  # algorithmic bytes per hop at 32-byte sector granularity
+# site-energy path: + the energy field, 4-byte words: 9 reads (the vacancy's site and
+# its 8 targets) and a read-modify-write of the 2 x 58 V-V partners moved with the hop
+B_ALG_PER_HOP_SITE = 160 + 4 * (9 + 2 * 2 * 58)
 
 
 def parse():
@@ -43,9 +46,10 @@ def parse():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    p.add_argument("--workload", default="batched", choices=["batched", "sweep", "bulk", "um"],
+    p.add_argument("--workload", default="batched", choices=["batched", "sweep", "bulk", "um", "fe"],
                    help="batched: 256 uneven replicas (the headline); sweep: SrTiO(3-x)H_x 32^3 at "
-                        "300..700 K; bulk: BaTiO(3-x)H_x 128^3; um: BaTiO3 L^3 under bias")
+                        "300..700 K; bulk: BaTiO(3-x)H_x 128^3; um: BaTiO3 L^3 under bias; fe: Fe-doped "
+                        "SrTiO3 96^3 with vacancy-vacancy and vacancy-Fe site energies at 600..1000 K")
     p.add_argument("--um-cells", type=int, default=2500, help="edge of the um-scale cube (cells)")
     p.add_argument("--no-autotune", action="store_true", help="use the workload's default edge")
     return p.parse_args()
@@ -132,12 +136,14 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ helpers
-def make_batch(fk, wl, seed, precision, replicas=None, edge=None, tracer=None, **opts):
+def make_batch(fk, wl, seed, precision, replicas=None, edge=None, tracer=None, site=True, **opts):
     reps = wl.replicas if replicas is None else [wl.replicas[i] for i in replicas]
     nf = reps[0].nfrag if (len(reps) == 1 and reps[0].nfrag) else None
-    b = fk.Batch([(*r.cells, r.a) for r in reps], [(r.n_vac, r.n_H) for r in reps], seed,
+    b = fk.Batch([(*r.cells, r.a) for r in reps], [(r.n_vac, r.n_H, r.n_Fe) for r in reps], seed,
                  edge=wl.edge if edge is None else edge, nfrag=nf, precision=precision,
                  tracer=wl.tracer if tracer is None else tracer, **opts)
+    if wl.site and site:
+        b.set_site_energy(wl.site["vv"], wl.site["fe"])
     b.set_barriers([r.Ea_O for r in reps], [r.Ea_H for r in reps], [r.T for r in reps],
                    field_z=[r.field_z for r in reps])
     return b
@@ -162,7 +168,9 @@ def cpu_oracle_rate(wl, seed, windows, budget_s, replicas=None):
         for r in order:
             rep = wl.replicas[r]
             nf = rep.nfrag or tuple(_nfrag(c, wl.edge) for c in rep.cells)
-            L = oracle.Lattice(rep.cells, nf, rep.n_vac, rep.n_H, seed=seed, replica=r)
+            L = oracle.Lattice(rep.cells, nf, rep.n_vac, rep.n_H, seed=seed, replica=r, n_Fe=rep.n_Fe)
+            if wl.site:
+                L.set_site_energy(vv=wl.site["vv"], fe=wl.site["fe"])
             L.set_rates(rep.Ea_O, rep.Ea_H, rep.T, Ez=rep.field_z, a_ang=rep.a, cap_v=cap,
                         precision=wl.precision)
             while True:  # single lattices keep running until the budget is spent
@@ -310,10 +318,11 @@ def main():
     fkmc.load()
     seed = args.seed + rank  # each rank simulates its own independent batch (weak scaling)
     makers = {"batched": workloads.batched_batio3, "sweep": workloads.srtio3_h_sweep,
-              "bulk": workloads.bulk_batio3, "um": lambda sd: workloads.um_batio3_bias(sd, args.um_cells)}
+              "bulk": workloads.bulk_batio3, "um": lambda sd: workloads.um_batio3_bias(sd, args.um_cells),
+              "fe": workloads.fe_srtio3}
     wl = makers[args.workload](seed)
     nrep = len(wl.replicas)
-    default_windows = {"batched": 64, "sweep": 64, "bulk": 16, "um": 2}
+    default_windows = {"batched": 64, "sweep": 64, "bulk": 16, "um": 2, "fe": 32}
     W = args.windows if args.windows else default_windows[args.workload]
     stream = torch.cuda.current_stream()
     reps = wl.replicas
@@ -385,15 +394,18 @@ def main():
     else:
         units = args.steps * W * 8  # one colour phase = one screen and one run launch
         tag = "k_phase_" + ("mixed_" if precision else "plain_") + args.workload
-        kname = "k_phase<%s> (colour-phase kernel)" % ("mixed" if precision else "plain")
+        kname = "k_phase<%s%s> (colour-phase kernel)" % ("mixed" if precision else "plain",
+                                                         ", site energies" if wl.site else "")
         note = ("a launch here is one colour phase (screen + run pass); neighbour words read from L2/HBM "
-                "with ld.global.cg; algorithmic bytes = 160 B per hop at 32-byte sectors")
+                "with ld.global.cg; algorithmic bytes = 160 B per hop at 32-byte sectors" +
+                (" + the energy-field words of the site-energy path" if wl.site else ""))
+    b_alg = B_ALG_PER_HOP_SITE if wl.site else B_ALG_PER_HOP
     avg_launch_s = kernel_ms / 1e3 / units
-    bytes_per_launch = hops / units * B_ALG_PER_HOP
+    bytes_per_launch = hops / units * b_alg
     achieved = bytes_per_launch / avg_launch_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": load_traffic(tag), "peak_kind": f"{peak_kind} hbm_gbs",
-                "kernel": kname, "bytes_per_hop": B_ALG_PER_HOP, "hops_per_launch": hops / units,
+                "kernel": kname, "bytes_per_hop": b_alg, "hops_per_launch": hops / units,
                 "avg_launch_us": avg_launch_s * 1e6, "note": note}
 
     extra = {}
@@ -420,7 +432,29 @@ def main():
             extra["e2e"] = {"value": None, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": 0,
                             "note": "state larger than 4 GiB: not re-uploaded every step"}
 
-        if not args.no_plain:
+        if wl.site:
+            # the paper's dopant comparison: D of the vacancies with the full model, without
+            # the V-V term, without the dopant term and without interactions, same draws
+            trend = {}
+            variants = {"vv_and_fe": (wl.site["vv"], wl.site["fe"]), "fe_only": ((), wl.site["fe"]),
+                        "vv_only": (wl.site["vv"], ()), "none": ((), ())}
+            rates = {}
+            for nm, (vv, fe) in variants.items():
+                bv = make_batch(fkmc, wl, seed, precision, edge=edge, site=False)
+                if vv or fe:
+                    bv.set_site_energy(vv, fe)
+                bv.run(2)
+                sv = bv.run(4 * W)
+                rates[nm] = sv.hops / (sv.gpu_ms / 1e3) if sv.gpu_ms > 0 else None
+                trend[nm] = [bv.D(r, fkmc.FKMC_V)[1] for r in range(nrep)]
+                bv.close()
+            extra["site_energy"] = {
+                "T": [r.T for r in reps], "D_V": trend, "windows": 4 * W + 2,
+                "hops_per_s": rates,
+                "note": "D_V (m^2/s) per temperature; the paper reports that the dopant term lowers D_V "
+                        "strongly and the V-V term raises it again",
+            }
+        if not args.no_plain and not wl.site:
             # accuracy: mixed vs plain FP64 from the same initial state, same draws
             Wacc = 4 * W
             bm = make_batch(fkmc, wl, seed, fkmc.FKMC_MIXED, edge=edge)

@@ -72,7 +72,32 @@ typedef struct {
 typedef struct {
     int64_t n_vac; /* O vacancies placed at creation */
     int64_t n_H;   /* H- ions placed at creation (on O sites) */
+    int64_t n_Fe;  /* dopants placed at creation on the B sites (cell corners); they do not move and
+                      act only through the site energies of kmc_set_site_energy */
 } kmc_composition;
+
+/* Site-energy interactions (the dopant/defect section of the paper and its
+ * Table add01): the energy of a vacancy at O site s is
+ *   E_site(s) = sum_k N_VV,k(s) vv_eV[k] + sum_k N_VFe,k(s) fe_eV[k],
+ * N counting the other vacancies at squared O-O distance vv_d2[k] and the
+ * dopants at squared O-B distance fe_d2[k] from s (both in units of (a/2)^2:
+ * O-O shells are even, 2 = a/sqrt2, 4 = a, 6, 8, 10, ...; O-B shells odd,
+ * 1 = a/2, 5, 9, 13, ...).  The hop s -> j then has barrier
+ * Ea + dU/2 + (E_site(j) - E_site(s))/2, E_site(j) counted without the hopping
+ * vacancy (the energy change of the whole configuration, so detailed balance
+ * holds).  Energies are rounded to multiples of 1e-4 eV (rint(e * 1e4)); the
+ * factor exp(-dE/(2 kB T)) of an energy difference of m such units is
+ * exp(-(512 m1) c) * exp(-m0 c), m = 512 m1 + m0, 0 <= m0 < 512,
+ * c = 1e-4 / (2 kB T), multiplied into the table rate in that order. */
+#define FKMC_MAX_SHELLS 8
+typedef struct {
+    int32_t n_vv;                   /* V-V shells in use, 0..8 */
+    int32_t vv_d2[FKMC_MAX_SHELLS]; /* squared O-O distance of each shell, (a/2)^2 units */
+    double vv_eV[FKMC_MAX_SHELLS];  /* pair energy of a vacancy in that shell, eV */
+    int32_t n_fe;                   /* vacancy-dopant shells in use, 0..8 */
+    int32_t fe_d2[FKMC_MAX_SHELLS]; /* squared O-B distance of each shell, (a/2)^2 units */
+    double fe_eV[FKMC_MAX_SHELLS];  /* pair energy of a vacancy and a dopant in that shell, eV */
+} kmc_site_energy;
 
 typedef struct {
     double Ea_O_eV;   /* barrier of the O <-> V exchange */
@@ -143,7 +168,9 @@ void kmc_default_opts(kmc_opts* opts);
  * images of 0, 1, 2, ... under a keyed bijection of the site indices (a
  * 4-round Feistel network with cycle walking); vacancy i gets id i.  The
  * paper gives no placement rule; this one gives exact counts and uniformly
- * random positions.
+ * random positions.  Dopants take the cells at the images of 0 ..
+ * comp[r].n_Fe - 1 under the same construction over the cell indices with
+ * its own key.
  * Errors: FKMC_EINVAL for n < 1, bad cells/partition/composition or opts;
  * FKMC_ENOMEM / FKMC_ECUDA; FKMC_EOVERFLOW if a fragment starts with more
  * vacancies than cap_v.  On error *out is NULL and nothing is leaked. */
@@ -165,10 +192,47 @@ int kmc_create_lattice(const kmc_cells* cells, const kmc_composition* comp, uint
 int kmc_set_barriers(kmc_batch* b, const kmc_barrier_table* tables, const double* T_K,
                      const double* field_z_Vpm);
 
+/* Turn the site-energy interactions on for every replica of the batch (e
+ * NULL, or no shells, turns them off).  Plain form only: the event rates are
+ * FP64 products of the table rate and the Boltzmann factor above, summed in
+ * the canonical order.  Every replica then runs the colour-phase kernels
+ * (the replica-resident kernel has no site energies).  The library keeps an
+ * int32 energy field of every O site (4 bytes per site), rebuilt from the
+ * vacancies and dopants at the next kmc_run after any state change, and
+ * moved with each hop.
+ * Errors: FKMC_EINVAL for the mixed form, more than 8 shells, a squared
+ * distance that is not a shell of the lattice or above 36, |energy| > 10 eV,
+ * a dimension shorter than 2 R + 1 cells (R = the largest cell offset of any
+ * shell: a partner would be counted twice) or, where a dimension has more
+ * than one fragment, a fragment edge below 2 + R_VV (R_VV from the V-V
+ * shells: same-colour fragments would then read each other's writes);
+ * FKMC_ENOMEM; FKMC_ECUDA. */
+int kmc_set_site_energy(kmc_batch* b, const kmc_site_energy* e);
+
+/* Host-only: the partner table of e for an O site of type t: rows
+ * {t2, dcx, dcy, dcz, energy} of the V-V partners (O site type t2 in the cell
+ * offset dc) followed by rows {-1, dcx, dcy, dcz, energy} of the B sites in
+ * the dopant shells; energies in 1e-4 eV units.  *n_rows gets the row count,
+ * at most max_rows rows are written.  Errors as kmc_set_site_energy's shell
+ * checks. */
+int kmc_site_shells(const kmc_site_energy* e, int32_t t, int32_t* rows, int32_t max_rows, int32_t* n_rows);
+
+/* Dopants of replica r, one byte per cell (1 = doped), cell index
+ * (z ny + y) nx + x.  kmc_write_dopants replaces them (the energy field is
+ * rebuilt at the next kmc_run).  n must equal nx ny nz. */
+int kmc_read_dopants(kmc_batch* b, int32_t r, uint8_t* host_cells, size_t n);
+int kmc_write_dopants(kmc_batch* b, int32_t r, const uint8_t* host_cells, size_t n);
+
+/* Energy field of replica r: E_site of every O site in 1e-4 eV units, site
+ * index as in kmc_read_state (FKMC_ESTATE while the interactions are off). */
+int kmc_read_site_field(kmc_batch* b, int32_t r, int32_t* host_field, size_t n);
+
 /* Run `windows` synchronisation windows on every replica.  Synchronous.
  * Errors: FKMC_ESTATE before kmc_set_barriers; FKMC_EOVERFLOW if a hand-off
  * found its target fragment full (the state is then invalid);
- * FKMC_ETIMEOUT if a device wait gave up; FKMC_ECUDA. */
+ * FKMC_ETIMEOUT if a device wait gave up; FKMC_ECUDA; FKMC_ESTATE if a site
+ * energy difference fell outside the tables' bound (cannot happen for a
+ * consistent field; the event was dropped). */
 int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats);
 
 /* Exact integer moments of the displacements of one species of replica r:

@@ -148,6 +148,20 @@ struct kmc_batch {
     int run_blocks = 0;
     cudaStream_t cap_st = nullptr;
     cudaGraphExec_t window_exec = nullptr;
+    // site-energy interactions (plain form, colour-phase kernels)
+    bool site_on = false;
+    bool field_valid = false;
+    std::vector<int64_t> n_fe;
+    std::vector<double> T;           // temperature of every replica (kmc_set_barriers)
+    int n_vv = 0, n_bo = 0, e_self = 0;
+    int64_t e_bound = 0;             // bound on |E_site|, 1e-4 eV units
+    int64_t ncell_total = 0;
+    uint8_t* fe = nullptr;           // one byte per cell, batch-wide cell index
+    int32_t* field = nullptr;        // E_site per O site
+    SiteOff* d_vv = nullptr;
+    SiteOff* d_bo = nullptr;
+    double* btab = nullptr;          // Boltzmann tables of every replica
+    size_t btab_bytes = 0;
 
     void* dalloc(size_t bytes)
     {
@@ -162,6 +176,19 @@ struct kmc_batch {
         }
         if (p) owned.push_back(p);
         return p;
+    }
+
+    void dfree(void* p)
+    {
+        if (!p) return;
+        auto it = std::find(owned.begin(), owned.end(), p);
+        if (it == owned.end()) return;
+        owned.erase(it);
+        if (opts.alloc) {
+            if (opts.free) opts.free(opts.alloc_ctx, p);
+        } else {
+            cudaFree(p);
+        }
     }
 
     void release()
@@ -202,6 +229,8 @@ int check_status(kmc_batch* b)
     if (s & STATUS_TIMEOUT) return fail(FKMC_ETIMEOUT, "a device-side wait ran out of time");
     if (s & STATUS_EVENT_LIMIT)
         return fail(FKMC_ETIMEOUT, "a fragment reached the per-phase event limit (window too long)");
+    if (s & STATUS_ENERGY_RANGE)
+        return fail(FKMC_ESTATE, "a site-energy difference fell outside the Boltzmann tables' bound");
     return FKMC_OK;
 }
 
@@ -256,7 +285,7 @@ int plan_residency(kmc_batch* b)
     }
     b->rclass.clear();
     const bool allowed = b->opts.precision == FKMC_MIXED && b->opts.schedule != 1 &&
-                         b->cap <= RESIDENT_MAX_SLOTS;
+                         b->cap <= RESIDENT_MAX_SLOTS && !b->site_on;
     // launch classes: (shared-memory bound, threads); a replica takes the first
     // class its state fits, so small replicas pack several CTAs per SM and the
     // largest get the most warps that still fit beside their state.  The
@@ -311,6 +340,170 @@ int plan_residency(kmc_batch* b)
                            b->st),
            "replica list upload");
     return FKMC_OK;
+}
+
+// ---------------------------------------------------------------- site energies
+// Partners of a site by displacement: a vector d (units a/2) from a site at p0
+// lands on an O site when exactly one coordinate of p0 + d is odd (that axis is
+// the O site's type), on a B site (cell corner) when all are even.
+struct Landing { int kind; int t2; int dc[3]; };  // kind 0: O site, 1: B site, -1: neither
+
+Landing land(const int p0[3], const int d[3])
+{
+    Landing L{-1, -1, {0, 0, 0}};
+    int p[3], odd = 0, axis = -1;
+    for (int k = 0; k < 3; ++k) {
+        p[k] = p0[k] + d[k];
+        if (p[k] & 1) { ++odd; axis = k; }
+    }
+    if (odd == 1) {
+        L.kind = 0;
+        L.t2 = axis;
+        for (int k = 0; k < 3; ++k) L.dc[k] = (p[k] - (k == axis)) / 2;
+    } else if (odd == 0) {
+        L.kind = 1;
+        for (int k = 0; k < 3; ++k) L.dc[k] = p[k] / 2;
+    }
+    return L;
+}
+
+int32_t energy_units(double eV) { return (int32_t)std::llrint(eV * 1e4); }
+
+// Partner tables of a shell set: V-V partners of each O site type, the O
+// sites around a B site (dopant scatter), the B sites around each O site type,
+// the reaches in cells, the bound on |E_site| and the a/sqrt2 shell energy.
+struct ShellTables {
+    std::vector<SiteOff> vv = std::vector<SiteOff>((size_t)3 * SITE_MAX_VV);
+    int nvv = 0;
+    std::vector<SiteOff> bo;
+    std::vector<SiteOff> ob[3];
+    int reach_vv = 0, reach_all = 0;
+    int64_t bound = 0;
+    int32_t e_self = 0;
+};
+
+int make_shells(const kmc_site_energy* e, ShellTables* out)
+{
+    if (e->n_vv < 0 || e->n_vv > FKMC_MAX_SHELLS || e->n_fe < 0 || e->n_fe > FKMC_MAX_SHELLS)
+        return fail(FKMC_EINVAL, "0 to 8 shells of each kind");
+    const int ns = e->n_vv + e->n_fe;
+    auto d2_of = [&](int k) { return k < e->n_vv ? e->vv_d2[k] : e->fe_d2[k - e->n_vv]; };
+    auto en_of = [&](int k) { return k < e->n_vv ? e->vv_eV[k] : e->fe_eV[k - e->n_vv]; };
+    for (int k = 0; k < ns; ++k) {
+        if (d2_of(k) < 1 || d2_of(k) > 36 || !std::isfinite(en_of(k)) || std::fabs(en_of(k)) > 10.0)
+            return fail(FKMC_EINVAL, "shell squared distances must be in [1, 36], energies finite within 10 eV");
+        for (int q = 0; q < k; ++q)
+            if ((q < e->n_vv) == (k < e->n_vv) && d2_of(q) == d2_of(k))
+                return fail(FKMC_EINVAL, "a shell is listed twice");
+    }
+    ShellTables& sh = *out;
+    int nvv[3] = {0, 0, 0};
+    std::vector<int> hit(ns, 0);
+    // centre = an O site of type t (t = 0..2) or a B site (t = 3); |d| <= 6
+    // half-units per axis covers every squared distance up to 36
+    for (int t = 0; t < 4; ++t) {
+        const int p0[3] = {t == 0, t == 1, t == 2};
+        int64_t sum = 0;
+        for (int dz = -6; dz <= 6; ++dz)
+            for (int dy = -6; dy <= 6; ++dy)
+                for (int dx = -6; dx <= 6; ++dx) {
+                    const int d[3] = {dx, dy, dz};
+                    const int d2 = dx * dx + dy * dy + dz * dz;
+                    const Landing L = land(p0, d);
+                    if (L.kind < 0) continue;
+                    // O centre: O partners in V-V shells, B partners in dopant shells;
+                    // B centre: O partners in dopant shells
+                    const bool want_vv = t < 3 && L.kind == 0;
+                    if (!want_vv && (L.kind == 0) == (t < 3)) continue;
+                    for (int k = want_vv ? 0 : e->n_vv; k < (want_vv ? e->n_vv : ns); ++k) {
+                        if (d2_of(k) != d2) continue;
+                        hit[k] = 1;
+                        SiteOff o;
+                        o.t2 = (int8_t)(L.kind == 0 ? L.t2 : -1);
+                        for (int a = 0; a < 3; ++a) o.dc[a] = (int8_t)L.dc[a];
+                        o.e = energy_units(en_of(k));
+                        int reach = 0;
+                        for (int a = 0; a < 3; ++a) reach = std::max(reach, std::abs(L.dc[a]));
+                        sh.reach_all = std::max(sh.reach_all, reach);
+                        if (t == 3) {
+                            if ((int)sh.bo.size() == SITE_MAX_BO) return fail(FKMC_EINVAL, "too many dopant partners");
+                            sh.bo.push_back(o);
+                            continue;
+                        }
+                        sum += o.e < 0 ? -(int64_t)o.e : o.e;
+                        if (want_vv) {
+                            sh.reach_vv = std::max(sh.reach_vv, reach);
+                            if (nvv[t] == SITE_MAX_VV) return fail(FKMC_EINVAL, "too many V-V partners per site");
+                            sh.vv[(size_t)t * SITE_MAX_VV + nvv[t]++] = o;
+                        } else {
+                            sh.ob[t].push_back(o);
+                        }
+                    }
+                }
+        if (t < 3) sh.bound = std::max(sh.bound, sum);
+    }
+    for (int k = 0; k < ns; ++k)
+        if (!hit[k]) return fail(FKMC_EINVAL, "a squared distance is not a shell of this lattice");
+    sh.nvv = nvv[0];
+    for (int k = 0; k < e->n_vv; ++k)
+        if (e->vv_d2[k] == 2) sh.e_self = energy_units(e->vv_eV[k]);
+    return FKMC_OK;
+}
+
+// Boltzmann tables of every replica: lo[m0] = exp(-m0 c), hi[i] = exp(-512 (i - mid) c),
+// c = 1e-4 / (2 kB T); |m| <= 2 e_bound, so m >> 9 stays within [-mid, mid].
+int build_btab(kmc_batch* b)
+{
+    const int mid = (int)((2 * b->e_bound + 511) / 512) + 1;
+    const int len = 2 * mid + 1;
+    const size_t per = (size_t)BOLTZ_LO + len;
+    std::vector<double> h(per * b->n);
+    for (int r = 0; r < b->n; ++r) {
+        const double c = 1e-4 / (2.0 * (KB_EV * b->T[r]));
+        double* lo = h.data() + per * r;
+        for (int m0 = 0; m0 < BOLTZ_LO; ++m0) lo[m0] = std::exp(-((double)m0 * c));
+        for (int i = 0; i < len; ++i) lo[BOLTZ_LO + i] = std::exp(-((double)(512 * (int64_t)(i - mid)) * c));
+        b->desc[r].btab_off = (int64_t)(per * r);
+        b->desc[r].bhi_mid = mid;
+        b->desc[r].bhi_len = len;
+    }
+    const size_t bytes = sizeof(double) * h.size();
+    if (bytes > b->btab_bytes) {
+        b->dfree(b->btab);
+        b->btab = (double*)b->dalloc(bytes);
+        b->btab_bytes = b->btab ? bytes : 0;
+        if (!b->btab) return fail(FKMC_ENOMEM, "device allocation failed (Boltzmann tables)");
+    }
+    CK(cudaMemcpyAsync(b->btab, h.data(), bytes, cudaMemcpyHostToDevice, b->st), "table upload");
+    CK(cudaStreamSynchronize(b->st), "synchronize");
+    return FKMC_OK;
+}
+
+SiteArgs site_args(const kmc_batch* b)
+{
+    SiteArgs a{};
+    a.vv = b->d_vv;
+    a.btab = b->btab;
+    a.field = b->field;
+    a.n_vv = b->n_vv;
+    a.e_self = b->e_self;
+    return a;
+}
+
+int rebuild_field(kmc_batch* b)
+{
+    const SiteArgs a = site_args(b);
+    CK(launch_site_field(b->d_desc, b->n, b->recs, b->counts, b->nfrag_total, b->cap, b->nsite_total, b->fe, b->d_bo,
+                         b->n_bo, a, b->st),
+       "energy field");
+    b->field_valid = true;
+    return FKMC_OK;
+}
+
+void drop_window_graph(kmc_batch* b)
+{
+    if (b->window_exec) cudaGraphExecDestroy(b->window_exec);
+    b->window_exec = nullptr;
 }
 
 }  // namespace
@@ -374,6 +567,8 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
     b->desc.resize(n);
     b->n_vac.resize(n);
     b->n_H.resize(n);
+    b->n_fe.assign(n, 0);
+    b->T.assign(n, 0.0);
     b->b_bits.resize(n);
     b->a_ang.resize(n);
     b->stats_host.assign(2 * (size_t)n, 0ull);
@@ -407,8 +602,13 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
             delete b;
             return fail(FKMC_EINVAL, "composition does not fit the lattice");
         }
+        if (comp[r].n_Fe < 0 || comp[r].n_Fe > (int64_t)L[0] * L[1] * L[2]) {
+            delete b;
+            return fail(FKMC_EINVAL, "dopant count must be in [0, nx ny nz]");
+        }
         b->n_vac[r] = comp[r].n_vac;
         b->n_H[r] = comp[r].n_H;
+        b->n_fe[r] = comp[r].n_Fe;
         b->a_ang[r] = c.a_angstrom;
         D.replica = (uint32_t)r;
         D.seed = seed;
@@ -462,6 +662,17 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
     b->perms = (uint32_t*)b->dalloc(sizeof(uint32_t) * n);
     b->act = (ActEntry*)b->dalloc(sizeof(ActEntry) * std::max<int64_t>(b->total_items, 1));
     b->act_count = (int32_t*)b->dalloc(sizeof(int32_t) * 8);
+    b->ncell_total = b->nsite_total / 3;
+    bool any_fe = false;
+    for (int r = 0; r < n; ++r) any_fe = any_fe || b->n_fe[r] > 0;
+    if (any_fe) {
+        b->fe = (uint8_t*)b->dalloc((size_t)b->ncell_total);
+        if (!b->fe) {
+            b->release();
+            delete b;
+            return fail(FKMC_ENOMEM, "device allocation failed");
+        }
+    }
     if (!b->occ || !b->recs || !b->counts || (o.tracer && !b->tracer) || !b->d_desc || !b->stats ||
         !b->status || !b->scratch || !b->scratch_all || !b->d_reps || !b->d_nvac || !b->wctl || !b->perms ||
         !b->act || !b->act_count) {
@@ -476,7 +687,7 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
     build_nb_table(b->nbt.e);
     step(upload_neighbours(&b->nbt.e[0][0]), "neighbour table upload");
     step(phase_prepare(b->cap), "kernel attributes");
-    step(run_pass_blocks(b->opts.precision, b->cap, &b->run_blocks), "occupancy query");
+    step(run_pass_blocks(b->opts.precision, b->cap, false, &b->run_blocks), "occupancy query");
     step(resident_prepare(), "kernel attributes");
     step(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "event");
     step(cudaEventCreate(&b->ev0), "event");
@@ -490,6 +701,14 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
         step(launch_init(b->desc[r], b->b_bits[r], b->n_vac[r], b->n_vac[r] + b->n_H[r], b->occ, b->recs,
                          b->counts, b->cap, b->status, b->st),
              "init kernel");
+    if (b->fe) {
+        step(cudaMemsetAsync(b->fe, 0, (size_t)b->ncell_total, b->st), "memset");
+        for (int r = 0; r < n && rc == FKMC_OK; ++r) {
+            int bb = 1;
+            while (((int64_t)1 << (2 * bb)) < b->desc[r].nsite / 3) ++bb;
+            step(launch_init_dopants(b->desc[r], bb, b->n_fe[r], b->fe, b->st), "dopant kernel");
+        }
+    }
     if (rc == FKMC_OK) rc = upload_desc(b);
     if (rc == FKMC_OK) rc = check_status(b);
     if (rc != FKMC_OK) {
@@ -533,7 +752,13 @@ int kmc_set_barriers(kmc_batch* b, const kmc_barrier_table* tables, const double
         D.theta_tau = D.tau * (double)kmax32;
     }
     b->desc = nd;
-    int rc = plan_residency(b);
+    for (int r = 0; r < b->n; ++r) b->T[r] = T_K[r];
+    int rc = FKMC_OK;
+    if (b->site_on) {
+        rc = build_btab(b);
+        if (rc) return rc;
+    }
+    rc = plan_residency(b);
     if (rc) return rc;
     CK(cudaMemcpyAsync(b->d_nvac, b->n_vac.data(), sizeof(int64_t) * b->n, cudaMemcpyHostToDevice, b->st),
        "vacancy count upload");
@@ -563,15 +788,23 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
             CK(cudaEventRecord(c.done, c.st), "event record");
         }
     }
+    uint64_t extra_launches = 0;
+    if (b->site_on && !b->field_valid) {
+        int rc0 = rebuild_field(b);
+        if (rc0) return rc0;
+        extra_launches = (b->n_vv > 0) + (b->n_bo > 0);
+    }
+    const SiteArgs sargs = site_args(b);
     if (b->any_global && windows > 0) {
         if (!b->window_exec) {
             // capture one window (set-up + 8 x (screen, run)) once; every argument is fixed
-            CK(cudaStreamCreateWithFlags(&b->cap_st, cudaStreamNonBlocking), "stream");
+            if (!b->cap_st) CK(cudaStreamCreateWithFlags(&b->cap_st, cudaStreamNonBlocking), "stream");
             cudaGraph_t graph = nullptr;
             CK(cudaStreamBeginCapture(b->cap_st, cudaStreamCaptureModeThreadLocal), "graph capture");
             cudaError_t le = launch_window(b->opts.precision, b->d_desc, b->n, b->total_items, b->wctl, b->perms,
                                            b->act, b->act_count, b->occ, b->recs, b->counts, b->tracer,
-                                           b->stats, b->status, b->cap, b->run_blocks, b->cap_st);
+                                           b->stats, b->status, b->cap, b->run_blocks,
+                                           b->site_on ? &sargs : nullptr, b->cap_st);
             cudaError_t ce = cudaStreamEndCapture(b->cap_st, &graph);
             if (le != cudaSuccess) return cuda_fail(le, "window capture");
             if (ce != cudaSuccess) return cuda_fail(ce, "window capture");
@@ -602,7 +835,8 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
             stats->handoffs += b->stats_host[2 * r + 1] - before[2 * r + 1];
         }
         stats->windows = windows;
-        stats->launches = (windows > 0 ? b->rclass.size() : 0) + (b->any_global ? 17 * windows : 0);
+        stats->launches =
+            (windows > 0 ? b->rclass.size() : 0) + (b->any_global ? 17 * windows : 0) + extra_launches;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, b->ev0, b->ev1);
         stats->gpu_ms = ms;
@@ -737,6 +971,7 @@ int kmc_write_state(kmc_batch* b, int32_t r, const uint8_t* host_occ, size_t n)
     CK(cudaStreamSynchronize(b->st), "synchronize");
     b->n_vac[r] = nv;
     b->n_H[r] = nh;
+    b->field_valid = false;
     if (b->rates_set) {
         int rc = plan_residency(b);
         if (rc) return rc;
@@ -839,6 +1074,149 @@ int kmc_upload_state(kmc_batch* b, const void* host, size_t bytes)
     CK(cudaMemcpyAsync(b->recs, h + a, c, cudaMemcpyHostToDevice, b->st), "state upload");
     CK(cudaMemcpyAsync(b->counts, h + a + c, sizeof(int32_t) * b->nfrag_total, cudaMemcpyHostToDevice, b->st),
        "state upload");
+    CK(cudaStreamSynchronize(b->st), "synchronize");
+    b->field_valid = false;
+    return FKMC_OK;
+}
+
+int kmc_set_site_energy(kmc_batch* b, const kmc_site_energy* e)
+{
+    if (!b) return fail(FKMC_EINVAL, "null batch");
+    if (!e || (e->n_vv == 0 && e->n_fe == 0)) {
+        if (b->site_on) {
+            b->site_on = false;
+            drop_window_graph(b);
+            CK(run_pass_blocks(b->opts.precision, b->cap, false, &b->run_blocks), "occupancy query");
+            if (b->rates_set) {
+                int rc = plan_residency(b);
+                if (rc) return rc;
+                rc = upload_desc(b);
+                if (rc) return rc;
+            }
+        }
+        return FKMC_OK;
+    }
+    if (b->opts.precision != FKMC_PLAIN) return fail(FKMC_EINVAL, "site energies need the plain form");
+    ShellTables sh;
+    int rc0 = make_shells(e, &sh);
+    if (rc0) return rc0;
+    const int reach_all = sh.reach_all, reach_vv = sh.reach_vv;
+    const std::vector<SiteOff>& vv = sh.vv;
+    const std::vector<SiteOff>& bo = sh.bo;
+    for (int r = 0; r < b->n; ++r)
+        for (int d = 0; d < 3; ++d) {
+            const RepDesc& D = b->desc[r];
+            if (D.L[d] < 2 * reach_all + 1)
+                return fail(FKMC_EINVAL, "a dimension is shorter than twice the interaction reach plus one cell");
+            if (D.nf[d] > 1 && D.base[d] < 2 + reach_vv)
+                return fail(FKMC_EINVAL, "fragment edges must be at least 2 + the V-V reach (cells)");
+        }
+    const int32_t eself = sh.e_self;
+
+    if (!b->field) b->field = (int32_t*)b->dalloc(sizeof(int32_t) * b->nsite_total);
+    if (!b->d_vv) b->d_vv = (SiteOff*)b->dalloc(sizeof(SiteOff) * 3 * SITE_MAX_VV);
+    if (!b->d_bo) b->d_bo = (SiteOff*)b->dalloc(sizeof(SiteOff) * SITE_MAX_BO);
+    if (!b->fe) {
+        b->fe = (uint8_t*)b->dalloc((size_t)b->ncell_total);
+        if (b->fe) CK(cudaMemsetAsync(b->fe, 0, (size_t)b->ncell_total, b->st), "memset");
+    }
+    if (!b->field || !b->d_vv || !b->d_bo || !b->fe) return fail(FKMC_ENOMEM, "device allocation failed");
+    b->n_vv = sh.nvv;
+    b->n_bo = (int)bo.size();
+    b->e_self = eself;
+    b->e_bound = sh.bound;
+    CK(cudaMemcpyAsync(b->d_vv, vv.data(), sizeof(SiteOff) * vv.size(), cudaMemcpyHostToDevice, b->st),
+       "table upload");
+    if (!bo.empty())
+        CK(cudaMemcpyAsync(b->d_bo, bo.data(), sizeof(SiteOff) * bo.size(), cudaMemcpyHostToDevice, b->st),
+           "table upload");
+    b->site_on = true;
+    b->field_valid = false;
+    drop_window_graph(b);
+    CK(run_pass_blocks(FKMC_PLAIN, b->cap, true, &b->run_blocks), "occupancy query");
+    if (b->rates_set) {
+        int rc = build_btab(b);
+        if (rc) return rc;
+        rc = plan_residency(b);
+        if (rc) return rc;
+        rc = upload_desc(b);
+        if (rc) return rc;
+    }
+    CK(cudaStreamSynchronize(b->st), "synchronize");
+    return FKMC_OK;
+}
+
+int kmc_site_shells(const kmc_site_energy* e, int32_t t, int32_t* rows, int32_t max_rows, int32_t* n_rows)
+{
+    if (!e || t < 0 || t > 2 || (!rows && max_rows > 0)) return fail(FKMC_EINVAL, "bad argument");
+    ShellTables sh;
+    int rc = make_shells(e, &sh);
+    if (rc) return rc;
+    int k = 0;
+    auto put = [&](const SiteOff& o) {
+        if (k < max_rows) {
+            int32_t* w = rows + 5 * k;
+            w[0] = o.t2;
+            for (int a = 0; a < 3; ++a) w[1 + a] = o.dc[a];
+            w[4] = o.e;
+        }
+        ++k;
+    };
+    for (int i = 0; i < sh.nvv; ++i) put(sh.vv[(size_t)t * SITE_MAX_VV + i]);
+    for (const SiteOff& o : sh.ob[t]) put(o);
+    if (n_rows) *n_rows = k;
+    return FKMC_OK;
+}
+
+int kmc_read_dopants(kmc_batch* b, int32_t r, uint8_t* host_cells, size_t n)
+{
+    if (!valid_replica(b, r) || !host_cells) return fail(FKMC_EINVAL, "bad replica or output");
+    const RepDesc& D = b->desc[r];
+    if ((int64_t)n != D.nsite / 3) return fail(FKMC_EINVAL, "n must equal nx ny nz");
+    if (!b->fe) {
+        std::memset(host_cells, 0, n);
+        return FKMC_OK;
+    }
+    CK(cudaMemcpyAsync(host_cells, b->fe + D.site_off / 3, n, cudaMemcpyDeviceToHost, b->st), "dopant copy");
+    CK(cudaStreamSynchronize(b->st), "synchronize");
+    return FKMC_OK;
+}
+
+int kmc_write_dopants(kmc_batch* b, int32_t r, const uint8_t* host_cells, size_t n)
+{
+    if (!valid_replica(b, r) || !host_cells) return fail(FKMC_EINVAL, "bad replica or input");
+    const RepDesc& D = b->desc[r];
+    if ((int64_t)n != D.nsite / 3) return fail(FKMC_EINVAL, "n must equal nx ny nz");
+    if (!b->fe) {
+        b->fe = (uint8_t*)b->dalloc((size_t)b->ncell_total);
+        if (!b->fe) return fail(FKMC_ENOMEM, "device allocation failed");
+        CK(cudaMemsetAsync(b->fe, 0, (size_t)b->ncell_total, b->st), "memset");
+    }
+    std::vector<uint8_t> h(n);
+    int64_t cnt = 0;
+    for (size_t c = 0; c < n; ++c) {
+        h[c] = host_cells[c] ? 1 : 0;
+        cnt += h[c];
+    }
+    CK(cudaMemcpyAsync(b->fe + D.site_off / 3, h.data(), n, cudaMemcpyHostToDevice, b->st), "dopant upload");
+    CK(cudaStreamSynchronize(b->st), "synchronize");
+    b->n_fe[r] = cnt;
+    b->field_valid = false;
+    return FKMC_OK;
+}
+
+int kmc_read_site_field(kmc_batch* b, int32_t r, int32_t* host_field, size_t n)
+{
+    if (!valid_replica(b, r) || !host_field) return fail(FKMC_EINVAL, "bad replica or output");
+    if (!b->site_on) return fail(FKMC_ESTATE, "site energies are off");
+    const RepDesc& D = b->desc[r];
+    if ((int64_t)n != D.nsite) return fail(FKMC_EINVAL, "n must equal 3 nx ny nz");
+    if (!b->field_valid) {
+        int rc = rebuild_field(b);
+        if (rc) return rc;
+    }
+    CK(cudaMemcpyAsync(host_field, b->field + D.site_off, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, b->st),
+       "field copy");
     CK(cudaStreamSynchronize(b->st), "synchronize");
     return FKMC_OK;
 }

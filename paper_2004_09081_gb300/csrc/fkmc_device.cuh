@@ -13,8 +13,8 @@
 namespace fkmc {
 
 constexpr int SP_O = 0, SP_H = 1, SP_V = 2;
-constexpr uint32_t PURPOSE_INIT = 1u, PURPOSE_PERM = 2u, PURPOSE_HOP = 3u;
-constexpr uint32_t STATUS_OVERFLOW = 1u, STATUS_TIMEOUT = 2u, STATUS_EVENT_LIMIT = 4u;
+constexpr uint32_t PURPOSE_INIT = 1u, PURPOSE_PERM = 2u, PURPOSE_HOP = 3u, PURPOSE_DOPE = 5u;
+constexpr uint32_t STATUS_OVERFLOW = 1u, STATUS_TIMEOUT = 2u, STATUS_EVENT_LIMIT = 4u, STATUS_ENERGY_RANGE = 8u;
 // Hard bound on the events one fragment may execute in one colour phase
 // (about 2.5e5 x the expected count at n_tau <= 64); reaching it ends the
 // phase and reports an error instead of running on.
@@ -53,6 +53,32 @@ struct RepDesc {
     double two_pow_F;      // 2^F, exact
     int32_t resident;      // 1: this replica runs in the replica-resident kernel
     int32_t pad_;
+    int64_t btab_off;      // site energies: first Boltzmann-table entry of this replica
+    int32_t bhi_mid;       // index of the high-table entry for m1 = 0
+    int32_t bhi_len;       // entries of the high table
+};
+
+// ---------------------------------------------------------------- site energies
+// Interaction shells of the dopant/defect section of the paper: an O site's
+// energy is a sum of pair energies (integers in units of 1e-4 eV) over the
+// vacancies and dopants at the listed squared distances.  SiteOff is one
+// partner position: site type t2 in the cell offset dc, energy e.
+struct SiteOff {
+    int8_t t2;
+    int8_t dc[3];
+    int32_t e;
+};
+constexpr int SITE_MAX_VV = 256;  // O partners of one O site inside the V-V shells
+constexpr int SITE_MAX_BO = 512;  // O sites inside the V-dopant shells of one B site
+constexpr int BOLTZ_LO = 512;     // Boltzmann factor of m units = hi[m >> 9] * lo[m & 511]
+
+// Kernel arguments of the site-energy path (fixed for a batch).
+struct SiteArgs {
+    const SiteOff* vv;    // [3][SITE_MAX_VV] offsets by site type of the centre
+    const double* btab;   // per replica: lo[BOLTZ_LO] then hi[bhi_len]
+    int32_t* field;       // E_site of every O site (batch-wide site index)
+    int32_t n_vv;         // offsets per site type
+    int32_t e_self;       // energy of the a/sqrt2 shell: a hop partner's share of its target
 };
 
 // ---------------------------------------------------------------- Philox

@@ -8,6 +8,8 @@
 //                Eq. AtomP).  One warp per fragment.
 //   k_moments_*  exact integer displacement moments (Sec. III: D from tracked
 //                trajectories).
+//   k_field_*    site energies of the dopant/defect section: the energy field
+//                E_site of every O site, scattered from vacancies and dopants.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -110,7 +112,10 @@ struct WarpSmem {
     uint16_t* order; // [cap] slot m -> index into rec
     int8_t* types;   // [8*cap] rate type of event e, -1 = no event
     uint8_t* alive;  // [cap]
+    double* rate;    // [8*cap] FP64 rate of event e (site-energy path only)
 };
+
+__host__ __device__ inline size_t warp_rate_offset(int cap) { return (size_t)((35 * cap + 7) / 8) * 8; }
 
 __device__ __forceinline__ WarpSmem carve(unsigned char* base, int cap)
 {
@@ -119,10 +124,15 @@ __device__ __forceinline__ WarpSmem carve(unsigned char* base, int cap)
     s.order = reinterpret_cast<uint16_t*>(base + 24 * cap);
     s.types = reinterpret_cast<int8_t*>(base + 26 * cap);
     s.alive = reinterpret_cast<uint8_t*>(base + 34 * cap);
+    s.rate = reinterpret_cast<double*>(base + warp_rate_offset(cap));
     return s;
 }
 
-__host__ __device__ inline size_t warp_smem_bytes(int cap) { return (size_t)((35 * cap + 15) / 16) * 16; }
+__host__ __device__ inline size_t warp_smem_bytes(int cap, bool site)
+{
+    const size_t b = site ? warp_rate_offset(cap) + 64 * (size_t)cap : 35 * (size_t)cap;
+    return (b + 15) / 16 * 16;
+}
 
 // Rate types of every event of the fragment, read from the occupancy words
 // in L2 (ld.global.cg, so that this warp's own exchanges are seen).
@@ -145,6 +155,76 @@ __device__ __forceinline__ void compute_types(const RepDesc& D, const uint32_t* 
             ty = code == SP_V ? -1 : code * 3 + nb.d[2] + 1;
         }
         S.types[e] = (int8_t)ty;
+    }
+}
+
+__device__ __forceinline__ int64_t site_lin(const RepDesc& D, int t, int x, int y, int z)
+{
+    return (((int64_t)t * D.L[2] + z) * D.L[1] + y) * D.L[0] + x;
+}
+
+// Site-energy path: rate type and FP64 rate of every event.  The barrier of
+// the hop s -> j is Ea + dU/2 + (E_site(j) - E_site(s))/2, E_site(j) without the
+// hopping vacancy itself (which sits in j's a/sqrt2 shell); the energy
+// difference m (1e-4 eV units) enters as k_table * hi[m >> 9] * lo[m & 511],
+// two FP64 products in that order.  Field words are read from L2 (ld.cg):
+// other warps of the phase update them with atomics.
+__device__ __forceinline__ void compute_rates_site(const RepDesc& D, const uint32_t* occ, const SiteArgs& sa,
+                                                   const WarpSmem& S, int nslots, int nch, int lane,
+                                                   uint32_t* status)
+{
+    const double* lo = sa.btab + D.btab_off;
+    const double* hi = lo + BOLTZ_LO;
+    const int32_t* field = sa.field + D.site_off;
+    for (int c = 0; c < nch; ++c) {
+        const int e = c * 32 + lane;
+        const int m = e >> 3, n = e & 7;
+        int ty = -1;
+        double k = 0.0;
+        if (m < nslots && S.alive[m]) {
+            int t, x, y, z;
+            split_key(S.rec[S.order[m]].key, t, x, y, z);
+            const NbEntry nb = c_nb[t][n];
+            const int jx = wrapc(x + nb.dc[0], D.L[0]);
+            const int jy = wrapc(y + nb.dc[1], D.L[1]);
+            const int jz = wrapc(z + nb.dc[2], D.L[2]);
+            const uint32_t w = __ldcg(occ + occ_word(D, nb.t2, jx, jy, jz));
+            const int code = (int)((w >> occ_shift(jx)) & 3u);
+            if (code != SP_V) {
+                ty = code * 3 + nb.d[2] + 1;
+                const int32_t Es = __ldcg(field + site_lin(D, t, x, y, z));
+                const int32_t Ej = __ldcg(field + site_lin(D, nb.t2, jx, jy, jz));
+                const int32_t dm = Ej - sa.e_self - Es;
+                const int hidx = D.bhi_mid + (dm >> 9);
+                if (hidx >= 0 && hidx < D.bhi_len) {
+                    k = __dmul_rn(__dmul_rn(D.k64[ty], __ldg(hi + hidx)), __ldg(lo + (dm & 511)));
+                } else {  // outside the bound the tables were built for: report, no event
+                    atomicOr(status, STATUS_ENERGY_RANGE);
+                    ty = -1;
+                }
+            }
+        }
+        S.types[e] = (int8_t)ty;
+        S.rate[e] = k;
+    }
+}
+
+// Move the hopping vacancy's share of the energy field from s to j: every O
+// site in a V-V shell of s loses the shell energy, every one around j gains it.
+// Integer atomics: fragments of one colour may touch the same field word.
+__device__ __forceinline__ void move_field(const RepDesc& D, const SiteArgs& sa, int t, int x, int y, int z, int t2,
+                                           int jx, int jy, int jz, int lane)
+{
+    int32_t* field = sa.field + D.site_off;
+    for (int o = lane; o < sa.n_vv; o += 32) {
+        const SiteOff a = sa.vv[t * SITE_MAX_VV + o];
+        atomicAdd(field + site_lin(D, a.t2, wrapc(x + a.dc[0], D.L[0]), wrapc(y + a.dc[1], D.L[1]),
+                                   wrapc(z + a.dc[2], D.L[2])),
+                  -a.e);
+        const SiteOff b = sa.vv[t2 * SITE_MAX_VV + o];
+        atomicAdd(field + site_lin(D, b.t2, wrapc(jx + b.dc[0], D.L[0]), wrapc(jy + b.dc[1], D.L[1]),
+                                   wrapc(jz + b.dc[2], D.L[2])),
+                  b.e);
     }
 }
 
@@ -233,13 +313,14 @@ __global__ void __launch_bounds__(256) k_screen(const RepDesc* __restrict__ desc
 
 // Run pass of a colour phase: one warp per screened fragment (grid-stride):
 // BKL on the fragment's vacancies until the next event would pass the window.
-template <int PREC>
+template <int PREC, bool SITE>
 __global__ void __launch_bounds__(128, 8) k_run(const RepDesc* __restrict__ descs, const ActEntry* __restrict__ act,
                                              const int32_t* __restrict__ act_count, int phase,
                                              const unsigned long long* wctl, uint32_t* occ, VacRec* recs,
                                              int32_t* counts, int32_t* tracer, unsigned long long* stats,
-                                             uint32_t* status, int cap)
+                                             uint32_t* status, int cap, SiteArgs sa)
 {
+    static_assert(!SITE || PREC == 0, "site energies use the plain form");
     using A = Arith<PREC>;
     using V = typename A::V;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -269,7 +350,7 @@ __global__ void __launch_bounds__(128, 8) k_run(const RepDesc* __restrict__ desc
         if (lane == 0) atomicOr(status, STATUS_OVERFLOW);
         nv = cap;
     }
-    WarpSmem S = carve(smem + warp_smem_bytes(cap) * wib, cap);
+    WarpSmem S = carve(smem + warp_smem_bytes(cap, SITE) * wib, cap);
 
     // slots: the fragment's records in ascending site order
     for (int k = lane; k < nv; k += 32) S.rec[k] = recs[g * cap + k];
@@ -284,8 +365,14 @@ __global__ void __launch_bounds__(128, 8) k_run(const RepDesc* __restrict__ desc
     __syncwarp();
     const int nslots = nv;
     const int nch = (nslots + 3) >> 2;  // 32 events per chunk
-    compute_types(D, occ, S, nslots, nch, lane);
+    if constexpr (SITE) compute_rates_site(D, occ, sa, S, nslots, nch, lane, status);
+    else compute_types(D, occ, S, nslots, nch, lane);
     __syncwarp();
+    // rate of event index e (lane-local chunk element)
+    auto rate_of = [&](int e) -> V {
+        if constexpr (SITE) return (V)S.rate[e];
+        else return A::rate(D, S.types[e]);
+    };
 
     const uint64_t hop_k1 = key_word(D.replica, PURPOSE_HOP);
     // draws for events [64*batch, 64*batch+64): lane l holds Philox block 32*batch + l
@@ -302,7 +389,7 @@ __global__ void __launch_bounds__(128, 8) k_run(const RepDesc* __restrict__ desc
         V carry = A::zero();
         V Plast = A::zero();
         for (int c = 0; c < nch; ++c) {
-            const V v = A::rate(D, S.types[c * 32 + lane]);
+            const V v = rate_of(c * 32 + lane);
             const V p = A::add(carry, warp_scan<PREC>(v, lane));
             carry = A::shfl(p, 31);
             Plast = p;
@@ -356,7 +443,7 @@ __global__ void __launch_bounds__(128, 8) k_run(const RepDesc* __restrict__ desc
             double cc = 0.0;
             for (int c = 0; c < nch; ++c) {
                 double p;
-                const double v = Arith<0>::rate(D, S.types[c * 32 + lane]);
+                const double v = (double)rate_of(c * 32 + lane);
                 if (nch == 1) {
                     p = (double)Plast;
                 } else {
@@ -371,8 +458,7 @@ __global__ void __launch_bounds__(128, 8) k_run(const RepDesc* __restrict__ desc
             }
             if (e_sel < 0) {  // rounding left no prefix above the target: last nonzero event
                 for (int c = nch - 1; c >= 0 && e_sel < 0; --c) {
-                    const unsigned bal =
-                        __ballot_sync(0xffffffffu, Arith<0>::rate(D, S.types[c * 32 + lane]) > 0.0);
+                    const unsigned bal = __ballot_sync(0xffffffffu, (double)rate_of(c * 32 + lane) > 0.0);
                     if (bal) e_sel = c * 32 + 31 - __clz(bal);
                 }
             }
@@ -385,7 +471,7 @@ __global__ void __launch_bounds__(128, 8) k_run(const RepDesc* __restrict__ desc
             const unsigned long long target = __umul64hi(xs, Sq);
             unsigned long long cc = 0ull;
             for (int c = 0; c < nch; ++c) {
-                const unsigned long long v = Arith<1>::rate(D, S.types[c * 32 + lane]);
+                const unsigned long long v = (unsigned long long)rate_of(c * 32 + lane);
                 unsigned long long p;
                 if (nch == 1) {
                     p = (unsigned long long)Plast;
@@ -401,6 +487,15 @@ __global__ void __launch_bounds__(128, 8) k_run(const RepDesc* __restrict__ desc
             }
         }
 
+        if constexpr (SITE) {
+            // every lane moves part of the hopping vacancy's energy share
+            int t, x, y, z;
+            split_key(S.rec[S.order[e_sel >> 3]].key, t, x, y, z);
+            const NbEntry nb = c_nb[t][e_sel & 7];
+            move_field(D, sa, t, x, y, z, nb.t2, wrapc(x + nb.dc[0], D.L[0]), wrapc(y + nb.dc[1], D.L[1]),
+                       wrapc(z + nb.dc[2], D.L[2]), lane);
+            __syncwarp();  // every lane has read the record before lane 0 rewrites it
+        }
         // apply the exchange (lane 0 writes; the rest of the warp waits)
         if (lane == 0) {
             const int m = e_sel >> 3, n = e_sel & 7;
@@ -443,10 +538,12 @@ __global__ void __launch_bounds__(128, 8) k_run(const RepDesc* __restrict__ desc
             }
             __threadfence_block();
         }
+        if constexpr (SITE) __threadfence_block();  // field atomics before the rate reads
         __syncwarp();
         clock = __dadd_rn(clock, dclock);
         ++i;
-        compute_types(D, occ, S, nslots, nch, lane);
+        if constexpr (SITE) compute_rates_site(D, occ, sa, S, nslots, nch, lane, status);
+        else compute_types(D, occ, S, nslots, nch, lane);
         __syncwarp();
     }
 
@@ -465,6 +562,89 @@ __global__ void __launch_bounds__(128, 8) k_run(const RepDesc* __restrict__ desc
         if (nhand) atomicAdd(stats + 2 * lo + 1, (unsigned long long)nhand);
     }
     __syncwarp();  // the warp's shared memory is reused by its next fragment
+    }
+}
+
+// ------------------------------------------------------------------ site energies
+// Dopant placement: cells f(0..n_fe-1) of a keyed Feistel bijection of the
+// cell indices (the vacancy placement's construction, its own key).
+__global__ void k_init_dopants(RepDesc D, int b_bits, int64_t n_fe, uint8_t* fe)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_fe) return;
+    const uint64_t ncell = (uint64_t)D.L[0] * D.L[1] * D.L[2];
+    const uint64_t mask = (1ull << b_bits) - 1ull;
+    const uint64_t k0 = D.seed, k1 = key_word(D.replica, PURPOSE_DOPE);
+    uint64_t v = (uint64_t)i;
+    do {
+        uint64_t Lh = v >> b_bits, Rh = v & mask;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const U64x4 o = philox4x64(Rh, (uint64_t)k, 0, 0, k0, k1);
+            const uint64_t nr = Lh ^ (o.x[0] & mask);
+            Lh = Rh;
+            Rh = nr;
+        }
+        v = (Lh << b_bits) | Rh;
+    } while (v >= ncell);
+    fe[D.site_off / 3 + (int64_t)v] = 1;
+}
+
+__device__ __forceinline__ int replica_of(const RepDesc* descs, int nrep, int64_t v, bool by_cell)
+{
+    int lo = 0, hi = nrep - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int64_t start = by_cell ? descs[mid].site_off / 3 : descs[mid].frag_base;
+        if (start <= v) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Energy field from the vacancies: each record adds its shell energies to the
+// O sites around it (the field starts at zero).
+__global__ void k_field_vac(const RepDesc* __restrict__ descs, int nrep, const VacRec* recs,
+                            const int32_t* counts, int64_t nfrag_total, int cap, SiteArgs sa)
+{
+    const int64_t total = nfrag_total * cap;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = k / cap;
+        const int slot = (int)(k % cap);
+        if (slot >= counts[g]) continue;
+        const RepDesc& D = descs[replica_of(descs, nrep, g, false)];
+        int t, x, y, z;
+        split_key(recs[g * cap + slot].key, t, x, y, z);
+        int32_t* field = sa.field + D.site_off;
+        for (int o = 0; o < sa.n_vv; ++o) {
+            const SiteOff a = sa.vv[t * SITE_MAX_VV + o];
+            atomicAdd(field + site_lin(D, a.t2, wrapc(x + a.dc[0], D.L[0]), wrapc(y + a.dc[1], D.L[1]),
+                                       wrapc(z + a.dc[2], D.L[2])),
+                      a.e);
+        }
+    }
+}
+
+// Energy field from the dopants: each doped B site adds its shell energies to
+// the O sites around it.
+__global__ void k_field_dopant(const RepDesc* __restrict__ descs, int nrep, const uint8_t* fe, int64_t ncell_total,
+                               const SiteOff* bo, int n_bo, int32_t* field_all)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell_total;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if (!fe[c]) continue;
+        const RepDesc& D = descs[replica_of(descs, nrep, c, true)];
+        const int64_t local = c - D.site_off / 3;
+        const int x = (int)(local % D.L[0]);
+        const int y = (int)((local / D.L[0]) % D.L[1]);
+        const int z = (int)(local / ((int64_t)D.L[0] * D.L[1]));
+        int32_t* field = field_all + D.site_off;
+        for (int o = 0; o < n_bo; ++o) {
+            const SiteOff a = bo[o];
+            atomicAdd(field + site_lin(D, a.t2, wrapc(x + a.dc[0], D.L[0]), wrapc(y + a.dc[1], D.L[1]),
+                                       wrapc(z + a.dc[2], D.L[2])),
+                      a.e);
+        }
     }
 }
 
@@ -597,26 +777,32 @@ cudaError_t launch_init(const RepDesc& D, int b_bits, int64_t n_vac, int64_t n_t
     return cudaGetLastError();
 }
 
-size_t phase_smem_bytes(int cap) { return warp_smem_bytes(cap) * 4; }
+size_t phase_smem_bytes(int cap, bool site) { return warp_smem_bytes(cap, site) * 4; }
 
 cudaError_t phase_prepare(int cap)
 {
-    const int bytes = (int)phase_smem_bytes(cap);
-    cudaError_t e = cudaFuncSetAttribute(k_run<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_run<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    const int bytes = (int)phase_smem_bytes(cap, false);
+    cudaError_t e = cudaFuncSetAttribute(k_run<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_run<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_run<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)phase_smem_bytes(cap, true));
+    return e;
 }
 
 // Blocks of the run pass: as many as fit on the GPU at once (it strides over
 // the screened fragments).
-cudaError_t run_pass_blocks(int prec, int cap, int* blocks)
+cudaError_t run_pass_blocks(int prec, int cap, bool site, int* blocks)
 {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = prec == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_run<0>, 128, phase_smem_bytes(cap))
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_run<1>, 128, phase_smem_bytes(cap));
+    if (e == cudaSuccess) {
+        const size_t smem = phase_smem_bytes(cap, site);
+        if (site) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_run<0, true>, 128, smem);
+        else if (prec == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_run<0, false>, 128, smem);
+        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_run<1, false>, 128, smem);
+    }
     *blocks = std::max(1, sms * std::max(per_sm, 1));
     return e;
 }
@@ -624,27 +810,66 @@ cudaError_t run_pass_blocks(int prec, int cap, int* blocks)
 // One window of the colour-phase path: set-up, then screen and run for each of
 // the 8 phases.  Every argument is fixed for the batch (the window offset is
 // read from wctl on the device), so the sequence can be captured in a graph.
+// `site` non-null selects the site-energy run pass (plain form).
 cudaError_t launch_window(int prec, const RepDesc* d_descs, int nrep, int64_t total_items,
                           unsigned long long* wctl, uint32_t* perms, ActEntry* act, int32_t* act_count,
                           uint32_t* occ, VacRec* recs, int32_t* counts, int32_t* tracer,
-                          unsigned long long* stats, uint32_t* status, int cap, int run_blocks, cudaStream_t st)
+                          unsigned long long* stats, uint32_t* status, int cap, int run_blocks,
+                          const SiteArgs* site, cudaStream_t st)
 {
     if (total_items <= 0) return cudaSuccess;
     k_window_setup<<<(nrep + 255) / 256, 256, 0, st>>>(d_descs, nrep, wctl, perms, act_count);
     const int64_t sblocks = (total_items + 255) / 256;
-    const size_t smem = phase_smem_bytes(cap);
+    const size_t smem = phase_smem_bytes(cap, site != nullptr);
+    const SiteArgs none{};
     for (int p = 0; p < 8; ++p) {
-        if (prec == 0) {
+        if (site) {
             k_screen<0><<<(unsigned)sblocks, 256, 0, st>>>(d_descs, nrep, total_items, p, wctl, perms, counts, act,
                                                            act_count);
-            k_run<0><<<run_blocks, 128, smem, st>>>(d_descs, act, act_count, p, wctl, occ, recs, counts, tracer,
-                                                    stats, status, cap);
+            k_run<0, true><<<run_blocks, 128, smem, st>>>(d_descs, act, act_count, p, wctl, occ, recs, counts,
+                                                          tracer, stats, status, cap, *site);
+        } else if (prec == 0) {
+            k_screen<0><<<(unsigned)sblocks, 256, 0, st>>>(d_descs, nrep, total_items, p, wctl, perms, counts, act,
+                                                           act_count);
+            k_run<0, false><<<run_blocks, 128, smem, st>>>(d_descs, act, act_count, p, wctl, occ, recs, counts,
+                                                           tracer, stats, status, cap, none);
         } else {
             k_screen<1><<<(unsigned)sblocks, 256, 0, st>>>(d_descs, nrep, total_items, p, wctl, perms, counts, act,
                                                            act_count);
-            k_run<1><<<run_blocks, 128, smem, st>>>(d_descs, act, act_count, p, wctl, occ, recs, counts, tracer,
-                                                    stats, status, cap);
+            k_run<1, false><<<run_blocks, 128, smem, st>>>(d_descs, act, act_count, p, wctl, occ, recs, counts,
+                                                           tracer, stats, status, cap, none);
         }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_dopants(const RepDesc& D, int b_bits, int64_t n_fe, uint8_t* fe, cudaStream_t st)
+{
+    if (n_fe <= 0) return cudaSuccess;
+    const int threads = 256;
+    k_init_dopants<<<(unsigned)((n_fe + threads - 1) / threads), threads, 0, st>>>(D, b_bits, n_fe, fe);
+    return cudaGetLastError();
+}
+
+// E_site of every O site of the batch from scratch: zero, then the vacancies'
+// and the dopants' shell energies scattered with integer atomics.
+cudaError_t launch_site_field(const RepDesc* d_descs, int nrep, const VacRec* recs, const int32_t* counts,
+                              int64_t nfrag_total, int cap, int64_t nsite_total, const uint8_t* fe,
+                              const SiteOff* bo, int n_bo, const SiteArgs& sa, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(sa.field, 0, sizeof(int32_t) * nsite_total, st);
+    if (e != cudaSuccess) return e;
+    const int threads = 256;
+    if (sa.n_vv > 0) {
+        const int64_t blocks = std::min<int64_t>(65536, (nfrag_total * cap + threads - 1) / threads);
+        k_field_vac<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, st>>>(d_descs, nrep, recs, counts,
+                                                                              nfrag_total, cap, sa);
+    }
+    if (fe && n_bo > 0) {
+        const int64_t ncell = nsite_total / 3;
+        const int64_t blocks = std::min<int64_t>(65536, (ncell + threads - 1) / threads);
+        k_field_dopant<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, st>>>(d_descs, nrep, fe, ncell, bo,
+                                                                                 n_bo, sa.field);
     }
     return cudaGetLastError();
 }

@@ -32,7 +32,15 @@ class kmc_cells(C.Structure):
 
 
 class kmc_composition(C.Structure):
-    _fields_ = [("n_vac", C.c_int64), ("n_H", C.c_int64)]
+    _fields_ = [("n_vac", C.c_int64), ("n_H", C.c_int64), ("n_Fe", C.c_int64)]
+
+
+FKMC_MAX_SHELLS = 8
+
+
+class kmc_site_energy(C.Structure):
+    _fields_ = [("n_vv", C.c_int32), ("vv_d2", C.c_int32 * FKMC_MAX_SHELLS), ("vv_eV", C.c_double * FKMC_MAX_SHELLS),
+                ("n_fe", C.c_int32), ("fe_d2", C.c_int32 * FKMC_MAX_SHELLS), ("fe_eV", C.c_double * FKMC_MAX_SHELLS)]
 
 
 class kmc_barrier_table(C.Structure):
@@ -88,6 +96,11 @@ _SIGNATURES = {
     "kmc_rate_table": (C.c_int, [_P, _D, _D, _D, _I32, _P, _P, _P, _P]),
     "kmc_neighbour_table": (None, [_P]),
     "kmc_vacancy_moments_noalloc": (C.c_int, [_P, _P, _P, _I32, _I32, _P, _P]),
+    "kmc_set_site_energy": (C.c_int, [_P, _P]),
+    "kmc_read_dopants": (C.c_int, [_P, _I32, _P, _SZ]),
+    "kmc_write_dopants": (C.c_int, [_P, _I32, _P, _SZ]),
+    "kmc_read_site_field": (C.c_int, [_P, _I32, _P, _SZ]),
+    "kmc_site_shells": (C.c_int, [_P, _I32, _P, _I32, _P]),
     "kmc_destroy": (C.c_int, [_P]),
     "kmc_last_error": (C.c_char_p, []),
 }
@@ -262,6 +275,55 @@ def kmc_vacancy_moments_noalloc(records_ptr: int, counts_ptr: int, fragment_offs
     return out[:n]
 
 
+def kmc_set_site_energy(h, vv=(), fe=()):
+    """vv, fe: sequences of (squared distance in (a/2)^2, energy in eV); both
+    empty turns the interactions off."""
+    if not vv and not fe:
+        _check(load().kmc_set_site_energy(h, None))
+        return
+    e = _site_energy_struct(vv, fe)
+    _check(load().kmc_set_site_energy(h, C.byref(e)))
+
+
+def _site_energy_struct(vv, fe) -> kmc_site_energy:
+    e = kmc_site_energy()
+    e.n_vv = len(vv)
+    e.n_fe = len(fe)
+    for k, (d2, en) in enumerate(vv):
+        e.vv_d2[k] = int(d2)
+        e.vv_eV[k] = float(en)
+    for k, (d2, en) in enumerate(fe):
+        e.fe_d2[k] = int(d2)
+        e.fe_eV[k] = float(en)
+    return e
+
+
+def kmc_site_shells(vv, fe, t: int) -> np.ndarray:
+    e = _site_energy_struct(vv, fe)
+    n = C.c_int32()
+    _check(load().kmc_site_shells(C.byref(e), int(t), None, 0, C.byref(n)))
+    out = np.zeros((max(n.value, 1), 5), np.int32)
+    _check(load().kmc_site_shells(C.byref(e), int(t), _ptr(out), n.value, C.byref(n)))
+    return out[: n.value]
+
+
+def kmc_read_dopants(h, r: int, ncell: int) -> np.ndarray:
+    out = np.zeros(ncell, np.uint8)
+    _check(load().kmc_read_dopants(h, r, _ptr(out), ncell))
+    return out
+
+
+def kmc_write_dopants(h, r: int, cells: np.ndarray):
+    cells = np.ascontiguousarray(cells, np.uint8)
+    _check(load().kmc_write_dopants(h, r, _ptr(cells), cells.size))
+
+
+def kmc_read_site_field(h, r: int, nsite: int) -> np.ndarray:
+    out = np.zeros(nsite, np.int32)
+    _check(load().kmc_read_site_field(h, r, _ptr(out), nsite))
+    return out
+
+
 def kmc_destroy(h):
     _check(load().kmc_destroy(h))
 
@@ -319,6 +381,7 @@ class Batch:
         o.free = self._alloc.c_free
         self._opts = o
         self.cells = [c if isinstance(c, kmc_cells) else kmc_cells(*c) for c in cells]
+        # (n_vac, n_H) or (n_vac, n_H, n_Fe)
         self.comps = [c if isinstance(c, kmc_composition) else kmc_composition(*c) for c in comps]
         self.h = kmc_create_batch(self.cells, self.comps, seed, o)
         self.n = len(self.cells)
@@ -371,3 +434,15 @@ class Batch:
 
     def info(self, r=0):
         return kmc_get_replica_info(self.h, r)
+
+    def set_site_energy(self, vv=(), fe=()):
+        kmc_set_site_energy(self.h, vv, fe)
+
+    def dopants(self, r=0):
+        return kmc_read_dopants(self.h, r, self.nsite(r) // 3)
+
+    def write_dopants(self, cells, r=0):
+        kmc_write_dopants(self.h, r, cells)
+
+    def site_field(self, r=0):
+        return kmc_read_site_field(self.h, r, self.nsite(r))

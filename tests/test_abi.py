@@ -68,3 +68,21 @@ def test_rate_table_rejects_bad_input(lib):
     with pytest.raises(lib.KmcError) as e:
         lib.kmc_rate_table(tab, -1.0, 0.0, 4.0, 64)
     assert e.value.code == lib.FKMC_EINVAL
+
+
+def test_site_shell_tables_match_oracle(lib):
+    """The library's interaction partners (built from displacement vectors)
+    equal the oracle's (built from a cell search), energies included."""
+    import oracle as orc
+    vv = [(2, 0.343), (4, 0.235), (6, 0.200), (8, 0.180), (10, 0.023), (16, 0.011)]
+    fe = [(1, -0.709), (5, -0.199), (9, -0.022), (13, 0.0005)]
+    ref = orc.Lattice((9, 9, 9), (1, 1, 1), 0, 0)
+    ref.set_site_energy(vv=vv, fe=fe)
+    for t in range(3):
+        got = sorted(map(tuple, lib.kmc_site_shells(vv, fe, t).tolist()))
+        want = sorted(map(tuple, ref.shells(t).tolist()))
+        assert got == want
+    with pytest.raises(lib.KmcError):
+        lib.kmc_site_shells([(3, 0.1)], [], 0)  # not an O-O distance
+    with pytest.raises(lib.KmcError):
+        lib.kmc_site_shells([(2, 0.1), (2, 0.2)], [], 0)  # listed twice
