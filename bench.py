@@ -444,12 +444,12 @@ def main():
                 if vv or fe:
                     bv.set_site_energy(vv, fe)
                 bv.run(2)
-                sv = bv.run(4 * W)
+                sv = bv.run(64 * W)  # long enough for the vacancies to meet the dopants
                 rates[nm] = sv.hops / (sv.gpu_ms / 1e3) if sv.gpu_ms > 0 else None
                 trend[nm] = [bv.D(r, fkmc.FKMC_V)[1] for r in range(nrep)]
                 bv.close()
             extra["site_energy"] = {
-                "T": [r.T for r in reps], "D_V": trend, "windows": 4 * W + 2,
+                "T": [r.T for r in reps], "D_V": trend, "windows": 64 * W + 2,
                 "hops_per_s": rates,
                 "note": "D_V (m^2/s) per temperature; the paper reports that the dopant term lowers D_V "
                         "strongly and the V-V term raises it again",

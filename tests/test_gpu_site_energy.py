@@ -108,7 +108,8 @@ def test_vv_only_and_fe_only(fk, orc):
 
 
 def test_batch_of_interacting_replicas(fk, orc):
-    cells = [(16, 16, 16), (12, 14, 10), (20, 16, 12)]
+    # sizes whose even fragment counts at edge 4 keep every edge >= 4 (the V-V reach rule)
+    cells = [(16, 16, 16), (8, 16, 24), (24, 8, 16)]
     comps = [(60, 0, 41), (30, 50, 20), (80, 0, 60)]
     T = [700.0, 850.0, 1000.0]
     b = fk.Batch([(*c, 4.01) for c in cells], comps, 13, edge=4, precision=fk.FKMC_PLAIN)
