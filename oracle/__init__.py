@@ -77,6 +77,9 @@ def lib():
             "orc_site_shells": (C.c_int, [P, C.c_int, P, C.c_int]),
             "orc_site_energy": (i64, [P, i64, i64]),
             "orc_event_rate": (d, [P, i64, C.c_int]),
+            "orc_null_pick": (u64, [u64, u64, u64, u32, u64]),
+            "orc_null_run": (C.c_int, [P, u64, i64]),
+            "orc_get_null": (None, [P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -122,6 +125,10 @@ def colour_perm(seed: int, replica: int, w: int) -> np.ndarray:
     out = np.zeros(8, np.int32)
     lib().orc_colour_perm(seed, replica, w, _ptr(out))
     return out
+
+
+def null_pick(p: int, n: int, seed: int, replica: int, step: int) -> int:
+    return int(lib().orc_null_pick(p, n, seed, replica, step))
 
 
 def rate_table(Ea_O, Ea_H, A, q_O, q_H, T, Ez, a_ang, cap_v=64):
@@ -175,6 +182,20 @@ class Lattice:
 
     def event_rate(self, s: int, n: int) -> float:
         return float(lib().orc_event_rate(self._h, int(s), int(n)))
+
+    # ---------------------------------------------- null-event form (Sec. II.B)
+    def null_run(self, steps: int, n_frg: int):
+        """The atom-based fragment kMC with null events: `steps` steps of
+        `n_frg` simultaneous vacancy picks."""
+        if lib().orc_null_run(self._h, int(steps), int(n_frg)):
+            raise RuntimeError("rates not set, site energies on, or bad n_frg")
+
+    def null_clock(self):
+        th, t = C.c_double(0), C.c_double(0)
+        st = C.c_uint64(0)
+        F = C.c_int32(0)
+        lib().orc_get_null(self._h, C.byref(th), C.byref(t), C.byref(st), C.byref(F))
+        return {"theta": th.value, "t": t.value, "steps": st.value, "F": F.value}
 
     def dopants(self) -> np.ndarray:
         out = np.zeros(self.ncell, np.uint8)
@@ -255,7 +276,7 @@ class Lattice:
         per-axis D_x = <dx^2>/(2t) and the mean z displacement."""
         m = self.moments(species)
         if t is None:
-            t = self.counters()["window"] * self.params()["tau"]
+            t = self.counters()["window"] * self.params()["tau"] + self.null_clock()["t"]
         n = max(int(m[0]), 1)
         h = 0.5 * self.a_ang * 1e-10
         msd = m[4:7].astype(np.float64) / n * h * h

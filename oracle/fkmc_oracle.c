@@ -28,6 +28,8 @@
  *                                                    Sec. "Oxygen vacancy diffusion
  *                                                    with dopant and defect
  *                                                    interaction", Table add01
+ *   - the atom-based fragment kMC with null events    Sec. II.B, Eqs. (AtomP),
+ *     (vacancies as the atoms, N_frg picks per step)   (TimeStepFrg)
  * The spatial fragments, checkerboard colour phases, synchronisation windows
  * and hand-off of boundary hops are the synchronous-sublattice reading of the
  * fragment scheme; every step is written out in fkmc_phase() below.
@@ -52,6 +54,8 @@
 #define PURPOSE_HOP 3u
 #define PURPOSE_BKL 4u
 #define PURPOSE_DOPE 5u
+#define PURPOSE_PICK 6u
+#define PURPOSE_NULL 7u
 
 /* ------------------------------------------------------------------ */
 /* Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers:
@@ -255,6 +259,10 @@ typedef struct {
     int n_vv, n_fe; /* offsets to the O sites / B sites inside the energy shells */
     struct { int t2; int dc[3]; int32_t e; } vv[3][512];
     struct { int dc[3]; int32_t e; } feo[3][512];
+    /* atom-based fragment kMC with null events (Sec. II.B) */
+    uint64_t null_step;
+    double theta_null; /* its clock in units of 1/k32max */
+    int64_t* claimed;  /* per site: 1 + the step whose earlier pick claimed it */
     /* counters */
     uint64_t window;
     uint64_t hops;
@@ -409,6 +417,7 @@ void orc_destroy(orc_lattice* lat)
     free(lat->occ);
     free(lat->tdisp);
     free(lat->fe);
+    free(lat->claimed);
     free(lat);
 }
 
@@ -919,6 +928,174 @@ int orc_bkl_run(orc_lattice* lat, double t_end, uint64_t stream, double* t_out)
     *t_out = t;
     free(v); free(r);
     return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* The atom-based fragment kMC of Sec. II.B with null events, the atoms I
+ * being the vacancies (each with its 8 exchanges).  One step:
+ *  1. R_I = the sum of vacancy I's rates, R_tot = sum_I R_I and
+ *     R_max = max_I R_I (Eq. AtomP).  Rates are the mixed form's fixed point
+ *     with F_null = 63 - ceil(log2(8 N_V)), so every sum is an exact integer
+ *     below 2^63.
+ *  2. N_frg distinct vacancies are picked: the images of 0 .. N_frg-1 under
+ *     a keyed bijection of the vacancy ids (the Feistel construction of the
+ *     placement, its own key, the step number in the round counter).
+ *  3. Pick p draws x and takes the first of its vacancy's events whose
+ *     running sum exceeds mulhi(x, R_max) -- probability k_i / R_max -- or the
+ *     null event when R_I does not (probability 1 - R_I / R_max).
+ *  4. The paper leaves open how simultaneous picks are reconciled.  Reading:
+ *     a pick whose exchange shares a site with the exchange of a non-null
+ *     pick of smaller index becomes null, so the updated events are disjoint
+ *     and commute.
+ *  5. The exchanges are applied; N_updated is their number and the clock
+ *     moves by -ln(r') / R_tot * N_updated (Eq. TimeStepFrg).
+ * With N_frg = 1 this is the conventional kMC of Sec. II.A in distribution.
+ */
+/* ------------------------------------------------------------------ */
+int64_t orc_n_records(const orc_lattice* lat);
+
+static uint64_t null_pick(uint64_t p, uint64_t n, uint64_t seed, uint32_t replica, uint64_t step)
+{
+    int b = 1;
+    while (((uint64_t)1 << (2 * b)) < n) b++;
+    uint64_t mask = ((uint64_t)1 << b) - 1;
+    uint64_t key[2];
+    key_for(seed, replica, PURPOSE_PICK, key);
+    uint64_t v = p;
+    do {
+        uint64_t Lh = v >> b, Rh = v & mask;
+        for (int k = 0; k < 4; k++) {
+            uint64_t ctr[4] = {Rh, (uint64_t)k, step, 0}, o[4];
+            orc_philox4x64(ctr, key, o);
+            uint64_t nl = Rh, nr = Lh ^ (o[0] & mask);
+            Lh = nl; Rh = nr;
+        }
+        v = (Lh << b) | Rh;
+    } while (v >= n);
+    return v;
+}
+
+uint64_t orc_null_pick(uint64_t p, uint64_t n, uint64_t seed, uint32_t replica, uint64_t step)
+{
+    return null_pick(p, n, seed, replica, step);
+}
+
+/* fixed-point table of the null-event form for N_V vacancies */
+static int null_table(const orc_lattice* lat, int64_t nv, uint64_t q[6])
+{
+    float kmax = 0.0f;
+    for (int i = 0; i < 6; i++) if (lat->k32[i] > kmax) kmax = lat->k32[i];
+    int lg = 0;
+    while (((int64_t)1 << lg) < 8 * (nv > 0 ? nv : 1)) lg++;
+    int F = 63 - lg;
+    for (int i = 0; i < 6; i++) q[i] = (uint64_t)llrint(ldexp((double)lat->k32[i] / (double)kmax, F));
+    return F;
+}
+
+int orc_null_run(orc_lattice* lat, uint64_t steps, int64_t n_frg)
+{
+    if (!lat->rates_set || lat->site_on || n_frg < 1) return -1;
+    int64_t nv = orc_n_records(lat);
+    if (nv == 0) { lat->null_step += steps; return 0; }
+    orc_rec* v = (orc_rec*)malloc(sizeof(orc_rec) * nv);
+    for (int f = 0; f < lat->nfrag; f++)
+        for (int m = 0; m < lat->frag[f].n; m++) {
+            orc_rec r = lat->frag[f].r[m];
+            if ((int64_t)r.id >= nv) { free(v); return -1; }
+            v[r.id] = r; /* vacancy ids are 0 .. N_V-1 */
+        }
+    if (!lat->claimed) lat->claimed = (int64_t*)calloc((size_t)lat->nsite, sizeof(int64_t));
+    uint64_t q[6];
+    int F = null_table(lat, nv, q);
+    int64_t nf = n_frg < nv ? n_frg : nv;
+    uint64_t key[2];
+    key_for(lat->seed, lat->replica, PURPOSE_NULL, key);
+    int64_t* pv = (int64_t*)malloc(sizeof(int64_t) * nf);
+    int* pn = (int*)malloc(sizeof(int) * nf);
+    for (uint64_t k = 0; k < steps; k++) {
+        uint64_t step = lat->null_step;
+        /* 1. per-vacancy totals */
+        uint64_t Rtot = 0, Rmax = 0;
+        for (int64_t i = 0; i < nv; i++) {
+            uint64_t R = 0;
+            for (int n = 0; n < 8; n++) {
+                int ty = event_type(lat, v[i].site, n);
+                R += ty < 0 ? 0 : q[ty];
+            }
+            Rtot += R;
+            if (R > Rmax) Rmax = R;
+        }
+        /* 2-3. picks and their proposals, all from the state before the step */
+        for (int64_t p = 0; p < nf; p++) {
+            int64_t id = (int64_t)null_pick((uint64_t)p, (uint64_t)nv, lat->seed, lat->replica, step);
+            uint64_t ctr[4] = {step, (uint64_t)p, 0, 0}, y[4];
+            orc_philox4x64(ctr, key, y);
+            uint64_t target = mulhi64(y[0], Rmax);
+            uint64_t P = 0;
+            int sel = -1;
+            for (int n = 0; n < 8; n++) {
+                int ty = event_type(lat, v[id].site, n);
+                P += ty < 0 ? 0 : q[ty];
+                if (P > target) { sel = n; break; }
+            }
+            pv[p] = id;
+            pn[p] = sel;
+        }
+        /* 4. a non-null pick loses to any earlier non-null pick sharing a site */
+        for (int64_t p = 0; p < nf; p++) {
+            if (pn[p] < 0) continue;
+            int64_t s = v[pv[p]].site, j = neighbour_site(lat, s, pn[p]);
+            int clash = lat->claimed[s] == (int64_t)step + 1 || lat->claimed[j] == (int64_t)step + 1;
+            lat->claimed[s] = lat->claimed[j] = (int64_t)step + 1;
+            if (clash) pn[p] = -1;
+        }
+        /* 5. apply (disjoint, so in any order) and advance the clock */
+        uint64_t nupd = 0;
+        for (int64_t p = 0; p < nf; p++) {
+            if (pn[p] < 0) continue;
+            orc_rec* r = &v[pv[p]];
+            int t, c[3];
+            site_coords(lat, r->site, &t, c);
+            int64_t s = r->site, j = neighbour_site(lat, s, pn[p]);
+            int ion = lat->occ[j];
+            lat->occ[s] = (uint8_t)ion;
+            lat->occ[j] = SP_V;
+            for (int d = 0; d < 3; d++) r->d[d] += NB[t][pn[p]].d[d];
+            if (lat->tracer)
+                for (int d = 0; d < 3; d++) {
+                    lat->tdisp[3 * s + d] = lat->tdisp[3 * j + d] - NB[t][pn[p]].d[d];
+                    lat->tdisp[3 * j + d] = 0;
+                }
+            r->site = j;
+            nupd++;
+        }
+        if (Rtot > 0) {
+            uint64_t ct[4] = {step, ~(uint64_t)0, 0, 0}, y[4];
+            orc_philox4x64(ct, key, y);
+            double E = orc_neglog64(y[0]);
+            double dth = ldexp(E / (double)Rtot, F) * (double)nupd;
+            lat->theta_null = lat->theta_null + dth;
+        }
+        lat->hops += nupd;
+        lat->null_step++;
+    }
+    /* records back to the fragments owning their sites */
+    for (int f = 0; f < lat->nfrag; f++) lat->frag[f].n = 0;
+    for (int64_t i = 0; i < nv; i++) list_push(&lat->frag[fragment_of_site(lat, v[i].site)], v[i]);
+    free(v); free(pv); free(pn);
+    return 0;
+}
+
+/* clock of the null-event form: {theta (1/k32max units), t (s)}, steps and F_null */
+void orc_get_null(const orc_lattice* lat, double* theta, double* t_s, uint64_t* steps, int32_t* F)
+{
+    uint64_t q[6];
+    float kmax = 0.0f;
+    for (int i = 0; i < 6; i++) if (lat->k32[i] > kmax) kmax = lat->k32[i];
+    *theta = lat->theta_null;
+    *t_s = kmax > 0.0f ? lat->theta_null / (double)kmax : 0.0;
+    *steps = lat->null_step;
+    *F = null_table(lat, orc_n_records(lat), q);
 }
 
 /* ------------------------------------------------------------------ */
