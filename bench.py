@@ -46,10 +46,11 @@ def parse():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    p.add_argument("--workload", default="batched", choices=["batched", "sweep", "bulk", "um", "fe"],
+    p.add_argument("--workload", default="batched", choices=["batched", "sweep", "bulk", "um", "fe", "null"],
                    help="batched: 256 uneven replicas (the headline); sweep: SrTiO(3-x)H_x 32^3 at "
                         "300..700 K; bulk: BaTiO(3-x)H_x 128^3; um: BaTiO3 L^3 under bias; fe: Fe-doped "
-                        "SrTiO3 96^3 with vacancy-vacancy and vacancy-Fe site energies at 600..1000 K")
+                        "SrTiO3 96^3 with vacancy-vacancy and vacancy-Fe site energies at 600..1000 K; null: "
+                        "the bulk lattice with the paper's atom-based null-event kMC, one pick per vacancy")
     p.add_argument("--um-cells", type=int, default=2500, help="edge of the um-scale cube (cells)")
     p.add_argument("--no-autotune", action="store_true", help="use the workload's default edge")
     return p.parse_args()
@@ -153,6 +154,23 @@ def D_from_moments(m, t, a):
     """D = <|d|^2>/(6t) (m^2/s) from the integer moments of one replica."""
     h = 0.5 * a * 1e-10
     return (m[4] + m[5] + m[6]) / max(m[0], 1) * h * h / (6 * t)
+
+
+def cpu_oracle_null_rate(wl, seed, steps, budget_s):
+    """The oracle's null-event form on the workload's lattice, `steps` at a time,
+    until the budget is spent; returns (hops/s, hops, seconds)."""
+    import oracle
+    oracle.build()
+    rep = wl.replicas[0]
+    L = oracle.Lattice(rep.cells, rep.nfrag, rep.n_vac, rep.n_H, seed=seed)
+    L.set_rates(rep.Ea_O, rep.Ea_H, rep.T, a_ang=rep.a, precision=wl.precision)
+    secs = 0.0
+    while secs < budget_s:
+        t0 = time.perf_counter()
+        L.null_run(steps, wl.notes["n_frg"])
+        secs += time.perf_counter() - t0
+    hops = L.counters()["hops"]
+    return hops / secs, hops, secs
 
 
 def cpu_oracle_rate(wl, seed, windows, budget_s, replicas=None):
@@ -319,10 +337,13 @@ def main():
     seed = args.seed + rank  # each rank simulates its own independent batch (weak scaling)
     makers = {"batched": workloads.batched_batio3, "sweep": workloads.srtio3_h_sweep,
               "bulk": workloads.bulk_batio3, "um": lambda sd: workloads.um_batio3_bias(sd, args.um_cells),
-              "fe": workloads.fe_srtio3}
+              "fe": workloads.fe_srtio3, "null": workloads.null_batio3}
     wl = makers[args.workload](seed)
     nrep = len(wl.replicas)
-    default_windows = {"batched": 64, "sweep": 64, "bulk": 16, "um": 2, "fe": 32}
+    default_windows = {"batched": 64, "sweep": 64, "bulk": 16, "um": 2, "fe": 32, "null": 100}
+    null = args.workload == "null"
+    if null:
+        args.no_plain = True  # the null-event form has one (integer) arithmetic
     W = args.windows if args.windows else default_windows[args.workload]
     stream = torch.cuda.current_stream()
     reps = wl.replicas
@@ -344,7 +365,7 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def step():
-        s = b.run(W)
+        s = b.run_null(W, wl.notes["n_frg"]) if null else b.run(W)
         b.moments_all()
         return s
 
@@ -382,8 +403,15 @@ def main():
     value = hops_all / t_max
 
     peak, peak_kind = load_peaks()
-    all_resident = n_launch <= args.steps * 5  # class launches only, no per-phase launches
-    if all_resident:
+    all_resident = (not null) and n_launch <= args.steps * 5  # class launches only, no per-phase launches
+    if null:
+        # one unit = one null-event step (rates, propose, apply, clock: four launches)
+        units = args.steps * W
+        tag, kname = "k_null_step_" + args.workload, "k_null_* (null-event step: rates, propose, apply, clock)"
+        note = ("algorithmic bytes per step, 4-byte words: every vacancy's record and 8 neighbour words "
+                "(rates), every pick's record, 8 words, proposal and 2 claims (propose), its proposal and "
+                "claims plus 2 words and a record per applied hop (apply)")
+    elif all_resident:
         # the replica-resident kernel: one launch per shared-memory size class per call, the
         # classes run concurrently, so a "launch" here is one call's concurrent set
         units = args.steps
@@ -402,6 +430,11 @@ def main():
     b_alg = B_ALG_PER_HOP_SITE if wl.site else B_ALG_PER_HOP
     avg_launch_s = kernel_ms / 1e3 / units
     bytes_per_launch = hops / units * b_alg
+    if null:
+        nv, nfr = wl.replicas[0].n_vac, wl.notes["n_frg"]
+        bytes_per_launch = nv * (24 + 8 * 4) + nfr * (24 + 8 * 4 + 16 + 2 * 8) + nfr * (16 + 2 * 8) + \
+            hops / units * (2 * 4 + 24)
+        b_alg = bytes_per_launch / max(hops / units, 1e-9)
     achieved = bytes_per_launch / avg_launch_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": load_traffic(tag), "peak_kind": f"{peak_kind} hbm_gbs",
@@ -432,6 +465,24 @@ def main():
             extra["e2e"] = {"value": None, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": 0,
                             "note": "state larger than 4 GiB: not re-uploaded every step"}
 
+        if null:
+            # cross-check of the spatial windowed scheme against the paper's own
+            # formulation: D of V, O and H over the same simulated time
+            bn = make_batch(fkmc, wl, seed, fkmc.FKMC_MIXED, tracer=True)
+            bn.run_null(20 * W, wl.notes["n_frg"])
+            t_null = bn.info(0).null_time_s
+            bs = make_batch(fkmc, wl, seed, fkmc.FKMC_MIXED, tracer=True)
+            Ws = max(1, int(round(t_null / bs.info(0).tau)))
+            ss = bs.run(Ws)
+            cmp = {"t_s": t_null, "null_steps": 20 * W, "spatial_windows": Ws,
+                   "hops_null": bn.info(0).hops, "hops_spatial": ss.hops,
+                   "spatial_hops_per_s": ss.hops / (ss.gpu_ms / 1e3) if ss.gpu_ms > 0 else None}
+            for sp, nm in ((fkmc.FKMC_V, "V"), (fkmc.FKMC_O, "O"), (fkmc.FKMC_H, "H")):
+                cmp["D_" + nm + "_null"] = bn.D(0, sp)[1]
+                cmp["D_" + nm + "_spatial"] = bs.D(0, sp)[1]
+            bn.close()
+            bs.close()
+            extra["null_vs_spatial"] = cmp
         if wl.site:
             # the paper's dopant comparison: D of the vacancies with the full model, without
             # the V-V term, without the dopant term and without interactions, same draws
@@ -503,7 +554,12 @@ def main():
                 "replicas_bit_identical": same, "replicas": nrep,
             }
         if not args.no_cpu:
-            if args.workload == "um":
+            if null:
+                rate, ch, cs = cpu_oracle_null_rate(wl, seed, 2, 12.0)
+                extra["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                         "sample": f"the same lattice, null-event steps of {wl.notes['n_frg']} "
+                                                   f"picks, serial C oracle ({ch} hops in {cs:.1f} s)"}
+            elif args.workload == "um":
                 # the oracle holds one byte per site: time it on a 120^3 cube with the same
                 # density, field and temperature, and quote hops/s
                 small = workloads.um_batio3_bias(seed, 120)
@@ -513,7 +569,8 @@ def main():
                 rate, ch, cs, cd = cpu_oracle_rate(wl, seed, min(W, 8) if nrep == 1 else W, 12.0)
                 smp = (f"{cd} replica runs of {W} windows" if nrep > 1 else "the same lattice") + \
                     f", serial C oracle ({ch} hops in {cs:.1f} s)"
-            extra["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": smp}
+            if not null:
+                extra["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": smp}
 
     if rank == 0:
         line = {
@@ -526,7 +583,9 @@ def main():
                                      if precision else "plain fp64"),
                        "n_tau": 1.0, "edge": edge, "launch_opts": tuned_opts, "autotune": tuned,
                        "l2": "flushed between timed steps (256 MiB write)",
-                       "schedule": ("replica-resident kernel per shared-memory size class" if all_resident
+                       "schedule": ("null-event steps (Sec. II.B), one pick per vacancy, %d steps per "
+                                    "benchmark step" % W if null else
+                                    "replica-resident kernel per shared-memory size class" if all_resident
                                     else "colour-phase kernel, one launch per phase"),
                        "seed": args.seed},
             "roofline": roofline,

@@ -154,6 +154,10 @@ typedef struct {
     uint64_t handoffs;
     int64_t nsite;      /* 3 nx ny nz */
     int64_t n_vac, n_H;
+    uint64_t null_steps; /* steps of the null-event form run so far (kmc_run_null) */
+    double null_theta;   /* its clock in units of 1/k32max */
+    double null_time_s;  /* its simulated time, s (included in kmc_read_msd's t) */
+    int64_t n_Fe;        /* dopants */
 } kmc_replica_info;
 
 typedef struct kmc_batch kmc_batch;
@@ -235,6 +239,37 @@ int kmc_read_site_field(kmc_batch* b, int32_t r, int32_t* host_field, size_t n);
  * consistent field; the event was dropped). */
 int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats);
 
+/* The paper's own atom-based fragment kMC with null events (Sec. II.B,
+ * Eqs. AtomP and TimeStepFrg), the atoms being the vacancies, for `steps`
+ * steps on every replica.  One step:
+ *   1. R_I = the sum of vacancy I's exchange rates, R_tot = sum_I R_I,
+ *      R_max = max_I R_I, all exact u64 (rates in the fixed point of the mixed
+ *      form with F_null = 63 - ceil(log2(8 N_V)), from the replica's fp32
+ *      table);
+ *   2. min(n_frg, N_V) distinct vacancies are picked: the images of
+ *      0 .. N_frg-1 under a keyed Feistel bijection of the vacancy ids, keyed
+ *      by (seed, replica) and the step number;
+ *   3. pick p draws x from Philox (step, p) and takes the first event whose
+ *      running sum over the vacancy's 8 exchanges exceeds mulhi(x, R_max), or
+ *      the null event when none does (probability 1 - R_I / R_max);
+ *   4. a pick whose exchange shares a site with the exchange of a non-null
+ *      pick of smaller index becomes null (the paper leaves the
+ *      reconciliation of simultaneous picks open; this keeps the applied
+ *      exchanges disjoint);
+ *   5. the exchanges are applied, and the replica's clock advances by
+ *      -ln(r') / R_tot * N_updated (r' from Philox (step, 2^64-1)).
+ * With n_frg = 1 this is the conventional kMC of Sec. II.A in distribution.
+ * The state is shared with kmc_run (records are regathered by id before and
+ * returned to their fragments after); kmc_read_msd's t adds this clock.
+ * Vacancy ids must be 0 .. N_V-1 (true after creation and kmc_write_state).
+ * Needs 8 bytes per site (claims) and 24 bytes per vacancy of extra device
+ * memory, allocated at the first call.
+ * Errors: FKMC_ESTATE before kmc_set_barriers; FKMC_EINVAL for n_frg < 1,
+ * more than 2^32 - 16 steps, or with site energies on; FKMC_ENOMEM;
+ * FKMC_EOVERFLOW if a fragment cannot take its vacancies back (cap_v);
+ * FKMC_ECUDA. */
+int kmc_run_null(kmc_batch* b, uint64_t steps, int64_t n_frg, kmc_run_stats* stats);
+
 /* Exact integer moments of the displacements of one species of replica r:
  * out = {count, sum dx, sum dy, sum dz, sum dx^2, sum dy^2, sum dz^2}, units
  * a/2 and (a/2)^2.  FKMC_V sums the vacancy records; FKMC_O / FKMC_H sum the
@@ -247,8 +282,8 @@ int kmc_read_moments(kmc_batch* b, int32_t r, int32_t species, int64_t out[7]);
 int kmc_read_moments_all(kmc_batch* b, int64_t* out, size_t n_out);
 
 /* Mean squared displacement per axis (m^2), mean displacement per axis (m)
- * and the simulated time t = windows * tau (s) of one species (Sec. III:
- * D from tracked trajectories). */
+ * and the simulated time t = windows * tau + the null-event clock (s) of one
+ * species (Sec. III: D from tracked trajectories). */
 int kmc_read_msd(kmc_batch* b, int32_t r, int32_t species, double msd_xyz[3],
                  double mean_xyz[3], double* t_s);
 

@@ -162,6 +162,18 @@ struct kmc_batch {
     SiteOff* d_bo = nullptr;
     double* btab = nullptr;          // Boltzmann tables of every replica
     size_t btab_bytes = 0;
+    // atom-based fragment kMC with null events (Sec. II.B)
+    VacRec* vac = nullptr;                 // vacancies by id, replica after replica
+    int64_t vac_cap = 0;
+    unsigned long long* claims = nullptr;  // per site: (step tag, pick) of the earliest claim
+    NullProp* props = nullptr;
+    int64_t props_cap = 0;
+    unsigned long long* nacc = nullptr;    // R_tot, R_max, N_updated per replica
+    double* theta = nullptr;               // null-event clock per replica (1/k32max units)
+    unsigned long long* nctl = nullptr;    // [0] steps of this call so far, [1] current step
+    std::vector<double> theta_host;
+    cudaGraphExec_t null_exec = nullptr;
+    int64_t null_exec_picks = -1, null_exec_vac = -1;
 
     void* dalloc(size_t bytes)
     {
@@ -211,6 +223,8 @@ struct kmc_batch {
         }
         rclass.clear();
         if (window_exec) cudaGraphExecDestroy(window_exec);
+        if (null_exec) cudaGraphExecDestroy(null_exec);
+        null_exec = nullptr;
         if (cap_st) cudaStreamDestroy(cap_st);
         window_exec = nullptr;
         cap_st = nullptr;
@@ -500,6 +514,14 @@ int rebuild_field(kmc_batch* b)
     return FKMC_OK;
 }
 
+// simulated time of the null-event form of replica r (s): its clock counts in 1/k32max
+double null_time(const kmc_batch* b, int r)
+{
+    float kmax = 0.0f;
+    for (int i = 0; i < 6; ++i) kmax = std::max(kmax, (float)b->desc[r].k64[i]);
+    return kmax > 0.0f ? b->theta_host[r] / (double)kmax : 0.0;
+}
+
 void drop_window_graph(kmc_batch* b)
 {
     if (b->window_exec) cudaGraphExecDestroy(b->window_exec);
@@ -569,6 +591,7 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
     b->n_H.resize(n);
     b->n_fe.assign(n, 0);
     b->T.assign(n, 0.0);
+    b->theta_host.assign(n, 0.0);
     b->b_bits.resize(n);
     b->a_ang.resize(n);
     b->stats_host.assign(2 * (size_t)n, 0ull);
@@ -844,6 +867,124 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
     return rc;
 }
 
+int kmc_run_null(kmc_batch* b, uint64_t steps, int64_t n_frg, kmc_run_stats* stats)
+{
+    if (!b) return fail(FKMC_EINVAL, "null batch");
+    if (!b->rates_set) return fail(FKMC_ESTATE, "kmc_set_barriers must come before kmc_run_null");
+    if (b->site_on) return fail(FKMC_EINVAL, "the null-event form has no site energies");
+    if (n_frg < 1) return fail(FKMC_EINVAL, "n_frg must be >= 1");
+    if (steps > 0xFFFFFFF0ull) return fail(FKMC_EINVAL, "at most 2^32 - 16 steps per call");
+    // per-replica tables and offsets
+    int64_t total_vac = 0, total_picks = 0;
+    for (int r = 0; r < b->n; ++r) {
+        RepDesc& D = b->desc[r];
+        float k32[6], kmax = 0.0f;
+        for (int i = 0; i < 6; ++i) {
+            k32[i] = (float)D.k64[i];
+            kmax = std::max(kmax, k32[i]);
+        }
+        const int64_t nv = b->n_vac[r];
+        const int F = 63 - ceil_log2(8 * std::max<int64_t>(nv, 1));
+        for (int i = 0; i < 6; ++i) D.qn[i] = (uint64_t)std::llrint(std::ldexp((double)k32[i] / (double)kmax, F));
+        D.two_pow_Fn = std::ldexp(1.0, F);
+        D.vac_off = total_vac;
+        D.null_nv = nv;
+        D.null_nfrg = std::min<int64_t>(n_frg, nv);
+        D.pick_off = total_picks;
+        total_vac += nv;
+        total_picks += D.null_nfrg;
+    }
+    if (total_vac > b->vac_cap) {
+        b->dfree(b->vac);
+        b->vac = (VacRec*)b->dalloc(sizeof(VacRec) * total_vac);
+        b->vac_cap = b->vac ? total_vac : 0;
+        if (!b->vac) return fail(FKMC_ENOMEM, "device allocation failed (null-event vacancies)");
+        if (b->null_exec) cudaGraphExecDestroy(b->null_exec);
+        b->null_exec = nullptr;
+    }
+    if (!b->claims) {
+        b->claims = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * b->nsite_total);
+        b->nacc = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * 3 * b->n);
+        b->theta = (double*)b->dalloc(sizeof(double) * b->n);
+        b->nctl = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * 2);
+        if (!b->claims || !b->nacc || !b->theta || !b->nctl)
+            return fail(FKMC_ENOMEM, "device allocation failed (null-event buffers)");
+        CK(cudaMemsetAsync(b->theta, 0, sizeof(double) * b->n, b->st), "memset");
+    }
+    if (total_picks > b->props_cap) {
+        if (b->null_exec) cudaGraphExecDestroy(b->null_exec);
+        b->null_exec = nullptr;
+        b->dfree(b->props);
+        b->props = (NullProp*)b->dalloc(sizeof(NullProp) * total_picks);
+        if (!b->props) {
+            b->props_cap = 0;
+            return fail(FKMC_ENOMEM, "device allocation failed (null-event picks)");
+        }
+        b->props_cap = total_picks;
+    }
+    int rc = upload_desc(b);
+    if (rc) return rc;
+    std::vector<unsigned long long> before = b->stats_host;
+    CK(cudaEventRecord(b->ev0, b->st), "event record");
+    uint64_t launches = 0;
+    CK(cudaMemsetAsync(b->claims, 0xFF, sizeof(unsigned long long) * b->nsite_total, b->st), "memset");
+    CK(cudaMemsetAsync(b->nacc, 0, sizeof(unsigned long long) * 3 * b->n, b->st), "memset");
+    CK(cudaMemsetAsync(b->nctl, 0, sizeof(unsigned long long) * 2, b->st), "memset");
+    CK(launch_null_gather(b->d_desc, b->n, b->recs, b->counts, b->nfrag_total, b->cap, b->vac, b->status, b->st),
+       "null gather");
+    ++launches;
+    if (steps > 0 && total_vac > 0) {
+        if (!b->null_exec || b->null_exec_picks != total_picks || b->null_exec_vac != total_vac) {
+            if (b->null_exec) cudaGraphExecDestroy(b->null_exec);
+            b->null_exec = nullptr;
+            if (!b->cap_st) CK(cudaStreamCreateWithFlags(&b->cap_st, cudaStreamNonBlocking), "stream");
+            cudaGraph_t graph = nullptr;
+            CK(cudaStreamBeginCapture(b->cap_st, cudaStreamCaptureModeThreadLocal), "graph capture");
+            cudaError_t le = launch_null_step(b->d_desc, b->n, total_vac, total_picks, b->vac, b->occ, b->nbt,
+                                              b->nacc, b->props, b->claims, b->tracer, b->theta, b->stats, b->nctl,
+                                              b->cap_st);
+            cudaError_t ce = cudaStreamEndCapture(b->cap_st, &graph);
+            if (le != cudaSuccess) return cuda_fail(le, "null step capture");
+            if (ce != cudaSuccess) return cuda_fail(ce, "null step capture");
+            cudaError_t ie = cudaGraphInstantiate(&b->null_exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) {
+                b->null_exec = nullptr;
+                return cuda_fail(ie, "graph instantiate");
+            }
+            b->null_exec_picks = total_picks;
+            b->null_exec_vac = total_vac;
+        }
+        for (uint64_t k = 0; k < steps; ++k) CK(cudaGraphLaunch(b->null_exec, b->st), "graph launch");
+        launches += 4 * steps;
+    }
+    CK(launch_null_scatter(b->d_desc, b->n, total_vac, b->vac, b->recs, b->counts, b->nfrag_total, b->cap, b->status,
+                           b->st),
+       "null scatter");
+    ++launches;
+    CK(cudaEventRecord(b->ev1, b->st), "event record");
+    for (int r = 0; r < b->n; ++r) b->desc[r].null_step += steps;
+    rc = upload_desc(b);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(b->stats_host.data(), b->stats, sizeof(unsigned long long) * 2 * b->n, cudaMemcpyDeviceToHost,
+                       b->st),
+       "stats copy");
+    CK(cudaMemcpyAsync(b->theta_host.data(), b->theta, sizeof(double) * b->n, cudaMemcpyDeviceToHost, b->st),
+       "clock copy");
+    rc = check_status(b);
+    b->field_valid = false;
+    if (stats) {
+        std::memset(stats, 0, sizeof *stats);
+        for (int r = 0; r < b->n; ++r) stats->hops += b->stats_host[2 * r] - before[2 * r];
+        stats->windows = 0;
+        stats->launches = launches;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+        stats->gpu_ms = ms;
+    }
+    return rc;
+}
+
 int kmc_read_moments(kmc_batch* b, int32_t r, int32_t species, int64_t out[7])
 {
     if (!valid_replica(b, r) || !out) return fail(FKMC_EINVAL, "bad replica or output");
@@ -884,7 +1025,7 @@ int kmc_read_msd(kmc_batch* b, int32_t r, int32_t species, double msd_xyz[3], do
         if (msd_xyz) msd_xyz[k] = (double)m[4 + k] / n * h * h;
         if (mean_xyz) mean_xyz[k] = (double)m[1 + k] / n * h;
     }
-    if (t_s) *t_s = (double)b->desc[r].window * b->desc[r].tau;
+    if (t_s) *t_s = (double)b->desc[r].window * b->desc[r].tau + null_time(b, r);
     return FKMC_OK;
 }
 
@@ -1242,6 +1383,10 @@ int kmc_get_replica_info(kmc_batch* b, int32_t r, kmc_replica_info* out)
     out->nsite = D.nsite;
     out->n_vac = b->n_vac[r];
     out->n_H = b->n_H[r];
+    out->null_steps = D.null_step;
+    out->null_theta = b->theta_host[r];
+    out->null_time_s = null_time(b, r);
+    out->n_Fe = b->n_fe[r];
     return FKMC_OK;
 }
 

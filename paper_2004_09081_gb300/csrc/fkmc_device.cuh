@@ -14,6 +14,7 @@ namespace fkmc {
 
 constexpr int SP_O = 0, SP_H = 1, SP_V = 2;
 constexpr uint32_t PURPOSE_INIT = 1u, PURPOSE_PERM = 2u, PURPOSE_HOP = 3u, PURPOSE_DOPE = 5u;
+constexpr uint32_t PURPOSE_PICK = 6u, PURPOSE_NULL = 7u;
 constexpr uint32_t STATUS_OVERFLOW = 1u, STATUS_TIMEOUT = 2u, STATUS_EVENT_LIMIT = 4u, STATUS_ENERGY_RANGE = 8u;
 // Hard bound on the events one fragment may execute in one colour phase
 // (about 2.5e5 x the expected count at n_tau <= 64); reaching it ends the
@@ -56,6 +57,21 @@ struct RepDesc {
     int64_t btab_off;      // site energies: first Boltzmann-table entry of this replica
     int32_t bhi_mid;       // index of the high-table entry for m1 = 0
     int32_t bhi_len;       // entries of the high table
+    // atom-based fragment kMC with null events (Sec. II.B)
+    int64_t vac_off;       // first vacancy of this replica in the id-ordered array
+    int64_t null_nv;       // vacancies (the atoms)
+    int64_t null_nfrg;     // picks per step, min(N_frg, null_nv)
+    int64_t pick_off;      // first pick of this replica in the batch-wide pick array
+    uint64_t null_step;    // steps completed before the current call
+    uint64_t qn[6];        // fixed-point rates, F_null = 63 - ceil(log2(8 null_nv))
+    double two_pow_Fn;     // 2^F_null
+};
+
+// One pick of the null-event form: the vacancy (by id) and its event (-1: null).
+struct NullProp {
+    int64_t v;
+    int32_t n;
+    int32_t pad;
 };
 
 // ---------------------------------------------------------------- site energies

@@ -231,6 +231,8 @@ __device__ __forceinline__ void move_field(const RepDesc& D, const SiteArgs& sa,
 // Per-window set-up: colour order of every replica for this window, and the
 // screen counters of the 8 phases cleared.  wctl[0] counts the windows of the
 // current kmc_run call, wctl[1] holds the offset of the window being run.
+// Every block reads wctl[0] here, so it is advanced later, by the first
+// screen pass of the window (a later launch on the same stream).
 __global__ void k_window_setup(const RepDesc* __restrict__ descs, int nrep, unsigned long long* wctl,
                                uint32_t* perms, int32_t* act_count)
 {
@@ -238,11 +240,7 @@ __global__ void k_window_setup(const RepDesc* __restrict__ descs, int nrep, unsi
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrep; r += gridDim.x * blockDim.x)
         perms[r] = colour_perm_packed(descs[r].seed, descs[r].replica, descs[r].window + wk);
     if (blockIdx.x == 0 && threadIdx.x < 8) act_count[threadIdx.x] = 0;
-    __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        wctl[1] = wk;
-        wctl[0] = wk + 1;
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) wctl[1] = wk;
 }
 
 // Screen pass of a colour phase: one thread per fragment of the phase's colour
@@ -251,12 +249,14 @@ __global__ void k_window_setup(const RepDesc* __restrict__ descs, int nrep, unsi
 // instead of once per fragment-warp.
 template <int PREC>
 __global__ void __launch_bounds__(256) k_screen(const RepDesc* __restrict__ descs, int nrep, int64_t total_items,
-                                                int phase, const unsigned long long* wctl,
+                                                int phase, unsigned long long* wctl,
                                                 const uint32_t* __restrict__ perms,
                                                 const int32_t* __restrict__ counts, ActEntry* act,
                                                 int32_t* act_count)
 {
     const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // the window count advances here (nothing in this launch reads wctl[0])
+    if (phase == 0 && item == 0) wctl[0] = wctl[1] + 1;
     bool keep = false;
     ActEntry e;
     if (item < total_items) {

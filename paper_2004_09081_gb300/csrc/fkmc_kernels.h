@@ -24,6 +24,16 @@ cudaError_t launch_init_dopants(const RepDesc& D, int b_bits, int64_t n_fe, uint
 cudaError_t launch_site_field(const RepDesc* d_descs, int nrep, const VacRec* recs, const int32_t* counts,
                               int64_t nfrag_total, int cap, int64_t nsite_total, const uint8_t* fe,
                               const SiteOff* bo, int n_bo, const SiteArgs& sa, cudaStream_t st);
+// atom-based fragment kMC with null events (fkmc_null.cu)
+cudaError_t launch_null_gather(const RepDesc* d_descs, int nrep, const VacRec* recs, const int32_t* counts,
+                               int64_t nfrag_total, int cap, VacRec* vac, uint32_t* status, cudaStream_t st);
+cudaError_t launch_null_scatter(const RepDesc* d_descs, int nrep, int64_t total_vac, const VacRec* vac,
+                                VacRec* recs, int32_t* counts, int64_t nfrag_total, int cap, uint32_t* status,
+                                cudaStream_t st);
+cudaError_t launch_null_step(const RepDesc* d_descs, int nrep, int64_t total_vac, int64_t total_picks, VacRec* vac,
+                             uint32_t* occ, const NbTable& nbt, unsigned long long* acc, NullProp* props,
+                             unsigned long long* claims, int32_t* tracer, double* theta,
+                             unsigned long long* stats, unsigned long long* nctl, cudaStream_t st);
 cudaError_t launch_moments(const RepDesc& D, int species, const uint32_t* occ, const VacRec* recs,
                            const int32_t* counts, const int32_t* tracer, int cap,
                            unsigned long long* out, cudaStream_t st);

@@ -70,7 +70,8 @@ class kmc_replica_info(C.Structure):
                 ("precision", C.c_int32), ("tau", C.c_double), ("theta_tau", C.c_double),
                 ("k64", C.c_double * 6), ("q", C.c_uint64 * 6), ("window", C.c_uint64),
                 ("hops", C.c_uint64), ("handoffs", C.c_uint64), ("nsite", C.c_int64),
-                ("n_vac", C.c_int64), ("n_H", C.c_int64)]
+                ("n_vac", C.c_int64), ("n_H", C.c_int64), ("null_steps", C.c_uint64),
+                ("null_theta", C.c_double), ("null_time_s", C.c_double), ("n_Fe", C.c_int64)]
 
 
 _P, _I32, _I64, _U64, _SZ, _D = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_size_t, C.c_double
@@ -80,6 +81,7 @@ _SIGNATURES = {
     "kmc_create_lattice": (C.c_int, [_P, _P, _U64, _P, _P]),
     "kmc_set_barriers": (C.c_int, [_P, _P, _P, _P]),
     "kmc_run": (C.c_int, [_P, _U64, _P]),
+    "kmc_run_null": (C.c_int, [_P, _U64, _I64, _P]),
     "kmc_read_moments": (C.c_int, [_P, _I32, _I32, _P]),
     "kmc_read_moments_all": (C.c_int, [_P, _P, _SZ]),
     "kmc_read_msd": (C.c_int, [_P, _I32, _I32, _P, _P, _P]),
@@ -170,6 +172,12 @@ def kmc_set_barriers(h, tables, T_K, field_z):
 def kmc_run(h, windows: int) -> kmc_run_stats:
     s = kmc_run_stats()
     _check(load().kmc_run(h, int(windows), C.byref(s)))
+    return s
+
+
+def kmc_run_null(h, steps: int, n_frg: int) -> kmc_run_stats:
+    s = kmc_run_stats()
+    _check(load().kmc_run_null(h, int(steps), int(n_frg), C.byref(s)))
     return s
 
 
@@ -410,6 +418,10 @@ class Batch:
 
     def run(self, windows):
         return kmc_run(self.h, windows)
+
+    def run_null(self, steps, n_frg):
+        """The atom-based fragment kMC with null events (Sec. II.B)."""
+        return kmc_run_null(self.h, steps, n_frg)
 
     def state(self, r=0):
         return kmc_read_state(self.h, r, self.nsite(r))
