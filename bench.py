@@ -46,11 +46,13 @@ def parse():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    p.add_argument("--workload", default="batched", choices=["batched", "sweep", "bulk", "um", "fe", "null"],
+    p.add_argument("--workload", default="batched",
+                   choices=["batched", "sweep", "bulk", "um", "fe", "null", "htrend"],
                    help="batched: 256 uneven replicas (the headline); sweep: SrTiO(3-x)H_x 32^3 at "
                         "300..700 K; bulk: BaTiO(3-x)H_x 128^3; um: BaTiO3 L^3 under bias; fe: Fe-doped "
                         "SrTiO3 96^3 with vacancy-vacancy and vacancy-Fe site energies at 600..1000 K; null: "
-                        "the bulk lattice with the paper's atom-based null-event kMC, one pick per vacancy")
+                        "the bulk lattice with the paper's atom-based null-event kMC, one pick per vacancy; "
+                        "htrend: the paper's 24 hydride runs (Table 2 trend), 32^3 each")
     p.add_argument("--um-cells", type=int, default=2500, help="edge of the um-scale cube (cells)")
     p.add_argument("--no-autotune", action="store_true", help="use the workload's default edge")
     return p.parse_args()
@@ -300,6 +302,8 @@ def physics_report(fkmc, b, wl):
     """The observables each workload is quoted with (Sec. Computational details):
     D of V (and O, H- with tracer), drift and the Arrhenius fit of the T sweep."""
     out = []
+    if wl.name.startswith("h_trend"):
+        return h_trend_report(fkmc, b, wl)
     if len(wl.replicas) > 8:
         return {"replicas": None, "note": "per-replica D in D_mixed_vs_plain; not listed for large batches"}
     for r, rep in enumerate(wl.replicas):
@@ -323,6 +327,33 @@ def physics_report(fkmc, b, wl):
     return rep
 
 
+def h_trend_report(fkmc, b, wl):
+    """Apparent barriers of the hydride runs: Arrhenius fits of D_H and D_O over
+    550..700 K for each material and H- fraction, beside the paper's Table 2."""
+    from paper_2004_09081_gb300 import workloads
+    kB = 8.617333262e-5
+    rows, k = [], 0
+    for mi, mat in enumerate(wl.notes["materials"]):
+        for x in wl.notes["x"]:
+            pts = {"H": [], "O": [], "V": []}
+            Ds = []
+            for T in wl.notes["T"]:
+                d = {nm: b.D(k, sp)[1] for sp, nm in ((fkmc.FKMC_H, "H"), (fkmc.FKMC_O, "O"), (fkmc.FKMC_V, "V"))}
+                for nm, v in d.items():
+                    if v > 0:
+                        pts[nm].append((1.0 / T, math.log(v)))
+                Ds.append({"T": T, "D_H": d["H"], "D_O": d["O"], "D_V": d["V"]})
+                k += 1
+            row = {"material": mat, "x": x, "paper_Ea_H_eV": workloads.PAPER_TABLE2[x][mi], "D": Ds}
+            for nm in ("H", "O", "V"):
+                if len(pts[nm]) >= 2:
+                    xs, ys = np.array(pts[nm]).T
+                    row["Ea_app_" + nm + "_eV"] = float(-np.polyfit(xs, ys, 1)[0] * kB)
+            rows.append(row)
+    return {"h_trend": rows, "note": "apparent barriers from D = MSD/(6t) of the tracked ions after the run; "
+                                     "the paper's Table 2 gives the H- values"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -337,13 +368,13 @@ def main():
     seed = args.seed + rank  # each rank simulates its own independent batch (weak scaling)
     makers = {"batched": workloads.batched_batio3, "sweep": workloads.srtio3_h_sweep,
               "bulk": workloads.bulk_batio3, "um": lambda sd: workloads.um_batio3_bias(sd, args.um_cells),
-              "fe": workloads.fe_srtio3, "null": workloads.null_batio3}
+              "fe": workloads.fe_srtio3, "null": workloads.null_batio3, "htrend": workloads.h_trend}
     wl = makers[args.workload](seed)
     nrep = len(wl.replicas)
-    default_windows = {"batched": 64, "sweep": 64, "bulk": 16, "um": 2, "fe": 32, "null": 100}
+    default_windows = {"batched": 64, "sweep": 64, "bulk": 16, "um": 2, "fe": 32, "null": 100, "htrend": 20000}
     null = args.workload == "null"
-    if null:
-        args.no_plain = True  # the null-event form has one (integer) arithmetic
+    if null or args.workload == "htrend":
+        args.no_plain = True  # null: one (integer) arithmetic; htrend: physics runs, mixed only
     W = args.windows if args.windows else default_windows[args.workload]
     stream = torch.cuda.current_stream()
     reps = wl.replicas
@@ -405,9 +436,9 @@ def main():
     peak, peak_kind = load_peaks()
     all_resident = (not null) and n_launch <= args.steps * 5  # class launches only, no per-phase launches
     if null:
-        # one unit = one null-event step (rates, propose, apply, clock: four launches)
+        # one unit = one null-event step (rates, propose, apply + clock: three launches)
         units = args.steps * W
-        tag, kname = "k_null_step_" + args.workload, "k_null_* (null-event step: rates, propose, apply, clock)"
+        tag, kname = "k_null_step_" + args.workload, "k_null_* (null-event step: rates, propose, apply + clock)"
         note = ("algorithmic bytes per step, 4-byte words: every vacancy's record and 8 neighbour words "
                 "(rates), every pick's record, 8 words, proposal and 2 claims (propose), its proposal and "
                 "claims plus 2 words and a record per applied hop (apply)")

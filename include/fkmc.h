@@ -247,8 +247,11 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats);
  *      form with F_null = 63 - ceil(log2(8 N_V)), from the replica's fp32
  *      table);
  *   2. min(n_frg, N_V) distinct vacancies are picked: the images of
- *      0 .. N_frg-1 under a keyed Feistel bijection of the vacancy ids, keyed
- *      by (seed, replica) and the step number;
+ *      0 .. N_frg-1 under a keyed bijection of the vacancy ids (an
+ *      alternating Feistel network on ceil(log2 N_V) bits, four rounds
+ *      x ^= fmix64(other half ^ k_r) with MurmurHash3's 64-bit finaliser, round
+ *      keys the Philox block (step, 0, 0, 0) of (seed, replica), cycle
+ *      walking back into [0, N_V));
  *   3. pick p draws x from Philox (step, p) and takes the first event whose
  *      running sum over the vacancy's 8 exchanges exceeds mulhi(x, R_max), or
  *      the null event when none does (probability 1 - R_I / R_max);

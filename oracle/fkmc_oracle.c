@@ -938,8 +938,9 @@ int orc_bkl_run(orc_lattice* lat, double t_end, uint64_t stream, double* t_out)
  *     with F_null = 63 - ceil(log2(8 N_V)), so every sum is an exact integer
  *     below 2^63.
  *  2. N_frg distinct vacancies are picked: the images of 0 .. N_frg-1 under
- *     a keyed bijection of the vacancy ids (the Feistel construction of the
- *     placement, its own key, the step number in the round counter).
+ *     a keyed bijection of the vacancy ids (an alternating Feistel network
+ *     with per-step round keys, null_pick below).  The paper says only that
+ *     the atoms are selected at random.
  *  3. Pick p draws x and takes the first of its vacancy's events whose
  *     running sum exceeds mulhi(x, R_max) -- probability k_i / R_max -- or the
  *     null event when R_I does not (probability 1 - R_I / R_max).
@@ -954,23 +955,41 @@ int orc_bkl_run(orc_lattice* lat, double t_end, uint64_t stream, double* t_out)
 /* ------------------------------------------------------------------ */
 int64_t orc_n_records(const orc_lattice* lat);
 
+/* 64-bit finaliser of MurmurHash3 (Appleby): xor-shift 33, multiply, xor-shift
+ * 33, multiply, xor-shift 33, with its two published odd multipliers. */
+static uint64_t fmix64(uint64_t h)
+{
+    h ^= h >> 33;
+    h *= 0xff51afd7ed558ccdull;
+    h ^= h >> 33;
+    h *= 0xc4ceb9fe1a85ec53ull;
+    h ^= h >> 33;
+    return h;
+}
+
+/* Pick p of step `step`: the image of p under a keyed bijection of [0, n):
+ * an alternating Feistel network on m = max(2, ceil(log2 n)) bits (high part
+ * m - m/2 bits, low part m/2 bits; round r = 0..3 XORs F_r of one part into
+ * the other, high first), with cycle walking (Black & Rogaway) back into
+ * [0, n).  F_r(x) = fmix64(x ^ k_r); the round keys k_0..k_3 are the Philox
+ * block (step, 0, 0, 0) under the key (seed, replica, PICK). */
 static uint64_t null_pick(uint64_t p, uint64_t n, uint64_t seed, uint32_t replica, uint64_t step)
 {
-    int b = 1;
-    while (((uint64_t)1 << (2 * b)) < n) b++;
-    uint64_t mask = ((uint64_t)1 << b) - 1;
-    uint64_t key[2];
+    int m = 2;
+    while (((uint64_t)1 << m) < n) m++;
+    int bl = m / 2, bh = m - bl;
+    uint64_t ml = ((uint64_t)1 << bl) - 1, mh = ((uint64_t)1 << bh) - 1;
+    uint64_t key[2], ctr[4] = {step, 0, 0, 0}, k[4];
     key_for(seed, replica, PURPOSE_PICK, key);
+    orc_philox4x64(ctr, key, k);
     uint64_t v = p;
     do {
-        uint64_t Lh = v >> b, Rh = v & mask;
-        for (int k = 0; k < 4; k++) {
-            uint64_t ctr[4] = {Rh, (uint64_t)k, step, 0}, o[4];
-            orc_philox4x64(ctr, key, o);
-            uint64_t nl = Rh, nr = Lh ^ (o[0] & mask);
-            Lh = nl; Rh = nr;
+        uint64_t hi = v >> bl, lo = v & ml;
+        for (int r = 0; r < 4; r++) {
+            if (r % 2 == 0) hi = hi ^ (fmix64(lo ^ k[r]) & mh);
+            else lo = lo ^ (fmix64(hi ^ k[r]) & ml);
         }
-        v = (Lh << b) | Rh;
+        v = (hi << bl) | lo;
     } while (v >= n);
     return v;
 }

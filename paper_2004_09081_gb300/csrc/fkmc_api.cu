@@ -170,7 +170,7 @@ struct kmc_batch {
     int64_t props_cap = 0;
     unsigned long long* nacc = nullptr;    // R_tot, R_max, N_updated per replica
     double* theta = nullptr;               // null-event clock per replica (1/k32max units)
-    unsigned long long* nctl = nullptr;    // [0] steps of this call so far, [1] current step
+    unsigned long long* nctl = nullptr;    // [0] steps of this call so far, [1] current step, [2] blocks done
     std::vector<double> theta_host;
     cudaGraphExec_t null_exec = nullptr;
     int64_t null_exec_picks = -1, null_exec_vac = -1;
@@ -906,7 +906,7 @@ int kmc_run_null(kmc_batch* b, uint64_t steps, int64_t n_frg, kmc_run_stats* sta
         b->claims = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * b->nsite_total);
         b->nacc = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * 3 * b->n);
         b->theta = (double*)b->dalloc(sizeof(double) * b->n);
-        b->nctl = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * 2);
+        b->nctl = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * 3);
         if (!b->claims || !b->nacc || !b->theta || !b->nctl)
             return fail(FKMC_ENOMEM, "device allocation failed (null-event buffers)");
         CK(cudaMemsetAsync(b->theta, 0, sizeof(double) * b->n, b->st), "memset");
@@ -929,7 +929,7 @@ int kmc_run_null(kmc_batch* b, uint64_t steps, int64_t n_frg, kmc_run_stats* sta
     uint64_t launches = 0;
     CK(cudaMemsetAsync(b->claims, 0xFF, sizeof(unsigned long long) * b->nsite_total, b->st), "memset");
     CK(cudaMemsetAsync(b->nacc, 0, sizeof(unsigned long long) * 3 * b->n, b->st), "memset");
-    CK(cudaMemsetAsync(b->nctl, 0, sizeof(unsigned long long) * 2, b->st), "memset");
+    CK(cudaMemsetAsync(b->nctl, 0, sizeof(unsigned long long) * 3, b->st), "memset");
     CK(launch_null_gather(b->d_desc, b->n, b->recs, b->counts, b->nfrag_total, b->cap, b->vac, b->status, b->st),
        "null gather");
     ++launches;
@@ -956,7 +956,7 @@ int kmc_run_null(kmc_batch* b, uint64_t steps, int64_t n_frg, kmc_run_stats* sta
             b->null_exec_vac = total_vac;
         }
         for (uint64_t k = 0; k < steps; ++k) CK(cudaGraphLaunch(b->null_exec, b->st), "graph launch");
-        launches += 4 * steps;
+        launches += 3 * steps;
     }
     CK(launch_null_scatter(b->d_desc, b->n, total_vac, b->vac, b->recs, b->counts, b->nfrag_total, b->cap, b->status,
                            b->st),

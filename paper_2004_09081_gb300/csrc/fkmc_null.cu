@@ -3,14 +3,16 @@
 // vacancies.  One step over every replica of the batch, four launches:
 //
 //   k_null_rates    R_I of every vacancy; R_tot = sum, R_max = max (exact u64)
-//   k_null_propose  N_frg picks (keyed bijection of the vacancy ids); each
+//   k_null_propose  N_frg picks (keyed bijection of the vacancy ids: an
+//                   alternating Feistel network with hash rounds); each
 //                   takes event i with probability q_i / R_max or the null
 //                   event, and claims the two sites of its exchange with an
 //                   atomic minimum of (step tag, pick index)
 //   k_null_apply    a pick that holds both its claims applies its exchange
 //                   (an earlier non-null pick sharing a site wins); the
-//                   updated exchanges are disjoint and commute
-//   k_null_time     clock += -ln(r') / R_tot * N_updated (Eq. TimeStepFrg)
+//                   updated exchanges are disjoint and commute.  The last
+//                   block to finish advances every replica's clock,
+//                   clock += -ln(r') / R_tot * N_updated (Eq. TimeStepFrg)
 //
 // Rates are the mixed form's fixed point with F_null = 63 - ceil(log2(8 N_V)),
 // so every sum is an exact integer and no reduction order enters the result.
@@ -37,26 +39,36 @@ __device__ __forceinline__ int null_replica(const RepDesc* descs, int nrep, int6
     return lo;
 }
 
-// Pick p of step `step`: the image of p under a 4-round Feistel bijection of
-// [0, n) with cycle walking (the placement's construction; Philox round
-// function keyed by (seed, replica, PICK), the step in the counter).
-__device__ __forceinline__ uint64_t null_pick(uint64_t p, uint64_t n, uint64_t seed, uint32_t replica, uint64_t step)
+// MurmurHash3's 64-bit finaliser (Appleby): three xor-shifts by 33 around its
+// two published odd multipliers.
+__device__ __forceinline__ uint64_t fmix64(uint64_t h)
 {
-    int b = 1;
-    while ((1ull << (2 * b)) < n) ++b;
-    const uint64_t mask = (1ull << b) - 1ull;
-    const uint64_t k1 = key_word(replica, PURPOSE_PICK);
+    h ^= h >> 33;
+    h *= 0xff51afd7ed558ccdull;
+    h ^= h >> 33;
+    h *= 0xc4ceb9fe1a85ec53ull;
+    h ^= h >> 33;
+    return h;
+}
+
+// Pick p of a step: the image of p under an alternating Feistel bijection of
+// [0, 2^m), m = max(2, ceil(log2 n)), high part m - m/2 bits, low part m/2,
+// four rounds (high, low, high, low) of x ^= fmix64(other ^ k_r), walked back
+// into [0, n).  k[] = the step's Philox block under (seed, replica, PICK).
+__device__ __forceinline__ uint64_t null_pick(uint64_t p, uint64_t n, const U64x4& k)
+{
+    int m = 2;
+    while ((1ull << m) < n) ++m;
+    const int bl = m / 2, bh = m - bl;
+    const uint64_t ml = (1ull << bl) - 1ull, mh = (1ull << bh) - 1ull;
     uint64_t v = p;
     do {
-        uint64_t Lh = v >> b, Rh = v & mask;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const U64x4 o = philox4x64(Rh, (uint64_t)k, step, 0, seed, k1);
-            const uint64_t nr = Lh ^ (o.x[0] & mask);
-            Lh = Rh;
-            Rh = nr;
-        }
-        v = (Lh << b) | Rh;
+        uint64_t hi = v >> bl, lo = v & ml;
+        hi ^= fmix64(lo ^ k.x[0]) & mh;
+        lo ^= fmix64(hi ^ k.x[1]) & ml;
+        hi ^= fmix64(lo ^ k.x[2]) & mh;
+        lo ^= fmix64(hi ^ k.x[3]) & ml;
+        v = (hi << bl) | lo;
     } while (v >= n);
     return v;
 }
@@ -174,7 +186,8 @@ __global__ void __launch_bounds__(256) k_null_propose(const RepDesc* __restrict_
     const int64_t p = i - D.pick_off;
     const uint64_t k = nctl[1];
     const uint64_t step = D.null_step + k;
-    const int64_t id = (int64_t)null_pick((uint64_t)p, (uint64_t)D.null_nv, D.seed, D.replica, step);
+    const U64x4 rk = philox4x64(step, 0, 0, 0, D.seed, key_word(D.replica, PURPOSE_PICK));
+    const int64_t id = (int64_t)null_pick((uint64_t)p, (uint64_t)D.null_nv, rk);
     int t, x, y, z;
     split_key(vac[D.vac_off + id].key, t, x, y, z);
     const U64x4 blk = philox4x64(step, (uint64_t)p, 0, 0, D.seed, key_word(D.replica, PURPOSE_NULL));
@@ -202,13 +215,33 @@ __global__ void __launch_bounds__(256) k_null_propose(const RepDesc* __restrict_
               mine);
 }
 
+// clock of replica r after a step: + -ln(r') / R_tot * N_updated, in units of
+// 1/k32max (r' from Philox (step, 2^64-1)); hop counter; accumulators cleared
+__device__ __forceinline__ void null_time(const RepDesc& D, int r, unsigned long long* acc, double* theta,
+                                          unsigned long long* stats, uint64_t k)
+{
+    const unsigned long long Rtot = __ldcg(acc + 3 * r), n = __ldcg(acc + 3 * r + 2);
+    if (Rtot > 0ull) {
+        const U64x4 blk = philox4x64(D.null_step + k, ~0ull, 0, 0, D.seed, key_word(D.replica, PURPOSE_NULL));
+        const double E = neglog64(blk.x[0]);
+        const double dth = __dmul_rn(__dmul_rn(__ddiv_rn(E, __ull2double_rn(Rtot)), D.two_pow_Fn), __ull2double_rn(n));
+        theta[r] = __dadd_rn(theta[r], dth);
+    }
+    stats[2 * r] += n;
+    acc[3 * r] = acc[3 * r + 1] = acc[3 * r + 2] = 0ull;
+}
+
+// nctl[2] counts the blocks of this launch that have finished
 __global__ void __launch_bounds__(256) k_null_apply(const RepDesc* __restrict__ descs, int nrep, int64_t total_picks,
                                                     VacRec* vac, uint32_t* occ, NbTable nbt,
                                                     const NullProp* __restrict__ props,
                                                     const unsigned long long* claims, int32_t* tracer,
-                                                    unsigned long long* acc, const unsigned long long* nctl)
+                                                    unsigned long long* acc, double* theta,
+                                                    unsigned long long* stats, unsigned long long* nctl)
 {
+    __shared__ bool last;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t k = nctl[1];
     bool did = false;
     int r = -1;
     if (i < total_picks) {
@@ -225,7 +258,7 @@ __global__ void __launch_bounds__(256) k_null_apply(const RepDesc* __restrict__ 
             const int jy = wrapc(y + nb.dc[1], D.L[1]);
             const int jz = wrapc(z + nb.dc[2], D.L[2]);
             const int64_t s_lin = lin(D, t, x, y, z), j_lin = lin(D, nb.t2, jx, jy, jz);
-            const unsigned long long mine = claim_of(nctl[1], p);
+            const unsigned long long mine = claim_of(k, p);
             if (claims[D.site_off + s_lin] == mine && claims[D.site_off + j_lin] == mine) {
                 const uint32_t w = __ldcg(occ + occ_word(D, nb.t2, jx, jy, jz));
                 const uint32_t ion = (w >> occ_shift(jx)) & 3u;
@@ -254,24 +287,15 @@ __global__ void __launch_bounds__(256) k_null_apply(const RepDesc* __restrict__ 
     } else if (did) {
         atomicAdd(acc + 3 * r + 2, 1ull);
     }
-}
-
-__global__ void k_null_time(const RepDesc* __restrict__ descs, int nrep, unsigned long long* acc, double* theta,
-                            unsigned long long* stats, const unsigned long long* nctl)
-{
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrep) return;
-    const RepDesc& D = descs[r];
-    const unsigned long long Rtot = acc[3 * r], n = acc[3 * r + 2];
-    if (Rtot > 0ull) {
-        const uint64_t step = D.null_step + nctl[1];
-        const U64x4 blk = philox4x64(step, ~0ull, 0, 0, D.seed, key_word(D.replica, PURPOSE_NULL));
-        const double E = neglog64(blk.x[0]);
-        const double dth = __dmul_rn(__dmul_rn(__ddiv_rn(E, __ull2double_rn(Rtot)), D.two_pow_Fn), __ull2double_rn(n));
-        theta[r] = __dadd_rn(theta[r], dth);
-    }
-    stats[2 * r] += n;
-    acc[3 * r] = acc[3 * r + 1] = acc[3 * r + 2] = 0ull;
+    // the last block to finish closes the step (threadFenceReduction pattern)
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(nctl + 2, 1ull) == (unsigned long long)(gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int q = threadIdx.x; q < nrep; q += blockDim.x) null_time(descs[q], q, acc, theta, stats, k);
+    if (threadIdx.x == 0) nctl[2] = 0ull;
 }
 
 constexpr int NT = 256;
@@ -302,8 +326,8 @@ cudaError_t launch_null_scatter(const RepDesc* d_descs, int nrep, int64_t total_
     return cudaGetLastError();
 }
 
-// One step of every replica (four launches; fixed arguments, so a graph can
-// hold it).
+// One step of every replica (three launches; fixed arguments, so a graph can
+// hold it).  nctl[2] must be 0 before the first step.
 cudaError_t launch_null_step(const RepDesc* d_descs, int nrep, int64_t total_vac, int64_t total_picks, VacRec* vac,
                              uint32_t* occ, const NbTable& nbt, unsigned long long* acc, NullProp* props,
                              unsigned long long* claims, int32_t* tracer, double* theta,
@@ -313,8 +337,7 @@ cudaError_t launch_null_step(const RepDesc* d_descs, int nrep, int64_t total_vac
     k_null_propose<<<grid_of(total_picks), NT, 0, st>>>(d_descs, nrep, total_picks, vac, occ, nbt, acc, props, claims,
                                                         nctl);
     k_null_apply<<<grid_of(total_picks), NT, 0, st>>>(d_descs, nrep, total_picks, vac, occ, nbt, props, claims, tracer,
-                                                      acc, nctl);
-    k_null_time<<<(nrep + NT - 1) / NT, NT, 0, st>>>(d_descs, nrep, acc, theta, stats, nctl);
+                                                      acc, theta, stats, nctl);
     return cudaGetLastError();
 }
 

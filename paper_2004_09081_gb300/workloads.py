@@ -111,6 +111,28 @@ def null_batio3(seed: int = 0) -> Workload:
     return wl
 
 
+# Apparent H- barriers of the paper's Table 2 (eV), x -> (SrTiO3, BaTiO3)
+PAPER_TABLE2 = {0.45: (0.300, 0.410), 0.35: (0.464, 0.611), 0.25: (0.545, 0.700)}
+
+
+def h_trend(seed: int = 0, L: int = 32) -> Workload:
+    """The paper's hydride experiments (Sec. "Oxygen and hydride ions diffusion
+    coefficients"): SrTiO(3-x)H_x (barriers O 0.60, H- 0.17 eV, a = 3.905 A) and
+    BaTiO(3-x)H_x (0.70, 0.28 eV, a = 4.01 A), x = 0.25, 0.35, 0.45, at 550, 600,
+    650 and 700 K: 24 replicas of L^3 cells (size unstated in the paper), 0.1% of
+    O sites vacant, tracer mode, mixed form, one batch."""
+    reps = []
+    nsite = 3 * L**3
+    for a, Ea_O, Ea_H in ((A_SRTIO3, 0.60, 0.17), (A_BATIO3, 0.70, 0.28)):
+        for x in (0.25, 0.35, 0.45):
+            for T in (550.0, 600.0, 650.0, 700.0):
+                reps.append(Replica((L, L, L), a, round_half_up(0.001 * nsite), round_half_up(x * L**3), T,
+                                    Ea_O, Ea_H))
+    return Workload(f"h_trend_{L}c_24rep", reps, edge=4, precision=1, tracer=True, windows=20000,
+                    notes={"x": [0.25, 0.35, 0.45], "T": [550.0, 600.0, 650.0, 700.0],
+                           "materials": ["SrTiO3", "BaTiO3"]})
+
+
 # Vacancy-vacancy and vacancy-Fe shell energies of the paper's Table add01 on the
 # ideal lattice (squared distances in (a/2)^2: O-O 2, 4, 6, 8, 10 = 2.76 .. 6.17 A
 # at a = 3.905 A; O-B 1, 5, 9 = 1.95, 4.37, 5.86 A).  The V-V energies vanish at the
@@ -134,4 +156,5 @@ def fe_srtio3(seed: int = 0, L: int = 96) -> Workload:
 
 
 ALL = {"small": small_srtio3, "sweep": srtio3_h_sweep, "batched": batched_batio3,
-       "bulk": bulk_batio3, "um": um_batio3_bias, "fe": fe_srtio3, "null": null_batio3}
+       "bulk": bulk_batio3, "um": um_batio3_bias, "fe": fe_srtio3, "null": null_batio3,
+       "htrend": h_trend}

@@ -32,8 +32,13 @@ def test_pick_is_a_bijection_per_step():
             p = [orc.null_pick(i, n, 3, 2, step) for i in range(n)]
             assert sorted(p) == list(range(n))
             perms.append(p)
-        if n >= 5:
+        if n >= 17:
             assert perms[0] != perms[1] and perms[1] != perms[2]
+    # the first pick of a step is uniform over the vacancies (chi-square, 16 dof)
+    n, trials = 17, 6800
+    cnt = np.bincount([orc.null_pick(0, n, 9, 0, st) for st in range(trials)], minlength=n)
+    chi2 = float(((cnt - trials / n) ** 2 / (trials / n)).sum())
+    assert chi2 < 40.0, chi2  # p ~ 1e-3
 
 
 def test_lone_vacancy_is_never_null_and_hops_at_8k(orc):
