@@ -55,6 +55,8 @@ def parse():
                         "htrend: the paper's 24 hydride runs (Table 2 trend), 32^3 each")
     p.add_argument("--um-cells", type=int, default=2500, help="edge of the um-scale cube (cells)")
     p.add_argument("--no-autotune", action="store_true", help="use the workload's default edge")
+    p.add_argument("--profile-run", action="store_true",
+                   help="timed steps only (no e2e, physics, comparison or CPU legs): for profiler launch lists")
     return p.parse_args()
 
 
@@ -473,7 +475,9 @@ def main():
                 "avg_launch_us": avg_launch_s * 1e6, "note": note}
 
     extra = {}
-    if rank == 0:
+    if rank == 0 and args.profile_run:
+        extra["note"] = "profile run: timed steps only"
+    if rank == 0 and not args.profile_run:
         extra["physics"] = physics_report(fkmc, b, wl)
         # end to end through the public API: host state blob -> GPU, run, moments -> host
         nbytes = fkmc.kmc_state_bytes(b.h)
@@ -496,6 +500,15 @@ def main():
             extra["e2e"] = {"value": None, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": 0,
                             "note": "state larger than 4 GiB: not re-uploaded every step"}
 
+        if args.workload == "htrend":
+            # the same runs stopped after a tenth of the windows: short runs see H- hopping
+            # inside H- clusters before O migration sets the long-time D_H
+            short_w = max(1, (args.warmup + args.steps) * W // 10)
+            bsh = make_batch(fkmc, wl, seed, precision)
+            bsh.run(short_w)
+            extra["physics_short_run"] = dict(h_trend_report(fkmc, bsh, wl), windows=short_w)
+            bsh.close()
+            extra["physics"]["windows"] = (args.warmup + args.steps) * W
         if null:
             # cross-check of the spatial windowed scheme against the paper's own
             # formulation: D of V, O and H over the same simulated time
