@@ -80,6 +80,8 @@ def lib():
             "orc_null_pick": (u64, [u64, u64, u64, u32, u64]),
             "orc_null_run": (C.c_int, [P, u64, i64]),
             "orc_get_null": (None, [P, P, P, P, P]),
+            "orc_set_grains": (C.c_int, [P, C.c_int, C.c_int, d]),
+            "orc_get_grains": (None, [P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -196,6 +198,18 @@ class Lattice:
         F = C.c_int32(0)
         lib().orc_get_null(self._h, C.byref(th), C.byref(t), C.byref(st), C.byref(F))
         return {"theta": th.value, "t": t.value, "steps": st.value, "F": F.value}
+
+    # ---------------------------------------------- grains (mu-scale model)
+    def set_grains(self, n_grains: int, width: int = 1, barrier_eV: float = 0.2):
+        """Voronoi grains; hops touching a boundary cell get barrier + barrier_eV."""
+        if lib().orc_set_grains(self._h, int(n_grains), int(width), float(barrier_eV)):
+            raise ValueError("invalid grain parameters for this lattice")
+
+    def grains(self):
+        g = np.zeros(self.ncell, np.int32)
+        bnd = np.zeros(self.ncell, np.uint8)
+        lib().orc_get_grains(self._h, _ptr(g), _ptr(bnd))
+        return g, bnd
 
     def dopants(self) -> np.ndarray:
         out = np.zeros(self.ncell, np.uint8)

@@ -30,6 +30,8 @@
  *                                                    interaction", Table add01
  *   - the atom-based fragment kMC with null events    Sec. II.B, Eqs. (AtomP),
  *     (vacancies as the atoms, N_frg picks per step)   (TimeStepFrg)
+ *   - Voronoi grains whose boundary layer raises the   Sec. "Oxygen diffusion in
+ *     barrier of every hop touching it (0.2 eV)          mu-scale BaTiO3 model"
  * The spatial fragments, checkerboard colour phases, synchronisation windows
  * and hand-off of boundary hops are the synchronous-sublattice reading of the
  * fragment scheme; every step is written out in fkmc_phase() below.
@@ -56,6 +58,7 @@
 #define PURPOSE_DOPE 5u
 #define PURPOSE_PICK 6u
 #define PURPOSE_NULL 7u
+#define PURPOSE_GRAIN 8u
 
 /* ------------------------------------------------------------------ */
 /* Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers:
@@ -253,6 +256,17 @@ typedef struct {
     double tau, theta_tau, k32max;
     int rates_set;
     double T;       /* temperature of the rate table (K) */
+    /* grains: boundary cells raise the barrier of hops touching them */
+    int grains_on;
+    int32_t* grain;    /* grain of each cell, [z][y][x] */
+    uint8_t* gbound;   /* 1 for a boundary cell */
+    double gb_eV;      /* barrier added to a boundary hop */
+    double k64g[6];    /* rate tables of boundary hops */
+    float k32g[6];
+    uint64_t qg[6];
+    double rate_args[8]; /* Ea_O, Ea_H, A, q_O, q_H, T, Ez, a of the last set_rates */
+    int rate_cap;
+    double rate_ntau;
     /* site-energy interactions (plain form only) */
     int site_on;
     uint8_t* fe;    /* dopant (Fe) on the B site of each cell, [z][y][x] */
@@ -418,6 +432,8 @@ void orc_destroy(orc_lattice* lat)
     free(lat->tdisp);
     free(lat->fe);
     free(lat->claimed);
+    free(lat->grain);
+    free(lat->gbound);
     free(lat);
 }
 
@@ -479,6 +495,28 @@ int orc_set_rates(orc_lattice* lat, double Ea_O, double Ea_H, double A, double q
     }
     if (lat->site_on && precision != 0) return -1;
     lat->T = T_K;
+    {
+        double a[8] = {Ea_O, Ea_H, A, q_O, q_H, T_K, Ez_Vpm, a_ang};
+        memcpy(lat->rate_args, a, sizeof a);
+        lat->rate_cap = cap_v;
+        lat->rate_ntau = n_tau;
+    }
+    if (lat->grains_on) {
+        /* boundary hops: the same table with both barriers raised by gb_eV; the
+         * mixed form quantises them against the bulk table's k32max */
+        int32_t Fg;
+        float k32b[6];
+        uint64_t qb[6];
+        if (orc_rate_table(Ea_O + lat->gb_eV, Ea_H + lat->gb_eV, A, q_O, q_H, T_K, Ez_Vpm, a_ang, cap_v,
+                           lat->k64g, k32b, qb, &Fg))
+            return -1;
+        float kmax = 0.0f;
+        for (int i = 0; i < 6; i++) if (lat->k32[i] > kmax) kmax = lat->k32[i];
+        for (int i = 0; i < 6; i++) {
+            lat->k32g[i] = k32b[i];
+            lat->qg[i] = (uint64_t)llrint(ldexp((double)k32b[i] / (double)kmax, F));
+        }
+    }
     lat->tau = n_tau / (8.0 * kmax);
     lat->k32max = (double)kmax32;
     lat->theta_tau = lat->tau * lat->k32max;
@@ -673,8 +711,94 @@ int64_t orc_site_energy(const orc_lattice* lat, int64_t s, int64_t exclude)
     return E;
 }
 
-/* rate of the event (vacancy at s, ion at neighbour j) of table type ty */
-static double site_rate(const orc_lattice* lat, int64_t s, int64_t j, int ty)
+/* ------------------------------------------------------------------ */
+/* Grains (Sec. "Oxygen diffusion in mu-scale BaTiO3 model"): a Voronoi
+ * tessellation of the cells, periodic in all three directions.  Seed g sits at
+ * X_d = mulhi(y_d, 256 L_d) in units of 1/256 cell (y = the Philox block (g, 0,
+ * 0, 0) under the key (seed, replica, GRAIN)); a cell, centre 256 c + 128,
+ * belongs to the nearest seed (squared minimum-image distance, exact
+ * integers; ties to the smaller g).  A cell is a boundary cell when a cell of
+ * another grain lies within Chebyshev distance `width` of it; an O site
+ * belongs to the cell it is attached to (site n + a/2 e_t to cell n).  A hop
+ * whose start or end site is a boundary site has its barrier raised by
+ * barrier_eV (0.2 eV in the paper: 0.9 eV in total through the boundary).  */
+/* ------------------------------------------------------------------ */
+int orc_set_grains(orc_lattice* lat, int n_grains, int width, double barrier_eV)
+{
+    if (n_grains <= 1) { lat->grains_on = 0; return 0; }
+    if (n_grains > 4096 || width < 1 || !(barrier_eV >= 0.0) || !(barrier_eV <= 10.0)) return -1;
+    for (int k = 0; k < 3; k++) if (lat->L[k] < 2 * width + 1) return -1;
+    int64_t ncell = (int64_t)lat->L[0] * lat->L[1] * lat->L[2];
+    int64_t* X = (int64_t*)malloc(sizeof(int64_t) * 3 * (size_t)n_grains);
+    uint64_t key[2];
+    key_for(lat->seed, lat->replica, PURPOSE_GRAIN, key);
+    for (int g = 0; g < n_grains; g++) {
+        uint64_t ctr[4] = {(uint64_t)g, 0, 0, 0}, y[4];
+        orc_philox4x64(ctr, key, y);
+        for (int d = 0; d < 3; d++) X[3 * g + d] = (int64_t)mulhi64(y[d], (uint64_t)256 * (uint64_t)lat->L[d]);
+    }
+    free(lat->grain);
+    free(lat->gbound);
+    lat->grain = (int32_t*)malloc(sizeof(int32_t) * (size_t)ncell);
+    lat->gbound = (uint8_t*)calloc((size_t)ncell, 1);
+    for (int64_t c = 0; c < ncell; c++) {
+        int64_t cc[3] = {c % lat->L[0], (c / lat->L[0]) % lat->L[1], c / ((int64_t)lat->L[0] * lat->L[1])};
+        int best = 0;
+        int64_t bd = -1;
+        for (int g = 0; g < n_grains; g++) {
+            int64_t d2 = 0;
+            for (int d = 0; d < 3; d++) {
+                int64_t box = 256 * (int64_t)lat->L[d];
+                int64_t dd = 256 * cc[d] + 128 - X[3 * g + d];
+                if (dd < 0) dd = -dd;
+                if (box - dd < dd) dd = box - dd;
+                d2 += dd * dd;
+            }
+            if (bd < 0 || d2 < bd) { bd = d2; best = g; }
+        }
+        lat->grain[c] = best;
+    }
+    for (int64_t c = 0; c < ncell; c++) {
+        int cx = (int)(c % lat->L[0]), cy = (int)((c / lat->L[0]) % lat->L[1]);
+        int cz = (int)(c / ((int64_t)lat->L[0] * lat->L[1]));
+        for (int dz = -width; dz <= width && !lat->gbound[c]; dz++)
+            for (int dy = -width; dy <= width && !lat->gbound[c]; dy++)
+                for (int dx = -width; dx <= width; dx++) {
+                    int64_t o = ((int64_t)wrap(cz + dz, lat->L[2]) * lat->L[1] + wrap(cy + dy, lat->L[1])) *
+                                    lat->L[0] + wrap(cx + dx, lat->L[0]);
+                    if (lat->grain[o] != lat->grain[c]) { lat->gbound[c] = 1; break; }
+                }
+    }
+    free(X);
+    lat->gb_eV = barrier_eV;
+    lat->grains_on = 1;
+    if (lat->rates_set) {
+        const double* a = lat->rate_args;
+        return orc_set_rates(lat, a[0], a[1], a[2], a[3], a[4], a[5], a[6], a[7], lat->rate_cap, lat->rate_ntau,
+                             lat->precision);
+    }
+    return 0;
+}
+
+void orc_get_grains(const orc_lattice* lat, int32_t* grain, uint8_t* boundary)
+{
+    int64_t ncell = (int64_t)lat->L[0] * lat->L[1] * lat->L[2];
+    for (int64_t c = 0; c < ncell; c++) {
+        grain[c] = lat->grains_on ? lat->grain[c] : 0;
+        boundary[c] = lat->grains_on ? lat->gbound[c] : 0;
+    }
+}
+
+/* 1 when the hop between sites s and j touches a boundary cell */
+static int boundary_hop(const orc_lattice* lat, int64_t s, int64_t j)
+{
+    if (!lat->grains_on) return 0;
+    int64_t ncell = (int64_t)lat->L[0] * lat->L[1] * lat->L[2];
+    return lat->gbound[s % ncell] || lat->gbound[j % ncell];
+}
+
+/* rate of the event (vacancy at s, ion at neighbour j) of table rate k0 */
+static double site_rate(const orc_lattice* lat, int64_t s, int64_t j, double k0)
 {
     int64_t m = orc_site_energy(lat, j, s) - orc_site_energy(lat, s, -1);
     int64_t m1 = m >= 0 ? m / 512 : -((-m + 511) / 512);
@@ -682,7 +806,7 @@ static double site_rate(const orc_lattice* lat, int64_t s, int64_t j, int ty)
     double c = 1e-4 / (2.0 * (KB_EV * lat->T));
     double f1 = exp(-((double)(512 * m1) * c));
     double f0 = exp(-((double)m0 * c));
-    double k = lat->k64[ty] * f1;
+    double k = k0 * f1;
     return k * f0;
 }
 
@@ -703,8 +827,18 @@ static double event_rate64(const orc_lattice* lat, int64_t s, int n)
 {
     int ty = event_type(lat, s, n);
     if (ty < 0) return 0.0;
-    if (!lat->site_on) return lat->k64[ty];
-    return site_rate(lat, s, neighbour_site(lat, s, n), ty);
+    int64_t j = neighbour_site(lat, s, n);
+    double k0 = boundary_hop(lat, s, j) ? lat->k64g[ty] : lat->k64[ty];
+    if (!lat->site_on) return k0;
+    return site_rate(lat, s, j, k0);
+}
+
+/* fixed-point rate of the event (s, n) of the mixed form */
+static uint64_t event_rate_q(const orc_lattice* lat, int64_t s, int n)
+{
+    int ty = event_type(lat, s, n);
+    if (ty < 0) return 0;
+    return boundary_hop(lat, s, neighbour_site(lat, s, n)) ? lat->qg[ty] : lat->q[ty];
 }
 
 double orc_event_rate(const orc_lattice* lat, int64_t s, int n) { return event_rate64(lat, s, n); }
@@ -766,7 +900,7 @@ static void fkmc_phase(orc_lattice* lat, int F, uint64_t w)
                 int e = 8 * m + nb;
                 int ty = alive[m] ? event_type(lat, slot[m].site, nb) : -1;
                 r64[e] = ty < 0 ? 0.0 : event_rate64(lat, slot[m].site, nb);
-                rq[e] = ty < 0 ? 0 : lat->q[ty];
+                rq[e] = ty < 0 ? 0 : event_rate_q(lat, slot[m].site, nb);
             }
         /* draws of event i: Philox block (F, w, i/2); even i takes words 0,1 */
         if ((i >> 1) != blk_id) {
@@ -999,8 +1133,9 @@ uint64_t orc_null_pick(uint64_t p, uint64_t n, uint64_t seed, uint32_t replica, 
     return null_pick(p, n, seed, replica, step);
 }
 
-/* fixed-point table of the null-event form for N_V vacancies */
-static int null_table(const orc_lattice* lat, int64_t nv, uint64_t q[6])
+/* fixed-point tables of the null-event form for N_V vacancies: q[0..5] bulk
+ * hops, q[6..11] boundary hops (grains) */
+static int null_table(const orc_lattice* lat, int64_t nv, uint64_t q[12])
 {
     float kmax = 0.0f;
     for (int i = 0; i < 6; i++) if (lat->k32[i] > kmax) kmax = lat->k32[i];
@@ -1008,7 +1143,16 @@ static int null_table(const orc_lattice* lat, int64_t nv, uint64_t q[6])
     while (((int64_t)1 << lg) < 8 * (nv > 0 ? nv : 1)) lg++;
     int F = 63 - lg;
     for (int i = 0; i < 6; i++) q[i] = (uint64_t)llrint(ldexp((double)lat->k32[i] / (double)kmax, F));
+    for (int i = 0; i < 6; i++)
+        q[6 + i] = lat->grains_on ? (uint64_t)llrint(ldexp((double)lat->k32g[i] / (double)kmax, F)) : q[i];
     return F;
+}
+
+static uint64_t null_q(const orc_lattice* lat, const uint64_t q[12], int64_t s, int n)
+{
+    int ty = event_type(lat, s, n);
+    if (ty < 0) return 0;
+    return q[ty + (boundary_hop(lat, s, neighbour_site(lat, s, n)) ? 6 : 0)];
 }
 
 int orc_null_run(orc_lattice* lat, uint64_t steps, int64_t n_frg)
@@ -1024,7 +1168,7 @@ int orc_null_run(orc_lattice* lat, uint64_t steps, int64_t n_frg)
             v[r.id] = r; /* vacancy ids are 0 .. N_V-1 */
         }
     if (!lat->claimed) lat->claimed = (int64_t*)calloc((size_t)lat->nsite, sizeof(int64_t));
-    uint64_t q[6];
+    uint64_t q[12];
     int F = null_table(lat, nv, q);
     int64_t nf = n_frg < nv ? n_frg : nv;
     uint64_t key[2];
@@ -1037,10 +1181,7 @@ int orc_null_run(orc_lattice* lat, uint64_t steps, int64_t n_frg)
         uint64_t Rtot = 0, Rmax = 0;
         for (int64_t i = 0; i < nv; i++) {
             uint64_t R = 0;
-            for (int n = 0; n < 8; n++) {
-                int ty = event_type(lat, v[i].site, n);
-                R += ty < 0 ? 0 : q[ty];
-            }
+            for (int n = 0; n < 8; n++) R += null_q(lat, q, v[i].site, n);
             Rtot += R;
             if (R > Rmax) Rmax = R;
         }
@@ -1053,8 +1194,7 @@ int orc_null_run(orc_lattice* lat, uint64_t steps, int64_t n_frg)
             uint64_t P = 0;
             int sel = -1;
             for (int n = 0; n < 8; n++) {
-                int ty = event_type(lat, v[id].site, n);
-                P += ty < 0 ? 0 : q[ty];
+                P += null_q(lat, q, v[id].site, n);
                 if (P > target) { sel = n; break; }
             }
             pv[p] = id;
@@ -1108,7 +1248,7 @@ int orc_null_run(orc_lattice* lat, uint64_t steps, int64_t n_frg)
 /* clock of the null-event form: {theta (1/k32max units), t (s)}, steps and F_null */
 void orc_get_null(const orc_lattice* lat, double* theta, double* t_s, uint64_t* steps, int32_t* F)
 {
-    uint64_t q[6];
+    uint64_t q[12];
     float kmax = 0.0f;
     for (int i = 0; i < 6; i++) if (lat->k32[i] > kmax) kmax = lat->k32[i];
     *theta = lat->theta_null;
