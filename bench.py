@@ -47,12 +47,13 @@ def parse():
     p.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--workload", default="batched",
-                   choices=["batched", "sweep", "bulk", "um", "fe", "null", "htrend"],
+                   choices=["batched", "sweep", "bulk", "um", "fe", "null", "htrend", "umgrains"],
                    help="batched: 256 uneven replicas (the headline); sweep: SrTiO(3-x)H_x 32^3 at "
                         "300..700 K; bulk: BaTiO(3-x)H_x 128^3; um: BaTiO3 L^3 under bias; fe: Fe-doped "
                         "SrTiO3 96^3 with vacancy-vacancy and vacancy-Fe site energies at 600..1000 K; null: "
                         "the bulk lattice with the paper's atom-based null-event kMC, one pick per vacancy; "
-                        "htrend: the paper's 24 hydride runs (Table 2 trend), 32^3 each")
+                        "htrend: the paper's 24 hydride runs (Table 2 trend), 32^3 each; umgrains: the paper's "
+                        "1600x400x2400-cell BaTiO3 model with Voronoi grains under bias")
     p.add_argument("--um-cells", type=int, default=2500, help="edge of the um-scale cube (cells)")
     p.add_argument("--no-autotune", action="store_true", help="use the workload's default edge")
     p.add_argument("--profile-run", action="store_true",
@@ -149,6 +150,8 @@ def make_batch(fk, wl, seed, precision, replicas=None, edge=None, tracer=None, s
                  tracer=wl.tracer if tracer is None else tracer, **opts)
     if wl.site and site:
         b.set_site_energy(wl.site["vv"], wl.site["fe"])
+    if "grains" in wl.notes:
+        b.set_grains(*wl.notes["grains"])
     b.set_barriers([r.Ea_O for r in reps], [r.Ea_H for r in reps], [r.T for r in reps],
                    field_z=[r.field_z for r in reps])
     return b
@@ -195,6 +198,8 @@ def cpu_oracle_rate(wl, seed, windows, budget_s, replicas=None):
                 L.set_site_energy(vv=wl.site["vv"], fe=wl.site["fe"])
             L.set_rates(rep.Ea_O, rep.Ea_H, rep.T, Ez=rep.field_z, a_ang=rep.a, cap_v=cap,
                         precision=wl.precision)
+            if "grains" in wl.notes:
+                L.set_grains(*wl.notes["grains"])
             while True:  # single lattices keep running until the budget is spent
                 t0 = time.perf_counter()
                 L.run(windows)
@@ -370,10 +375,12 @@ def main():
     seed = args.seed + rank  # each rank simulates its own independent batch (weak scaling)
     makers = {"batched": workloads.batched_batio3, "sweep": workloads.srtio3_h_sweep,
               "bulk": workloads.bulk_batio3, "um": lambda sd: workloads.um_batio3_bias(sd, args.um_cells),
-              "fe": workloads.fe_srtio3, "null": workloads.null_batio3, "htrend": workloads.h_trend}
+              "fe": workloads.fe_srtio3, "null": workloads.null_batio3, "htrend": workloads.h_trend,
+              "umgrains": workloads.um_grains}
     wl = makers[args.workload](seed)
     nrep = len(wl.replicas)
-    default_windows = {"batched": 64, "sweep": 64, "bulk": 16, "um": 2, "fe": 32, "null": 100, "htrend": 20000}
+    default_windows = {"batched": 64, "sweep": 64, "bulk": 16, "um": 2, "fe": 32, "null": 100, "htrend": 20000,
+                       "umgrains": 2}
     null = args.workload == "null"
     if null or args.workload == "htrend":
         args.no_plain = True  # null: one (integer) arithmetic; htrend: physics runs, mixed only
@@ -603,10 +610,12 @@ def main():
                 extra["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                          "sample": f"the same lattice, null-event steps of {wl.notes['n_frg']} "
                                                    f"picks, serial C oracle ({ch} hops in {cs:.1f} s)"}
-            elif args.workload == "um":
+            elif args.workload in ("um", "umgrains"):
                 # the oracle holds one byte per site: time it on a 120^3 cube with the same
-                # density, field and temperature, and quote hops/s
+                # density, field and temperature (and grains), and quote hops/s
                 small = workloads.um_batio3_bias(seed, 120)
+                if args.workload == "umgrains":
+                    small.notes["grains"] = wl.notes["grains"]
                 rate, ch, cs, cd = cpu_oracle_rate(small, seed, 2, 12.0)
                 smp = f"120^3-cell cube with the same density, field and T ({ch} hops in {cs:.1f} s)"
             else:

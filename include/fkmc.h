@@ -231,6 +231,37 @@ int kmc_write_dopants(kmc_batch* b, int32_t r, const uint8_t* host_cells, size_t
  * index as in kmc_read_state (FKMC_ESTATE while the interactions are off). */
 int kmc_read_site_field(kmc_batch* b, int32_t r, int32_t* host_field, size_t n);
 
+/* Grains (the mu-scale model section of the paper): a periodic Voronoi
+ * tessellation of each replica's cells.  Seed g of replica r sits at
+ * X_d = mulhi(y_d, 256 L_d) in units of 1/256 cell, y the Philox4x64-10 block
+ * (g, 0, 0, 0) under the key (seed, r << 8 | 8); a cell (centre 256 c + 128)
+ * belongs to the nearest seed by squared minimum-image distance (exact
+ * integers; ties to the smaller g).  A cell is a boundary cell when a cell of
+ * another grain lies within Chebyshev distance `width`; an O site belongs to
+ * the cell it is attached to (site n + a/2 e_t to cell n).  Every hop that
+ * starts or ends on a boundary site has its barrier raised by barrier_eV (the
+ * paper's 0.2 eV, 0.9 eV in total through a boundary): the mixed form
+ * quantises those rates against the bulk table's k32max, so tau and F are
+ * unchanged. */
+typedef struct {
+    int32_t n_grains;  /* seeds per replica, 2..4096; <= 1 turns grains off */
+    int32_t width;     /* boundary-layer reach in cells, >= 1 (each dimension must be >= 2 width + 1) */
+    double barrier_eV; /* added to the barrier of boundary hops, 0 .. 10 eV */
+} kmc_grains;
+
+/* Set (or with NULL / n_grains <= 1 clear) the grains of every replica.  The
+ * grain map costs O(cells x n_grains) once.  Grains run in the colour-phase
+ * kernels and the null-event form (the replica-resident kernel has no grain
+ * tables), in both arithmetic forms and with site energies.
+ * Errors: FKMC_EINVAL for bad parameters or a dimension shorter than
+ * 2 width + 1; FKMC_ENOMEM (5 bytes per cell); FKMC_ECUDA. */
+int kmc_set_grains(kmc_batch* b, const kmc_grains* g);
+
+/* Grain of every cell (int32) and its boundary flag (uint8) for replica r,
+ * cell index (z ny + y) nx + x; n must equal nx ny nz.  FKMC_ESTATE without
+ * grains. */
+int kmc_read_grains(kmc_batch* b, int32_t r, int32_t* grain, uint8_t* boundary, size_t n);
+
 /* Run `windows` synchronisation windows on every replica.  Synchronous.
  * Errors: FKMC_ESTATE before kmc_set_barriers; FKMC_EOVERFLOW if a hand-off
  * found its target fragment full (the state is then invalid);

@@ -162,6 +162,15 @@ struct kmc_batch {
     SiteOff* d_bo = nullptr;
     double* btab = nullptr;          // Boltzmann tables of every replica
     size_t btab_bytes = 0;
+    // grains (mu-scale model): boundary cells raise the barrier of hops touching them
+    bool grains_on = false;
+    kmc_grains grains{};
+    int32_t* grain = nullptr;              // grain of every cell
+    uint8_t* gbound = nullptr;             // boundary flag of every cell
+    int64_t* gX = nullptr;                 // seed positions
+    int64_t gX_len = 0;
+    std::vector<kmc_barrier_table> tables; // of the last kmc_set_barriers
+    std::vector<double> Ez;
     // atom-based fragment kMC with null events (Sec. II.B)
     VacRec* vac = nullptr;                 // vacancies by id, replica after replica
     int64_t vac_cap = 0;
@@ -170,10 +179,12 @@ struct kmc_batch {
     int64_t props_cap = 0;
     unsigned long long* nacc = nullptr;    // R_tot, R_max, N_updated per replica
     double* theta = nullptr;               // null-event clock per replica (1/k32max units)
+    double* nE = nullptr;                  // the current step's clock variate per replica
     unsigned long long* nctl = nullptr;    // [0] steps of this call so far, [1] current step, [2] blocks done
     std::vector<double> theta_host;
     cudaGraphExec_t null_exec = nullptr;
     int64_t null_exec_picks = -1, null_exec_vac = -1;
+    bool null_exec_grains = false;
 
     void* dalloc(size_t bytes)
     {
@@ -299,7 +310,7 @@ int plan_residency(kmc_batch* b)
     }
     b->rclass.clear();
     const bool allowed = b->opts.precision == FKMC_MIXED && b->opts.schedule != 1 &&
-                         b->cap <= RESIDENT_MAX_SLOTS && !b->site_on;
+                         b->cap <= RESIDENT_MAX_SLOTS && !b->site_on && !b->grains_on;
     // launch classes: (shared-memory bound, threads); a replica takes the first
     // class its state fits, so small replicas pack several CTAs per SM and the
     // largest get the most warps that still fit beside their state.  The
@@ -501,7 +512,33 @@ SiteArgs site_args(const kmc_batch* b)
     a.field = b->field;
     a.n_vv = b->n_vv;
     a.e_self = b->e_self;
+    a.gbound = b->grains_on ? b->gbound : nullptr;
     return a;
+}
+
+// Rate tables of boundary hops: barriers raised by the grains' barrier, the
+// mixed form quantised against the bulk table's k32max (same F).
+int grain_tables(kmc_batch* b, int r)
+{
+    RepDesc& D = b->desc[r];
+    if (!b->grains_on) {
+        for (int i = 0; i < 6; ++i) {
+            D.k64g[i] = D.k64[i];
+            D.qg[i] = D.q[i];
+        }
+        return FKMC_OK;
+    }
+    kmc_barrier_table t = b->tables[r];
+    t.Ea_O_eV += b->grains.barrier_eV;
+    t.Ea_H_eV += b->grains.barrier_eV;
+    float k32g[6], kmax = 0.0f;
+    uint64_t qtmp[6];
+    int32_t F;
+    int rc = rate_table_impl(&t, b->T[r], b->Ez[r], b->a_ang[r], b->cap, D.k64g, k32g, qtmp, &F);
+    if (rc) return rc;
+    for (int i = 0; i < 6; ++i) kmax = std::max(kmax, (float)D.k64[i]);
+    for (int i = 0; i < 6; ++i) D.qg[i] = (uint64_t)std::llrint(std::ldexp((double)k32g[i] / (double)kmax, D.F));
+    return FKMC_OK;
 }
 
 int rebuild_field(kmc_batch* b)
@@ -710,7 +747,7 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
     build_nb_table(b->nbt.e);
     step(upload_neighbours(&b->nbt.e[0][0]), "neighbour table upload");
     step(phase_prepare(b->cap), "kernel attributes");
-    step(run_pass_blocks(b->opts.precision, b->cap, false, &b->run_blocks), "occupancy query");
+    step(run_pass_blocks(b->opts.precision, b->cap, false, false, &b->run_blocks), "occupancy query");
     step(resident_prepare(), "kernel attributes");
     step(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "event");
     step(cudaEventCreate(&b->ev0), "event");
@@ -775,8 +812,15 @@ int kmc_set_barriers(kmc_batch* b, const kmc_barrier_table* tables, const double
         D.theta_tau = D.tau * (double)kmax32;
     }
     b->desc = nd;
-    for (int r = 0; r < b->n; ++r) b->T[r] = T_K[r];
+    b->tables.assign(tables, tables + b->n);
+    b->Ez.assign(b->n, 0.0);
+    for (int r = 0; r < b->n; ++r) {
+        b->T[r] = T_K[r];
+        b->Ez[r] = field_z_Vpm ? field_z_Vpm[r] : 0.0;
+    }
     int rc = FKMC_OK;
+    for (int r = 0; r < b->n && rc == FKMC_OK; ++r) rc = grain_tables(b, r);
+    if (rc) return rc;
     if (b->site_on) {
         rc = build_btab(b);
         if (rc) return rc;
@@ -824,10 +868,11 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
             if (!b->cap_st) CK(cudaStreamCreateWithFlags(&b->cap_st, cudaStreamNonBlocking), "stream");
             cudaGraph_t graph = nullptr;
             CK(cudaStreamBeginCapture(b->cap_st, cudaStreamCaptureModeThreadLocal), "graph capture");
+            SiteArgs wa = sargs;
+            if (!b->site_on) wa.field = nullptr;  // the table-rate run pass
             cudaError_t le = launch_window(b->opts.precision, b->d_desc, b->n, b->total_items, b->wctl, b->perms,
                                            b->act, b->act_count, b->occ, b->recs, b->counts, b->tracer,
-                                           b->stats, b->status, b->cap, b->run_blocks,
-                                           b->site_on ? &sargs : nullptr, b->cap_st);
+                                           b->stats, b->status, b->cap, b->run_blocks, wa, b->cap_st);
             cudaError_t ce = cudaStreamEndCapture(b->cap_st, &graph);
             if (le != cudaSuccess) return cuda_fail(le, "window capture");
             if (ce != cudaSuccess) return cuda_fail(ce, "window capture");
@@ -886,6 +931,9 @@ int kmc_run_null(kmc_batch* b, uint64_t steps, int64_t n_frg, kmc_run_stats* sta
         const int64_t nv = b->n_vac[r];
         const int F = 63 - ceil_log2(8 * std::max<int64_t>(nv, 1));
         for (int i = 0; i < 6; ++i) D.qn[i] = (uint64_t)std::llrint(std::ldexp((double)k32[i] / (double)kmax, F));
+        for (int i = 0; i < 6; ++i)
+            D.qng[i] = b->grains_on ? (uint64_t)std::llrint(std::ldexp((double)(float)D.k64g[i] / (double)kmax, F))
+                                    : D.qn[i];
         D.two_pow_Fn = std::ldexp(1.0, F);
         D.vac_off = total_vac;
         D.null_nv = nv;
@@ -906,8 +954,9 @@ int kmc_run_null(kmc_batch* b, uint64_t steps, int64_t n_frg, kmc_run_stats* sta
         b->claims = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * b->nsite_total);
         b->nacc = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * 3 * b->n);
         b->theta = (double*)b->dalloc(sizeof(double) * b->n);
+        b->nE = (double*)b->dalloc(sizeof(double) * b->n);
         b->nctl = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * 3);
-        if (!b->claims || !b->nacc || !b->theta || !b->nctl)
+        if (!b->claims || !b->nacc || !b->theta || !b->nE || !b->nctl)
             return fail(FKMC_ENOMEM, "device allocation failed (null-event buffers)");
         CK(cudaMemsetAsync(b->theta, 0, sizeof(double) * b->n, b->st), "memset");
     }
@@ -934,15 +983,16 @@ int kmc_run_null(kmc_batch* b, uint64_t steps, int64_t n_frg, kmc_run_stats* sta
        "null gather");
     ++launches;
     if (steps > 0 && total_vac > 0) {
-        if (!b->null_exec || b->null_exec_picks != total_picks || b->null_exec_vac != total_vac) {
+        if (!b->null_exec || b->null_exec_picks != total_picks || b->null_exec_vac != total_vac ||
+            b->null_exec_grains != b->grains_on) {
             if (b->null_exec) cudaGraphExecDestroy(b->null_exec);
             b->null_exec = nullptr;
             if (!b->cap_st) CK(cudaStreamCreateWithFlags(&b->cap_st, cudaStreamNonBlocking), "stream");
             cudaGraph_t graph = nullptr;
             CK(cudaStreamBeginCapture(b->cap_st, cudaStreamCaptureModeThreadLocal), "graph capture");
             cudaError_t le = launch_null_step(b->d_desc, b->n, total_vac, total_picks, b->vac, b->occ, b->nbt,
-                                              b->nacc, b->props, b->claims, b->tracer, b->theta, b->stats, b->nctl,
-                                              b->cap_st);
+                                              b->grains_on ? b->gbound : nullptr, b->nacc, b->props, b->claims, b->tracer, b->theta, b->nE, b->stats,
+                                              b->nctl, b->cap_st);
             cudaError_t ce = cudaStreamEndCapture(b->cap_st, &graph);
             if (le != cudaSuccess) return cuda_fail(le, "null step capture");
             if (ce != cudaSuccess) return cuda_fail(ce, "null step capture");
@@ -954,6 +1004,7 @@ int kmc_run_null(kmc_batch* b, uint64_t steps, int64_t n_frg, kmc_run_stats* sta
             }
             b->null_exec_picks = total_picks;
             b->null_exec_vac = total_vac;
+            b->null_exec_grains = b->grains_on;
         }
         for (uint64_t k = 0; k < steps; ++k) CK(cudaGraphLaunch(b->null_exec, b->st), "graph launch");
         launches += 3 * steps;
@@ -1227,7 +1278,7 @@ int kmc_set_site_energy(kmc_batch* b, const kmc_site_energy* e)
         if (b->site_on) {
             b->site_on = false;
             drop_window_graph(b);
-            CK(run_pass_blocks(b->opts.precision, b->cap, false, &b->run_blocks), "occupancy query");
+            CK(run_pass_blocks(b->opts.precision, b->cap, false, b->grains_on, &b->run_blocks), "occupancy query");
             if (b->rates_set) {
                 int rc = plan_residency(b);
                 if (rc) return rc;
@@ -1274,7 +1325,7 @@ int kmc_set_site_energy(kmc_batch* b, const kmc_site_energy* e)
     b->site_on = true;
     b->field_valid = false;
     drop_window_graph(b);
-    CK(run_pass_blocks(FKMC_PLAIN, b->cap, true, &b->run_blocks), "occupancy query");
+    CK(run_pass_blocks(FKMC_PLAIN, b->cap, true, b->grains_on, &b->run_blocks), "occupancy query");
     if (b->rates_set) {
         int rc = build_btab(b);
         if (rc) return rc;
@@ -1306,6 +1357,67 @@ int kmc_site_shells(const kmc_site_energy* e, int32_t t, int32_t* rows, int32_t 
     for (int i = 0; i < sh.nvv; ++i) put(sh.vv[(size_t)t * SITE_MAX_VV + i]);
     for (const SiteOff& o : sh.ob[t]) put(o);
     if (n_rows) *n_rows = k;
+    return FKMC_OK;
+}
+
+int kmc_set_grains(kmc_batch* b, const kmc_grains* g)
+{
+    if (!b) return fail(FKMC_EINVAL, "null batch");
+    const bool on = g && g->n_grains > 1;
+    if (on && b->opts.schedule == 2)
+        return fail(FKMC_EINVAL, "grains need the colour-phase kernels (schedule 0 or 1)");
+    if (on) {
+        if (g->n_grains > 4096 || g->width < 1 || !(g->barrier_eV >= 0.0) || !(g->barrier_eV <= 10.0))
+            return fail(FKMC_EINVAL, "grains: 2..4096 seeds, width >= 1, barrier in [0, 10] eV");
+        for (int r = 0; r < b->n; ++r)
+            for (int d = 0; d < 3; ++d)
+                if (b->desc[r].L[d] < 2 * g->width + 1)
+                    return fail(FKMC_EINVAL, "grains: every dimension must be >= 2 width + 1 cells");
+        if (!b->grain) {
+            b->grain = (int32_t*)b->dalloc(sizeof(int32_t) * b->ncell_total);
+            b->gbound = (uint8_t*)b->dalloc((size_t)b->ncell_total);
+            if (!b->grain || !b->gbound) return fail(FKMC_ENOMEM, "device allocation failed (grains)");
+        }
+        const int64_t need = 3 * (int64_t)b->n * g->n_grains;
+        if (need > b->gX_len) {
+            b->dfree(b->gX);
+            b->gX = (int64_t*)b->dalloc(sizeof(int64_t) * need);
+            b->gX_len = b->gX ? need : 0;
+            if (!b->gX) return fail(FKMC_ENOMEM, "device allocation failed (grain seeds)");
+        }
+        CK(launch_grains(b->d_desc, b->n, b->ncell_total, g->n_grains, g->width, b->gX, b->grain, b->gbound, b->st),
+           "grain kernels");
+        b->grains = *g;
+    }
+    if (!on && !b->grains_on) return FKMC_OK;
+    b->grains_on = on;
+    drop_window_graph(b);
+    CK(run_pass_blocks(b->site_on ? FKMC_PLAIN : b->opts.precision, b->cap, b->site_on, on, &b->run_blocks),
+       "occupancy query");
+    if (b->rates_set) {
+        for (int r = 0; r < b->n; ++r) {
+            int rc = grain_tables(b, r);
+            if (rc) return rc;
+        }
+        int rc = plan_residency(b);
+        if (rc) return rc;
+        rc = upload_desc(b);
+        if (rc) return rc;
+    }
+    CK(cudaStreamSynchronize(b->st), "synchronize");
+    return FKMC_OK;
+}
+
+int kmc_read_grains(kmc_batch* b, int32_t r, int32_t* grain, uint8_t* boundary, size_t n)
+{
+    if (!valid_replica(b, r) || !grain || !boundary) return fail(FKMC_EINVAL, "bad replica or output");
+    if (!b->grains_on) return fail(FKMC_ESTATE, "grains are off");
+    const RepDesc& D = b->desc[r];
+    if ((int64_t)n != D.nsite / 3) return fail(FKMC_EINVAL, "n must equal nx ny nz");
+    CK(cudaMemcpyAsync(grain, b->grain + D.site_off / 3, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, b->st),
+       "grain copy");
+    CK(cudaMemcpyAsync(boundary, b->gbound + D.site_off / 3, n, cudaMemcpyDeviceToHost, b->st), "grain copy");
+    CK(cudaStreamSynchronize(b->st), "synchronize");
     return FKMC_OK;
 }
 

@@ -14,7 +14,7 @@ namespace fkmc {
 
 constexpr int SP_O = 0, SP_H = 1, SP_V = 2;
 constexpr uint32_t PURPOSE_INIT = 1u, PURPOSE_PERM = 2u, PURPOSE_HOP = 3u, PURPOSE_DOPE = 5u;
-constexpr uint32_t PURPOSE_PICK = 6u, PURPOSE_NULL = 7u;
+constexpr uint32_t PURPOSE_PICK = 6u, PURPOSE_NULL = 7u, PURPOSE_GRAIN = 8u;
 constexpr uint32_t STATUS_OVERFLOW = 1u, STATUS_TIMEOUT = 2u, STATUS_EVENT_LIMIT = 4u, STATUS_ENERGY_RANGE = 8u;
 // Hard bound on the events one fragment may execute in one colour phase
 // (about 2.5e5 x the expected count at n_tau <= 64); reaching it ends the
@@ -65,6 +65,10 @@ struct RepDesc {
     uint64_t null_step;    // steps completed before the current call
     uint64_t qn[6];        // fixed-point rates, F_null = 63 - ceil(log2(8 null_nv))
     double two_pow_Fn;     // 2^F_null
+    // grains: hops touching a boundary cell use these tables (type index - 6)
+    double k64g[6];
+    uint64_t qg[6];
+    uint64_t qng[6];
 };
 
 // One pick of the null-event form: the vacancy (by id) and its event (-1: null).
@@ -95,7 +99,14 @@ struct SiteArgs {
     int32_t* field;       // E_site of every O site (batch-wide site index)
     int32_t n_vv;         // offsets per site type
     int32_t e_self;       // energy of the a/sqrt2 shell: a hop partner's share of its target
+    const uint8_t* gbound;  // grains: 1 per boundary cell (batch-wide cell index), or null
 };
+
+// cell of a site, batch-wide index (a replica's cells start at site_off / 3)
+__device__ __forceinline__ int64_t cell_index(const RepDesc& D, int x, int y, int z)
+{
+    return D.site_off / 3 + ((int64_t)z * D.L[1] + y) * D.L[0] + x;
+}
 
 // ---------------------------------------------------------------- Philox
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the

@@ -75,7 +75,12 @@ struct Arith<0> {
     using V = double;
     static __device__ __forceinline__ V zero() { return 0.0; }
     static __device__ __forceinline__ V add(V a, V b) { return __dadd_rn(a, b); }
-    static __device__ __forceinline__ V rate(const RepDesc& D, int ty) { return ty < 0 ? 0.0 : D.k64[ty]; }
+    template <bool GRAIN = false>
+    static __device__ __forceinline__ V rate(const RepDesc& D, int ty)
+    {
+        if constexpr (GRAIN) return ty < 0 ? 0.0 : (ty < 6 ? D.k64[ty] : D.k64g[ty - 6]);
+        else return ty < 0 ? 0.0 : D.k64[ty];
+    }
     static __device__ __forceinline__ V shfl_up(V v, int off) { return __shfl_up_sync(0xffffffffu, v, off); }
     static __device__ __forceinline__ V shfl(V v, int src) { return __shfl_sync(0xffffffffu, v, src); }
     static __device__ __forceinline__ bool pos(V v) { return v > 0.0; }
@@ -87,7 +92,12 @@ struct Arith<1> {
     using V = unsigned long long;
     static __device__ __forceinline__ V zero() { return 0ull; }
     static __device__ __forceinline__ V add(V a, V b) { return a + b; }
-    static __device__ __forceinline__ V rate(const RepDesc& D, int ty) { return ty < 0 ? 0ull : (V)D.q[ty]; }
+    template <bool GRAIN = false>
+    static __device__ __forceinline__ V rate(const RepDesc& D, int ty)
+    {
+        if constexpr (GRAIN) return ty < 0 ? 0ull : (V)(ty < 6 ? D.q[ty] : D.qg[ty - 6]);
+        else return ty < 0 ? 0ull : (V)D.q[ty];
+    }
     static __device__ __forceinline__ V shfl_up(V v, int off) { return __shfl_up_sync(0xffffffffu, v, off); }
     static __device__ __forceinline__ V shfl(V v, int src) { return __shfl_sync(0xffffffffu, v, src); }
     static __device__ __forceinline__ bool pos(V v) { return v != 0ull; }
@@ -136,8 +146,9 @@ __host__ __device__ inline size_t warp_smem_bytes(int cap, bool site)
 
 // Rate types of every event of the fragment, read from the occupancy words
 // in L2 (ld.global.cg, so that this warp's own exchanges are seen).
+template <bool GRAIN = false>
 __device__ __forceinline__ void compute_types(const RepDesc& D, const uint32_t* occ, const WarpSmem& S,
-                                              int nslots, int nch, int lane)
+                                              int nslots, int nch, int lane, const uint8_t* gb = nullptr)
 {
     for (int c = 0; c < nch; ++c) {
         const int e = c * 32 + lane;
@@ -153,6 +164,9 @@ __device__ __forceinline__ void compute_types(const RepDesc& D, const uint32_t* 
             const uint32_t w = __ldcg(occ + occ_word(D, nb.t2, jx, jy, jz));
             const int code = (int)((w >> occ_shift(jx)) & 3u);
             ty = code == SP_V ? -1 : code * 3 + nb.d[2] + 1;
+            if constexpr (GRAIN) {  // a hop touching a boundary cell takes the raised table
+                if (ty >= 0 && (gb[cell_index(D, x, y, z)] | gb[cell_index(D, jx, jy, jz)])) ty += 6;
+            }
         }
         S.types[e] = (int8_t)ty;
     }
@@ -163,12 +177,14 @@ __device__ __forceinline__ int64_t site_lin(const RepDesc& D, int t, int x, int 
     return (((int64_t)t * D.L[2] + z) * D.L[1] + y) * D.L[0] + x;
 }
 
-// Site-energy path: rate type and FP64 rate of every event.  The barrier of
+// Site-energy path: rate type and FP64 rate of every event (type + 6 for a
+// hop touching a grain-boundary cell, whose table rate is the raised one).  The barrier of
 // the hop s -> j is Ea + dU/2 + (E_site(j) - E_site(s))/2, E_site(j) without the
 // hopping vacancy itself (which sits in j's a/sqrt2 shell); the energy
 // difference m (1e-4 eV units) enters as k_table * hi[m >> 9] * lo[m & 511],
 // two FP64 products in that order.  Field words are read from L2 (ld.cg):
 // other warps of the phase update them with atomics.
+template <bool GRAIN>
 __device__ __forceinline__ void compute_rates_site(const RepDesc& D, const uint32_t* occ, const SiteArgs& sa,
                                                    const WarpSmem& S, int nslots, int nch, int lane,
                                                    uint32_t* status)
@@ -192,12 +208,19 @@ __device__ __forceinline__ void compute_rates_site(const RepDesc& D, const uint3
             const int code = (int)((w >> occ_shift(jx)) & 3u);
             if (code != SP_V) {
                 ty = code * 3 + nb.d[2] + 1;
+                double k0 = D.k64[ty];
+                if constexpr (GRAIN) {
+                    if (sa.gbound[cell_index(D, x, y, z)] | sa.gbound[cell_index(D, jx, jy, jz)]) {
+                        k0 = D.k64g[ty];
+                        ty += 6;
+                    }
+                }
                 const int32_t Es = __ldcg(field + site_lin(D, t, x, y, z));
                 const int32_t Ej = __ldcg(field + site_lin(D, nb.t2, jx, jy, jz));
                 const int32_t dm = Ej - sa.e_self - Es;
                 const int hidx = D.bhi_mid + (dm >> 9);
                 if (hidx >= 0 && hidx < D.bhi_len) {
-                    k = __dmul_rn(__dmul_rn(D.k64[ty], __ldg(hi + hidx)), __ldg(lo + (dm & 511)));
+                    k = __dmul_rn(__dmul_rn(k0, __ldg(hi + hidx)), __ldg(lo + (dm & 511)));
                 } else {  // outside the bound the tables were built for: report, no event
                     atomicOr(status, STATUS_ENERGY_RANGE);
                     ty = -1;
@@ -313,7 +336,7 @@ __global__ void __launch_bounds__(256) k_screen(const RepDesc* __restrict__ desc
 
 // Run pass of a colour phase: one warp per screened fragment (grid-stride):
 // BKL on the fragment's vacancies until the next event would pass the window.
-template <int PREC, bool SITE>
+template <int PREC, bool SITE, bool GRAIN>
 __global__ void __launch_bounds__(128, 8) k_run(const RepDesc* __restrict__ descs, const ActEntry* __restrict__ act,
                                              const int32_t* __restrict__ act_count, int phase,
                                              const unsigned long long* wctl, uint32_t* occ, VacRec* recs,
@@ -365,13 +388,13 @@ __global__ void __launch_bounds__(128, 8) k_run(const RepDesc* __restrict__ desc
     __syncwarp();
     const int nslots = nv;
     const int nch = (nslots + 3) >> 2;  // 32 events per chunk
-    if constexpr (SITE) compute_rates_site(D, occ, sa, S, nslots, nch, lane, status);
-    else compute_types(D, occ, S, nslots, nch, lane);
+    if constexpr (SITE) compute_rates_site<GRAIN>(D, occ, sa, S, nslots, nch, lane, status);
+    else compute_types<GRAIN>(D, occ, S, nslots, nch, lane, sa.gbound);
     __syncwarp();
     // rate of event index e (lane-local chunk element)
     auto rate_of = [&](int e) -> V {
         if constexpr (SITE) return (V)S.rate[e];
-        else return A::rate(D, S.types[e]);
+        else return A::template rate<GRAIN>(D, S.types[e]);
     };
 
     const uint64_t hop_k1 = key_word(D.replica, PURPOSE_HOP);
@@ -506,7 +529,7 @@ __global__ void __launch_bounds__(128, 8) k_run(const RepDesc* __restrict__ desc
             const int jx = wrapc(x + nb.dc[0], D.L[0]);
             const int jy = wrapc(y + nb.dc[1], D.L[1]);
             const int jz = wrapc(z + nb.dc[2], D.L[2]);
-            const uint32_t ion = (uint32_t)(S.types[e_sel] / 3);
+            const uint32_t ion = (uint32_t)((S.types[e_sel] % 6) / 3);
             atomicXor(occ + occ_word(D, t, x, y, z), ((uint32_t)SP_V ^ ion) << occ_shift(x));
             atomicXor(occ + occ_word(D, nb.t2, jx, jy, jz), (ion ^ (uint32_t)SP_V) << occ_shift(jx));
             r.d[0] += nb.d[0];
@@ -542,8 +565,8 @@ __global__ void __launch_bounds__(128, 8) k_run(const RepDesc* __restrict__ desc
         __syncwarp();
         clock = __dadd_rn(clock, dclock);
         ++i;
-        if constexpr (SITE) compute_rates_site(D, occ, sa, S, nslots, nch, lane, status);
-        else compute_types(D, occ, S, nslots, nch, lane);
+        if constexpr (SITE) compute_rates_site<GRAIN>(D, occ, sa, S, nslots, nch, lane, status);
+        else compute_types<GRAIN>(D, occ, S, nslots, nch, lane, sa.gbound);
         __syncwarp();
     }
 
@@ -646,6 +669,95 @@ __global__ void k_field_dopant(const RepDesc* __restrict__ descs, int nrep, cons
                       a.e);
         }
     }
+}
+
+// ------------------------------------------------------------------ grains
+// Seed g of a replica's Voronoi tessellation at X_d = mulhi(y_d, 256 L_d)
+// (1/256-cell units), y = Philox block (g, 0, 0, 0) of (seed, replica, GRAIN).
+__global__ void k_grain_seeds(const RepDesc* __restrict__ descs, int nrep, int n_grains, int64_t* X)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)nrep * n_grains) return;
+    const int r = (int)(i / n_grains), g = (int)(i % n_grains);
+    const RepDesc& D = descs[r];
+    const U64x4 y = philox4x64((uint64_t)g, 0, 0, 0, D.seed, key_word(D.replica, PURPOSE_GRAIN));
+#pragma unroll
+    for (int d = 0; d < 3; ++d) X[3 * i + d] = (int64_t)__umul64hi(y.x[d], 256ull * (uint64_t)D.L[d]);
+}
+
+// Grain of every cell: the nearest seed by squared minimum-image distance from
+// the cell centre 256 c + 128 (exact integers; ties to the smaller seed).
+__global__ void k_grain_map(const RepDesc* __restrict__ descs, int nrep, int64_t ncell_total, int n_grains,
+                            const int64_t* __restrict__ X, int32_t* grain)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell_total;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nrep - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (descs[mid].site_off / 3 <= c) lo = mid; else hi = mid - 1;
+        }
+        const RepDesc& D = descs[lo];
+        const int64_t local = c - D.site_off / 3;
+        const int64_t cc[3] = {local % D.L[0], (local / D.L[0]) % D.L[1], local / ((int64_t)D.L[0] * D.L[1])};
+        const int64_t* Xr = X + 3 * (int64_t)lo * n_grains;
+        int best = 0;
+        int64_t bd = INT64_MAX;
+        for (int g = 0; g < n_grains; ++g) {
+            int64_t d2 = 0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const int64_t box = 256 * (int64_t)D.L[d];
+                int64_t dd = 256 * cc[d] + 128 - Xr[3 * g + d];
+                dd = dd < 0 ? -dd : dd;
+                dd = box - dd < dd ? box - dd : dd;
+                d2 += dd * dd;
+            }
+            if (d2 < bd) {
+                bd = d2;
+                best = g;
+            }
+        }
+        grain[c] = best;
+    }
+}
+
+// Boundary layer: a cell with a cell of another grain within Chebyshev distance w.
+__global__ void k_grain_boundary(const RepDesc* __restrict__ descs, int nrep, int64_t ncell_total, int w,
+                                 const int32_t* __restrict__ grain, uint8_t* gb)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell_total;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nrep - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (descs[mid].site_off / 3 <= c) lo = mid; else hi = mid - 1;
+        }
+        const RepDesc& D = descs[lo];
+        const int64_t c0 = D.site_off / 3, local = c - c0;
+        const int x = (int)(local % D.L[0]), y = (int)((local / D.L[0]) % D.L[1]);
+        const int z = (int)(local / ((int64_t)D.L[0] * D.L[1]));
+        const int32_t own = grain[c];
+        uint8_t b = 0;
+        for (int dz = -w; dz <= w && !b; ++dz)
+            for (int dy = -w; dy <= w && !b; ++dy)
+                for (int dx = -w; dx <= w && !b; ++dx)
+                    b = grain[c0 + ((int64_t)wrapc(z + dz, D.L[2]) * D.L[1] + wrapc(y + dy, D.L[1])) * D.L[0] +
+                              wrapc(x + dx, D.L[0])] != own;
+        gb[c] = b;
+    }
+}
+
+cudaError_t launch_grains(const RepDesc* d_descs, int nrep, int64_t ncell_total, int n_grains, int width, int64_t* X,
+                          int32_t* grain, uint8_t* gb, cudaStream_t st)
+{
+    const int threads = 256;
+    const int64_t ns = (int64_t)nrep * n_grains;
+    k_grain_seeds<<<(unsigned)((ns + threads - 1) / threads), threads, 0, st>>>(d_descs, nrep, n_grains, X);
+    const unsigned blocks = (unsigned)std::min<int64_t>(65536, (ncell_total + threads - 1) / threads);
+    k_grain_map<<<blocks, threads, 0, st>>>(d_descs, nrep, ncell_total, n_grains, X, grain);
+    k_grain_boundary<<<blocks, threads, 0, st>>>(d_descs, nrep, ncell_total, width, grain, gb);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ moments
@@ -779,30 +891,41 @@ cudaError_t launch_init(const RepDesc& D, int b_bits, int64_t n_vac, int64_t n_t
 
 size_t phase_smem_bytes(int cap, bool site) { return warp_smem_bytes(cap, site) * 4; }
 
+using RunFn = void (*)(const RepDesc*, const ActEntry*, const int32_t*, int, const unsigned long long*, uint32_t*,
+                      VacRec*, int32_t*, int32_t*, unsigned long long*, uint32_t*, int, SiteArgs);
+
+// the run-pass instantiation for an arithmetic form, the site-energy path and grains
+static RunFn run_kernel(int prec, bool site, bool grain)
+{
+    if (site) return grain ? k_run<0, true, true> : k_run<0, true, false>;
+    if (prec == 0) return grain ? k_run<0, false, true> : k_run<0, false, false>;
+    return grain ? k_run<1, false, true> : k_run<1, false, false>;
+}
+
 cudaError_t phase_prepare(int cap)
 {
-    const int bytes = (int)phase_smem_bytes(cap, false);
-    cudaError_t e = cudaFuncSetAttribute(k_run<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_run<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_run<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)phase_smem_bytes(cap, true));
+    cudaError_t e = cudaSuccess;
+    for (int prec = 0; prec < 2; ++prec)
+        for (int site = 0; site < 2; ++site)
+            for (int grain = 0; grain < 2; ++grain) {
+                if (site && prec) continue;
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(run_kernel(prec, site, grain), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)phase_smem_bytes(cap, site));
+            }
     return e;
 }
 
 // Blocks of the run pass: as many as fit on the GPU at once (it strides over
 // the screened fragments).
-cudaError_t run_pass_blocks(int prec, int cap, bool site, int* blocks)
+cudaError_t run_pass_blocks(int prec, int cap, bool site, bool grain, int* blocks)
 {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) {
-        const size_t smem = phase_smem_bytes(cap, site);
-        if (site) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_run<0, true>, 128, smem);
-        else if (prec == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_run<0, false>, 128, smem);
-        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_run<1, false>, 128, smem);
-    }
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, run_kernel(site ? 0 : prec, site, grain), 128,
+                                                          phase_smem_bytes(cap, site));
     *blocks = std::max(1, sms * std::max(per_sm, 1));
     return e;
 }
@@ -810,35 +933,29 @@ cudaError_t run_pass_blocks(int prec, int cap, bool site, int* blocks)
 // One window of the colour-phase path: set-up, then screen and run for each of
 // the 8 phases.  Every argument is fixed for the batch (the window offset is
 // read from wctl on the device), so the sequence can be captured in a graph.
-// `site` non-null selects the site-energy run pass (plain form).
+// `sa.field` non-null selects the site-energy run pass (plain form),
+// `sa.gbound` non-null the grain tables.
 cudaError_t launch_window(int prec, const RepDesc* d_descs, int nrep, int64_t total_items,
                           unsigned long long* wctl, uint32_t* perms, ActEntry* act, int32_t* act_count,
                           uint32_t* occ, VacRec* recs, int32_t* counts, int32_t* tracer,
                           unsigned long long* stats, uint32_t* status, int cap, int run_blocks,
-                          const SiteArgs* site, cudaStream_t st)
+                          const SiteArgs& sa, cudaStream_t st)
 {
     if (total_items <= 0) return cudaSuccess;
+    const bool site = sa.field != nullptr, grain = sa.gbound != nullptr;
     k_window_setup<<<(nrep + 255) / 256, 256, 0, st>>>(d_descs, nrep, wctl, perms, act_count);
     const int64_t sblocks = (total_items + 255) / 256;
-    const size_t smem = phase_smem_bytes(cap, site != nullptr);
-    const SiteArgs none{};
+    const size_t smem = phase_smem_bytes(cap, site);
+    const RunFn run = run_kernel(site ? 0 : prec, site, grain);
     for (int p = 0; p < 8; ++p) {
-        if (site) {
+        if (site || prec == 0)
             k_screen<0><<<(unsigned)sblocks, 256, 0, st>>>(d_descs, nrep, total_items, p, wctl, perms, counts, act,
                                                            act_count);
-            k_run<0, true><<<run_blocks, 128, smem, st>>>(d_descs, act, act_count, p, wctl, occ, recs, counts,
-                                                          tracer, stats, status, cap, *site);
-        } else if (prec == 0) {
-            k_screen<0><<<(unsigned)sblocks, 256, 0, st>>>(d_descs, nrep, total_items, p, wctl, perms, counts, act,
-                                                           act_count);
-            k_run<0, false><<<run_blocks, 128, smem, st>>>(d_descs, act, act_count, p, wctl, occ, recs, counts,
-                                                           tracer, stats, status, cap, none);
-        } else {
+        else
             k_screen<1><<<(unsigned)sblocks, 256, 0, st>>>(d_descs, nrep, total_items, p, wctl, perms, counts, act,
                                                            act_count);
-            k_run<1, false><<<run_blocks, 128, smem, st>>>(d_descs, act, act_count, p, wctl, occ, recs, counts,
-                                                           tracer, stats, status, cap, none);
-        }
+        run<<<run_blocks, 128, smem, st>>>(d_descs, act, act_count, p, wctl, occ, recs, counts, tracer, stats, status,
+                                           cap, sa);
     }
     return cudaGetLastError();
 }

@@ -14,12 +14,14 @@ cudaError_t launch_init(const RepDesc& D, int b_bits, int64_t n_vac, int64_t n_t
                         VacRec* recs, int32_t* counts, int cap, uint32_t* status, cudaStream_t st);
 size_t phase_smem_bytes(int cap, bool site);
 cudaError_t phase_prepare(int cap);
-cudaError_t run_pass_blocks(int prec, int cap, bool site, int* blocks);
+cudaError_t run_pass_blocks(int prec, int cap, bool site, bool grain, int* blocks);
 cudaError_t launch_window(int prec, const RepDesc* d_descs, int nrep, int64_t total_items,
                           unsigned long long* wctl, uint32_t* perms, ActEntry* act, int32_t* act_count,
                           uint32_t* occ, VacRec* recs, int32_t* counts, int32_t* tracer,
                           unsigned long long* stats, uint32_t* status, int cap, int run_blocks,
-                          const SiteArgs* site, cudaStream_t st);
+                          const SiteArgs& sa, cudaStream_t st);
+cudaError_t launch_grains(const RepDesc* d_descs, int nrep, int64_t ncell_total, int n_grains, int width, int64_t* X,
+                          int32_t* grain, uint8_t* gb, cudaStream_t st);
 cudaError_t launch_init_dopants(const RepDesc& D, int b_bits, int64_t n_fe, uint8_t* fe, cudaStream_t st);
 cudaError_t launch_site_field(const RepDesc* d_descs, int nrep, const VacRec* recs, const int32_t* counts,
                               int64_t nfrag_total, int cap, int64_t nsite_total, const uint8_t* fe,
@@ -31,8 +33,9 @@ cudaError_t launch_null_scatter(const RepDesc* d_descs, int nrep, int64_t total_
                                 VacRec* recs, int32_t* counts, int64_t nfrag_total, int cap, uint32_t* status,
                                 cudaStream_t st);
 cudaError_t launch_null_step(const RepDesc* d_descs, int nrep, int64_t total_vac, int64_t total_picks, VacRec* vac,
-                             uint32_t* occ, const NbTable& nbt, unsigned long long* acc, NullProp* props,
-                             unsigned long long* claims, int32_t* tracer, double* theta,
+                             uint32_t* occ, const NbTable& nbt, const uint8_t* gb, unsigned long long* acc,
+                             NullProp* props,
+                             unsigned long long* claims, int32_t* tracer, double* theta, double* nE,
                              unsigned long long* stats, unsigned long long* nctl, cudaStream_t st);
 cudaError_t launch_moments(const RepDesc& D, int species, const uint32_t* occ, const VacRec* recs,
                            const int32_t* counts, const int32_t* tracer, int cap,

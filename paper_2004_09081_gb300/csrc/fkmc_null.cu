@@ -78,9 +78,10 @@ __device__ __forceinline__ int64_t lin(const RepDesc& D, int t, int x, int y, in
     return (((int64_t)t * D.L[2] + z) * D.L[1] + y) * D.L[0] + x;
 }
 
-// fixed-point rate of neighbour n of a vacancy at (t, x, y, z); 0 for a vacancy
-__device__ __forceinline__ uint64_t null_rate(const RepDesc& D, const NbTable& nbt, const uint32_t* occ, int t,
-                                              int x, int y, int z, int n)
+// fixed-point rate of neighbour n of a vacancy at (t, x, y, z); 0 for a
+// vacancy; the raised table for a hop touching a grain-boundary cell (gb)
+__device__ __forceinline__ uint64_t null_rate(const RepDesc& D, const NbTable& nbt, const uint32_t* occ,
+                                              const uint8_t* gb, int t, int x, int y, int z, int n)
 {
     const NbEntry nb = nbt.e[t][n];
     const int jx = wrapc(x + nb.dc[0], D.L[0]);
@@ -88,7 +89,10 @@ __device__ __forceinline__ uint64_t null_rate(const RepDesc& D, const NbTable& n
     const int jz = wrapc(z + nb.dc[2], D.L[2]);
     const uint32_t w = __ldcg(occ + occ_word(D, nb.t2, jx, jy, jz));
     const int code = (int)((w >> occ_shift(jx)) & 3u);
-    return code == SP_V ? 0ull : D.qn[code * 3 + nb.d[2] + 1];
+    if (code == SP_V) return 0ull;
+    const int ty = code * 3 + nb.d[2] + 1;
+    if (gb && (gb[cell_index(D, x, y, z)] | gb[cell_index(D, jx, jy, jz)])) return D.qng[ty];
+    return D.qn[ty];
 }
 
 // step tag of step k of a call: later steps have smaller tags, so a claim left
@@ -139,7 +143,8 @@ __global__ void k_null_scatter(const RepDesc* __restrict__ descs, int nrep, int6
 // acc[3 r + 0] = R_tot, acc[3 r + 1] = R_max, acc[3 r + 2] = N_updated
 __global__ void __launch_bounds__(256) k_null_rates(const RepDesc* __restrict__ descs, int nrep, int64_t total_vac,
                                                     const VacRec* __restrict__ vac, const uint32_t* occ, NbTable nbt,
-                                                    unsigned long long* acc, unsigned long long* nctl)
+                                                    const uint8_t* __restrict__ gb, unsigned long long* acc,
+                                                    unsigned long long* nctl)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) {  // nothing else in this launch reads nctl
         nctl[1] = nctl[0];
@@ -154,7 +159,7 @@ __global__ void __launch_bounds__(256) k_null_rates(const RepDesc* __restrict__ 
         int t, x, y, z;
         split_key(vac[i].key, t, x, y, z);
 #pragma unroll
-        for (int n = 0; n < 8; ++n) R += null_rate(D, nbt, occ, t, x, y, z, n);
+        for (int n = 0; n < 8; ++n) R += null_rate(D, nbt, occ, gb, t, x, y, z, n);
     }
     const int r0 = __shfl_sync(0xffffffffu, r, 0);
     if (__all_sync(0xffffffffu, valid && r == r0)) {  // one replica: reduce in the warp first
@@ -176,8 +181,10 @@ __global__ void __launch_bounds__(256) k_null_rates(const RepDesc* __restrict__ 
 
 __global__ void __launch_bounds__(256) k_null_propose(const RepDesc* __restrict__ descs, int nrep, int64_t total_picks,
                                                       const VacRec* __restrict__ vac, const uint32_t* occ, NbTable nbt,
-                                                      const unsigned long long* acc, NullProp* props,
-                                                      unsigned long long* claims, const unsigned long long* nctl)
+                                                      const uint8_t* __restrict__ gb, const unsigned long long* acc,
+                                                      NullProp* props,
+                                                      unsigned long long* claims, double* nE,
+                                                      const unsigned long long* nctl)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= total_picks) return;
@@ -192,14 +199,19 @@ __global__ void __launch_bounds__(256) k_null_propose(const RepDesc* __restrict_
     split_key(vac[D.vac_off + id].key, t, x, y, z);
     const U64x4 blk = philox4x64(step, (uint64_t)p, 0, 0, D.seed, key_word(D.replica, PURPOSE_NULL));
     const unsigned long long target = __umul64hi(blk.x[0], acc[3 * r + 1]);
+    unsigned long long q[8];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) q[n] = null_rate(D, nbt, occ, gb, t, x, y, z, n);  // 8 independent loads
     unsigned long long P = 0ull;
     int sel = -1;
+#pragma unroll
     for (int n = 0; n < 8; ++n) {
-        P += null_rate(D, nbt, occ, t, x, y, z, n);
-        if (P > target) {
-            sel = n;
-            break;
-        }
+        P += q[n];
+        if (sel < 0 && P > target) sel = n;
+    }
+    if (p == 0) {  // the step's clock variate, off the critical path of the last apply block
+        const U64x4 tb = philox4x64(step, ~0ull, 0, 0, D.seed, key_word(D.replica, PURPOSE_NULL));
+        nE[r] = neglog64(tb.x[0]);
     }
     NullProp pr;
     pr.v = id;
@@ -216,14 +228,14 @@ __global__ void __launch_bounds__(256) k_null_propose(const RepDesc* __restrict_
 }
 
 // clock of replica r after a step: + -ln(r') / R_tot * N_updated, in units of
-// 1/k32max (r' from Philox (step, 2^64-1)); hop counter; accumulators cleared
+// 1/k32max (E = -ln(r'), r' from Philox (step, 2^64-1), drawn by the propose
+// pass); hop counter; accumulators cleared
 __device__ __forceinline__ void null_time(const RepDesc& D, int r, unsigned long long* acc, double* theta,
-                                          unsigned long long* stats, uint64_t k)
+                                          unsigned long long* stats, const double* nE)
 {
     const unsigned long long Rtot = __ldcg(acc + 3 * r), n = __ldcg(acc + 3 * r + 2);
     if (Rtot > 0ull) {
-        const U64x4 blk = philox4x64(D.null_step + k, ~0ull, 0, 0, D.seed, key_word(D.replica, PURPOSE_NULL));
-        const double E = neglog64(blk.x[0]);
+        const double E = __ldcg(nE + r);
         const double dth = __dmul_rn(__dmul_rn(__ddiv_rn(E, __ull2double_rn(Rtot)), D.two_pow_Fn), __ull2double_rn(n));
         theta[r] = __dadd_rn(theta[r], dth);
     }
@@ -237,7 +249,8 @@ __global__ void __launch_bounds__(256) k_null_apply(const RepDesc* __restrict__ 
                                                     const NullProp* __restrict__ props,
                                                     const unsigned long long* claims, int32_t* tracer,
                                                     unsigned long long* acc, double* theta,
-                                                    unsigned long long* stats, unsigned long long* nctl)
+                                                    unsigned long long* stats, const double* nE,
+                                                    unsigned long long* nctl)
 {
     __shared__ bool last;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -294,7 +307,7 @@ __global__ void __launch_bounds__(256) k_null_apply(const RepDesc* __restrict__ 
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int q = threadIdx.x; q < nrep; q += blockDim.x) null_time(descs[q], q, acc, theta, stats, k);
+    for (int q = threadIdx.x; q < nrep; q += blockDim.x) null_time(descs[q], q, acc, theta, stats, nE);
     if (threadIdx.x == 0) nctl[2] = 0ull;
 }
 
@@ -329,15 +342,16 @@ cudaError_t launch_null_scatter(const RepDesc* d_descs, int nrep, int64_t total_
 // One step of every replica (three launches; fixed arguments, so a graph can
 // hold it).  nctl[2] must be 0 before the first step.
 cudaError_t launch_null_step(const RepDesc* d_descs, int nrep, int64_t total_vac, int64_t total_picks, VacRec* vac,
-                             uint32_t* occ, const NbTable& nbt, unsigned long long* acc, NullProp* props,
-                             unsigned long long* claims, int32_t* tracer, double* theta,
+                             uint32_t* occ, const NbTable& nbt, const uint8_t* gb, unsigned long long* acc,
+                             NullProp* props,
+                             unsigned long long* claims, int32_t* tracer, double* theta, double* nE,
                              unsigned long long* stats, unsigned long long* nctl, cudaStream_t st)
 {
-    k_null_rates<<<grid_of(total_vac), NT, 0, st>>>(d_descs, nrep, total_vac, vac, occ, nbt, acc, nctl);
-    k_null_propose<<<grid_of(total_picks), NT, 0, st>>>(d_descs, nrep, total_picks, vac, occ, nbt, acc, props, claims,
-                                                        nctl);
+    k_null_rates<<<grid_of(total_vac), NT, 0, st>>>(d_descs, nrep, total_vac, vac, occ, nbt, gb, acc, nctl);
+    k_null_propose<<<grid_of(total_picks), NT, 0, st>>>(d_descs, nrep, total_picks, vac, occ, nbt, gb, acc, props,
+                                                        claims, nE, nctl);
     k_null_apply<<<grid_of(total_picks), NT, 0, st>>>(d_descs, nrep, total_picks, vac, occ, nbt, props, claims, tracer,
-                                                      acc, theta, stats, nctl);
+                                                      acc, theta, stats, nE, nctl);
     return cudaGetLastError();
 }
 

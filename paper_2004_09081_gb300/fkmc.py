@@ -43,6 +43,10 @@ class kmc_site_energy(C.Structure):
                 ("n_fe", C.c_int32), ("fe_d2", C.c_int32 * FKMC_MAX_SHELLS), ("fe_eV", C.c_double * FKMC_MAX_SHELLS)]
 
 
+class kmc_grains(C.Structure):
+    _fields_ = [("n_grains", C.c_int32), ("width", C.c_int32), ("barrier_eV", C.c_double)]
+
+
 class kmc_barrier_table(C.Structure):
     _fields_ = [("Ea_O_eV", C.c_double), ("Ea_H_eV", C.c_double), ("prefactor", C.c_double),
                 ("q_O", C.c_double), ("q_H", C.c_double)]
@@ -103,6 +107,8 @@ _SIGNATURES = {
     "kmc_write_dopants": (C.c_int, [_P, _I32, _P, _SZ]),
     "kmc_read_site_field": (C.c_int, [_P, _I32, _P, _SZ]),
     "kmc_site_shells": (C.c_int, [_P, _I32, _P, _I32, _P]),
+    "kmc_set_grains": (C.c_int, [_P, _P]),
+    "kmc_read_grains": (C.c_int, [_P, _I32, _P, _P, _SZ]),
     "kmc_destroy": (C.c_int, [_P]),
     "kmc_last_error": (C.c_char_p, []),
 }
@@ -315,6 +321,22 @@ def kmc_site_shells(vv, fe, t: int) -> np.ndarray:
     return out[: n.value]
 
 
+def kmc_set_grains(h, n_grains: int, width: int = 1, barrier_eV: float = 0.2):
+    """Voronoi grains; n_grains <= 1 turns them off."""
+    if n_grains <= 1:
+        _check(load().kmc_set_grains(h, None))
+        return
+    g = kmc_grains(int(n_grains), int(width), float(barrier_eV))
+    _check(load().kmc_set_grains(h, C.byref(g)))
+
+
+def kmc_read_grains(h, r: int, ncell: int):
+    grain = np.zeros(ncell, np.int32)
+    bnd = np.zeros(ncell, np.uint8)
+    _check(load().kmc_read_grains(h, r, _ptr(grain), _ptr(bnd), ncell))
+    return grain, bnd
+
+
 def kmc_read_dopants(h, r: int, ncell: int) -> np.ndarray:
     out = np.zeros(ncell, np.uint8)
     _check(load().kmc_read_dopants(h, r, _ptr(out), ncell))
@@ -449,6 +471,12 @@ class Batch:
 
     def set_site_energy(self, vv=(), fe=()):
         kmc_set_site_energy(self.h, vv, fe)
+
+    def set_grains(self, n_grains, width=1, barrier_eV=0.2):
+        kmc_set_grains(self.h, n_grains, width, barrier_eV)
+
+    def grains(self, r=0):
+        return kmc_read_grains(self.h, r, self.nsite(r) // 3)
 
     def dopants(self, r=0):
         return kmc_read_dopants(self.h, r, self.nsite(r) // 3)

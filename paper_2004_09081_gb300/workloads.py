@@ -99,6 +99,19 @@ def um_batio3_bias(seed: int = 0, L: int = 2500) -> Workload:
     return Workload(f"batio3_{L}c_bias", [r], edge=8, precision=1, windows=4)
 
 
+def um_grains(seed: int = 0, L=(1600, 400, 2400), n_grains: int = 16) -> Workload:
+    """The paper's mu-scale BaTiO3 model: 641.6 x 160.4 x 962.4 nm = 1600 x 400 x
+    2400 cells (7.68e9 atoms), 0.1% O vacancies, Voronoi grains (count unstated:
+    16) whose one-cell boundary layer raises the barrier by 0.2 eV (0.9 eV in
+    total), the bias of +-10 V over the z extent as a uniform field
+    (20 V / 962.4 nm = 2.08e7 V/m), 400 K, fragments of 8^3 cells, mixed form."""
+    nsite = 3 * L[0] * L[1] * L[2]
+    Ez = 20.0 / (L[2] * A_BATIO3 * 1e-10)
+    r = Replica(tuple(L), A_BATIO3, round_half_up(0.001 * nsite), 0, 400.0, 0.70, 0.70, field_z=Ez)
+    return Workload(f"batio3_{L[0]}x{L[1]}x{L[2]}c_grains", [r], edge=8, precision=1, windows=2,
+                    notes={"grains": (n_grains, 1, 0.2)})
+
+
 def null_batio3(seed: int = 0) -> Workload:
     """The 128^3 BaTiO(3-x)H_x lattice (x = 0.05: 104,858 H; 0.3% vacancies:
     18,874 V; 400 K; barriers 0.70 / 0.35 eV) run with the paper's atom-based
@@ -157,4 +170,4 @@ def fe_srtio3(seed: int = 0, L: int = 96) -> Workload:
 
 ALL = {"small": small_srtio3, "sweep": srtio3_h_sweep, "batched": batched_batio3,
        "bulk": bulk_batio3, "um": um_batio3_bias, "fe": fe_srtio3, "null": null_batio3,
-       "htrend": h_trend}
+       "htrend": h_trend, "umgrains": um_grains}
