@@ -138,10 +138,13 @@ __device__ __forceinline__ WarpSmem carve(unsigned char* base, int cap)
     return s;
 }
 
+// Per-warp shared memory in bytes.  Kept in 32-bit arithmetic (cap <= 256):
+// the run pass multiplies it by the warp index for its base address, and a
+// 64-bit product there costs the kernel registers it cannot spare.
 __host__ __device__ inline size_t warp_smem_bytes(int cap, bool site)
 {
-    const size_t b = site ? warp_rate_offset(cap) + 64 * (size_t)cap : 35 * (size_t)cap;
-    return (b + 15) / 16 * 16;
+    const int b = site ? (35 * cap + 7) / 8 * 8 + 64 * cap : 35 * cap;
+    return (size_t)((b + 15) / 16) * 16;
 }
 
 // Rate types of every event of the fragment, read from the occupancy words
