@@ -81,6 +81,7 @@ def lib():
             "orc_null_run": (C.c_int, [P, u64, i64]),
             "orc_get_null": (None, [P, P, P, P, P]),
             "orc_set_grains": (C.c_int, [P, C.c_int, C.c_int, d]),
+            "orc_set_elec": (C.c_int, [P, P, P]),
             "orc_get_grains": (None, [P, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -198,6 +199,19 @@ class Lattice:
         F = C.c_int32(0)
         lib().orc_get_null(self._h, C.byref(th), C.byref(t), C.byref(st), C.byref(F))
         return {"theta": th.value, "t": t.value, "steps": st.value, "F": F.value}
+
+    # ---------------------------------------------- electrostatics (mu-scale model)
+    def set_elec(self, u=None, g=None):
+        """Frozen electrostatic field: u = rint(q phi 1e4) per O site and the
+        self table g[3][8] (oracle/poisson.py); None turns it off."""
+        if u is None:
+            lib().orc_set_elec(self._h, None, None)
+            return
+        self._elec_u = np.ascontiguousarray(u, dtype=np.int32)
+        self._elec_g = np.ascontiguousarray(g, dtype=np.int32)
+        assert self._elec_u.size == self.nsite and self._elec_g.size == 24
+        if lib().orc_set_elec(self._h, _ptr(self._elec_u), _ptr(self._elec_g)):
+            raise ValueError("electrostatics need the plain form")
 
     # ---------------------------------------------- grains (mu-scale model)
     def set_grains(self, n_grains: int, width: int = 1, barrier_eV: float = 0.2):

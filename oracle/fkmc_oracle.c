@@ -269,6 +269,9 @@ typedef struct {
     double rate_ntau;
     /* site-energy interactions (plain form only) */
     int site_on;
+    int elec_on;        /* electrostatic potential of the vacancy charges (frozen field) */
+    int32_t* elec_u;    /* q phi of every O site, 1e-4 eV units */
+    int32_t elec_g[3][8]; /* a hop's share of the vacancy's own potential, 1e-4 eV units */
     uint8_t* fe;    /* dopant (Fe) on the B site of each cell, [z][y][x] */
     int n_vv, n_fe; /* offsets to the O sites / B sites inside the energy shells */
     struct { int t2; int dc[3]; int32_t e; } vv[3][512];
@@ -434,6 +437,7 @@ void orc_destroy(orc_lattice* lat)
     free(lat->claimed);
     free(lat->grain);
     free(lat->gbound);
+    free(lat->elec_u);
     free(lat);
 }
 
@@ -493,7 +497,7 @@ int orc_set_rates(orc_lattice* lat, double Ea_O, double Ea_H, double A, double q
         if ((i < 3 || nH > 0) && lat->k64[i] > kmax) kmax = lat->k64[i];
         if (lat->k32[i] > kmax32) kmax32 = lat->k32[i];
     }
-    if (lat->site_on && precision != 0) return -1;
+    if ((lat->site_on || lat->elec_on) && precision != 0) return -1;
     lat->T = T_K;
     {
         double a[8] = {Ea_O, Ea_H, A, q_O, q_H, T_K, Ez_Vpm, a_ang};
@@ -689,13 +693,31 @@ int orc_site_shells(const orc_lattice* lat, int t, int32_t* out, int max_rows)
     return k;
 }
 
+/* Electrostatics (the Poisson-solved potential of the mu-scale model, with
+ * the vacancy charges as its source): a frozen field u(s) = rint(q phi(s) 1e4)
+ * joins E_site, and a hop s -> j (neighbour n of a type-t site) leaves out the
+ * vacancy's own potential: its energy difference loses g[t][n] =
+ * rint(q^2 (G(j, s) - G(s, s)) 1e4).  u and g are inputs (oracle/poisson.py
+ * computes them); NULL u turns the term off. */
+int orc_set_elec(orc_lattice* lat, const int32_t* u, const int32_t* g)
+{
+    if (!u) { lat->elec_on = 0; return 0; }
+    if (lat->rates_set && lat->precision != 0) return -1;
+    free(lat->elec_u);
+    lat->elec_u = (int32_t*)malloc(sizeof(int32_t) * (size_t)lat->nsite);
+    memcpy(lat->elec_u, u, sizeof(int32_t) * (size_t)lat->nsite);
+    memcpy(lat->elec_g, g, sizeof(lat->elec_g));
+    lat->elec_on = 1;
+    return 0;
+}
+
 /* E_site of site s in energy units, the site `exclude` counted as empty */
 int64_t orc_site_energy(const orc_lattice* lat, int64_t s, int64_t exclude)
 {
-    if (!lat->site_on) return 0;
+    if (!lat->site_on && !lat->elec_on) return 0;
     int t, c[3];
     site_coords(lat, s, &t, c);
-    int64_t E = 0;
+    int64_t E = lat->elec_on ? lat->elec_u[s] : 0;
     for (int i = 0; i < lat->n_vv; i++) {
         int64_t u = site_index(lat, lat->vv[t][i].t2, wrap(c[0] + lat->vv[t][i].dc[0], lat->L[0]),
                                wrap(c[1] + lat->vv[t][i].dc[1], lat->L[1]),
@@ -797,10 +819,12 @@ static int boundary_hop(const orc_lattice* lat, int64_t s, int64_t j)
     return lat->gbound[s % ncell] || lat->gbound[j % ncell];
 }
 
-/* rate of the event (vacancy at s, ion at neighbour j) of table rate k0 */
-static double site_rate(const orc_lattice* lat, int64_t s, int64_t j, double k0)
+/* rate of the event (vacancy at s of type t, ion at its neighbour n = j) of
+ * table rate k0 */
+static double site_rate(const orc_lattice* lat, int64_t s, int64_t j, int t, int n, double k0)
 {
     int64_t m = orc_site_energy(lat, j, s) - orc_site_energy(lat, s, -1);
+    if (lat->elec_on) m -= lat->elec_g[t][n];
     int64_t m1 = m >= 0 ? m / 512 : -((-m + 511) / 512);
     int64_t m0 = m - 512 * m1;
     double c = 1e-4 / (2.0 * (KB_EV * lat->T));
@@ -829,8 +853,10 @@ static double event_rate64(const orc_lattice* lat, int64_t s, int n)
     if (ty < 0) return 0.0;
     int64_t j = neighbour_site(lat, s, n);
     double k0 = boundary_hop(lat, s, j) ? lat->k64g[ty] : lat->k64[ty];
-    if (!lat->site_on) return k0;
-    return site_rate(lat, s, j, k0);
+    if (!lat->site_on && !lat->elec_on) return k0;
+    int t, c[3];
+    site_coords(lat, s, &t, c);
+    return site_rate(lat, s, j, t, n, k0);
 }
 
 /* fixed-point rate of the event (s, n) of the mixed form */
@@ -1157,7 +1183,7 @@ static uint64_t null_q(const orc_lattice* lat, const uint64_t q[12], int64_t s, 
 
 int orc_null_run(orc_lattice* lat, uint64_t steps, int64_t n_frg)
 {
-    if (!lat->rates_set || lat->site_on || n_frg < 1) return -1;
+    if (!lat->rates_set || lat->site_on || lat->elec_on || n_frg < 1) return -1;
     int64_t nv = orc_n_records(lat);
     if (nv == 0) { lat->null_step += steps; return 0; }
     orc_rec* v = (orc_rec*)malloc(sizeof(orc_rec) * nv);
