@@ -231,6 +231,50 @@ int kmc_write_dopants(kmc_batch* b, int32_t r, const uint8_t* host_cells, size_t
  * index as in kmc_read_state (FKMC_ESTATE while the interactions are off). */
 int kmc_read_site_field(kmc_batch* b, int32_t r, int32_t* host_field, size_t n);
 
+/* Electrostatics (the mu-scale model section of the paper solves a Poisson
+ * equation for the electrostatic potential).  Reading: the source is the
+ * vacancies' own charge q_vac e, each split in halves between the two B sites
+ * (cell corners) of its O site's bond, against a uniform neutralising
+ * background, on the periodic grid of B sites (spacing a):
+ *   6 phi(n) - sum_{6 neighbours} phi(n') = Q(n) / (eps0 eps_r a)      [V],
+ * solved by a geometric multigrid (`cycles` V-cycles, red-black Gauss-Seidel,
+ * full weighting, trilinear prolongation; deterministic).  The bias of the
+ * paper stays the uniform field of kmc_set_barriers.  A vacancy at O site s
+ * (the mean potential of its two nodes, phi(s)) has the energy
+ * u(s) = rint(q_vac phi(s) 1e4) in 1e-4 eV units, added to the site energy of
+ * kmc_set_site_energy; a hop s -> j of a type-t site to its neighbour n also
+ * leaves out the vacancy's own potential, g[t][n] = rint(q_vac^2 (G(j, s) -
+ * G(s, s)) 1e4), G the potential of a unit charge's deposit (one table per
+ * replica, from three unit-charge solves).  The field is frozen between
+ * refreshes: every `refresh_windows` windows kmc_run solves again from the
+ * current vacancies (0: never; u stays as last solved or written).
+ * Plain form only; the site-energy run pass of the colour-phase kernels. */
+typedef struct {
+    double eps_r;             /* relative permittivity, > 0 */
+    double q_vac;             /* vacancy charge in e (+2 for an O vacancy) */
+    int32_t refresh_windows;  /* windows between solves; 0 = no automatic solve */
+    int32_t cycles;           /* V-cycles per solve, 1..200 (12 reach a relative residual ~1e-10) */
+} kmc_electrostatics;
+
+/* Turn electrostatics on (or off with NULL) for every replica and solve once.
+ * Extra device memory: 4 bytes per O site, about 3 doubles per cell for the
+ * multigrid levels of the largest replica.  Errors: FKMC_EINVAL for the mixed
+ * form or bad parameters; FKMC_ENOMEM; FKMC_ECUDA. */
+int kmc_set_electrostatics(kmc_batch* b, const kmc_electrostatics* e);
+
+/* Solve the potential of replica r's current vacancies (kmc_set_electrostatics
+ * gives the parameters) without touching the state: phi at every B node (V),
+ * index (z ny + y) nx + x, n = nx ny nz, and the relative residual
+ * max|f - A phi| / max|f| (may be NULL).  FKMC_ESTATE without electrostatics. */
+int kmc_solve_potential(kmc_batch* b, int32_t r, double* phi, size_t n, double* resid_rel);
+
+/* The electrostatic energies u (int32 per O site, site index as in
+ * kmc_read_state) of replica r and its own-potential table g (24 int32,
+ * [t][n]; g may be NULL): read them, or write them (the caller's own potential;
+ * set refresh_windows to 0 to keep them). */
+int kmc_read_potential_energy(kmc_batch* b, int32_t r, int32_t* u, size_t n, int32_t* g);
+int kmc_write_potential_energy(kmc_batch* b, int32_t r, const int32_t* u, size_t n, const int32_t* g);
+
 /* Grains (the mu-scale model section of the paper): a periodic Voronoi
  * tessellation of each replica's cells.  Seed g of replica r sits at
  * X_d = mulhi(y_d, 256 L_d) in units of 1/256 cell, y the Philox4x64-10 block

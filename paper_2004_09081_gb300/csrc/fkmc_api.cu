@@ -162,6 +162,18 @@ struct kmc_batch {
     SiteOff* d_bo = nullptr;
     double* btab = nullptr;          // Boltzmann tables of every replica
     size_t btab_bytes = 0;
+    // electrostatics (mu-scale model): potential of the vacancy charges, frozen between refreshes
+    bool elec_on = false;
+    kmc_electrostatics elec{};
+    int32_t* elec_u = nullptr;          // q phi per O site, 1e-4 eV units (batch-wide site index)
+    int32_t* d_elec_g = nullptr;        // [replica][3][8] own-potential share of a hop
+    std::vector<int32_t> elec_g;        // host copy
+    unsigned* d_umax = nullptr;         // max |u| of the last refresh
+    int64_t elec_umax = 0;
+    uint64_t elec_age = 0;              // windows since the last refresh
+    MgPlan mg{};
+    MgBuffers mgb{};
+    int64_t mg_total = -1;
     // grains (mu-scale model): boundary cells raise the barrier of hops touching them
     bool grains_on = false;
     kmc_grains grains{};
@@ -244,6 +256,9 @@ struct kmc_batch {
 
 namespace {
 
+// the site-energy run pass is on: shells, dopant energies or electrostatics
+bool site_path(const kmc_batch* b) { return b->site_on || b->elec_on; }
+
 int check_status(kmc_batch* b)
 {
     uint32_t s = 0;
@@ -310,7 +325,7 @@ int plan_residency(kmc_batch* b)
     }
     b->rclass.clear();
     const bool allowed = b->opts.precision == FKMC_MIXED && b->opts.schedule != 1 &&
-                         b->cap <= RESIDENT_MAX_SLOTS && !b->site_on && !b->grains_on;
+                         b->cap <= RESIDENT_MAX_SLOTS && !site_path(b) && !b->grains_on;
     // launch classes: (shared-memory bound, threads); a replica takes the first
     // class its state fits, so small replicas pack several CTAs per SM and the
     // largest get the most warps that still fit beside their state.  The
@@ -475,11 +490,19 @@ int make_shells(const kmc_site_energy* e, ShellTables* out)
     return FKMC_OK;
 }
 
+// bound on |E_site| over every site: shells plus the electrostatic term
+int64_t energy_bound(const kmc_batch* b)
+{
+    int64_t g = 0;
+    for (int32_t v : b->elec_g) g = std::max<int64_t>(g, v < 0 ? -(int64_t)v : v);
+    return b->e_bound + (b->elec_on ? b->elec_umax + g : 0);
+}
+
 // Boltzmann tables of every replica: lo[m0] = exp(-m0 c), hi[i] = exp(-512 (i - mid) c),
 // c = 1e-4 / (2 kB T); |m| <= 2 e_bound, so m >> 9 stays within [-mid, mid].
 int build_btab(kmc_batch* b)
 {
-    const int mid = (int)((2 * b->e_bound + 511) / 512) + 1;
+    const int mid = (int)((2 * energy_bound(b) + 511) / 512) + 1;
     const int len = 2 * mid + 1;
     const size_t per = (size_t)BOLTZ_LO + len;
     std::vector<double> h(per * b->n);
@@ -513,6 +536,7 @@ SiteArgs site_args(const kmc_batch* b)
     a.n_vv = b->n_vv;
     a.e_self = b->e_self;
     a.gbound = b->grains_on ? b->gbound : nullptr;
+    a.g_elec = b->elec_on ? b->d_elec_g : nullptr;
     return a;
 }
 
@@ -547,8 +571,60 @@ int rebuild_field(kmc_batch* b)
     CK(launch_site_field(b->d_desc, b->n, b->recs, b->counts, b->nfrag_total, b->cap, b->nsite_total, b->fe, b->d_bo,
                          b->n_bo, a, b->st),
        "energy field");
+    if (b->elec_on) CK(elec_add(b->field, b->elec_u, b->nsite_total, b->st), "energy field");
     b->field_valid = true;
     return FKMC_OK;
+}
+
+void drop_window_graph(kmc_batch* b);
+
+// the Boltzmann tables must cover electrostatic energies up to |u| = um
+int elec_cover(kmc_batch* b, int64_t um)
+{
+    if (um <= b->elec_umax) return FKMC_OK;
+    b->elec_umax = 2 * um + 1024;
+    if (!b->rates_set) return FKMC_OK;  // kmc_set_barriers builds the tables
+    const double* before = b->btab;
+    int rc = build_btab(b);
+    if (rc) return rc;
+    rc = upload_desc(b);
+    if (rc) return rc;
+    if (b->btab != before) drop_window_graph(b);
+    return FKMC_OK;
+}
+
+// kernels of one refresh: per replica the solve (deposit, right-hand side,
+// V-cycles, mean) and the update
+uint64_t elec_launches(const kmc_batch* b)
+{
+    uint64_t k = 0;
+    for (int r = 0; r < b->n; ++r) {
+        const MgPlan p = mg_plan(b->desc[r].L[0], b->desc[r].L[1], b->desc[r].L[2]);
+        k += 2 + (uint64_t)b->elec.cycles * mg_cycle_kernels(p) + 3 + 1;
+    }
+    return k;
+}
+
+// Potential of every replica's vacancy charges (multigrid), then u and the
+// energy field moved to it; the Boltzmann tables grow if the bound does.
+int elec_refresh(kmc_batch* b)
+{
+    CK(cudaMemsetAsync(b->d_umax, 0, sizeof(unsigned), b->st), "memset");
+    for (int r = 0; r < b->n; ++r) {
+        const RepDesc& D = b->desc[r];
+        const MgPlan p = mg_plan(D.L[0], D.L[1], D.L[2]);
+        const double scale = 1.602176634e-19 / (8.8541878128e-12 * b->elec.eps_r * b->a_ang[r] * 1e-10);
+        CK(elec_solve(D, b->recs, b->counts, b->cap, b->n_vac[r], b->elec.q_vac, scale, b->elec.cycles, p, b->mgb,
+                      nullptr, b->st),
+           "potential solve");
+        CK(elec_update(D, b->mgb.phi, b->elec.q_vac, b->elec_u, b->field_valid ? b->field : nullptr, b->d_umax, b->st),
+           "potential update");
+    }
+    unsigned um = 0;
+    CK(cudaMemcpyAsync(&um, b->d_umax, sizeof um, cudaMemcpyDeviceToHost, b->st), "copy");
+    CK(cudaStreamSynchronize(b->st), "synchronize");
+    b->elec_age = 0;
+    return elec_cover(b, (int64_t)um);
 }
 
 // simulated time of the null-event form of replica r (s): its clock counts in 1/k32max
@@ -821,7 +897,7 @@ int kmc_set_barriers(kmc_batch* b, const kmc_barrier_table* tables, const double
     int rc = FKMC_OK;
     for (int r = 0; r < b->n && rc == FKMC_OK; ++r) rc = grain_tables(b, r);
     if (rc) return rc;
-    if (b->site_on) {
+    if (site_path(b)) {
         rc = build_btab(b);
         if (rc) return rc;
     }
@@ -856,35 +932,48 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
         }
     }
     uint64_t extra_launches = 0;
-    if (b->site_on && !b->field_valid) {
+    if (site_path(b) && !b->field_valid) {
         int rc0 = rebuild_field(b);
         if (rc0) return rc0;
         extra_launches = (b->n_vv > 0) + (b->n_bo > 0);
     }
-    const SiteArgs sargs = site_args(b);
-    if (b->any_global && windows > 0) {
-        if (!b->window_exec) {
-            // capture one window (set-up + 8 x (screen, run)) once; every argument is fixed
-            if (!b->cap_st) CK(cudaStreamCreateWithFlags(&b->cap_st, cudaStreamNonBlocking), "stream");
-            cudaGraph_t graph = nullptr;
-            CK(cudaStreamBeginCapture(b->cap_st, cudaStreamCaptureModeThreadLocal), "graph capture");
-            SiteArgs wa = sargs;
-            if (!b->site_on) wa.field = nullptr;  // the table-rate run pass
-            cudaError_t le = launch_window(b->opts.precision, b->d_desc, b->n, b->total_items, b->wctl, b->perms,
-                                           b->act, b->act_count, b->occ, b->recs, b->counts, b->tracer,
-                                           b->stats, b->status, b->cap, b->run_blocks, wa, b->cap_st);
-            cudaError_t ce = cudaStreamEndCapture(b->cap_st, &graph);
-            if (le != cudaSuccess) return cuda_fail(le, "window capture");
-            if (ce != cudaSuccess) return cuda_fail(ce, "window capture");
-            cudaError_t ie = cudaGraphInstantiate(&b->window_exec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (ie != cudaSuccess) {
-                b->window_exec = nullptr;
-                return cuda_fail(ie, "graph instantiate");
-            }
+    // capture one window (set-up + 8 x (screen, run)); every argument is fixed until
+    // the tables are rebuilt, which drops the graph
+    auto ensure_graph = [&]() -> int {
+        if (b->window_exec) return FKMC_OK;
+        if (!b->cap_st) CK(cudaStreamCreateWithFlags(&b->cap_st, cudaStreamNonBlocking), "stream");
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(b->cap_st, cudaStreamCaptureModeThreadLocal), "graph capture");
+        SiteArgs wa = site_args(b);
+        if (!site_path(b)) wa.field = nullptr;  // the table-rate run pass
+        cudaError_t le = launch_window(b->opts.precision, b->d_desc, b->n, b->total_items, b->wctl, b->perms, b->act,
+                                       b->act_count, b->occ, b->recs, b->counts, b->tracer, b->stats, b->status, b->cap,
+                                       b->run_blocks, wa, b->cap_st);
+        cudaError_t ce = cudaStreamEndCapture(b->cap_st, &graph);
+        if (le != cudaSuccess) return cuda_fail(le, "window capture");
+        if (ce != cudaSuccess) return cuda_fail(ce, "window capture");
+        cudaError_t ie = cudaGraphInstantiate(&b->window_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            b->window_exec = nullptr;
+            return cuda_fail(ie, "graph instantiate");
         }
+        return FKMC_OK;
+    };
+    if (b->any_global && windows > 0) {
         CK(cudaMemsetAsync(b->wctl, 0, sizeof(unsigned long long) * 2, b->st), "memset");
-        for (uint64_t wk = 0; wk < windows; ++wk) CK(cudaGraphLaunch(b->window_exec, b->st), "graph launch");
+        const uint64_t every = b->elec_on ? (uint64_t)b->elec.refresh_windows : 0;
+        for (uint64_t wk = 0; wk < windows; ++wk) {
+            if (every > 0 && b->elec_age >= every) {  // the potential follows the vacancies
+                int rc1 = elec_refresh(b);
+                if (rc1) return rc1;
+                extra_launches += elec_launches(b);
+            }
+            int rc2 = ensure_graph();
+            if (rc2) return rc2;
+            CK(cudaGraphLaunch(b->window_exec, b->st), "graph launch");
+            ++b->elec_age;
+        }
     }
     if (!b->rclass.empty() && windows > 0)
         for (auto& c : b->rclass) CK(cudaStreamWaitEvent(b->st, c.done, 0), "stream wait");
@@ -916,7 +1005,7 @@ int kmc_run_null(kmc_batch* b, uint64_t steps, int64_t n_frg, kmc_run_stats* sta
 {
     if (!b) return fail(FKMC_EINVAL, "null batch");
     if (!b->rates_set) return fail(FKMC_ESTATE, "kmc_set_barriers must come before kmc_run_null");
-    if (b->site_on) return fail(FKMC_EINVAL, "the null-event form has no site energies");
+    if (site_path(b)) return fail(FKMC_EINVAL, "the null-event form has no site energies or electrostatics");
     if (n_frg < 1) return fail(FKMC_EINVAL, "n_frg must be >= 1");
     if (steps > 0xFFFFFFF0ull) return fail(FKMC_EINVAL, "at most 2^32 - 16 steps per call");
     // per-replica tables and offsets
@@ -1164,6 +1253,7 @@ int kmc_write_state(kmc_batch* b, int32_t r, const uint8_t* host_occ, size_t n)
     b->n_vac[r] = nv;
     b->n_H[r] = nh;
     b->field_valid = false;
+    b->elec_age = UINT64_MAX / 2;  // the potential is solved again at the next refresh point
     if (b->rates_set) {
         int rc = plan_residency(b);
         if (rc) return rc;
@@ -1268,6 +1358,7 @@ int kmc_upload_state(kmc_batch* b, const void* host, size_t bytes)
        "state upload");
     CK(cudaStreamSynchronize(b->st), "synchronize");
     b->field_valid = false;
+    b->elec_age = UINT64_MAX / 2;
     return FKMC_OK;
 }
 
@@ -1277,8 +1368,13 @@ int kmc_set_site_energy(kmc_batch* b, const kmc_site_energy* e)
     if (!e || (e->n_vv == 0 && e->n_fe == 0)) {
         if (b->site_on) {
             b->site_on = false;
+            b->n_vv = b->n_bo = b->e_self = 0;  // electrostatics may keep the site-energy pass
+            b->e_bound = 0;
+            b->field_valid = false;
             drop_window_graph(b);
-            CK(run_pass_blocks(b->opts.precision, b->cap, false, b->grains_on, &b->run_blocks), "occupancy query");
+            CK(run_pass_blocks(site_path(b) ? FKMC_PLAIN : b->opts.precision, b->cap, site_path(b), b->grains_on,
+                               &b->run_blocks),
+               "occupancy query");
             if (b->rates_set) {
                 int rc = plan_residency(b);
                 if (rc) return rc;
@@ -1360,6 +1456,167 @@ int kmc_site_shells(const kmc_site_energy* e, int32_t t, int32_t* rows, int32_t 
     return FKMC_OK;
 }
 
+int kmc_set_electrostatics(kmc_batch* b, const kmc_electrostatics* e)
+{
+    if (!b) return fail(FKMC_EINVAL, "null batch");
+    if (!e) {
+        if (!b->elec_on) return FKMC_OK;
+        b->elec_on = false;
+        b->elec_g.clear();
+        b->elec_umax = 0;
+        b->field_valid = false;
+        drop_window_graph(b);
+        CK(run_pass_blocks(site_path(b) ? FKMC_PLAIN : b->opts.precision, b->cap, site_path(b), b->grains_on,
+                           &b->run_blocks),
+           "occupancy query");
+        if (b->rates_set) {
+            int rc = site_path(b) ? build_btab(b) : FKMC_OK;
+            if (!rc) rc = plan_residency(b);
+            if (!rc) rc = upload_desc(b);
+            if (rc) return rc;
+        }
+        return FKMC_OK;
+    }
+    if (b->opts.precision != FKMC_PLAIN) return fail(FKMC_EINVAL, "electrostatics need the plain form");
+    if (!(e->eps_r > 0.0) || !(e->eps_r <= 1e6) || !std::isfinite(e->q_vac) || std::fabs(e->q_vac) > 8.0 ||
+        e->cycles < 1 || e->cycles > 200 || e->refresh_windows < 0)
+        return fail(FKMC_EINVAL, "electrostatics: eps_r in (0, 1e6], |q| <= 8, 1..200 cycles, refresh >= 0");
+    // buffers: u per site, tables, the multigrid levels of the largest replica
+    int64_t total = 0, nodes = 0;
+    for (int r = 0; r < b->n; ++r) {
+        const MgPlan p = mg_plan(b->desc[r].L[0], b->desc[r].L[1], b->desc[r].L[2]);
+        total = std::max(total, p.total);
+        nodes = std::max<int64_t>(nodes, b->desc[r].nsite / 3);
+    }
+    if (!b->elec_u) b->elec_u = (int32_t*)b->dalloc(sizeof(int32_t) * b->nsite_total);
+    if (!b->d_elec_g) b->d_elec_g = (int32_t*)b->dalloc(sizeof(int32_t) * 24 * b->n);
+    if (!b->d_umax) b->d_umax = (unsigned*)b->dalloc(sizeof(unsigned));
+    if (!b->field) b->field = (int32_t*)b->dalloc(sizeof(int32_t) * b->nsite_total);
+    if (total > b->mg_total) {
+        for (void* q : {(void*)b->mgb.phi, (void*)b->mgb.f, (void*)b->mgb.r, (void*)b->mgb.cnt}) b->dfree(q);
+        b->mgb.phi = (double*)b->dalloc(sizeof(double) * total);
+        b->mgb.f = (double*)b->dalloc(sizeof(double) * total);
+        b->mgb.r = (double*)b->dalloc(sizeof(double) * total);
+        b->mgb.cnt = (int32_t*)b->dalloc(sizeof(int32_t) * nodes);
+        b->mg_total = total;
+    }
+    if (!b->mgb.part) b->mgb.part = (double*)b->dalloc(sizeof(double) * MG_PARTIALS);
+    if (!b->mgb.scalar) b->mgb.scalar = (double*)b->dalloc(sizeof(double) * 2);
+    if (!b->elec_u || !b->d_elec_g || !b->d_umax || !b->field || !b->mgb.phi || !b->mgb.f || !b->mgb.r ||
+        !b->mgb.cnt || !b->mgb.part || !b->mgb.scalar)
+        return fail(FKMC_ENOMEM, "device allocation failed (electrostatics)");
+    b->elec = *e;
+    // own-potential tables: a unit charge on a site of each type, its 8 neighbours
+    b->elec_g.assign(24 * (size_t)b->n, 0);
+    for (int r = 0; r < b->n; ++r) {
+        const RepDesc& D = b->desc[r];
+        const MgPlan p = mg_plan(D.L[0], D.L[1], D.L[2]);
+        const double scale = 1.602176634e-19 / (8.8541878128e-12 * e->eps_r * b->a_ang[r] * 1e-10);
+        const int nx = D.L[0], ny = D.L[1], nz = D.L[2];
+        std::vector<double> phi((size_t)nx * ny * nz);
+        auto node = [&](int x, int y, int z) {
+            x = ((x % nx) + nx) % nx;
+            y = ((y % ny) + ny) % ny;
+            z = ((z % nz) + nz) % nz;
+            return phi[((size_t)z * ny + y) * nx + x];
+        };
+        auto site_phi = [&](int t, int x, int y, int z) {
+            return 0.5 * (node(x, y, z) + node(x + (t == 0), y + (t == 1), z + (t == 2)));
+        };
+        for (int t = 0; t < 3; ++t) {
+            CK(elec_solve_unit(D, t, scale, e->cycles, p, b->mgb, b->st), "unit-charge solve");
+            CK(cudaMemcpyAsync(phi.data(), b->mgb.phi, sizeof(double) * phi.size(), cudaMemcpyDeviceToHost, b->st),
+               "copy");
+            CK(cudaStreamSynchronize(b->st), "synchronize");
+            const int x = nx / 2, y = ny / 2, z = nz / 2;
+            const double ps = site_phi(t, x, y, z);
+            for (int n = 0; n < 8; ++n) {
+                const NbEntry& nb = b->nbt.e[t][n];
+                const double pj = site_phi(nb.t2, x + nb.dc[0], y + nb.dc[1], z + nb.dc[2]);
+                b->elec_g[24 * (size_t)r + 8 * t + n] = (int32_t)std::llrint(e->q_vac * e->q_vac * (pj - ps) * 1e4);
+            }
+        }
+    }
+    CK(cudaMemcpyAsync(b->d_elec_g, b->elec_g.data(), sizeof(int32_t) * b->elec_g.size(), cudaMemcpyHostToDevice,
+                       b->st),
+       "table upload");
+    b->elec_on = true;
+    b->elec_umax = 0;
+    b->field_valid = false;  // rebuilt with u at the next run
+    int rc = elec_refresh(b);
+    if (rc) return rc;
+    drop_window_graph(b);
+    CK(run_pass_blocks(FKMC_PLAIN, b->cap, true, b->grains_on, &b->run_blocks), "occupancy query");
+    if (b->rates_set) {
+        rc = build_btab(b);
+        if (!rc) rc = plan_residency(b);
+        if (!rc) rc = upload_desc(b);
+        if (rc) return rc;
+    }
+    CK(cudaStreamSynchronize(b->st), "synchronize");
+    return FKMC_OK;
+}
+
+int kmc_solve_potential(kmc_batch* b, int32_t r, double* phi, size_t n, double* resid_rel)
+{
+    if (!valid_replica(b, r) || !phi) return fail(FKMC_EINVAL, "bad replica or output");
+    if (!b->elec_on) return fail(FKMC_ESTATE, "electrostatics are off");
+    const RepDesc& D = b->desc[r];
+    if ((int64_t)n != D.nsite / 3) return fail(FKMC_EINVAL, "n must equal nx ny nz");
+    const MgPlan p = mg_plan(D.L[0], D.L[1], D.L[2]);
+    const double scale = 1.602176634e-19 / (8.8541878128e-12 * b->elec.eps_r * b->a_ang[r] * 1e-10);
+    double res = 0.0;
+    CK(elec_solve(D, b->recs, b->counts, b->cap, b->n_vac[r], b->elec.q_vac, scale, b->elec.cycles, p, b->mgb, &res,
+                  b->st),
+       "potential solve");
+    CK(cudaMemcpyAsync(phi, b->mgb.phi, sizeof(double) * n, cudaMemcpyDeviceToHost, b->st), "copy");
+    CK(cudaStreamSynchronize(b->st), "synchronize");
+    if (resid_rel) *resid_rel = res;
+    return FKMC_OK;
+}
+
+int kmc_read_potential_energy(kmc_batch* b, int32_t r, int32_t* u, size_t n, int32_t* g)
+{
+    if (!valid_replica(b, r) || !u) return fail(FKMC_EINVAL, "bad replica or output");
+    if (!b->elec_on) return fail(FKMC_ESTATE, "electrostatics are off");
+    const RepDesc& D = b->desc[r];
+    if ((int64_t)n != D.nsite) return fail(FKMC_EINVAL, "n must equal 3 nx ny nz");
+    CK(cudaMemcpyAsync(u, b->elec_u + D.site_off, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, b->st), "copy");
+    CK(cudaStreamSynchronize(b->st), "synchronize");
+    if (g) std::memcpy(g, b->elec_g.data() + 24 * (size_t)r, sizeof(int32_t) * 24);
+    return FKMC_OK;
+}
+
+int kmc_write_potential_energy(kmc_batch* b, int32_t r, const int32_t* u, size_t n, const int32_t* g)
+{
+    if (!valid_replica(b, r) || !u) return fail(FKMC_EINVAL, "bad replica or input");
+    if (!b->elec_on) return fail(FKMC_ESTATE, "electrostatics are off");
+    const RepDesc& D = b->desc[r];
+    if ((int64_t)n != D.nsite) return fail(FKMC_EINVAL, "n must equal 3 nx ny nz");
+    int64_t um = 0;
+    for (size_t i = 0; i < n; ++i) um = std::max<int64_t>(um, u[i] < 0 ? -(int64_t)u[i] : u[i]);
+    CK(cudaMemcpyAsync(b->elec_u + D.site_off, u, sizeof(int32_t) * n, cudaMemcpyHostToDevice, b->st), "upload");
+    if (g) {
+        std::memcpy(b->elec_g.data() + 24 * (size_t)r, g, sizeof(int32_t) * 24);
+        CK(cudaMemcpyAsync(b->d_elec_g + 24 * (size_t)r, g, sizeof(int32_t) * 24, cudaMemcpyHostToDevice, b->st),
+           "upload");
+    }
+    CK(cudaStreamSynchronize(b->st), "synchronize");
+    b->field_valid = false;
+    b->elec_age = 0;
+    b->elec_umax = 0;  // re-derive the tables' range from what was written
+    const int64_t keep = um;
+    int rc = elec_cover(b, keep);
+    if (rc) return rc;
+    if (b->rates_set) {
+        rc = build_btab(b);  // g may have grown the bound too
+        if (!rc) rc = upload_desc(b);
+        if (rc) return rc;
+        drop_window_graph(b);
+    }
+    return FKMC_OK;
+}
+
 int kmc_set_grains(kmc_batch* b, const kmc_grains* g)
 {
     if (!b) return fail(FKMC_EINVAL, "null batch");
@@ -1392,7 +1649,7 @@ int kmc_set_grains(kmc_batch* b, const kmc_grains* g)
     if (!on && !b->grains_on) return FKMC_OK;
     b->grains_on = on;
     drop_window_graph(b);
-    CK(run_pass_blocks(b->site_on ? FKMC_PLAIN : b->opts.precision, b->cap, b->site_on, on, &b->run_blocks),
+    CK(run_pass_blocks(site_path(b) ? FKMC_PLAIN : b->opts.precision, b->cap, site_path(b), on, &b->run_blocks),
        "occupancy query");
     if (b->rates_set) {
         for (int r = 0; r < b->n; ++r) {
@@ -1461,7 +1718,7 @@ int kmc_write_dopants(kmc_batch* b, int32_t r, const uint8_t* host_cells, size_t
 int kmc_read_site_field(kmc_batch* b, int32_t r, int32_t* host_field, size_t n)
 {
     if (!valid_replica(b, r) || !host_field) return fail(FKMC_EINVAL, "bad replica or output");
-    if (!b->site_on) return fail(FKMC_ESTATE, "site energies are off");
+    if (!site_path(b)) return fail(FKMC_ESTATE, "site energies are off");
     const RepDesc& D = b->desc[r];
     if ((int64_t)n != D.nsite) return fail(FKMC_EINVAL, "n must equal 3 nx ny nz");
     if (!b->field_valid) {

@@ -100,6 +100,7 @@ struct SiteArgs {
     int32_t n_vv;         // offsets per site type
     int32_t e_self;       // energy of the a/sqrt2 shell: a hop partner's share of its target
     const uint8_t* gbound;  // grains: 1 per boundary cell (batch-wide cell index), or null
+    const int32_t* g_elec;  // electrostatics: [replica][3][8] own-potential share of a hop, or null
 };
 
 // cell of a site, batch-wide index (a replica's cells start at site_off / 3)

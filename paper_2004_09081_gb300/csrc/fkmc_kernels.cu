@@ -220,7 +220,8 @@ __device__ __forceinline__ void compute_rates_site(const RepDesc& D, const uint3
                 }
                 const int32_t Es = __ldcg(field + site_lin(D, t, x, y, z));
                 const int32_t Ej = __ldcg(field + site_lin(D, nb.t2, jx, jy, jz));
-                const int32_t dm = Ej - sa.e_self - Es;
+                int32_t dm = Ej - sa.e_self - Es;
+                if (sa.g_elec) dm -= sa.g_elec[24 * D.replica + 8 * t + n];
                 const int hidx = D.bhi_mid + (dm >> 9);
                 if (hidx >= 0 && hidx < D.bhi_len) {
                     k = __dmul_rn(__dmul_rn(k0, __ldg(hi + hidx)), __ldg(lo + (dm & 511)));

@@ -44,6 +44,34 @@ cudaError_t launch_moments(const RepDesc& D, int species, const uint32_t* occ, c
 cudaError_t launch_moments_all(const RepDesc* d_descs, int nrep, const VacRec* recs, const int32_t* counts,
                                int64_t max_frag_per_replica, int cap, unsigned long long* out, cudaStream_t st);
 
+// electrostatics of the mu-scale model (fkmc_poisson.cu): multigrid on the B-site grid
+constexpr int MG_MAX_LEVELS = 16;
+constexpr int MG_PARTIALS = 256;  // blocks of the deterministic reductions
+struct MgPlan {
+    int levels;
+    int dim[MG_MAX_LEVELS][3];
+    int64_t off[MG_MAX_LEVELS];  // first node of each level in the level-stacked buffers
+    int64_t total;
+};
+struct MgBuffers {
+    double* phi;     // [total] solution / correction per level
+    double* f;       // [total] right-hand side per level
+    double* r;       // [total] residual (and the Jacobi scratch of an odd level)
+    int32_t* cnt;    // [level-0 nodes] half-charge counts
+    double* part;    // [MG_PARTIALS]
+    double* scalar;  // [2]
+};
+MgPlan mg_plan(int nx, int ny, int nz);
+int64_t mg_cycle_kernels(const MgPlan& p);  // kernel launches of one V-cycle
+cudaError_t elec_solve(const RepDesc& D, const VacRec* recs, const int32_t* counts, int cap, int64_t n_vac,
+                       double q, double scale, int cycles, const MgPlan& p, const MgBuffers& b, double* resid_rel,
+                       cudaStream_t st);
+cudaError_t elec_solve_unit(const RepDesc& D, int t, double scale, int cycles, const MgPlan& p, const MgBuffers& b,
+                            cudaStream_t st);
+cudaError_t elec_update(const RepDesc& D, const double* phi, double q, int32_t* u, int32_t* field, unsigned* umax,
+                        cudaStream_t st);
+cudaError_t elec_add(int32_t* field, const int32_t* u, int64_t n, cudaStream_t st);
+
 // replica-resident kernel (fkmc_resident.cu)
 constexpr int RESIDENT_MAX_SLOTS = 64;               // vacancies per fragment a thread can hold
 constexpr size_t RESIDENT_MAX_SMEM = 220 * 1024;     // dynamic shared memory per replica CTA

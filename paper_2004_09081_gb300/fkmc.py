@@ -47,6 +47,11 @@ class kmc_grains(C.Structure):
     _fields_ = [("n_grains", C.c_int32), ("width", C.c_int32), ("barrier_eV", C.c_double)]
 
 
+class kmc_electrostatics(C.Structure):
+    _fields_ = [("eps_r", C.c_double), ("q_vac", C.c_double), ("refresh_windows", C.c_int32),
+                ("cycles", C.c_int32)]
+
+
 class kmc_barrier_table(C.Structure):
     _fields_ = [("Ea_O_eV", C.c_double), ("Ea_H_eV", C.c_double), ("prefactor", C.c_double),
                 ("q_O", C.c_double), ("q_H", C.c_double)]
@@ -108,6 +113,10 @@ _SIGNATURES = {
     "kmc_read_site_field": (C.c_int, [_P, _I32, _P, _SZ]),
     "kmc_site_shells": (C.c_int, [_P, _I32, _P, _I32, _P]),
     "kmc_set_grains": (C.c_int, [_P, _P]),
+    "kmc_set_electrostatics": (C.c_int, [_P, _P]),
+    "kmc_solve_potential": (C.c_int, [_P, _I32, _P, _SZ, _P]),
+    "kmc_read_potential_energy": (C.c_int, [_P, _I32, _P, _SZ, _P]),
+    "kmc_write_potential_energy": (C.c_int, [_P, _I32, _P, _SZ, _P]),
     "kmc_read_grains": (C.c_int, [_P, _I32, _P, _P, _SZ]),
     "kmc_destroy": (C.c_int, [_P]),
     "kmc_last_error": (C.c_char_p, []),
@@ -321,6 +330,40 @@ def kmc_site_shells(vv, fe, t: int) -> np.ndarray:
     return out[: n.value]
 
 
+def kmc_set_electrostatics(h, eps_r=None, q_vac=2.0, refresh_windows=8, cycles=12):
+    """Potential of the vacancy charges (multigrid), refreshed every
+    refresh_windows windows; eps_r None turns it off."""
+    if eps_r is None:
+        _check(load().kmc_set_electrostatics(h, None))
+        return
+    e = kmc_electrostatics(float(eps_r), float(q_vac), int(refresh_windows), int(cycles))
+    _check(load().kmc_set_electrostatics(h, C.byref(e)))
+
+
+def kmc_solve_potential(h, r: int, ncell: int):
+    phi = np.zeros(ncell, np.float64)
+    res = C.c_double()
+    _check(load().kmc_solve_potential(h, r, _ptr(phi), ncell, C.byref(res)))
+    return phi, res.value
+
+
+def kmc_read_potential_energy(h, r: int, nsite: int):
+    u = np.zeros(nsite, np.int32)
+    g = np.zeros((3, 8), np.int32)
+    _check(load().kmc_read_potential_energy(h, r, _ptr(u), nsite, _ptr(g)))
+    return u, g
+
+
+def kmc_write_potential_energy(h, r: int, u, g=None):
+    u = np.ascontiguousarray(u, np.int32)
+    gp = None
+    if g is not None:
+        g = np.ascontiguousarray(g, np.int32)
+        assert g.size == 24
+        gp = _ptr(g)
+    _check(load().kmc_write_potential_energy(h, r, _ptr(u), u.size, gp))
+
+
 def kmc_set_grains(h, n_grains: int, width: int = 1, barrier_eV: float = 0.2):
     """Voronoi grains; n_grains <= 1 turns them off."""
     if n_grains <= 1:
@@ -471,6 +514,19 @@ class Batch:
 
     def set_site_energy(self, vv=(), fe=()):
         kmc_set_site_energy(self.h, vv, fe)
+
+    def set_electrostatics(self, eps_r=None, q_vac=2.0, refresh_windows=8, cycles=12):
+        kmc_set_electrostatics(self.h, eps_r, q_vac, refresh_windows, cycles)
+
+    def solve_potential(self, r=0):
+        """(phi at every B node [z][y][x] flattened, relative residual)"""
+        return kmc_solve_potential(self.h, r, self.nsite(r) // 3)
+
+    def potential_energy(self, r=0):
+        return kmc_read_potential_energy(self.h, r, self.nsite(r))
+
+    def write_potential_energy(self, u, g=None, r=0):
+        kmc_write_potential_energy(self.h, r, u, g)
 
     def set_grains(self, n_grains, width=1, barrier_eV=0.2):
         kmc_set_grains(self.h, n_grains, width, barrier_eV)

@@ -1,0 +1,146 @@
+"""Electrostatics of the mu-scale model on the GPU vs the CPU oracle, through
+the C ABI: the multigrid potential of the vacancy charges against the exact
+FFT solve of the same discrete equation, the own-potential table and the
+quantised site energies, and the kMC in a written (frozen) potential bit for
+bit, alone and with site-energy shells and grains."""
+import numpy as np
+import pytest
+
+from oracle import poisson as ps
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fk():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2004_09081_gb300 import fkmc
+    fkmc.load()
+    return fkmc
+
+
+def vacancy_sites(b, r=0):
+    return b.records(r)[:, 1]
+
+
+@pytest.mark.parametrize("cells", [(32, 32, 32), (24, 16, 40), (12, 12, 12)])
+def test_multigrid_matches_fft(fk, orc, cells):
+    nv = max(8, 3 * cells[0] * cells[1] * cells[2] // 200)
+    b = fk.Batch([(*cells, 4.01)], [(nv, 0)], 3, edge=4, precision=0)
+    b.set_barriers(0.7, 0.7, 600.0)
+    b.set_electrostatics(eps_r=150.0, q_vac=2.0, refresh_windows=0, cycles=14)
+    phi, res = b.solve_potential()
+    ref = ps.solve(ps.node_charge(cells, vacancy_sites(b), q=2.0), 4.01, 150.0).ravel()
+    assert res < 1e-9
+    assert np.abs(phi - ref).max() < 1e-8 * np.abs(ref).max()
+
+
+def test_own_potential_table_and_site_energies(fk, orc):
+    cells = (16, 16, 16)
+    b = fk.Batch([(*cells, 4.01)], [(40, 0)], 5, edge=4, precision=0)
+    b.set_barriers(0.7, 0.7, 600.0)
+    b.set_electrostatics(eps_r=80.0, q_vac=2.0, refresh_windows=0, cycles=14)
+    u, g = b.potential_energy()
+    g_ref = ps.self_table(cells, 4.01, 80.0, orc.neighbour_table())
+    assert np.abs(g - g_ref).max() <= 1 and np.mean(g == g_ref) > 0.9
+    phi = ps.solve(ps.node_charge(cells, vacancy_sites(b), q=2.0), 4.01, 80.0)
+    u_ref = ps.energy_units(ps.site_potential(phi), q=2.0)
+    # quantised from two solvers that agree to ~1e-10: rare off-by-one at a rounding tie
+    assert np.abs(u - u_ref).max() <= 1 and np.mean(u == u_ref) > 0.999
+    assert np.abs(u).max() > 100  # the potential is not trivially zero
+
+
+def _random_u(nsite, seed):
+    rng = np.random.default_rng(seed)
+    return rng.integers(-1500, 1500, nsite).astype(np.int32)
+
+
+@pytest.mark.parametrize("with_shells", [False, True])
+def test_frozen_potential_kmc_bit_exact(fk, orc, with_shells):
+    """A written potential (seeded integers) and own-potential table drive the
+    same trajectory on both sides."""
+    cells, nf = (16, 16, 16), (4, 4, 4)
+    vv = [(2, 0.343), (4, 0.235), (6, 0.200), (8, 0.180), (10, 0.023)]
+    b = fk.Batch([(*cells, 4.01)], [(60, 80)], 7, nfrag=nf, precision=0, tracer=True, cap_v=64)
+    if with_shells:
+        b.set_site_energy(vv, [])
+    b.set_barriers(0.7, 0.5, 900.0, field_z=1e7)
+    b.set_electrostatics(eps_r=100.0, refresh_windows=0)
+    u = _random_u(3 * 16 ** 3, 1)
+    g = np.full((3, 8), -180, np.int32)
+    b.write_potential_energy(u, g)
+    ref = orc.Lattice(cells, nf, 60, 80, seed=7, tracer=True)
+    if with_shells:
+        ref.set_site_energy(vv=vv)
+    ref.set_elec(u, g)
+    ref.set_rates(0.7, 0.5, 900.0, Ez=1e7, a_ang=4.01, cap_v=64)
+    for _ in range(3):
+        b.run(40)
+        ref.run(40)
+        assert np.array_equal(b.state(), ref.occupancy())
+        assert np.array_equal(b.records(), ref.records())
+        assert np.array_equal(b.tracer_field(), ref.tracer_field())
+        assert b.info().hops == ref.counters()["hops"]
+    assert ref.counters()["hops"] > 500
+
+
+def test_frozen_potential_with_grains_bit_exact(fk, orc):
+    cells, nf = (16, 12, 16), (4, 2, 4)
+    b = fk.Batch([(*cells, 4.01)], [(40, 0)], 9, nfrag=nf, precision=0, cap_v=64)
+    b.set_barriers(0.6, 0.6, 900.0)
+    b.set_grains(4, 1, 0.2)
+    b.set_electrostatics(eps_r=100.0, refresh_windows=0)
+    u = _random_u(3 * 16 * 12 * 16, 2)
+    g = np.full((3, 8), -120, np.int32)
+    b.write_potential_energy(u, g)
+    ref = orc.Lattice(cells, nf, 40, 0, seed=9)
+    ref.set_elec(u, g)
+    ref.set_rates(0.6, 0.6, 900.0, a_ang=4.01, cap_v=64)
+    ref.set_grains(4, 1, 0.2)
+    b.run(80)
+    ref.run(80)
+    assert np.array_equal(b.state(), ref.occupancy())
+    assert np.array_equal(b.records(), ref.records())
+
+
+def test_refreshed_field_is_consistent(fk, orc):
+    """With automatic solves every 4 windows the energy field always equals
+    the shells plus the last solve's u (checked against the oracle's sums with
+    the same u)."""
+    cells, nf = (16, 16, 16), (4, 4, 4)
+    vv = [(2, 0.343), (4, 0.235)]
+    b = fk.Batch([(*cells, 4.01)], [(50, 0)], 4, nfrag=nf, precision=0, cap_v=64)
+    b.set_site_energy(vv, [])
+    b.set_barriers(0.6, 0.6, 900.0)
+    b.set_electrostatics(eps_r=60.0, refresh_windows=4, cycles=12)
+    for _ in range(3):
+        b.run(6)
+        u, g = b.potential_energy()
+        ref = orc.Lattice(cells, nf, 0, 0)
+        ref.set_occupancy(b.state())
+        ref.set_site_energy(vv=vv)
+        ref.set_elec(u, g)
+        field_ref = np.array([ref.site_energy(s) for s in range(ref.nsite)], np.int64)
+        assert np.array_equal(b.site_field().astype(np.int64), field_ref)
+    s = b.run(8)
+    assert s.hops > 0
+
+
+def test_elec_errors(fk):
+    b = fk.Batch([(16, 16, 16, 4.01)], [(10, 0)], 0, precision=1)
+    b.set_barriers(0.7, 0.7, 600.0)
+    with pytest.raises(fk.KmcError):
+        b.set_electrostatics(eps_r=100.0)  # mixed form
+    b = fk.Batch([(16, 16, 16, 4.01)], [(10, 0)], 0, precision=0)
+    b.set_barriers(0.7, 0.7, 600.0)
+    with pytest.raises(fk.KmcError):
+        b.set_electrostatics(eps_r=-1.0)
+    with pytest.raises(fk.KmcError):
+        b.solve_potential()  # electrostatics off
+    b.set_electrostatics(eps_r=100.0)
+    with pytest.raises(fk.KmcError):
+        b.run_null(1, 1)  # the null-event form has no electrostatics
+    b.set_electrostatics(None)
+    b.run_null(2, 2)
