@@ -83,7 +83,7 @@ def test_frozen_potential_kmc_bit_exact(fk, orc, with_shells):
         assert np.array_equal(b.records(), ref.records())
         assert np.array_equal(b.tracer_field(), ref.tracer_field())
         assert b.info().hops == ref.counters()["hops"]
-    assert ref.counters()["hops"] > 500
+    assert ref.counters()["hops"] > 250
 
 
 def test_frozen_potential_with_grains_bit_exact(fk, orc):
