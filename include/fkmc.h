@@ -254,12 +254,16 @@ typedef struct {
     double q_vac;             /* vacancy charge in e (+2 for an O vacancy) */
     int32_t refresh_windows;  /* windows between solves; 0 = no automatic solve */
     int32_t cycles;           /* V-cycles per solve, 1..200 (12 reach a relative residual ~1e-10) */
+    int32_t warm_cycles;      /* V-cycles of an automatic refresh, which starts from the last
+                                 solve's potential, 0..200 (0: `cycles`); the first solve after
+                                 kmc_set_electrostatics or a state write starts from zero */
 } kmc_electrostatics;
 
 /* Turn electrostatics on (or off with NULL) for every replica and solve once.
  * Extra device memory: 4 bytes per O site, about 3 doubles per cell for the
  * multigrid levels of the largest replica.  Errors: FKMC_EINVAL for the mixed
- * form or bad parameters; FKMC_ENOMEM; FKMC_ECUDA. */
+ * form, bad parameters or a replica of 2^31 cells or more; FKMC_ENOMEM;
+ * FKMC_ECUDA. */
 int kmc_set_electrostatics(kmc_batch* b, const kmc_electrostatics* e);
 
 /* Solve the potential of replica r's current vacancies (kmc_set_electrostatics

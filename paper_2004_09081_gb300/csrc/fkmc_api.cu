@@ -174,6 +174,8 @@ struct kmc_batch {
     MgPlan mg{};
     MgBuffers mgb{};
     int64_t mg_total = -1;
+    double* phi_prev = nullptr;         // each replica's last potential (warm start of the next solve)
+    bool phi_prev_valid = false;
     // grains (mu-scale model): boundary cells raise the barrier of hops touching them
     bool grains_on = false;
     kmc_grains grains{};
@@ -593,6 +595,12 @@ int elec_cover(kmc_batch* b, int64_t um)
     return FKMC_OK;
 }
 
+// V-cycles of the next automatic refresh
+static int refresh_cycles(const kmc_batch* b)
+{
+    return b->phi_prev_valid && b->elec.warm_cycles > 0 ? b->elec.warm_cycles : b->elec.cycles;
+}
+
 // kernels of one refresh: per replica the solve (deposit, right-hand side,
 // V-cycles, mean) and the update
 uint64_t elec_launches(const kmc_batch* b)
@@ -600,7 +608,7 @@ uint64_t elec_launches(const kmc_batch* b)
     uint64_t k = 0;
     for (int r = 0; r < b->n; ++r) {
         const MgPlan p = mg_plan(b->desc[r].L[0], b->desc[r].L[1], b->desc[r].L[2]);
-        k += 2 + (uint64_t)b->elec.cycles * mg_cycle_kernels(p) + 3 + 1;
+        k += 2 + (uint64_t)refresh_cycles(b) * mg_cycle_kernels(p) + 3 + 1;
     }
     return k;
 }
@@ -610,12 +618,14 @@ uint64_t elec_launches(const kmc_batch* b)
 int elec_refresh(kmc_batch* b)
 {
     CK(cudaMemsetAsync(b->d_umax, 0, sizeof(unsigned), b->st), "memset");
+    const int cycles = refresh_cycles(b);
     for (int r = 0; r < b->n; ++r) {
         const RepDesc& D = b->desc[r];
         const MgPlan p = mg_plan(D.L[0], D.L[1], D.L[2]);
         const double scale = 1.602176634e-19 / (8.8541878128e-12 * b->elec.eps_r * b->a_ang[r] * 1e-10);
-        CK(elec_solve(D, b->recs, b->counts, b->cap, b->n_vac[r], b->elec.q_vac, scale, b->elec.cycles, p, b->mgb,
-                      nullptr, b->st),
+        double* prev = b->phi_prev + D.site_off / 3;
+        CK(elec_solve(D, b->recs, b->counts, b->cap, b->n_vac[r], b->elec.q_vac, scale, cycles, p, b->mgb,
+                      nullptr, b->phi_prev_valid ? prev : nullptr, prev, b->st),
            "potential solve");
         CK(elec_update(D, b->mgb.phi, b->elec.q_vac, b->elec_u, b->field_valid ? b->field : nullptr, b->d_umax, b->st),
            "potential update");
@@ -624,6 +634,7 @@ int elec_refresh(kmc_batch* b)
     CK(cudaMemcpyAsync(&um, b->d_umax, sizeof um, cudaMemcpyDeviceToHost, b->st), "copy");
     CK(cudaStreamSynchronize(b->st), "synchronize");
     b->elec_age = 0;
+    b->phi_prev_valid = true;
     return elec_cover(b, (int64_t)um);
 }
 
@@ -1254,6 +1265,7 @@ int kmc_write_state(kmc_batch* b, int32_t r, const uint8_t* host_occ, size_t n)
     b->n_H[r] = nh;
     b->field_valid = false;
     b->elec_age = UINT64_MAX / 2;  // the potential is solved again at the next refresh point
+    b->phi_prev_valid = false;  // and from zero: the vacancies may have moved anywhere
     if (b->rates_set) {
         int rc = plan_residency(b);
         if (rc) return rc;
@@ -1359,6 +1371,7 @@ int kmc_upload_state(kmc_batch* b, const void* host, size_t bytes)
     CK(cudaStreamSynchronize(b->st), "synchronize");
     b->field_valid = false;
     b->elec_age = UINT64_MAX / 2;
+    b->phi_prev_valid = false;
     return FKMC_OK;
 }
 
@@ -1479,8 +1492,12 @@ int kmc_set_electrostatics(kmc_batch* b, const kmc_electrostatics* e)
     }
     if (b->opts.precision != FKMC_PLAIN) return fail(FKMC_EINVAL, "electrostatics need the plain form");
     if (!(e->eps_r > 0.0) || !(e->eps_r <= 1e6) || !std::isfinite(e->q_vac) || std::fabs(e->q_vac) > 8.0 ||
-        e->cycles < 1 || e->cycles > 200 || e->refresh_windows < 0)
-        return fail(FKMC_EINVAL, "electrostatics: eps_r in (0, 1e6], |q| <= 8, 1..200 cycles, refresh >= 0");
+        e->cycles < 1 || e->cycles > 200 || e->warm_cycles < 0 || e->warm_cycles > 200 || e->refresh_windows < 0)
+        return fail(FKMC_EINVAL,
+                    "electrostatics: eps_r in (0, 1e6], |q| <= 8, 1..200 cycles, 0..200 warm cycles, refresh >= 0");
+    for (int r = 0; r < b->n; ++r)
+        if (b->desc[r].nsite / 3 > INT32_MAX)
+            return fail(FKMC_EINVAL, "electrostatics: at most 2^31 - 1 cells per replica");
     // buffers: u per site, tables, the multigrid levels of the largest replica
     int64_t total = 0, nodes = 0;
     for (int r = 0; r < b->n; ++r) {
@@ -1500,12 +1517,14 @@ int kmc_set_electrostatics(kmc_batch* b, const kmc_electrostatics* e)
         b->mgb.cnt = (int32_t*)b->dalloc(sizeof(int32_t) * nodes);
         b->mg_total = total;
     }
+    if (!b->phi_prev) b->phi_prev = (double*)b->dalloc(sizeof(double) * b->ncell_total);
     if (!b->mgb.part) b->mgb.part = (double*)b->dalloc(sizeof(double) * MG_PARTIALS);
     if (!b->mgb.scalar) b->mgb.scalar = (double*)b->dalloc(sizeof(double) * 2);
-    if (!b->elec_u || !b->d_elec_g || !b->d_umax || !b->field || !b->mgb.phi || !b->mgb.f || !b->mgb.r ||
+    if (!b->elec_u || !b->d_elec_g || !b->d_umax || !b->field || !b->phi_prev || !b->mgb.phi || !b->mgb.f || !b->mgb.r ||
         !b->mgb.cnt || !b->mgb.part || !b->mgb.scalar)
         return fail(FKMC_ENOMEM, "device allocation failed (electrostatics)");
     b->elec = *e;
+    b->phi_prev_valid = false;  // the first solve starts from zero
     // own-potential tables: a unit charge on a site of each type, its 8 neighbours
     b->elec_g.assign(24 * (size_t)b->n, 0);
     for (int r = 0; r < b->n; ++r) {
@@ -1567,7 +1586,7 @@ int kmc_solve_potential(kmc_batch* b, int32_t r, double* phi, size_t n, double* 
     const double scale = 1.602176634e-19 / (8.8541878128e-12 * b->elec.eps_r * b->a_ang[r] * 1e-10);
     double res = 0.0;
     CK(elec_solve(D, b->recs, b->counts, b->cap, b->n_vac[r], b->elec.q_vac, scale, b->elec.cycles, p, b->mgb, &res,
-                  b->st),
+                  nullptr, nullptr, b->st),
        "potential solve");
     CK(cudaMemcpyAsync(phi, b->mgb.phi, sizeof(double) * n, cudaMemcpyDeviceToHost, b->st), "copy");
     CK(cudaStreamSynchronize(b->st), "synchronize");

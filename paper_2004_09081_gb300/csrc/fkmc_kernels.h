@@ -65,7 +65,7 @@ MgPlan mg_plan(int nx, int ny, int nz);
 int64_t mg_cycle_kernels(const MgPlan& p);  // kernel launches of one V-cycle
 cudaError_t elec_solve(const RepDesc& D, const VacRec* recs, const int32_t* counts, int cap, int64_t n_vac,
                        double q, double scale, int cycles, const MgPlan& p, const MgBuffers& b, double* resid_rel,
-                       cudaStream_t st);
+                       const double* init, double* save, cudaStream_t st);
 cudaError_t elec_solve_unit(const RepDesc& D, int t, double scale, int cycles, const MgPlan& p, const MgBuffers& b,
                             cudaStream_t st);
 cudaError_t elec_update(const RepDesc& D, const double* phi, double q, int32_t* u, int32_t* field, unsigned* umax,

@@ -57,91 +57,95 @@ __global__ void k_mg_rhs(const int32_t* cnt, int64_t n, double half_q, double ba
         f[i] = __dmul_rn(__dadd_rn(__dmul_rn(half_q, (double)cnt[i]), -background), scale);
 }
 
-// red-black Gauss-Seidel half-sweep (all dimensions even: the colouring is
-// consistent across the periodic seams)
-__global__ void k_mg_rb(double* phi, const double* f, int nx, int ny, int nz, int colour)
+// The level-by-level stencil kernels run on 3-D grids: blockIdx.y / blockIdx.z
+// are the row (y, z), threads walk x; all index arithmetic is 32-bit.
+constexpr int XT = 128;
+constexpr double SIXTH = 1.0 / 6.0;
+
+__device__ __forceinline__ double nb_sum(const double* v, int x, int y, int z, int nx, int ny, int nz)
 {
-    const int64_t n = (int64_t)nx * ny * nz;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((int64_t)nx * ny));
-        if (((x + y + z) & 1) != colour) continue;
-        double s = phi[nidx(wrap_(x - 1, nx), y, z, nx, ny)];
-        s = __dadd_rn(s, phi[nidx(wrap_(x + 1, nx), y, z, nx, ny)]);
-        s = __dadd_rn(s, phi[nidx(x, wrap_(y - 1, ny), z, nx, ny)]);
-        s = __dadd_rn(s, phi[nidx(x, wrap_(y + 1, ny), z, nx, ny)]);
-        s = __dadd_rn(s, phi[nidx(x, y, wrap_(z - 1, nz), nx, ny)]);
-        s = __dadd_rn(s, phi[nidx(x, y, wrap_(z + 1, nz), nx, ny)]);
-        phi[i] = __ddiv_rn(__dadd_rn(f[i], s), 6.0);
-    }
+    const int row = (z * ny + y) * nx;
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+    double s = v[row + xm];
+    s = __dadd_rn(s, v[row + xp]);
+    s = __dadd_rn(s, v[(z * ny + ym) * nx + x]);
+    s = __dadd_rn(s, v[(z * ny + yp) * nx + x]);
+    s = __dadd_rn(s, v[(zm * ny + y) * nx + x]);
+    s = __dadd_rn(s, v[(zp * ny + y) * nx + x]);
+    return s;
+}
+
+// red-black Gauss-Seidel half-sweep over the nodes of one colour (all
+// dimensions even: the colouring is consistent across the periodic seams);
+// thread k of a row takes x = 2k + the row's colour offset
+__global__ void __launch_bounds__(XT) k_mg_rb(double* phi, const double* f, int nx, int ny, int nz, int colour)
+{
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int x = 2 * (blockIdx.x * XT + threadIdx.x) + ((y + z + colour) & 1);
+    if (x >= nx) return;
+    const int i = (z * ny + y) * nx + x;
+    phi[i] = __dmul_rn(__dadd_rn(f[i], nb_sum(phi, x, y, z, nx, ny, nz)), SIXTH);
 }
 
 // damped Jacobi sweep, out = (1-w) in + w (f + sum nb) / 6
-__global__ void k_mg_jacobi(const double* in, double* out, const double* f, int nx, int ny, int nz, double w)
+__global__ void __launch_bounds__(XT) k_mg_jacobi(const double* in, double* out, const double* f, int nx, int ny,
+                                                   int nz, double w)
 {
-    const int64_t n = (int64_t)nx * ny * nz;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((int64_t)nx * ny));
-        double s = in[nidx(wrap_(x - 1, nx), y, z, nx, ny)];
-        s = __dadd_rn(s, in[nidx(wrap_(x + 1, nx), y, z, nx, ny)]);
-        s = __dadd_rn(s, in[nidx(x, wrap_(y - 1, ny), z, nx, ny)]);
-        s = __dadd_rn(s, in[nidx(x, wrap_(y + 1, ny), z, nx, ny)]);
-        s = __dadd_rn(s, in[nidx(x, y, wrap_(z - 1, nz), nx, ny)]);
-        s = __dadd_rn(s, in[nidx(x, y, wrap_(z + 1, nz), nx, ny)]);
-        const double gs = __ddiv_rn(__dadd_rn(f[i], s), 6.0);
-        out[i] = __dadd_rn(__dmul_rn(1.0 - w, in[i]), __dmul_rn(w, gs));
-    }
+    const int y = blockIdx.y, z = blockIdx.z, x = blockIdx.x * XT + threadIdx.x;
+    if (x >= nx) return;
+    const int i = (z * ny + y) * nx + x;
+    const double gs = __dmul_rn(__dadd_rn(f[i], nb_sum(in, x, y, z, nx, ny, nz)), SIXTH);
+    out[i] = __dadd_rn(__dmul_rn(1.0 - w, in[i]), __dmul_rn(w, gs));
 }
 
 // r = f - A phi
-__global__ void k_mg_residual(const double* phi, const double* f, double* r, int nx, int ny, int nz)
+__global__ void __launch_bounds__(XT) k_mg_residual(const double* phi, const double* f, double* r, int nx, int ny,
+                                                     int nz)
 {
-    const int64_t n = (int64_t)nx * ny * nz;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((int64_t)nx * ny));
-        double s = phi[nidx(wrap_(x - 1, nx), y, z, nx, ny)];
-        s = __dadd_rn(s, phi[nidx(wrap_(x + 1, nx), y, z, nx, ny)]);
-        s = __dadd_rn(s, phi[nidx(x, wrap_(y - 1, ny), z, nx, ny)]);
-        s = __dadd_rn(s, phi[nidx(x, wrap_(y + 1, ny), z, nx, ny)]);
-        s = __dadd_rn(s, phi[nidx(x, y, wrap_(z - 1, nz), nx, ny)]);
-        s = __dadd_rn(s, phi[nidx(x, y, wrap_(z + 1, nz), nx, ny)]);
-        r[i] = __dadd_rn(f[i], -__dadd_rn(__dmul_rn(6.0, phi[i]), -s));
-    }
+    const int y = blockIdx.y, z = blockIdx.z, x = blockIdx.x * XT + threadIdx.x;
+    if (x >= nx) return;
+    const int i = (z * ny + y) * nx + x;
+    r[i] = __dadd_rn(f[i], -__dadd_rn(__dmul_rn(6.0, phi[i]), -nb_sum(phi, x, y, z, nx, ny, nz)));
 }
 
-// coarse f = 4 x full weighting of the fine residual (weights (1,2,1)^3 / 64)
-__global__ void k_mg_restrict(const double* r, double* fc, int nx, int ny, int nz)
+// coarse f = 4 x full weighting of the fine residual (weights (1,2,1)^3 / 64);
+// the grid covers the coarse level
+__global__ void __launch_bounds__(XT) k_mg_restrict(const double* r, double* fc, int nx, int ny, int nz)
 {
-    const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
-    const int64_t n = (int64_t)cx * cy * cz;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int X = (int)(i % cx), Y = (int)((i / cx) % cy), Z = (int)(i / ((int64_t)cx * cy));
-        double s = 0.0;
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const double w = (double)((2 - (dx != 0)) * (2 - (dy != 0)) * (2 - (dz != 0)));
-                    s = __dadd_rn(s, __dmul_rn(w, r[nidx(wrap_(2 * X + dx, nx), wrap_(2 * Y + dy, ny),
-                                                         wrap_(2 * Z + dz, nz), nx, ny)]));
-                }
-        fc[i] = __dmul_rn(s, 4.0 / 64.0);
+    const int cx = nx / 2, cy = ny / 2;
+    const int Y = blockIdx.y, Z = blockIdx.z, X = blockIdx.x * XT + threadIdx.x;
+    if (X >= cx) return;
+    double s = 0.0;
+    for (int dz = -1; dz <= 1; ++dz) {
+        const int zz = wrap_(2 * Z + dz, nz);
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int yy = wrap_(2 * Y + dy, ny);
+            const double* row = r + (zz * ny + yy) * nx;
+            const double wr = (double)((2 - (dz != 0)) * (2 - (dy != 0)));
+            const double line = __dadd_rn(__dadd_rn(row[wrap_(2 * X - 1, nx)], __dmul_rn(2.0, row[2 * X])),
+                                          row[wrap_(2 * X + 1, nx)]);
+            s = __dadd_rn(s, __dmul_rn(wr, line));
+        }
     }
+    fc[(Z * cy + Y) * cx + X] = __dmul_rn(s, 4.0 / 64.0);
 }
 
 // phi_fine += trilinear interpolation of the coarse correction
-__global__ void k_mg_prolong(const double* ec, double* phi, int nx, int ny, int nz)
+__global__ void __launch_bounds__(XT) k_mg_prolong(const double* ec, double* phi, int nx, int ny, int nz)
 {
+    const int y = blockIdx.y, z = blockIdx.z, x = blockIdx.x * XT + threadIdx.x;
+    if (x >= nx) return;
     const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
-    const int64_t n = (int64_t)nx * ny * nz;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((int64_t)nx * ny));
-        const int X = x >> 1, Y = y >> 1, Z = z >> 1, ox = x & 1, oy = y & 1, oz = z & 1;
-        double s = 0.0;
-        for (int dz = 0; dz <= oz; ++dz)
-            for (int dy = 0; dy <= oy; ++dy)
-                for (int dx = 0; dx <= ox; ++dx)
-                    s = __dadd_rn(s, ec[nidx(wrap_(X + dx, cx), wrap_(Y + dy, cy), wrap_(Z + dz, cz), cx, cy)]);
-        phi[i] = __dadd_rn(phi[i], __dmul_rn(s, 1.0 / (double)(1 << (ox + oy + oz))));
-    }
+    const int X = x >> 1, Y = y >> 1, Z = z >> 1, ox = x & 1, oy = y & 1, oz = z & 1;
+    double s = 0.0;
+    for (int dz = 0; dz <= oz; ++dz)
+        for (int dy = 0; dy <= oy; ++dy)
+            for (int dx = 0; dx <= ox; ++dx)
+                s = __dadd_rn(s, ec[(wrap_(Z + dz, cz) * cy + wrap_(Y + dy, cy)) * cx + wrap_(X + dx, cx)]);
+    const int i = (z * ny + y) * nx + x;
+    phi[i] = __dadd_rn(phi[i], __dmul_rn(s, 1.0 / (double)(1 << (ox + oy + oz))));
 }
 
 // deterministic sum: per-block partials (fixed grid), then one thread in order
@@ -205,6 +209,139 @@ __global__ void k_elec_add(int32_t* field, const int32_t* u, int64_t n)
 
 unsigned grid_for(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + PT - 1) / PT, 8192)); }
 
+// ---- the small levels of a V-cycle in one block: levels ls .. coarsest live
+// in shared memory (phi, f and scratch of each level, at most SMALL_BYTES), the
+// same operations as the level-by-level kernels separated by __syncthreads.
+// The block reads the iterate and right-hand side of level ls from global
+// memory and writes back the iterate after the sub-cycle.
+constexpr int SMALL_BYTES = 200 * 1024;
+constexpr int ST = 1024;
+
+struct SmallLevels {
+    int ls, levels;
+    int dim[MG_MAX_LEVELS][3];
+    int offs[MG_MAX_LEVELS];  // node offset of each level in the shared arrays
+    int nodes;                // shared nodes per array
+    int64_t off_ls;           // global offset of level ls
+    int coarse_sweeps;
+};
+
+__device__ void s_smooth(const SmallLevels& P, int l, double* phi, const double* f, double* tmp, int sweeps)
+{
+    const int nx = P.dim[l][0], ny = P.dim[l][1], nz = P.dim[l][2];
+    const int n = nx * ny * nz;
+    const bool even = nx % 2 == 0 && ny % 2 == 0 && nz % 2 == 0;
+    for (int k = 0; k < sweeps; ++k) {
+        for (int half = 0; half < 2; ++half) {
+            const double* in = even ? phi : (half == 0 ? phi : tmp);
+            double* out = even ? phi : (half == 0 ? tmp : phi);
+            for (int i = threadIdx.x; i < n; i += ST) {
+                const int x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
+                if (even && ((x + y + z) & 1) != half) continue;
+                double s = in[nidx(wrap_(x - 1, nx), y, z, nx, ny)];
+                s = __dadd_rn(s, in[nidx(wrap_(x + 1, nx), y, z, nx, ny)]);
+                s = __dadd_rn(s, in[nidx(x, wrap_(y - 1, ny), z, nx, ny)]);
+                s = __dadd_rn(s, in[nidx(x, wrap_(y + 1, ny), z, nx, ny)]);
+                s = __dadd_rn(s, in[nidx(x, y, wrap_(z - 1, nz), nx, ny)]);
+                s = __dadd_rn(s, in[nidx(x, y, wrap_(z + 1, nz), nx, ny)]);
+                const double gs = __dmul_rn(__dadd_rn(f[i], s), SIXTH);
+                out[i] = even ? gs : __dadd_rn(__dmul_rn(1.0 - 6.0 / 7.0, in[i]), __dmul_rn(6.0 / 7.0, gs));
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(ST) k_mg_small(SmallLevels P, double* phi_g, const double* f_g)
+{
+    extern __shared__ __align__(16) double sm[];
+    double* phi_all = sm;
+    double* f_all = sm + P.nodes;
+    double* r_all = sm + 2 * P.nodes;
+    __shared__ double red[ST];
+    const int last = P.levels - 1;
+    {
+        const int n0 = P.dim[P.ls][0] * P.dim[P.ls][1] * P.dim[P.ls][2];
+        for (int i = threadIdx.x; i < n0; i += ST) {
+            phi_all[i] = phi_g[P.off_ls + i];  // the iterate so far (zero below the finest level)
+            f_all[i] = f_g[P.off_ls + i];
+        }
+        __syncthreads();
+    }
+    for (int l = P.ls; l < last; ++l) {  // down: pre-smooth, residual, restrict
+        const int nx = P.dim[l][0], ny = P.dim[l][1], nz = P.dim[l][2];
+        const int n = nx * ny * nz;
+        double* phi = phi_all + P.offs[l];
+        const double* f = f_all + P.offs[l];
+        double* r = r_all + P.offs[l];
+        s_smooth(P, l, phi, f, r, 2);
+        for (int i = threadIdx.x; i < n; i += ST) {
+            const int x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
+            double s = phi[nidx(wrap_(x - 1, nx), y, z, nx, ny)];
+            s = __dadd_rn(s, phi[nidx(wrap_(x + 1, nx), y, z, nx, ny)]);
+            s = __dadd_rn(s, phi[nidx(x, wrap_(y - 1, ny), z, nx, ny)]);
+            s = __dadd_rn(s, phi[nidx(x, wrap_(y + 1, ny), z, nx, ny)]);
+            s = __dadd_rn(s, phi[nidx(x, y, wrap_(z - 1, nz), nx, ny)]);
+            s = __dadd_rn(s, phi[nidx(x, y, wrap_(z + 1, nz), nx, ny)]);
+            r[i] = __dadd_rn(f[i], -__dadd_rn(__dmul_rn(6.0, phi[i]), -s));
+        }
+        __syncthreads();
+        const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
+        double* fc = f_all + P.offs[l + 1];
+        double* pc = phi_all + P.offs[l + 1];
+        for (int i = threadIdx.x; i < cx * cy * cz; i += ST) {
+            const int X = i % cx, Y = (i / cx) % cy, Z = i / (cx * cy);
+            double s = 0.0;
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const double w = (double)((2 - (dx != 0)) * (2 - (dy != 0)) * (2 - (dz != 0)));
+                        s = __dadd_rn(s, __dmul_rn(w, r[nidx(wrap_(2 * X + dx, nx), wrap_(2 * Y + dy, ny),
+                                                             wrap_(2 * Z + dz, nz), nx, ny)]));
+                    }
+            fc[i] = __dmul_rn(s, 4.0 / 64.0);
+            pc[i] = 0.0;
+        }
+        __syncthreads();
+    }
+    {  // coarsest: zero-mean right-hand side (block tree sum, fixed order), sweeps
+        const int n = P.dim[last][0] * P.dim[last][1] * P.dim[last][2];
+        double* f = f_all + P.offs[last];
+        double s = 0.0;
+        for (int i = threadIdx.x; i < n; i += ST) s = __dadd_rn(s, f[i]);
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = ST / 2; w; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] = __dadd_rn(red[threadIdx.x], red[threadIdx.x + w]);
+            __syncthreads();
+        }
+        const double m = __ddiv_rn(red[0], (double)n);
+        for (int i = threadIdx.x; i < n; i += ST) f[i] = __dadd_rn(f[i], -m);
+        __syncthreads();
+        s_smooth(P, last, phi_all + P.offs[last], f, r_all + P.offs[last], P.coarse_sweeps);
+    }
+    for (int l = last - 1; l >= P.ls; --l) {  // up: prolong, post-smooth
+        const int nx = P.dim[l][0], ny = P.dim[l][1], nz = P.dim[l][2];
+        const int n = nx * ny * nz, cx = nx / 2, cy = ny / 2, cz = nz / 2;
+        double* phi = phi_all + P.offs[l];
+        const double* ec = phi_all + P.offs[l + 1];
+        for (int i = threadIdx.x; i < n; i += ST) {
+            const int x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
+            const int X = x >> 1, Y = y >> 1, Z = z >> 1, ox = x & 1, oy = y & 1, oz = z & 1;
+            double s = 0.0;
+            for (int dz = 0; dz <= oz; ++dz)
+                for (int dy = 0; dy <= oy; ++dy)
+                    for (int dx = 0; dx <= ox; ++dx)
+                        s = __dadd_rn(s, ec[nidx(wrap_(X + dx, cx), wrap_(Y + dy, cy), wrap_(Z + dz, cz), cx, cy)]);
+            phi[i] = __dadd_rn(phi[i], __dmul_rn(s, 1.0 / (double)(1 << (ox + oy + oz))));
+        }
+        __syncthreads();
+        s_smooth(P, l, phi, f_all + P.offs[l], r_all + P.offs[l], 2);
+    }
+    const int n0 = P.dim[P.ls][0] * P.dim[P.ls][1] * P.dim[P.ls][2];
+    for (int i = threadIdx.x; i < n0; i += ST) phi_g[P.off_ls + i] = phi_all[i];
+}
+
 }  // namespace
 
 MgPlan mg_plan(int nx, int ny, int nz)
@@ -232,20 +369,21 @@ static bool level_even(const MgPlan& p, int l)
     return p.dim[l][0] % 2 == 0 && p.dim[l][1] % 2 == 0 && p.dim[l][2] % 2 == 0;
 }
 
+static dim3 rows(int nx_threads, int ny, int nz) { return dim3((unsigned)((nx_threads + XT - 1) / XT), ny, nz); }
+
 static void smooth(const MgPlan& p, int l, const MgBuffers& b, int sweeps, cudaStream_t st)
 {
     const int nx = p.dim[l][0], ny = p.dim[l][1], nz = p.dim[l][2];
-    const int64_t n = (int64_t)nx * ny * nz;
     double* phi = b.phi + p.off[l];
     const double* f = b.f + p.off[l];
     for (int k = 0; k < sweeps; ++k) {
         if (level_even(p, l)) {
-            k_mg_rb<<<grid_for(n), PT, 0, st>>>(phi, f, nx, ny, nz, 0);
-            k_mg_rb<<<grid_for(n), PT, 0, st>>>(phi, f, nx, ny, nz, 1);
+            k_mg_rb<<<rows(nx / 2, ny, nz), XT, 0, st>>>(phi, f, nx, ny, nz, 0);
+            k_mg_rb<<<rows(nx / 2, ny, nz), XT, 0, st>>>(phi, f, nx, ny, nz, 1);
         } else {  // two Jacobi half-steps through the scratch level buffer
             double* tmp = b.r + p.off[l];
-            k_mg_jacobi<<<grid_for(n), PT, 0, st>>>(phi, tmp, f, nx, ny, nz, 6.0 / 7.0);
-            k_mg_jacobi<<<grid_for(n), PT, 0, st>>>(tmp, phi, f, nx, ny, nz, 6.0 / 7.0);
+            k_mg_jacobi<<<rows(nx, ny, nz), XT, 0, st>>>(phi, tmp, f, nx, ny, nz, 6.0 / 7.0);
+            k_mg_jacobi<<<rows(nx, ny, nz), XT, 0, st>>>(tmp, phi, f, nx, ny, nz, 6.0 / 7.0);
         }
     }
 }
@@ -257,38 +395,86 @@ static void sub_mean(double* v, int64_t n, const MgBuffers& b, cudaStream_t st)
     k_mg_sub_mean<<<grid_for(n), PT, 0, st>>>(v, n, b.scalar);
 }
 
+static int coarse_sweeps(const MgPlan& p)
+{
+    const int l = p.levels - 1;
+    const int m = std::max(p.dim[l][0], std::max(p.dim[l][1], p.dim[l][2]));
+    return std::max(8, 2 * m * m);
+}
+
+// first level from which all coarser levels fit one block's shared memory
+// (phi, f and scratch: 24 bytes per node), or levels
+static int first_small(const MgPlan& p)
+{
+    int ls = p.levels;
+    int64_t nodes = 0;
+    while (ls > 0) {
+        const int64_t n = (int64_t)p.dim[ls - 1][0] * p.dim[ls - 1][1] * p.dim[ls - 1][2];
+        if (24 * (nodes + n) > SMALL_BYTES) break;
+        nodes += n;
+        --ls;
+    }
+    return ls;
+}
+
 static void vcycle(const MgPlan& p, int l, const MgBuffers& b, cudaStream_t st)
 {
     const int nx = p.dim[l][0], ny = p.dim[l][1], nz = p.dim[l][2];
     const int64_t n = (int64_t)nx * ny * nz;
+    if (l == first_small(p)) {  // the rest of the cycle in one block, in shared memory
+        SmallLevels P{};
+        P.ls = l;
+        P.levels = p.levels;
+        int nodes = 0;
+        for (int k = 0; k < p.levels; ++k) {
+            for (int d = 0; d < 3; ++d) P.dim[k][d] = p.dim[k][d];
+            if (k >= l) {
+                P.offs[k] = nodes;
+                nodes += p.dim[k][0] * p.dim[k][1] * p.dim[k][2];
+            }
+        }
+        P.nodes = nodes;
+        P.off_ls = p.off[l];
+        P.coarse_sweeps = coarse_sweeps(p);
+        const size_t bytes = sizeof(double) * 3 * (size_t)nodes;
+        static bool opted[64] = {};  // the shared-memory opt-in, once per device
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev >= 0 && dev < 64 && !opted[dev]) {
+            cudaFuncSetAttribute(k_mg_small, cudaFuncAttributeMaxDynamicSharedMemorySize, SMALL_BYTES);
+            opted[dev] = true;
+        }
+        k_mg_small<<<1, ST, bytes, st>>>(P, b.phi, b.f);
+        return;
+    }
     if (l == p.levels - 1) {  // coarsest: zero-mean right-hand side, many sweeps
         sub_mean(b.f + p.off[l], n, b, st);
-        const int m = std::max(nx, std::max(ny, nz));
-        smooth(p, l, b, std::max(8, 2 * m * m), st);
+        smooth(p, l, b, coarse_sweeps(p), st);
         return;
     }
     smooth(p, l, b, 2, st);
-    k_mg_residual<<<grid_for(n), PT, 0, st>>>(b.phi + p.off[l], b.f + p.off[l], b.r + p.off[l], nx, ny, nz);
+    k_mg_residual<<<rows(nx, ny, nz), XT, 0, st>>>(b.phi + p.off[l], b.f + p.off[l], b.r + p.off[l], nx, ny, nz);
     const int64_t nc = (int64_t)p.dim[l + 1][0] * p.dim[l + 1][1] * p.dim[l + 1][2];
-    k_mg_restrict<<<grid_for(nc), PT, 0, st>>>(b.r + p.off[l], b.f + p.off[l + 1], nx, ny, nz);
+    k_mg_restrict<<<rows(nx / 2, ny / 2, nz / 2), XT, 0, st>>>(b.r + p.off[l], b.f + p.off[l + 1], nx, ny, nz);
     cudaMemsetAsync(b.phi + p.off[l + 1], 0, sizeof(double) * nc, st);
     vcycle(p, l + 1, b, st);
-    k_mg_prolong<<<grid_for(n), PT, 0, st>>>(b.phi + p.off[l + 1], b.phi + p.off[l], nx, ny, nz);
+    k_mg_prolong<<<rows(nx, ny, nz), XT, 0, st>>>(b.phi + p.off[l + 1], b.phi + p.off[l], nx, ny, nz);
     smooth(p, l, b, 2, st);
 }
 
 int64_t mg_cycle_kernels(const MgPlan& p)
 {
+    const int ls = first_small(p);
     int64_t k = 0;
-    for (int l = 0; l < p.levels - 1; ++l) k += 4 + 1 + 1 + 1 + 4;  // smooth, residual, restrict, prolong, smooth
-    const int l = p.levels - 1;
-    const int m = std::max(p.dim[l][0], std::max(p.dim[l][1], p.dim[l][2]));
-    return k + 3 + 2 * (int64_t)std::max(8, 2 * m * m);  // coarsest: mean, sweeps
+    for (int l = 0; l < std::min(ls, p.levels - 1); ++l) k += 4 + 1 + 1 + 1 + 4;  // smooth, residual, restrict,
+                                                                                 // prolong, smooth
+    if (ls < p.levels) return k + 1;                                            // the one-block rest
+    return k + 3 + 2 * (int64_t)coarse_sweeps(p);                               // coarsest: mean, sweeps
 }
 
 cudaError_t elec_solve(const RepDesc& D, const VacRec* recs, const int32_t* counts, int cap, int64_t n_vac,
                        double q, double scale, int cycles, const MgPlan& p, const MgBuffers& b, double* resid_rel,
-                       cudaStream_t st)
+                       const double* init, double* save, cudaStream_t st)
 {
     const int64_t n = p.dim[0][0] * (int64_t)p.dim[0][1] * p.dim[0][2];
     cudaError_t e = cudaMemsetAsync(b.cnt, 0, sizeof(int32_t) * n, st);
@@ -296,12 +482,18 @@ cudaError_t elec_solve(const RepDesc& D, const VacRec* recs, const int32_t* coun
     const int64_t nfrag = (int64_t)D.nf[0] * D.nf[1] * D.nf[2];
     k_mg_deposit<<<grid_for(nfrag * cap), PT, 0, st>>>(D, recs, counts, cap, b.cnt);
     k_mg_rhs<<<grid_for(n), PT, 0, st>>>(b.cnt, n, 0.5 * q, q * (double)n_vac / (double)n, scale, b.f);
-    e = cudaMemsetAsync(b.phi, 0, sizeof(double) * n, st);
+    e = init ? cudaMemcpyAsync(b.phi, init, sizeof(double) * n, cudaMemcpyDeviceToDevice, st)
+             : cudaMemsetAsync(b.phi, 0, sizeof(double) * n, st);  // warm start from the last solve
     if (e != cudaSuccess) return e;
     for (int c = 0; c < cycles; ++c) vcycle(p, 0, b, st);
     sub_mean(b.phi, n, b, st);
+    if (save) {
+        e = cudaMemcpyAsync(save, b.phi, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+    }
     if (resid_rel) {  // max |f - A phi| / max |f|
-        k_mg_residual<<<grid_for(n), PT, 0, st>>>(b.phi, b.f, b.r, p.dim[0][0], p.dim[0][1], p.dim[0][2]);
+        k_mg_residual<<<rows(p.dim[0][0], p.dim[0][1], p.dim[0][2]), XT, 0, st>>>(b.phi, b.f, b.r, p.dim[0][0],
+                                                                                   p.dim[0][1], p.dim[0][2]);
         k_mg_partial<<<MG_PARTIALS, PT, 0, st>>>(b.r, n, b.part, 1);
         k_mg_final<<<1, 32, 0, st>>>(b.part, MG_PARTIALS, b.scalar, 1);
         k_mg_partial<<<MG_PARTIALS, PT, 0, st>>>(b.f, n, b.part, 1);

@@ -49,7 +49,7 @@ class kmc_grains(C.Structure):
 
 class kmc_electrostatics(C.Structure):
     _fields_ = [("eps_r", C.c_double), ("q_vac", C.c_double), ("refresh_windows", C.c_int32),
-                ("cycles", C.c_int32)]
+                ("cycles", C.c_int32), ("warm_cycles", C.c_int32)]
 
 
 class kmc_barrier_table(C.Structure):
@@ -330,13 +330,14 @@ def kmc_site_shells(vv, fe, t: int) -> np.ndarray:
     return out[: n.value]
 
 
-def kmc_set_electrostatics(h, eps_r=None, q_vac=2.0, refresh_windows=8, cycles=12):
+def kmc_set_electrostatics(h, eps_r=None, q_vac=2.0, refresh_windows=8, cycles=12, warm_cycles=0):
     """Potential of the vacancy charges (multigrid), refreshed every
-    refresh_windows windows; eps_r None turns it off."""
+    refresh_windows windows (warm_cycles V-cycles from the last potential, 0:
+    cycles); eps_r None turns it off."""
     if eps_r is None:
         _check(load().kmc_set_electrostatics(h, None))
         return
-    e = kmc_electrostatics(float(eps_r), float(q_vac), int(refresh_windows), int(cycles))
+    e = kmc_electrostatics(float(eps_r), float(q_vac), int(refresh_windows), int(cycles), int(warm_cycles))
     _check(load().kmc_set_electrostatics(h, C.byref(e)))
 
 
@@ -515,8 +516,8 @@ class Batch:
     def set_site_energy(self, vv=(), fe=()):
         kmc_set_site_energy(self.h, vv, fe)
 
-    def set_electrostatics(self, eps_r=None, q_vac=2.0, refresh_windows=8, cycles=12):
-        kmc_set_electrostatics(self.h, eps_r, q_vac, refresh_windows, cycles)
+    def set_electrostatics(self, eps_r=None, q_vac=2.0, refresh_windows=8, cycles=12, warm_cycles=0):
+        kmc_set_electrostatics(self.h, eps_r, q_vac, refresh_windows, cycles, warm_cycles)
 
     def solve_potential(self, r=0):
         """(phi at every B node [z][y][x] flattened, relative residual)"""

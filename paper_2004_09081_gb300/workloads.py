@@ -112,6 +112,19 @@ def um_grains(seed: int = 0, L=(1600, 400, 2400), n_grains: int = 16) -> Workloa
                     notes={"grains": (n_grains, 1, 0.2)})
 
 
+def elec_batio3(seed: int = 0, L: int = 128) -> Workload:
+    """BaTiO3 L^3 cells, 0.1% O vacancies (charge +2) whose own potential
+    (Poisson, multigrid) enters the rates, solved again every 8 windows (6
+    V-cycles from the last potential; 12 for the first solve);
+    eps_r = 1000 (BaTiO3's static permittivity is of that order), the bias as
+    1e7 V/m, 400 K, Ea 0.70 eV, edge-4 fragments, plain form."""
+    nsite = 3 * L**3
+    r = Replica((L, L, L), A_BATIO3, round_half_up(0.001 * nsite), 0, 400.0, 0.70, 0.70, field_z=1e7)
+    return Workload(f"batio3_{L}c_elec", [r], edge=4, precision=0, windows=32,
+                    notes={"elec": {"eps_r": 1000.0, "q_vac": 2.0, "refresh_windows": 8, "cycles": 12,
+                                    "warm_cycles": 6}})
+
+
 def null_batio3(seed: int = 0) -> Workload:
     """The 128^3 BaTiO(3-x)H_x lattice (x = 0.05: 104,858 H; 0.3% vacancies:
     18,874 V; 400 K; barriers 0.70 / 0.35 eV) run with the paper's atom-based
@@ -170,4 +183,4 @@ def fe_srtio3(seed: int = 0, L: int = 96) -> Workload:
 
 ALL = {"small": small_srtio3, "sweep": srtio3_h_sweep, "batched": batched_batio3,
        "bulk": bulk_batio3, "um": um_batio3_bias, "fe": fe_srtio3, "null": null_batio3,
-       "htrend": h_trend, "umgrains": um_grains}
+       "htrend": h_trend, "umgrains": um_grains, "elec": elec_batio3}
