@@ -173,8 +173,14 @@ struct kmc_batch {
     uint64_t elec_age = 0;              // windows since the last refresh
     MgPlan mg{};
     MgBuffers mgb{};
-    int64_t mg_total = -1;
+    int64_t mg_total = -1, mg_nodes = -1;
     double* phi_prev = nullptr;         // each replica's last potential (warm start of the next solve)
+    struct ElecGraph {                  // one refresh solve + update of replica r, captured
+        int r, cycles;
+        bool warm, field;
+        cudaGraphExec_t exec;
+    };
+    std::vector<ElecGraph> elec_graphs;
     bool phi_prev_valid = false;
     // grains (mu-scale model): boundary cells raise the barrier of hops touching them
     bool grains_on = false;
@@ -250,6 +256,8 @@ struct kmc_batch {
         if (window_exec) cudaGraphExecDestroy(window_exec);
         if (null_exec) cudaGraphExecDestroy(null_exec);
         null_exec = nullptr;
+        for (auto& g : elec_graphs) cudaGraphExecDestroy(g.exec);
+        elec_graphs.clear();
         if (cap_st) cudaStreamDestroy(cap_st);
         window_exec = nullptr;
         cap_st = nullptr;
@@ -619,16 +627,35 @@ int elec_refresh(kmc_batch* b)
 {
     CK(cudaMemsetAsync(b->d_umax, 0, sizeof(unsigned), b->st), "memset");
     const int cycles = refresh_cycles(b);
+    const bool warm = b->phi_prev_valid, with_field = b->field_valid;
+    if (!b->cap_st) CK(cudaStreamCreateWithFlags(&b->cap_st, cudaStreamNonBlocking), "stream");
     for (int r = 0; r < b->n; ++r) {
-        const RepDesc& D = b->desc[r];
-        const MgPlan p = mg_plan(D.L[0], D.L[1], D.L[2]);
-        const double scale = 1.602176634e-19 / (8.8541878128e-12 * b->elec.eps_r * b->a_ang[r] * 1e-10);
-        double* prev = b->phi_prev + D.site_off / 3;
-        CK(elec_solve(D, b->recs, b->counts, b->cap, b->n_vac[r], b->elec.q_vac, scale, cycles, p, b->mgb,
-                      nullptr, b->phi_prev_valid ? prev : nullptr, prev, b->st),
-           "potential solve");
-        CK(elec_update(D, b->mgb.phi, b->elec.q_vac, b->elec_u, b->field_valid ? b->field : nullptr, b->d_umax, b->st),
-           "potential update");
+        // each replica's solve is one graph (some 40 launches per V-cycle); every
+        // argument is fixed until the window graph is dropped, which drops these too
+        cudaGraphExec_t exec = nullptr;
+        for (auto& g : b->elec_graphs)
+            if (g.r == r && g.cycles == cycles && g.warm == warm && g.field == with_field) exec = g.exec;
+        if (!exec) {
+            const RepDesc& D = b->desc[r];
+            const MgPlan p = mg_plan(D.L[0], D.L[1], D.L[2]);
+            const double scale = 1.602176634e-19 / (8.8541878128e-12 * b->elec.eps_r * b->a_ang[r] * 1e-10);
+            double* prev = b->phi_prev + D.site_off / 3;
+            cudaGraph_t graph = nullptr;
+            CK(cudaStreamBeginCapture(b->cap_st, cudaStreamCaptureModeThreadLocal), "graph capture");
+            cudaError_t le = elec_solve(D, b->recs, b->counts, b->cap, b->n_vac[r], b->elec.q_vac, scale, cycles, p,
+                                        b->mgb, nullptr, warm ? prev : nullptr, prev, b->cap_st);
+            if (le == cudaSuccess)
+                le = elec_update(D, b->mgb.phi, b->elec.q_vac, b->elec_u, with_field ? b->field : nullptr, b->d_umax,
+                                 b->cap_st);
+            cudaError_t ce = cudaStreamEndCapture(b->cap_st, &graph);
+            if (le != cudaSuccess) return cuda_fail(le, "potential solve capture");
+            if (ce != cudaSuccess) return cuda_fail(ce, "potential solve capture");
+            cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) return cuda_fail(ie, "graph instantiate");
+            b->elec_graphs.push_back({r, cycles, warm, with_field, exec});
+        }
+        CK(cudaGraphLaunch(exec, b->st), "graph launch");
     }
     unsigned um = 0;
     CK(cudaMemcpyAsync(&um, b->d_umax, sizeof um, cudaMemcpyDeviceToHost, b->st), "copy");
@@ -650,6 +677,8 @@ void drop_window_graph(kmc_batch* b)
 {
     if (b->window_exec) cudaGraphExecDestroy(b->window_exec);
     b->window_exec = nullptr;
+    for (auto& g : b->elec_graphs) cudaGraphExecDestroy(g.exec);
+    b->elec_graphs.clear();
 }
 
 }  // namespace
@@ -1266,6 +1295,7 @@ int kmc_write_state(kmc_batch* b, int32_t r, const uint8_t* host_occ, size_t n)
     b->field_valid = false;
     b->elec_age = UINT64_MAX / 2;  // the potential is solved again at the next refresh point
     b->phi_prev_valid = false;  // and from zero: the vacancies may have moved anywhere
+    drop_window_graph(b);       // the captured solves hold the vacancy count
     if (b->rates_set) {
         int rc = plan_residency(b);
         if (rc) return rc;
@@ -1372,6 +1402,7 @@ int kmc_upload_state(kmc_batch* b, const void* host, size_t bytes)
     b->field_valid = false;
     b->elec_age = UINT64_MAX / 2;
     b->phi_prev_valid = false;
+    drop_window_graph(b);
     return FKMC_OK;
 }
 
@@ -1509,19 +1540,25 @@ int kmc_set_electrostatics(kmc_batch* b, const kmc_electrostatics* e)
     if (!b->d_elec_g) b->d_elec_g = (int32_t*)b->dalloc(sizeof(int32_t) * 24 * b->n);
     if (!b->d_umax) b->d_umax = (unsigned*)b->dalloc(sizeof(unsigned));
     if (!b->field) b->field = (int32_t*)b->dalloc(sizeof(int32_t) * b->nsite_total);
-    if (total > b->mg_total) {
-        for (void* q : {(void*)b->mgb.phi, (void*)b->mgb.f, (void*)b->mgb.r, (void*)b->mgb.cnt}) b->dfree(q);
-        b->mgb.phi = (double*)b->dalloc(sizeof(double) * total);
-        b->mgb.f = (double*)b->dalloc(sizeof(double) * total);
-        b->mgb.r = (double*)b->dalloc(sizeof(double) * total);
+    if (total > b->mg_total || nodes > b->mg_nodes) {
+        for (void* q : {(void*)b->mgb.phi, (void*)b->mgb.f, (void*)b->mgb.r, (void*)b->mgb.e, (void*)b->mgb.g,
+                        (void*)b->mgb.s, (void*)b->mgb.cnt})
+            b->dfree(q);
+        b->mgb.phi = (double*)b->dalloc(sizeof(double) * nodes);
+        b->mgb.f = (double*)b->dalloc(sizeof(double) * nodes);
+        b->mgb.r = (double*)b->dalloc(sizeof(double) * nodes);
+        b->mgb.e = (float*)b->dalloc(sizeof(float) * total);
+        b->mgb.g = (float*)b->dalloc(sizeof(float) * total);
+        b->mgb.s = (float*)b->dalloc(sizeof(float) * total);
         b->mgb.cnt = (int32_t*)b->dalloc(sizeof(int32_t) * nodes);
         b->mg_total = total;
+        b->mg_nodes = nodes;
     }
     if (!b->phi_prev) b->phi_prev = (double*)b->dalloc(sizeof(double) * b->ncell_total);
     if (!b->mgb.part) b->mgb.part = (double*)b->dalloc(sizeof(double) * MG_PARTIALS);
     if (!b->mgb.scalar) b->mgb.scalar = (double*)b->dalloc(sizeof(double) * 2);
     if (!b->elec_u || !b->d_elec_g || !b->d_umax || !b->field || !b->phi_prev || !b->mgb.phi || !b->mgb.f || !b->mgb.r ||
-        !b->mgb.cnt || !b->mgb.part || !b->mgb.scalar)
+        !b->mgb.e || !b->mgb.g || !b->mgb.s || !b->mgb.cnt || !b->mgb.part || !b->mgb.scalar)
         return fail(FKMC_ENOMEM, "device allocation failed (electrostatics)");
     b->elec = *e;
     b->phi_prev_valid = false;  // the first solve starts from zero

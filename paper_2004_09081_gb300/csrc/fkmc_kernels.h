@@ -54,9 +54,12 @@ struct MgPlan {
     int64_t total;
 };
 struct MgBuffers {
-    double* phi;     // [total] solution / correction per level
-    double* f;       // [total] right-hand side per level
-    double* r;       // [total] residual (and the Jacobi scratch of an odd level)
+    double* phi;     // [level-0 nodes] the potential (FP64)
+    double* f;       // [level-0 nodes] right-hand side (FP64)
+    double* r;       // [level-0 nodes] residual of the final check
+    float* e;        // [total] FP32 correction per level
+    float* g;        // [total] FP32 right-hand side per level (level 0: the FP64 defect, rounded)
+    float* s;        // [total] FP32 residual (and the Jacobi scratch of an odd level)
     int32_t* cnt;    // [level-0 nodes] half-charge counts
     double* part;    // [MG_PARTIALS]
     double* scalar;  // [2]

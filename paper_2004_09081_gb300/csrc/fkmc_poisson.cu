@@ -7,10 +7,11 @@
 //
 //     6 phi(n) - sum_{6 neighbours} phi(n') = Q(n) / (eps0 eps_r a)        [V]
 //
-// solved by a geometric multigrid V-cycle (vertex-centred coarsening by 2
-// while every dimension is even; red-black Gauss-Seidel where all dimensions
-// of a level are even, damped Jacobi otherwise and on the coarsest level;
-// full-weighting restriction, trilinear prolongation).  Every reduction is
+// solved by defect correction in FP64 around geometric multigrid V-cycles in
+// FP32 (vertex-centred coarsening by 2 while every dimension is even;
+// red-black Gauss-Seidel where all dimensions of a level are even, damped
+// Jacobi otherwise and on the coarsest level; full-weighting restriction,
+// trilinear prolongation).  Every reduction is
 // deterministic (block partials summed in a fixed order), so a solve is
 // reproducible bit for bit.  The potential then enters the hop rates through
 // the site-energy field: u(s) = rint(q phi(s) 1e4), phi(s) the mean of the
@@ -58,103 +59,133 @@ __global__ void k_mg_rhs(const int32_t* cnt, int64_t n, double half_q, double ba
 }
 
 // The level-by-level stencil kernels run on 3-D grids: blockIdx.y / blockIdx.z
-// are the row (y, z), threads walk x; all index arithmetic is 32-bit.
+// are the row (y, z), threads walk x; all index arithmetic is 32-bit.  They are
+// templates over the number type: the V-cycle runs in FP32 (below, the FP64
+// defect correction around it), the final residual check in FP64.
 constexpr int XT = 128;
 constexpr double SIXTH = 1.0 / 6.0;
 
-__device__ __forceinline__ double nb_sum(const double* v, int x, int y, int z, int nx, int ny, int nz)
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+
+template <typename T>
+__device__ __forceinline__ T nb_sum(const T* v, int x, int y, int z, int nx, int ny, int nz)
 {
     const int row = (z * ny + y) * nx;
     const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
     const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
     const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-    double s = v[row + xm];
-    s = __dadd_rn(s, v[row + xp]);
-    s = __dadd_rn(s, v[(z * ny + ym) * nx + x]);
-    s = __dadd_rn(s, v[(z * ny + yp) * nx + x]);
-    s = __dadd_rn(s, v[(zm * ny + y) * nx + x]);
-    s = __dadd_rn(s, v[(zp * ny + y) * nx + x]);
+    T s = v[row + xm];
+    s = add_rn(s, v[row + xp]);
+    s = add_rn(s, v[(z * ny + ym) * nx + x]);
+    s = add_rn(s, v[(z * ny + yp) * nx + x]);
+    s = add_rn(s, v[(zm * ny + y) * nx + x]);
+    s = add_rn(s, v[(zp * ny + y) * nx + x]);
     return s;
 }
 
 // red-black Gauss-Seidel half-sweep over the nodes of one colour (all
 // dimensions even: the colouring is consistent across the periodic seams);
 // thread k of a row takes x = 2k + the row's colour offset
-__global__ void __launch_bounds__(XT) k_mg_rb(double* phi, const double* f, int nx, int ny, int nz, int colour)
+template <typename T>
+__global__ void __launch_bounds__(XT) k_mg_rb(T* phi, const T* f, int nx, int ny, int nz, int colour)
 {
     const int y = blockIdx.y, z = blockIdx.z;
     const int x = 2 * (blockIdx.x * XT + threadIdx.x) + ((y + z + colour) & 1);
     if (x >= nx) return;
     const int i = (z * ny + y) * nx + x;
-    phi[i] = __dmul_rn(__dadd_rn(f[i], nb_sum(phi, x, y, z, nx, ny, nz)), SIXTH);
+    phi[i] = mul_rn(add_rn(f[i], nb_sum(phi, x, y, z, nx, ny, nz)), (T)SIXTH);
 }
 
 // damped Jacobi sweep, out = (1-w) in + w (f + sum nb) / 6
-__global__ void __launch_bounds__(XT) k_mg_jacobi(const double* in, double* out, const double* f, int nx, int ny,
-                                                   int nz, double w)
+template <typename T>
+__global__ void __launch_bounds__(XT) k_mg_jacobi(const T* in, T* out, const T* f, int nx, int ny, int nz, T w)
 {
     const int y = blockIdx.y, z = blockIdx.z, x = blockIdx.x * XT + threadIdx.x;
     if (x >= nx) return;
     const int i = (z * ny + y) * nx + x;
-    const double gs = __dmul_rn(__dadd_rn(f[i], nb_sum(in, x, y, z, nx, ny, nz)), SIXTH);
-    out[i] = __dadd_rn(__dmul_rn(1.0 - w, in[i]), __dmul_rn(w, gs));
+    const T gs = mul_rn(add_rn(f[i], nb_sum(in, x, y, z, nx, ny, nz)), (T)SIXTH);
+    out[i] = add_rn(mul_rn((T)1 - w, in[i]), mul_rn(w, gs));
 }
 
 // r = f - A phi
-__global__ void __launch_bounds__(XT) k_mg_residual(const double* phi, const double* f, double* r, int nx, int ny,
-                                                     int nz)
+template <typename T>
+__global__ void __launch_bounds__(XT) k_mg_residual(const T* phi, const T* f, T* r, int nx, int ny, int nz)
 {
     const int y = blockIdx.y, z = blockIdx.z, x = blockIdx.x * XT + threadIdx.x;
     if (x >= nx) return;
     const int i = (z * ny + y) * nx + x;
-    r[i] = __dadd_rn(f[i], -__dadd_rn(__dmul_rn(6.0, phi[i]), -nb_sum(phi, x, y, z, nx, ny, nz)));
+    r[i] = add_rn(f[i], -add_rn(mul_rn((T)6, phi[i]), -nb_sum(phi, x, y, z, nx, ny, nz)));
+}
+
+// the defect of the FP64 potential, d = f - A phi in FP64, rounded to FP32: the
+// right-hand side of the FP32 correction cycle
+__global__ void __launch_bounds__(XT) k_mg_defect(const double* phi, const double* f, float* d, int nx, int ny,
+                                                   int nz)
+{
+    const int y = blockIdx.y, z = blockIdx.z, x = blockIdx.x * XT + threadIdx.x;
+    if (x >= nx) return;
+    const int i = (z * ny + y) * nx + x;
+    d[i] = __double2float_rn(__dadd_rn(f[i], -__dadd_rn(__dmul_rn(6.0, phi[i]), -nb_sum(phi, x, y, z, nx, ny, nz))));
+}
+
+// phi += e (the FP32 correction, converted exactly)
+__global__ void k_mg_correct(double* phi, const float* e, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        phi[i] = __dadd_rn(phi[i], (double)e[i]);
 }
 
 // coarse f = 4 x full weighting of the fine residual (weights (1,2,1)^3 / 64);
 // the grid covers the coarse level
-__global__ void __launch_bounds__(XT) k_mg_restrict(const double* r, double* fc, int nx, int ny, int nz)
+template <typename T>
+__global__ void __launch_bounds__(XT) k_mg_restrict(const T* r, T* fc, int nx, int ny, int nz)
 {
     const int cx = nx / 2, cy = ny / 2;
     const int Y = blockIdx.y, Z = blockIdx.z, X = blockIdx.x * XT + threadIdx.x;
     if (X >= cx) return;
-    double s = 0.0;
+    T s = 0;
     for (int dz = -1; dz <= 1; ++dz) {
         const int zz = wrap_(2 * Z + dz, nz);
         for (int dy = -1; dy <= 1; ++dy) {
             const int yy = wrap_(2 * Y + dy, ny);
-            const double* row = r + (zz * ny + yy) * nx;
-            const double wr = (double)((2 - (dz != 0)) * (2 - (dy != 0)));
-            const double line = __dadd_rn(__dadd_rn(row[wrap_(2 * X - 1, nx)], __dmul_rn(2.0, row[2 * X])),
-                                          row[wrap_(2 * X + 1, nx)]);
-            s = __dadd_rn(s, __dmul_rn(wr, line));
+            const T* row = r + (zz * ny + yy) * nx;
+            const T wr = (T)((2 - (dz != 0)) * (2 - (dy != 0)));
+            const T line = add_rn(add_rn(row[wrap_(2 * X - 1, nx)], mul_rn((T)2, row[2 * X])), row[wrap_(2 * X + 1, nx)]);
+            s = add_rn(s, mul_rn(wr, line));
         }
     }
-    fc[(Z * cy + Y) * cx + X] = __dmul_rn(s, 4.0 / 64.0);
+    fc[(Z * cy + Y) * cx + X] = mul_rn(s, (T)(4.0 / 64.0));
 }
 
 // phi_fine += trilinear interpolation of the coarse correction
-__global__ void __launch_bounds__(XT) k_mg_prolong(const double* ec, double* phi, int nx, int ny, int nz)
+template <typename T>
+__global__ void __launch_bounds__(XT) k_mg_prolong(const T* ec, T* phi, int nx, int ny, int nz)
 {
     const int y = blockIdx.y, z = blockIdx.z, x = blockIdx.x * XT + threadIdx.x;
     if (x >= nx) return;
     const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
     const int X = x >> 1, Y = y >> 1, Z = z >> 1, ox = x & 1, oy = y & 1, oz = z & 1;
-    double s = 0.0;
+    T s = 0;
     for (int dz = 0; dz <= oz; ++dz)
         for (int dy = 0; dy <= oy; ++dy)
             for (int dx = 0; dx <= ox; ++dx)
-                s = __dadd_rn(s, ec[(wrap_(Z + dz, cz) * cy + wrap_(Y + dy, cy)) * cx + wrap_(X + dx, cx)]);
+                s = add_rn(s, ec[(wrap_(Z + dz, cz) * cy + wrap_(Y + dy, cy)) * cx + wrap_(X + dx, cx)]);
     const int i = (z * ny + y) * nx + x;
-    phi[i] = __dadd_rn(phi[i], __dmul_rn(s, 1.0 / (double)(1 << (ox + oy + oz))));
+    phi[i] = add_rn(phi[i], mul_rn(s, (T)(1.0 / (double)(1 << (ox + oy + oz)))));
 }
 
-// deterministic sum: per-block partials (fixed grid), then one thread in order
-__global__ void k_mg_partial(const double* v, int64_t n, double* part, int absmax)
+// deterministic sum (or max |v|) in FP64: per-block partials (fixed grid), then
+// one thread in order
+template <typename T>
+__global__ void k_mg_partial(const T* v, int64_t n, double* part, int absmax)
 {
     __shared__ double sh[PT];
     double s = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * PT + threadIdx.x; i < n; i += (int64_t)gridDim.x * PT)
-        s = absmax ? fmax(s, fabs(v[i])) : __dadd_rn(s, v[i]);
+        s = absmax ? fmax(s, fabs((double)v[i])) : __dadd_rn(s, (double)v[i]);
     sh[threadIdx.x] = s;
     __syncthreads();
     for (int w = PT / 2; w; w >>= 1) {
@@ -175,11 +206,12 @@ __global__ void k_mg_final(const double* part, int nb, double* out, int absmax)
 }
 
 // v -= sum / n (sum from k_mg_final)
-__global__ void k_mg_sub_mean(double* v, int64_t n, const double* sum)
+template <typename T>
+__global__ void k_mg_sub_mean(T* v, int64_t n, const double* sum)
 {
-    const double m = __ddiv_rn(*sum, (double)n);
+    const T m = (T)__ddiv_rn(*sum, (double)n);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        v[i] = __dadd_rn(v[i], -m);
+        v[i] = add_rn(v[i], -m);
 }
 
 // u(s) = rint(q phi(s) 1e4) per O site of replica D, phi(s) the mean of the two
@@ -209,55 +241,79 @@ __global__ void k_elec_add(int32_t* field, const int32_t* u, int64_t n)
 
 unsigned grid_for(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + PT - 1) / PT, 8192)); }
 
+
 // ---- the small levels of a V-cycle in one block: levels ls .. coarsest live
 // in shared memory (phi, f and scratch of each level, at most SMALL_BYTES), the
 // same operations as the level-by-level kernels separated by __syncthreads.
 // The block reads the iterate and right-hand side of level ls from global
-// memory and writes back the iterate after the sub-cycle.
+// memory and writes back the iterate after the sub-cycle.  Node coordinates
+// come from exact multiply-high division: for 2 <= d and i, d < 2^16,
+// floor(i / d) = umulhi(i, ceil(2^32 / d)) (the rounding excess of the
+// reciprocal, times i, stays below 2^32).
 constexpr int SMALL_BYTES = 200 * 1024;
 constexpr int ST = 1024;
 
 struct SmallLevels {
     int ls, levels;
     int dim[MG_MAX_LEVELS][3];
+    unsigned rx[MG_MAX_LEVELS], ry[MG_MAX_LEVELS];  // ceil(2^32 / nx), ceil(2^32 / ny)
     int offs[MG_MAX_LEVELS];  // node offset of each level in the shared arrays
     int nodes;                // shared nodes per array
     int64_t off_ls;           // global offset of level ls
     int coarse_sweeps;
 };
 
-__device__ void s_smooth(const SmallLevels& P, int l, double* phi, const double* f, double* tmp, int sweeps)
+__device__ __forceinline__ void s_coords(const SmallLevels& P, int l, int i, int& x, int& y, int& z)
+{
+    const int nx = P.dim[l][0], ny = P.dim[l][1];
+    const int q = (int)__umulhi((unsigned)i, P.rx[l]);
+    x = i - q * nx;
+    z = (int)__umulhi((unsigned)q, P.ry[l]);
+    y = q - z * ny;
+}
+
+template <typename T>
+__device__ __forceinline__ T s_nb(const T* v, int x, int y, int z, int nx, int ny, int nz)
+{
+    T s = v[nidx(wrap_(x - 1, nx), y, z, nx, ny)];
+    s = add_rn(s, v[nidx(wrap_(x + 1, nx), y, z, nx, ny)]);
+    s = add_rn(s, v[nidx(x, wrap_(y - 1, ny), z, nx, ny)]);
+    s = add_rn(s, v[nidx(x, wrap_(y + 1, ny), z, nx, ny)]);
+    s = add_rn(s, v[nidx(x, y, wrap_(z - 1, nz), nx, ny)]);
+    s = add_rn(s, v[nidx(x, y, wrap_(z + 1, nz), nx, ny)]);
+    return s;
+}
+
+template <typename T>
+__device__ void s_smooth(const SmallLevels& P, int l, T* phi, const T* f, T* tmp, int sweeps)
 {
     const int nx = P.dim[l][0], ny = P.dim[l][1], nz = P.dim[l][2];
     const int n = nx * ny * nz;
     const bool even = nx % 2 == 0 && ny % 2 == 0 && nz % 2 == 0;
+    const T w = (T)(6.0 / 7.0);
     for (int k = 0; k < sweeps; ++k) {
         for (int half = 0; half < 2; ++half) {
-            const double* in = even ? phi : (half == 0 ? phi : tmp);
-            double* out = even ? phi : (half == 0 ? tmp : phi);
+            const T* in = even ? phi : (half == 0 ? phi : tmp);
+            T* out = even ? phi : (half == 0 ? tmp : phi);
             for (int i = threadIdx.x; i < n; i += ST) {
-                const int x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
+                int x, y, z;
+                s_coords(P, l, i, x, y, z);
                 if (even && ((x + y + z) & 1) != half) continue;
-                double s = in[nidx(wrap_(x - 1, nx), y, z, nx, ny)];
-                s = __dadd_rn(s, in[nidx(wrap_(x + 1, nx), y, z, nx, ny)]);
-                s = __dadd_rn(s, in[nidx(x, wrap_(y - 1, ny), z, nx, ny)]);
-                s = __dadd_rn(s, in[nidx(x, wrap_(y + 1, ny), z, nx, ny)]);
-                s = __dadd_rn(s, in[nidx(x, y, wrap_(z - 1, nz), nx, ny)]);
-                s = __dadd_rn(s, in[nidx(x, y, wrap_(z + 1, nz), nx, ny)]);
-                const double gs = __dmul_rn(__dadd_rn(f[i], s), SIXTH);
-                out[i] = even ? gs : __dadd_rn(__dmul_rn(1.0 - 6.0 / 7.0, in[i]), __dmul_rn(6.0 / 7.0, gs));
+                const T gs = mul_rn(add_rn(f[i], s_nb(in, x, y, z, nx, ny, nz)), (T)SIXTH);
+                out[i] = even ? gs : add_rn(mul_rn((T)1 - w, in[i]), mul_rn(w, gs));
             }
             __syncthreads();
         }
     }
 }
 
-__global__ void __launch_bounds__(ST) k_mg_small(SmallLevels P, double* phi_g, const double* f_g)
+template <typename T>
+__global__ void __launch_bounds__(ST) k_mg_small(SmallLevels P, T* phi_g, const T* f_g)
 {
-    extern __shared__ __align__(16) double sm[];
-    double* phi_all = sm;
-    double* f_all = sm + P.nodes;
-    double* r_all = sm + 2 * P.nodes;
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    T* phi_all = reinterpret_cast<T*>(s_raw);
+    T* f_all = phi_all + P.nodes;
+    T* r_all = phi_all + 2 * P.nodes;
     __shared__ double red[ST];
     const int last = P.levels - 1;
     {
@@ -271,72 +327,69 @@ __global__ void __launch_bounds__(ST) k_mg_small(SmallLevels P, double* phi_g, c
     for (int l = P.ls; l < last; ++l) {  // down: pre-smooth, residual, restrict
         const int nx = P.dim[l][0], ny = P.dim[l][1], nz = P.dim[l][2];
         const int n = nx * ny * nz;
-        double* phi = phi_all + P.offs[l];
-        const double* f = f_all + P.offs[l];
-        double* r = r_all + P.offs[l];
+        T* phi = phi_all + P.offs[l];
+        const T* f = f_all + P.offs[l];
+        T* r = r_all + P.offs[l];
         s_smooth(P, l, phi, f, r, 2);
         for (int i = threadIdx.x; i < n; i += ST) {
-            const int x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
-            double s = phi[nidx(wrap_(x - 1, nx), y, z, nx, ny)];
-            s = __dadd_rn(s, phi[nidx(wrap_(x + 1, nx), y, z, nx, ny)]);
-            s = __dadd_rn(s, phi[nidx(x, wrap_(y - 1, ny), z, nx, ny)]);
-            s = __dadd_rn(s, phi[nidx(x, wrap_(y + 1, ny), z, nx, ny)]);
-            s = __dadd_rn(s, phi[nidx(x, y, wrap_(z - 1, nz), nx, ny)]);
-            s = __dadd_rn(s, phi[nidx(x, y, wrap_(z + 1, nz), nx, ny)]);
-            r[i] = __dadd_rn(f[i], -__dadd_rn(__dmul_rn(6.0, phi[i]), -s));
+            int x, y, z;
+            s_coords(P, l, i, x, y, z);
+            r[i] = add_rn(f[i], -add_rn(mul_rn((T)6, phi[i]), -s_nb(phi, x, y, z, nx, ny, nz)));
         }
         __syncthreads();
         const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
-        double* fc = f_all + P.offs[l + 1];
-        double* pc = phi_all + P.offs[l + 1];
+        T* fc = f_all + P.offs[l + 1];
+        T* pc = phi_all + P.offs[l + 1];
         for (int i = threadIdx.x; i < cx * cy * cz; i += ST) {
-            const int X = i % cx, Y = (i / cx) % cy, Z = i / (cx * cy);
-            double s = 0.0;
+            int X, Y, Z;
+            s_coords(P, l + 1, i, X, Y, Z);
+            T s = 0;
             for (int dz = -1; dz <= 1; ++dz)
                 for (int dy = -1; dy <= 1; ++dy)
                     for (int dx = -1; dx <= 1; ++dx) {
-                        const double w = (double)((2 - (dx != 0)) * (2 - (dy != 0)) * (2 - (dz != 0)));
-                        s = __dadd_rn(s, __dmul_rn(w, r[nidx(wrap_(2 * X + dx, nx), wrap_(2 * Y + dy, ny),
-                                                             wrap_(2 * Z + dz, nz), nx, ny)]));
+                        const T w = (T)((2 - (dx != 0)) * (2 - (dy != 0)) * (2 - (dz != 0)));
+                        s = add_rn(s, mul_rn(w, r[nidx(wrap_(2 * X + dx, nx), wrap_(2 * Y + dy, ny),
+                                                       wrap_(2 * Z + dz, nz), nx, ny)]));
                     }
-            fc[i] = __dmul_rn(s, 4.0 / 64.0);
-            pc[i] = 0.0;
+            fc[i] = mul_rn(s, (T)(4.0 / 64.0));
+            pc[i] = 0;
         }
         __syncthreads();
     }
-    {  // coarsest: zero-mean right-hand side (block tree sum, fixed order), sweeps
+    {  // coarsest: zero-mean right-hand side (block tree sum in FP64, fixed order), sweeps
         const int n = P.dim[last][0] * P.dim[last][1] * P.dim[last][2];
-        double* f = f_all + P.offs[last];
+        T* f = f_all + P.offs[last];
         double s = 0.0;
-        for (int i = threadIdx.x; i < n; i += ST) s = __dadd_rn(s, f[i]);
+        for (int i = threadIdx.x; i < n; i += ST) s = __dadd_rn(s, (double)f[i]);
         red[threadIdx.x] = s;
         __syncthreads();
         for (int w = ST / 2; w; w >>= 1) {
             if (threadIdx.x < w) red[threadIdx.x] = __dadd_rn(red[threadIdx.x], red[threadIdx.x + w]);
             __syncthreads();
         }
-        const double m = __ddiv_rn(red[0], (double)n);
-        for (int i = threadIdx.x; i < n; i += ST) f[i] = __dadd_rn(f[i], -m);
+        const T m = (T)__ddiv_rn(red[0], (double)n);
+        for (int i = threadIdx.x; i < n; i += ST) f[i] = add_rn(f[i], -m);
         __syncthreads();
-        s_smooth(P, last, phi_all + P.offs[last], f, r_all + P.offs[last], P.coarse_sweeps);
+        s_smooth(P, last, phi_all + P.offs[last], (const T*)f, r_all + P.offs[last], P.coarse_sweeps);
     }
     for (int l = last - 1; l >= P.ls; --l) {  // up: prolong, post-smooth
-        const int nx = P.dim[l][0], ny = P.dim[l][1], nz = P.dim[l][2];
-        const int n = nx * ny * nz, cx = nx / 2, cy = ny / 2, cz = nz / 2;
-        double* phi = phi_all + P.offs[l];
-        const double* ec = phi_all + P.offs[l + 1];
+        const int nx = P.dim[l][0], ny = P.dim[l][1];
+        const int n = nx * ny * P.dim[l][2], cx = nx / 2, cy = ny / 2, cz = P.dim[l][2] / 2;
+        T* phi = phi_all + P.offs[l];
+        const T* ec = phi_all + P.offs[l + 1];
         for (int i = threadIdx.x; i < n; i += ST) {
-            const int x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
+            int x, y, z;
+            s_coords(P, l, i, x, y, z);
             const int X = x >> 1, Y = y >> 1, Z = z >> 1, ox = x & 1, oy = y & 1, oz = z & 1;
-            double s = 0.0;
+            T s = 0;
             for (int dz = 0; dz <= oz; ++dz)
                 for (int dy = 0; dy <= oy; ++dy)
                     for (int dx = 0; dx <= ox; ++dx)
-                        s = __dadd_rn(s, ec[nidx(wrap_(X + dx, cx), wrap_(Y + dy, cy), wrap_(Z + dz, cz), cx, cy)]);
-            phi[i] = __dadd_rn(phi[i], __dmul_rn(s, 1.0 / (double)(1 << (ox + oy + oz))));
+                        s = add_rn(s, ec[nidx(wrap_(X + dx, cx), wrap_(Y + dy, cy), wrap_(Z + dz, cz), cx, cy)]);
+            phi[i] = add_rn(phi[i], mul_rn(s, (T)(1.0 / (double)(1 << (ox + oy + oz)))));
         }
         __syncthreads();
-        s_smooth(P, l, phi, f_all + P.offs[l], r_all + P.offs[l], 2);
+        s_smooth(P, l, phi, (const T*)(f_all + P.offs[l]), r_all + P.offs[l], 2);
     }
     const int n0 = P.dim[P.ls][0] * P.dim[P.ls][1] * P.dim[P.ls][2];
     for (int i = threadIdx.x; i < n0; i += ST) phi_g[P.off_ls + i] = phi_all[i];
@@ -371,28 +424,32 @@ static bool level_even(const MgPlan& p, int l)
 
 static dim3 rows(int nx_threads, int ny, int nz) { return dim3((unsigned)((nx_threads + XT - 1) / XT), ny, nz); }
 
-static void smooth(const MgPlan& p, int l, const MgBuffers& b, int sweeps, cudaStream_t st)
+// `sweeps` smoothing sweeps of level l on the level-stacked arrays u (iterate), f
+// and tmp (Jacobi scratch)
+template <typename T>
+static void smooth(const MgPlan& p, int l, T* u, const T* f, T* tmp, int sweeps, cudaStream_t st)
 {
     const int nx = p.dim[l][0], ny = p.dim[l][1], nz = p.dim[l][2];
-    double* phi = b.phi + p.off[l];
-    const double* f = b.f + p.off[l];
+    u += p.off[l];
+    f += p.off[l];
+    tmp += p.off[l];
     for (int k = 0; k < sweeps; ++k) {
         if (level_even(p, l)) {
-            k_mg_rb<<<rows(nx / 2, ny, nz), XT, 0, st>>>(phi, f, nx, ny, nz, 0);
-            k_mg_rb<<<rows(nx / 2, ny, nz), XT, 0, st>>>(phi, f, nx, ny, nz, 1);
+            k_mg_rb<T><<<rows(nx / 2, ny, nz), XT, 0, st>>>(u, f, nx, ny, nz, 0);
+            k_mg_rb<T><<<rows(nx / 2, ny, nz), XT, 0, st>>>(u, f, nx, ny, nz, 1);
         } else {  // two Jacobi half-steps through the scratch level buffer
-            double* tmp = b.r + p.off[l];
-            k_mg_jacobi<<<rows(nx, ny, nz), XT, 0, st>>>(phi, tmp, f, nx, ny, nz, 6.0 / 7.0);
-            k_mg_jacobi<<<rows(nx, ny, nz), XT, 0, st>>>(tmp, phi, f, nx, ny, nz, 6.0 / 7.0);
+            k_mg_jacobi<T><<<rows(nx, ny, nz), XT, 0, st>>>(u, tmp, f, nx, ny, nz, (T)(6.0 / 7.0));
+            k_mg_jacobi<T><<<rows(nx, ny, nz), XT, 0, st>>>(tmp, u, f, nx, ny, nz, (T)(6.0 / 7.0));
         }
     }
 }
 
-static void sub_mean(double* v, int64_t n, const MgBuffers& b, cudaStream_t st)
+template <typename T>
+static void sub_mean(T* v, int64_t n, const MgBuffers& b, cudaStream_t st)
 {
-    k_mg_partial<<<MG_PARTIALS, PT, 0, st>>>(v, n, b.part, 0);
+    k_mg_partial<T><<<MG_PARTIALS, PT, 0, st>>>(v, n, b.part, 0);
     k_mg_final<<<1, 32, 0, st>>>(b.part, MG_PARTIALS, b.scalar, 0);
-    k_mg_sub_mean<<<grid_for(n), PT, 0, st>>>(v, n, b.scalar);
+    k_mg_sub_mean<T><<<grid_for(n), PT, 0, st>>>(v, n, b.scalar);
 }
 
 static int coarse_sweeps(const MgPlan& p)
@@ -403,21 +460,24 @@ static int coarse_sweeps(const MgPlan& p)
 }
 
 // first level from which all coarser levels fit one block's shared memory
-// (phi, f and scratch: 24 bytes per node), or levels
+// (iterate, right-hand side and scratch: 12 bytes per node in FP32), or levels
 static int first_small(const MgPlan& p)
 {
     int ls = p.levels;
     int64_t nodes = 0;
     while (ls > 0) {
-        const int64_t n = (int64_t)p.dim[ls - 1][0] * p.dim[ls - 1][1] * p.dim[ls - 1][2];
-        if (24 * (nodes + n) > SMALL_BYTES) break;
+        const int* d = p.dim[ls - 1];
+        const int64_t n = (int64_t)d[0] * d[1] * d[2];
+        if (3 * (int64_t)sizeof(float) * (nodes + n) > SMALL_BYTES || d[0] < 2 || d[1] < 2) break;
         nodes += n;
         --ls;
     }
     return ls;
 }
 
-static void vcycle(const MgPlan& p, int l, const MgBuffers& b, cudaStream_t st)
+// one V-cycle from level l on the level-stacked FP32 arrays: u the iterate
+// (correction), f the right-hand side, r the residual / scratch
+static void vcycle(const MgPlan& p, int l, float* u, float* f, float* r, const MgBuffers& b, cudaStream_t st)
 {
     const int nx = p.dim[l][0], ny = p.dim[l][1], nz = p.dim[l][2];
     const int64_t n = (int64_t)nx * ny * nz;
@@ -431,41 +491,58 @@ static void vcycle(const MgPlan& p, int l, const MgBuffers& b, cudaStream_t st)
             if (k >= l) {
                 P.offs[k] = nodes;
                 nodes += p.dim[k][0] * p.dim[k][1] * p.dim[k][2];
+                P.rx[k] = (unsigned)(((1ull << 32) + p.dim[k][0] - 1) / p.dim[k][0]);
+                P.ry[k] = (unsigned)(((1ull << 32) + p.dim[k][1] - 1) / p.dim[k][1]);
             }
         }
         P.nodes = nodes;
         P.off_ls = p.off[l];
         P.coarse_sweeps = coarse_sweeps(p);
-        const size_t bytes = sizeof(double) * 3 * (size_t)nodes;
+        const size_t bytes = sizeof(float) * 3 * (size_t)nodes;
         static bool opted[64] = {};  // the shared-memory opt-in, once per device
         int dev = 0;
         cudaGetDevice(&dev);
         if (dev >= 0 && dev < 64 && !opted[dev]) {
-            cudaFuncSetAttribute(k_mg_small, cudaFuncAttributeMaxDynamicSharedMemorySize, SMALL_BYTES);
+            cudaFuncSetAttribute(k_mg_small<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMALL_BYTES);
             opted[dev] = true;
         }
-        k_mg_small<<<1, ST, bytes, st>>>(P, b.phi, b.f);
+        k_mg_small<float><<<1, ST, bytes, st>>>(P, u, f);
         return;
     }
     if (l == p.levels - 1) {  // coarsest: zero-mean right-hand side, many sweeps
-        sub_mean(b.f + p.off[l], n, b, st);
-        smooth(p, l, b, coarse_sweeps(p), st);
+        sub_mean(f + p.off[l], n, b, st);
+        smooth(p, l, u, f, r, coarse_sweeps(p), st);
         return;
     }
-    smooth(p, l, b, 2, st);
-    k_mg_residual<<<rows(nx, ny, nz), XT, 0, st>>>(b.phi + p.off[l], b.f + p.off[l], b.r + p.off[l], nx, ny, nz);
+    smooth(p, l, u, f, r, 2, st);
+    k_mg_residual<float><<<rows(nx, ny, nz), XT, 0, st>>>(u + p.off[l], f + p.off[l], r + p.off[l], nx, ny, nz);
     const int64_t nc = (int64_t)p.dim[l + 1][0] * p.dim[l + 1][1] * p.dim[l + 1][2];
-    k_mg_restrict<<<rows(nx / 2, ny / 2, nz / 2), XT, 0, st>>>(b.r + p.off[l], b.f + p.off[l + 1], nx, ny, nz);
-    cudaMemsetAsync(b.phi + p.off[l + 1], 0, sizeof(double) * nc, st);
-    vcycle(p, l + 1, b, st);
-    k_mg_prolong<<<rows(nx, ny, nz), XT, 0, st>>>(b.phi + p.off[l + 1], b.phi + p.off[l], nx, ny, nz);
-    smooth(p, l, b, 2, st);
+    k_mg_restrict<float><<<rows(nx / 2, ny / 2, nz / 2), XT, 0, st>>>(r + p.off[l], f + p.off[l + 1], nx, ny, nz);
+    cudaMemsetAsync(u + p.off[l + 1], 0, sizeof(float) * nc, st);
+    vcycle(p, l + 1, u, f, r, b, st);
+    k_mg_prolong<float><<<rows(nx, ny, nz), XT, 0, st>>>(u + p.off[l + 1], u + p.off[l], nx, ny, nz);
+    smooth(p, l, u, f, r, 2, st);
+}
+
+// One cycle of defect correction: the FP64 defect of phi, one FP32 V-cycle on
+// the correction equation A e = d from e = 0, phi += e.  Each cycle removes the
+// same share of the error as an FP64 V-cycle (the FP32 rounding is relative to
+// the current defect), so the iteration still converges to FP64 accuracy, and
+// only the fine-level defect and update use the FP64 pipe.
+static void mixed_cycle(const MgPlan& p, const MgBuffers& b, cudaStream_t st)
+{
+    const int nx = p.dim[0][0], ny = p.dim[0][1], nz = p.dim[0][2];
+    const int64_t n = (int64_t)nx * ny * nz;
+    k_mg_defect<<<rows(nx, ny, nz), XT, 0, st>>>(b.phi, b.f, b.g, nx, ny, nz);
+    cudaMemsetAsync(b.e, 0, sizeof(float) * n, st);
+    vcycle(p, 0, b.e, b.g, b.s, b, st);
+    k_mg_correct<<<grid_for(n), PT, 0, st>>>(b.phi, b.e, n);
 }
 
 int64_t mg_cycle_kernels(const MgPlan& p)
 {
     const int ls = first_small(p);
-    int64_t k = 0;
+    int64_t k = 2;                                                               // defect, correction
     for (int l = 0; l < std::min(ls, p.levels - 1); ++l) k += 4 + 1 + 1 + 1 + 4;  // smooth, residual, restrict,
                                                                                  // prolong, smooth
     if (ls < p.levels) return k + 1;                                            // the one-block rest
@@ -485,18 +562,18 @@ cudaError_t elec_solve(const RepDesc& D, const VacRec* recs, const int32_t* coun
     e = init ? cudaMemcpyAsync(b.phi, init, sizeof(double) * n, cudaMemcpyDeviceToDevice, st)
              : cudaMemsetAsync(b.phi, 0, sizeof(double) * n, st);  // warm start from the last solve
     if (e != cudaSuccess) return e;
-    for (int c = 0; c < cycles; ++c) vcycle(p, 0, b, st);
+    for (int c = 0; c < cycles; ++c) mixed_cycle(p, b, st);
     sub_mean(b.phi, n, b, st);
     if (save) {
         e = cudaMemcpyAsync(save, b.phi, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return e;
     }
-    if (resid_rel) {  // max |f - A phi| / max |f|
-        k_mg_residual<<<rows(p.dim[0][0], p.dim[0][1], p.dim[0][2]), XT, 0, st>>>(b.phi, b.f, b.r, p.dim[0][0],
-                                                                                   p.dim[0][1], p.dim[0][2]);
-        k_mg_partial<<<MG_PARTIALS, PT, 0, st>>>(b.r, n, b.part, 1);
+    if (resid_rel) {  // max |f - A phi| / max |f|, all in FP64
+        k_mg_residual<double><<<rows(p.dim[0][0], p.dim[0][1], p.dim[0][2]), XT, 0, st>>>(
+            b.phi, b.f, b.r, p.dim[0][0], p.dim[0][1], p.dim[0][2]);
+        k_mg_partial<double><<<MG_PARTIALS, PT, 0, st>>>(b.r, n, b.part, 1);
         k_mg_final<<<1, 32, 0, st>>>(b.part, MG_PARTIALS, b.scalar, 1);
-        k_mg_partial<<<MG_PARTIALS, PT, 0, st>>>(b.f, n, b.part, 1);
+        k_mg_partial<double><<<MG_PARTIALS, PT, 0, st>>>(b.f, n, b.part, 1);
         k_mg_final<<<1, 32, 0, st>>>(b.part, MG_PARTIALS, b.scalar + 1, 1);
         double h[2];
         e = cudaMemcpyAsync(h, b.scalar, sizeof h, cudaMemcpyDeviceToHost, st);
@@ -523,7 +600,7 @@ cudaError_t elec_solve_unit(const RepDesc& D, int t, double scale, int cycles, c
     k_mg_rhs<<<grid_for(n), PT, 0, st>>>(b.cnt, n, 0.5, 1.0 / (double)n, scale, b.f);
     e = cudaMemsetAsync(b.phi, 0, sizeof(double) * n, st);
     if (e != cudaSuccess) return e;
-    for (int c = 0; c < cycles; ++c) vcycle(p, 0, b, st);
+    for (int c = 0; c < cycles; ++c) mixed_cycle(p, b, st);
     sub_mean(b.phi, n, b, st);
     e = cudaStreamSynchronize(st);  // the caller reads b.phi next (host copy in the same stream)
     return e != cudaSuccess ? e : cudaGetLastError();
