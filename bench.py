@@ -30,10 +30,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = "hops/s on 1 GB300 (batched mixed vs plain FP64) at D within 1%; HBM roofline frac"
 UNIT = "hops/s"
-B_ALG_PER_HOP = 160  # algorithmic bytes per hop at 32-byte sector granularity
+# algorithmic bytes per hop at 32-byte sector granularity: the 8 neighbour words of
+# the vacancy's site (one sector each), the two site words written and its record
+B_ALG_PER_HOP = 160
 # site-energy path: + the energy field, 4-byte words: 9 reads (the vacancy's site and
 # its 8 targets) and a read-modify-write of the 2 x 58 V-V partners moved with the hop
 B_ALG_PER_HOP_SITE = 160 + 4 * (9 + 2 * 2 * 58)
+# electrostatics alone: the 9 energy-field reads, no partners to move
+B_ALG_PER_HOP_ELEC = 160 + 4 * 9
 
 
 def parse():
@@ -230,6 +234,16 @@ def cpu_oracle_rate(wl, seed, windows, budget_s, replicas=None):
     return hops / secs if secs > 0 else 0.0, hops, secs, done
 
 
+def oracle_jobs(wl, seed):
+    """Every replica of the workload as a job for the parallel oracle timing."""
+    from oracle import timing
+    cap = _auto_cap(wl)
+    return [timing.replica_job(r, rep.cells, rep.nfrag or tuple(_nfrag(c, wl.edge) for c in rep.cells), rep.n_vac,
+                               rep.n_H, rep.T, rep.Ea_O, rep.Ea_H, rep.field_z, rep.a, cap, wl.precision, seed,
+                               rep.n_Fe, wl.site or None)
+            for r, rep in enumerate(wl.replicas)]
+
+
 def _nfrag(L, edge):
     nf = 2 * int(math.floor(L / (2.0 * edge) + 0.5))
     if nf < 2:
@@ -258,12 +272,13 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
-    """sha256 over the CUDA sources; a traffic figure taken on other sources is stale."""
+def kernel_source_hash(names=None) -> str:
+    """sha256 over the named CUDA sources (default: all of them); a traffic figure
+    taken on other sources is stale."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2004_09081_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in sorted(names or os.listdir(csrc)):
         if name.endswith((".cu", ".cuh", ".h")):
             with open(os.path.join(csrc, name), "rb") as f:
                 h.update(name.encode() + b"\0" + f.read())
@@ -279,7 +294,7 @@ def load_traffic(kernel_tag):
     with open(p) as f:
         d = json.load(f)
     e = d.get(kernel_tag)
-    if e is None or e.get("source_sha256") != kernel_source_hash():
+    if e is None or e.get("source_sha256") != kernel_source_hash(e.get("sources")):
         return None
     return e.get("bytes_per_launch")
 
@@ -290,16 +305,20 @@ def run_reference(args):
     ws, rank, _ = dist_setup(False)
     if rank != 0:
         return
+    from oracle import timing
     wl = workloads.batched_batio3(args.seed)
     nrep = len(wl.replicas)
     args.windows = args.windows or 64
     per_step_budget = 8.0
     times, hops_all, reps_done = [], 0, 0
-    cursor = 0
+    jobs = oracle_jobs(wl, args.seed)
+    cores = 1
     for k in range(args.warmup + args.steps):
-        sample = [(cursor + i) % nrep for i in range(nrep)]
-        rate, hops, secs, done = cpu_oracle_rate(wl, args.seed, args.windows, per_step_budget, sample)
-        cursor = (cursor + done) % nrep
+        # the replicas are independent: one serial oracle per host core, each step
+        # starting further along the replica list
+        shift = (k * 37) % nrep
+        rate, hops, secs, done, cores = timing.parallel_rate(jobs[shift:] + jobs[:shift], args.windows,
+                                                             per_step_budget)
         if k >= args.warmup:
             times.append(secs)
             hops_all += hops
@@ -313,9 +332,10 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": wl.name, "replicas": nrep, "windows_per_step": args.windows,
                    "precision": "mixed"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{reps_done} replica runs of {args.windows} windows each over "
-                                   f"{args.steps} steps (~{per_step_budget:.0f} s of serial C per step)"},
+                                   f"{args.steps} steps, one serial C oracle per process on {cores} "
+                                   f"processes (~{per_step_budget:.0f} s each per step)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -479,12 +499,13 @@ def main():
     else:
         units = args.steps * W * 8  # one colour phase = one screen and one run launch
         tag = "k_phase_" + ("mixed_" if precision else "plain_") + args.workload
-        kname = "k_phase<%s%s> (colour-phase kernel)" % ("mixed" if precision else "plain",
-                                                         ", site energies" if wl.site else "")
+        kname = "k_phase<%s%s> (colour-phase kernel)" % (
+            "mixed" if precision else "plain",
+            ", site energies" if wl.site else (", electrostatic site energies" if "elec" in wl.notes else ""))
         note = ("a launch here is one colour phase (screen + run pass); neighbour words read from L2/HBM "
                 "with ld.global.cg; algorithmic bytes = 160 B per hop at 32-byte sectors" +
-                (" + the energy-field words of the site-energy path" if wl.site else ""))
-    b_alg = B_ALG_PER_HOP_SITE if wl.site else B_ALG_PER_HOP
+                (" + the energy-field words of the site-energy path" if wl.site or "elec" in wl.notes else ""))
+    b_alg = B_ALG_PER_HOP_SITE if wl.site else (B_ALG_PER_HOP_ELEC if "elec" in wl.notes else B_ALG_PER_HOP)
     avg_launch_s = kernel_ms / 1e3 / units
     bytes_per_launch = hops / units * b_alg
     if null:
@@ -670,6 +691,15 @@ def main():
                     f", serial C oracle ({ch} hops in {cs:.1f} s)"
             if not null:
                 extra["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": smp}
+            if not null and nrep > 1 and "grains" not in wl.notes and "elec" not in wl.notes:
+                # independent replicas: the same oracle on every host core at once
+                from oracle import timing
+                prate, ph, ps_, pd, pc = timing.parallel_rate(oracle_jobs(wl, seed), W, 12.0)
+                extra["cpu_baseline"] = {
+                    "value": prate, "unit": UNIT, "cores": pc, "kind": "oracle",
+                    "sample": f"{pd} replica runs of {W} windows, one serial C oracle per process on {pc} "
+                              f"processes ({ph} hops, longest worker {ps_:.1f} s)",
+                    "single_core": {"value": rate, "sample": smp}}
 
     if rank == 0:
         line = {

@@ -45,3 +45,28 @@ def test_two_gloo_ranks_shard_replicas_and_reduce_timing():
     assert sig0 != sig1           # each rank draws its own replicas
     assert t0 == t1 == 2.5        # max over ranks
     assert h0 == h1 == 300.0      # hops summed over ranks
+
+
+def test_parallel_oracle_timing_matches_serial_runs():
+    """The host-parallel CPU baseline: worker processes run the oracle as it
+    stands on their share of the replicas; with a budget that admits one run
+    per replica, the summed hop count equals the serial runs' exactly."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    import oracle
+    from oracle import timing
+    from paper_2004_09081_gb300 import workloads
+    wl = workloads.batched_batio3(0)
+    wl.replicas = [r for r in wl.replicas if r.cells[0] <= 20][:3]
+    jobs = bench.oracle_jobs(wl, 0)
+    rate, hops, secs, done, procs = timing.parallel_rate(jobs, 2, 1e-9, cores=3)
+    assert procs == 3 and done == 3 and rate > 0
+    want = 0
+    for j in jobs:
+        L = oracle.Lattice(j["cells"], j["nf"], j["n_vac"], j["n_H"], seed=0, replica=j["r"])
+        L.set_rates(j["Ea_O"], j["Ea_H"], j["T"], Ez=j["Ez"], a_ang=j["a"], cap_v=j["cap"],
+                    precision=j["precision"])
+        L.run(2)
+        want += L.counters()["hops"]
+    assert hops == want
