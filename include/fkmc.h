@@ -129,7 +129,11 @@ typedef struct {
                             and takes half of every phase's fragments; writes are mirrored
                             through distributed shared memory).  -1 (default) = SMs / 8,
                             0 = none */
-    int32_t reserved[6];
+    int32_t small_pass; /* colour-phase kernels: fragments holding one or two vacancies run in a
+                           pass of their own (4 or 2 fragments per warp, lock-step) beside the
+                           general pass; same trajectory.  0 (default) = where a phase holds
+                           32768 fragments or more, 1 = always, -1 = never */
+    int32_t reserved[5];
 } kmc_opts;
 
 typedef struct {

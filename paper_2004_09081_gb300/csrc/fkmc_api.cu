@@ -138,13 +138,15 @@ struct kmc_batch {
     struct RClass { int start, count; size_t smem; int threads; int cluster; cudaStream_t st; cudaEvent_t done; };
     std::vector<RClass> rclass;
     cudaEvent_t fork = nullptr;
+    cudaStream_t side_st = nullptr;       // the small-fragment run pass, beside the general one
+    cudaEvent_t side_fork = nullptr, side_join = nullptr;
     bool any_global = true;
     int cluster_top = 0;  // how many of the largest replicas run as 2-CTA clusters (kmc_opts)
     // colour-phase path: per-window set-up, screen and run, captured once in a graph
     unsigned long long* wctl = nullptr;  // [0] windows of this call so far, [1] current offset
     uint32_t* perms = nullptr;           // colour order of every replica, this window
     ActEntry* act = nullptr;             // screened fragments of a phase
-    int32_t* act_count = nullptr;        // per phase
+    int32_t* act_count = nullptr;        // per list and phase
     int run_blocks = 0;
     cudaStream_t cap_st = nullptr;
     cudaGraphExec_t window_exec = nullptr;
@@ -248,6 +250,11 @@ struct kmc_batch {
         if (ev1) cudaEventDestroy(ev1);
         if (fork) cudaEventDestroy(fork);
         ev0 = ev1 = fork = nullptr;
+        if (side_fork) cudaEventDestroy(side_fork);
+        if (side_join) cudaEventDestroy(side_join);
+        if (side_st) cudaStreamDestroy(side_st);
+        side_fork = side_join = nullptr;
+        side_st = nullptr;
         for (auto& c : rclass) {
             if (c.st) cudaStreamDestroy(c.st);
             if (c.done) cudaEventDestroy(c.done);
@@ -734,6 +741,7 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
     if (o.cap_v != 0 && (o.cap_v < 8 || o.cap_v > 256 || o.cap_v % 8))
         return fail(FKMC_EINVAL, "cap_v must be 0 or a multiple of 8 in [8, 256]");
     if (o.schedule < 0 || o.schedule > 2) return fail(FKMC_EINVAL, "schedule must be 0, 1 or 2");
+    if (o.small_pass < -1 || o.small_pass > 1) return fail(FKMC_EINVAL, "small_pass must be -1, 0 or 1");
 
     kmc_batch* b = new kmc_batch();
     b->n = n;
@@ -836,8 +844,8 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
     b->d_nvac = (int64_t*)b->dalloc(sizeof(int64_t) * n);
     b->wctl = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * 2);
     b->perms = (uint32_t*)b->dalloc(sizeof(uint32_t) * n);
-    b->act = (ActEntry*)b->dalloc(sizeof(ActEntry) * std::max<int64_t>(b->total_items, 1));
-    b->act_count = (int32_t*)b->dalloc(sizeof(int32_t) * 8);
+    b->act = (ActEntry*)b->dalloc(sizeof(ActEntry) * 3 * std::max<int64_t>(b->total_items, 1));
+    b->act_count = (int32_t*)b->dalloc(sizeof(int32_t) * 24);
     b->ncell_total = b->nsite_total / 3;
     bool any_fe = false;
     for (int r = 0; r < n; ++r) any_fe = any_fe || b->n_fe[r] > 0;
@@ -983,12 +991,21 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
         if (b->window_exec) return FKMC_OK;
         if (!b->cap_st) CK(cudaStreamCreateWithFlags(&b->cap_st, cudaStreamNonBlocking), "stream");
         cudaGraph_t graph = nullptr;
+        int small_blocks = 1;
+        const bool split = window_split(site_path(b), b->total_items, b->opts.small_pass);
+        if (split) CK(small_pass_blocks(b->opts.precision, b->grains_on, &small_blocks), "occupancy query");
+        if (!b->side_st) {
+            CK(cudaStreamCreateWithFlags(&b->side_st, cudaStreamNonBlocking), "stream");
+            CK(cudaEventCreateWithFlags(&b->side_fork, cudaEventDisableTiming), "event");
+            CK(cudaEventCreateWithFlags(&b->side_join, cudaEventDisableTiming), "event");
+        }
         CK(cudaStreamBeginCapture(b->cap_st, cudaStreamCaptureModeThreadLocal), "graph capture");
         SiteArgs wa = site_args(b);
         if (!site_path(b)) wa.field = nullptr;  // the table-rate run pass
         cudaError_t le = launch_window(b->opts.precision, b->d_desc, b->n, b->total_items, b->wctl, b->perms, b->act,
                                        b->act_count, b->occ, b->recs, b->counts, b->tracer, b->stats, b->status, b->cap,
-                                       b->run_blocks, wa, b->cap_st);
+                                       b->run_blocks, small_blocks, split, wa, b->cap_st, b->side_st, b->side_fork,
+                                       b->side_join);
         cudaError_t ce = cudaStreamEndCapture(b->cap_st, &graph);
         if (le != cudaSuccess) return cuda_fail(le, "window capture");
         if (ce != cudaSuccess) return cuda_fail(ce, "window capture");
@@ -1033,7 +1050,9 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
         }
         stats->windows = windows;
         stats->launches =
-            (windows > 0 ? b->rclass.size() : 0) + (b->any_global ? 17 * windows : 0) + extra_launches;
+            (windows > 0 ? b->rclass.size() : 0) +
+            (b->any_global ? (window_split(site_path(b), b->total_items, b->opts.small_pass) ? 25 : 17) * windows : 0) +
+            extra_launches;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, b->ev0, b->ev1);
         stats->gpu_ms = ms;

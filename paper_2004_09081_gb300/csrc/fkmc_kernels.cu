@@ -255,6 +255,24 @@ __device__ __forceinline__ void move_field(const RepDesc& D, const SiteArgs& sa,
     }
 }
 
+// Coordinates (c0, c1, c2) of index i in an n0 x n1 x n2 box, i = (c2 n1 + c1) n0 + c0:
+// 32-bit division where the index fits (a 64-bit division is a long
+// instruction sequence on the GPU).
+__device__ __forceinline__ void unflatten3(int64_t i, int n0, int n1, int c[3])
+{
+    if (i <= 0x7fffffffll) {
+        const unsigned u = (unsigned)i, m0 = (unsigned)n0, m1 = (unsigned)n1;
+        const unsigned q = u / m0;
+        c[0] = (int)(u - q * m0);
+        c[1] = (int)(q % m1);
+        c[2] = (int)(q / m1);
+    } else {
+        c[0] = (int)(i % n0);
+        c[1] = (int)((i / n0) % n1);
+        c[2] = (int)(i / ((int64_t)n0 * n1));
+    }
+}
+
 // Per-window set-up: colour order of every replica for this window, and the
 // screen counters of the 8 phases cleared.  wctl[0] counts the windows of the
 // current kmc_run call, wctl[1] holds the offset of the window being run.
@@ -266,25 +284,29 @@ __global__ void k_window_setup(const RepDesc* __restrict__ descs, int nrep, unsi
     const uint64_t wk = wctl[0];
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrep; r += gridDim.x * blockDim.x)
         perms[r] = colour_perm_packed(descs[r].seed, descs[r].replica, descs[r].window + wk);
-    if (blockIdx.x == 0 && threadIdx.x < 8) act_count[threadIdx.x] = 0;
+    if (blockIdx.x == 0 && threadIdx.x < 24) act_count[threadIdx.x] = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) wctl[1] = wk;
 }
 
 // Screen pass of a colour phase: one thread per fragment of the phase's colour
-// (every replica).  Fragments with vacancies go to the active list together
+// (every replica).  Fragments with vacancies go to an active list together
 // with their first Philox block, drawn here thirty-two fragments per warp
-// instead of once per fragment-warp.
+// instead of once per fragment-warp.  With `split`, fragments holding one or
+// two vacancies go to lists of their own (act + total_items, act + 2
+// total_items; counters act_count[8 + phase], act_count[16 + phase]) for the
+// small-fragment run pass; the rest (or all) to act, act_count[phase].
 template <int PREC>
 __global__ void __launch_bounds__(256) k_screen(const RepDesc* __restrict__ descs, int nrep, int64_t total_items,
                                                 int phase, unsigned long long* wctl,
                                                 const uint32_t* __restrict__ perms,
                                                 const int32_t* __restrict__ counts, ActEntry* act,
-                                                int32_t* act_count)
+                                                int32_t* act_count, int split)
 {
     const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     // the window count advances here (nothing in this launch reads wctl[0])
     if (phase == 0 && item == 0) wctl[0] = wctl[1] + 1;
     bool keep = false;
+    int list = 0;
     ActEntry e;
     if (item < total_items) {
         int lo = 0, hi = nrep - 1;
@@ -302,19 +324,21 @@ __global__ void __launch_bounds__(256) k_screen(const RepDesc* __restrict__ desc
             cnt[d] = D.nf[d] == 1 ? (bit[d] == 0 ? 1 : 0) : D.nf[d] / 2;
         }
         if (!D.resident && local < (int64_t)cnt[0] * cnt[1] * cnt[2]) {
-            int f0 = (int)(local % cnt[0]);
-            int f1 = (int)((local / cnt[0]) % cnt[1]);
-            int f2 = (int)(local / ((int64_t)cnt[0] * cnt[1]));
+            int fc[3];
+            unflatten3(local, cnt[0], cnt[1], fc);
+            int f0 = fc[0], f1 = fc[1], f2 = fc[2];
             f0 = D.nf[0] == 1 ? 0 : 2 * f0 + bit[0];
             f1 = D.nf[1] == 1 ? 0 : 2 * f1 + bit[1];
             f2 = D.nf[2] == 1 ? 0 : 2 * f2 + bit[2];
             const int64_t fid = ((int64_t)f2 * D.nf[1] + f1) * D.nf[0] + f0;
-            if (counts[D.frag_base + fid] > 0) {
+            const int nv = counts[D.frag_base + fid];
+            if (nv > 0) {
                 keep = true;
+                list = split && nv <= 2 ? nv : 0;
                 const uint64_t w = D.window + wctl[1];
                 const U64x4 blk = philox4x64((uint64_t)fid, w, 0, 0, D.seed, key_word(D.replica, PURPOSE_HOP));
                 e.rep = lo;
-                e.pad = 0;
+                e.pad = nv;
                 e.fid = fid;
                 e.xs[0] = blk.x[1];
                 e.xs[1] = blk.x[3];
@@ -328,14 +352,17 @@ __global__ void __launch_bounds__(256) k_screen(const RepDesc* __restrict__ desc
             }
         }
     }
-    // one atomic per warp for the slots of its kept fragments
-    const unsigned bal = __ballot_sync(0xffffffffu, keep);
-    if (!bal) return;
+    // one atomic per warp and list for the slots of its kept fragments
     const int lane = threadIdx.x & 31;
-    int base = 0;
-    if (lane == __ffs(bal) - 1) base = atomicAdd(act_count + phase, __popc(bal));
-    base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
-    if (keep) act[base + __popc(bal & ((1u << lane) - 1u))] = e;
+    for (int l = 0; l < 3; ++l) {
+        const bool mine = keep && list == l;
+        const unsigned bal = __ballot_sync(0xffffffffu, mine);
+        if (!bal) continue;
+        int base = 0;
+        if (lane == __ffs(bal) - 1) base = atomicAdd(act_count + 8 * l + phase, __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
+        if (mine) act[l * total_items + base + __popc(bal & ((1u << lane) - 1u))] = e;
+    }
 }
 
 // Run pass of a colour phase: one warp per screened fragment (grid-stride):
@@ -362,9 +389,7 @@ __global__ void __launch_bounds__(128, 8) k_run(const RepDesc* __restrict__ desc
     const uint64_t w = D.window + wctl[1];
     const int64_t fid = ent.fid;
     int f[3], lo_c[3], hi_c[3];
-    f[0] = (int)(fid % D.nf[0]);
-    f[1] = (int)((fid / D.nf[0]) % D.nf[1]);
-    f[2] = (int)(fid / ((int64_t)D.nf[0] * D.nf[1]));
+    unflatten3(fid, D.nf[0], D.nf[1], f);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         lo_c[d] = frag_start(f[d], D.base[d], D.rem[d]);
@@ -589,6 +614,241 @@ __global__ void __launch_bounds__(128, 8) k_run(const RepDesc* __restrict__ desc
         if (nhand) atomicAdd(stats + 2 * lo + 1, (unsigned long long)nhand);
     }
     __syncwarp();  // the warp's shared memory is reused by its next fragment
+    }
+}
+
+// Run pass for fragments holding one or two vacancies (table-rate path): a
+// fragment takes a group of G = 8 nv lanes, lane = event index 8 slot +
+// neighbour, and the groups of a warp (four of 8 lanes or two of 16) run in
+// lock-step, so their memory round trips overlap and their instructions are
+// issued once.  The group's Kogge-Stone scan over its G lanes yields the same
+// partial sums as the general pass's 32-lane scan (strides of G and more only
+// add the zero rates of empty lanes), the draws are the same Philox words
+// (events 0, 1 from the screen pass, event i >= 2 from block 1 + (i-2)/2), and
+// the selection and exchange are the same, so both passes compute the same
+// trajectory.  Records and rate types live in registers.
+template <int PREC, bool GRAIN>
+__global__ void __launch_bounds__(128, 8) k_run_small(const RepDesc* __restrict__ descs,
+                                                   const ActEntry* __restrict__ act, int64_t list_stride,
+                                                   const int32_t* __restrict__ act_count, int phase,
+                                                   const unsigned long long* wctl, uint32_t* occ, VacRec* recs,
+                                                   int32_t* counts, int32_t* tracer, unsigned long long* stats,
+                                                   uint32_t* status, int cap, const uint8_t* gb)
+{
+    using A = Arith<PREC>;
+    using V = typename A::V;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int n1 = act_count[8 + phase], n2 = act_count[16 + phase];
+    const int items1 = (n1 + 3) >> 2;
+    const int items = items1 + ((n2 + 1) >> 1);
+    const int nwarps_grid = gridDim.x * (blockDim.x >> 5);
+    for (int it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items; it += nwarps_grid) {
+        const bool two = it >= items1;  // warp-uniform: 2 x 16 lanes, else 4 x 8
+        const int G = two ? 16 : 8;
+        const int grp = two ? lane >> 4 : lane >> 3;
+        const int sub = lane & (G - 1);
+        const int n = sub & 7;
+        const unsigned gmask = (two ? 0xffffu : 0xffu) << (grp * G);
+        const int idx = two ? 2 * (it - items1) + grp : 4 * it + grp;
+        const bool active = idx < (two ? n2 : n1);
+        const ActEntry* list = act + (two ? 2 : 1) * list_stride;
+        ActEntry ent{};
+        if (active) ent = list[idx];
+        const RepDesc& D = descs[ent.rep];
+        const int64_t fid = ent.fid;
+        const int64_t g = D.frag_base + fid;
+        VacRec rec{};
+        if (active) rec = recs[g * cap + (sub >> 3)];
+        if (two) {  // slots in ascending site order: swap the halves' records if needed
+            const uint64_t ok = __shfl_xor_sync(FULL, rec.key, 8);
+            const int od0 = __shfl_xor_sync(FULL, rec.d[0], 8);
+            const int od1 = __shfl_xor_sync(FULL, rec.d[1], 8);
+            const int od2 = __shfl_xor_sync(FULL, rec.d[2], 8);
+            const uint32_t oid = __shfl_xor_sync(FULL, rec.id, 8);
+            const bool swap = (sub >> 3) == 0 ? ok < rec.key : rec.key < ok;
+            if (swap) {
+                rec.key = ok;
+                rec.d[0] = od0;
+                rec.d[1] = od1;
+                rec.d[2] = od2;
+                rec.id = oid;
+            }
+        }
+        int lo_c[3] = {0, 0, 0}, hi_c[3] = {0, 0, 0};
+        {
+            int f[3];
+            unflatten3(fid, D.nf[0], D.nf[1], f);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                lo_c[d] = frag_start(f[d], D.base[d], D.rem[d]);
+                hi_c[d] = frag_start(f[d] + 1, D.base[d], D.rem[d]);
+            }
+        }
+        const uint64_t w = D.window + wctl[1];
+        bool alive = active;  // this lane's vacancy is still in the fragment
+        int ty = -1;
+        auto types = [&]() {
+            ty = -1;
+            if (alive) {
+                int t, x, y, z;
+                split_key(rec.key, t, x, y, z);
+                const NbEntry nb = c_nb[t][n];
+                const int jx = wrapc(x + nb.dc[0], D.L[0]);
+                const int jy = wrapc(y + nb.dc[1], D.L[1]);
+                const int jz = wrapc(z + nb.dc[2], D.L[2]);
+                const uint32_t word = __ldcg(occ + occ_word(D, nb.t2, jx, jy, jz));
+                const int code = (int)((word >> occ_shift(jx)) & 3u);
+                ty = code == SP_V ? -1 : code * 3 + nb.d[2] + 1;
+                if constexpr (GRAIN) {
+                    if (ty >= 0 && (gb[cell_index(D, x, y, z)] | gb[cell_index(D, jx, jy, jz)])) ty += 6;
+                }
+            }
+        };
+        types();
+        double clock = 0.0;
+        uint64_t i = 0;
+        uint64_t xs_even = 0, xs_odd = 0;
+        double Ed_even = 0.0, Ed_odd = 0.0;
+        float Ef_even = 0.f, Ef_odd = 0.f;
+        bool run = active;
+        while (__any_sync(FULL, run)) {
+            const V v = run ? A::template rate<GRAIN>(D, ty) : A::zero();
+            V p = v;
+#pragma unroll
+            for (int off = 1; off < 16; off <<= 1) {
+                if (off < G) {
+                    const V t = __shfl_up_sync(FULL, p, off, G);
+                    if (sub >= off) p = A::add(p, t);
+                }
+            }
+            const V total = __shfl_sync(FULL, p, G - 1, G);
+            bool go = run && A::pos(total);
+            if (go && i >= MAX_EVENTS_PER_PHASE) {
+                if (sub == 0) atomicOr(status, STATUS_EVENT_LIMIT);
+                go = false;
+            }
+            uint64_t xs = 0;
+            double Ed = 0.0;
+            float Ef = 0.f;
+            if (go) {
+                if (i < 2) {
+                    xs = ent.xs[i];
+                    if constexpr (PREC == 0) Ed = __longlong_as_double((long long)ent.E[i]);
+                    else Ef = __uint_as_float((uint32_t)ent.E[i]);
+                } else {
+                    const uint64_t k = i - 2;
+                    if ((k & 1) == 0) {
+                        const U64x4 blk = philox4x64((uint64_t)fid, w, 1 + (k >> 1), 0, D.seed,
+                                                     key_word(D.replica, PURPOSE_HOP));
+                        xs_even = blk.x[1];
+                        xs_odd = blk.x[3];
+                        if constexpr (PREC == 0) {
+                            Ed_even = neglog64(blk.x[0]);
+                            Ed_odd = neglog64(blk.x[2]);
+                        } else {
+                            Ef_even = neglog32(blk.x[0]);
+                            Ef_odd = neglog32(blk.x[2]);
+                        }
+                    }
+                    const bool odd = (k & 1) != 0;
+                    xs = odd ? xs_odd : xs_even;
+                    if constexpr (PREC == 0) Ed = odd ? Ed_odd : Ed_even;
+                    else Ef = odd ? Ef_odd : Ef_even;
+                }
+            }
+            double dclock = 0.0;
+            bool cont;
+            int e_sel;
+            if constexpr (PREC == 0) {
+                const double R = total;
+                const double dt = go ? __ddiv_rn(Ed, R) : 0.0;
+                cont = go && !(__dadd_rn(clock, dt) > D.tau);
+                dclock = dt;
+                const double target = __dmul_rn(__dmul_rn(__ull2double_rn(xs >> 11), 0x1p-53), R);
+                const unsigned b1 = __ballot_sync(FULL, cont && v > 0.0 && p > target) & gmask;
+                const unsigned b2 = __ballot_sync(FULL, cont && v > 0.0) & gmask;
+                e_sel = b1 ? __ffs(b1) - 1 : (b2 ? 31 - __clz(b2) : -1);
+            } else {
+                const unsigned long long Sq = total;
+                const float ratio = go ? __fdiv_rn(Ef, __ull2float_rn(Sq)) : 0.f;
+                const double dth = __dmul_rn((double)ratio, D.two_pow_F);
+                cont = go && !(__dadd_rn(clock, dth) > D.theta_tau);
+                dclock = dth;
+                const unsigned long long target = __umul64hi(xs, Sq);
+                const unsigned b1 = __ballot_sync(FULL, cont && p > target) & gmask;
+                e_sel = b1 ? __ffs(b1) - 1 : -1;
+            }
+            if (cont && lane == e_sel) {  // the selected event's own lane applies the exchange
+                int t, x, y, z;
+                split_key(rec.key, t, x, y, z);
+                const NbEntry nb = c_nb[t][n];
+                const int jx = wrapc(x + nb.dc[0], D.L[0]);
+                const int jy = wrapc(y + nb.dc[1], D.L[1]);
+                const int jz = wrapc(z + nb.dc[2], D.L[2]);
+                const uint32_t ion = (uint32_t)((ty % 6) / 3);
+                atomicXor(occ + occ_word(D, t, x, y, z), ((uint32_t)SP_V ^ ion) << occ_shift(x));
+                atomicXor(occ + occ_word(D, nb.t2, jx, jy, jz), (ion ^ (uint32_t)SP_V) << occ_shift(jx));
+                rec.d[0] += nb.d[0];
+                rec.d[1] += nb.d[1];
+                rec.d[2] += nb.d[2];
+                if (tracer) {
+                    const int64_t s_lin = (((int64_t)t * D.L[2] + z) * D.L[1] + y) * D.L[0] + x;
+                    const int64_t j_lin = (((int64_t)nb.t2 * D.L[2] + jz) * D.L[1] + jy) * D.L[0] + jx;
+                    int32_t* ts = tracer + 3 * (D.site_off + s_lin);
+                    int32_t* tj = tracer + 3 * (D.site_off + j_lin);
+                    ts[0] = tj[0] - nb.d[0];
+                    ts[1] = tj[1] - nb.d[1];
+                    ts[2] = tj[2] - nb.d[2];
+                    tj[0] = tj[1] = tj[2] = 0;
+                }
+                rec.key = make_key(nb.t2, jx, jy, jz);
+                const bool owned = jx >= lo_c[0] && jx < hi_c[0] && jy >= lo_c[1] && jy < hi_c[1] &&
+                                   jz >= lo_c[2] && jz < hi_c[2];
+                if (!owned) {
+                    const int gx = frag_of(jx, D.base[0], D.rem[0]);
+                    const int gy = frag_of(jy, D.base[1], D.rem[1]);
+                    const int gz = frag_of(jz, D.base[2], D.rem[2]);
+                    const int64_t g2 = D.frag_base + ((int64_t)gz * D.nf[1] + gy) * D.nf[0] + gx;
+                    const int slot = atomicAdd(counts + g2, 1);
+                    if (slot < cap) recs[g2 * cap + slot] = rec;
+                    else atomicOr(status, STATUS_OVERFLOW);
+                    alive = false;
+                }
+                __threadfence_block();
+            }
+            __syncwarp();
+            // the selected lane's record and flag go to the other lanes of its vacancy
+            const int src = e_sel < 0 ? lane : e_sel;
+            const uint64_t nkey = __shfl_sync(FULL, rec.key, src);
+            const int nd0 = __shfl_sync(FULL, rec.d[0], src);
+            const int nd1 = __shfl_sync(FULL, rec.d[1], src);
+            const int nd2 = __shfl_sync(FULL, rec.d[2], src);
+            const bool nalive = __shfl_sync(FULL, alive, src);
+            if (cont && (src >> 3) == (lane >> 3)) {
+                rec.key = nkey;
+                rec.d[0] = nd0;
+                rec.d[1] = nd1;
+                rec.d[2] = nd2;
+                alive = nalive;
+            }
+            if (cont) {
+                clock = __dadd_rn(clock, dclock);
+                ++i;
+            }
+            run = cont;
+            if (run) types();
+        }
+        // surviving records stay with the fragment, in slot order
+        const bool lead = active && n == 0;
+        const unsigned surv = __ballot_sync(FULL, lead && alive) & gmask;
+        if (lead && alive) recs[g * cap + __popc(surv & ((1u << lane) - 1u))] = rec;
+        if (active && sub == 0) {
+            const int kept = __popc(surv);
+            counts[g] = kept;
+            if (i) atomicAdd(stats + 2 * ent.rep, (unsigned long long)i);
+            if (ent.pad > kept) atomicAdd(stats + 2 * ent.rep + 1, (unsigned long long)(ent.pad - kept));
+        }
     }
 }
 
@@ -906,6 +1166,24 @@ static RunFn run_kernel(int prec, bool site, bool grain)
     return grain ? k_run<1, false, true> : k_run<1, false, false>;
 }
 
+// The small-fragment pass runs beside the general one where a phase holds
+// enough fragments to fill both: on a 1000^3 lattice (244k fragments per phase)
+// it gains 15%, on 128^3 (512 per phase) the two extra launches per phase cost
+// 20% (A/B on one GB300, identical hop counts).  It has no site energies.
+bool window_split(bool site, int64_t total_items, int mode)
+{
+    return !site && (mode > 0 || (mode == 0 && total_items >= SPLIT_MIN_ITEMS));
+}
+
+using SmallFn = void (*)(const RepDesc*, const ActEntry*, int64_t, const int32_t*, int, const unsigned long long*,
+                        uint32_t*, VacRec*, int32_t*, int32_t*, unsigned long long*, uint32_t*, int, const uint8_t*);
+
+static SmallFn small_kernel(int prec, bool grain)
+{
+    if (prec == 0) return grain ? k_run_small<0, true> : k_run_small<0, false>;
+    return grain ? k_run_small<1, true> : k_run_small<1, false>;
+}
+
 cudaError_t phase_prepare(int cap)
 {
     cudaError_t e = cudaSuccess;
@@ -934,6 +1212,16 @@ cudaError_t run_pass_blocks(int prec, int cap, bool site, bool grain, int* block
     return e;
 }
 
+cudaError_t small_pass_blocks(int prec, bool grain, int* blocks)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, small_kernel(prec, grain), 128, 0);
+    *blocks = std::max(1, sms * std::max(per_sm, 1));
+    return e;
+}
+
 // One window of the colour-phase path: set-up, then screen and run for each of
 // the 8 phases.  Every argument is fixed for the batch (the window offset is
 // read from wctl on the device), so the sequence can be captured in a graph.
@@ -943,7 +1231,8 @@ cudaError_t launch_window(int prec, const RepDesc* d_descs, int nrep, int64_t to
                           unsigned long long* wctl, uint32_t* perms, ActEntry* act, int32_t* act_count,
                           uint32_t* occ, VacRec* recs, int32_t* counts, int32_t* tracer,
                           unsigned long long* stats, uint32_t* status, int cap, int run_blocks,
-                          const SiteArgs& sa, cudaStream_t st)
+                          int small_blocks, bool split_pass, const SiteArgs& sa, cudaStream_t st, cudaStream_t side,
+                          cudaEvent_t fork, cudaEvent_t join)
 {
     if (total_items <= 0) return cudaSuccess;
     const bool site = sa.field != nullptr, grain = sa.gbound != nullptr;
@@ -951,15 +1240,30 @@ cudaError_t launch_window(int prec, const RepDesc* d_descs, int nrep, int64_t to
     const int64_t sblocks = (total_items + 255) / 256;
     const size_t smem = phase_smem_bytes(cap, site);
     const RunFn run = run_kernel(site ? 0 : prec, site, grain);
+    const int split = split_pass && !site ? 1 : 0;
+    const SmallFn small = small_kernel(prec, grain);
     for (int p = 0; p < 8; ++p) {
         if (site || prec == 0)
             k_screen<0><<<(unsigned)sblocks, 256, 0, st>>>(d_descs, nrep, total_items, p, wctl, perms, counts, act,
-                                                           act_count);
+                                                           act_count, split);
         else
             k_screen<1><<<(unsigned)sblocks, 256, 0, st>>>(d_descs, nrep, total_items, p, wctl, perms, counts, act,
-                                                           act_count);
+                                                           act_count, split);
+        if (split) {  // the two run passes touch disjoint fragments: run them side by side
+            cudaError_t e = cudaEventRecord(fork, st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
+            if (e != cudaSuccess) return e;
+            small<<<small_blocks, 128, 0, side>>>(d_descs, act, total_items, act_count, p, wctl, occ, recs, counts,
+                                                  tracer, stats, status, cap, sa.gbound);
+            e = cudaEventRecord(join, side);
+            if (e != cudaSuccess) return e;
+        }
         run<<<run_blocks, 128, smem, st>>>(d_descs, act, act_count, p, wctl, occ, recs, counts, tracer, stats, status,
                                            cap, sa);
+        if (split) {
+            const cudaError_t e = cudaStreamWaitEvent(st, join, 0);
+            if (e != cudaSuccess) return e;
+        }
     }
     return cudaGetLastError();
 }

@@ -66,7 +66,7 @@ class kmc_opts(C.Structure):
                 ("tracer", C.c_int32), ("cap_v", C.c_int32), ("n_tau", C.c_double),
                 ("stream", C.c_void_p), ("alloc", kmc_alloc_fn), ("free", kmc_free_fn),
                 ("alloc_ctx", C.c_void_p), ("schedule", C.c_int32), ("cluster_top", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("small_pass", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class kmc_run_stats(C.Structure):
@@ -435,7 +435,7 @@ class Batch:
     """A batch of replicas (one lattice = a batch of one) on the current GPU."""
 
     def __init__(self, cells, comps, seed=0, *, edge=4, nfrag=None, precision=FKMC_PLAIN,
-                 tracer=False, cap_v=0, n_tau=1.0, schedule=0, cluster_top=-1, stream=None):
+                 tracer=False, cap_v=0, n_tau=1.0, schedule=0, cluster_top=-1, small_pass=0, stream=None):
         import torch
         self._alloc = TorchAllocator()
         o = kmc_default_opts()
@@ -449,6 +449,7 @@ class Batch:
         o.n_tau = float(n_tau)
         o.schedule = int(schedule)
         o.cluster_top = int(cluster_top)
+        o.small_pass = int(small_pass)
         st = stream if stream is not None else torch.cuda.current_stream()
         o.stream = C.c_void_p(st.cuda_stream)
         o.alloc = self._alloc.c_alloc

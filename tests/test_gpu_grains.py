@@ -40,10 +40,12 @@ def test_grain_map_matches_oracle(fk, orc):
             assert np.array_equal(bnd, rb)
 
 
+@pytest.mark.parametrize("small", [-1, 1])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_grains_colour_phase_bit_exact(fk, orc, prec):
+def test_grains_colour_phase_bit_exact(fk, orc, prec, small):
     cells, nf = (16, 12, 16), (4, 2, 4)
-    b = fk.Batch([(*cells, 4.01)], [(40, 150)], 7, nfrag=nf, precision=prec, tracer=True, cap_v=64)
+    b = fk.Batch([(*cells, 4.01)], [(40, 150)], 7, nfrag=nf, precision=prec, tracer=True, cap_v=64,
+                 small_pass=small)
     b.set_grains(5, 1, 0.2)
     b.set_barriers(0.6, 0.5, 900.0, field_z=2e7)
     ref = orc.Lattice(cells, nf, 40, 150, seed=7, tracer=True)

@@ -27,8 +27,9 @@ def fk():
 
 def run_pair(fk, orc, cells, nf, nv, nh, seed, windows, prec, tracer=True, T=800.0, Ea=(0.6, 0.3),
              Ez=0.0, a=3.905, cap=64, n_tau=1.0, chunks=1, schedule=0):
+    sched, small = form(schedule)
     b = fk.Batch([(*cells, a)], [(nv, nh)], seed, nfrag=nf, precision=prec, tracer=tracer, cap_v=cap,
-                 n_tau=n_tau, schedule=schedule)
+                 n_tau=n_tau, schedule=sched, small_pass=small)
     b.set_barriers(Ea[0], Ea[1], T, field_z=Ez)
     ref = orc.Lattice(cells, nf, nv, nh, seed=seed, tracer=tracer)
     ref.set_rates(Ea[0], Ea[1], T, Ez=Ez, a_ang=a, cap_v=cap, n_tau=n_tau, precision=prec)
@@ -52,8 +53,15 @@ def run_pair(fk, orc, cells, nf, nv, nh, seed, windows, prec, tracer=True, T=800
 
 
 # (precision, schedule): plain FP64 runs the colour-phase kernel; the mixed form
-# runs both the colour-phase kernel (1) and the replica-resident kernel (2)
-FORMS = [(0, 0), (1, 1), (1, 2)]
+# runs both the colour-phase kernel (1) and the replica-resident kernel (2);
+# "+small" forces the small-fragment run pass (fragments with one or two
+# vacancies, four or two per warp) beside the general one
+FORMS = [(0, 0), (1, 1), (1, 2), (0, 10), (1, 11)]
+
+
+def form(sched):
+    """schedule and small_pass of a FORMS entry (10 + s: schedule s, small pass forced)"""
+    return (sched % 10, 1) if sched >= 10 else (sched, -1)
 
 
 @pytest.mark.parametrize("prec,sched", FORMS)
@@ -94,7 +102,7 @@ def test_batch_of_uneven_replicas(fk, orc):
     Ts = [800.0, 650.0, 500.0, 900.0, 1000.0]
     for prec, sched in FORMS:
         b = fk.Batch([(*c, 4.01) for c in cells], comps, 21, edge=4, precision=prec, tracer=True, cap_v=64,
-                     schedule=sched)
+                     schedule=form(sched)[0], small_pass=form(sched)[1])
         b.set_barriers(0.7, 0.35, Ts, field_z=[0, 1e7, 0, -1e7, 0])
         b.run(40)
         for r, (c, (nv, nh), T) in enumerate(zip(cells, comps, Ts)):
