@@ -285,9 +285,9 @@ def kernel_source_hash(names=None) -> str:
     return h.hexdigest()
 
 
-def load_traffic(kernel_tag):
-    """dram__bytes_read.sum + dram__bytes_write.sum per launch from the committed
-    ncu summary, or None when absent or taken on different kernel sources."""
+def load_counters(kernel_tag):
+    """The committed ncu figures of a kernel (profiles/traffic.json), or None when
+    absent or taken on different kernel sources."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -296,7 +296,14 @@ def load_traffic(kernel_tag):
     e = d.get(kernel_tag)
     if e is None or e.get("source_sha256") != kernel_source_hash(e.get("sources")):
         return None
-    return e.get("bytes_per_launch")
+    return e
+
+
+def load_traffic(kernel_tag):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch from the committed
+    ncu summary, or None when absent or stale."""
+    e = load_counters(kernel_tag)
+    return e.get("bytes_per_launch") if e else None
 
 
 # ------------------------------------------------------------------ reference arm
@@ -518,6 +525,22 @@ def main():
                 "traffic": load_traffic(tag), "peak_kind": f"{peak_kind} hbm_gbs",
                 "kernel": kname, "bytes_per_hop": b_alg, "hops_per_launch": hops / units,
                 "avg_launch_us": avg_launch_s * 1e6, "note": note}
+    cnt = load_counters(tag) if all_resident else None
+    if cnt and cnt.get("smem_wavefronts_per_launch") and clk.get("sm_mhz"):
+        # the replica-resident kernel works out of shared memory: its shared-memory
+        # wavefronts and warp instructions (ncu, per window) over the live launch time,
+        # against one wavefront and four warp instructions per SM per cycle
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        hz = clk["sm_mhz"] * 1e6
+        per_w = W / cnt["counters_windows"]
+        wf = cnt["smem_wavefronts_per_launch"] * per_w
+        wi = cnt["warp_inst_per_launch"] * per_w
+        roofline["smem"] = {"frac": wf / avg_launch_s / (nsm * hz), "wavefronts_per_launch": wf,
+                            "peak_wavefronts_per_s": nsm * hz}
+        roofline["issue"] = {"frac": wi / avg_launch_s / (4 * nsm * hz), "warp_inst_per_launch": wi,
+                             "peak_warp_inst_per_s": 4 * nsm * hz}
+        roofline["counters_note"] = ("smem and issue: ncu counts per window (profiles/traffic.json) x windows "
+                                     "per launch / CUDA-event launch time; peaks at the measured SM clock")
 
     extra = {}
     if rank == 0 and args.profile_run:
