@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "fkmc_device.cuh"
 #include "fkmc_kernels.h"
@@ -20,6 +21,18 @@
 namespace fkmc {
 
 __constant__ NbEntry c_nb[3][8];
+// The same table in global memory for lookups whose (t, n) differ across the
+// lanes of a warp: a global load serves them in one or two L1 wavefronts, a
+// constant-memory load would be split into one request per distinct entry.
+__device__ __align__(8) NbEntry g_nb[3][8];
+
+__device__ __forceinline__ NbEntry nb_entry(int t, int n)
+{
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(&g_nb[0][0]) + 8 * t + n);
+    NbEntry e;
+    memcpy(&e, &v, sizeof e);
+    return e;
+}
 
 // ------------------------------------------------------------------ init
 __global__ void k_init(RepDesc D, int b_bits, int64_t n_vac, int64_t n_total, uint32_t* occ,
@@ -160,7 +173,7 @@ __device__ __forceinline__ void compute_types(const RepDesc& D, const uint32_t* 
         if (m < nslots && S.alive[m]) {
             int t, x, y, z;
             split_key(S.rec[S.order[m]].key, t, x, y, z);
-            const NbEntry nb = c_nb[t][n];
+            const NbEntry nb = nb_entry(t, n);
             const int jx = wrapc(x + nb.dc[0], D.L[0]);
             const int jy = wrapc(y + nb.dc[1], D.L[1]);
             const int jz = wrapc(z + nb.dc[2], D.L[2]);
@@ -203,7 +216,7 @@ __device__ __forceinline__ void compute_rates_site(const RepDesc& D, const uint3
         if (m < nslots && S.alive[m]) {
             int t, x, y, z;
             split_key(S.rec[S.order[m]].key, t, x, y, z);
-            const NbEntry nb = c_nb[t][n];
+            const NbEntry nb = nb_entry(t, n);
             const int jx = wrapc(x + nb.dc[0], D.L[0]);
             const int jy = wrapc(y + nb.dc[1], D.L[1]);
             const int jz = wrapc(z + nb.dc[2], D.L[2]);
@@ -693,7 +706,7 @@ __global__ void __launch_bounds__(128, 8) k_run_small(const RepDesc* __restrict_
             if (alive) {
                 int t, x, y, z;
                 split_key(rec.key, t, x, y, z);
-                const NbEntry nb = c_nb[t][n];
+                const NbEntry nb = nb_entry(t, n);
                 const int jx = wrapc(x + nb.dc[0], D.L[0]);
                 const int jy = wrapc(y + nb.dc[1], D.L[1]);
                 const int jz = wrapc(z + nb.dc[2], D.L[2]);
@@ -782,7 +795,7 @@ __global__ void __launch_bounds__(128, 8) k_run_small(const RepDesc* __restrict_
             if (cont && lane == e_sel) {  // the selected event's own lane applies the exchange
                 int t, x, y, z;
                 split_key(rec.key, t, x, y, z);
-                const NbEntry nb = c_nb[t][n];
+                const NbEntry nb = nb_entry(t, n);
                 const int jx = wrapc(x + nb.dc[0], D.L[0]);
                 const int jy = wrapc(y + nb.dc[1], D.L[1]);
                 const int jz = wrapc(z + nb.dc[2], D.L[2]);
@@ -1139,7 +1152,8 @@ __global__ void k_moments_ion(RepDesc D, const uint32_t* occ, const int32_t* tra
 // ------------------------------------------------------------------ launchers
 cudaError_t upload_neighbours(const NbEntry* host)
 {
-    return cudaMemcpyToSymbol(c_nb, host, sizeof(NbEntry) * 24);
+    const cudaError_t e = cudaMemcpyToSymbol(c_nb, host, sizeof(NbEntry) * 24);
+    return e != cudaSuccess ? e : cudaMemcpyToSymbol(g_nb, host, sizeof(NbEntry) * 24);
 }
 
 cudaError_t launch_init(const RepDesc& D, int b_bits, int64_t n_vac, int64_t n_total, uint32_t* occ,
