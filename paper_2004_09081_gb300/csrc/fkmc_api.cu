@@ -870,6 +870,7 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
     };
     build_nb_table(b->nbt.e);
     step(upload_neighbours(&b->nbt.e[0][0]), "neighbour table upload");
+    step(null_upload_neighbours(&b->nbt.e[0][0]), "neighbour table upload");
     step(phase_prepare(b->cap), "kernel attributes");
     step(run_pass_blocks(b->opts.precision, b->cap, false, false, &b->run_blocks), "occupancy query");
     step(resident_prepare(), "kernel attributes");
@@ -1138,9 +1139,9 @@ int kmc_run_null(kmc_batch* b, uint64_t steps, int64_t n_frg, kmc_run_stats* sta
             if (!b->cap_st) CK(cudaStreamCreateWithFlags(&b->cap_st, cudaStreamNonBlocking), "stream");
             cudaGraph_t graph = nullptr;
             CK(cudaStreamBeginCapture(b->cap_st, cudaStreamCaptureModeThreadLocal), "graph capture");
-            cudaError_t le = launch_null_step(b->d_desc, b->n, total_vac, total_picks, b->vac, b->occ, b->nbt,
-                                              b->grains_on ? b->gbound : nullptr, b->nacc, b->props, b->claims, b->tracer, b->theta, b->nE, b->stats,
-                                              b->nctl, b->cap_st);
+            cudaError_t le = launch_null_step(b->d_desc, b->n, total_vac, total_picks, b->vac, b->occ,
+                                              b->grains_on ? b->gbound : nullptr, b->nacc, b->props, b->claims,
+                                              b->tracer, b->theta, b->nE, b->stats, b->nctl, b->cap_st);
             cudaError_t ce = cudaStreamEndCapture(b->cap_st, &graph);
             if (le != cudaSuccess) return cuda_fail(le, "null step capture");
             if (ce != cudaSuccess) return cuda_fail(ce, "null step capture");

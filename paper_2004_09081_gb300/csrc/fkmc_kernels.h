@@ -39,8 +39,9 @@ cudaError_t launch_null_gather(const RepDesc* d_descs, int nrep, const VacRec* r
 cudaError_t launch_null_scatter(const RepDesc* d_descs, int nrep, int64_t total_vac, const VacRec* vac,
                                 VacRec* recs, int32_t* counts, int64_t nfrag_total, int cap, uint32_t* status,
                                 cudaStream_t st);
+cudaError_t null_upload_neighbours(const NbEntry* host24);
 cudaError_t launch_null_step(const RepDesc* d_descs, int nrep, int64_t total_vac, int64_t total_picks, VacRec* vac,
-                             uint32_t* occ, const NbTable& nbt, const uint8_t* gb, unsigned long long* acc,
+                             uint32_t* occ, const uint8_t* gb, unsigned long long* acc,
                              NullProp* props,
                              unsigned long long* claims, int32_t* tracer, double* theta, double* nE,
                              unsigned long long* stats, unsigned long long* nctl, cudaStream_t st);

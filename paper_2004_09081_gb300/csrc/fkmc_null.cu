@@ -18,6 +18,8 @@
 // so every sum is an exact integer and no reduction order enters the result.
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include <algorithm>
 
 #include "fkmc_device.cuh"
@@ -80,10 +82,23 @@ __device__ __forceinline__ int64_t lin(const RepDesc& D, int t, int x, int y, in
 
 // fixed-point rate of neighbour n of a vacancy at (t, x, y, z); 0 for a
 // vacancy; the raised table for a hop touching a grain-boundary cell (gb)
-__device__ __forceinline__ uint64_t null_rate(const RepDesc& D, const NbTable& nbt, const uint32_t* occ,
-                                              const uint8_t* gb, int t, int x, int y, int z, int n)
+// The neighbour table in global memory: threads of a warp index it with
+// different site types, which a kernel-parameter (constant bank) table would
+// serve one distinct entry at a time.
+__device__ __align__(8) NbEntry g_nbn[3][8];
+
+__device__ __forceinline__ NbEntry null_nb(int t, int n)
 {
-    const NbEntry nb = nbt.e[t][n];
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(&g_nbn[0][0]) + 8 * t + n);
+    NbEntry e;
+    memcpy(&e, &v, sizeof e);
+    return e;
+}
+
+__device__ __forceinline__ uint64_t null_rate(const RepDesc& D, const uint32_t* occ, const uint8_t* gb, int t, int x,
+                                              int y, int z, int n)
+{
+    const NbEntry nb = null_nb(t, n);
     const int jx = wrapc(x + nb.dc[0], D.L[0]);
     const int jy = wrapc(y + nb.dc[1], D.L[1]);
     const int jz = wrapc(z + nb.dc[2], D.L[2]);
@@ -142,7 +157,7 @@ __global__ void k_null_scatter(const RepDesc* __restrict__ descs, int nrep, int6
 
 // acc[3 r + 0] = R_tot, acc[3 r + 1] = R_max, acc[3 r + 2] = N_updated
 __global__ void __launch_bounds__(256) k_null_rates(const RepDesc* __restrict__ descs, int nrep, int64_t total_vac,
-                                                    const VacRec* __restrict__ vac, const uint32_t* occ, NbTable nbt,
+                                                    const VacRec* __restrict__ vac, const uint32_t* occ,
                                                     const uint8_t* __restrict__ gb, unsigned long long* acc,
                                                     unsigned long long* nctl)
 {
@@ -159,7 +174,7 @@ __global__ void __launch_bounds__(256) k_null_rates(const RepDesc* __restrict__ 
         int t, x, y, z;
         split_key(vac[i].key, t, x, y, z);
 #pragma unroll
-        for (int n = 0; n < 8; ++n) R += null_rate(D, nbt, occ, gb, t, x, y, z, n);
+        for (int n = 0; n < 8; ++n) R += null_rate(D, occ, gb, t, x, y, z, n);
     }
     const int r0 = __shfl_sync(0xffffffffu, r, 0);
     if (__all_sync(0xffffffffu, valid && r == r0)) {  // one replica: reduce in the warp first
@@ -180,7 +195,7 @@ __global__ void __launch_bounds__(256) k_null_rates(const RepDesc* __restrict__ 
 }
 
 __global__ void __launch_bounds__(256) k_null_propose(const RepDesc* __restrict__ descs, int nrep, int64_t total_picks,
-                                                      const VacRec* __restrict__ vac, const uint32_t* occ, NbTable nbt,
+                                                      const VacRec* __restrict__ vac, const uint32_t* occ,
                                                       const uint8_t* __restrict__ gb, const unsigned long long* acc,
                                                       NullProp* props,
                                                       unsigned long long* claims, double* nE,
@@ -201,7 +216,7 @@ __global__ void __launch_bounds__(256) k_null_propose(const RepDesc* __restrict_
     const unsigned long long target = __umul64hi(blk.x[0], acc[3 * r + 1]);
     unsigned long long q[8];
 #pragma unroll
-    for (int n = 0; n < 8; ++n) q[n] = null_rate(D, nbt, occ, gb, t, x, y, z, n);  // 8 independent loads
+    for (int n = 0; n < 8; ++n) q[n] = null_rate(D, occ, gb, t, x, y, z, n);  // 8 independent loads
     unsigned long long P = 0ull;
     int sel = -1;
 #pragma unroll
@@ -219,7 +234,7 @@ __global__ void __launch_bounds__(256) k_null_propose(const RepDesc* __restrict_
     pr.pad = 0;
     props[i] = pr;
     if (sel < 0) return;
-    const NbEntry nb = nbt.e[t][sel];
+    const NbEntry nb = null_nb(t, sel);
     const unsigned long long mine = claim_of(k, p);
     atomicMin(claims + D.site_off + lin(D, t, x, y, z), mine);
     atomicMin(claims + D.site_off +
@@ -245,7 +260,7 @@ __device__ __forceinline__ void null_time(const RepDesc& D, int r, unsigned long
 
 // nctl[2] counts the blocks of this launch that have finished
 __global__ void __launch_bounds__(256) k_null_apply(const RepDesc* __restrict__ descs, int nrep, int64_t total_picks,
-                                                    VacRec* vac, uint32_t* occ, NbTable nbt,
+                                                    VacRec* vac, uint32_t* occ,
                                                     const NullProp* __restrict__ props,
                                                     const unsigned long long* claims, int32_t* tracer,
                                                     unsigned long long* acc, double* theta,
@@ -266,7 +281,7 @@ __global__ void __launch_bounds__(256) k_null_apply(const RepDesc* __restrict__ 
             VacRec& v = vac[D.vac_off + pr.v];
             int t, x, y, z;
             split_key(v.key, t, x, y, z);
-            const NbEntry nb = nbt.e[t][pr.n];
+            const NbEntry nb = null_nb(t, pr.n);
             const int jx = wrapc(x + nb.dc[0], D.L[0]);
             const int jy = wrapc(y + nb.dc[1], D.L[1]);
             const int jz = wrapc(z + nb.dc[2], D.L[2]);
@@ -339,18 +354,23 @@ cudaError_t launch_null_scatter(const RepDesc* d_descs, int nrep, int64_t total_
     return cudaGetLastError();
 }
 
+cudaError_t null_upload_neighbours(const NbEntry* host24)
+{
+    return cudaMemcpyToSymbol(g_nbn, host24, sizeof(NbEntry) * 24);
+}
+
 // One step of every replica (three launches; fixed arguments, so a graph can
 // hold it).  nctl[2] must be 0 before the first step.
 cudaError_t launch_null_step(const RepDesc* d_descs, int nrep, int64_t total_vac, int64_t total_picks, VacRec* vac,
-                             uint32_t* occ, const NbTable& nbt, const uint8_t* gb, unsigned long long* acc,
+                             uint32_t* occ, const uint8_t* gb, unsigned long long* acc,
                              NullProp* props,
                              unsigned long long* claims, int32_t* tracer, double* theta, double* nE,
                              unsigned long long* stats, unsigned long long* nctl, cudaStream_t st)
 {
-    k_null_rates<<<grid_of(total_vac), NT, 0, st>>>(d_descs, nrep, total_vac, vac, occ, nbt, gb, acc, nctl);
-    k_null_propose<<<grid_of(total_picks), NT, 0, st>>>(d_descs, nrep, total_picks, vac, occ, nbt, gb, acc, props,
+    k_null_rates<<<grid_of(total_vac), NT, 0, st>>>(d_descs, nrep, total_vac, vac, occ, gb, acc, nctl);
+    k_null_propose<<<grid_of(total_picks), NT, 0, st>>>(d_descs, nrep, total_picks, vac, occ, gb, acc, props,
                                                         claims, nE, nctl);
-    k_null_apply<<<grid_of(total_picks), NT, 0, st>>>(d_descs, nrep, total_picks, vac, occ, nbt, props, claims, tracer,
+    k_null_apply<<<grid_of(total_picks), NT, 0, st>>>(d_descs, nrep, total_picks, vac, occ, props, claims, tracer,
                                                       acc, theta, stats, nE, nctl);
     return cudaGetLastError();
 }
