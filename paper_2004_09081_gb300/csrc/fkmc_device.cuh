@@ -205,7 +205,8 @@ __device__ __forceinline__ float neglog32(uint64_t x)
 // with the first Philox block of its phase (events 0 and 1).
 struct ActEntry {
     int32_t rep;        // replica index in the batch
-    int32_t pad;
+    int32_t nv;         // the fragment's vacancy count (unchanged until its run pass: hops leave a
+                        // fragment only for fragments of other colours)
     int64_t fid;        // fragment index inside the replica
     uint64_t xs[2];     // selection words of events 0, 1
     uint64_t E[2];      // their exponential variates: fp64 bits (plain) or fp32 bits (mixed)

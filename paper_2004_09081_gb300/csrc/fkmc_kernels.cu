@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(256) k_screen(const RepDesc* __restrict__ desc
                 const uint64_t w = D.window + wctl[1];
                 const U64x4 blk = philox4x64((uint64_t)fid, w, 0, 0, D.seed, key_word(D.replica, PURPOSE_HOP));
                 e.rep = lo;
-                e.pad = nv;
+                e.nv = nv;
                 e.fid = fid;
                 e.xs[0] = blk.x[1];
                 e.xs[1] = blk.x[3];
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(128, 8) k_run(const RepDesc* __restrict__ desc
     }
     const int64_t g = D.frag_base + fid;
 
-    int nv = counts[g];
+    int nv = ent.nv;  // the screen pass's count
     if (nv > cap) {
         if (lane == 0) atomicOr(status, STATUS_OVERFLOW);
         nv = cap;
@@ -860,7 +860,7 @@ __global__ void __launch_bounds__(128, 8) k_run_small(const RepDesc* __restrict_
             const int kept = __popc(surv);
             counts[g] = kept;
             if (i) atomicAdd(stats + 2 * ent.rep, (unsigned long long)i);
-            if (ent.pad > kept) atomicAdd(stats + 2 * ent.rep + 1, (unsigned long long)(ent.pad - kept));
+            if (ent.nv > kept) atomicAdd(stats + 2 * ent.rep + 1, (unsigned long long)(ent.nv - kept));
         }
     }
 }
