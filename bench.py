@@ -525,6 +525,12 @@ def main():
                 "traffic": load_traffic(tag), "peak_kind": f"{peak_kind} hbm_gbs",
                 "kernel": kname, "bytes_per_hop": b_alg, "hops_per_launch": hops / units,
                 "avg_launch_us": avg_launch_s * 1e6, "note": note}
+    if roofline["traffic"]:
+        # the measured side: ncu's DRAM bytes per launch over the live launch time,
+        # and per hop (against the algorithmic bytes_per_hop)
+        gbs = roofline["traffic"] / avg_launch_s / 1e9
+        roofline["measured_dram"] = {"GBps": gbs, "frac": gbs / peak,
+                                     "bytes_per_hop": roofline["traffic"] / max(hops / units, 1e-9)}
     cnt = load_counters(tag) if all_resident else None
     if cnt and cnt.get("smem_wavefronts_per_launch") and clk.get("sm_mhz"):
         # the replica-resident kernel works out of shared memory: its shared-memory
