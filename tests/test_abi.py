@@ -86,3 +86,20 @@ def test_site_shell_tables_match_oracle(lib):
         lib.kmc_site_shells([(3, 0.1)], [], 0)  # not an O-O distance
     with pytest.raises(lib.KmcError):
         lib.kmc_site_shells([(2, 0.1), (2, 0.2)], [], 0)  # listed twice
+
+
+@pytest.mark.parametrize("field,value", [("small_pass", 2), ("small_pass", -2), ("schedule", 3), ("precision", 5),
+                                         ("cap_v", 12), ("n_tau", 0.0), ("n_tau", 65.0)])
+def test_create_batch_rejects_bad_options(lib, field, value):
+    """Options are checked before any device work: a bad value is FKMC_EINVAL
+    (so this runs without a GPU)."""
+    o = lib.kmc_default_opts()
+    setattr(o, field, value)
+    with pytest.raises(lib.KmcError) as e:
+        lib.kmc_create_batch([lib.kmc_cells(8, 8, 8, 3.905)], [lib.kmc_composition(5, 0, 0)], 0, o)
+    assert e.value.code == lib.FKMC_EINVAL
+
+
+def test_default_options_of_the_run_passes(lib):
+    o = lib.kmc_default_opts()
+    assert o.small_pass == 0 and o.schedule == 0 and o.cluster_top == -1
