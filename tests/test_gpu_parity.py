@@ -275,3 +275,24 @@ def test_cluster_pairs_bit_exact(fk, orc):
         assert info.hops == ref.counters()["hops"] > 0
         assert np.array_equal(b.state(r), ref.occupancy()), r
         assert np.array_equal(b.records(r), ref.records()), r
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_small_pass_by_default_on_a_large_phase(fk, orc, prec):
+    """128^3 cells in 2^3-cell fragments: 32768 fragments per colour phase, so
+    the small-fragment pass runs beside the general one by default (on a second
+    stream inside the window graph); bit for bit against the oracle."""
+    cells, nf = (128, 128, 128), (64, 64, 64)
+    nv = 3 * 128 ** 3 // 1000
+    b = fk.Batch([(*cells, 4.01)], [(nv, 0)], 17, nfrag=nf, precision=prec, tracer=True, cap_v=16)
+    b.set_barriers(0.7, 0.35, 600.0, field_z=1e7)
+    ref = orc.Lattice(cells, nf, nv, 0, seed=17, tracer=True)
+    ref.set_rates(0.7, 0.35, 600.0, Ez=1e7, a_ang=4.01, cap_v=16, precision=prec)
+    s = b.run(8)
+    assert s.launches >= 8 * 25  # the split window: 8 x (screen, general and small run passes) + set-up
+    ref.run(8)
+    assert np.array_equal(b.state(), ref.occupancy())
+    assert np.array_equal(b.records(), ref.records())
+    assert np.array_equal(b.tracer_field(), ref.tracer_field())
+    info, c = b.info(), ref.counters()
+    assert (info.hops, info.handoffs) == (c["hops"], c["handoffs"]) and c["hops"] > 30000
