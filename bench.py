@@ -359,8 +359,9 @@ def physics_report(fkmc, b, wl):
         return {"replicas": None, "note": "per-replica D in D_mixed_vs_plain; not listed for large batches"}
     for r, rep in enumerate(wl.replicas):
         row = {"T": rep.T, "cells": rep.cells[0], "n_vac": rep.n_vac, "n_H": rep.n_H}
-        Dx, D, v = b.D(r, fkmc.FKMC_V)
-        row.update({"D_V": D, "D_V_z": Dx[2], "D_V_xy": 0.5 * (Dx[0] + Dx[1]), "v_z_V": v})
+        Dx, D, Dxy, v = b.D(r, fkmc.FKMC_V)
+        row.update({"D_V": D, "D_V_z": Dx[2], "D_V_xy": Dxy, "v_z_V": float(v[2]),
+                    "D_V_z_definition": "(<dz^2> - <dz>^2) / (2t), drift removed"})
         if wl.tracer:
             for sp, nm in ((fkmc.FKMC_O, "O"), (fkmc.FKMC_H, "H")):
                 if nm == "H" and rep.n_H == 0:

@@ -133,7 +133,11 @@ typedef struct {
                            pass of their own (4 or 2 fragments per warp, lock-step) beside the
                            general pass; same trajectory.  0 (default) = where a phase holds
                            32768 fragments or more, 1 = always, -1 = never */
-    int32_t reserved[5];
+    int32_t test_stuck_wait_us; /* test of the device-side bounded wait (0 = off): the replica-resident
+                                   kernel, after staging its state, waits on a barrier that nothing
+                                   completes, gives up after this many microseconds (<= 2e6) and
+                                   kmc_run returns FKMC_ETIMEOUT with the state untouched */
+    int32_t reserved[4];
 } kmc_opts;
 
 typedef struct {
@@ -373,10 +377,20 @@ int kmc_read_moments_all(kmc_batch* b, int64_t* out, size_t n_out);
 int kmc_read_msd(kmc_batch* b, int32_t r, int32_t species, double msd_xyz[3],
                  double mean_xyz[3], double* t_s);
 
-/* D_axis = <d_axis^2>/(2t), D = MSD/(6t) (m^2/s), and the drift velocity
- * v_z = <dz>/t (m/s) of one species. */
-int kmc_read_D(kmc_batch* b, int32_t r, int32_t species, double D_xyz[3], double* D,
-               double* v_drift_z);
+/* Diffusion coefficients of one species of replica r from the tracked
+ * displacements after t = kmc_read_msd's time (Sec. III: D from the
+ * trajectories of the particles; the bias run of the mu-scale model section):
+ *   D_xyz[k]   = (<d_k^2> - <d_k>^2) / (2t)   per axis, the drift removed
+ *                (D_z = D_xyz[2] along the field)                       m^2/s
+ *   D          = (<dx^2> + <dy^2> + <dz^2>) / (6t)   MSD / (6t)           m^2/s
+ *   D_xy       = (<dx^2> + <dy^2>) / (4t)    in the plane normal to the field
+ *   v_drift[k] = <d_k> / t                   drift velocity               m/s
+ * Means are over the replica's particles of that species, so the drift-removed
+ * D_xyz needs many of them (with one particle it is 0).  Any output pointer
+ * may be NULL.  Errors: as kmc_read_moments; FKMC_ESTATE before any simulated
+ * time. */
+int kmc_read_D(kmc_batch* b, int32_t r, int32_t species, double D_xyz[3], double* D, double* D_xy,
+               double v_drift[3]);
 
 /* Occupancy of replica r, one species code per site, site index
  * ((t nz + z) ny + y) nx + x with t the site type (0: a/2 x, 1: a/2 y,
@@ -397,10 +411,22 @@ int kmc_read_records(kmc_batch* b, int32_t r, int64_t* rows, int64_t max_rows, i
 /* Tracer displacements of replica r, 3 int32 per site (FKMC_ESTATE without tracer). */
 int kmc_read_tracer(kmc_batch* b, int32_t r, int32_t* host_disp, size_t n_sites);
 
-/* Packed device state of the whole batch (occupancy planes, vacancy records,
- * counts) as one opaque blob, for end-to-end transfers: kmc_state_bytes gives
- * its size; kmc_download_state / kmc_upload_state copy it to / from host
- * memory (pinned memory gives full copy bandwidth). */
+/* The whole mutable state of the batch as one opaque blob, for checkpoints
+ * and end-to-end transfers: a header (magic, batch shape), per replica its
+ * window and null-event step counters, hop and hand-off counters, null-event
+ * clock and vacancy / H- counts, then the device arrays -- occupancy planes,
+ * vacancy records and counts, and where present the tracer field, the dopants,
+ * the electrostatic energies u and each replica's last potential (the warm
+ * start of the next solve) with the windows since that solve.  A batch
+ * created with the same cells, compositions, seed and options, given the same
+ * kmc_set_barriers / kmc_set_site_energy / kmc_set_grains /
+ * kmc_set_electrostatics calls, continues from an uploaded blob exactly as
+ * the batch it was downloaded from (the random streams are keyed by the
+ * restored counters).  kmc_state_bytes gives the size; kmc_download_state /
+ * kmc_upload_state copy it to / from host memory (pinned memory gives full
+ * copy bandwidth).  Errors: FKMC_EINVAL for a wrong size or a blob of another
+ * batch shape (replica count, sizes, cap_v, tracer, dopants, electrostatics
+ * on/off); FKMC_ECUDA. */
 int kmc_state_bytes(kmc_batch* b, size_t* bytes);
 int kmc_download_state(kmc_batch* b, void* host, size_t bytes);
 int kmc_upload_state(kmc_batch* b, const void* host, size_t bytes);
@@ -426,22 +452,28 @@ void kmc_neighbour_table(int32_t out[168]);
  * routine here.
  *   d_records        device array of offsets[n_groups] x cap_v 24-byte records
  *                    {u64 site key, int32 d[3], uint32 id} (the batch's layout),
- *                    fragment-major; only the displacements d are read
+ *                    fragment-major; only the displacements d are read; it must
+ *                    hold offsets[n_groups] x cap_v records on the current device
  *   d_counts         device int32[offsets[n_groups]]: slots in use per fragment
+ *                    (each <= cap_v), on the current device
  *   fragment_offsets host int64[n_groups + 1]: group g owns fragments
  *                    [offsets[g], offsets[g+1]); offsets[0] = 0, non-decreasing
+ *                    (a group may be empty); offsets[n_groups] x cap_v must fit
+ *                    in int64
  *   n_groups         1 .. FKMC_NOALLOC_MAX_GROUPS
  *   out              host int64[7 n_groups], as in kmc_read_moments
- *   stream           cudaStream_t (NULL = legacy default stream); synchronous
- * Its only scratch (the offsets and the accumulators, about 256 KiB) is a
- * static device array that every GPU loading the library holds until the
- * process exits.  The first call on a device looks up that array's address
- * (cudaGetSymbolAddress) with the device current; make that first call before
- * any stream capture.  All calls share the array and it keeps the last call's
- * contents (the accumulators are cleared at the start of each call), so calls
- * that overlap on the GPU -- on two streams, or from two threads -- race.
+ *   stream           cudaStream_t (NULL = legacy default stream)
+ * The call is synchronous (it waits for the stream and copies into `out`), so
+ * it must not be made while its stream is being captured: it then returns
+ * FKMC_EINVAL.  Its only scratch (the offsets and the accumulators, about
+ * 256 KiB) is a static device array that every GPU loading the library holds
+ * until the process exits.  The first call on a device looks up that array's
+ * address (cudaGetSymbolAddress) and the SM count with the device current.
+ * All calls share the array and it keeps the last call's contents (the
+ * accumulators are cleared at the start of each call), so calls that overlap
+ * on the GPU -- on two streams, or from two threads -- race.
  * Errors: FKMC_EINVAL for null pointers, n_groups outside [1, 4096], cap_v
- * outside [1, 256] or bad offsets; FKMC_ECUDA. */
+ * outside [1, 256], bad offsets or a capturing stream; FKMC_ECUDA. */
 #define FKMC_NOALLOC_MAX_GROUPS 4096
 int kmc_vacancy_moments_noalloc(const void* d_records, const int32_t* d_counts,
                                 const int64_t* fragment_offsets, int32_t n_groups, int32_t cap_v,

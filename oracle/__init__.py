@@ -52,6 +52,8 @@ def lib():
         sig = {
             "orc_philox4x64": (None, [P, P, P]),
             "orc_neglog64": (d, [u64]),
+            "orc_neglog64_batch": (None, [P, P, i64]),
+            "orc_partition_count": (C.c_int, [C.c_int, C.c_int]),
             "orc_neglog32": (C.c_float, [u64]),
             "orc_neighbour_table": (None, [P]),
             "orc_feistel": (u64, [u64, u64, u64, u32]),
@@ -109,6 +111,19 @@ def neglog64(x: int) -> float:
     return lib().orc_neglog64(int(x))
 
 
+def neglog64_batch(x: np.ndarray) -> np.ndarray:
+    xs = np.ascontiguousarray(x, dtype=np.uint64)
+    out = np.zeros(xs.size, np.float64)
+    lib().orc_neglog64_batch(_ptr(xs), _ptr(out), xs.size)
+    return out
+
+
+def partition(cells, edge: int):
+    """Fragments per dimension for a target fragment edge (even count nearest
+    L/edge with edges >= 2 cells, else one fragment)."""
+    return tuple(int(lib().orc_partition_count(int(L), int(edge))) for L in cells)
+
+
 def neglog32(x: int) -> float:
     return lib().orc_neglog32(int(x))
 
@@ -148,10 +163,13 @@ def rate_table(Ea_O, Ea_H, A, q_O, q_H, T, Ez, a_ang, cap_v=64):
 
 # ---------------------------------------------------------------- lattice
 class Lattice:
-    """One replica held by the oracle.  ``nf`` = fragments per dimension."""
+    """One replica held by the oracle.  ``nf`` = fragments per dimension, or
+    None to derive them from the target fragment edge ``edge`` (partition)."""
 
-    def __init__(self, cells, nf, n_vac, n_H, seed=0, replica=0, tracer=False, n_Fe=0):
+    def __init__(self, cells, nf, n_vac, n_H, seed=0, replica=0, tracer=False, n_Fe=0, edge=None):
         self.L = tuple(int(c) for c in cells)
+        if nf is None:
+            nf = partition(self.L, 4 if edge is None else edge)
         self.nf = tuple(int(f) for f in nf)
         self.nsite = 3 * self.L[0] * self.L[1] * self.L[2]
         self.ncell = self.L[0] * self.L[1] * self.L[2]
@@ -300,13 +318,28 @@ class Lattice:
         return out
 
     def diffusion(self, species=SP_V, t=None):
-        """D (m^2/s): MSD/(6t) from tracked displacements (Sec. III), plus the
-        per-axis D_x = <dx^2>/(2t) and the mean z displacement."""
+        """D of one species from its tracked displacements (Sec. III, D from
+        per-atom trajectories); see diffusion_from_moments."""
         m = self.moments(species)
         if t is None:
             t = self.counters()["window"] * self.params()["tau"] + self.null_clock()["t"]
-        n = max(int(m[0]), 1)
-        h = 0.5 * self.a_ang * 1e-10
-        msd = m[4:7].astype(np.float64) / n * h * h
-        mean = m[1:4].astype(np.float64) / n * h
-        return {"D": msd.sum() / (6 * t), "D_axes": msd / (2 * t), "mean": mean, "t": t, "n": n}
+        return diffusion_from_moments(m, t, self.a_ang)
+
+
+def diffusion_from_moments(m, t: float, a_ang: float):
+    """D from the integer moments m = {count, sum d_k, sum d_k^2} (units a/2)
+    after time t (s), a in Angstrom; every mean is over the tracked particles:
+      D      = (<dx^2> + <dy^2> + <dz^2>) / (6 t)        mean squared displacement
+      D_xy   = (<dx^2> + <dy^2>) / (4 t)                 in-plane
+      D_axes = (<d_k^2> - <d_k>^2) / (2 t)               per axis, drift removed
+      D_z    = D_axes[2]                                 along the field
+      v      = <d_k> / t                                 drift velocity
+    Moments of several independent lattices may be summed first (pooled)."""
+    m = np.asarray(m, dtype=np.int64)
+    n = max(int(m[0]), 1)
+    h = 0.5 * a_ang * 1e-10
+    msd = m[4:7].astype(np.float64) / n * h * h
+    mean = m[1:4].astype(np.float64) / n * h
+    var = msd - mean * mean
+    return {"D": msd.sum() / (6 * t), "D_xy": (msd[0] + msd[1]) / (4 * t), "D_axes": var / (2 * t),
+            "D_z": var[2] / (2 * t), "v": mean / t, "msd": msd, "mean": mean, "t": t, "n": n}

@@ -106,7 +106,18 @@ static void key_for(uint64_t seed, uint32_t replica, uint32_t purpose, uint64_t 
  * these two functions.                                                  */
 /* ------------------------------------------------------------------ */
 
-/* FP64: u = (2 floor(x/2^12) + 1) 2^-53, an exact double in (0,1). Returns -ln u. */
+/* ln 2 split so that e * LN2_HI is exact for |e| < 2^20: LN2_HI is ln 2
+ * rounded to 32 fraction bits, LN2_LO the double nearest ln 2 - LN2_HI. */
+static const double LN2_HI = 0x1.62e42ff000000p-1;
+static const double LN2_LO = -0x1.718432a1b0e26p-35;
+
+/* FP64: u = (2 floor(x/2^12) + 1) 2^-53, an exact double in (0,1). Returns -ln u.
+ * With f = m - 1 (exact), s = f / (2 + f) and R = 2 s^3/3 + 2 s^5/5 + ... =
+ * s Q, Q = s^2 (2/3 + 2 s^2/5 + ...), the identity 2 s = f - f^2/2 + s f^2/2
+ * gives ln m = f - (f^2/2 - s (f^2/2 + Q)): the exact f carries the result and
+ * rounding enters only through the smaller terms.  The order of the final sum
+ * is that of the classic fdlibm log (Sun Microsystems, 1993); with it the
+ * result is within 1 ulp of the correctly rounded -ln u. */
 double orc_neglog64(uint64_t x)
 {
     double u = (double)(2 * (x >> 12) + 1) * 0x1p-53;
@@ -117,7 +128,8 @@ double orc_neglog64(uint64_t x)
     double m;
     memcpy(&m, &mb, 8); /* m in [0.5, 1) */
     if (m < 0.70710678118654752440) { m = m * 2.0; e = e - 1; }
-    double s = (m - 1.0) / (m + 1.0);
+    double f = m - 1.0;
+    double s = f / (2.0 + f);
     double s2 = s * s;
     double p = 2.0 / 21.0;
     p = 2.0 / 19.0 + s2 * p;
@@ -129,10 +141,17 @@ double orc_neglog64(uint64_t x)
     p = 2.0 / 7.0 + s2 * p;
     p = 2.0 / 5.0 + s2 * p;
     p = 2.0 / 3.0 + s2 * p;
-    p = 2.0 + s2 * p;
-    double lnm = s * p;
-    double ln_u = (double)e * 0.69314718055994530942 + lnm;
+    double Q = s2 * p;
+    double hfsq = (0.5 * f) * f;
+    double de = (double)e;
+    double ln_u = de * LN2_HI - ((hfsq - (s * (hfsq + Q) + de * LN2_LO)) - f);
     return -ln_u;
+}
+
+/* orc_neglog64 of n inputs (for the accuracy pin over many points). */
+void orc_neglog64_batch(const uint64_t* x, double* out, int64_t n)
+{
+    for (int64_t i = 0; i < n; i++) out[i] = orc_neglog64(x[i]);
 }
 
 /* FP32 with the full 64-bit range: the leading one of x (x|1) fixes the
@@ -286,6 +305,26 @@ typedef struct {
     uint64_t handoffs;
     double clock_sum; /* sum over fragment phases of the final clock (diagnostic) */
 } orc_lattice;
+
+/* Fragments per dimension for a target edge e (the paper fixes neither; the
+ * reading): the even count nearest L/e, ties to the larger, among the even
+ * counts 2, 4, ... that keep every fragment at least 2 cells long (edges are
+ * floor(L/n) or ceil(L/n)); one fragment when no even count does (L < 4). */
+int orc_partition_count(int L, int e)
+{
+    if (L < 1 || e < 1) return 0;
+    double target = (double)L / (double)e;
+    int best = 1;
+    double best_dist = 0.0;
+    for (int n = 2; L / n >= 2; n += 2) {
+        double dist = fabs((double)n - target);
+        if (best == 1 || dist <= best_dist) {
+            best = n;
+            best_dist = dist;
+        }
+    }
+    return best;
+}
 
 static int frag_start(int L, int nf, int i)
 {
@@ -1129,23 +1168,29 @@ static uint64_t fmix64(uint64_t h)
 
 /* Pick p of step `step`: the image of p under a keyed bijection of [0, n):
  * an alternating Feistel network on m = max(2, ceil(log2 n)) bits (high part
- * m - m/2 bits, low part m/2 bits; round r = 0..3 XORs F_r of one part into
+ * m - m/2 bits, low part m/2 bits; round r = 0..11 XORs F_r of one part into
  * the other, high first), with cycle walking (Black & Rogaway) back into
- * [0, n).  F_r(x) = fmix64(x ^ k_r); the round keys k_0..k_3 are the Philox
- * block (step, 0, 0, 0) under the key (seed, replica, PICK). */
+ * [0, n).  F_r(x) = fmix64(x ^ k_r); the round keys k_0..k_11 are the Philox
+ * blocks (step, j, 0, 0), j = 0, 1, 2, under the key (seed, replica, PICK),
+ * k_{4j+i} = word i of block j.  Twelve rounds make the permutation of a
+ * small domain (n = 3..6) close to uniform over all n! orders; four are not. */
+#define NULL_PICK_ROUNDS 12
 static uint64_t null_pick(uint64_t p, uint64_t n, uint64_t seed, uint32_t replica, uint64_t step)
 {
     int m = 2;
     while (((uint64_t)1 << m) < n) m++;
     int bl = m / 2, bh = m - bl;
     uint64_t ml = ((uint64_t)1 << bl) - 1, mh = ((uint64_t)1 << bh) - 1;
-    uint64_t key[2], ctr[4] = {step, 0, 0, 0}, k[4];
+    uint64_t key[2], k[NULL_PICK_ROUNDS];
     key_for(seed, replica, PURPOSE_PICK, key);
-    orc_philox4x64(ctr, key, k);
+    for (int j = 0; j < NULL_PICK_ROUNDS / 4; j++) {
+        uint64_t ctr[4] = {step, (uint64_t)j, 0, 0};
+        orc_philox4x64(ctr, key, k + 4 * j);
+    }
     uint64_t v = p;
     do {
         uint64_t hi = v >> bl, lo = v & ml;
-        for (int r = 0; r < 4; r++) {
+        for (int r = 0; r < NULL_PICK_ROUNDS; r++) {
             if (r % 2 == 0) hi = hi ^ (fmix64(lo ^ k[r]) & mh);
             else lo = lo ^ (fmix64(hi ^ k[r]) & ml);
         }

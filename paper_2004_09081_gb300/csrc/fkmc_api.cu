@@ -742,6 +742,8 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
         return fail(FKMC_EINVAL, "cap_v must be 0 or a multiple of 8 in [8, 256]");
     if (o.schedule < 0 || o.schedule > 2) return fail(FKMC_EINVAL, "schedule must be 0, 1 or 2");
     if (o.small_pass < -1 || o.small_pass > 1) return fail(FKMC_EINVAL, "small_pass must be -1, 0 or 1");
+    if (o.test_stuck_wait_us < 0 || o.test_stuck_wait_us > 2000000)
+        return fail(FKMC_EINVAL, "test_stuck_wait_us must be in [0, 2e6]");
 
     kmc_batch* b = new kmc_batch();
     b->n = n;
@@ -975,7 +977,7 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
             CK(cudaStreamWaitEvent(c.st, b->fork, 0), "stream wait");
             CK(launch_resident(b->d_desc, b->d_reps + c.start, c.count, b->d_nvac, c.smem, c.threads, c.cluster,
                                windows, b->occ, b->recs, b->counts, b->tracer, b->stats, b->status, b->cap, b->nbt,
-                               c.st),
+                               (uint32_t)b->opts.test_stuck_wait_us, c.st),
                "resident kernel");
             CK(cudaEventRecord(c.done, c.st), "event record");
         }
@@ -1107,7 +1109,8 @@ int kmc_run_null(kmc_batch* b, uint64_t steps, int64_t n_frg, kmc_run_stats* sta
         b->nctl = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * 3);
         if (!b->claims || !b->nacc || !b->theta || !b->nE || !b->nctl)
             return fail(FKMC_ENOMEM, "device allocation failed (null-event buffers)");
-        CK(cudaMemsetAsync(b->theta, 0, sizeof(double) * b->n, b->st), "memset");
+        CK(cudaMemcpyAsync(b->theta, b->theta_host.data(), sizeof(double) * b->n, cudaMemcpyHostToDevice, b->st),
+           "clock upload");
     }
     if (total_picks > b->props_cap) {
         if (b->null_exec) cudaGraphExecDestroy(b->null_exec);
@@ -1229,16 +1232,20 @@ int kmc_read_msd(kmc_batch* b, int32_t r, int32_t species, double msd_xyz[3], do
     return FKMC_OK;
 }
 
-int kmc_read_D(kmc_batch* b, int32_t r, int32_t species, double D_xyz[3], double* D, double* v_drift_z)
+int kmc_read_D(kmc_batch* b, int32_t r, int32_t species, double D_xyz[3], double* D, double* D_xy,
+               double v_drift[3])
 {
     double msd[3], mean[3], t;
     int rc = kmc_read_msd(b, r, species, msd, mean, &t);
     if (rc) return rc;
     if (!(t > 0.0)) return fail(FKMC_ESTATE, "no simulated time yet");
-    for (int k = 0; k < 3; ++k)
-        if (D_xyz) D_xyz[k] = msd[k] / (2.0 * t);
+    for (int k = 0; k < 3; ++k) {
+        // the variance of the displacement along each axis: the drift is removed
+        if (D_xyz) D_xyz[k] = (msd[k] - mean[k] * mean[k]) / (2.0 * t);
+        if (v_drift) v_drift[k] = mean[k] / t;
+    }
     if (D) *D = (msd[0] + msd[1] + msd[2]) / (6.0 * t);
-    if (v_drift_z) *v_drift_z = mean[2] / t;
+    if (D_xy) *D_xy = (msd[0] + msd[1]) / (4.0 * t);
     return FKMC_OK;
 }
 
@@ -1382,11 +1389,67 @@ int kmc_read_tracer(kmc_batch* b, int32_t r, int32_t* host_disp, size_t n_sites)
     return FKMC_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The state blob: a header, one row of counters per replica, then every
+// mutable device array of the batch (each part starts on an 8-byte boundary).
+constexpr uint64_t BLOB_MAGIC = 0x31415453434d4b46ull;  // "FKMCSTA1"
+enum : uint32_t { BLOB_TRACER = 1u, BLOB_DOPANTS = 2u, BLOB_ELEC = 4u };
+struct BlobHeader {
+    uint64_t magic;
+    uint32_t n, flags;
+    uint64_t occ_words, nfrag_total, cap, nsite_total;
+    uint64_t elec_age, phi_prev_valid;
+};
+struct BlobReplica {
+    uint64_t window, null_step, hops, handoffs;
+    double null_theta;
+    int64_t n_vac, n_H;
+};
+static_assert(sizeof(BlobHeader) == 64 && sizeof(BlobReplica) == 56, "blob layout");
+
+uint32_t blob_flags(const kmc_batch* b)
+{
+    return (b->tracer ? BLOB_TRACER : 0u) | (b->fe ? BLOB_DOPANTS : 0u) | (b->elec_on ? BLOB_ELEC : 0u);
+}
+
+struct BlobPart {
+    void* dev;
+    size_t bytes;
+};
+
+// the device arrays of the blob in order, and the header + rows size
+size_t blob_parts(const kmc_batch* b, std::vector<BlobPart>* parts)
+{
+    const uint32_t f = blob_flags(b);
+    parts->clear();
+    parts->push_back({b->occ, sizeof(uint32_t) * b->occ_words});
+    parts->push_back({b->recs, sizeof(VacRec) * b->nfrag_total * b->cap});
+    parts->push_back({b->counts, sizeof(int32_t) * b->nfrag_total});
+    if (f & BLOB_TRACER) parts->push_back({b->tracer, sizeof(int32_t) * 3 * b->nsite_total});
+    if (f & BLOB_DOPANTS) parts->push_back({b->fe, (size_t)b->ncell_total});
+    if (f & BLOB_ELEC) {
+        parts->push_back({b->elec_u, sizeof(int32_t) * b->nsite_total});
+        parts->push_back({b->phi_prev, sizeof(double) * b->ncell_total});
+    }
+    return sizeof(BlobHeader) + sizeof(BlobReplica) * (size_t)b->n;
+}
+
+size_t align8(size_t v) { return (v + 7) & ~(size_t)7; }
+
+}  // namespace
+
+extern "C" {
+
 int kmc_state_bytes(kmc_batch* b, size_t* bytes)
 {
     if (!b || !bytes) return fail(FKMC_EINVAL, "null argument");
-    *bytes = sizeof(uint32_t) * b->occ_words + sizeof(VacRec) * b->nfrag_total * b->cap +
-             sizeof(int32_t) * b->nfrag_total;
+    std::vector<BlobPart> parts;
+    size_t total = blob_parts(b, &parts);
+    for (const BlobPart& p : parts) total = align8(total) + p.bytes;
+    *bytes = align8(total);
     return FKMC_OK;
 }
 
@@ -1397,11 +1460,29 @@ int kmc_download_state(kmc_batch* b, void* host, size_t bytes)
     if (rc) return rc;
     if (!host || bytes != need) return fail(FKMC_EINVAL, "buffer size must equal kmc_state_bytes");
     char* h = (char*)host;
-    const size_t a = sizeof(uint32_t) * b->occ_words, c = sizeof(VacRec) * b->nfrag_total * b->cap;
-    CK(cudaMemcpyAsync(h, b->occ, a, cudaMemcpyDeviceToHost, b->st), "state copy");
-    CK(cudaMemcpyAsync(h + a, b->recs, c, cudaMemcpyDeviceToHost, b->st), "state copy");
-    CK(cudaMemcpyAsync(h + a + c, b->counts, sizeof(int32_t) * b->nfrag_total, cudaMemcpyDeviceToHost, b->st),
-       "state copy");
+    std::vector<BlobPart> parts;
+    size_t off = blob_parts(b, &parts);
+    BlobHeader hd{};
+    hd.magic = BLOB_MAGIC;
+    hd.n = (uint32_t)b->n;
+    hd.flags = blob_flags(b);
+    hd.occ_words = (uint64_t)b->occ_words;
+    hd.nfrag_total = (uint64_t)b->nfrag_total;
+    hd.cap = (uint64_t)b->cap;
+    hd.nsite_total = (uint64_t)b->nsite_total;
+    hd.elec_age = b->elec_age;
+    hd.phi_prev_valid = b->phi_prev_valid ? 1u : 0u;
+    std::memcpy(h, &hd, sizeof hd);
+    for (int r = 0; r < b->n; ++r) {
+        BlobReplica row{b->desc[r].window, b->desc[r].null_step, b->stats_host[2 * r], b->stats_host[2 * r + 1],
+                        b->theta_host[r], b->n_vac[r], b->n_H[r]};
+        std::memcpy(h + sizeof hd + sizeof row * r, &row, sizeof row);
+    }
+    for (const BlobPart& p : parts) {
+        off = align8(off);
+        CK(cudaMemcpyAsync(h + off, p.dev, p.bytes, cudaMemcpyDeviceToHost, b->st), "state copy");
+        off += p.bytes;
+    }
     CK(cudaStreamSynchronize(b->st), "synchronize");
     return FKMC_OK;
 }
@@ -1413,17 +1494,58 @@ int kmc_upload_state(kmc_batch* b, const void* host, size_t bytes)
     if (rc) return rc;
     if (!host || bytes != need) return fail(FKMC_EINVAL, "buffer size must equal kmc_state_bytes");
     const char* h = (const char*)host;
-    const size_t a = sizeof(uint32_t) * b->occ_words, c = sizeof(VacRec) * b->nfrag_total * b->cap;
-    CK(cudaMemcpyAsync(b->occ, h, a, cudaMemcpyHostToDevice, b->st), "state upload");
-    CK(cudaMemcpyAsync(b->recs, h + a, c, cudaMemcpyHostToDevice, b->st), "state upload");
-    CK(cudaMemcpyAsync(b->counts, h + a + c, sizeof(int32_t) * b->nfrag_total, cudaMemcpyHostToDevice, b->st),
-       "state upload");
+    BlobHeader hd;
+    std::memcpy(&hd, h, sizeof hd);
+    if (hd.magic != BLOB_MAGIC || hd.n != (uint32_t)b->n || hd.flags != blob_flags(b) ||
+        hd.occ_words != (uint64_t)b->occ_words || hd.nfrag_total != (uint64_t)b->nfrag_total ||
+        hd.cap != (uint64_t)b->cap || hd.nsite_total != (uint64_t)b->nsite_total)
+        return fail(FKMC_EINVAL, "state blob of another batch shape (replicas, sizes, cap_v, tracer, dopants, "
+                                 "electrostatics)");
+    std::vector<BlobReplica> rows(b->n);
+    for (int r = 0; r < b->n; ++r) {
+        std::memcpy(&rows[r], h + sizeof hd + sizeof(BlobReplica) * r, sizeof(BlobReplica));
+        if (rows[r].n_vac < 0 || rows[r].n_H < 0 || rows[r].n_vac + rows[r].n_H > b->desc[r].nsite)
+            return fail(FKMC_EINVAL, "state blob: bad composition");
+    }
+    std::vector<BlobPart> parts;
+    size_t off = blob_parts(b, &parts);
+    for (const BlobPart& p : parts) {
+        off = align8(off);
+        CK(cudaMemcpyAsync(p.dev, h + off, p.bytes, cudaMemcpyHostToDevice, b->st), "state upload");
+        off += p.bytes;
+    }
+    for (int r = 0; r < b->n; ++r) {
+        b->desc[r].window = rows[r].window;
+        b->desc[r].null_step = rows[r].null_step;
+        b->stats_host[2 * r] = rows[r].hops;
+        b->stats_host[2 * r + 1] = rows[r].handoffs;
+        b->theta_host[r] = rows[r].null_theta;
+        b->n_vac[r] = rows[r].n_vac;
+        b->n_H[r] = rows[r].n_H;
+    }
+    CK(cudaMemcpyAsync(b->stats, b->stats_host.data(), sizeof(unsigned long long) * 2 * b->n, cudaMemcpyHostToDevice,
+                       b->st),
+       "counter upload");
+    if (b->theta)
+        CK(cudaMemcpyAsync(b->theta, b->theta_host.data(), sizeof(double) * b->n, cudaMemcpyHostToDevice, b->st),
+           "clock upload");
     CK(cudaStreamSynchronize(b->st), "synchronize");
-    b->field_valid = false;
-    b->elec_age = UINT64_MAX / 2;
-    b->phi_prev_valid = false;
-    drop_window_graph(b);
-    return FKMC_OK;
+    b->field_valid = false;  // the site-energy field is rebuilt from the restored vacancies, dopants and u
+    if (blob_flags(b) & BLOB_ELEC) {
+        b->elec_age = hd.elec_age;
+        b->phi_prev_valid = hd.phi_prev_valid != 0;
+    } else {
+        b->elec_age = UINT64_MAX / 2;
+        b->phi_prev_valid = false;
+    }
+    drop_window_graph(b);  // the captured solves hold the vacancy counts
+    if (b->rates_set) {
+        rc = plan_residency(b);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(b->d_nvac, b->n_vac.data(), sizeof(int64_t) * b->n, cudaMemcpyHostToDevice, b->st),
+           "vacancy count upload");
+    }
+    return upload_desc(b);
 }
 
 int kmc_set_site_energy(kmc_batch* b, const kmc_site_energy* e)

@@ -145,7 +145,17 @@ __device__ __forceinline__ uint64_t key_word(uint32_t replica, uint32_t purpose)
 // s = (m-1)/(m+1), m in [sqrt(1/2), sqrt(2)) (Abramowitz & Stegun 4.1.27),
 // with u = m 2^e.
 
+// ln 2 split for an exact e * LN2_HI (|e| < 2^20): ln 2 rounded to 32
+// fraction bits, and the double nearest the remainder.
+constexpr double LN2_HI = 0x1.62e42ff000000p-1;
+constexpr double LN2_LO = -0x1.718432a1b0e26p-35;
+
 // FP64 form: u = (2 floor(x/2^12) + 1) 2^-53, exactly representable in (0,1).
+// With f = m - 1 (exact), s = f/(2+f), Q = s^2 (2/3 + 2 s^2/5 + ...), the
+// identity 2s = f - f^2/2 + s f^2/2 gives ln m = f - (f^2/2 - s (f^2/2 + Q)):
+// the exact f carries the result, rounding enters through the small terms;
+// the final sum is ordered as in the classic fdlibm log (Sun, 1993).  Within
+// 1 ulp of the correctly rounded -ln u.
 __device__ __forceinline__ double neglog64(uint64_t x)
 {
     const double u = __dmul_rn(__ull2double_rn(2ull * (x >> 12) + 1ull), 0x1p-53);
@@ -156,7 +166,8 @@ __device__ __forceinline__ double neglog64(uint64_t x)
         m = __dmul_rn(m, 2.0);
         e -= 1;
     }
-    const double s = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
+    const double f = __dsub_rn(m, 1.0);
+    const double s = __ddiv_rn(f, __dadd_rn(2.0, f));
     const double s2 = __dmul_rn(s, s);
     double p = 2.0 / 21.0;
     p = __dadd_rn(2.0 / 19.0, __dmul_rn(s2, p));
@@ -168,9 +179,11 @@ __device__ __forceinline__ double neglog64(uint64_t x)
     p = __dadd_rn(2.0 / 7.0, __dmul_rn(s2, p));
     p = __dadd_rn(2.0 / 5.0, __dmul_rn(s2, p));
     p = __dadd_rn(2.0 / 3.0, __dmul_rn(s2, p));
-    p = __dadd_rn(2.0, __dmul_rn(s2, p));
-    const double lnm = __dmul_rn(s, p);
-    const double ln_u = __dadd_rn(__dmul_rn(__int2double_rn(e), 0.69314718055994530942), lnm);
+    const double Q = __dmul_rn(s2, p);
+    const double hfsq = __dmul_rn(__dmul_rn(0.5, f), f);
+    const double de = __int2double_rn(e);
+    const double inner = __dadd_rn(__dmul_rn(s, __dadd_rn(hfsq, Q)), __dmul_rn(de, LN2_LO));
+    const double ln_u = __dsub_rn(__dmul_rn(de, LN2_HI), __dsub_rn(__dsub_rn(hfsq, inner), f));
     return -ln_u;
 }
 

@@ -91,6 +91,6 @@ cudaError_t resident_prepare();
 cudaError_t launch_resident(const RepDesc* d_descs, const int32_t* d_reps, int nreps, const int64_t* d_nvac,
                             size_t smem, int threads, int cluster, uint64_t windows, uint32_t* occ, VacRec* recs,
                             int32_t* counts, int32_t* tracer, unsigned long long* stats, uint32_t* status,
-                            int cap, const NbTable& nbt, cudaStream_t st);
+                            int cap, const NbTable& nbt, uint32_t stuck_wait_us, cudaStream_t st);
 
 }  // namespace fkmc

@@ -55,9 +55,27 @@ __device__ __forceinline__ uint64_t fmix64(uint64_t h)
 
 // Pick p of a step: the image of p under an alternating Feistel bijection of
 // [0, 2^m), m = max(2, ceil(log2 n)), high part m - m/2 bits, low part m/2,
-// four rounds (high, low, high, low) of x ^= fmix64(other ^ k_r), walked back
-// into [0, n).  k[] = the step's Philox block under (seed, replica, PICK).
-__device__ __forceinline__ uint64_t null_pick(uint64_t p, uint64_t n, const U64x4& k)
+// twelve rounds (high, low, high, ...) of x ^= fmix64(other ^ k_r), walked back
+// into [0, n).  k[4j + i] = word i of the step's Philox block (step, j) under
+// (seed, replica, PICK), j = 0, 1, 2.
+constexpr int NULL_PICK_ROUNDS = 12;
+struct PickKeys {
+    uint64_t k[NULL_PICK_ROUNDS];
+};
+
+__device__ __forceinline__ PickKeys pick_keys(uint64_t step, uint64_t seed, uint32_t replica)
+{
+    PickKeys pk;
+#pragma unroll
+    for (int j = 0; j < NULL_PICK_ROUNDS / 4; ++j) {
+        const U64x4 b = philox4x64(step, (uint64_t)j, 0, 0, seed, key_word(replica, PURPOSE_PICK));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) pk.k[4 * j + i] = b.x[i];
+    }
+    return pk;
+}
+
+__device__ __forceinline__ uint64_t null_pick(uint64_t p, uint64_t n, const PickKeys& pk)
 {
     int m = 2;
     while ((1ull << m) < n) ++m;
@@ -66,10 +84,11 @@ __device__ __forceinline__ uint64_t null_pick(uint64_t p, uint64_t n, const U64x
     uint64_t v = p;
     do {
         uint64_t hi = v >> bl, lo = v & ml;
-        hi ^= fmix64(lo ^ k.x[0]) & mh;
-        lo ^= fmix64(hi ^ k.x[1]) & ml;
-        hi ^= fmix64(lo ^ k.x[2]) & mh;
-        lo ^= fmix64(hi ^ k.x[3]) & ml;
+#pragma unroll
+        for (int r = 0; r < NULL_PICK_ROUNDS; r += 2) {
+            hi ^= fmix64(lo ^ pk.k[r]) & mh;
+            lo ^= fmix64(hi ^ pk.k[r + 1]) & ml;
+        }
         v = (hi << bl) | lo;
     } while (v >= n);
     return v;
@@ -208,7 +227,7 @@ __global__ void __launch_bounds__(256) k_null_propose(const RepDesc* __restrict_
     const int64_t p = i - D.pick_off;
     const uint64_t k = nctl[1];
     const uint64_t step = D.null_step + k;
-    const U64x4 rk = philox4x64(step, 0, 0, 0, D.seed, key_word(D.replica, PURPOSE_PICK));
+    const PickKeys rk = pick_keys(step, D.seed, D.replica);
     const int64_t id = (int64_t)null_pick((uint64_t)p, (uint64_t)D.null_nv, rk);
     int t, x, y, z;
     split_key(vac[D.vac_off + id].key, t, x, y, z);

@@ -182,6 +182,7 @@ struct Shared {
     RepDesc D;
     NbEntry nb[3][8];
     uint64_t bar;
+    uint64_t bar_test;   // the wait test's barrier, which nothing completes
     uint32_t perms[64];  // colour orders of 64 consecutive windows (nibble p = colour of phase p)
     int nv_count;
     int nact;
@@ -329,7 +330,8 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                                                   const int64_t* __restrict__ nvac, uint64_t windows,
                                                   uint32_t* occ, VacRec* recs, int32_t* counts,
                                                   int32_t* tracer, unsigned long long* stats,
-                                                  uint32_t* status, int cap, NbTable nbt)
+                                                  uint32_t* status, int cap, NbTable nbt,
+                                                  uint32_t stuck_wait_us)
 {
     extern __shared__ __align__(128) unsigned char dyn[];
     __shared__ Shared sh;
@@ -406,6 +408,19 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
         mbar_wait_bounded(&sh.bar, 0, WAIT_NS);  // let copies in flight land before leaving
     }
     __syncthreads();
+    if (stuck_wait_us && rank == 0 && !sh.abort) {
+        // test of the bounded wait: no copy is in flight here, and the barrier
+        // below is never completed, so the wait must give up after
+        // stuck_wait_us, report FKMC_ETIMEOUT and leave the state untouched
+        if (tid == 0) mbar_init(&sh.bar_test, 1);
+        __syncthreads();
+        const bool done = mbar_wait_bounded(&sh.bar_test, 0, (uint64_t)stuck_wait_us * 1000ull);
+        if (!done && tid == 0) {
+            atomicOr(status, STATUS_TIMEOUT);
+            sh.abort = 1;
+        }
+        __syncthreads();
+    }
     if constexpr (CL > 1) {
         // every CTA of the cluster passes the same barriers: the decision to stop
         // is read from the first CTA after the cluster barrier
@@ -790,7 +805,7 @@ cudaError_t resident_prepare()
 cudaError_t launch_resident(const RepDesc* d_descs, const int32_t* d_reps, int nreps, const int64_t* d_nvac,
                             size_t smem, int threads, int cluster, uint64_t windows, uint32_t* occ, VacRec* recs,
                             int32_t* counts, int32_t* tracer, unsigned long long* stats, uint32_t* status,
-                            int cap, const NbTable& nbt, cudaStream_t st)
+                            int cap, const NbTable& nbt, uint32_t stuck_wait_us, cudaStream_t st)
 {
     if (nreps <= 0) return cudaSuccess;
     if (cluster == 2 && threads == 1024) {
@@ -807,20 +822,20 @@ cudaError_t launch_resident(const RepDesc* d_descs, const int32_t* d_reps, int n
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         return cudaLaunchKernelEx(&cfg, k_resident<1024, 2>, d_descs, d_reps, d_nvac, windows, occ, recs, counts,
-                                  tracer, stats, status, cap, nbt);
+                                  tracer, stats, status, cap, nbt, stuck_wait_us);
     }
     if (threads == 128)
         k_resident<128, 1><<<nreps, 128, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts, tracer,
-                                                     stats, status, cap, nbt);
+                                                     stats, status, cap, nbt, stuck_wait_us);
     else if (threads == 256)
         k_resident<256, 1><<<nreps, 256, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts, tracer,
-                                                     stats, status, cap, nbt);
+                                                     stats, status, cap, nbt, stuck_wait_us);
     else if (threads == 1024)
         k_resident<1024, 1><<<nreps, 1024, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts,
-                                                       tracer, stats, status, cap, nbt);
+                                                       tracer, stats, status, cap, nbt, stuck_wait_us);
     else
         k_resident<512, 1><<<nreps, 512, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts, tracer,
-                                                     stats, status, cap, nbt);
+                                                     stats, status, cap, nbt, stuck_wait_us);
     return cudaGetLastError();
 }
 

@@ -66,7 +66,7 @@ class kmc_opts(C.Structure):
                 ("tracer", C.c_int32), ("cap_v", C.c_int32), ("n_tau", C.c_double),
                 ("stream", C.c_void_p), ("alloc", kmc_alloc_fn), ("free", kmc_free_fn),
                 ("alloc_ctx", C.c_void_p), ("schedule", C.c_int32), ("cluster_top", C.c_int32),
-                ("small_pass", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("small_pass", C.c_int32), ("test_stuck_wait_us", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class kmc_run_stats(C.Structure):
@@ -94,7 +94,7 @@ _SIGNATURES = {
     "kmc_read_moments": (C.c_int, [_P, _I32, _I32, _P]),
     "kmc_read_moments_all": (C.c_int, [_P, _P, _SZ]),
     "kmc_read_msd": (C.c_int, [_P, _I32, _I32, _P, _P, _P]),
-    "kmc_read_D": (C.c_int, [_P, _I32, _I32, _P, _P, _P]),
+    "kmc_read_D": (C.c_int, [_P, _I32, _I32, _P, _P, _P, _P]),
     "kmc_read_state": (C.c_int, [_P, _I32, _P, _SZ]),
     "kmc_write_state": (C.c_int, [_P, _I32, _P, _SZ]),
     "kmc_read_records": (C.c_int, [_P, _I32, _P, _I64, _P]),
@@ -215,9 +215,10 @@ def kmc_read_msd(h, r: int, species: int):
 
 
 def kmc_read_D(h, r: int, species: int):
-    Dx, D, v = np.zeros(3), C.c_double(), C.c_double()
-    _check(load().kmc_read_D(h, r, species, _ptr(Dx), C.byref(D), C.byref(v)))
-    return Dx, D.value, v.value
+    """(D_xyz drift-removed per axis, D = MSD/6t, D_xy, v_drift[3]); m^2/s, m/s."""
+    Dx, D, Dxy, v = np.zeros(3), C.c_double(), C.c_double(), np.zeros(3)
+    _check(load().kmc_read_D(h, r, species, _ptr(Dx), C.byref(D), C.byref(Dxy), _ptr(v)))
+    return Dx, D.value, Dxy.value, v
 
 
 def kmc_read_state(h, r: int, nsite: int) -> np.ndarray:
@@ -435,7 +436,8 @@ class Batch:
     """A batch of replicas (one lattice = a batch of one) on the current GPU."""
 
     def __init__(self, cells, comps, seed=0, *, edge=4, nfrag=None, precision=FKMC_PLAIN,
-                 tracer=False, cap_v=0, n_tau=1.0, schedule=0, cluster_top=-1, small_pass=0, stream=None):
+                 tracer=False, cap_v=0, n_tau=1.0, schedule=0, cluster_top=-1, small_pass=0, stream=None,
+                 test_stuck_wait_us=0, alloc=None):
         import torch
         self._alloc = TorchAllocator()
         o = kmc_default_opts()
@@ -450,8 +452,11 @@ class Batch:
         o.schedule = int(schedule)
         o.cluster_top = int(cluster_top)
         o.small_pass = int(small_pass)
+        o.test_stuck_wait_us = int(test_stuck_wait_us)
         st = stream if stream is not None else torch.cuda.current_stream()
         o.stream = C.c_void_p(st.cuda_stream)
+        if alloc is not None:  # an allocator of the caller's: an object with c_alloc / c_free callbacks
+            self._alloc = alloc
         o.alloc = self._alloc.c_alloc
         o.free = self._alloc.c_free
         self._opts = o

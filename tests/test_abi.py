@@ -103,3 +103,51 @@ def test_create_batch_rejects_bad_options(lib, field, value):
 def test_default_options_of_the_run_passes(lib):
     o = lib.kmc_default_opts()
     assert o.small_pass == 0 and o.schedule == 0 and o.cluster_top == -1
+
+
+@pytest.mark.parametrize("tracer,n_fe", [(0, 0), (1, 0), (0, 3)])
+def test_allocation_failure_is_enomem_and_frees_everything(lib, tracer, n_fe):
+    """Failure injected on the host: the caller's allocator returns NULL from
+    its k-th call on, for every k.  kmc_create_batch must return FKMC_ENOMEM
+    and hand every block it did get back to the caller's free.  The allocator
+    never returns a full set of blocks, so the library never touches one on
+    the device: this runs with or without a GPU."""
+    import ctypes as C
+
+    def attempt(k):
+        got, freed = [], []
+
+        def alloc(ctx, n):
+            if len(got) + 1 >= k:
+                got.append(None)
+                return None
+            got.append(0x10000 * (len(got) + 1))  # distinct, never dereferenced
+            return got[-1]
+
+        def free(ctx, p):
+            freed.append(p)
+
+        ca, cf = lib.kmc_alloc_fn(alloc), lib.kmc_free_fn(free)
+        o = lib.kmc_default_opts()
+        o.tracer = tracer
+        o.cluster_top = 0
+        o.alloc, o.free = ca, cf
+        with pytest.raises(lib.KmcError) as e:
+            lib.kmc_create_batch([lib.kmc_cells(8, 8, 8, 3.905), lib.kmc_cells(6, 6, 6, 3.905)],
+                                 [lib.kmc_composition(5, 3, n_fe), lib.kmc_composition(2, 0, n_fe)], 0, o)
+        assert e.value.code == lib.FKMC_ENOMEM
+        assert sorted(freed) == sorted(p for p in got if p is not None)
+        return len(got)
+
+    total = attempt(1)  # every call fails: counts the allocations of a batch
+    assert total >= 14
+    for k in range(2, total + 1):
+        attempt(k)
+
+
+def test_create_batch_rejects_bad_wait_test_option(lib):
+    o = lib.kmc_default_opts()
+    o.test_stuck_wait_us = -1
+    with pytest.raises(lib.KmcError) as e:
+        lib.kmc_create_batch([lib.kmc_cells(8, 8, 8, 3.905)], [lib.kmc_composition(5, 0, 0)], 0, o)
+    assert e.value.code == lib.FKMC_EINVAL

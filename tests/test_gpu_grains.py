@@ -32,7 +32,8 @@ def test_grain_map_matches_oracle(fk, orc):
     for G, w in ((7, 1), (2, 2), (40, 1)):
         b.set_grains(G, w, 0.2)
         for r, c in enumerate(cells):
-            ref = orc.Lattice(c, tuple(b.info(r).nfrag), 5, 0, seed=3, replica=r)
+            ref = orc.Lattice(c, None, 5, 0, seed=3, replica=r, edge=4)
+            assert tuple(b.info(r).nfrag) == ref.nf
             ref.set_grains(G, w, 0.2)
             g, bnd = b.grains(r)
             rg, rb = ref.grains()

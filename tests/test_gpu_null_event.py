@@ -68,7 +68,8 @@ def test_batch_of_replicas(fk, orc):
     b.set_barriers(0.7, 0.35, T)
     b.run_null(400, 30)
     for r in range(3):
-        ref = orc.Lattice(cells[r], tuple(b.info(r).nfrag), *comps[r], seed=11, replica=r, tracer=True)
+        ref = orc.Lattice(cells[r], None, *comps[r], seed=11, replica=r, tracer=True, edge=4)
+        assert tuple(b.info(r).nfrag) == ref.nf
         ref.set_rates(0.7, 0.35, T[r], a_ang=4.01, cap_v=b.info(r).cap_v, precision=1)
         ref.null_run(400, 30)
         same(b, ref, r)

@@ -107,7 +107,8 @@ def test_batch_of_uneven_replicas(fk, orc):
         b.run(40)
         for r, (c, (nv, nh), T) in enumerate(zip(cells, comps, Ts)):
             info = b.info(r)
-            ref = orc.Lattice(c, tuple(info.nfrag), nv, nh, seed=21, replica=r, tracer=True)
+            ref = orc.Lattice(c, None, nv, nh, seed=21, replica=r, tracer=True, edge=4)
+            assert tuple(info.nfrag) == ref.nf
             ref.set_rates(0.7, 0.35, T, Ez=[0, 1e7, 0, -1e7, 0][r], a_ang=4.01, cap_v=64, precision=prec)
             ref.run(40)
             assert np.array_equal(b.state(r), ref.occupancy()), r
@@ -118,14 +119,23 @@ def test_batch_of_uneven_replicas(fk, orc):
                 assert np.array_equal(b.moments(r, sp), ref.moments(sp))
 
 
-def test_D_matches_oracle(fk, orc):
-    b, ref = run_pair(fk, orc, (12, 12, 12), (2, 2, 2), 20, 80, 5, 200, 1, T=900.0, Ez=1e7, schedule=2)
+@pytest.mark.parametrize("sched", [1, 2])
+def test_D_matches_oracle(fk, orc, sched):
+    """K6 under a field: D = MSD/6t, D_xy, the drift-removed per-axis D (D_z
+    along the field) and the drift velocity of every species, against the
+    oracle's statement of the same from the same trajectories."""
+    b, ref = run_pair(fk, orc, (12, 12, 12), (2, 2, 2), 40, 80, 5, 200, 1, T=900.0, Ez=1e8, schedule=sched)
     for sp in (0, 1, 2):
-        Dx, D, v = b.D(0, sp)
+        Dx, D, Dxy, v = b.D(0, sp)
         d = ref.diffusion(sp)
         assert D == pytest.approx(d["D"], rel=1e-12)
-        assert np.allclose(Dx, d["D_axes"], rtol=1e-12)
-        assert v == pytest.approx(d["mean"][2] / d["t"], rel=1e-12, abs=1e-30)
+        assert Dxy == pytest.approx(d["D_xy"], rel=1e-12)
+        assert np.allclose(Dx, d["D_axes"], rtol=1e-12, atol=0)
+        assert Dx[2] == pytest.approx(d["D_z"], rel=1e-12)
+        assert np.allclose(v, d["v"], rtol=1e-12, atol=1e-30)
+    # the field drives the vacancies along +z, and the drift is removed from D_z
+    Dx, D, Dxy, v = b.D(0, fk.FKMC_V)
+    assert v[2] > 0 and Dx[2] < b.moments(0, 2)[6] / 40 * (0.5 * 3.905e-10) ** 2 / (2 * ref.diffusion(2)["t"])
 
 
 def test_edge_cases(fk, orc):
@@ -213,7 +223,8 @@ def test_batched_workload_full_size_sampled(fk, orc):
     for r in sorted(set(largest) | {0, 1, 97, 200, 255}):
         rep = reps[r]
         info = b.info(r)
-        ref = orc.Lattice(rep.cells, tuple(info.nfrag), rep.n_vac, rep.n_H, seed=0, replica=r)
+        ref = orc.Lattice(rep.cells, None, rep.n_vac, rep.n_H, seed=0, replica=r, edge=wl.edge)
+        assert tuple(info.nfrag) == ref.nf
         ref.set_rates(rep.Ea_O, rep.Ea_H, rep.T, a_ang=rep.a, cap_v=cap, precision=wl.precision)
         ref.run(W)
         occ = b.state(r)
@@ -247,7 +258,7 @@ def test_um_scale_full_size_properties(fk):
     k0 = 1e13 * math.exp(-rep.Ea_O / (kB * rep.T))
     eps = q * rep.field_z * a / (4 * kB * rep.T)
     v_exact = 8.0 / 3.0 * a * k0 * math.sinh(eps)
-    _, _, vz = b.D(0, fk.FKMC_V)
+    vz = b.D(0, fk.FKMC_V)[3][2]
     t = b.info().window * b.info().tau
     h = 0.5 * a
     var = (m[6] / m[0] - (m[3] / m[0]) ** 2) * h * h / t**2
@@ -269,7 +280,8 @@ def test_cluster_pairs_bit_exact(fk, orc):
     b.run(12)
     for r, (c, (nv, nh), T) in enumerate(zip(cells, comps, Ts)):
         info = b.info(r)
-        ref = orc.Lattice(c, tuple(info.nfrag), nv, nh, seed=13, replica=r)
+        ref = orc.Lattice(c, None, nv, nh, seed=13, replica=r, edge=4)
+        assert tuple(info.nfrag) == ref.nf
         ref.set_rates(0.7, 0.35, T, a_ang=4.01, cap_v=32, precision=1)
         ref.run(12)
         assert info.hops == ref.counters()["hops"] > 0

@@ -117,8 +117,8 @@ def test_batch_of_interacting_replicas(fk, orc):
     b.set_barriers(0.7, 0.35, T)
     b.run(25)
     for r in range(3):
-        nf = tuple(b.info(r).nfrag)
-        ref = orc.Lattice(cells[r], nf, comps[r][0], comps[r][1], seed=13, replica=r, n_Fe=comps[r][2])
+        ref = orc.Lattice(cells[r], None, comps[r][0], comps[r][1], seed=13, replica=r, n_Fe=comps[r][2], edge=4)
+        assert tuple(b.info(r).nfrag) == ref.nf
         ref.set_site_energy(vv=PAPER_VV, fe=PAPER_VFE)
         ref.set_rates(0.7, 0.35, T[r], a_ang=4.01)
         ref.run(25)
@@ -183,7 +183,8 @@ def test_full_size_fe_workload_sampled(fk, orc):
     b.run(3)
     for r in (0, len(reps) - 1):
         rep = reps[r]
-        ref = orc.Lattice(rep.cells, tuple(b.info(r).nfrag), rep.n_vac, rep.n_H, seed=0, replica=r, n_Fe=rep.n_Fe)
+        ref = orc.Lattice(rep.cells, None, rep.n_vac, rep.n_H, seed=0, replica=r, n_Fe=rep.n_Fe, edge=wl.edge)
+        assert tuple(b.info(r).nfrag) == ref.nf
         ref.set_site_energy(vv=wl.site["vv"], fe=wl.site["fe"])
         ref.set_rates(rep.Ea_O, rep.Ea_H, rep.T, a_ang=rep.a, cap_v=b.info(r).cap_v)
         ref.run(3)

@@ -32,13 +32,32 @@ def test_pick_is_a_bijection_per_step():
             p = [orc.null_pick(i, n, 3, 2, step) for i in range(n)]
             assert sorted(p) == list(range(n))
             perms.append(p)
-        if n >= 17:
-            assert perms[0] != perms[1] and perms[1] != perms[2]
+        if n >= 5:
+            assert perms[0] != perms[1] and perms[1] != perms[2] and perms[0] != perms[2]
     # the first pick of a step is uniform over the vacancies (chi-square, 16 dof)
     n, trials = 17, 6800
     cnt = np.bincount([orc.null_pick(0, n, 9, 0, st) for st in range(trials)], minlength=n)
     chi2 = float(((cnt - trials / n) ** 2 / (trials / n)).sum())
     assert chi2 < 40.0, chi2  # p ~ 1e-3
+
+
+def test_pick_order_is_uniform_on_small_domains():
+    """"Selected randomly" (Sec. II.B): on a small domain every one of the n!
+    orders of the vacancies is equally likely from step to step (chi-square
+    over all orders; a four-round network fails this for n >= 4)."""
+    import oracle as orc
+    for n, per in ((3, 400), (4, 100), (5, 40)):
+        nf = math.factorial(n)
+        steps = per * nf
+        cnt = {}
+        for st in range(steps):
+            p = tuple(orc.null_pick(i, n, 5, 1, st) for i in range(n))
+            cnt[p] = cnt.get(p, 0) + 1
+        assert len(cnt) == nf
+        c = np.array(list(cnt.values()), float)
+        chi2 = float(((c - per) ** 2 / per).sum())
+        dof = nf - 1
+        assert chi2 < dof + 4.5 * math.sqrt(2 * dof), (n, chi2, dof)
 
 
 def test_lone_vacancy_is_never_null_and_hops_at_8k(orc):

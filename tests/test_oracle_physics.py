@@ -232,3 +232,117 @@ def test_mixed_and_plain_agree(orc):
     assert h0 > 10000
     assert abs(D0 - D1) <= 0.01 * D0
     assert abs(h0 - h1) <= 0.01 * h0
+
+
+# ------------------------------------------------------------------ field: D tensor and drift
+def _single_vacancy_chain(eps):
+    """Exact long-time drift and D tensor of one vacancy under a z field, in
+    units a = 1, k0 = 1, from the site-type Markov chain of the O sublattice
+    (written from the geometry, not from the oracle): a type-t site hops by
+    s_t e_t + s_u e_u (units a/2) to a type-u site, u != t, s = +-1, at rate
+    exp(eps dz).  D_axis = sigma^2/2 with the asymptotic variance of an
+    additive functional of a Markov chain, sigma^2 = sum_t pi_t sum_hops
+    r (d + g(u) - g(t))^2, g solving Q g = -(b - vbar) (b: drift of type t)."""
+    hops = {t: [] for t in range(3)}
+    for t in range(3):
+        for u in range(3):
+            if u != t:
+                for st in (-1, 1):
+                    for su in (-1, 1):
+                        d = np.zeros(3)
+                        d[t], d[u] = st, su
+                        hops[t].append((u, d, math.exp(eps * d[2])))
+    Q, b = np.zeros((3, 3)), np.zeros((3, 3))
+    for t in range(3):
+        for u, d, r in hops[t]:
+            Q[t, u] += r
+            Q[t, t] -= r
+            b[t] += r * d
+    pi = np.linalg.lstsq(np.vstack([Q.T, np.ones(3)]), np.r_[0.0, 0.0, 0.0, 1.0], rcond=None)[0]
+    vbar = pi @ b
+    D = np.zeros(3)
+    for ax in range(3):
+        g = np.linalg.lstsq(np.vstack([Q, pi]), np.r_[-(b[:, ax] - vbar[ax]), 0.0], rcond=None)[0]
+        s2 = sum(pi[t] * r * (d[ax] + g[u] - g[t]) ** 2 for t in range(3) for u, d, r in hops[t])
+        D[ax] = s2 / 2 * 0.25          # (a/2)^2 per (unit displacement)^2
+    return D, vbar * 0.5, pi
+
+
+def test_single_vacancy_chain_reduces_to_closed_forms():
+    """The exact chain reproduces the closed forms: D_xx = (1/3) a^2 k0 (1 +
+    cosh eps) and v_z = (8/3) a k0 sinh eps exactly, D_zz = (2/3) a^2 k0 cosh eps
+    to O(eps^2), D = (2/3) k a^2 at zero field, Einstein v = D qE/kT to O(eps^2)."""
+    for eps in (0.0, 0.0582, 0.3, 1.0):
+        D, v, pi = _single_vacancy_chain(eps)
+        assert np.allclose(pi, 1 / 3)
+        assert D[0] == pytest.approx((1 + math.cosh(eps)) / 3, rel=1e-12)
+        assert D[1] == pytest.approx((1 + math.cosh(eps)) / 3, rel=1e-12)
+        assert v[2] == pytest.approx(8 / 3 * math.sinh(eps), rel=1e-12, abs=1e-15)
+        assert abs(D[2] / (2 / 3 * math.cosh(eps)) - 1) < 0.15 * eps * eps + 1e-12
+        if eps:
+            # qE/kT = 4 eps / a
+            assert abs(v[2] / (D[2] * 4 * eps) - 1) < eps * eps
+
+
+def _field_walkers(orc, eps, seeds, windows, nv=4, cells=(12, 12, 12), T=800.0, Ea=0.6, a=3.905, q=2.0):
+    """Dilute vacancies under the field of strength eps = qEa/(4kT), one
+    fragment (exact scheme).  Returns pooled moments, per-seed moments, t, Ez."""
+    Ez = eps * 4 * KB * T / (q * a * 1e-10)
+    pooled, per = np.zeros(7, np.int64), []
+    t = None
+    for s in seeds:
+        L = orc.Lattice(cells, (1, 1, 1), nv, 0, seed=s)
+        L.set_rates(Ea, Ea, T, Ez=Ez, a_ang=a, q_O=q)
+        L.run(windows)
+        m = L.moments(2)
+        pooled += m
+        per.append(m)
+        t = windows * L.params()["tau"]
+    return pooled, np.array(per), t, Ez
+
+
+def test_field_D_tensor_and_drift(orc):
+    """Strong field (eps = 1): the drift-corrected D_z of Sec. III's tracked
+    trajectories against the exact chain value, D_xy against (1/3) a^2 k0 (1 +
+    cosh eps), v_z against (8/3) a k0 sinh eps, each within 3 sigma of the
+    spread over 384 independent lattices.  Without the drift correction D_z
+    would be several times too large."""
+    eps, T, Ea, a = 1.0, 800.0, 0.6, 3.905
+    k0 = k_of(Ea, T)
+    pooled, per, t, _ = _field_walkers(orc, eps, range(384), 700)
+    d = orc.diffusion_from_moments(pooled, t, a)
+    Dc, vc, _ = _single_vacancy_chain(eps)
+    am = a * 1e-10
+    D_exact = Dc * k0 * am * am
+    v_exact = vc[2] * k0 * am
+    h = 0.5 * am
+    mu = pooled[3] / pooled[0]
+    # per-lattice estimates about the pooled drift, for the spread
+    n = per[:, 0].astype(float)
+    varz = (per[:, 6] - 2 * mu * per[:, 3] + mu * mu * n) / n * h * h / (2 * t)
+    dxy = (per[:, 4] + per[:, 5]) / n * h * h / (4 * t)
+    vz = per[:, 3] / n * h / t
+    se = lambda x: x.std(ddof=1) / math.sqrt(len(x))  # noqa: E731
+    assert abs(d["D_z"] - D_exact[2]) < 3 * se(varz), (d["D_z"] / D_exact[2], se(varz) / D_exact[2])
+    assert abs(d["D_xy"] - D_exact[0]) < 3 * se(dxy), (d["D_xy"] / D_exact[0], se(dxy) / D_exact[0])
+    assert d["D_xy"] == pytest.approx(((1 + math.cosh(eps)) / 3) * k0 * am * am, rel=6 * se(dxy) / D_exact[0])
+    assert abs(d["v"][2] - v_exact) < 3 * se(vz), (d["v"][2] / v_exact, se(vz) / v_exact)
+    # the per-axis estimates of x and y carry no drift
+    assert abs(d["v"][0]) < 3 * se(per[:, 1] / n * h / t) + 1e-30
+    # the drift term is large here: <dz^2>/(2t) without it is far above D_z
+    assert d["msd"][2] / (2 * t) > 3 * d["D_z"]
+    # the zero-order form (2/3) a^2 k0 cosh eps is 6% low at eps = 1: the
+    # measurement resolves the exact value from it
+    assert D_exact[2] > 1.05 * (2 / 3) * math.cosh(eps) * k0 * am * am
+
+
+def test_einstein_relation(orc):
+    """Weak field (eps = 0.15): v_z = D_z qE/kT to O(eps^2) (Einstein), with the
+    drift-corrected D_z measured on the same trajectories."""
+    eps, T, a, q = 0.15, 800.0, 3.905, 2.0
+    pooled, per, t, Ez = _field_walkers(orc, eps, range(384), 700)
+    d = orc.diffusion_from_moments(pooled, t, a)
+    ratio = d["v"][2] / (d["D_z"] * q * Ez / (KB * T))
+    # relative spread of D_z over 1536 dilute vacancies (variance of a variance)
+    rel = math.sqrt(2.0 / pooled[0])
+    assert abs(ratio - 1) < 3 * rel + eps * eps / 3, (ratio, rel)

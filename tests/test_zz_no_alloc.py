@@ -51,3 +51,46 @@ def test_noalloc_moments_match_batch_reduction():
     with pytest.raises(fkmc.KmcError) as e:
         fkmc.kmc_vacancy_moments_noalloc(d_recs.data_ptr(), d_counts.data_ptr(), too_many, cap, stream)
     assert e.value.code == fkmc.FKMC_EINVAL
+
+
+def _numpy_moments(recs, counts, offsets, cap):
+    out = np.zeros((len(offsets) - 1, 7), np.int64)
+    for g in range(len(offsets) - 1):
+        for f in range(offsets[g], offsets[g + 1]):
+            d = recs[f * cap: f * cap + counts[f]]["d"].astype(np.int64)
+            out[g, 0] += len(d)
+            out[g, 1:4] += d.sum(0)
+            out[g, 4:7] += (d * d).sum(0)
+    return out
+
+
+@pytest.mark.parametrize("n_groups,empty_every", [(4096, 3), (37, 2)])
+def test_noalloc_at_the_group_limit_and_with_empty_groups(n_groups, empty_every):
+    """At FKMC_NOALLOC_MAX_GROUPS groups (the last offset and accumulator of
+    the static scratch in use) and with empty groups between non-empty ones
+    (equal offsets: the group search must give each record to the group that
+    owns its fragment), on two calls in a row, against numpy sums."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2004_09081_gb300 import fkmc
+    fkmc.load()
+    rng = np.random.default_rng(n_groups)
+    cap = 8
+    sizes = rng.integers(1, 4, n_groups)
+    sizes[::empty_every] = 0          # empty groups, including the first
+    sizes[-1] = max(sizes[-1], 1)     # the last group holds records
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    nfrag = int(offsets[-1])
+    stream = torch.cuda.current_stream().cuda_stream
+    for call in range(2):
+        counts = rng.integers(0, cap + 1, nfrag).astype(np.int32)
+        recs = np.zeros(nfrag * cap, REC)
+        recs["d"] = rng.integers(-50, 51, (nfrag * cap, 3))
+        recs["key"] = rng.integers(0, 2**40, nfrag * cap)
+        d_recs = torch.from_numpy(recs.view(np.uint8)).cuda()
+        d_counts = torch.from_numpy(counts).cuda()
+        torch.cuda.synchronize()
+        got = fkmc.kmc_vacancy_moments_noalloc(d_recs.data_ptr(), d_counts.data_ptr(), offsets, cap, stream)
+        assert np.array_equal(got, _numpy_moments(recs, counts, offsets, cap)), call
+        assert (got[sizes == 0] == 0).all()
