@@ -150,6 +150,7 @@ class ClockSampler:
 def make_batch(fk, wl, seed, precision, replicas=None, edge=None, tracer=None, site=True, **opts):
     reps = wl.replicas if replicas is None else [wl.replicas[i] for i in replicas]
     nf = reps[0].nfrag if (len(reps) == 1 and reps[0].nfrag) else None
+    opts.setdefault("n_tau", wl.n_tau)
     b = fk.Batch([(*r.cells, r.a) for r in reps], [(r.n_vac, r.n_H, r.n_Fe) for r in reps], seed,
                  edge=wl.edge if edge is None else edge, nfrag=nf, precision=precision,
                  tracer=wl.tracer if tracer is None else tracer, **opts)
@@ -199,12 +200,12 @@ def cpu_oracle_rate(wl, seed, windows, budget_s, replicas=None):
     while secs < budget_s:
         for r in order:
             rep = wl.replicas[r]
-            nf = rep.nfrag or tuple(_nfrag(c, wl.edge) for c in rep.cells)
+            nf = rep.nfrag or oracle.partition(rep.cells, wl.edge)
             L = oracle.Lattice(rep.cells, nf, rep.n_vac, rep.n_H, seed=seed, replica=r, n_Fe=rep.n_Fe)
             if wl.site:
                 L.set_site_energy(vv=wl.site["vv"], fe=wl.site["fe"])
             L.set_rates(rep.Ea_O, rep.Ea_H, rep.T, Ez=rep.field_z, a_ang=rep.a, cap_v=cap,
-                        precision=wl.precision)
+                        n_tau=wl.n_tau, precision=wl.precision)
             if "grains" in wl.notes:
                 L.set_grains(*wl.notes["grains"])
             refresh = None
@@ -236,27 +237,22 @@ def cpu_oracle_rate(wl, seed, windows, budget_s, replicas=None):
 
 def oracle_jobs(wl, seed):
     """Every replica of the workload as a job for the parallel oracle timing."""
+    import oracle
     from oracle import timing
     cap = _auto_cap(wl)
-    return [timing.replica_job(r, rep.cells, rep.nfrag or tuple(_nfrag(c, wl.edge) for c in rep.cells), rep.n_vac,
+    return [timing.replica_job(r, rep.cells, rep.nfrag or oracle.partition(rep.cells, wl.edge), rep.n_vac,
                                rep.n_H, rep.T, rep.Ea_O, rep.Ea_H, rep.field_z, rep.a, cap, wl.precision, seed,
-                               rep.n_Fe, wl.site or None)
+                               rep.n_Fe, wl.site or None, wl.n_tau)
             for r, rep in enumerate(wl.replicas)]
 
 
-def _nfrag(L, edge):
-    nf = 2 * int(math.floor(L / (2.0 * edge) + 0.5))
-    if nf < 2:
-        nf = 2 if L >= 4 else 1
-    while nf > 1 and L // nf < 2:
-        nf -= 2
-    return max(nf, 1)
-
-
 def _auto_cap(wl):
+    """The library's default vacancy slots per fragment (kmc_opts.cap_v = 0)
+    for the oracle legs, from the oracle's own partition."""
+    import oracle
     worst = 0.0
     for r in wl.replicas:
-        nf = r.nfrag or tuple(_nfrag(c, wl.edge) for c in r.cells)
+        nf = r.nfrag or oracle.partition(r.cells, wl.edge)
         worst = max(worst, r.n_vac / (nf[0] * nf[1] * nf[2]))
     cap = int(math.ceil(worst + 10.0 * math.sqrt(worst + 1.0) + 8.0))
     cap = ((cap + 7) // 8) * 8
@@ -315,7 +311,7 @@ def run_reference(args):
     from oracle import timing
     wl = workloads.batched_batio3(args.seed)
     nrep = len(wl.replicas)
-    args.windows = args.windows or 64
+    args.windows = args.windows or wl.windows
     per_step_budget = 8.0
     times, hops_all, reps_done = [], 0, 0
     jobs = oracle_jobs(wl, args.seed)
@@ -338,7 +334,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+u64",
         "data": "synthetic",
         "config": {"workload": wl.name, "replicas": nrep, "windows_per_step": args.windows,
-                   "precision": "mixed"},
+                   "precision": "mixed", "edge": wl.edge, "n_tau": wl.n_tau},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{reps_done} replica runs of {args.windows} windows each over "
                                    f"{args.steps} steps, one serial C oracle per process on {cores} "
@@ -424,7 +420,7 @@ def main():
               "umgrains": workloads.um_grains, "elec": workloads.elec_batio3}
     wl = makers[args.workload](seed)
     nrep = len(wl.replicas)
-    default_windows = {"batched": 64, "sweep": 64, "bulk": 16, "um": 2, "fe": 32, "null": 100, "htrend": 20000,
+    default_windows = {"batched": 1024, "sweep": 64, "bulk": 16, "um": 2, "fe": 32, "null": 100, "htrend": 20000,
                        "umgrains": 2, "elec": 32}
     null = args.workload == "null"
     if null or args.workload in ("htrend", "elec"):
@@ -434,17 +430,30 @@ def main():
     reps = wl.replicas
     precision = wl.precision
 
-    # K7: pick the fragment edge (batched workload; single lattices keep their stated partition)
-    edge, tuned = wl.edge, None
+    # K7: fragment edge, window length and launch options, subject to the
+    # windowing-accuracy bound (batched workload; single lattices keep their
+    # stated partition)
+    tuned, deficit = None, None
     if args.workload == "batched" and not args.no_autotune:
         best, res = autotune.autotune([(*r.cells, r.a) for r in reps], [(r.n_vac, r.n_H) for r in reps], seed,
                                       [r.Ea_O for r in reps], [r.Ea_H for r in reps], [r.T for r in reps],
                                       precision=precision)
-        edge = best["edge"]
+        wl.edge, wl.n_tau = best["edge"], best["n_tau"]
         tuned_opts = {"schedule": best["schedule"], "cluster_top": best["cluster_top"]}
-        tuned = [dict(c, hops_per_s=h, cap_v=cap) for c, h, cap in res]
+        tuned = [dict(r["candidate"], deficit=r["deficit"]["vacancies_only"]["deficit"], at_edge=r["at_edge"],
+                      accepted=r["accepted"], hops_per_s=r["hops_per_s"]) for r in res]
     else:
-        tuned_opts = {}
+        tuned_opts = dict(wl.notes.get("launch_opts", {}))
+    if args.workload == "batched":
+        table = autotune.deficit_table()
+        worst, e_min, est = autotune.batch_deficit(table, [r.cells for r in reps], wl.edge, wl.n_tau)
+        deficit = {"at_fragment_edge": e_min, "accepted": autotune.accepted(est, 0.01),
+                   "by_composition": {k: {"deficit": v[0], "se": v[1]} for k, v in est.items()},
+                   "bound": 0.01, "what": "hop-rate deficit of the windowed scheme against the serial BKL "
+                                          "(Sec. II.A) at the shortest fragment edge of the batch; oracle table "
+                                          "paper_2004_09081_gb300/window_deficit.json (se from the seed scatter; "
+                                          "a row is binding where deficit > 2 se)"}
+    edge = wl.edge
 
     b = make_batch(fkmc, wl, seed, precision, edge=edge, **tuned_opts)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -534,20 +543,30 @@ def main():
                                      "bytes_per_hop": roofline["traffic"] / max(hops / units, 1e-9)}
     cnt = load_counters(tag) if all_resident else None
     if cnt and cnt.get("smem_wavefronts_per_launch") and clk.get("sm_mhz"):
-        # the replica-resident kernel works out of shared memory: its shared-memory
-        # wavefronts and warp instructions (ncu, per window) over the live launch time,
-        # against one wavefront and four warp instructions per SM per cycle
+        # the replica-resident kernel works out of shared memory and is bound by
+        # its dependent instruction chains: its warp instructions and shared-memory
+        # wavefronts (ncu, per window) over the live launch time, against four warp
+        # instructions and one wavefront per SM per cycle at the sampled SM clock;
+        # the HBM figures stay beside them
         nsm = torch.cuda.get_device_properties(dev).multi_processor_count
         hz = clk["sm_mhz"] * 1e6
         per_w = W / cnt["counters_windows"]
         wf = cnt["smem_wavefronts_per_launch"] * per_w
         wi = cnt["warp_inst_per_launch"] * per_w
-        roofline["smem"] = {"frac": wf / avg_launch_s / (nsm * hz), "wavefronts_per_launch": wf,
-                            "peak_wavefronts_per_s": nsm * hz}
-        roofline["issue"] = {"frac": wi / avg_launch_s / (4 * nsm * hz), "warp_inst_per_launch": wi,
-                             "peak_warp_inst_per_s": 4 * nsm * hz}
-        roofline["counters_note"] = ("smem and issue: ncu counts per window (profiles/traffic.json) x windows "
-                                     "per launch / CUDA-event launch time; peaks at the measured SM clock")
+        hbm = {k: roofline[k] for k in ("achieved", "peak", "unit", "frac", "peak_kind", "bytes_per_hop")}
+        if "measured_dram" in roofline:
+            hbm["measured_dram"] = roofline.pop("measured_dram")
+        issue_peak = 4 * nsm * hz / 1e9
+        roofline.update({
+            "bound": "alu", "achieved": wi / avg_launch_s / 1e9, "peak": issue_peak, "unit": "Gwarp-inst/s",
+            "frac": wi / avg_launch_s / 1e9 / issue_peak,
+            "peak_kind": "instruction issue: 4 warp instructions per SM per cycle x %d SMs x sampled %.0f MHz" % (
+                nsm, clk["sm_mhz"]),
+            "warp_inst_per_launch": wi, "hbm": hbm,
+            "smem": {"frac": wf / avg_launch_s / (nsm * hz), "wavefronts_per_launch": wf,
+                     "peak_wavefronts_per_s": nsm * hz},
+            "counters_note": ("warp instructions and shared-memory wavefronts: ncu counts per window "
+                              "(profiles/traffic.json) x windows per launch / CUDA-event launch time")})
 
     extra = {}
     if rank == 0 and args.profile_run:
@@ -653,20 +672,28 @@ def main():
                 "note": "D_V (m^2/s) per temperature; the paper reports that the dopant term lowers D_V "
                         "strongly and the V-V term raises it again",
             }
+        W_cmp = min(W, 64)  # the comparison legs: rates and D do not need the timed step's length
         if not args.no_plain and not wl.site:
             # accuracy: mixed vs plain FP64 from the same initial state, same draws
-            Wacc = 4 * W
+            Wacc = 4 * W_cmp
             bm = make_batch(fkmc, wl, seed, fkmc.FKMC_MIXED, edge=edge)
             bp = make_batch(fkmc, wl, seed, fkmc.FKMC_PLAIN, edge=edge)
             hm, hp = bm.run(Wacc).hops, bp.run(Wacc).hops
             mm, mp = bm.moments_all(), bp.moments_all()
-            rel = []
+            rel, zs = [], []
             for r in range(nrep):
                 tr = bp.info(r).window * bp.info(r).tau
                 Dm = D_from_moments(mm[r], tr, reps[r].a)
                 Dp = D_from_moments(mp[r], tr, reps[r].a)
                 if Dp > 0:
                     rel.append(abs(Dm - Dp) / Dp)
+                    # sigma_D: the statistical error of D from the replica's vacancies
+                    # (squared displacements of the plain run's records)
+                    d2 = (bp.records(r)[:, 2:5].astype(np.float64) ** 2).sum(1)
+                    h = 0.5 * reps[r].a * 1e-10
+                    sd = d2.std(ddof=1) / math.sqrt(len(d2)) * h * h / (6 * tr) if len(d2) > 1 else 0.0
+                    if sd > 0:
+                        zs.append(abs(Dm - Dp) / sd)
             agg_m = float(mm[:, 4:7].sum()) / max(float(mm[:, 0].sum()), 1.0)
             agg_p = float(mp[:, 4:7].sum()) / max(float(mp[:, 0].sum()), 1.0)
             same = sum(int(np.array_equal(mm[r], mp[r])) for r in range(nrep))
@@ -680,7 +707,7 @@ def main():
                 for r in range(nrep):
                     # a batch of one is keyed as replica 0: its own stream, throughput comparison only
                     b1 = make_batch(fkmc, wl, seed, fkmc.FKMC_PLAIN, replicas=[r], edge=edge)
-                    s1 = b1.run(W)
+                    s1 = b1.run(W_cmp)
                     p_hops += s1.hops
                     p_ms += s1.gpu_ms
                     b1.close()
@@ -689,7 +716,7 @@ def main():
                 plain["mixed_over_plain_one_at_a_time"] = value / plain["one_at_a_time"]["value"]
             bpb = make_batch(fkmc, wl, seed, fkmc.FKMC_PLAIN, edge=edge)
             bpb.run(2)
-            spb = bpb.run(W)
+            spb = bpb.run(W_cmp)
             bpb.close()
             plain["batched"] = {"value": spb.hops / (spb.gpu_ms / 1e3), "unit": UNIT}
             plain["mixed_over_plain_batched"] = value / plain["batched"]["value"] if spb.hops else None
@@ -699,6 +726,12 @@ def main():
                 "aggregate_msd_rel_err": abs(agg_m - agg_p) / agg_p if agg_p else None,
                 "per_replica_rel_err_median": float(np.median(rel)) if rel else None,
                 "per_replica_rel_err_max": float(np.max(rel)) if rel else None,
+                "per_replica_err_over_sigma_D_max": float(np.max(zs)) if zs else None,
+                "per_replica_err_over_sigma_D_median": float(np.median(zs)) if zs else None,
+                "replicas_beyond_2_sigma_D": int(sum(z > 2.0 for z in zs)),
+                "sigma_D_note": "sigma_D = std(|d|^2)/sqrt(N) h^2/(6t) over each replica's vacancies (plain "
+                                "run): the two forms draw the same numbers and part only at a rare "
+                                "rounding-induced divergence, after which they are independent samples",
                 "replicas_bit_identical": same, "replicas": nrep,
             }
         if not args.no_cpu:
@@ -740,7 +773,8 @@ def main():
             "config": {"workload": wl.name, "replicas": nrep, "windows_per_step": W,
                        "precision": ("mixed (fp32 rates -> u64 fixed point, fp32 variate, fp64 clock)"
                                      if precision else "plain fp64"),
-                       "n_tau": 1.0, "edge": edge, "launch_opts": tuned_opts, "autotune": tuned,
+                       "n_tau": wl.n_tau, "edge": edge, "launch_opts": tuned_opts, "autotune": tuned,
+                       "window_deficit": deficit,
                        "l2": "flushed between timed steps (256 MiB write)",
                        "schedule": ("null-event steps (Sec. II.B), one pick per vacancy, %d steps per "
                                     "benchmark step" % W if null else

@@ -438,6 +438,14 @@ int32_t kmc_num_replicas(const kmc_batch* b);
 int kmc_rate_table(const kmc_barrier_table* t, double T_K, double field_z_Vpm, double a_angstrom,
                    int32_t cap_v, double k64[6], float k32[6], uint64_t q[6], int32_t* F);
 
+/* Host-only: fragments along one dimension of L cells for a target fragment
+ * edge (what kmc_create_batch uses where kmc_opts.nfrag[d] == 0).  The paper
+ * cuts a lattice into fragments without fixing their number; the reading: the
+ * even count nearest L / edge (half-way cases up), but at least 2, reduced
+ * while a fragment would be shorter than 2 cells; 1 for L < 4.  Edges are then
+ * floor(L / n) or floor(L / n) + 1.  Returns 0 for L < 1 or edge < 1. */
+int32_t kmc_partition_count(int32_t L, int32_t edge);
+
 /* Host-only: the 8 neighbours of each site type as rows {t2, dcx, dcy, dcz,
  * dx, dy, dz} (24 rows of int32): neighbour cell offset and displacement in
  * units of a/2, ascending in (dx, dy, dz). */

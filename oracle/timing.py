@@ -14,12 +14,13 @@ import os
 import time
 
 
-def replica_job(r, cells, nf, n_vac, n_H, T, Ea_O, Ea_H, Ez, a, cap, precision, seed, n_Fe=0, site=None):
+def replica_job(r, cells, nf, n_vac, n_H, T, Ea_O, Ea_H, Ez, a, cap, precision, seed, n_Fe=0, site=None,
+                n_tau=1.0):
     """One replica's parameters as a plain dict (what a worker needs to build it)."""
     return {"r": int(r), "cells": tuple(int(c) for c in cells), "nf": tuple(int(f) for f in nf),
             "n_vac": int(n_vac), "n_H": int(n_H), "T": float(T), "Ea_O": float(Ea_O), "Ea_H": float(Ea_H),
             "Ez": float(Ez), "a": float(a), "cap": int(cap), "precision": int(precision), "seed": int(seed),
-            "n_Fe": int(n_Fe), "site": site}
+            "n_Fe": int(n_Fe), "site": site, "n_tau": float(n_tau)}
 
 
 def run_jobs(jobs, windows, budget_s):
@@ -36,7 +37,7 @@ def run_jobs(jobs, windows, budget_s):
         if j["site"]:
             L.set_site_energy(vv=j["site"]["vv"], fe=j["site"]["fe"])
         L.set_rates(j["Ea_O"], j["Ea_H"], j["T"], Ez=j["Ez"], a_ang=j["a"], cap_v=j["cap"],
-                    precision=j["precision"])
+                    n_tau=j.get("n_tau", 1.0), precision=j["precision"])
         t0 = time.perf_counter()
         L.run(windows)
         secs += time.perf_counter() - t0

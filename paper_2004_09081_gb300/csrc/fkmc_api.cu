@@ -704,6 +704,12 @@ void kmc_default_opts(kmc_opts* o)
     o->cluster_top = -1;
 }
 
+int32_t kmc_partition_count(int32_t L, int32_t edge)
+{
+    if (L < 1 || edge < 1) return 0;
+    return partition_count(L, edge);
+}
+
 void kmc_neighbour_table(int32_t out[168])
 {
     NbEntry tab[3][8];

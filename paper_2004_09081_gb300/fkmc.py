@@ -106,6 +106,7 @@ _SIGNATURES = {
     "kmc_num_replicas": (_I32, [_P]),
     "kmc_rate_table": (C.c_int, [_P, _D, _D, _D, _I32, _P, _P, _P, _P]),
     "kmc_neighbour_table": (None, [_P]),
+    "kmc_partition_count": (_I32, [_I32, _I32]),
     "kmc_vacancy_moments_noalloc": (C.c_int, [_P, _P, _P, _I32, _I32, _P, _P]),
     "kmc_set_site_energy": (C.c_int, [_P, _P]),
     "kmc_read_dopants": (C.c_int, [_P, _I32, _P, _SZ]),
@@ -276,6 +277,10 @@ def kmc_rate_table(table: kmc_barrier_table, T_K: float, field_z: float, a_ang: 
     _check(load().kmc_rate_table(C.byref(table), T_K, field_z, a_ang, cap_v, _ptr(k64), _ptr(k32),
                                  _ptr(q), C.byref(F)))
     return k64, k32, q, F.value
+
+
+def kmc_partition_count(L: int, edge: int) -> int:
+    return int(load().kmc_partition_count(int(L), int(edge)))
 
 
 def kmc_neighbour_table() -> np.ndarray:

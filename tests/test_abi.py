@@ -151,3 +151,12 @@ def test_create_batch_rejects_bad_wait_test_option(lib):
     with pytest.raises(lib.KmcError) as e:
         lib.kmc_create_batch([lib.kmc_cells(8, 8, 8, 3.905)], [lib.kmc_composition(5, 0, 0)], 0, o)
     assert e.value.code == lib.FKMC_EINVAL
+
+
+def test_partition_matches_the_oracles_reading(lib, orc):
+    """The library's fragment count per dimension (a closed form) equals the
+    oracle's (a search over even counts) on every L <= 300 and edge 1..12."""
+    for L in range(1, 301):
+        for e in range(1, 13):
+            assert lib.kmc_partition_count(L, e) == orc.partition((L,), e)[0], (L, e)
+    assert lib.kmc_partition_count(0, 4) == 0 and lib.kmc_partition_count(8, 0) == 0

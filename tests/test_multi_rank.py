@@ -66,7 +66,7 @@ def test_parallel_oracle_timing_matches_serial_runs():
     for j in jobs:
         L = oracle.Lattice(j["cells"], j["nf"], j["n_vac"], j["n_H"], seed=0, replica=j["r"])
         L.set_rates(j["Ea_O"], j["Ea_H"], j["T"], Ez=j["Ez"], a_ang=j["a"], cap_v=j["cap"],
-                    precision=j["precision"])
+                    n_tau=j["n_tau"], precision=j["precision"])
         L.run(2)
         want += L.counters()["hops"]
     assert hops == want
