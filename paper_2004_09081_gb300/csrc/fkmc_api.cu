@@ -138,6 +138,10 @@ struct kmc_batch {
     struct RClass { int start, count; size_t smem; int threads; int cluster; cudaStream_t st; cudaEvent_t done; };
     std::vector<RClass> rclass;
     cudaEvent_t fork = nullptr;
+    cudaGraphExec_t res_exec = nullptr;  // one call's class launches (fork, launches, join), captured
+    uint64_t res_exec_windows = 0;
+    cudaStream_t res_st = nullptr;       // the graph's stream, beside the colour-phase launches
+    cudaEvent_t res_fork = nullptr, res_join = nullptr;
     cudaStream_t side_st = nullptr;       // the small-fragment run pass, beside the general one
     cudaEvent_t side_fork = nullptr, side_join = nullptr;
     bool any_global = true;
@@ -261,6 +265,13 @@ struct kmc_batch {
         }
         rclass.clear();
         if (window_exec) cudaGraphExecDestroy(window_exec);
+        if (res_exec) cudaGraphExecDestroy(res_exec);
+        res_exec = nullptr;
+        if (res_st) cudaStreamDestroy(res_st);
+        if (res_fork) cudaEventDestroy(res_fork);
+        if (res_join) cudaEventDestroy(res_join);
+        res_st = nullptr;
+        res_fork = res_join = nullptr;
         if (null_exec) cudaGraphExecDestroy(null_exec);
         null_exec = nullptr;
         for (auto& g : elec_graphs) cudaGraphExecDestroy(g.exec);
@@ -336,6 +347,8 @@ bool valid_replica(const kmc_batch* b, int32_t r) { return b && r >= 0 && r < b-
 // into shared-memory size classes (one launch per class, on forked streams).
 int plan_residency(kmc_batch* b)
 {
+    if (b->res_exec) cudaGraphExecDestroy(b->res_exec);  // it holds the old classes' launches
+    b->res_exec = nullptr;
     for (auto& c : b->rclass) {
         if (c.st) cudaStreamDestroy(c.st);
         if (c.done) cudaEventDestroy(c.done);
@@ -975,18 +988,47 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
     std::vector<unsigned long long> before = b->stats_host;
     CK(cudaEventRecord(b->ev0, b->st), "event record");
     if (!b->rclass.empty() && windows > 0) {
-        // replica-resident classes on forked streams, joined back before ev1
-        CK(cudaEventRecord(b->fork, b->st), "event record");
-        // largest classes first: their CTAs run longest and should take SMs first
-        for (auto it = b->rclass.rbegin(); it != b->rclass.rend(); ++it) {
-            auto& c = *it;
-            CK(cudaStreamWaitEvent(c.st, b->fork, 0), "stream wait");
-            CK(launch_resident(b->d_desc, b->d_reps + c.start, c.count, b->d_nvac, c.smem, c.threads, c.cluster,
-                               windows, b->occ, b->recs, b->counts, b->tracer, b->stats, b->status, b->cap, b->nbt,
-                               (uint32_t)b->opts.test_stuck_wait_us, c.st),
-               "resident kernel");
-            CK(cudaEventRecord(c.done, c.st), "event record");
+        // replica-resident classes on forked streams, joined back: captured once
+        // per window count into a graph (fork, one launch per class, join) and
+        // replayed on the caller's stream
+        if (!b->res_exec || b->res_exec_windows != windows) {
+            if (b->res_exec) cudaGraphExecDestroy(b->res_exec);
+            b->res_exec = nullptr;
+            if (!b->cap_st) CK(cudaStreamCreateWithFlags(&b->cap_st, cudaStreamNonBlocking), "stream");
+            cudaGraph_t graph = nullptr;
+            CK(cudaStreamBeginCapture(b->cap_st, cudaStreamCaptureModeThreadLocal), "graph capture");
+            cudaError_t le = cudaEventRecord(b->fork, b->cap_st);
+            // largest classes first: their CTAs run longest and should take SMs first
+            for (auto it = b->rclass.rbegin(); it != b->rclass.rend() && le == cudaSuccess; ++it) {
+                auto& c = *it;
+                le = cudaStreamWaitEvent(c.st, b->fork, 0);
+                if (le == cudaSuccess)
+                    le = launch_resident(b->d_desc, b->d_reps + c.start, c.count, b->d_nvac, c.smem, c.threads,
+                                         c.cluster, windows, b->occ, b->recs, b->counts, b->tracer, b->stats,
+                                         b->status, b->cap, b->nbt, (uint32_t)b->opts.test_stuck_wait_us, c.st);
+                if (le == cudaSuccess) le = cudaEventRecord(c.done, c.st);
+                if (le == cudaSuccess) le = cudaStreamWaitEvent(b->cap_st, c.done, 0);
+            }
+            cudaError_t ce = cudaStreamEndCapture(b->cap_st, &graph);
+            if (le != cudaSuccess) return cuda_fail(le, "resident capture");
+            if (ce != cudaSuccess) return cuda_fail(ce, "resident capture");
+            cudaError_t ie = cudaGraphInstantiate(&b->res_exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) {
+                b->res_exec = nullptr;
+                return cuda_fail(ie, "graph instantiate");
+            }
+            b->res_exec_windows = windows;
         }
+        if (!b->res_st) {
+            CK(cudaStreamCreateWithFlags(&b->res_st, cudaStreamNonBlocking), "stream");
+            CK(cudaEventCreateWithFlags(&b->res_fork, cudaEventDisableTiming), "event");
+            CK(cudaEventCreateWithFlags(&b->res_join, cudaEventDisableTiming), "event");
+        }
+        CK(cudaEventRecord(b->res_fork, b->st), "event record");
+        CK(cudaStreamWaitEvent(b->res_st, b->res_fork, 0), "stream wait");
+        CK(cudaGraphLaunch(b->res_exec, b->res_st), "graph launch");
+        CK(cudaEventRecord(b->res_join, b->res_st), "event record");
     }
     uint64_t extra_launches = 0;
     if (site_path(b) && !b->field_valid) {
@@ -1041,8 +1083,7 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
             ++b->elec_age;
         }
     }
-    if (!b->rclass.empty() && windows > 0)
-        for (auto& c : b->rclass) CK(cudaStreamWaitEvent(b->st, c.done, 0), "stream wait");
+    if (!b->rclass.empty() && windows > 0) CK(cudaStreamWaitEvent(b->st, b->res_join, 0), "stream wait");
     CK(cudaEventRecord(b->ev1, b->st), "event record");
     for (int r = 0; r < b->n; ++r) b->desc[r].window += windows;
     int rc = upload_desc(b);

@@ -265,40 +265,35 @@ struct NbSite {
     int t2, jx, jy, jz;
 };
 
-__device__ __forceinline__ NbSite nb_site(const Shared& sh, int t, int x, int y, int z, int q)
+// lattice sizes, row words, fragment counts, clock scale and window: loaded
+// into registers once (shared-memory reads would be repeated after every
+// atomic and warp barrier)
+struct Geo {
+    int L0, L1, L2, RW, nf0, nf1, F;
+    double theta;
+};
+
+__device__ __forceinline__ NbSite nb_site(const Shared& sh, const Geo& g, int t, int x, int y, int z, int q)
 {
     const NbEntry nb = sh.nb[t][q];
     NbSite s;
     s.t2 = nb.t2;
-    s.jx = wrapc(x + nb.dc[0], sh.D.L[0]);
-    s.jy = wrapc(y + nb.dc[1], sh.D.L[1]);
-    s.jz = wrapc(z + nb.dc[2], sh.D.L[2]);
+    s.jx = wrapc(x + nb.dc[0], g.L0);
+    s.jy = wrapc(y + nb.dc[1], g.L1);
+    s.jz = wrapc(z + nb.dc[2], g.L2);
     return s;
 }
 
-__device__ __forceinline__ int site_code(const Shared& sh, const uint32_t* occ, int t, int x, int y, int z)
+__device__ __forceinline__ int site_code(const Geo& g, const uint32_t* occ, int t, int x, int y, int z)
 {
-    const RepDesc& D = sh.D;
-    const uint32_t w = occ[((t * D.L[2] + z) * D.L[1] + y) * D.row_words + (x >> 4)];
+    const uint32_t w = occ[((t * g.L2 + z) * g.L1 + y) * g.RW + (x >> 4)];
     return (int)((w >> occ_shift(x)) & 3u);
 }
 
-// fixed-point rate of the exchange of the vacancy at key k with neighbour q
-__device__ __forceinline__ unsigned long long event_rate(const Shared& sh, const uint32_t* occ, uint32_t k,
-                                                         int q, int* code_out)
-{
-    int t, x, y, z;
-    split32(k, t, x, y, z);
-    const NbSite s = nb_site(sh, t, x, y, z, q);
-    const int code = site_code(sh, occ, s.t2, s.jx, s.jy, s.jz);
-    if (code_out) *code_out = code;
-    return code == SP_V ? 0ull : (unsigned long long)sh.D.q[code * 3 + sh.nb[t][q].d[2] + 1];
-}
-
 // owner fragment of cell (x,y,z), from the per-dimension tables
-__device__ __forceinline__ int owner_of(const RepDesc& D, const uint16_t* fo, int x, int y, int z)
+__device__ __forceinline__ int owner_of(const Geo& g, const uint16_t* fo, int x, int y, int z)
 {
-    return (fo[D.L[0] + D.L[1] + z] * D.nf[1] + fo[D.L[0] + y]) * D.nf[0] + fo[x];
+    return (fo[g.L0 + g.L1 + z] * g.nf1 + fo[g.L0 + y]) * g.nf0 + fo[x];
 }
 
 // exact product 2^F * d for a positive normal double (exponent add)
@@ -443,6 +438,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
     if (sh.abort) return;
 
     const uint64_t hop_k1 = key_word(D.replica, PURPOSE_HOP);
+    const Geo geo{D.L[0], D.L[1], D.L[2], D.row_words, D.nf[0], D.nf[1], D.F, D.theta_tau};
     const int lane = tid & 31;
     const int warp = tid >> 5;
     const unsigned FULL = 0xffffffffu;
@@ -487,7 +483,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                 bool active = dirty;
                 if (!active) {
                     const float ratio = __fdiv_rn(E0, __ull2float_rn(tot));
-                    active = !(__dadd_rn(0.0, scale_pow2((double)ratio, D.F)) > D.theta_tau);
+                    active = !(__dadd_rn(0.0, scale_pow2((double)ratio, geo.F)) > geo.theta);
                 }
                 if (active) {
                     const int a = atomicAdd(&sh.nact, 1);
@@ -522,16 +518,30 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                             atomicOr(status, STATUS_OVERFLOW);
                             break;
                         }
-                        const uint32_t k = S.key[v];
-                        int m = n++;
-                        while (m > 0 && S.key[wslot[m - 1]] > k) {
+                        wslot[n++] = (int16_t)v;
+                    }
+                }
+                n = __shfl_sync(FULL, n, 0);
+                __syncwarp();
+                if (n <= 32) {  // rank by site (sites are distinct)
+                    const int vk = lane < n ? wslot[lane] : -1;
+                    const uint32_t kk = lane < n ? S.key[vk] : 0xffffffffu;
+                    int rnk = 0;
+                    for (int q = 0; q < n; ++q) rnk += __shfl_sync(FULL, kk, q) < kk ? 1 : 0;
+                    __syncwarp();
+                    if (lane < n) wslot[rnk] = (int16_t)vk;
+                } else if (lane == 0) {
+                    for (int k = 1; k < n; ++k) {
+                        const int v = wslot[k];
+                        const uint32_t kv = S.key[v];
+                        int m = k;
+                        while (m > 0 && S.key[wslot[m - 1]] > kv) {
                             wslot[m] = wslot[m - 1];
                             --m;
                         }
                         wslot[m] = (int16_t)v;
                     }
                 }
-                n = __shfl_sync(FULL, n, 0);
                 __syncwarp();
                 const int nch = (n + 3) >> 2;
                 auto compute_types = [&]() {
@@ -539,10 +549,13 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                         const int e = c * 32 + lane, m = e >> 3;
                         int ty = -1;
                         if (m < n && wslot[m] >= 0) {
-                            int code;
                             const uint32_t k = S.key[wslot[m]];
-                            event_rate(sh, S.occ, k, e & 7, &code);
-                            ty = code == SP_V ? -1 : code * 3 + sh.nb[k >> 30][e & 7].d[2] + 1;
+                            int t, x, y, z;
+                            split32(k, t, x, y, z);
+                            const NbEntry nbe = sh.nb[t][e & 7];
+                            const int code = site_code(geo, S.occ, nbe.t2, wrapc(x + nbe.dc[0], geo.L0),
+                                                         wrapc(y + nbe.dc[1], geo.L1), wrapc(z + nbe.dc[2], geo.L2));
+                            ty = code == SP_V ? -1 : code * 3 + nbe.d[2] + 1;
                         }
                         wtype[e] = (int8_t)ty;
                     }
@@ -618,8 +631,8 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                         E = __shfl_sync(FULL, odd ? E_odd : E_even, src);
                     }
                     const float ratio = __fdiv_rn(E, __ull2float_rn(tot));
-                    const double nclock = __dadd_rn(clock, scale_pow2((double)ratio, D.F));
-                    if (nclock > D.theta_tau) break;
+                    const double nclock = __dadd_rn(clock, scale_pow2((double)ratio, geo.F));
+                    if (nclock > geo.theta) break;
                     const unsigned long long target = __umul64hi(xs, tot);
                     // first event whose running sum exceeds the target
                     int e_sel = -1;
@@ -659,13 +672,13 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                     int t, x, y, z;
                     split32(S.key[v], t, x, y, z);
                     const NbEntry nb = sh.nb[t][qd];
-                    const NbSite j = nb_site(sh, t, x, y, z, qd);
+                    const NbSite j = nb_site(sh, geo, t, x, y, z, qd);
                     const bool owned = j.jx >= lo0 && j.jx < hi0 && j.jy >= lo1 && j.jy < hi1 && j.jz >= lo2 &&
                                        j.jz < hi2;
                     if (lane == 0) {  // apply the exchange
                         const uint32_t ion = (uint32_t)(wtype[e_sel] / 3);
-                        uint32_t* ws = S.occ + ((t * D.L[2] + z) * D.L[1] + y) * D.row_words + (x >> 4);
-                        uint32_t* wj = S.occ + ((j.t2 * D.L[2] + j.jz) * D.L[1] + j.jy) * D.row_words + (j.jx >> 4);
+                        uint32_t* ws = S.occ + ((t * geo.L2 + z) * geo.L1 + y) * geo.RW + (x >> 4);
+                        uint32_t* wj = S.occ + ((j.t2 * geo.L2 + j.jz) * geo.L1 + j.jy) * geo.RW + (j.jx >> 4);
                         const uint32_t ms = ((uint32_t)SP_V ^ ion) << occ_shift(x);
                         const uint32_t mj = (ion ^ (uint32_t)SP_V) << occ_shift(j.jx);
                         atomicXor(ws, ms);
@@ -696,7 +709,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                             // phase, so that list only receives pushes; links are read after
                             // the phase barrier)
                             wslot[m] = -1;
-                            const int g2 = owner_of(D, S.frag_of_c, j.jx, j.jy, j.jz);
+                            const int g2 = owner_of(geo, S.frag_of_c, j.jx, j.jy, j.jz);
                             S.next[v] = (int16_t)atomicExch(S.head + g2, v);
                             if constexpr (CL > 1)
                                 st_peer16(peer_addr(S.next + v, peer),
@@ -710,9 +723,9 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                     if (lane < 16) {
                         const int bt = lane < 8 ? t : j.t2;
                         const int bx = lane < 8 ? x : j.jx, by = lane < 8 ? y : j.jy, bz = lane < 8 ? z : j.jz;
-                        const NbSite c = nb_site(sh, bt, bx, by, bz, lane & 7);
-                        if (site_code(sh, S.occ, c.t2, c.jx, c.jy, c.jz) == SP_V) {
-                            const int g = owner_of(D, S.frag_of_c, c.jx, c.jy, c.jz);
+                        const NbSite c = nb_site(sh, geo, bt, bx, by, bz, lane & 7);
+                        if (site_code(geo, S.occ, c.t2, c.jx, c.jy, c.jz) == SP_V) {
+                            const int g = owner_of(geo, S.frag_of_c, c.jx, c.jy, c.jz);
                             if (g != fid) {
                                 S.dirty[g] = 1;
                                 if constexpr (CL > 1) st_peer8(peer_addr(S.dirty + g, peer), 1);
