@@ -36,7 +36,8 @@ class Workload:
     name: str
     replicas: list
     edge: int = 4
-    n_tau: float = 1.0  # window length tau = n_tau / (8 k_fast)
+    n_tau: float = 1.0  # window length tau = n_tau / (8 k_fast); the workloads use 0.5, where the
+                        # windowing deficit against the serial BKL is within 1% (window_deficit.json)
     precision: int = 0
     tracer: bool = False
     windows: int = 1
@@ -50,9 +51,9 @@ def round_half_up(v: float) -> int:
 
 def small_srtio3(seed: int = 0) -> Workload:
     """8^3 cells SrTiO3 (1536 O sites), 15 vacancies, no H, 2^3 fragments of
-    4^3 cells, Ea 0.60 eV, 800 K, plain FP64; ~1e5 hops = 6700 windows."""
+    4^3 cells, Ea 0.60 eV, 800 K, plain FP64; ~1e5 hops = 13400 windows at n_tau 0.5."""
     r = Replica((8, 8, 8), A_SRTIO3, 15, 0, 800.0, 0.60, 0.60, nfrag=(2, 2, 2))
-    return Workload("srtio3_8c_15v", [r], precision=0, windows=6700)
+    return Workload("srtio3_8c_15v", [r], n_tau=0.5, precision=0, windows=13400)
 
 
 def srtio3_h_sweep(seed: int = 0) -> Workload:
@@ -62,7 +63,7 @@ def srtio3_h_sweep(seed: int = 0) -> Workload:
     nsite = 3 * 32**3
     reps = [Replica(cells, A_SRTIO3, round_half_up(0.005 * nsite), round_half_up(0.1 * 32**3), T,
                     0.60, 0.30, nfrag=(8, 8, 8)) for T in (300.0, 400.0, 500.0, 600.0, 700.0)]
-    return Workload("srtio3h_32c_Tsweep", reps, precision=0, tracer=True, windows=200)
+    return Workload("srtio3h_32c_Tsweep", reps, n_tau=0.5, precision=0, tracer=True, windows=200)
 
 
 def batched_batio3(seed: int = 0, n: int = 256) -> Workload:
@@ -93,7 +94,7 @@ def bulk_batio3(seed: int = 0) -> Workload:
     nsite = 3 * 128**3
     r = Replica(cells, A_BATIO3, round_half_up(0.003 * nsite), round_half_up(0.05 * 128**3), 400.0,
                 0.70, 0.35, nfrag=(16, 16, 16))
-    return Workload("batio3h_128c", [r], precision=1, windows=10)
+    return Workload("batio3h_128c", [r], n_tau=0.5, precision=1, windows=10)
 
 
 def um_batio3_bias(seed: int = 0, L: int = 2500) -> Workload:
@@ -101,7 +102,7 @@ def um_batio3_bias(seed: int = 0, L: int = 2500) -> Workload:
     field 1e7 V/m along z, Ea 0.70 eV, 400 K, fragments of 8^3 cells."""
     nsite = 3 * L**3
     r = Replica((L, L, L), A_BATIO3, round_half_up(0.001 * nsite), 0, 400.0, 0.70, 0.70, field_z=1e7)
-    return Workload(f"batio3_{L}c_bias", [r], edge=8, precision=1, windows=4)
+    return Workload(f"batio3_{L}c_bias", [r], edge=8, n_tau=0.5, precision=1, windows=4)
 
 
 def um_grains(seed: int = 0, L=(1600, 400, 2400), n_grains: int = 16) -> Workload:
@@ -113,7 +114,7 @@ def um_grains(seed: int = 0, L=(1600, 400, 2400), n_grains: int = 16) -> Workloa
     nsite = 3 * L[0] * L[1] * L[2]
     Ez = 20.0 / (L[2] * A_BATIO3 * 1e-10)
     r = Replica(tuple(L), A_BATIO3, round_half_up(0.001 * nsite), 0, 400.0, 0.70, 0.70, field_z=Ez)
-    return Workload(f"batio3_{L[0]}x{L[1]}x{L[2]}c_grains", [r], edge=8, precision=1, windows=2,
+    return Workload(f"batio3_{L[0]}x{L[1]}x{L[2]}c_grains", [r], edge=8, n_tau=0.5, precision=1, windows=2,
                     notes={"grains": (n_grains, 1, 0.2)})
 
 
@@ -125,7 +126,7 @@ def elec_batio3(seed: int = 0, L: int = 128) -> Workload:
     1e7 V/m, 400 K, Ea 0.70 eV, edge-4 fragments, plain form."""
     nsite = 3 * L**3
     r = Replica((L, L, L), A_BATIO3, round_half_up(0.001 * nsite), 0, 400.0, 0.70, 0.70, field_z=1e7)
-    return Workload(f"batio3_{L}c_elec", [r], edge=4, precision=0, windows=32,
+    return Workload(f"batio3_{L}c_elec", [r], edge=4, n_tau=0.5, precision=0, windows=32,
                     notes={"elec": {"eps_r": 1000.0, "q_vac": 2.0, "refresh_windows": 8, "cycles": 12,
                                     "warm_cycles": 6}})
 
@@ -159,7 +160,7 @@ def h_trend(seed: int = 0, L: int = 32) -> Workload:
             for T in (550.0, 600.0, 650.0, 700.0):
                 reps.append(Replica((L, L, L), a, round_half_up(0.001 * nsite), round_half_up(x * L**3), T,
                                     Ea_O, Ea_H))
-    return Workload(f"h_trend_{L}c_24rep", reps, edge=4, precision=1, tracer=True, windows=20000,
+    return Workload(f"h_trend_{L}c_24rep", reps, edge=4, n_tau=0.5, precision=1, tracer=True, windows=20000,
                     notes={"x": [0.25, 0.35, 0.45], "T": [550.0, 600.0, 650.0, 700.0],
                            "materials": ["SrTiO3", "BaTiO3"]})
 
@@ -182,7 +183,7 @@ def fe_srtio3(seed: int = 0, L: int = 96) -> Workload:
     nsite = 3 * L**3
     reps = [Replica(cells, A_SRTIO3, round_half_up(0.001 * nsite), 0, T, 0.60, 0.60,
                     n_Fe=round_half_up(0.001 * L**3)) for T in (600.0, 700.0, 800.0, 900.0, 1000.0)]
-    return Workload(f"fe_srtio3_{L}c_Tsweep", reps, edge=4, precision=0, windows=32,
+    return Workload(f"fe_srtio3_{L}c_Tsweep", reps, edge=4, n_tau=0.5, precision=0, windows=32,
                     site={"vv": PAPER_VV, "fe": PAPER_VFE})
 
 

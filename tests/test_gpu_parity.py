@@ -209,7 +209,7 @@ def test_batched_workload_full_size_sampled(fk, orc):
     wl = workloads.batched_batio3(0)
     reps = wl.replicas
     b = fk.Batch([(*r.cells, r.a) for r in reps], [(r.n_vac, r.n_H) for r in reps], 0, edge=wl.edge,
-                 precision=wl.precision)
+                 precision=wl.precision, n_tau=wl.n_tau, **wl.notes.get("launch_opts", {}))
     assert all(b.info(r).n_vac == reps[r].n_vac for r in range(len(reps)))
     b.set_barriers([r.Ea_O for r in reps], [r.Ea_H for r in reps], [r.T for r in reps])
     W = 8
@@ -225,7 +225,7 @@ def test_batched_workload_full_size_sampled(fk, orc):
         info = b.info(r)
         ref = orc.Lattice(rep.cells, None, rep.n_vac, rep.n_H, seed=0, replica=r, edge=wl.edge)
         assert tuple(info.nfrag) == ref.nf
-        ref.set_rates(rep.Ea_O, rep.Ea_H, rep.T, a_ang=rep.a, cap_v=cap, precision=wl.precision)
+        ref.set_rates(rep.Ea_O, rep.Ea_H, rep.T, a_ang=rep.a, cap_v=cap, n_tau=wl.n_tau, precision=wl.precision)
         ref.run(W)
         occ = b.state(r)
         assert np.array_equal(np.bincount(occ, minlength=3)[1:], [rep.n_H, rep.n_vac])
