@@ -129,10 +129,12 @@ typedef struct {
                             and takes half of every phase's fragments; writes are mirrored
                             through distributed shared memory).  -1 (default) = SMs / 8,
                             0 = none */
-    int32_t small_pass; /* colour-phase kernels: fragments holding one or two vacancies run in a
-                           pass of their own (4 or 2 fragments per warp, lock-step) beside the
-                           general pass; same trajectory.  0 (default) = where a phase holds
-                           32768 fragments or more, 1 = always, -1 = never */
+    int32_t small_pass; /* colour-phase kernels: sparse fragments run in a pass of their own beside
+                           the general one (one warp per fragment); same trajectory.  Mixed form:
+                           fragments holding up to 4 vacancies, one thread per fragment; plain
+                           form (and mode 2): fragments holding one or two vacancies, 4 or 2 per
+                           warp in lock-step.  0 (default) = where a phase holds 32768 fragments
+                           or more, 1 = always, 2 = always and in the grouped form, -1 = never */
     int32_t test_stuck_wait_us; /* test of the device-side bounded wait (0 = off): the replica-resident
                                    kernel, after staging its state, waits on a barrier that nothing
                                    completes, gives up after this many microseconds (<= 2e6) and

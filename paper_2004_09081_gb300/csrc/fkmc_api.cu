@@ -760,7 +760,7 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
     if (o.cap_v != 0 && (o.cap_v < 8 || o.cap_v > 256 || o.cap_v % 8))
         return fail(FKMC_EINVAL, "cap_v must be 0 or a multiple of 8 in [8, 256]");
     if (o.schedule < 0 || o.schedule > 2) return fail(FKMC_EINVAL, "schedule must be 0, 1 or 2");
-    if (o.small_pass < -1 || o.small_pass > 1) return fail(FKMC_EINVAL, "small_pass must be -1, 0 or 1");
+    if (o.small_pass < -1 || o.small_pass > 2) return fail(FKMC_EINVAL, "small_pass must be -1, 0, 1 or 2");
     if (o.test_stuck_wait_us < 0 || o.test_stuck_wait_us > 2000000)
         return fail(FKMC_EINVAL, "test_stuck_wait_us must be in [0, 2e6]");
 
@@ -1055,8 +1055,9 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
         if (!site_path(b)) wa.field = nullptr;  // the table-rate run pass
         cudaError_t le = launch_window(b->opts.precision, b->d_desc, b->n, b->total_items, b->wctl, b->perms, b->act,
                                        b->act_count, b->occ, b->recs, b->counts, b->tracer, b->stats, b->status, b->cap,
-                                       b->run_blocks, small_blocks, split, wa, b->cap_st, b->side_st, b->side_fork,
-                                       b->side_join);
+                                       b->run_blocks, small_blocks, split,
+                                       window_lane(b->opts.precision, b->opts.small_pass), wa, b->cap_st, b->side_st,
+                                       b->side_fork, b->side_join);
         cudaError_t ce = cudaStreamEndCapture(b->cap_st, &graph);
         if (le != cudaSuccess) return cuda_fail(le, "window capture");
         if (ce != cudaSuccess) return cuda_fail(ce, "window capture");

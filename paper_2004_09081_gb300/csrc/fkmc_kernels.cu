@@ -308,6 +308,49 @@ __global__ void k_window_setup(const RepDesc* __restrict__ descs, int nrep, unsi
 // two vacancies go to lists of their own (act + total_items, act + 2
 // total_items; counters act_count[8 + phase], act_count[16 + phase]) for the
 // small-fragment run pass; the rest (or all) to act, act_count[phase].
+// Fragment of work item `item` in colour phase `phase`: the replica (binary
+// search over the items' prefix) and the fragment index inside it, or false
+// where the replica has fewer fragments of that colour than items or runs in
+// the replica-resident kernel.  Each replica's items enumerate the fragments
+// of one colour (parity bits per dimension; a single-fragment dimension holds
+// only colour bit 0).
+__device__ __forceinline__ bool item_fragment(const RepDesc* __restrict__ descs, int nrep, int64_t item, int phase,
+                                              const uint32_t* __restrict__ perms, int& rep, int64_t& fid)
+{
+    int lo = 0, hi = nrep - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (descs[mid].items_off <= item) lo = mid; else hi = mid - 1;
+    }
+    const RepDesc& D = descs[lo];
+    const int64_t local = item - D.items_off;
+    const int colour = (int)((perms[lo] >> (4 * phase)) & 15u);
+    int cnt[3], bit[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        bit[d] = (colour >> d) & 1;
+        cnt[d] = D.nf[d] == 1 ? (bit[d] == 0 ? 1 : 0) : D.nf[d] / 2;
+    }
+    if (D.resident || local >= (int64_t)cnt[0] * cnt[1] * cnt[2]) return false;
+    int fc[3];
+    unflatten3(local, cnt[0], cnt[1], fc);
+    const int f0 = D.nf[0] == 1 ? 0 : 2 * fc[0] + bit[0];
+    const int f1 = D.nf[1] == 1 ? 0 : 2 * fc[1] + bit[1];
+    const int f2 = D.nf[2] == 1 ? 0 : 2 * fc[2] + bit[2];
+    rep = lo;
+    fid = ((int64_t)f2 * D.nf[1] + f1) * D.nf[0] + f0;
+    return true;
+}
+
+// Screen pass of a colour phase: one thread per fragment of the phase's colour
+// (every replica).  Fragments with vacancies go to an active list together
+// with their first Philox block, drawn here thirty-two fragments per warp
+// instead of once per fragment-warp.  split = 1: fragments holding one or
+// two vacancies go to lists of their own (act + total_items, act + 2
+// total_items; counters act_count[8 + phase], act_count[16 + phase]) for the
+// grouped small-fragment pass; split = 2: fragments holding at most
+// LANE_MAX_V vacancies are left to the one-thread-per-fragment pass; the rest
+// (or all) go to act, act_count[phase].
 template <int PREC>
 __global__ void __launch_bounds__(256) k_screen(const RepDesc* __restrict__ descs, int nrep, int64_t total_items,
                                                 int phase, unsigned long long* wctl,
@@ -321,47 +364,27 @@ __global__ void __launch_bounds__(256) k_screen(const RepDesc* __restrict__ desc
     bool keep = false;
     int list = 0;
     ActEntry e;
-    if (item < total_items) {
-        int lo = 0, hi = nrep - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (descs[mid].items_off <= item) lo = mid; else hi = mid - 1;
-        }
+    int lo;
+    int64_t fid;
+    if (item < total_items && item_fragment(descs, nrep, item, phase, perms, lo, fid)) {
         const RepDesc& D = descs[lo];
-        const int64_t local = item - D.items_off;
-        const int colour = (int)((perms[lo] >> (4 * phase)) & 15u);
-        int cnt[3], bit[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            bit[d] = (colour >> d) & 1;
-            cnt[d] = D.nf[d] == 1 ? (bit[d] == 0 ? 1 : 0) : D.nf[d] / 2;
-        }
-        if (!D.resident && local < (int64_t)cnt[0] * cnt[1] * cnt[2]) {
-            int fc[3];
-            unflatten3(local, cnt[0], cnt[1], fc);
-            int f0 = fc[0], f1 = fc[1], f2 = fc[2];
-            f0 = D.nf[0] == 1 ? 0 : 2 * f0 + bit[0];
-            f1 = D.nf[1] == 1 ? 0 : 2 * f1 + bit[1];
-            f2 = D.nf[2] == 1 ? 0 : 2 * f2 + bit[2];
-            const int64_t fid = ((int64_t)f2 * D.nf[1] + f1) * D.nf[0] + f0;
-            const int nv = counts[D.frag_base + fid];
-            if (nv > 0) {
-                keep = true;
-                list = split && nv <= 2 ? nv : 0;
-                const uint64_t w = D.window + wctl[1];
-                const U64x4 blk = philox4x64((uint64_t)fid, w, 0, 0, D.seed, key_word(D.replica, PURPOSE_HOP));
-                e.rep = lo;
-                e.nv = nv;
-                e.fid = fid;
-                e.xs[0] = blk.x[1];
-                e.xs[1] = blk.x[3];
-                if constexpr (PREC == 0) {
-                    e.E[0] = (uint64_t)__double_as_longlong(neglog64(blk.x[0]));
-                    e.E[1] = (uint64_t)__double_as_longlong(neglog64(blk.x[2]));
-                } else {
-                    e.E[0] = (uint64_t)__float_as_uint(neglog32(blk.x[0]));
-                    e.E[1] = (uint64_t)__float_as_uint(neglog32(blk.x[2]));
-                }
+        const int nv = counts[D.frag_base + fid];
+        if (nv > 0 && !(split == 2 && nv <= LANE_MAX_V)) {
+            keep = true;
+            list = split == 1 && nv <= 2 ? nv : 0;
+            const uint64_t w = D.window + wctl[1];
+            const U64x4 blk = philox4x64((uint64_t)fid, w, 0, 0, D.seed, key_word(D.replica, PURPOSE_HOP));
+            e.rep = lo;
+            e.nv = nv;
+            e.fid = fid;
+            e.xs[0] = blk.x[1];
+            e.xs[1] = blk.x[3];
+            if constexpr (PREC == 0) {
+                e.E[0] = (uint64_t)__double_as_longlong(neglog64(blk.x[0]));
+                e.E[1] = (uint64_t)__double_as_longlong(neglog64(blk.x[2]));
+            } else {
+                e.E[0] = (uint64_t)__float_as_uint(neglog32(blk.x[0]));
+                e.E[1] = (uint64_t)__float_as_uint(neglog32(blk.x[2]));
             }
         }
     }
@@ -865,6 +888,312 @@ __global__ void __launch_bounds__(128, 8) k_run_small(const RepDesc* __restrict_
     }
 }
 
+// ------------------------------------------------------------------ one thread per fragment
+// Rate types of the 8 events of the vacancy at `key` (mixed form), packed as
+// nibbles n = type + 1 (0: no event), and the sum of their fixed-point rates.
+// The 8 neighbour words are read from L2 (ld.global.cg: this thread's own
+// exchanges are atomics there) before any is used.
+template <bool GRAIN>
+__device__ __forceinline__ uint32_t lane_types(const RepDesc& D, const uint32_t* occ, const uint8_t* gb, uint64_t key,
+                                               unsigned long long& sum)
+{
+    int t, x, y, z;
+    split_key(key, t, x, y, z);
+    uint32_t w[8];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+        const NbEntry nb = nb_entry(t, n);
+        w[n] = __ldcg(occ + occ_word(D, nb.t2, wrapc(x + nb.dc[0], D.L[0]), wrapc(y + nb.dc[1], D.L[1]),
+                                     wrapc(z + nb.dc[2], D.L[2])));
+    }
+    uint8_t gs = 0;
+    if constexpr (GRAIN) gs = __ldg(gb + cell_index(D, x, y, z));
+    uint32_t packed = 0;
+    unsigned long long s = 0ull;
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+        const NbEntry nb = nb_entry(t, n);
+        const int jx = wrapc(x + nb.dc[0], D.L[0]);
+        const int code = (int)((w[n] >> occ_shift(jx)) & 3u);
+        if (code != SP_V) {
+            int ty = code * 3 + nb.d[2] + 1;
+            unsigned long long q;
+            if constexpr (GRAIN) {
+                const int jy = wrapc(y + nb.dc[1], D.L[1]);
+                const int jz = wrapc(z + nb.dc[2], D.L[2]);
+                if (gs | __ldg(gb + cell_index(D, jx, jy, jz))) {
+                    q = D.qg[ty];
+                    ty += 6;
+                } else {
+                    q = D.q[ty];
+                }
+            } else {
+                q = D.q[ty];
+            }
+            s += q;
+            packed |= (uint32_t)(ty + 1) << (4 * n);
+        }
+    }
+    sum = s;
+    return packed;
+}
+
+// Whether two O sites lie within one half-cell of each other along every axis
+// (periodic): true for every pair of nearest neighbours.  A site's position in
+// half-cells is 2 (x, y, z) + e_t.
+__device__ __forceinline__ bool within_half_cell(const RepDesc& D, uint64_t a, uint64_t b)
+{
+    int ta, xa, ya, za, tb, xb, yb, zb;
+    split_key(a, ta, xa, ya, za);
+    split_key(b, tb, xb, yb, zb);
+    const int h[3] = {2 * (xa - xb) + (ta == 0) - (tb == 0), 2 * (ya - yb) + (ta == 1) - (tb == 1),
+                      2 * (za - zb) + (ta == 2) - (tb == 2)};
+    bool near = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        int v = h[d];
+        if (v > D.L[d]) v -= 2 * D.L[d];
+        else if (v < -D.L[d]) v += 2 * D.L[d];
+        near = near && v >= -1 && v <= 1;
+    }
+    return near;
+}
+
+__device__ __forceinline__ void order_pair(VacRec& a, VacRec& b)
+{
+    if (b.key < a.key) {
+        const VacRec t = a;
+        a = b;
+        b = t;
+    }
+}
+
+// Run pass for fragments holding one to LANE_MAX_V vacancies, mixed form: one
+// thread per fragment of the phase's colour (the screen pass's items), with
+// the fragment's records, packed rate types and per-vacancy rate sums in
+// registers, so that a warp runs 32 fragments.  The mixed form's sums are
+// exact integers: the total and the first event whose inclusive prefix
+// exceeds the target are those of the warp passes' scans over the same slot
+// order (ascending site).  The draws are the same Philox words (event i:
+// block i/2, words 1 and 0 for even i, 3 and 2 for odd i), the window test,
+// selection and exchange are the same, so the trajectory is the same.  After
+// a hop only the moved vacancy and those within a half-cell of its old or new
+// site re-read their neighbour words; every other rate is unchanged.
+template <bool GRAIN>
+__global__ void __launch_bounds__(128) k_run_lane(const RepDesc* __restrict__ descs, int nrep, int64_t total_items,
+                                                  int phase, const unsigned long long* wctl,
+                                                  const uint32_t* __restrict__ perms, uint32_t* occ, VacRec* recs,
+                                                  int32_t* counts, int32_t* tracer, unsigned long long* stats,
+                                                  uint32_t* status, int cap, const uint8_t* gb)
+{
+    constexpr int NL = LANE_MAX_V;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int rep = -1;
+    int64_t fid = 0;
+    int nv = 0;
+    if (item < total_items && item_fragment(descs, nrep, item, phase, perms, rep, fid))
+        nv = counts[descs[rep].frag_base + fid];
+    uint32_t hops = 0, nhand = 0;
+    if (nv > 0 && nv <= NL) {
+        const RepDesc& D = descs[rep];
+        const int64_t g = D.frag_base + fid;
+        if (nv > cap) {
+            atomicOr(status, STATUS_OVERFLOW);
+            nv = cap;
+        }
+        // slots in ascending site order (a 4-input sorting network; empty slots last)
+        VacRec r[NL];
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            if (k < nv) {
+                r[k] = recs[g * cap + k];
+            } else {
+                r[k].key = ~0ull;
+                r[k].d[0] = r[k].d[1] = r[k].d[2] = 0;
+                r[k].id = 0;
+            }
+        }
+        static_assert(NL == 4, "sorting network for four slots");
+        order_pair(r[0], r[1]);
+        order_pair(r[2], r[3]);
+        order_pair(r[0], r[2]);
+        order_pair(r[1], r[3]);
+        order_pair(r[1], r[2]);
+        int lo_c[3], hi_c[3];
+        {
+            int f[3];
+            unflatten3(fid, D.nf[0], D.nf[1], f);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                lo_c[d] = frag_start(f[d], D.base[d], D.rem[d]);
+                hi_c[d] = frag_start(f[d] + 1, D.base[d], D.rem[d]);
+            }
+        }
+        uint32_t ty[NL];
+        unsigned long long sm[NL];
+        uint32_t alive = (1u << nv) - 1u;
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            sm[k] = 0ull;
+            ty[k] = k < nv ? lane_types<GRAIN>(D, occ, gb, r[k].key, sm[k]) : 0u;
+        }
+        const uint64_t w = D.window + wctl[1];
+        const uint64_t k1 = key_word(D.replica, PURPOSE_HOP);
+        U64x4 blk{};
+        double clock = 0.0;
+        uint64_t i = 0;
+        for (;;) {
+            unsigned long long total = 0ull;
+#pragma unroll
+            for (int k = 0; k < NL; ++k) total += sm[k];
+            if (total == 0ull) break;
+            if (i >= MAX_EVENTS_PER_PHASE) {
+                atomicOr(status, STATUS_EVENT_LIMIT);
+                break;
+            }
+            if ((i & 1) == 0) blk = philox4x64((uint64_t)fid, w, i >> 1, 0, D.seed, k1);
+            const bool odd = (i & 1) != 0;
+            const uint64_t xs = odd ? blk.x[3] : blk.x[1];
+            const float Ef = neglog32(odd ? blk.x[2] : blk.x[0]);
+            const float ratio = __fdiv_rn(Ef, __ull2float_rn(total));
+            const double dth = __dmul_rn((double)ratio, D.two_pow_F);
+            if (__dadd_rn(clock, dth) > D.theta_tau) break;
+            const unsigned long long target = __umul64hi(xs, total);
+            // slot m and neighbour n of the first event whose prefix exceeds the target
+            int m = NL - 1;
+            unsigned long long acc = 0ull;
+            bool found = false;
+#pragma unroll
+            for (int k = 0; k < NL; ++k) {
+                if (!found) {
+                    if (acc + sm[k] > target) {
+                        m = k;
+                        found = true;
+                    } else {
+                        acc += sm[k];
+                    }
+                }
+            }
+            VacRec cur = r[0];
+            uint32_t tym = ty[0];
+#pragma unroll
+            for (int k = 1; k < NL; ++k) {
+                if (k == m) {
+                    cur = r[k];
+                    tym = ty[k];
+                }
+            }
+            int n = 7;
+            found = false;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int nib = (int)((tym >> (4 * e)) & 15u);
+                if (!found && nib) {
+                    const int tv = nib - 1;
+                    acc += GRAIN ? (tv < 6 ? D.q[tv] : D.qg[tv - 6]) : D.q[tv];
+                    if (acc > target) {
+                        n = e;
+                        found = true;
+                    }
+                }
+            }
+            // the exchange
+            const uint64_t s_key = cur.key;
+            int t, x, y, z;
+            split_key(s_key, t, x, y, z);
+            const NbEntry nb = nb_entry(t, n);
+            const int jx = wrapc(x + nb.dc[0], D.L[0]);
+            const int jy = wrapc(y + nb.dc[1], D.L[1]);
+            const int jz = wrapc(z + nb.dc[2], D.L[2]);
+            const int tyv = (int)((tym >> (4 * n)) & 15u) - 1;
+            const uint32_t ion = (uint32_t)((tyv % 6) / 3);
+            atomicXor(occ + occ_word(D, t, x, y, z), ((uint32_t)SP_V ^ ion) << occ_shift(x));
+            atomicXor(occ + occ_word(D, nb.t2, jx, jy, jz), (ion ^ (uint32_t)SP_V) << occ_shift(jx));
+            cur.d[0] += nb.d[0];
+            cur.d[1] += nb.d[1];
+            cur.d[2] += nb.d[2];
+            if (tracer) {
+                const int64_t s_lin = (((int64_t)t * D.L[2] + z) * D.L[1] + y) * D.L[0] + x;
+                const int64_t j_lin = (((int64_t)nb.t2 * D.L[2] + jz) * D.L[1] + jy) * D.L[0] + jx;
+                int32_t* ts = tracer + 3 * (D.site_off + s_lin);
+                int32_t* tj = tracer + 3 * (D.site_off + j_lin);
+                ts[0] = tj[0] - nb.d[0];
+                ts[1] = tj[1] - nb.d[1];
+                ts[2] = tj[2] - nb.d[2];
+                tj[0] = tj[1] = tj[2] = 0;
+            }
+            cur.key = make_key(nb.t2, jx, jy, jz);
+            const bool owned = jx >= lo_c[0] && jx < hi_c[0] && jy >= lo_c[1] && jy < hi_c[1] && jz >= lo_c[2] &&
+                               jz < hi_c[2];
+            if (!owned) {
+                const int gx = frag_of(jx, D.base[0], D.rem[0]);
+                const int gy = frag_of(jy, D.base[1], D.rem[1]);
+                const int gz = frag_of(jz, D.base[2], D.rem[2]);
+                const int64_t g2 = D.frag_base + ((int64_t)gz * D.nf[1] + gy) * D.nf[0] + gx;
+                const int slot = atomicAdd(counts + g2, 1);
+                if (slot < cap) recs[g2 * cap + slot] = cur;
+                else atomicOr(status, STATUS_OVERFLOW);
+                alive &= ~(1u << m);
+                ++nhand;
+            }
+            __threadfence_block();
+#pragma unroll
+            for (int k = 0; k < NL; ++k)
+                if (k == m) r[k] = cur;
+            clock = __dadd_rn(clock, dth);
+            ++i;
+            // rates after the exchange: vacancies near s or j read their words again
+            uint32_t redo = 0;
+#pragma unroll
+            for (int k = 0; k < NL; ++k) {
+                const bool live = (alive >> k) & 1u;
+                if (!live) {
+                    ty[k] = 0u;
+                    sm[k] = 0ull;
+                } else if (k == m || within_half_cell(D, r[k].key, s_key) || within_half_cell(D, r[k].key, cur.key)) {
+                    redo |= 1u << k;
+                }
+            }
+            while (redo) {
+                const int k = __ffs(redo) - 1;
+                redo &= redo - 1u;
+                uint64_t kk = r[0].key;
+#pragma unroll
+                for (int q = 1; q < NL; ++q)
+                    if (q == k) kk = r[q].key;
+                unsigned long long sk = 0ull;
+                const uint32_t tk = lane_types<GRAIN>(D, occ, gb, kk, sk);
+#pragma unroll
+                for (int q = 0; q < NL; ++q)
+                    if (q == k) {
+                        ty[q] = tk;
+                        sm[q] = sk;
+                    }
+            }
+        }
+        hops = (uint32_t)i;
+        // surviving records stay with the fragment, in slot order
+        int pos = 0;
+#pragma unroll
+        for (int k = 0; k < NL; ++k)
+            if ((alive >> k) & 1u) recs[g * cap + pos++] = r[k];
+        counts[g] = pos;
+    }
+    // hop and hand-off counters: one atomic per warp where its fragments share a replica
+    const int r0 = __shfl_sync(FULL, rep, 0);
+    if (__all_sync(FULL, rep == r0 || (hops == 0 && nhand == 0)) && r0 >= 0) {
+        const unsigned hs = __reduce_add_sync(FULL, hops), ns = __reduce_add_sync(FULL, nhand);
+        if ((threadIdx.x & 31) == 0) {
+            if (hs) atomicAdd(stats + 2 * r0, (unsigned long long)hs);
+            if (ns) atomicAdd(stats + 2 * r0 + 1, (unsigned long long)ns);
+        }
+    } else {
+        if (hops) atomicAdd(stats + 2 * rep, (unsigned long long)hops);
+        if (nhand) atomicAdd(stats + 2 * rep + 1, (unsigned long long)nhand);
+    }
+}
+
 // ------------------------------------------------------------------ site energies
 // Dopant placement: cells f(0..n_fe-1) of a keyed Feistel bijection of the
 // cell indices (the vacancy placement's construction, its own key).
@@ -1189,6 +1518,13 @@ bool window_split(bool site, int64_t total_items, int mode)
     return !site && (mode > 0 || (mode == 0 && total_items >= SPLIT_MIN_ITEMS));
 }
 
+// The mixed form runs its small fragments one thread per fragment (up to
+// LANE_MAX_V vacancies), unless the grouped pass is asked for (mode 2).
+bool window_lane(int prec, int mode) { return prec == 1 && mode != 2; }
+
+using LaneFn = void (*)(const RepDesc*, int, int64_t, int, const unsigned long long*, const uint32_t*, uint32_t*,
+                        VacRec*, int32_t*, int32_t*, unsigned long long*, uint32_t*, int, const uint8_t*);
+
 using SmallFn = void (*)(const RepDesc*, const ActEntry*, int64_t, const int32_t*, int, const unsigned long long*,
                         uint32_t*, VacRec*, int32_t*, int32_t*, unsigned long long*, uint32_t*, int, const uint8_t*);
 
@@ -1245,8 +1581,8 @@ cudaError_t launch_window(int prec, const RepDesc* d_descs, int nrep, int64_t to
                           unsigned long long* wctl, uint32_t* perms, ActEntry* act, int32_t* act_count,
                           uint32_t* occ, VacRec* recs, int32_t* counts, int32_t* tracer,
                           unsigned long long* stats, uint32_t* status, int cap, int run_blocks,
-                          int small_blocks, bool split_pass, const SiteArgs& sa, cudaStream_t st, cudaStream_t side,
-                          cudaEvent_t fork, cudaEvent_t join)
+                          int small_blocks, bool split_pass, bool lane_pass, const SiteArgs& sa, cudaStream_t st,
+                          cudaStream_t side, cudaEvent_t fork, cudaEvent_t join)
 {
     if (total_items <= 0) return cudaSuccess;
     const bool site = sa.field != nullptr, grain = sa.gbound != nullptr;
@@ -1254,16 +1590,28 @@ cudaError_t launch_window(int prec, const RepDesc* d_descs, int nrep, int64_t to
     const int64_t sblocks = (total_items + 255) / 256;
     const size_t smem = phase_smem_bytes(cap, site);
     const RunFn run = run_kernel(site ? 0 : prec, site, grain);
-    const int split = split_pass && !site ? 1 : 0;
+    const bool lane = split_pass && !site && lane_pass && prec == 1;
+    const int split = split_pass && !site ? (lane ? 2 : 1) : 0;
     const SmallFn small = small_kernel(prec, grain);
+    const LaneFn lanek = grain ? k_run_lane<true> : k_run_lane<false>;
     for (int p = 0; p < 8; ++p) {
+        if (lane) {  // reads only the counts: beside the screen and the general pass
+            cudaError_t e = cudaEventRecord(fork, st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
+            if (e != cudaSuccess) return e;
+            lanek<<<(unsigned)((total_items + 127) / 128), 128, 0, side>>>(d_descs, nrep, total_items, p, wctl, perms,
+                                                                          occ, recs, counts, tracer, stats, status,
+                                                                          cap, sa.gbound);
+            e = cudaEventRecord(join, side);
+            if (e != cudaSuccess) return e;
+        }
         if (site || prec == 0)
             k_screen<0><<<(unsigned)sblocks, 256, 0, st>>>(d_descs, nrep, total_items, p, wctl, perms, counts, act,
                                                            act_count, split);
         else
             k_screen<1><<<(unsigned)sblocks, 256, 0, st>>>(d_descs, nrep, total_items, p, wctl, perms, counts, act,
                                                            act_count, split);
-        if (split) {  // the two run passes touch disjoint fragments: run them side by side
+        if (split == 1) {  // the two run passes touch disjoint fragments: run them side by side
             cudaError_t e = cudaEventRecord(fork, st);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
             if (e != cudaSuccess) return e;

@@ -17,16 +17,19 @@ cudaError_t phase_prepare(int cap);
 cudaError_t run_pass_blocks(int prec, int cap, bool site, bool grain, int* blocks);
 cudaError_t small_pass_blocks(int prec, bool grain, int* blocks);
 constexpr int64_t SPLIT_MIN_ITEMS = 32768;  // fragments per phase from which the small-fragment pass runs
-// mode: kmc_opts.small_pass (0 auto, 1 always, -1 never)
+constexpr int LANE_MAX_V = 4;  // vacancies a fragment may hold to run in the one-thread-per-fragment pass
+// mode: kmc_opts.small_pass (0 auto, 1 always, 2 always and grouped, -1 never)
 bool window_split(bool site, int64_t total_items, int mode);
+// the small-fragment pass in its one-thread-per-fragment form (mixed form only)
+bool window_lane(int prec, int mode);
 // act: 3 lists of total_items entries (general, one vacancy, two vacancies);
 // act_count: 24 counters (list l, phase p at 8 l + p)
 cudaError_t launch_window(int prec, const RepDesc* d_descs, int nrep, int64_t total_items,
                           unsigned long long* wctl, uint32_t* perms, ActEntry* act, int32_t* act_count,
                           uint32_t* occ, VacRec* recs, int32_t* counts, int32_t* tracer,
                           unsigned long long* stats, uint32_t* status, int cap, int run_blocks,
-                          int small_blocks, bool split, const SiteArgs& sa, cudaStream_t st, cudaStream_t side,
-                          cudaEvent_t fork, cudaEvent_t join);
+                          int small_blocks, bool split, bool lane, const SiteArgs& sa, cudaStream_t st,
+                          cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
 cudaError_t launch_grains(const RepDesc* d_descs, int nrep, int64_t ncell_total, int n_grains, int width, int64_t* X,
                           int32_t* grain, uint8_t* gb, cudaStream_t st);
 cudaError_t launch_init_dopants(const RepDesc& D, int b_bits, int64_t n_fe, uint8_t* fe, cudaStream_t st);

@@ -88,7 +88,7 @@ def test_site_shell_tables_match_oracle(lib):
         lib.kmc_site_shells([(2, 0.1), (2, 0.2)], [], 0)  # listed twice
 
 
-@pytest.mark.parametrize("field,value", [("small_pass", 2), ("small_pass", -2), ("schedule", 3), ("precision", 5),
+@pytest.mark.parametrize("field,value", [("small_pass", 3), ("small_pass", -2), ("schedule", 3), ("precision", 5),
                                          ("cap_v", 12), ("n_tau", 0.0), ("n_tau", 65.0)])
 def test_create_batch_rejects_bad_options(lib, field, value):
     """Options are checked before any device work: a bad value is FKMC_EINVAL

@@ -41,8 +41,7 @@ def test_grain_map_matches_oracle(fk, orc):
             assert np.array_equal(bnd, rb)
 
 
-@pytest.mark.parametrize("small", [-1, 1])
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec,small", [(0, -1), (0, 1), (1, -1), (1, 1), (1, 2)])
 def test_grains_colour_phase_bit_exact(fk, orc, prec, small):
     cells, nf = (16, 12, 16), (4, 2, 4)
     b = fk.Batch([(*cells, 4.01)], [(40, 150)], 7, nfrag=nf, precision=prec, tracer=True, cap_v=64,

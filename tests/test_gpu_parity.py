@@ -54,13 +54,17 @@ def run_pair(fk, orc, cells, nf, nv, nh, seed, windows, prec, tracer=True, T=800
 
 # (precision, schedule): plain FP64 runs the colour-phase kernel; the mixed form
 # runs both the colour-phase kernel (1) and the replica-resident kernel (2);
-# "+small" forces the small-fragment run pass (fragments with one or two
-# vacancies, four or two per warp) beside the general one
-FORMS = [(0, 0), (1, 1), (1, 2), (0, 10), (1, 11)]
+# 10 + s forces the small-fragment run pass beside the general one (plain:
+# fragments with one or two vacancies, four or two per warp; mixed: up to four
+# vacancies, one thread per fragment); 20 + s forces the grouped form in the
+# mixed form too
+FORMS = [(0, 0), (1, 1), (1, 2), (0, 10), (1, 11), (1, 21)]
 
 
 def form(sched):
-    """schedule and small_pass of a FORMS entry (10 + s: schedule s, small pass forced)"""
+    """schedule and small_pass of a FORMS entry"""
+    if sched >= 20:
+        return sched % 10, 2
     return (sched % 10, 1) if sched >= 10 else (sched, -1)
 
 
@@ -289,14 +293,16 @@ def test_cluster_pairs_bit_exact(fk, orc):
         assert np.array_equal(b.records(r), ref.records()), r
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_small_pass_by_default_on_a_large_phase(fk, orc, prec):
+@pytest.mark.parametrize("prec,small", [(0, 0), (1, 0), (1, 2)])
+def test_small_pass_by_default_on_a_large_phase(fk, orc, prec, small):
     """128^3 cells in 2^3-cell fragments: 32768 fragments per colour phase, so
     the small-fragment pass runs beside the general one by default (on a second
-    stream inside the window graph); bit for bit against the oracle."""
+    stream inside the window graph; the mixed form's one-thread-per-fragment
+    pass, or its grouped form on request); bit for bit against the oracle."""
     cells, nf = (128, 128, 128), (64, 64, 64)
     nv = 3 * 128 ** 3 // 1000
-    b = fk.Batch([(*cells, 4.01)], [(nv, 0)], 17, nfrag=nf, precision=prec, tracer=True, cap_v=16)
+    b = fk.Batch([(*cells, 4.01)], [(nv, 0)], 17, nfrag=nf, precision=prec, tracer=True, cap_v=16,
+                 small_pass=small)
     b.set_barriers(0.7, 0.35, 600.0, field_z=1e7)
     ref = orc.Lattice(cells, nf, nv, 0, seed=17, tracer=True)
     ref.set_rates(0.7, 0.35, 600.0, Ez=1e7, a_ang=4.01, cap_v=16, precision=prec)
@@ -308,3 +314,18 @@ def test_small_pass_by_default_on_a_large_phase(fk, orc, prec):
     assert np.array_equal(b.tracer_field(), ref.tracer_field())
     info, c = b.info(), ref.counters()
     assert (info.hops, info.handoffs) == (c["hops"], c["handoffs"]) and c["hops"] > 30000
+
+
+@pytest.mark.parametrize("small", [1, 2])
+def test_lane_pass_dense_fragments(fk, orc, small):
+    """Mixed form, 8^3 cells in 64 fragments of 2^3 cells (24 O sites) with 200
+    vacancies: fragments of every count from 0 past 4 (the most the
+    one-thread-per-fragment pass takes, the rest go to the warp pass),
+    neighbouring vacancies inside one fragment (their rates change with each
+    other's hops), hand-offs every few events, H- and a field."""
+    cells, nf = (8, 8, 8), (4, 4, 4)
+    per_frag = np.bincount(orc.Lattice(cells, nf, 200, 300, seed=29).records()[:, 0], minlength=64)
+    assert {1, 4, 5}.issubset(set(per_frag.tolist()))
+    b, ref = run_pair(fk, orc, cells, nf, 200, 300, 29, 120, 1, T=750.0, Ez=2e7, cap=32, chunks=3,
+                      schedule=10 * small + 1)
+    assert ref.counters()["hops"] > 3000 and ref.counters()["handoffs"] > 1000
