@@ -129,17 +129,21 @@ typedef struct {
                             and takes half of every phase's fragments; writes are mirrored
                             through distributed shared memory).  -1 (default) = SMs / 8,
                             0 = none */
-    int32_t small_pass; /* colour-phase kernels: sparse fragments run in a pass of their own beside
+    int32_t small_pass; /* colour-phase kernels: sparse fragments run in a pass of their own besides
                            the general one (one warp per fragment); same trajectory.  Mixed form:
-                           fragments holding up to 4 vacancies, one thread per fragment; plain
-                           form (and mode 2): fragments holding one or two vacancies, 4 or 2 per
-                           warp in lock-step.  0 (default) = where a phase holds 32768 fragments
-                           or more, 1 = always, 2 = always and in the grouped form, -1 = never */
+                           one thread per fragment (see lane_form); plain form (and mode 2):
+                           fragments holding one or two vacancies, 4 or 2 per warp in lock-step.
+                           0 (default) = where a phase holds 32768 fragments or more,
+                           1 = always, 2 = always and in the grouped form, -1 = never */
     int32_t test_stuck_wait_us; /* test of the device-side bounded wait (0 = off): the replica-resident
                                    kernel, after staging its state, waits on a barrier that nothing
                                    completes, gives up after this many microseconds (<= 2e6) and
                                    kmc_run returns FKMC_ETIMEOUT with the state untouched */
-    int32_t reserved[4];
+    int32_t lane_form;  /* mixed form, one-thread-per-fragment pass: 0 (default) = by phase size,
+                           1 = registers (up to 4 vacancies, beside the general pass),
+                           2 = persistent (up to 8 vacancies in shared memory, a grid that
+                           stays resident for the phase; the general pass after it) */
+    int32_t reserved[3];
 } kmc_opts;
 
 typedef struct {

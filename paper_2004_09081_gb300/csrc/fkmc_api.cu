@@ -151,6 +151,7 @@ struct kmc_batch {
     uint32_t* perms = nullptr;           // colour order of every replica, this window
     ActEntry* act = nullptr;             // screened fragments of a phase
     int32_t* act_count = nullptr;        // per list and phase
+    uint8_t* cls = nullptr;              // per work item: the screen's class for the register lane pass
     int run_blocks = 0;
     cudaStream_t cap_st = nullptr;
     cudaGraphExec_t window_exec = nullptr;
@@ -286,6 +287,18 @@ namespace {
 
 // the site-energy run pass is on: shells, dopant energies or electrostatics
 bool site_path(const kmc_batch* b) { return b->site_on || b->elec_on; }
+
+// kernel launches of one window of the colour-phase path: set-up, then per phase
+// screen + run, + the grouped small pass where it runs, or the one-thread-per-
+// fragment pass + run
+uint64_t window_launches(const kmc_batch* b)
+{
+    const bool split = window_split(site_path(b), b->total_items, b->opts.small_pass);
+    return split && window_lane(b->opts.precision, b->opts.small_pass, b->opts.lane_form, b->total_items) !=
+                        LANE_PERSISTENT
+               ? 25
+               : 17;
+}
 
 int check_status(kmc_batch* b)
 {
@@ -761,6 +774,7 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
         return fail(FKMC_EINVAL, "cap_v must be 0 or a multiple of 8 in [8, 256]");
     if (o.schedule < 0 || o.schedule > 2) return fail(FKMC_EINVAL, "schedule must be 0, 1 or 2");
     if (o.small_pass < -1 || o.small_pass > 2) return fail(FKMC_EINVAL, "small_pass must be -1, 0, 1 or 2");
+    if (o.lane_form < 0 || o.lane_form > 2) return fail(FKMC_EINVAL, "lane_form must be 0, 1 or 2");
     if (o.test_stuck_wait_us < 0 || o.test_stuck_wait_us > 2000000)
         return fail(FKMC_EINVAL, "test_stuck_wait_us must be in [0, 2e6]");
 
@@ -866,7 +880,8 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
     b->wctl = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * 2);
     b->perms = (uint32_t*)b->dalloc(sizeof(uint32_t) * n);
     b->act = (ActEntry*)b->dalloc(sizeof(ActEntry) * 3 * std::max<int64_t>(b->total_items, 1));
-    b->act_count = (int32_t*)b->dalloc(sizeof(int32_t) * 24);
+    b->act_count = (int32_t*)b->dalloc(sizeof(int32_t) * ACT_COUNTERS);
+    b->cls = (uint8_t*)b->dalloc((size_t)std::max<int64_t>(b->total_items, 1));
     b->ncell_total = b->nsite_total / 3;
     bool any_fe = false;
     for (int r = 0; r < n; ++r) any_fe = any_fe || b->n_fe[r] > 0;
@@ -880,7 +895,7 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
     }
     if (!b->occ || !b->recs || !b->counts || (o.tracer && !b->tracer) || !b->d_desc || !b->stats ||
         !b->status || !b->scratch || !b->scratch_all || !b->d_reps || !b->d_nvac || !b->wctl || !b->perms ||
-        !b->act || !b->act_count) {
+        !b->act || !b->act_count || !b->cls) {
         b->release();
         delete b;
         return fail(FKMC_ENOMEM, "device allocation failed");
@@ -1044,7 +1059,8 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
         cudaGraph_t graph = nullptr;
         int small_blocks = 1;
         const bool split = window_split(site_path(b), b->total_items, b->opts.small_pass);
-        if (split) CK(small_pass_blocks(b->opts.precision, b->grains_on, &small_blocks), "occupancy query");
+        const int lane = window_lane(b->opts.precision, b->opts.small_pass, b->opts.lane_form, b->total_items);
+        if (split) CK(small_pass_blocks(b->opts.precision, b->grains_on, lane, &small_blocks), "occupancy query");
         if (!b->side_st) {
             CK(cudaStreamCreateWithFlags(&b->side_st, cudaStreamNonBlocking), "stream");
             CK(cudaEventCreateWithFlags(&b->side_fork, cudaEventDisableTiming), "event");
@@ -1054,9 +1070,8 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
         SiteArgs wa = site_args(b);
         if (!site_path(b)) wa.field = nullptr;  // the table-rate run pass
         cudaError_t le = launch_window(b->opts.precision, b->d_desc, b->n, b->total_items, b->wctl, b->perms, b->act,
-                                       b->act_count, b->occ, b->recs, b->counts, b->tracer, b->stats, b->status, b->cap,
-                                       b->run_blocks, small_blocks, split,
-                                       window_lane(b->opts.precision, b->opts.small_pass), wa, b->cap_st, b->side_st,
+                                       b->act_count, b->cls, b->occ, b->recs, b->counts, b->tracer, b->stats, b->status, b->cap,
+                                       b->run_blocks, small_blocks, split, lane, wa, b->cap_st, b->side_st,
                                        b->side_fork, b->side_join);
         cudaError_t ce = cudaStreamEndCapture(b->cap_st, &graph);
         if (le != cudaSuccess) return cuda_fail(le, "window capture");
@@ -1102,7 +1117,7 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
         stats->windows = windows;
         stats->launches =
             (windows > 0 ? b->rclass.size() : 0) +
-            (b->any_global ? (window_split(site_path(b), b->total_items, b->opts.small_pass) ? 25 : 17) * windows : 0) +
+            (b->any_global ? window_launches(b) * windows : 0) +
             extra_launches;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, b->ev0, b->ev1);

@@ -287,7 +287,8 @@ __device__ __forceinline__ void unflatten3(int64_t i, int n0, int n1, int c[3])
 }
 
 // Per-window set-up: colour order of every replica for this window, and the
-// screen counters of the 8 phases cleared.  wctl[0] counts the windows of the
+// counters of the 8 phases cleared (act_count: 3 lists x 8 phases, then the
+// one-thread-per-fragment pass's window tickets of each phase).  wctl[0] counts the windows of the
 // current kmc_run call, wctl[1] holds the offset of the window being run.
 // Every block reads wctl[0] here, so it is advanced later, by the first
 // screen pass of the window (a later launch on the same stream).
@@ -297,17 +298,10 @@ __global__ void k_window_setup(const RepDesc* __restrict__ descs, int nrep, unsi
     const uint64_t wk = wctl[0];
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrep; r += gridDim.x * blockDim.x)
         perms[r] = colour_perm_packed(descs[r].seed, descs[r].replica, descs[r].window + wk);
-    if (blockIdx.x == 0 && threadIdx.x < 24) act_count[threadIdx.x] = 0;
+    if (blockIdx.x == 0 && threadIdx.x < ACT_COUNTERS) act_count[threadIdx.x] = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) wctl[1] = wk;
 }
 
-// Screen pass of a colour phase: one thread per fragment of the phase's colour
-// (every replica).  Fragments with vacancies go to an active list together
-// with their first Philox block, drawn here thirty-two fragments per warp
-// instead of once per fragment-warp.  With `split`, fragments holding one or
-// two vacancies go to lists of their own (act + total_items, act + 2
-// total_items; counters act_count[8 + phase], act_count[16 + phase]) for the
-// small-fragment run pass; the rest (or all) to act, act_count[phase].
 // Fragment of work item `item` in colour phase `phase`: the replica (binary
 // search over the items' prefix) and the fragment index inside it, or false
 // where the replica has fewer fragments of that colour than items or runs in
@@ -345,18 +339,18 @@ __device__ __forceinline__ bool item_fragment(const RepDesc* __restrict__ descs,
 // Screen pass of a colour phase: one thread per fragment of the phase's colour
 // (every replica).  Fragments with vacancies go to an active list together
 // with their first Philox block, drawn here thirty-two fragments per warp
-// instead of once per fragment-warp.  split = 1: fragments holding one or
-// two vacancies go to lists of their own (act + total_items, act + 2
-// total_items; counters act_count[8 + phase], act_count[16 + phase]) for the
-// grouped small-fragment pass; split = 2: fragments holding at most
-// LANE_MAX_V vacancies are left to the one-thread-per-fragment pass; the rest
-// (or all) go to act, act_count[phase].
+// instead of once per fragment-warp.  split = 1: fragments holding one or two
+// vacancies go to lists of their own (act + total_items, act + 2 total_items;
+// counters act_count[8 + phase], act_count[16 + phase]) for the grouped
+// small-fragment pass; split = 2: cls[item] = 1 marks a fragment holding 1 to
+// LANE_REG_MAX_V vacancies, left to the one-thread-per-fragment pass in
+// registers; the rest (or all) go to act, act_count[phase].
 template <int PREC>
 __global__ void __launch_bounds__(256) k_screen(const RepDesc* __restrict__ descs, int nrep, int64_t total_items,
                                                 int phase, unsigned long long* wctl,
                                                 const uint32_t* __restrict__ perms,
                                                 const int32_t* __restrict__ counts, ActEntry* act,
-                                                int32_t* act_count, int split)
+                                                int32_t* act_count, int split, uint8_t* cls)
 {
     const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     // the window count advances here (nothing in this launch reads wctl[0])
@@ -366,10 +360,13 @@ __global__ void __launch_bounds__(256) k_screen(const RepDesc* __restrict__ desc
     ActEntry e;
     int lo;
     int64_t fid;
+    if (split == 2 && item < total_items) cls[item] = 0;
     if (item < total_items && item_fragment(descs, nrep, item, phase, perms, lo, fid)) {
         const RepDesc& D = descs[lo];
         const int nv = counts[D.frag_base + fid];
-        if (nv > 0 && !(split == 2 && nv <= LANE_MAX_V)) {
+        const bool sparse = split == 2 && nv > 0 && nv <= LANE_REG_MAX_V;
+        if (split == 2) cls[item] = sparse;
+        if (nv > 0 && !sparse) {
             keep = true;
             list = split == 1 && nv <= 2 ? nv : 0;
             const uint64_t w = D.window + wctl[1];
@@ -889,39 +886,73 @@ __global__ void __launch_bounds__(128, 8) k_run_small(const RepDesc* __restrict_
 }
 
 // ------------------------------------------------------------------ one thread per fragment
+// The neighbour table per site type for the one-thread-per-fragment pass:
+// x, y = 8 bits per neighbour n (n-th byte): t2 | (dc_x+1) << 2 | (dc_y+1) << 4 |
+// (dc_z+1) << 6; z = 2 bits per neighbour: d_z + 1.
+__device__ __align__(16) uint4 g_lgeo[3];
+
 // Rate types of the 8 events of the vacancy at `key` (mixed form), packed as
 // nibbles n = type + 1 (0: no event), and the sum of their fixed-point rates.
 // The 8 neighbour words are read from L2 (ld.global.cg: this thread's own
-// exchanges are atomics there) before any is used.
+// exchanges are atomics there) before any is used.  Away from the lattice's
+// faces no coordinate wraps, and a neighbour's row is the vacancy's row plus
+// a 32-bit offset.
 template <bool GRAIN>
 __device__ __forceinline__ uint32_t lane_types(const RepDesc& D, const uint32_t* occ, const uint8_t* gb, uint64_t key,
                                                unsigned long long& sum)
 {
     int t, x, y, z;
     split_key(key, t, x, y, z);
+    const uint4 geo = __ldg(g_lgeo + t);
+    const uint64_t g8 = ((uint64_t)geo.y << 32) | geo.x;
+    const int L0 = D.L[0], L1 = D.L[1], L2 = D.L[2];
+    const uint32_t* occ_r = occ + D.occ_word_off;
+    const int64_t rw = D.row_words;
     uint32_t w[8];
+    uint32_t xlo = 0;   // nibble n: x of neighbour n, mod 16
+    uint32_t gbit = 0;  // grains: bit n set where neighbour n's cell is a boundary cell
+    int64_t cells = 0;
+    if constexpr (GRAIN) cells = D.site_off / 3;
+    if (x >= 1 && x <= L0 - 2 && y >= 1 && y <= L1 - 2 && z >= 1 && z <= L2 - 2) {
+        const int rb = (t * L2 + z) * L1 + y;
+        const int plane = L1 * L2;
 #pragma unroll
-    for (int n = 0; n < 8; ++n) {
-        const NbEntry nb = nb_entry(t, n);
-        w[n] = __ldcg(occ + occ_word(D, nb.t2, wrapc(x + nb.dc[0], D.L[0]), wrapc(y + nb.dc[1], D.L[1]),
-                                     wrapc(z + nb.dc[2], D.L[2])));
+        for (int n = 0; n < 8; ++n) {
+            const uint32_t f = (uint32_t)(g8 >> (8 * n));
+            const int t2 = (int)(f & 3u);
+            const int jx = x + (int)((f >> 2) & 3u) - 1;
+            const int dcy = (int)((f >> 4) & 3u) - 1, dcz = (int)((f >> 6) & 3u) - 1;
+            const int row = rb + (t2 - t) * plane + dcz * L1 + dcy;
+            w[n] = __ldcg(occ_r + (int64_t)row * rw + (jx >> 4));
+            xlo |= (uint32_t)(jx & 15) << (4 * n);
+            if constexpr (GRAIN)
+                gbit |= (uint32_t)__ldg(gb + cells + ((int64_t)(z + dcz) * L1 + (y + dcy)) * L0 + jx) << n;
+        }
+    } else {
+#pragma unroll
+        for (int n = 0; n < 8; ++n) {
+            const uint32_t f = (uint32_t)(g8 >> (8 * n));
+            const int t2 = (int)(f & 3u);
+            const int jx = wrapc(x + (int)((f >> 2) & 3u) - 1, L0);
+            const int jy = wrapc(y + (int)((f >> 4) & 3u) - 1, L1);
+            const int jz = wrapc(z + (int)((f >> 6) & 3u) - 1, L2);
+            w[n] = __ldcg(occ_r + ((int64_t)(t2 * L2 + jz) * L1 + jy) * rw + (jx >> 4));
+            xlo |= (uint32_t)(jx & 15) << (4 * n);
+            if constexpr (GRAIN) gbit |= (uint32_t)__ldg(gb + cells + ((int64_t)jz * L1 + jy) * L0 + jx) << n;
+        }
     }
-    uint8_t gs = 0;
-    if constexpr (GRAIN) gs = __ldg(gb + cell_index(D, x, y, z));
+    uint32_t gs = 0;
+    if constexpr (GRAIN) gs = __ldg(gb + cells + ((int64_t)z * L1 + y) * L0 + x);
     uint32_t packed = 0;
     unsigned long long s = 0ull;
 #pragma unroll
     for (int n = 0; n < 8; ++n) {
-        const NbEntry nb = nb_entry(t, n);
-        const int jx = wrapc(x + nb.dc[0], D.L[0]);
-        const int code = (int)((w[n] >> occ_shift(jx)) & 3u);
+        const int code = (int)((w[n] >> (2 * ((xlo >> (4 * n)) & 15u))) & 3u);
         if (code != SP_V) {
-            int ty = code * 3 + nb.d[2] + 1;
+            int ty = code * 3 + (int)((geo.z >> (2 * n)) & 3u);
             unsigned long long q;
             if constexpr (GRAIN) {
-                const int jy = wrapc(y + nb.dc[1], D.L[1]);
-                const int jz = wrapc(z + nb.dc[2], D.L[2]);
-                if (gs | __ldg(gb + cell_index(D, jx, jy, jz))) {
+                if (gs | ((gbit >> n) & 1u)) {
                     q = D.qg[ty];
                     ty += 6;
                 } else {
@@ -968,34 +999,38 @@ __device__ __forceinline__ void order_pair(VacRec& a, VacRec& b)
     }
 }
 
-// Run pass for fragments holding one to LANE_MAX_V vacancies, mixed form: one
-// thread per fragment of the phase's colour (the screen pass's items), with
-// the fragment's records, packed rate types and per-vacancy rate sums in
-// registers, so that a warp runs 32 fragments.  The mixed form's sums are
-// exact integers: the total and the first event whose inclusive prefix
-// exceeds the target are those of the warp passes' scans over the same slot
-// order (ascending site).  The draws are the same Philox words (event i:
-// block i/2, words 1 and 0 for even i, 3 and 2 for odd i), the window test,
-// selection and exchange are the same, so the trajectory is the same.  After
-// a hop only the moved vacancy and those within a half-cell of its old or new
-// site re-read their neighbour words; every other rate is unchanged.
+// One colour phase of the mixed form for the fragments the screen pass
+// classed as sparse (one to LANE_REG_MAX_V vacancies): one thread per work
+// item, with the fragment's records, packed rate types and per-vacancy rate
+// sums in registers, so that a warp runs 32 fragments.  It runs beside the
+// warp-per-fragment pass on the screen's list; the class byte (not the count,
+// which that pass rewrites when it finishes a fragment) decides which pass
+// owns a fragment.  The mixed form's sums are exact integers: the total and
+// the first event whose inclusive prefix exceeds the target are those of the
+// warp passes' scans over the same slot order (ascending site).  The draws
+// are the same Philox words (event i: block i/2, words 1 and 0 for even i, 3
+// and 2 for odd i), the window test, selection and exchange are the same, so
+// the trajectory is the same.  After a hop only the moved vacancy and those
+// within a half-cell of its old or new site re-read their neighbour words;
+// every other rate is unchanged.
 template <bool GRAIN>
-__global__ void __launch_bounds__(128) k_run_lane(const RepDesc* __restrict__ descs, int nrep, int64_t total_items,
-                                                  int phase, const unsigned long long* wctl,
-                                                  const uint32_t* __restrict__ perms, uint32_t* occ, VacRec* recs,
-                                                  int32_t* counts, int32_t* tracer, unsigned long long* stats,
-                                                  uint32_t* status, int cap, const uint8_t* gb)
+__global__ void __launch_bounds__(128) k_run_lane_reg(const RepDesc* __restrict__ descs, int nrep,
+                                                      int64_t total_items, int phase, const unsigned long long* wctl,
+                                                      const uint32_t* __restrict__ perms,
+                                                      const uint8_t* __restrict__ cls, uint32_t* occ, VacRec* recs,
+                                                      int32_t* counts, int32_t* tracer, unsigned long long* stats,
+                                                      uint32_t* status, int cap, const uint8_t* gb)
 {
-    constexpr int NL = LANE_MAX_V;
+    constexpr int NL = LANE_REG_MAX_V;
     constexpr unsigned FULL = 0xffffffffu;
     const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int rep = -1;
     int64_t fid = 0;
     int nv = 0;
-    if (item < total_items && item_fragment(descs, nrep, item, phase, perms, rep, fid))
+    if (item < total_items && cls[item] && item_fragment(descs, nrep, item, phase, perms, rep, fid))
         nv = counts[descs[rep].frag_base + fid];
     uint32_t hops = 0, nhand = 0;
-    if (nv > 0 && nv <= NL) {
+    if (nv > 0) {
         const RepDesc& D = descs[rep];
         const int64_t g = D.frag_base + fid;
         if (nv > cap) {
@@ -1191,6 +1226,391 @@ __global__ void __launch_bounds__(128) k_run_lane(const RepDesc* __restrict__ de
     } else {
         if (hops) atomicAdd(stats + 2 * rep, (unsigned long long)hops);
         if (nhand) atomicAdd(stats + 2 * rep + 1, (unsigned long long)nhand);
+    }
+}
+
+// n-th (from 0) set bit of m; m holds more than n set bits
+__device__ __forceinline__ int nth_set_bit(unsigned m, int n)
+{
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const int c = __popc((m >> pos) & ((1u << w) - 1u));
+        if (n >= c) {
+            n -= c;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
+constexpr int LANE_THREADS = 128;
+
+// The fragment slots of the lanes of one block in shared memory: slot k of
+// thread x at [k][x], so that a warp's accesses to one slot are contiguous.
+struct LaneSlots {
+    unsigned long long key[LANE_MAX_V][LANE_THREADS];
+    unsigned long long sum[LANE_MAX_V][LANE_THREADS];  // fixed-point rate sum of the slot's 8 events
+    int32_t d[3][LANE_MAX_V][LANE_THREADS];
+    uint32_t id[LANE_MAX_V][LANE_THREADS];
+    uint32_t ty[LANE_MAX_V][LANE_THREADS];             // packed rate types (lane_types)
+};
+
+__device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src)
+{
+    const unsigned lo = __shfl_sync(0xffffffffu, (unsigned)v, src);
+    const unsigned hi = __shfl_sync(0xffffffffu, (unsigned)(v >> 32), src);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+// One colour phase of the mixed form for every fragment of the phase's colour,
+// one fragment per lane at a time.  A persistent grid: the warps take windows
+// of 32 consecutive work items (fragments) from a ticket counter, each
+// window's vacancy counts loaded while the one before is in use and its
+// ticket drawn a window earlier still.  Fragments holding
+// more than LANE_MAX_V vacancies go to the warp-per-fragment pass (act list 0,
+// with their first Philox block), which runs after this one.
+//
+// Each lane runs a small state machine, one step of each kind per loop turn:
+//   take      a lane without a fragment takes the next one of the window that
+//             holds 1..LANE_MAX_V vacancies: records to its shared-memory
+//             slots, slot order = ascending site (a rank permutation), draw
+//             block 0;
+//   rates     one slot whose rate types are stale reads its 8 neighbour words;
+//   event     the window test, then BKL selection and the exchange, or the
+//             fragment's records are written back.
+// A lane therefore moves on to its next fragment as soon as its current one
+// ends, instead of waiting for the warp's longest event chain.
+//
+// Same trajectory as the warp passes: the mixed form's sums are exact
+// integers, so the total and the first event whose inclusive prefix exceeds
+// the target (slot order, then neighbour order) are those of their scans; the
+// draws are the same Philox words (event i: block i/2, words 1 and 0 for even
+// i, 3 and 2 for odd i); the window test, selection and exchange are the same.
+// After a hop only the moved vacancy and those within a half-cell of its old
+// or new site re-read their neighbour words; every other rate is unchanged.
+template <bool GRAIN>
+__global__ void __launch_bounds__(LANE_THREADS) k_run_lane(const RepDesc* __restrict__ descs, int nrep,
+                                                           int64_t total_items, int phase, unsigned long long* wctl,
+                                                           const uint32_t* __restrict__ perms, ActEntry* act,
+                                                           int32_t* act_count, uint32_t* occ, VacRec* recs,
+                                                           int32_t* counts, int32_t* tracer,
+                                                           unsigned long long* stats, uint32_t* status, int cap,
+                                                           const uint8_t* gb)
+{
+    constexpr int NL = LANE_MAX_V;
+    static_assert(NL <= 8, "slot order packs 8 slot indices of 4 bits");
+    constexpr unsigned FULL = 0xffffffffu;
+    __shared__ LaneSlots S;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const uint64_t wk = wctl[1];
+    // the window count advances here (nothing in this launch reads wctl[0])
+    if (phase == 0 && blockIdx.x == 0 && tid == 0) wctl[0] = wk + 1;
+
+    // windows of 32 items from the phase's ticket counter
+    int32_t* ticket = act_count + 24 + phase;
+    const int64_t nwin = (total_items + 31) / 32;
+    auto item_count = [&](int64_t it, int& rp, int64_t& fd) -> int {
+        if (it >= total_items || !item_fragment(descs, nrep, it, phase, perms, rp, fd)) return 0;
+        return __ldcg(counts + descs[rp].frag_base + fd);
+    };
+    int64_t wbase = 0;   // window in use: lane l describes item wbase + l
+    int64_t next_win;    // the next window (its counts are loading)
+    int drawn = 0;       // lane 0: the ticket after it
+    int cur_rep = 0, cur_cnt = 0;
+    int64_t cur_fid = 0;
+    unsigned avail = 0;  // window items not yet taken that hold 1..NL vacancies
+    int next_cnt;
+    {
+        int t0 = 0;
+        if (lane == 0) t0 = atomicAdd(ticket, 1);
+        next_win = __shfl_sync(FULL, t0, 0);
+        if (lane == 0) drawn = atomicAdd(ticket, 1);
+        int rp;
+        int64_t fd;
+        next_cnt = item_count(next_win * 32 + lane, rp, fd);
+    }
+
+    // the lane's fragment
+    bool active = false;
+    int rep = 0, nv = 0;
+    int64_t fid = 0, g = 0;
+    uint64_t wnd = 0;
+    uint32_t ord = 0, alive = 0, pending = 0, nhand = 0;
+    int lo_c[3] = {0, 0, 0}, hi_c[3] = {0, 0, 0};
+    U64x4 blk{};
+    double clock = 0.0;
+    uint64_t i = 0;
+    // hop and hand-off counts of the lane, for replica acc_rep
+    int acc_rep = -1;
+    unsigned long long acc_hops = 0, acc_hand = 0;
+
+    for (;;) {
+        // ---- take: lanes without a fragment take the window's next ones
+        for (;;) {
+            const unsigned need = __ballot_sync(FULL, !active);
+            if (need == 0) break;
+            if (avail == 0) {
+                if (next_win >= nwin) break;  // every window is taken
+                wbase = next_win * 32;
+                cur_cnt = next_cnt;
+                if (!item_fragment(descs, nrep, wbase + lane, phase, perms, cur_rep, cur_fid)) cur_cnt = 0;
+                next_win = __shfl_sync(FULL, drawn, 0);
+                if (lane == 0 && next_win < nwin) drawn = atomicAdd(ticket, 1);
+                {
+                    int rp;
+                    int64_t fd;
+                    next_cnt = item_count(next_win * 32 + lane, rp, fd);
+                }
+                // fragments too dense for a lane: to the warp pass, with their first draws
+                const bool big = cur_cnt > NL;
+                const unsigned bal = __ballot_sync(FULL, big);
+                if (bal) {
+                    int base = 0;
+                    if (lane == __ffs(bal) - 1) base = atomicAdd(act_count + phase, __popc(bal));
+                    base = __shfl_sync(FULL, base, __ffs(bal) - 1);
+                    if (big) {
+                        const RepDesc& Dc = descs[cur_rep];
+                        const U64x4 b0 = philox4x64((uint64_t)cur_fid, Dc.window + wk, 0, 0, Dc.seed,
+                                                    key_word(Dc.replica, PURPOSE_HOP));
+                        ActEntry e;
+                        e.rep = cur_rep;
+                        e.nv = cur_cnt;
+                        e.fid = cur_fid;
+                        e.xs[0] = b0.x[1];
+                        e.xs[1] = b0.x[3];
+                        e.E[0] = (uint64_t)__float_as_uint(neglog32(b0.x[0]));
+                        e.E[1] = (uint64_t)__float_as_uint(neglog32(b0.x[2]));
+                        act[base + __popc(bal & below)] = e;
+                    }
+                }
+                avail = __ballot_sync(FULL, cur_cnt > 0 && cur_cnt <= NL);
+                continue;
+            }
+            const int na = __popc(avail), take = min(na, __popc(need));
+            const int k = __popc(need & below);
+            const bool mine = !active && k < take;
+            const int pos = mine ? nth_set_bit(avail, k) : lane;
+            const int c = __shfl_sync(FULL, cur_cnt, pos);
+            const int rp = __shfl_sync(FULL, cur_rep, pos);
+            const uint64_t fd = shfl_u64((uint64_t)cur_fid, pos);
+            avail = take == na ? 0u : avail & ~((2u << nth_set_bit(avail, take - 1)) - 1u);
+            if (mine) {
+                const RepDesc& D = descs[rp];
+                rep = rp;
+                fid = (int64_t)fd;
+                g = D.frag_base + fid;
+                nv = c;
+                if (nv > cap) {
+                    atomicOr(status, STATUS_OVERFLOW);
+                    nv = cap;
+                }
+                // records to the slots; slot order by ascending site
+                uint32_t rank = 0;  // nibble k: rank of record k
+                for (int q = 0; q < nv; ++q) {
+                    const VacRec r = recs[g * cap + q];
+                    S.key[q][tid] = r.key;
+                    S.d[0][q][tid] = r.d[0];
+                    S.d[1][q][tid] = r.d[1];
+                    S.d[2][q][tid] = r.d[2];
+                    S.id[q][tid] = r.id;
+                    uint32_t rq = 0;
+                    for (int j = 0; j < q; ++j) {
+                        const bool less = S.key[j][tid] < r.key;
+                        rq += less;
+                        rank += (uint32_t)(!less) << (4 * j);
+                    }
+                    rank |= rq << (4 * q);
+                }
+                ord = 0;
+                for (int q = 0; q < nv; ++q) ord |= (uint32_t)q << (4 * ((rank >> (4 * q)) & 15u));
+                int f[3];
+                unflatten3(fid, D.nf[0], D.nf[1], f);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    lo_c[d] = frag_start(f[d], D.base[d], D.rem[d]);
+                    hi_c[d] = frag_start(f[d] + 1, D.base[d], D.rem[d]);
+                }
+                alive = pending = (1u << nv) - 1u;
+                wnd = D.window + wk;
+                blk = philox4x64((uint64_t)fid, wnd, 0, 0, D.seed, key_word(D.replica, PURPOSE_HOP));
+                clock = 0.0;
+                i = 0;
+                nhand = 0;
+                if (rep != acc_rep) {
+                    if (acc_hops) atomicAdd(stats + 2 * acc_rep, acc_hops);
+                    if (acc_hand) atomicAdd(stats + 2 * acc_rep + 1, acc_hand);
+                    acc_hops = acc_hand = 0;
+                    acc_rep = rep;
+                }
+                active = true;
+            }
+        }
+        if (!__any_sync(FULL, active)) break;
+        const RepDesc& D = descs[rep];
+
+        // ---- rates: one stale slot
+        if (active && pending) {
+            const int k = __ffs(pending) - 1;
+            pending &= pending - 1u;
+            unsigned long long sk;
+            S.ty[k][tid] = lane_types<GRAIN>(D, occ, gb, S.key[k][tid], sk);
+            S.sum[k][tid] = sk;
+        }
+
+        // ---- event: the window test, then selection and exchange, or the end of the visit
+        if (active && !pending) {
+            unsigned long long total = 0ull;
+            for (int k = 0; k < nv; ++k)
+                if ((alive >> k) & 1u) total += S.sum[k][tid];
+            bool fin = total == 0ull;
+            if (!fin && i >= MAX_EVENTS_PER_PHASE) {
+                atomicOr(status, STATUS_EVENT_LIMIT);
+                fin = true;
+            }
+            if (!fin) {
+                if ((i & 1) == 0 && i > 0)
+                    blk = philox4x64((uint64_t)fid, wnd, i >> 1, 0, D.seed, key_word(D.replica, PURPOSE_HOP));
+                const bool odd = (i & 1) != 0;
+                const uint64_t xs = odd ? blk.x[3] : blk.x[1];
+                const float Ef = neglog32(odd ? blk.x[2] : blk.x[0]);
+                const float ratio = __fdiv_rn(Ef, __ull2float_rn(total));
+                const double dth = __dmul_rn((double)ratio, D.two_pow_F);
+                if (__dadd_rn(clock, dth) > D.theta_tau) {
+                    fin = true;
+                } else {
+                    // slot m and neighbour n of the first event whose prefix exceeds the target
+                    const unsigned long long target = __umul64hi(xs, total);
+                    unsigned long long acc = 0ull;
+                    int m = (int)(ord & 15u);
+                    for (int sl = 0; sl < nv; ++sl) {
+                        const int k = (int)((ord >> (4 * sl)) & 15u);
+                        if ((alive >> k) & 1u) {
+                            const unsigned long long sk = S.sum[k][tid];
+                            m = k;
+                            if (acc + sk > target) break;
+                            acc += sk;
+                        }
+                    }
+                    const uint32_t tym = S.ty[m][tid];
+                    int n = 7;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int nib = (int)((tym >> (4 * e)) & 15u);
+                        if (nib) {
+                            const int tv = nib - 1;
+                            acc += GRAIN ? (tv < 6 ? D.q[tv] : D.qg[tv - 6]) : D.q[tv];
+                            if (acc > target) {
+                                n = e;
+                                break;
+                            }
+                        }
+                    }
+                    // the exchange
+                    const uint64_t s_key = S.key[m][tid];
+                    int t, x, y, z;
+                    split_key(s_key, t, x, y, z);
+                    const NbEntry nb = nb_entry(t, n);
+                    const int jx = wrapc(x + nb.dc[0], D.L[0]);
+                    const int jy = wrapc(y + nb.dc[1], D.L[1]);
+                    const int jz = wrapc(z + nb.dc[2], D.L[2]);
+                    const int tyv = (int)((tym >> (4 * n)) & 15u) - 1;
+                    const uint32_t ion = (uint32_t)((tyv % 6) / 3);
+                    atomicXor(occ + occ_word(D, t, x, y, z), ((uint32_t)SP_V ^ ion) << occ_shift(x));
+                    atomicXor(occ + occ_word(D, nb.t2, jx, jy, jz), (ion ^ (uint32_t)SP_V) << occ_shift(jx));
+                    const int d0 = S.d[0][m][tid] + nb.d[0];
+                    const int d1 = S.d[1][m][tid] + nb.d[1];
+                    const int d2 = S.d[2][m][tid] + nb.d[2];
+                    if (tracer) {
+                        const int64_t s_lin = (((int64_t)t * D.L[2] + z) * D.L[1] + y) * D.L[0] + x;
+                        const int64_t j_lin = (((int64_t)nb.t2 * D.L[2] + jz) * D.L[1] + jy) * D.L[0] + jx;
+                        int32_t* ts = tracer + 3 * (D.site_off + s_lin);
+                        int32_t* tj = tracer + 3 * (D.site_off + j_lin);
+                        ts[0] = tj[0] - nb.d[0];
+                        ts[1] = tj[1] - nb.d[1];
+                        ts[2] = tj[2] - nb.d[2];
+                        tj[0] = tj[1] = tj[2] = 0;
+                    }
+                    const uint64_t j_key = make_key(nb.t2, jx, jy, jz);
+                    const bool owned = jx >= lo_c[0] && jx < hi_c[0] && jy >= lo_c[1] && jy < hi_c[1] &&
+                                       jz >= lo_c[2] && jz < hi_c[2];
+                    if (owned) {
+                        S.key[m][tid] = j_key;
+                        S.d[0][m][tid] = d0;
+                        S.d[1][m][tid] = d1;
+                        S.d[2][m][tid] = d2;
+                    } else {
+                        const int gx = frag_of(jx, D.base[0], D.rem[0]);
+                        const int gy = frag_of(jy, D.base[1], D.rem[1]);
+                        const int gz = frag_of(jz, D.base[2], D.rem[2]);
+                        const int64_t g2 = D.frag_base + ((int64_t)gz * D.nf[1] + gy) * D.nf[0] + gx;
+                        const int slot = atomicAdd(counts + g2, 1);
+                        if (slot < cap) {
+                            VacRec r;
+                            r.key = j_key;
+                            r.d[0] = d0;
+                            r.d[1] = d1;
+                            r.d[2] = d2;
+                            r.id = S.id[m][tid];
+                            recs[g2 * cap + slot] = r;
+                        } else {
+                            atomicOr(status, STATUS_OVERFLOW);
+                        }
+                        alive &= ~(1u << m);
+                        ++nhand;
+                    }
+                    __threadfence_block();
+                    clock = __dadd_rn(clock, dth);
+                    ++i;
+                    // stale rates: the moved vacancy's, and those of vacancies near s or j
+                    pending = owned ? 1u << m : 0u;
+                    for (int k = 0; k < nv; ++k) {
+                        if (k != m && ((alive >> k) & 1u)) {
+                            const uint64_t kk = S.key[k][tid];
+                            if (within_half_cell(D, kk, s_key) || within_half_cell(D, kk, j_key)) pending |= 1u << k;
+                        }
+                    }
+                }
+            }
+            if (fin) {
+                // surviving records stay with the fragment, in slot order
+                int pos = 0;
+                for (int sl = 0; sl < nv; ++sl) {
+                    const int k = (int)((ord >> (4 * sl)) & 15u);
+                    if ((alive >> k) & 1u) {
+                        VacRec r;
+                        r.key = S.key[k][tid];
+                        r.d[0] = S.d[0][k][tid];
+                        r.d[1] = S.d[1][k][tid];
+                        r.d[2] = S.d[2][k][tid];
+                        r.id = S.id[k][tid];
+                        recs[g * cap + pos++] = r;
+                    }
+                }
+                counts[g] = pos;
+                acc_hops += i;
+                acc_hand += nhand;
+                active = false;
+            }
+        }
+    }
+    // counters: one atomic per warp where its lanes share a replica
+    const int r0 = __shfl_sync(FULL, acc_rep, 0);
+    if (__all_sync(FULL, acc_rep == r0 || (acc_hops == 0 && acc_hand == 0)) && r0 >= 0) {
+        unsigned long long hs = acc_hops, ns = acc_hand;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            hs += __shfl_xor_sync(FULL, hs, o);
+            ns += __shfl_xor_sync(FULL, ns, o);
+        }
+        if (lane == 0) {
+            if (hs) atomicAdd(stats + 2 * r0, hs);
+            if (ns) atomicAdd(stats + 2 * r0 + 1, ns);
+        }
+    } else {
+        if (acc_hops) atomicAdd(stats + 2 * acc_rep, acc_hops);
+        if (acc_hand) atomicAdd(stats + 2 * acc_rep + 1, acc_hand);
     }
 }
 
@@ -1481,8 +1901,22 @@ __global__ void k_moments_ion(RepDesc D, const uint32_t* occ, const int32_t* tra
 // ------------------------------------------------------------------ launchers
 cudaError_t upload_neighbours(const NbEntry* host)
 {
-    const cudaError_t e = cudaMemcpyToSymbol(c_nb, host, sizeof(NbEntry) * 24);
-    return e != cudaSuccess ? e : cudaMemcpyToSymbol(g_nb, host, sizeof(NbEntry) * 24);
+    uint4 lg[3];
+    for (int t = 0; t < 3; ++t) {
+        uint64_t g8 = 0;
+        uint32_t dz = 0;
+        for (int n = 0; n < 8; ++n) {
+            const NbEntry& e = host[8 * t + n];
+            const uint64_t f = (uint64_t)e.t2 | (uint64_t)(e.dc[0] + 1) << 2 | (uint64_t)(e.dc[1] + 1) << 4 |
+                               (uint64_t)(e.dc[2] + 1) << 6;
+            g8 |= f << (8 * n);
+            dz |= (uint32_t)(e.d[2] + 1) << (2 * n);
+        }
+        lg[t] = make_uint4((uint32_t)g8, (uint32_t)(g8 >> 32), dz, 0u);
+    }
+    cudaError_t e = cudaMemcpyToSymbol(c_nb, host, sizeof(NbEntry) * 24);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_nb, host, sizeof(NbEntry) * 24);
+    return e != cudaSuccess ? e : cudaMemcpyToSymbol(g_lgeo, lg, sizeof lg);
 }
 
 cudaError_t launch_init(const RepDesc& D, int b_bits, int64_t n_vac, int64_t n_total, uint32_t* occ,
@@ -1518,12 +1952,29 @@ bool window_split(bool site, int64_t total_items, int mode)
     return !site && (mode > 0 || (mode == 0 && total_items >= SPLIT_MIN_ITEMS));
 }
 
-// The mixed form runs its small fragments one thread per fragment (up to
-// LANE_MAX_V vacancies), unless the grouped pass is asked for (mode 2).
-bool window_lane(int prec, int mode) { return prec == 1 && mode != 2; }
+// The mixed form runs its small fragments one thread per fragment, unless the
+// grouped pass is asked for (small_pass 2): in registers beside the general
+// pass, or, on phases of LANE_PERSIST_ITEMS fragments or more, in the
+// persistent form (up to LANE_MAX_V vacancies in shared memory, the general
+// pass after it).  On the bias cube (0.1% V, edge 8, n_tau 0.5; A/B on one
+// GB300, identical hop counts) the register form ran 1.07e9 / 1.15e9 /
+// 1.19e9 / 1.23e9 hops/s on 1000^3 / 1400^3 / 1800^3 / 2500^3, the
+// persistent form 0.86e9 / 1.18e9 / 1.32e9 / 1.42e9.
+int window_lane(int prec, int mode, int form, int64_t total_items)
+{
+    if (prec != 1 || mode == 2) return LANE_NONE;
+    if (form == 1) return LANE_REGISTERS;
+    if (form == 2) return LANE_PERSISTENT;
+    return total_items >= LANE_PERSIST_ITEMS ? LANE_PERSISTENT : LANE_REGISTERS;
+}
 
-using LaneFn = void (*)(const RepDesc*, int, int64_t, int, const unsigned long long*, const uint32_t*, uint32_t*,
-                        VacRec*, int32_t*, int32_t*, unsigned long long*, uint32_t*, int, const uint8_t*);
+using LaneFn = void (*)(const RepDesc*, int, int64_t, int, unsigned long long*, const uint32_t*, ActEntry*, int32_t*,
+                        uint32_t*, VacRec*, int32_t*, int32_t*, unsigned long long*, uint32_t*, int, const uint8_t*);
+using LaneRegFn = void (*)(const RepDesc*, int, int64_t, int, const unsigned long long*, const uint32_t*,
+                           const uint8_t*, uint32_t*, VacRec*, int32_t*, int32_t*, unsigned long long*, uint32_t*, int,
+                           const uint8_t*);
+
+static LaneFn lane_kernel(bool grain) { return grain ? k_run_lane<true> : k_run_lane<false>; }
 
 using SmallFn = void (*)(const RepDesc*, const ActEntry*, int64_t, const int32_t*, int, const unsigned long long*,
                         uint32_t*, VacRec*, int32_t*, int32_t*, unsigned long long*, uint32_t*, int, const uint8_t*);
@@ -1562,12 +2013,20 @@ cudaError_t run_pass_blocks(int prec, int cap, bool site, bool grain, int* block
     return e;
 }
 
-cudaError_t small_pass_blocks(int prec, bool grain, int* blocks)
+// Blocks of the small-fragment pass: as many as fit on the GPU at once (the
+// grouped pass strides over its lists; the one-thread-per-fragment pass is a
+// persistent grid whose warps split the phase's fragments).
+cudaError_t small_pass_blocks(int prec, bool grain, int lane, int* blocks)
 {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, small_kernel(prec, grain), 128, 0);
+    if (e == cudaSuccess) {
+        if (lane == LANE_PERSISTENT)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lane_kernel(grain), LANE_THREADS, 0);
+        else
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, small_kernel(prec, grain), 128, 0);
+    }
     *blocks = std::max(1, sms * std::max(per_sm, 1));
     return e;
 }
@@ -1579,9 +2038,9 @@ cudaError_t small_pass_blocks(int prec, bool grain, int* blocks)
 // `sa.gbound` non-null the grain tables.
 cudaError_t launch_window(int prec, const RepDesc* d_descs, int nrep, int64_t total_items,
                           unsigned long long* wctl, uint32_t* perms, ActEntry* act, int32_t* act_count,
-                          uint32_t* occ, VacRec* recs, int32_t* counts, int32_t* tracer,
+                          uint8_t* cls, uint32_t* occ, VacRec* recs, int32_t* counts, int32_t* tracer,
                           unsigned long long* stats, uint32_t* status, int cap, int run_blocks,
-                          int small_blocks, bool split_pass, bool lane_pass, const SiteArgs& sa, cudaStream_t st,
+                          int small_blocks, bool split_pass, int lane_form, const SiteArgs& sa, cudaStream_t st,
                           cudaStream_t side, cudaEvent_t fork, cudaEvent_t join)
 {
     if (total_items <= 0) return cudaSuccess;
@@ -1590,33 +2049,33 @@ cudaError_t launch_window(int prec, const RepDesc* d_descs, int nrep, int64_t to
     const int64_t sblocks = (total_items + 255) / 256;
     const size_t smem = phase_smem_bytes(cap, site);
     const RunFn run = run_kernel(site ? 0 : prec, site, grain);
-    const bool lane = split_pass && !site && lane_pass && prec == 1;
-    const int split = split_pass && !site ? (lane ? 2 : 1) : 0;
+    const int lane = split_pass && !site && prec == 1 ? lane_form : LANE_NONE;
+    const int split = !split_pass || site ? 0 : (lane == LANE_REGISTERS ? 2 : (lane == LANE_NONE ? 1 : 0));
     const SmallFn small = small_kernel(prec, grain);
-    const LaneFn lanek = grain ? k_run_lane<true> : k_run_lane<false>;
+    const LaneFn lanek = lane_kernel(grain);
+    const LaneRegFn lanereg = grain ? k_run_lane_reg<true> : k_run_lane_reg<false>;
     for (int p = 0; p < 8; ++p) {
-        if (lane) {  // reads only the counts: beside the screen and the general pass
-            cudaError_t e = cudaEventRecord(fork, st);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
-            if (e != cudaSuccess) return e;
-            lanek<<<(unsigned)((total_items + 127) / 128), 128, 0, side>>>(d_descs, nrep, total_items, p, wctl, perms,
-                                                                          occ, recs, counts, tracer, stats, status,
-                                                                          cap, sa.gbound);
-            e = cudaEventRecord(join, side);
-            if (e != cudaSuccess) return e;
-        }
-        if (site || prec == 0)
+        if (lane == LANE_PERSISTENT) {  // every fragment of the colour; the dense ones listed for the warp pass after it
+            lanek<<<small_blocks, LANE_THREADS, 0, st>>>(d_descs, nrep, total_items, p, wctl, perms, act, act_count,
+                                                        occ, recs, counts, tracer, stats, status, cap, sa.gbound);
+        } else if (site || prec == 0) {
             k_screen<0><<<(unsigned)sblocks, 256, 0, st>>>(d_descs, nrep, total_items, p, wctl, perms, counts, act,
-                                                           act_count, split);
-        else
+                                                           act_count, split, cls);
+        } else {
             k_screen<1><<<(unsigned)sblocks, 256, 0, st>>>(d_descs, nrep, total_items, p, wctl, perms, counts, act,
-                                                           act_count, split);
-        if (split == 1) {  // the two run passes touch disjoint fragments: run them side by side
+                                                           act_count, split, cls);
+        }
+        if (split) {  // the small-fragment pass and the general one touch disjoint fragments: side by side
             cudaError_t e = cudaEventRecord(fork, st);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
             if (e != cudaSuccess) return e;
-            small<<<small_blocks, 128, 0, side>>>(d_descs, act, total_items, act_count, p, wctl, occ, recs, counts,
-                                                  tracer, stats, status, cap, sa.gbound);
+            if (split == 1)
+                small<<<small_blocks, 128, 0, side>>>(d_descs, act, total_items, act_count, p, wctl, occ, recs,
+                                                      counts, tracer, stats, status, cap, sa.gbound);
+            else
+                lanereg<<<(unsigned)((total_items + 127) / 128), 128, 0, side>>>(
+                    d_descs, nrep, total_items, p, wctl, perms, cls, occ, recs, counts, tracer, stats, status, cap,
+                    sa.gbound);
             e = cudaEventRecord(join, side);
             if (e != cudaSuccess) return e;
         }

@@ -15,20 +15,27 @@ cudaError_t launch_init(const RepDesc& D, int b_bits, int64_t n_vac, int64_t n_t
 size_t phase_smem_bytes(int cap, bool site);
 cudaError_t phase_prepare(int cap);
 cudaError_t run_pass_blocks(int prec, int cap, bool site, bool grain, int* blocks);
-cudaError_t small_pass_blocks(int prec, bool grain, int* blocks);
+cudaError_t small_pass_blocks(int prec, bool grain, int lane, int* blocks);
 constexpr int64_t SPLIT_MIN_ITEMS = 32768;  // fragments per phase from which the small-fragment pass runs
-constexpr int LANE_MAX_V = 4;  // vacancies a fragment may hold to run in the one-thread-per-fragment pass
+constexpr int ACT_COUNTERS = 32;  // act_count: 3 active lists x 8 phases, 8 window tickets
+constexpr int LANE_MAX_V = 8;      // vacancies per fragment of the persistent one-thread-per-fragment pass
+constexpr int LANE_REG_MAX_V = 4;  // ... of its register form
+constexpr int64_t LANE_PERSIST_ITEMS = 1 << 19;  // fragments per phase from which the persistent form runs
+constexpr int LANE_NONE = 0, LANE_REGISTERS = 1, LANE_PERSISTENT = 2;
 // mode: kmc_opts.small_pass (0 auto, 1 always, 2 always and grouped, -1 never)
 bool window_split(bool site, int64_t total_items, int mode);
-// the small-fragment pass in its one-thread-per-fragment form (mixed form only)
-bool window_lane(int prec, int mode);
+// form of the one-thread-per-fragment pass (mixed form only; LANE_NONE: the
+// grouped pass); form: kmc_opts.lane_form (0 auto, 1 registers, 2 persistent)
+int window_lane(int prec, int mode, int form, int64_t total_items);
 // act: 3 lists of total_items entries (general, one vacancy, two vacancies);
-// act_count: 24 counters (list l, phase p at 8 l + p)
+// act_count: ACT_COUNTERS counters (list l, phase p at 8 l + p; the window
+// ticket of phase p of the one-thread-per-fragment pass at 24 + p)
+// cls: total_items bytes (the screen's class of each item for the register form)
 cudaError_t launch_window(int prec, const RepDesc* d_descs, int nrep, int64_t total_items,
                           unsigned long long* wctl, uint32_t* perms, ActEntry* act, int32_t* act_count,
-                          uint32_t* occ, VacRec* recs, int32_t* counts, int32_t* tracer,
+                          uint8_t* cls, uint32_t* occ, VacRec* recs, int32_t* counts, int32_t* tracer,
                           unsigned long long* stats, uint32_t* status, int cap, int run_blocks,
-                          int small_blocks, bool split, bool lane, const SiteArgs& sa, cudaStream_t st,
+                          int small_blocks, bool split, int lane_form, const SiteArgs& sa, cudaStream_t st,
                           cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
 cudaError_t launch_grains(const RepDesc* d_descs, int nrep, int64_t ncell_total, int n_grains, int width, int64_t* X,
                           int32_t* grain, uint8_t* gb, cudaStream_t st);

@@ -27,9 +27,9 @@ def fk():
 
 def run_pair(fk, orc, cells, nf, nv, nh, seed, windows, prec, tracer=True, T=800.0, Ea=(0.6, 0.3),
              Ez=0.0, a=3.905, cap=64, n_tau=1.0, chunks=1, schedule=0):
-    sched, small = form(schedule)
+    sched, small, lane = form(schedule)
     b = fk.Batch([(*cells, a)], [(nv, nh)], seed, nfrag=nf, precision=prec, tracer=tracer, cap_v=cap,
-                 n_tau=n_tau, schedule=sched, small_pass=small)
+                 n_tau=n_tau, schedule=sched, small_pass=small, lane_form=lane)
     b.set_barriers(Ea[0], Ea[1], T, field_z=Ez)
     ref = orc.Lattice(cells, nf, nv, nh, seed=seed, tracer=tracer)
     ref.set_rates(Ea[0], Ea[1], T, Ez=Ez, a_ang=a, cap_v=cap, n_tau=n_tau, precision=prec)
@@ -55,17 +55,16 @@ def run_pair(fk, orc, cells, nf, nv, nh, seed, windows, prec, tracer=True, T=800
 # (precision, schedule): plain FP64 runs the colour-phase kernel; the mixed form
 # runs both the colour-phase kernel (1) and the replica-resident kernel (2);
 # 10 + s forces the small-fragment run pass beside the general one (plain:
-# fragments with one or two vacancies, four or two per warp; mixed: up to four
-# vacancies, one thread per fragment); 20 + s forces the grouped form in the
-# mixed form too
-FORMS = [(0, 0), (1, 1), (1, 2), (0, 10), (1, 11), (1, 21)]
+# fragments with one or two vacancies, four or two per warp; mixed: one thread
+# per fragment, in registers); 20 + s forces the grouped form in the mixed form
+# too; 30 + s the persistent one-thread-per-fragment form
+FORMS = [(0, 0), (1, 1), (1, 2), (0, 10), (1, 11), (1, 21), (1, 31)]
 
 
 def form(sched):
-    """schedule and small_pass of a FORMS entry"""
-    if sched >= 20:
-        return sched % 10, 2
-    return (sched % 10, 1) if sched >= 10 else (sched, -1)
+    """schedule, small_pass and lane_form of a FORMS entry"""
+    k, s = divmod(sched, 10)
+    return {0: (s, -1, 0), 1: (s, 1, 1), 2: (s, 2, 0), 3: (s, 1, 2)}[k]
 
 
 @pytest.mark.parametrize("prec,sched", FORMS)
@@ -105,8 +104,9 @@ def test_batch_of_uneven_replicas(fk, orc):
     comps = [(15, 0), (20, 40), (60, 300), (3, 10), (12, 30)]
     Ts = [800.0, 650.0, 500.0, 900.0, 1000.0]
     for prec, sched in FORMS:
+        sc, sm, lf = form(sched)
         b = fk.Batch([(*c, 4.01) for c in cells], comps, 21, edge=4, precision=prec, tracer=True, cap_v=64,
-                     schedule=form(sched)[0], small_pass=form(sched)[1])
+                     schedule=sc, small_pass=sm, lane_form=lf)
         b.set_barriers(0.7, 0.35, Ts, field_z=[0, 1e7, 0, -1e7, 0])
         b.run(40)
         for r, (c, (nv, nh), T) in enumerate(zip(cells, comps, Ts)):
@@ -293,21 +293,25 @@ def test_cluster_pairs_bit_exact(fk, orc):
         assert np.array_equal(b.records(r), ref.records()), r
 
 
-@pytest.mark.parametrize("prec,small", [(0, 0), (1, 0), (1, 2)])
-def test_small_pass_by_default_on_a_large_phase(fk, orc, prec, small):
+@pytest.mark.parametrize("prec,small,lane", [(0, 0, 0), (1, 0, 0), (1, 0, 2), (1, 2, 0)])
+def test_small_pass_by_default_on_a_large_phase(fk, orc, prec, small, lane):
     """128^3 cells in 2^3-cell fragments: 32768 fragments per colour phase, so
-    the small-fragment pass runs beside the general one by default (on a second
-    stream inside the window graph; the mixed form's one-thread-per-fragment
-    pass, or its grouped form on request); bit for bit against the oracle."""
+    the small-fragment pass runs by default: beside the general one on a second
+    stream inside the window graph (the plain form's grouped pass, the mixed
+    form's one-thread-per-fragment pass in registers, or its grouped form on
+    request), or in the mixed form's persistent form before it; bit for bit
+    against the oracle."""
     cells, nf = (128, 128, 128), (64, 64, 64)
     nv = 3 * 128 ** 3 // 1000
     b = fk.Batch([(*cells, 4.01)], [(nv, 0)], 17, nfrag=nf, precision=prec, tracer=True, cap_v=16,
-                 small_pass=small)
+                 small_pass=small, lane_form=lane)
     b.set_barriers(0.7, 0.35, 600.0, field_z=1e7)
     ref = orc.Lattice(cells, nf, nv, 0, seed=17, tracer=True)
     ref.set_rates(0.7, 0.35, 600.0, Ez=1e7, a_ang=4.01, cap_v=16, precision=prec)
     s = b.run(8)
-    assert s.launches >= 8 * 25  # the split window: 8 x (screen, general and small run passes) + set-up
+    # per window: set-up + 8 x (screen, small and general pass), or 8 x (the
+    # persistent one-thread-per-fragment pass, general pass)
+    assert s.launches == 8 * (17 if lane == 2 else 25)
     ref.run(8)
     assert np.array_equal(b.state(), ref.occupancy())
     assert np.array_equal(b.records(), ref.records())
@@ -316,11 +320,11 @@ def test_small_pass_by_default_on_a_large_phase(fk, orc, prec, small):
     assert (info.hops, info.handoffs) == (c["hops"], c["handoffs"]) and c["hops"] > 30000
 
 
-@pytest.mark.parametrize("small", [1, 2])
+@pytest.mark.parametrize("small", [1, 2, 3])
 def test_lane_pass_dense_fragments(fk, orc, small):
     """Mixed form, 8^3 cells in 64 fragments of 2^3 cells (24 O sites) with 200
-    vacancies: fragments of every count from 0 past 4 (the most the
-    one-thread-per-fragment pass takes, the rest go to the warp pass),
+    vacancies: fragments of every count from 1 to 7 (the register form takes
+    up to 4, the persistent form up to 8, the rest go to the warp pass),
     neighbouring vacancies inside one fragment (their rates change with each
     other's hops), hand-offs every few events, H- and a field."""
     cells, nf = (8, 8, 8), (4, 4, 4)
@@ -329,3 +333,23 @@ def test_lane_pass_dense_fragments(fk, orc, small):
     b, ref = run_pair(fk, orc, cells, nf, 200, 300, 29, 120, 1, T=750.0, Ez=2e7, cap=32, chunks=3,
                       schedule=10 * small + 1)
     assert ref.counters()["hops"] > 3000 and ref.counters()["handoffs"] > 1000
+
+
+def test_persistent_lane_form_by_default_on_the_largest_phases(fk):
+    """324^3 cells in 2^3-cell fragments: 531441 fragments per colour phase, at
+    least the 2^19 from which the mixed form runs its persistent
+    one-thread-per-fragment pass (two launches per phase); the register form on
+    request takes the same trajectory (both are checked against the oracle on
+    smaller lattices)."""
+    cells, nf = (324, 324, 324), (162, 162, 162)
+    nv = 3 * 324 ** 3 // 1000
+    res = []
+    for lane in (0, 1):
+        b = fk.Batch([(*cells, 4.01)], [(nv, 0)], 5, nfrag=nf, precision=1, cap_v=16, lane_form=lane)
+        b.set_barriers(0.7, 0.35, 600.0, field_z=1e7)
+        s = b.run(2)
+        assert s.launches == 2 * (17 if lane == 0 else 25)
+        res.append((s.hops, b.info().handoffs, b.state(), b.records()))
+        b.close()
+    assert res[0][0] == res[1][0] > 0 and res[0][1] == res[1][1]
+    assert np.array_equal(res[0][2], res[1][2]) and np.array_equal(res[0][3], res[1][3])
