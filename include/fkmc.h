@@ -143,7 +143,14 @@ typedef struct {
                            1 = registers (up to 4 vacancies, beside the general pass),
                            2 = persistent (up to 8 vacancies in shared memory, a grid that
                            stays resident for the phase; the general pass after it) */
-    int32_t reserved[3];
+    int32_t cluster_ctas; /* mixed form: a replica too large for one SM's shared memory runs in the
+                             cluster-resident kernel (a thread-block cluster of up to 16 CTAs,
+                             each holding a z-slab of fragment layers in shared memory, peers'
+                             slabs reached through distributed shared memory) where its slabs
+                             fit.  0 (default) = so, with the fewest CTAs that fit; -1 = never
+                             (the colour-phase kernels); 2..16 = every replica with that many
+                             fragment layers or more, with exactly this many CTAs */
+    int32_t reserved[2];
 } kmc_opts;
 
 typedef struct {

@@ -134,8 +134,20 @@ struct kmc_batch {
     // replica-resident kernel: replicas grouped by shared-memory size class
     NbTable nbt{};
     int32_t* d_reps = nullptr;   // resident replica ids, class by class
+    ClusterPlan* d_plans = nullptr;  // cluster-resident replicas' slab plans, grouped by CTA count
     int64_t* d_nvac = nullptr;   // vacancies per replica
-    struct RClass { int start, count; size_t smem; int threads; int cluster; cudaStream_t st; cudaEvent_t done; };
+    // a launch of the replica-resident kernel (one CTA, or a 2-CTA mirrored pair, per
+    // replica; start/count index d_reps) or of the cluster-resident kernel (slabs
+    // == true: one cluster of `cluster` CTAs per replica; start/count index d_plans)
+    struct RClass {
+        int start, count;
+        size_t smem;
+        int threads;
+        int cluster;
+        cudaStream_t st;
+        cudaEvent_t done;
+        bool slabs;
+    };
     std::vector<RClass> rclass;
     cudaEvent_t fork = nullptr;
     cudaGraphExec_t res_exec = nullptr;  // one call's class launches (fork, launches, join), captured
@@ -378,6 +390,7 @@ int plan_residency(kmc_batch* b)
     const int threads[5] = {128, 128, 256, 1024, 512};
     std::vector<std::vector<int>> cls(6);
     std::vector<size_t> cmax(6, 0), need_of(b->n, 0);
+    std::vector<ClusterPlan> plans;
     b->any_global = false;
     for (int r = 0; r < b->n; ++r) {
         int c = -1;
@@ -385,6 +398,20 @@ int plan_residency(kmc_batch* b)
         for (int k = 0; k < 5 && allowed && c < 0; ++k) {
             need = resident_smem_bytes(b->desc[r], b->n_vac[r], b->cap, threads[k]);
             if (need <= bounds[k]) c = k;
+        }
+        // the cluster-resident kernel: a replica too large for one SM (or every
+        // replica, with cluster_ctas forced) held by a cluster of CTAs, one z-slab each
+        const int force = b->opts.cluster_ctas;
+        if (allowed && force >= 0 && (c < 0 || force >= 2)) {
+            ClusterPlan pl{};
+            const int lo = force >= 2 ? force : 2, hi = force >= 2 ? force : CLUSTER_MAX_CTAS;
+            if (make_cluster_plan(b->desc[r], b->n_vac[r], b->cap, lo, hi, &pl) &&
+                cluster_fits(pl.ncta, cluster_smem_bytes(b->desc[r], pl, b->cap)) > 0) {
+                pl.rep = r;
+                plans.push_back(pl);
+                b->desc[r].resident = 1;
+                continue;
+            }
         }
         b->desc[r].resident = c >= 0 ? 1 : 0;
         if (c < 0) {
@@ -412,7 +439,7 @@ int plan_residency(kmc_batch* b)
     for (int c = 0; c < 6; ++c) {
         if (cls[c].empty()) continue;
         kmc_batch::RClass rc{(int)order.size(), (int)cls[c].size(), cmax[c], c == 5 ? 1024 : threads[c],
-                             c == 5 ? 2 : 1, nullptr, nullptr};
+                             c == 5 ? 2 : 1, nullptr, nullptr, false};
         for (int r : cls[c]) order.push_back(r);
         CK(cudaStreamCreateWithFlags(&rc.st, cudaStreamNonBlocking), "stream");
         CK(cudaEventCreateWithFlags(&rc.done, cudaEventDisableTiming), "event");
@@ -422,6 +449,25 @@ int plan_residency(kmc_batch* b)
         CK(cudaMemcpyAsync(b->d_reps, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice,
                            b->st),
            "replica list upload");
+    // cluster-resident replicas: one launch per CTA count (a launch has one cluster shape)
+    std::stable_sort(plans.begin(), plans.end(),
+                     [](const ClusterPlan& x, const ClusterPlan& y) { return x.ncta < y.ncta; });
+    for (size_t k = 0; k < plans.size();) {
+        size_t e = k, smem = 0;
+        while (e < plans.size() && plans[e].ncta == plans[k].ncta) {
+            smem = std::max(smem, cluster_smem_bytes(b->desc[plans[e].rep], plans[e], b->cap));
+            ++e;
+        }
+        kmc_batch::RClass rc{(int)k, (int)(e - k), smem, CLUSTER_THREADS, plans[k].ncta, nullptr, nullptr, true};
+        CK(cudaStreamCreateWithFlags(&rc.st, cudaStreamNonBlocking), "stream");
+        CK(cudaEventCreateWithFlags(&rc.done, cudaEventDisableTiming), "event");
+        b->rclass.push_back(rc);  // launched last-first: a cluster takes its SMs before single CTAs spread out
+        k = e;
+    }
+    if (!plans.empty())
+        CK(cudaMemcpyAsync(b->d_plans, plans.data(), sizeof(ClusterPlan) * plans.size(), cudaMemcpyHostToDevice,
+                           b->st),
+           "cluster plan upload");
     return FKMC_OK;
 }
 
@@ -775,6 +821,8 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
     if (o.schedule < 0 || o.schedule > 2) return fail(FKMC_EINVAL, "schedule must be 0, 1 or 2");
     if (o.small_pass < -1 || o.small_pass > 2) return fail(FKMC_EINVAL, "small_pass must be -1, 0, 1 or 2");
     if (o.lane_form < 0 || o.lane_form > 2) return fail(FKMC_EINVAL, "lane_form must be 0, 1 or 2");
+    if (o.cluster_ctas < -1 || o.cluster_ctas == 1 || o.cluster_ctas > CLUSTER_MAX_CTAS)
+        return fail(FKMC_EINVAL, "cluster_ctas must be -1, 0 or 2..16");
     if (o.test_stuck_wait_us < 0 || o.test_stuck_wait_us > 2000000)
         return fail(FKMC_EINVAL, "test_stuck_wait_us must be in [0, 2e6]");
 
@@ -876,6 +924,7 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
     b->scratch = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * 8);
     b->scratch_all = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * 7 * n);
     b->d_reps = (int32_t*)b->dalloc(sizeof(int32_t) * n);
+    b->d_plans = (ClusterPlan*)b->dalloc(sizeof(ClusterPlan) * n);
     b->d_nvac = (int64_t*)b->dalloc(sizeof(int64_t) * n);
     b->wctl = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * 2);
     b->perms = (uint32_t*)b->dalloc(sizeof(uint32_t) * n);
@@ -894,7 +943,8 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
         }
     }
     if (!b->occ || !b->recs || !b->counts || (o.tracer && !b->tracer) || !b->d_desc || !b->stats ||
-        !b->status || !b->scratch || !b->scratch_all || !b->d_reps || !b->d_nvac || !b->wctl || !b->perms ||
+        !b->status || !b->scratch || !b->scratch_all || !b->d_reps || !b->d_plans || !b->d_nvac || !b->wctl ||
+        !b->perms ||
         !b->act || !b->act_count || !b->cls) {
         b->release();
         delete b;
@@ -910,6 +960,7 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
     step(phase_prepare(b->cap), "kernel attributes");
     step(run_pass_blocks(b->opts.precision, b->cap, false, false, &b->run_blocks), "occupancy query");
     step(resident_prepare(), "kernel attributes");
+    step(cluster_prepare(), "kernel attributes");
     step(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "event");
     step(cudaEventCreate(&b->ev0), "event");
     step(cudaEventCreate(&b->ev1), "event");
@@ -1017,7 +1068,10 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
             for (auto it = b->rclass.rbegin(); it != b->rclass.rend() && le == cudaSuccess; ++it) {
                 auto& c = *it;
                 le = cudaStreamWaitEvent(c.st, b->fork, 0);
-                if (le == cudaSuccess)
+                if (le == cudaSuccess && c.slabs)
+                    le = launch_cluster(b->d_desc, b->d_plans + c.start, c.count, c.cluster, c.smem, windows, b->occ,
+                                        b->recs, b->counts, b->tracer, b->stats, b->status, b->cap, b->nbt, c.st);
+                else if (le == cudaSuccess)
                     le = launch_resident(b->d_desc, b->d_reps + c.start, c.count, b->d_nvac, c.smem, c.threads,
                                          c.cluster, windows, b->occ, b->recs, b->counts, b->tracer, b->stats,
                                          b->status, b->cap, b->nbt, (uint32_t)b->opts.test_stuck_wait_us, c.st);

@@ -93,6 +93,28 @@ cudaError_t elec_update(const RepDesc& D, const double* phi, double q, int32_t* 
                         cudaStream_t st);
 cudaError_t elec_add(int32_t* field, const int32_t* u, int64_t n, cudaStream_t st);
 
+// cluster-resident kernel (fkmc_resident.cu): one replica per thread-block cluster,
+// CTA c holding the z-slab of fragment layers [fz0[c], fz0[c+1])
+constexpr int CLUSTER_MAX_CTAS = 16;
+constexpr int CLUSTER_THREADS = 512;
+struct ClusterPlan {
+    int32_t rep;                          // replica index in the batch
+    int32_t ncta;                         // CTAs of the cluster
+    int32_t fz0[CLUSTER_MAX_CTAS + 1];    // fragment layers of CTA c: [fz0[c], fz0[c + 1])
+    int32_t zs;                           // cells in z of the thickest slab (the common layout)
+    int32_t nfl;                          // fragments of the thickest slab
+    int32_t vcap;                         // vacancy slots per CTA
+    int32_t icap;                         // inbox entries per phase parity per CTA
+};
+size_t cluster_smem_bytes(const RepDesc& D, const ClusterPlan& p, int cap);
+// the plan with the fewest CTAs in [min_ctas, max_ctas] whose slabs fit one SM's shared memory
+bool make_cluster_plan(const RepDesc& D, int64_t n_vac, int cap, int min_ctas, int max_ctas, ClusterPlan* out);
+cudaError_t cluster_prepare();
+int cluster_fits(int ncta, size_t smem);  // clusters of ncta CTAs with this much shared memory the GPU can hold at once
+cudaError_t launch_cluster(const RepDesc* d_descs, const ClusterPlan* d_plans, int nplans, int ncta, size_t smem,
+                           uint64_t windows, uint32_t* occ, VacRec* recs, int32_t* counts, int32_t* tracer,
+                           unsigned long long* stats, uint32_t* status, int cap, const NbTable& nbt, cudaStream_t st);
+
 // replica-resident kernel (fkmc_resident.cu)
 constexpr int RESIDENT_MAX_SLOTS = 64;               // vacancies per fragment a thread can hold
 constexpr size_t RESIDENT_MAX_SMEM = 220 * 1024;     // dynamic shared memory per replica CTA

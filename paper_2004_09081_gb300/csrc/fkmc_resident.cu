@@ -26,6 +26,9 @@
 // back to the per-fragment lists.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
+
 #include "fkmc_device.cuh"
 #include "fkmc_kernels.h"
 
@@ -802,6 +805,773 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
         if (rank == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     }
     if constexpr (CL > 1) cluster_sync();  // no CTA leaves while its peer may still address it
+}
+
+// ---------------------------------------------------------------- cluster-resident kernel
+// One replica too large for one SM's shared memory, held by a thread-block
+// cluster of P.ncta CTAs (up to 16): CTA c holds the z-slab of fragment layers
+// [P.fz0[c], P.fz0[c+1]) -- its occupancy planes, its vacancies (a pool of
+// P.vcap slots with a free-slot stack) and its fragments' lists, totals and
+// dirty flags.  Every CTA has the same layout, so a peer's copy of an array is
+// addressed through distributed shared memory (mapa) at the same offset.  The
+// colour phases are those of the replica-resident kernel, with a cluster
+// barrier between phases:
+//   - a neighbour site in another slab is read from that CTA's shared memory
+//     (ld.shared::cluster), an exchange there is an atomic XOR on it
+//     (red.shared::cluster);
+//   - a vacancy leaving the slab is written into the owning CTA's inbox
+//     (double-buffered by phase parity; the slot taken with a remote atomic
+//     add) and its slot returns to the free stack; at the start of the next
+//     phase the owner moves its inbox into free slots and onto the fragments'
+//     lists (the receiving fragment has another colour, so it does not run in
+//     the phase that filled the inbox);
+//   - dirty marks on a peer's fragments are remote byte stores.
+// Fragments of one colour never touch each other's sites, so the result is
+// the replica-resident kernel's (and the oracle's) bit for bit.
+
+struct InboxRec {
+    uint32_t key;
+    int32_t d[3];
+    uint32_t id;
+    int32_t lf;  // the receiving CTA's local fragment index
+};
+static_assert(sizeof(InboxRec) == 24, "inbox record");
+
+struct CShared {
+    RepDesc D;
+    NbEntry nb[3][8];
+    ClusterPlan P;
+    uint32_t perms[64];
+    int zbeg[CLUSTER_MAX_CTAS + 1];  // first z cell of CTA c's slab
+    int nact;
+    int next_act;
+    int inbox_n[2];
+    int free_top;
+    int pool_n;
+    unsigned long long hops, hand;
+};
+
+struct CLayout {
+    uint32_t* occ;       // [3][zs][L1][RW]
+    uint32_t* key;       // vacancy pool [vcap]
+    int32_t* d;
+    uint32_t* id;
+    int16_t* next;
+    int16_t* fstack;     // free pool slots
+    int32_t* head;       // local fragments [nfl]
+    unsigned long long* S;
+    uint8_t* dirty;
+    int32_t* act;        // screened local fragments, with their first draws
+    uint64_t* act_xs;
+    float* act_E;
+    int16_t* wslot;      // per warp
+    int8_t* wtype;
+    InboxRec* inbox;     // [2][icap]
+    uint16_t* frag_of_c; // cell -> global fragment coordinate: x cells, then y, then z
+    uint8_t* cta_of_fz;  // fragment layer -> CTA
+};
+
+__host__ __device__ inline size_t cluster_layout_bytes(const RepDesc& D, const ClusterPlan& P, int cap, int nwarps,
+                                                       size_t* off /* 17 offsets or null */)
+{
+    const size_t words = (size_t)3 * P.zs * D.L[1] * D.row_words;
+    const size_t sz[17] = {
+        words * 4,                          // 0 occupancy slab
+        (size_t)P.vcap * 4,                 // 1 keys
+        (size_t)P.vcap * 12,                // 2 displacements
+        (size_t)P.vcap * 4,                 // 3 ids
+        (size_t)P.vcap * 2,                 // 4 next links
+        (size_t)P.vcap * 2,                 // 5 free-slot stack
+        (size_t)P.nfl * 4,                  // 6 list heads
+        (size_t)P.nfl * 8,                  // 7 cached totals
+        (size_t)P.nfl,                      // 8 dirty flags
+        (size_t)P.nfl * 4,                  // 9 screened list
+        (size_t)P.nfl * 16,                 // 10 screened: selection words
+        (size_t)P.nfl * 8,                  // 11 screened: variates
+        (size_t)nwarps * cap * 2,           // 12 per-warp slots
+        (size_t)nwarps * cap * 8,           // 13 per-warp event types
+        (size_t)2 * P.icap * sizeof(InboxRec),  // 14 inboxes
+        (size_t)(D.L[0] + D.L[1] + D.L[2]) * 2, // 15 cell -> fragment tables
+        (size_t)D.nf[2],                    // 16 fragment layer -> CTA
+    };
+    size_t b = 0;
+    for (int k = 0; k < 17; ++k) {
+        if (off) off[k] = b;
+        b += (sz[k] + 15) & ~(size_t)15;
+    }
+    return (b + 127) & ~(size_t)127;
+}
+
+namespace {
+
+__device__ __forceinline__ CLayout ccarve(unsigned char* dyn, const RepDesc& D, const ClusterPlan& P, int cap,
+                                          int nwarps)
+{
+    size_t o[17];
+    cluster_layout_bytes(D, P, cap, nwarps, o);
+    CLayout L;
+    L.occ = reinterpret_cast<uint32_t*>(dyn + o[0]);
+    L.key = reinterpret_cast<uint32_t*>(dyn + o[1]);
+    L.d = reinterpret_cast<int32_t*>(dyn + o[2]);
+    L.id = reinterpret_cast<uint32_t*>(dyn + o[3]);
+    L.next = reinterpret_cast<int16_t*>(dyn + o[4]);
+    L.fstack = reinterpret_cast<int16_t*>(dyn + o[5]);
+    L.head = reinterpret_cast<int32_t*>(dyn + o[6]);
+    L.S = reinterpret_cast<unsigned long long*>(dyn + o[7]);
+    L.dirty = reinterpret_cast<uint8_t*>(dyn + o[8]);
+    L.act = reinterpret_cast<int32_t*>(dyn + o[9]);
+    L.act_xs = reinterpret_cast<uint64_t*>(dyn + o[10]);
+    L.act_E = reinterpret_cast<float*>(dyn + o[11]);
+    L.wslot = reinterpret_cast<int16_t*>(dyn + o[12]);
+    L.wtype = reinterpret_cast<int8_t*>(dyn + o[13]);
+    L.inbox = reinterpret_cast<InboxRec*>(dyn + o[14]);
+    L.frag_of_c = reinterpret_cast<uint16_t*>(dyn + o[15]);
+    L.cta_of_fz = reinterpret_cast<uint8_t*>(dyn + o[16]);
+    return L;
+}
+
+__device__ __forceinline__ uint32_t atom_peer_add(uint32_t a, uint32_t v)
+{
+    uint32_t o;
+    asm volatile("atom.shared::cluster.add.u32 %0, [%1], %2;" : "=r"(o) : "r"(a), "r"(v) : "memory");
+    return o;
+}
+
+__device__ __forceinline__ uint32_t cluster_nctas()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+// where a site's occupancy word lives: the CTA holding its z, and the word's
+// index in that CTA's slab (every CTA has the same slab layout)
+struct CWord {
+    uint32_t cta;
+    int idx;
+};
+
+__device__ __forceinline__ CWord cword(const CShared& sh, const CLayout& S, const Geo& g, int t, int x, int y, int z)
+{
+    const int fz = S.frag_of_c[g.L0 + g.L1 + z];
+    const uint32_t o = S.cta_of_fz[fz];
+    CWord w;
+    w.cta = o;
+    w.idx = ((t * sh.P.zs + (z - sh.zbeg[o])) * g.L1 + y) * g.RW + (x >> 4);
+    return w;
+}
+
+__device__ __forceinline__ int csite_code(const CShared& sh, const CLayout& S, const Geo& g, uint32_t me, int t,
+                                          int x, int y, int z)
+{
+    const CWord w = cword(sh, S, g, t, x, y, z);
+    const uint32_t v = w.cta == me ? S.occ[w.idx] : (uint32_t)ld_peer(peer_addr(S.occ + w.idx, w.cta));
+    return (int)((v >> occ_shift(x)) & 3u);
+}
+
+__device__ __forceinline__ void csite_xor(const CShared& sh, const CLayout& S, const Geo& g, uint32_t me, int t, int x,
+                                          int y, int z, uint32_t m)
+{
+    const CWord w = cword(sh, S, g, t, x, y, z);
+    if (w.cta == me) atomicXor(S.occ + w.idx, m);
+    else red_peer_xor(peer_addr(S.occ + w.idx, w.cta), m);
+}
+
+__device__ __forceinline__ NbSite cnb_site(const CShared& sh, const Geo& g, int t, int x, int y, int z, int q)
+{
+    const NbEntry nb = sh.nb[t][q];
+    NbSite s;
+    s.t2 = nb.t2;
+    s.jx = wrapc(x + nb.dc[0], g.L0);
+    s.jy = wrapc(y + nb.dc[1], g.L1);
+    s.jz = wrapc(z + nb.dc[2], g.L2);
+    return s;
+}
+
+// owner of cell (x,y,z): its CTA and that CTA's local fragment index
+__device__ __forceinline__ void cowner(const CShared& sh, const CLayout& S, const Geo& g, int x, int y, int z,
+                                       uint32_t& cta, int& lf)
+{
+    const int fx = S.frag_of_c[x], fy = S.frag_of_c[g.L0 + y], fz = S.frag_of_c[g.L0 + g.L1 + z];
+    cta = S.cta_of_fz[fz];
+    lf = ((fz - sh.P.fz0[cta]) * g.nf1 + fy) * g.nf0 + fx;
+}
+
+}  // namespace
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ descs,
+                                                   const ClusterPlan* __restrict__ plans, uint64_t windows,
+                                                   uint32_t* occ, VacRec* recs, int32_t* counts, int32_t* tracer,
+                                                   unsigned long long* stats, uint32_t* status, int cap, NbTable nbt)
+{
+    extern __shared__ __align__(128) unsigned char dyn[];
+    __shared__ CShared sh;
+    const int tid = threadIdx.x;
+    const uint32_t me = cluster_ctarank();
+    const int ci = (int)(blockIdx.x / cluster_nctas());
+    if (tid == 0) {
+        sh.P = plans[ci];
+        sh.D = descs[sh.P.rep];
+        for (int c = 0; c <= sh.P.ncta; ++c) sh.zbeg[c] = frag_start(sh.P.fz0[c], sh.D.base[2], sh.D.rem[2]);
+        sh.nact = 0;
+        sh.next_act = 0;
+        sh.inbox_n[0] = sh.inbox_n[1] = 0;
+        sh.pool_n = 0;
+        sh.hops = 0;
+        sh.hand = 0;
+    }
+    if (tid < 24) (&sh.nb[0][0])[tid] = (&nbt.e[0][0])[tid];
+    __syncthreads();
+    const RepDesc& D = sh.D;
+    const ClusterPlan& P = sh.P;
+    const CLayout S = ccarve(dyn, D, P, cap, NT / 32);
+    const Geo geo{D.L[0], D.L[1], D.L[2], D.row_words, D.nf[0], D.nf[1], D.F, D.theta_tau};
+    const int fzb = P.fz0[me], fze = P.fz0[me + 1];
+    const int zb = sh.zbeg[me], zl = sh.zbeg[me + 1] - zb;
+    const int nfl_me = (fze - fzb) * D.nf[0] * D.nf[1];
+
+    // ---- stage in: this slab's occupancy planes and vacancies, the lookup tables
+    const int plane = zl * D.L[1] * D.row_words;  // words of one site type's slab
+    for (int k = tid; k < 3 * plane; k += NT) {
+        const int t = k / plane, r = k - t * plane;
+        S.occ[t * P.zs * D.L[1] * D.row_words + r] =
+            occ[D.occ_word_off + ((int64_t)t * D.L[2] + zb) * D.L[1] * D.row_words + r];
+    }
+    for (int k = tid; k < D.L[0] + D.L[1] + D.L[2]; k += NT) {
+        const int d = k < D.L[0] ? 0 : (k < D.L[0] + D.L[1] ? 1 : 2);
+        const int c = d == 0 ? k : (d == 1 ? k - D.L[0] : k - D.L[0] - D.L[1]);
+        S.frag_of_c[k] = (uint16_t)frag_of(c, D.base[d], D.rem[d]);
+    }
+    for (int fz = tid; fz < D.nf[2]; fz += NT) {
+        int c = 0;
+        while (c + 1 < P.ncta && P.fz0[c + 1] <= fz) ++c;
+        S.cta_of_fz[fz] = (uint8_t)c;
+    }
+    for (int lf = tid; lf < nfl_me; lf += NT) {
+        const int fid = (fzb * D.nf[1]) * D.nf[0] + lf;  // layers are contiguous in the global order
+        const int64_t g = D.frag_base + fid;
+        const int c = counts[g];
+        int head = -1;
+        for (int k = 0; k < c && k < cap; ++k) {
+            const int v = atomicAdd(&sh.pool_n, 1);
+            if (v >= P.vcap) {
+                atomicOr(status, STATUS_OVERFLOW);
+                break;
+            }
+            const VacRec rr = recs[g * cap + k];
+            int t, x, y, z;
+            split_key(rr.key, t, x, y, z);
+            S.key[v] = key32(t, x, y, z);
+            S.d[3 * v] = rr.d[0];
+            S.d[3 * v + 1] = rr.d[1];
+            S.d[3 * v + 2] = rr.d[2];
+            S.id[v] = rr.id;
+            S.next[v] = (int16_t)head;
+            head = v;
+        }
+        if (c > cap) atomicOr(status, STATUS_OVERFLOW);
+        S.head[lf] = head;
+        S.dirty[lf] = 1;
+        S.S[lf] = 0ull;
+    }
+    __syncthreads();
+    {
+        const int used = min(sh.pool_n, P.vcap);
+        for (int k = tid; k < P.vcap - used; k += NT) S.fstack[k] = (int16_t)(used + k);
+        if (tid == 0) sh.free_top = P.vcap - used;
+    }
+    cluster_sync();  // every slab is in place before any CTA reads a peer's
+
+    const uint64_t hop_k1 = key_word(D.replica, PURPOSE_HOP);
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const unsigned FULL = 0xffffffffu;
+    int16_t* wslot = S.wslot + warp * cap;
+    int8_t* wtype = S.wtype + warp * cap * 8;
+    unsigned long long my_hops = 0, my_hand = 0;
+
+    // the inbox of phase parity b into free slots and onto the fragments' lists
+    auto drain = [&](int b) {
+        const int n = min(sh.inbox_n[b], P.icap);
+        if (sh.inbox_n[b] > P.icap && tid == 0) atomicOr(status, STATUS_OVERFLOW);
+        for (int e = tid; e < n; e += NT) {
+            const InboxRec r = S.inbox[b * P.icap + e];
+            const int top = atomicSub(&sh.free_top, 1) - 1;
+            if (top < 0) {
+                atomicOr(status, STATUS_OVERFLOW);
+                continue;
+            }
+            const int v = S.fstack[top];
+            S.key[v] = r.key;
+            S.d[3 * v] = r.d[0];
+            S.d[3 * v + 1] = r.d[1];
+            S.d[3 * v + 2] = r.d[2];
+            S.id[v] = r.id;
+            S.next[v] = (int16_t)atomicExch(S.head + r.lf, v);
+            S.dirty[r.lf] = 1;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            sh.inbox_n[b] = 0;
+            if (sh.free_top < 0) sh.free_top = 0;
+        }
+    };
+
+    uint32_t ph = 0;
+    for (uint64_t wk = 0; wk < windows; ++wk) {
+        const uint64_t w = D.window + wk;
+        if ((wk & 63) == 0) {
+            if (tid < 64 && wk + tid < windows) sh.perms[tid] = colour_perm_packed(D.seed, D.replica, w + tid);
+            __syncthreads();
+        }
+        const uint32_t wperm = sh.perms[wk & 63];
+        for (int p = 0; p < 8; ++p, ++ph) {
+            if (ph > 0) drain((ph - 1) & 1);
+            const int colour = (int)((wperm >> (4 * p)) & 15u);
+            int cnt[2], bit[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) bit[d] = (colour >> d) & 1;
+#pragma unroll
+            for (int d = 0; d < 2; ++d) cnt[d] = D.nf[d] == 1 ? (bit[d] == 0 ? 1 : 0) : D.nf[d] / 2;
+            // this slab's layers of the colour's z parity
+            const int lz0 = D.nf[2] == 1 ? 0 : (fzb + ((fzb & 1) != bit[2] ? 1 : 0));
+            const int nlz = D.nf[2] == 1 ? (bit[2] == 0 ? 1 : 0) : (fze > lz0 ? (fze - lz0 + 1) / 2 : 0);
+            const int ncls = cnt[0] * cnt[1] * nlz;
+            if (tid == 0) {
+                sh.nact = 0;
+                sh.next_act = 0;
+            }
+            __syncthreads();
+            // ---- screen: one thread per local fragment of the colour
+            for (int l = tid; l < ncls; l += NT) {
+                int f0 = l % cnt[0], f1 = (l / cnt[0]) % cnt[1], f2 = l / (cnt[0] * cnt[1]);
+                f0 = D.nf[0] == 1 ? 0 : 2 * f0 + bit[0];
+                f1 = D.nf[1] == 1 ? 0 : 2 * f1 + bit[1];
+                f2 = lz0 + 2 * f2;
+                const int lf = ((f2 - fzb) * D.nf[1] + f1) * D.nf[0] + f0;
+                const int fid = (f2 * D.nf[1] + f1) * D.nf[0] + f0;
+                if (S.head[lf] < 0) continue;
+                const bool dirty = S.dirty[lf] != 0;
+                const unsigned long long tot = S.S[lf];
+                if (!dirty && tot == 0ull) continue;
+                const U64x4 blk = philox4x64((uint64_t)fid, w, 0, 0, D.seed, hop_k1);
+                const float E0 = neglog32(blk.x[0]);
+                bool active = dirty;
+                if (!active) {
+                    const float ratio = __fdiv_rn(E0, __ull2float_rn(tot));
+                    active = !(__dadd_rn(0.0, scale_pow2((double)ratio, geo.F)) > geo.theta);
+                }
+                if (active) {
+                    const int a = atomicAdd(&sh.nact, 1);
+                    S.act[a] = lf;
+                    S.act_E[2 * a] = E0;
+                    S.act_E[2 * a + 1] = neglog32(blk.x[2]);
+                    S.act_xs[2 * a] = blk.x[1];
+                    S.act_xs[2 * a + 1] = blk.x[3];
+                }
+            }
+            __syncthreads();
+            // ---- run: one warp per listed fragment
+            const int nact = sh.nact;
+            for (;;) {
+                int a = 0;
+                if (lane == 0) a = atomicAdd(&sh.next_act, 1);
+                a = __shfl_sync(FULL, a, 0);
+                if (a >= nact) break;
+                const int lf = S.act[a];
+                const int fx = lf % D.nf[0];
+                const int fy = (lf / D.nf[0]) % D.nf[1];
+                const int fz = fzb + lf / (D.nf[0] * D.nf[1]);
+                const int fid = (fz * D.nf[1] + fy) * D.nf[0] + fx;
+                const int lo0 = frag_start(fx, D.base[0], D.rem[0]), hi0 = frag_start(fx + 1, D.base[0], D.rem[0]);
+                const int lo1 = frag_start(fy, D.base[1], D.rem[1]), hi1 = frag_start(fy + 1, D.base[1], D.rem[1]);
+                const int lo2 = frag_start(fz, D.base[2], D.rem[2]), hi2 = frag_start(fz + 1, D.base[2], D.rem[2]);
+                // slots: the fragment's vacancies in ascending site order
+                int n = 0;
+                if (lane == 0) {
+                    for (int v = S.head[lf]; v >= 0; v = S.next[v]) {
+                        if (n >= cap) {
+                            atomicOr(status, STATUS_OVERFLOW);
+                            break;
+                        }
+                        wslot[n++] = (int16_t)v;
+                    }
+                }
+                n = __shfl_sync(FULL, n, 0);
+                __syncwarp();
+                if (n <= 32) {
+                    const int vk = lane < n ? wslot[lane] : -1;
+                    const uint32_t kk = lane < n ? S.key[vk] : 0xffffffffu;
+                    int rnk = 0;
+                    for (int q = 0; q < n; ++q) rnk += __shfl_sync(FULL, kk, q) < kk ? 1 : 0;
+                    __syncwarp();
+                    if (lane < n) wslot[rnk] = (int16_t)vk;
+                } else if (lane == 0) {
+                    for (int k = 1; k < n; ++k) {
+                        const int v = wslot[k];
+                        const uint32_t kv = S.key[v];
+                        int m = k;
+                        while (m > 0 && S.key[wslot[m - 1]] > kv) {
+                            wslot[m] = wslot[m - 1];
+                            --m;
+                        }
+                        wslot[m] = (int16_t)v;
+                    }
+                }
+                __syncwarp();
+                const int nch = (n + 3) >> 2;
+                auto compute_types = [&]() {
+                    for (int c = 0; c < nch; ++c) {
+                        const int e = c * 32 + lane, m = e >> 3;
+                        int ty = -1;
+                        if (m < n && wslot[m] >= 0) {
+                            int t, x, y, z;
+                            split32(S.key[wslot[m]], t, x, y, z);
+                            const NbEntry nbe = sh.nb[t][e & 7];
+                            const int code = csite_code(sh, S, geo, me, nbe.t2, wrapc(x + nbe.dc[0], geo.L0),
+                                                        wrapc(y + nbe.dc[1], geo.L1), wrapc(z + nbe.dc[2], geo.L2));
+                            ty = code == SP_V ? -1 : code * 3 + nbe.d[2] + 1;
+                        }
+                        wtype[e] = (int8_t)ty;
+                    }
+                    __syncwarp();
+                };
+                compute_types();
+
+                double clock = 0.0;
+                uint64_t i = 0, batch = ~0ull;
+                uint64_t xs_even = 0, xs_odd = 0;
+                float E_even = 0.f, E_odd = 0.f;
+                unsigned long long tot = 0;
+                for (;;) {
+                    // exact total (order-free integer sum) and, for up to two chunks, the
+                    // inclusive prefixes the selection needs
+                    unsigned long long inc0 = 0, inc1 = 0;
+                    if (nch <= 2) {
+                        const int t0 = wtype[lane];
+                        inc0 = t0 < 0 ? 0ull : (unsigned long long)D.q[t0];
+#pragma unroll
+                        for (int off = 1; off < 32; off <<= 1) {
+                            const unsigned long long t2 = __shfl_up_sync(FULL, inc0, off);
+                            if (lane >= off) inc0 += t2;
+                        }
+                        tot = __shfl_sync(FULL, inc0, 31);
+                        if (nch == 2) {
+                            const int t1 = wtype[32 + lane];
+                            inc1 = t1 < 0 ? 0ull : (unsigned long long)D.q[t1];
+#pragma unroll
+                            for (int off = 1; off < 32; off <<= 1) {
+                                const unsigned long long t2 = __shfl_up_sync(FULL, inc1, off);
+                                if (lane >= off) inc1 += t2;
+                            }
+                            inc1 += tot;
+                            tot = __shfl_sync(FULL, inc1, 31);
+                        }
+                    } else {
+                        unsigned long long part = 0;
+                        for (int c = 0; c < nch; ++c) {
+                            const int ty = wtype[c * 32 + lane];
+                            part += ty < 0 ? 0ull : (unsigned long long)D.q[ty];
+                        }
+#pragma unroll
+                        for (int off = 16; off; off >>= 1) part += __shfl_xor_sync(FULL, part, off);
+                        tot = part;
+                    }
+                    if (tot == 0ull) break;
+                    if (i >= MAX_EVENTS_PER_PHASE) {
+                        if (lane == 0) atomicOr(status, STATUS_EVENT_LIMIT);
+                        break;
+                    }
+                    uint64_t xs;
+                    float E;
+                    if (i < 2) {
+                        xs = S.act_xs[2 * a + (int)i];
+                        E = S.act_E[2 * a + (int)i];
+                    } else {
+                        const uint64_t k = i - 2;
+                        if ((k >> 6) != batch) {
+                            batch = k >> 6;
+                            const U64x4 blk =
+                                philox4x64((uint64_t)fid, w, 1 + 32 * batch + lane, 0, D.seed, hop_k1);
+                            xs_even = blk.x[1];
+                            xs_odd = blk.x[3];
+                            E_even = neglog32(blk.x[0]);
+                            E_odd = neglog32(blk.x[2]);
+                        }
+                        const int src = (int)((k >> 1) & 31);
+                        const bool odd = (k & 1) != 0;
+                        xs = __shfl_sync(FULL, odd ? xs_odd : xs_even, src);
+                        E = __shfl_sync(FULL, odd ? E_odd : E_even, src);
+                    }
+                    const float ratio = __fdiv_rn(E, __ull2float_rn(tot));
+                    const double nclock = __dadd_rn(clock, scale_pow2((double)ratio, geo.F));
+                    if (nclock > geo.theta) break;
+                    const unsigned long long target = __umul64hi(xs, tot);
+                    int e_sel = -1;
+                    if (nch <= 2) {
+                        unsigned bal = __ballot_sync(FULL, inc0 > target);
+                        if (bal) {
+                            e_sel = __ffs(bal) - 1;
+                        } else {
+                            bal = __ballot_sync(FULL, inc1 > target);
+                            if (bal && nch == 2) e_sel = 32 + __ffs(bal) - 1;
+                        }
+                    } else {
+                        unsigned long long carry = 0;
+                        for (int c = 0; c < nch; ++c) {
+                            const int ty = wtype[c * 32 + lane];
+                            unsigned long long inc = ty < 0 ? 0ull : (unsigned long long)D.q[ty];
+#pragma unroll
+                            for (int off = 1; off < 32; off <<= 1) {
+                                const unsigned long long t2 = __shfl_up_sync(FULL, inc, off);
+                                if (lane >= off) inc += t2;
+                            }
+                            inc += carry;
+                            const unsigned bal = __ballot_sync(FULL, inc > target);
+                            if (bal) {
+                                e_sel = c * 32 + __ffs(bal) - 1;
+                                break;
+                            }
+                            carry = __shfl_sync(FULL, inc, 31);
+                        }
+                    }
+                    if (e_sel < 0) {  // cannot happen: the target lies below the total
+                        if (lane == 0) atomicOr(status, STATUS_OVERFLOW);
+                        break;
+                    }
+                    const int m = e_sel >> 3, qd = e_sel & 7;
+                    const int v = wslot[m];
+                    int t, x, y, z;
+                    split32(S.key[v], t, x, y, z);
+                    const NbEntry nb = sh.nb[t][qd];
+                    const NbSite j = cnb_site(sh, geo, t, x, y, z, qd);
+                    const bool owned = j.jx >= lo0 && j.jx < hi0 && j.jy >= lo1 && j.jy < hi1 && j.jz >= lo2 &&
+                                       j.jz < hi2;
+                    if (lane == 0) {  // apply the exchange
+                        const uint32_t ion = (uint32_t)(wtype[e_sel] / 3);
+                        csite_xor(sh, S, geo, me, t, x, y, z, ((uint32_t)SP_V ^ ion) << occ_shift(x));
+                        csite_xor(sh, S, geo, me, j.t2, j.jx, j.jy, j.jz, (ion ^ (uint32_t)SP_V) << occ_shift(j.jx));
+                        const int d0 = S.d[3 * v] + nb.d[0], d1 = S.d[3 * v + 1] + nb.d[1],
+                                  d2 = S.d[3 * v + 2] + nb.d[2];
+                        if (tracer) {
+                            const int64_t s_lin = (((int64_t)t * D.L[2] + z) * D.L[1] + y) * D.L[0] + x;
+                            const int64_t j_lin = (((int64_t)j.t2 * D.L[2] + j.jz) * D.L[1] + j.jy) * D.L[0] + j.jx;
+                            int32_t* ts = tracer + 3 * (D.site_off + s_lin);
+                            int32_t* tj = tracer + 3 * (D.site_off + j_lin);
+                            ts[0] = tj[0] - nb.d[0];
+                            ts[1] = tj[1] - nb.d[1];
+                            ts[2] = tj[2] - nb.d[2];
+                            tj[0] = tj[1] = tj[2] = 0;
+                        }
+                        const uint32_t jk = key32(j.t2, j.jx, j.jy, j.jz);
+                        if (owned) {
+                            S.d[3 * v] = d0;
+                            S.d[3 * v + 1] = d1;
+                            S.d[3 * v + 2] = d2;
+                            S.key[v] = jk;
+                        } else {
+                            wslot[m] = -1;
+                            uint32_t o2;
+                            int lf2;
+                            cowner(sh, S, geo, j.jx, j.jy, j.jz, o2, lf2);
+                            if (o2 == me) {  // another fragment of this slab: onto its list
+                                S.d[3 * v] = d0;
+                                S.d[3 * v + 1] = d1;
+                                S.d[3 * v + 2] = d2;
+                                S.key[v] = jk;
+                                S.next[v] = (int16_t)atomicExch(S.head + lf2, v);
+                            } else {  // another slab: into its inbox, the slot back to the free stack
+                                const int bidx = (int)(ph & 1u);
+                                const uint32_t e =
+                                    atom_peer_add(peer_addr(&sh.inbox_n[bidx], o2), 1u);
+                                if ((int)e < P.icap) {
+                                    const uint32_t base = peer_addr(S.inbox + bidx * P.icap + (int)e, o2);
+                                    st_peer(base, jk);
+                                    st_peer(base + 4, d0);
+                                    st_peer(base + 8, d1);
+                                    st_peer(base + 12, d2);
+                                    st_peer(base + 16, S.id[v]);
+                                    st_peer(base + 20, lf2);
+                                } else {
+                                    atomicOr(status, STATUS_OVERFLOW);
+                                }
+                                S.fstack[atomicAdd(&sh.free_top, 1)] = (int16_t)v;
+                            }
+                            ++my_hand;
+                        }
+                    }
+                    __syncwarp();
+                    // the fragments whose totals changed: owners of the vacancies next to
+                    // the two changed sites (lanes 0-7 look around s, 8-15 around j)
+                    if (lane < 16) {
+                        const int bt = lane < 8 ? t : j.t2;
+                        const int bx = lane < 8 ? x : j.jx, by = lane < 8 ? y : j.jy, bz = lane < 8 ? z : j.jz;
+                        const NbSite c = cnb_site(sh, geo, bt, bx, by, bz, lane & 7);
+                        if (csite_code(sh, S, geo, me, c.t2, c.jx, c.jy, c.jz) == SP_V) {
+                            uint32_t oc;
+                            int lc;
+                            cowner(sh, S, geo, c.jx, c.jy, c.jz, oc, lc);
+                            if (oc == me) {
+                                if (lc != lf) S.dirty[lc] = 1;
+                            } else {
+                                st_peer8(peer_addr(S.dirty + lc, oc), 1);
+                            }
+                        }
+                    }
+                    compute_types();
+                    clock = nclock;
+                    ++i;
+                }
+                // surviving vacancies stay linked to this fragment, in slot order
+                if (lane == 0) {
+                    int head = -1;
+                    for (int m = n - 1; m >= 0; --m) {
+                        const int v = wslot[m];
+                        if (v < 0) continue;
+                        S.next[v] = (int16_t)head;
+                        head = v;
+                    }
+                    S.head[lf] = head;
+                    S.S[lf] = tot;
+                    S.dirty[lf] = 0;
+                    my_hops += i;
+                }
+                __syncwarp();
+            }
+            cluster_sync();  // every write of the phase, local and remote, is visible
+        }
+    }
+    if (ph > 0) drain((ph - 1) & 1);
+
+    // ---- stage out: this slab's occupancy planes, its fragments' records
+    for (int k = tid; k < 3 * plane; k += NT) {
+        const int t = k / plane, r = k - t * plane;
+        occ[D.occ_word_off + ((int64_t)t * D.L[2] + zb) * D.L[1] * D.row_words + r] =
+            S.occ[t * P.zs * D.L[1] * D.row_words + r];
+    }
+    for (int lf = tid; lf < nfl_me; lf += NT) {
+        const int64_t g = D.frag_base + (int64_t)fzb * D.nf[1] * D.nf[0] + lf;
+        int k = 0;
+        for (int v = S.head[lf]; v >= 0; v = S.next[v], ++k) {
+            if (k >= cap) {
+                atomicOr(status, STATUS_OVERFLOW);
+                break;
+            }
+            int t, x, y, z;
+            split32(S.key[v], t, x, y, z);
+            VacRec rr;
+            rr.key = make_key(t, x, y, z);
+            rr.d[0] = S.d[3 * v];
+            rr.d[1] = S.d[3 * v + 1];
+            rr.d[2] = S.d[3 * v + 2];
+            rr.id = S.id[v];
+            recs[g * cap + k] = rr;
+        }
+        counts[g] = k;
+    }
+    atomicAdd(&sh.hops, my_hops);
+    atomicAdd(&sh.hand, my_hand);
+    __syncthreads();
+    if (tid == 0) {
+        if (sh.hops) atomicAdd(stats + 2 * P.rep, sh.hops);
+        if (sh.hand) atomicAdd(stats + 2 * P.rep + 1, sh.hand);
+    }
+    cluster_sync();  // no CTA leaves while a peer may still address it
+}
+
+size_t cluster_smem_bytes(const RepDesc& D, const ClusterPlan& p, int cap)
+{
+    return cluster_layout_bytes(D, p, cap, CLUSTER_THREADS / 32, nullptr);
+}
+
+bool make_cluster_plan(const RepDesc& D, int64_t n_vac, int cap, int min_ctas, int max_ctas, ClusterPlan* out)
+{
+    if (D.L[0] > 1024 || D.L[1] > 1024 || D.L[2] > 1024 || D.nf[2] < 2) return false;
+    const int nf2 = D.nf[2];
+    for (int nc = std::max(2, min_ctas); nc <= std::min(max_ctas, CLUSTER_MAX_CTAS) && nc <= nf2; ++nc) {
+        ClusterPlan p{};
+        p.ncta = nc;
+        int zs = 0, layers = 0;
+        for (int c = 0; c <= nc; ++c) p.fz0[c] = (int)((int64_t)c * nf2 / nc);
+        for (int c = 0; c < nc; ++c) {
+            const int z0 = p.fz0[c] * D.base[2] + std::min(p.fz0[c], D.rem[2]);
+            const int z1 = p.fz0[c + 1] * D.base[2] + std::min(p.fz0[c + 1], D.rem[2]);
+            zs = std::max(zs, z1 - z0);
+            layers = std::max(layers, p.fz0[c + 1] - p.fz0[c]);
+        }
+        p.zs = zs;
+        p.nfl = layers * D.nf[0] * D.nf[1];
+        // the inbox takes a phase's arrivals through the slab's two faces: at most the
+        // vacancies of the two neighbouring cell layers (a vacancy crosses once per
+        // phase), with a margin of eight standard deviations
+        const double per_layer = 2.0 * (double)n_vac / D.L[2];
+        p.icap = (int)std::min<double>(8192.0, std::ceil(per_layer + 8.0 * std::sqrt(per_layer) + 64.0));
+        // the vacancy pool: whatever shared memory is left, at least twice the slab's share
+        p.vcap = 0;
+        const size_t fixed = cluster_layout_bytes(D, p, cap, CLUSTER_THREADS / 32, nullptr);
+        if (fixed > RESIDENT_MAX_SMEM) continue;
+        const int64_t share = (n_vac * layers + nf2 - 1) / nf2;
+        const int64_t room = (int64_t)(RESIDENT_MAX_SMEM - fixed) / 24 - 64;
+        const int64_t vcap = std::min<int64_t>(32767, room);
+        if (vcap < 2 * share + 64) continue;
+        p.vcap = (int)vcap;
+        if (cluster_layout_bytes(D, p, cap, CLUSTER_THREADS / 32, nullptr) > RESIDENT_MAX_SMEM) continue;
+        *out = p;
+        return true;
+    }
+    return false;
+}
+
+cudaError_t cluster_prepare()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_cluster<CLUSTER_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)RESIDENT_MAX_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_cluster<CLUSTER_THREADS>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
+int cluster_fits(int ncta, size_t smem)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ncta);
+    cfg.blockDim = dim3(CLUSTER_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)ncta;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_cluster<CLUSTER_THREADS>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+cudaError_t launch_cluster(const RepDesc* d_descs, const ClusterPlan* d_plans, int nplans, int ncta, size_t smem,
+                           uint64_t windows, uint32_t* occ, VacRec* recs, int32_t* counts, int32_t* tracer,
+                           unsigned long long* stats, uint32_t* status, int cap, const NbTable& nbt, cudaStream_t st)
+{
+    if (nplans <= 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(ncta * nplans));
+    cfg.blockDim = dim3(CLUSTER_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)ncta;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_cluster<CLUSTER_THREADS>, d_descs, d_plans, windows, occ, recs, counts, tracer,
+                              stats, status, cap, nbt);
 }
 
 cudaError_t resident_prepare()

@@ -67,7 +67,7 @@ class kmc_opts(C.Structure):
                 ("stream", C.c_void_p), ("alloc", kmc_alloc_fn), ("free", kmc_free_fn),
                 ("alloc_ctx", C.c_void_p), ("schedule", C.c_int32), ("cluster_top", C.c_int32),
                 ("small_pass", C.c_int32), ("test_stuck_wait_us", C.c_int32), ("lane_form", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("cluster_ctas", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class kmc_run_stats(C.Structure):
@@ -443,7 +443,7 @@ class Batch:
 
     def __init__(self, cells, comps, seed=0, *, edge=4, nfrag=None, precision=FKMC_PLAIN,
                  tracer=False, cap_v=0, n_tau=1.0, schedule=0, cluster_top=-1, small_pass=0, stream=None,
-                 test_stuck_wait_us=0, alloc=None, lane_form=0):
+                 test_stuck_wait_us=0, alloc=None, lane_form=0, cluster_ctas=0):
         import torch
         self._alloc = TorchAllocator()
         o = kmc_default_opts()
@@ -459,6 +459,7 @@ class Batch:
         o.cluster_top = int(cluster_top)
         o.small_pass = int(small_pass)
         o.lane_form = int(lane_form)
+        o.cluster_ctas = int(cluster_ctas)
         o.test_stuck_wait_us = int(test_stuck_wait_us)
         st = stream if stream is not None else torch.cuda.current_stream()
         o.stream = C.c_void_p(st.cuda_stream)

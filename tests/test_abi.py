@@ -90,7 +90,8 @@ def test_site_shell_tables_match_oracle(lib):
 
 @pytest.mark.parametrize("field,value", [("small_pass", 3), ("small_pass", -2), ("schedule", 3), ("precision", 5),
                                          ("cap_v", 12), ("n_tau", 0.0), ("n_tau", 65.0), ("lane_form", 3),
-                                         ("lane_form", -1)])
+                                         ("lane_form", -1), ("cluster_ctas", 1), ("cluster_ctas", -2),
+                                         ("cluster_ctas", 17)])
 def test_create_batch_rejects_bad_options(lib, field, value):
     """Options are checked before any device work: a bad value is FKMC_EINVAL
     (so this runs without a GPU)."""
@@ -104,6 +105,7 @@ def test_create_batch_rejects_bad_options(lib, field, value):
 def test_default_options_of_the_run_passes(lib):
     o = lib.kmc_default_opts()
     assert o.small_pass == 0 and o.schedule == 0 and o.cluster_top == -1 and o.lane_form == 0
+    assert o.cluster_ctas == 0
 
 
 @pytest.mark.parametrize("tracer,n_fe", [(0, 0), (1, 0), (0, 3)])
