@@ -135,6 +135,7 @@ struct kmc_batch {
     NbTable nbt{};
     int32_t* d_reps = nullptr;   // resident replica ids, class by class
     ClusterPlan* d_plans = nullptr;  // cluster-resident replicas' slab plans, grouped by CTA count
+    ResCache rcache{};               // fragment totals the resident kernels carry from call to call
     int64_t* d_nvac = nullptr;   // vacancies per replica
     // a launch of the replica-resident kernel (one CTA, or a 2-CTA mirrored pair, per
     // replica; start/count index d_reps) or of the cluster-resident kernel (slabs
@@ -300,6 +301,14 @@ namespace {
 // the site-energy run pass is on: shells, dopant energies or electrostatics
 bool site_path(const kmc_batch* b) { return b->site_on || b->elec_on; }
 
+// anything but a resident run changed a replica's state or rates: the resident
+// kernels' fragment totals from the last call no longer hold
+int drop_resident_cache(kmc_batch* b)
+{
+    if (b->rcache.valid) CK(cudaMemsetAsync(b->rcache.valid, 0, (size_t)b->n, b->st), "memset");
+    return FKMC_OK;
+}
+
 // kernel launches of one window of the colour-phase path: set-up, then per phase
 // screen + run, + the grouped small pass where it runs, or the one-thread-per-
 // fragment pass + run
@@ -372,6 +381,7 @@ bool valid_replica(const kmc_batch* b, int32_t r) { return b && r >= 0 && r < b-
 // into shared-memory size classes (one launch per class, on forked streams).
 int plan_residency(kmc_batch* b)
 {
+    if (int rc0 = drop_resident_cache(b)) return rc0;
     if (b->res_exec) cudaGraphExecDestroy(b->res_exec);  // it holds the old classes' launches
     b->res_exec = nullptr;
     for (auto& c : b->rclass) {
@@ -925,6 +935,9 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
     b->scratch_all = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * 7 * n);
     b->d_reps = (int32_t*)b->dalloc(sizeof(int32_t) * n);
     b->d_plans = (ClusterPlan*)b->dalloc(sizeof(ClusterPlan) * n);
+    b->rcache.tot = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * std::max<int64_t>(b->nfrag_total, 1));
+    b->rcache.dirty = (uint8_t*)b->dalloc((size_t)std::max<int64_t>(b->nfrag_total, 1));
+    b->rcache.valid = (uint8_t*)b->dalloc((size_t)n);
     b->d_nvac = (int64_t*)b->dalloc(sizeof(int64_t) * n);
     b->wctl = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * 2);
     b->perms = (uint32_t*)b->dalloc(sizeof(uint32_t) * n);
@@ -943,7 +956,8 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
         }
     }
     if (!b->occ || !b->recs || !b->counts || (o.tracer && !b->tracer) || !b->d_desc || !b->stats ||
-        !b->status || !b->scratch || !b->scratch_all || !b->d_reps || !b->d_plans || !b->d_nvac || !b->wctl ||
+        !b->status || !b->scratch || !b->scratch_all || !b->d_reps || !b->d_plans || !b->rcache.tot ||
+        !b->rcache.dirty || !b->rcache.valid || !b->d_nvac || !b->wctl ||
         !b->perms ||
         !b->act || !b->act_count || !b->cls) {
         b->release();
@@ -968,6 +982,7 @@ int kmc_create_batch(int32_t n, const kmc_cells* cells, const kmc_composition* c
     step(cudaMemsetAsync(b->counts, 0, sizeof(int32_t) * b->nfrag_total, b->st), "memset");
     if (o.tracer) step(cudaMemsetAsync(b->tracer, 0, sizeof(int32_t) * 3 * b->nsite_total, b->st), "memset");
     step(cudaMemsetAsync(b->stats, 0, sizeof(unsigned long long) * 2 * n, b->st), "memset");
+    step(cudaMemsetAsync(b->rcache.valid, 0, (size_t)n, b->st), "memset");
     step(cudaMemsetAsync(b->status, 0, sizeof(uint32_t), b->st), "memset");
     for (int r = 0; r < n && rc == FKMC_OK; ++r)
         step(launch_init(b->desc[r], b->b_bits[r], b->n_vac[r], b->n_vac[r] + b->n_H[r], b->occ, b->recs,
@@ -1070,11 +1085,13 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
                 le = cudaStreamWaitEvent(c.st, b->fork, 0);
                 if (le == cudaSuccess && c.slabs)
                     le = launch_cluster(b->d_desc, b->d_plans + c.start, c.count, c.cluster, c.smem, windows, b->occ,
-                                        b->recs, b->counts, b->tracer, b->stats, b->status, b->cap, b->nbt, c.st);
+                                        b->recs, b->counts, b->tracer, b->stats, b->status, b->cap, b->nbt, b->rcache,
+                                        c.st);
                 else if (le == cudaSuccess)
                     le = launch_resident(b->d_desc, b->d_reps + c.start, c.count, b->d_nvac, c.smem, c.threads,
                                          c.cluster, windows, b->occ, b->recs, b->counts, b->tracer, b->stats,
-                                         b->status, b->cap, b->nbt, (uint32_t)b->opts.test_stuck_wait_us, c.st);
+                                         b->status, b->cap, b->nbt, (uint32_t)b->opts.test_stuck_wait_us, b->rcache,
+                                         c.st);
                 if (le == cudaSuccess) le = cudaEventRecord(c.done, c.st);
                 if (le == cudaSuccess) le = cudaStreamWaitEvent(b->cap_st, c.done, 0);
             }
@@ -1293,6 +1310,10 @@ int kmc_run_null(kmc_batch* b, uint64_t steps, int64_t n_frg, kmc_run_stats* sta
        "clock copy");
     rc = check_status(b);
     b->field_valid = false;
+    {
+        const int rc_ = drop_resident_cache(b);
+        if (rc_) return rc_;
+    }
     if (stats) {
         std::memset(stats, 0, sizeof *stats);
         for (int r = 0; r < b->n; ++r) stats->hops += b->stats_host[2 * r] - before[2 * r];
@@ -1437,6 +1458,10 @@ int kmc_write_state(kmc_batch* b, int32_t r, const uint8_t* host_occ, size_t n)
     b->n_vac[r] = nv;
     b->n_H[r] = nh;
     b->field_valid = false;
+    {
+        const int rc_ = drop_resident_cache(b);
+        if (rc_) return rc_;
+    }
     b->elec_age = UINT64_MAX / 2;  // the potential is solved again at the next refresh point
     b->phi_prev_valid = false;  // and from zero: the vacancies may have moved anywhere
     drop_window_graph(b);       // the captured solves hold the vacancy count
@@ -1648,6 +1673,10 @@ int kmc_upload_state(kmc_batch* b, const void* host, size_t bytes)
            "clock upload");
     CK(cudaStreamSynchronize(b->st), "synchronize");
     b->field_valid = false;  // the site-energy field is rebuilt from the restored vacancies, dopants and u
+    {
+        const int rc_ = drop_resident_cache(b);
+        if (rc_) return rc_;
+    }
     if (blob_flags(b) & BLOB_ELEC) {
         b->elec_age = hd.elec_age;
         b->phi_prev_valid = hd.phi_prev_valid != 0;
@@ -1674,6 +1703,10 @@ int kmc_set_site_energy(kmc_batch* b, const kmc_site_energy* e)
             b->n_vv = b->n_bo = b->e_self = 0;  // electrostatics may keep the site-energy pass
             b->e_bound = 0;
             b->field_valid = false;
+            {
+                const int rc_ = drop_resident_cache(b);
+                if (rc_) return rc_;
+            }
             drop_window_graph(b);
             CK(run_pass_blocks(site_path(b) ? FKMC_PLAIN : b->opts.precision, b->cap, site_path(b), b->grains_on,
                                &b->run_blocks),
@@ -1723,6 +1756,10 @@ int kmc_set_site_energy(kmc_batch* b, const kmc_site_energy* e)
            "table upload");
     b->site_on = true;
     b->field_valid = false;
+    {
+        const int rc_ = drop_resident_cache(b);
+        if (rc_) return rc_;
+    }
     drop_window_graph(b);
     CK(run_pass_blocks(FKMC_PLAIN, b->cap, true, b->grains_on, &b->run_blocks), "occupancy query");
     if (b->rates_set) {
@@ -1768,6 +1805,10 @@ int kmc_set_electrostatics(kmc_batch* b, const kmc_electrostatics* e)
         b->elec_g.clear();
         b->elec_umax = 0;
         b->field_valid = false;
+        {
+            const int rc_ = drop_resident_cache(b);
+            if (rc_) return rc_;
+        }
         drop_window_graph(b);
         CK(run_pass_blocks(site_path(b) ? FKMC_PLAIN : b->opts.precision, b->cap, site_path(b), b->grains_on,
                            &b->run_blocks),
@@ -1858,6 +1899,10 @@ int kmc_set_electrostatics(kmc_batch* b, const kmc_electrostatics* e)
     b->elec_on = true;
     b->elec_umax = 0;
     b->field_valid = false;  // rebuilt with u at the next run
+    {
+        const int rc_ = drop_resident_cache(b);
+        if (rc_) return rc_;
+    }
     int rc = elec_refresh(b);
     if (rc) return rc;
     drop_window_graph(b);
@@ -1918,6 +1963,10 @@ int kmc_write_potential_energy(kmc_batch* b, int32_t r, const int32_t* u, size_t
     }
     CK(cudaStreamSynchronize(b->st), "synchronize");
     b->field_valid = false;
+    {
+        const int rc_ = drop_resident_cache(b);
+        if (rc_) return rc_;
+    }
     b->elec_age = 0;
     b->elec_umax = 0;  // re-derive the tables' range from what was written
     const int64_t keep = um;
@@ -2027,6 +2076,10 @@ int kmc_write_dopants(kmc_batch* b, int32_t r, const uint8_t* host_cells, size_t
     CK(cudaStreamSynchronize(b->st), "synchronize");
     b->n_fe[r] = cnt;
     b->field_valid = false;
+    {
+        const int rc_ = drop_resident_cache(b);
+        if (rc_) return rc_;
+    }
     return FKMC_OK;
 }
 

@@ -93,6 +93,16 @@ cudaError_t elec_update(const RepDesc& D, const double* phi, double q, int32_t* 
                         cudaStream_t st);
 cudaError_t elec_add(int32_t* field, const int32_t* u, int64_t n, cudaStream_t st);
 
+// Per-fragment event totals and dirty flags the resident kernels leave at the end
+// of a call (batch-wide fragment index), and per replica whether they are still
+// valid: the host clears `valid` whenever anything but a resident run changes a
+// replica's state or rates, and the next call then starts from every fragment dirty.
+struct ResCache {
+    unsigned long long* tot;
+    uint8_t* dirty;
+    uint8_t* valid;
+};
+
 // cluster-resident kernel (fkmc_resident.cu): one replica per thread-block cluster,
 // CTA c holding the z-slab of fragment layers [fz0[c], fz0[c+1])
 constexpr int CLUSTER_MAX_CTAS = 16;
@@ -113,7 +123,8 @@ cudaError_t cluster_prepare();
 int cluster_fits(int ncta, size_t smem);  // clusters of ncta CTAs with this much shared memory the GPU can hold at once
 cudaError_t launch_cluster(const RepDesc* d_descs, const ClusterPlan* d_plans, int nplans, int ncta, size_t smem,
                            uint64_t windows, uint32_t* occ, VacRec* recs, int32_t* counts, int32_t* tracer,
-                           unsigned long long* stats, uint32_t* status, int cap, const NbTable& nbt, cudaStream_t st);
+                           unsigned long long* stats, uint32_t* status, int cap, const NbTable& nbt,
+                           const ResCache& rc, cudaStream_t st);
 
 // replica-resident kernel (fkmc_resident.cu)
 constexpr int RESIDENT_MAX_SLOTS = 64;               // vacancies per fragment a thread can hold
@@ -123,6 +134,7 @@ cudaError_t resident_prepare();
 cudaError_t launch_resident(const RepDesc* d_descs, const int32_t* d_reps, int nreps, const int64_t* d_nvac,
                             size_t smem, int threads, int cluster, uint64_t windows, uint32_t* occ, VacRec* recs,
                             int32_t* counts, int32_t* tracer, unsigned long long* stats, uint32_t* status,
-                            int cap, const NbTable& nbt, uint32_t stuck_wait_us, cudaStream_t st);
+                            int cap, const NbTable& nbt, uint32_t stuck_wait_us, const ResCache& rc,
+                            cudaStream_t st);
 
 }  // namespace fkmc

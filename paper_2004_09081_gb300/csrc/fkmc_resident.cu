@@ -192,6 +192,7 @@ struct Shared {
     int next_act;
     unsigned long long hops, hand;
     int abort;
+    int cached;  // the fragment totals of the last call are valid
 };
 
 struct Layout {
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                                                   uint32_t* occ, VacRec* recs, int32_t* counts,
                                                   int32_t* tracer, unsigned long long* stats,
                                                   uint32_t* status, int cap, NbTable nbt,
-                                                  uint32_t stuck_wait_us)
+                                                  uint32_t stuck_wait_us, ResCache rc)
 {
     extern __shared__ __align__(128) unsigned char dyn[];
     __shared__ Shared sh;
@@ -345,6 +346,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
         sh.hops = 0;
         sh.hand = 0;
         sh.abort = 0;
+        sh.cached = rc.valid[r];
     }
     if (tid < 24) (&sh.nb[0][0])[tid] = (&nbt.e[0][0])[tid];  // threads index it with different t
     __syncthreads();
@@ -394,8 +396,9 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
         }
         if (c > cap) atomicOr(status, STATUS_OVERFLOW);
         S.head[f] = head;
-        S.dirty[f] = 1;
-        S.S[f] = 0ull;
+        // the fragment totals the last call left, where nothing changed the replica since
+        S.dirty[f] = sh.cached ? rc.dirty[g] : 1;
+        S.S[f] = sh.cached ? rc.tot[g] : 0ull;
     }
     __syncthreads();  // the barrier init is visible to every thread from here on
     if (rank == 0 && !mbar_wait_bounded(&sh.bar, 0, WAIT_NS)) {
@@ -795,6 +798,8 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
             recs[g * cap + k] = rr;
         }
         counts[g] = k;
+        rc.tot[g] = S.S[f];
+        rc.dirty[g] = S.dirty[f];
     }
     atomicAdd(&sh.hops, my_hops);
     atomicAdd(&sh.hand, my_hand);
@@ -802,7 +807,10 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
     if (tid == 0) {
         if (sh.hops) atomicAdd(stats + 2 * r, sh.hops);
         if (sh.hand) atomicAdd(stats + 2 * r + 1, sh.hand);
-        if (rank == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        if (rank == 0) {
+            asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+            rc.valid[r] = 1;
+        }
     }
     if constexpr (CL > 1) cluster_sync();  // no CTA leaves while its peer may still address it
 }
@@ -848,6 +856,7 @@ struct CShared {
     int inbox_n[2];
     int free_top;
     int pool_n;
+    int cached;  // the fragment totals of the last call are valid
     unsigned long long hops, hand;
 };
 
@@ -1003,7 +1012,8 @@ template <int NT>
 __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ descs,
                                                    const ClusterPlan* __restrict__ plans, uint64_t windows,
                                                    uint32_t* occ, VacRec* recs, int32_t* counts, int32_t* tracer,
-                                                   unsigned long long* stats, uint32_t* status, int cap, NbTable nbt)
+                                                   unsigned long long* stats, uint32_t* status, int cap, NbTable nbt,
+                                                   ResCache rc)
 {
     extern __shared__ __align__(128) unsigned char dyn[];
     __shared__ CShared sh;
@@ -1020,6 +1030,7 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
         sh.pool_n = 0;
         sh.hops = 0;
         sh.hand = 0;
+        sh.cached = rc.valid[sh.P.rep];
     }
     if (tid < 24) (&sh.nb[0][0])[tid] = (&nbt.e[0][0])[tid];
     __syncthreads();
@@ -1072,8 +1083,8 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
         }
         if (c > cap) atomicOr(status, STATUS_OVERFLOW);
         S.head[lf] = head;
-        S.dirty[lf] = 1;
-        S.S[lf] = 0ull;
+        S.dirty[lf] = sh.cached ? rc.dirty[g] : 1;
+        S.S[lf] = sh.cached ? rc.tot[g] : 0ull;
     }
     __syncthreads();
     {
@@ -1469,6 +1480,8 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
             recs[g * cap + k] = rr;
         }
         counts[g] = k;
+        rc.tot[g] = S.S[lf];
+        rc.dirty[g] = S.dirty[lf];
     }
     atomicAdd(&sh.hops, my_hops);
     atomicAdd(&sh.hand, my_hand);
@@ -1478,6 +1491,7 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
         if (sh.hand) atomicAdd(stats + 2 * P.rep + 1, sh.hand);
     }
     cluster_sync();  // no CTA leaves while a peer may still address it
+    if (tid == 0 && me == 0) rc.valid[P.rep] = 1;
 }
 
 size_t cluster_smem_bytes(const RepDesc& D, const ClusterPlan& p, int cap)
@@ -1555,7 +1569,8 @@ int cluster_fits(int ncta, size_t smem)
 
 cudaError_t launch_cluster(const RepDesc* d_descs, const ClusterPlan* d_plans, int nplans, int ncta, size_t smem,
                            uint64_t windows, uint32_t* occ, VacRec* recs, int32_t* counts, int32_t* tracer,
-                           unsigned long long* stats, uint32_t* status, int cap, const NbTable& nbt, cudaStream_t st)
+                           unsigned long long* stats, uint32_t* status, int cap, const NbTable& nbt,
+                           const ResCache& rc, cudaStream_t st)
 {
     if (nplans <= 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
@@ -1571,7 +1586,7 @@ cudaError_t launch_cluster(const RepDesc* d_descs, const ClusterPlan* d_plans, i
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_cluster<CLUSTER_THREADS>, d_descs, d_plans, windows, occ, recs, counts, tracer,
-                              stats, status, cap, nbt);
+                              stats, status, cap, nbt, rc);
 }
 
 cudaError_t resident_prepare()
@@ -1588,7 +1603,7 @@ cudaError_t resident_prepare()
 cudaError_t launch_resident(const RepDesc* d_descs, const int32_t* d_reps, int nreps, const int64_t* d_nvac,
                             size_t smem, int threads, int cluster, uint64_t windows, uint32_t* occ, VacRec* recs,
                             int32_t* counts, int32_t* tracer, unsigned long long* stats, uint32_t* status,
-                            int cap, const NbTable& nbt, uint32_t stuck_wait_us, cudaStream_t st)
+                            int cap, const NbTable& nbt, uint32_t stuck_wait_us, const ResCache& rc, cudaStream_t st)
 {
     if (nreps <= 0) return cudaSuccess;
     if (cluster == 2 && threads == 1024) {
@@ -1605,20 +1620,20 @@ cudaError_t launch_resident(const RepDesc* d_descs, const int32_t* d_reps, int n
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         return cudaLaunchKernelEx(&cfg, k_resident<1024, 2>, d_descs, d_reps, d_nvac, windows, occ, recs, counts,
-                                  tracer, stats, status, cap, nbt, stuck_wait_us);
+                                  tracer, stats, status, cap, nbt, stuck_wait_us, rc);
     }
     if (threads == 128)
         k_resident<128, 1><<<nreps, 128, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts, tracer,
-                                                     stats, status, cap, nbt, stuck_wait_us);
+                                                     stats, status, cap, nbt, stuck_wait_us, rc);
     else if (threads == 256)
         k_resident<256, 1><<<nreps, 256, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts, tracer,
-                                                     stats, status, cap, nbt, stuck_wait_us);
+                                                     stats, status, cap, nbt, stuck_wait_us, rc);
     else if (threads == 1024)
         k_resident<1024, 1><<<nreps, 1024, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts,
-                                                       tracer, stats, status, cap, nbt, stuck_wait_us);
+                                                       tracer, stats, status, cap, nbt, stuck_wait_us, rc);
     else
         k_resident<512, 1><<<nreps, 512, smem, st>>>(d_descs, d_reps, d_nvac, windows, occ, recs, counts, tracer,
-                                                     stats, status, cap, nbt, stuck_wait_us);
+                                                     stats, status, cap, nbt, stuck_wait_us, rc);
     return cudaGetLastError();
 }
 

@@ -353,3 +353,35 @@ def test_persistent_lane_form_by_default_on_the_largest_phases(fk):
         b.close()
     assert res[0][0] == res[1][0] > 0 and res[0][1] == res[1][1]
     assert np.array_equal(res[0][2], res[1][2]) and np.array_equal(res[0][3], res[1][3])
+
+
+@pytest.mark.parametrize("cluster", [0, 2])
+def test_resident_totals_carried_between_calls_and_dropped_on_change(fk, orc, cluster):
+    """The resident kernels keep each fragment's exact event total from one call
+    to the next; new rates (another temperature) or a rewritten state make them
+    start over.  Runs split into calls, a rate change and a state round trip in
+    between, bit for bit against the oracle doing the same."""
+    cells, nf, nv, nh = (12, 12, 16), (2, 2, 4), 60, 150
+    b = fk.Batch([(*cells, 4.01)], [(nv, nh)], 31, nfrag=nf, precision=1, cap_v=32, schedule=2,
+                 cluster_ctas=cluster)
+    ref = orc.Lattice(cells, nf, nv, nh, seed=31)
+    b.set_barriers(0.6, 0.35, 900.0)
+    ref.set_rates(0.6, 0.35, 900.0, a_ang=4.01, cap_v=32, precision=1)
+    for w in (7, 1, 12):
+        b.run(w)
+        ref.run(w)
+    assert np.array_equal(b.state(), ref.occupancy())
+    b.set_barriers(0.6, 0.35, 1200.0)
+    ref.set_rates(0.6, 0.35, 1200.0, a_ang=4.01, cap_v=32, precision=1)
+    for w in (5, 9):
+        b.run(w)
+        ref.run(w)
+    assert np.array_equal(b.state(), ref.occupancy())
+    assert np.array_equal(b.records(), ref.records())
+    # the same occupancy written back (records rebuilt from it: new ids, zero
+    # displacements): the totals are recomputed and the occupancy goes on as the oracle's
+    b.write_state(b.state())
+    b.run(10)
+    ref.run(10)
+    assert np.array_equal(b.state(), ref.occupancy())
+    assert b.info().hops == ref.counters()["hops"] > 200
