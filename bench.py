@@ -498,6 +498,8 @@ def main():
 
     peak, peak_kind = load_peaks()
     all_resident = (not null) and n_launch <= args.steps * 5  # class launches only, no per-phase launches
+    kinds = [b.info(r).kernel for r in range(nrep)]
+    on_cluster = all_resident and all(k == 2 for k in kinds)
     if null:
         # one unit = one null-event step (rates, propose, apply + clock: three launches)
         units = args.steps * W
@@ -506,10 +508,14 @@ def main():
                 "(rates), every pick's record, 8 words, proposal and 2 claims (propose), its proposal and "
                 "claims plus 2 words and a record per applied hop (apply)")
     elif all_resident:
-        # the replica-resident kernel: one launch per shared-memory size class per call, the
-        # classes run concurrently, so a "launch" here is one call's concurrent set
+        # the resident kernels: one launch per class per call (the classes run concurrently),
+        # so a "launch" here is one call's concurrent set
         units = args.steps
-        tag, kname = "k_resident_batched", "k_resident (replica-resident window kernel)"
+        if on_cluster:
+            tag = "k_cluster_" + args.workload
+            kname = "k_cluster (cluster-resident window kernel, %d CTAs per replica)" % b.info(0).ctas
+        else:
+            tag, kname = "k_resident_" + args.workload, "k_resident (replica-resident window kernel)"
         note = ("lattice state lives in shared memory for the whole launch: DRAM traffic is the stage-in/out "
                 "of the state, not per hop; the kernel is bound by instruction issue and dependent latency "
                 "(see profiles/)")
@@ -778,7 +784,9 @@ def main():
                        "l2": "flushed between timed steps (256 MiB write)",
                        "schedule": ("null-event steps (Sec. II.B), one pick per vacancy, %d steps per "
                                     "benchmark step" % W if null else
-                                    "replica-resident kernel per shared-memory size class" if all_resident
+                                    ("cluster-resident kernel: one thread-block cluster per replica, a z-slab "
+                                     "of fragment layers per CTA" if on_cluster else
+                                     "replica-resident kernel per shared-memory size class") if all_resident
                                     else "colour-phase kernel, one launch per phase"),
                        "seed": args.seed},
             "roofline": roofline,

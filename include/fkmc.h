@@ -179,6 +179,11 @@ typedef struct {
     double null_theta;   /* its clock in units of 1/k32max */
     double null_time_s;  /* its simulated time, s (included in kmc_read_msd's t) */
     int64_t n_Fe;        /* dopants */
+    int32_t kernel;      /* how kmc_run advances the replica under the current rates and options:
+                            0 = colour-phase kernels (one launch per phase), 1 = replica-resident
+                            kernel (state in one SM's shared memory, or a 2-CTA mirrored pair),
+                            2 = cluster-resident kernel (z-slabs in a thread-block cluster) */
+    int32_t ctas;        /* CTAs holding the replica (kernels 1 and 2), else 0 */
 } kmc_replica_info;
 
 typedef struct kmc_batch kmc_batch;

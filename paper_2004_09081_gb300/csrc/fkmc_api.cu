@@ -159,6 +159,7 @@ struct kmc_batch {
     cudaEvent_t side_fork = nullptr, side_join = nullptr;
     bool any_global = true;
     int cluster_top = 0;  // how many of the largest replicas run as 2-CTA clusters (kmc_opts)
+    std::vector<int32_t> run_kernel, run_ctas;  // per replica: kmc_replica_info.kernel and .ctas
     // colour-phase path: per-window set-up, screen and run, captured once in a graph
     unsigned long long* wctl = nullptr;  // [0] windows of this call so far, [1] current offset
     uint32_t* perms = nullptr;           // colour order of every replica, this window
@@ -402,6 +403,8 @@ int plan_residency(kmc_batch* b)
     std::vector<size_t> cmax(6, 0), need_of(b->n, 0);
     std::vector<ClusterPlan> plans;
     b->any_global = false;
+    b->run_kernel.assign(b->n, 0);
+    b->run_ctas.assign(b->n, 0);
     for (int r = 0; r < b->n; ++r) {
         int c = -1;
         size_t need = 0;
@@ -420,6 +423,8 @@ int plan_residency(kmc_batch* b)
                 pl.rep = r;
                 plans.push_back(pl);
                 b->desc[r].resident = 1;
+                b->run_kernel[r] = 2;
+                b->run_ctas[r] = pl.ncta;
                 continue;
             }
         }
@@ -430,6 +435,8 @@ int plan_residency(kmc_batch* b)
         }
         cls[c].push_back(r);
         need_of[r] = need;
+        b->run_kernel[r] = 1;
+        b->run_ctas[r] = 1;
     }
     // largest replicas (by vacancies, the work per phase) first in every class: the
     // longest-running CTAs start earliest, which shortens the tail of the launch
@@ -441,6 +448,7 @@ int plan_residency(kmc_batch* b)
     const int ntop = std::min<int>((int)cls[3].size(), b->cluster_top);
     cls[5].assign(cls[3].begin(), cls[3].begin() + ntop);
     cls[3].erase(cls[3].begin(), cls[3].begin() + ntop);
+    for (int r : cls[5]) b->run_ctas[r] = 2;
     for (int c = 0; c < 6; ++c)
         for (int r : cls[c]) cmax[c] = std::max(cmax[c], need_of[r]);
     if (b->opts.schedule == 2 && b->any_global)
@@ -2124,6 +2132,10 @@ int kmc_get_replica_info(kmc_batch* b, int32_t r, kmc_replica_info* out)
     out->null_theta = b->theta_host[r];
     out->null_time_s = null_time(b, r);
     out->n_Fe = b->n_fe[r];
+    if ((int)b->run_kernel.size() == b->n) {
+        out->kernel = b->run_kernel[r];
+        out->ctas = b->run_ctas[r];
+    }
     return FKMC_OK;
 }
 

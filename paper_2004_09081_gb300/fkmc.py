@@ -81,7 +81,8 @@ class kmc_replica_info(C.Structure):
                 ("k64", C.c_double * 6), ("q", C.c_uint64 * 6), ("window", C.c_uint64),
                 ("hops", C.c_uint64), ("handoffs", C.c_uint64), ("nsite", C.c_int64),
                 ("n_vac", C.c_int64), ("n_H", C.c_int64), ("null_steps", C.c_uint64),
-                ("null_theta", C.c_double), ("null_time_s", C.c_double), ("n_Fe", C.c_int64)]
+                ("null_theta", C.c_double), ("null_time_s", C.c_double), ("n_Fe", C.c_int64),
+                ("kernel", C.c_int32), ("ctas", C.c_int32)]
 
 
 _P, _I32, _I64, _U64, _SZ, _D = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_size_t, C.c_double

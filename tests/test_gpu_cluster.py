@@ -43,6 +43,7 @@ def test_forced_slabs_bit_exact(fk, orc, cells, nf, ncta):
     b.set_barriers(0.6, 0.4, 1000.0, field_z=3e7)
     ref = orc.Lattice(cells, nf, nv, nh, seed=9, tracer=True)
     ref.set_rates(0.6, 0.4, 1000.0, Ez=3e7, a_ang=4.01, cap_v=32, n_tau=2.0, precision=1)
+    assert (b.info().kernel, b.info().ctas) == (2, ncta)
     for _ in range(3):
         s = b.run(40)
         assert s.launches == 1  # one cluster launch per call
@@ -60,6 +61,7 @@ def test_large_replica_takes_the_cluster_by_default(fk, orc):
     comps = [(2000, 6000), (20, 50)]
     b = fk.Batch([(*c, 4.01) for c in cells], comps, 4, edge=4, precision=1, cap_v=32)
     b.set_barriers(0.7, 0.35, [600.0, 900.0], field_z=[1e7, 0.0])
+    assert b.info(0).kernel == 2 and b.info(1).kernel == 1 and b.info(1).ctas == 1
     s = b.run(12)
     assert s.launches == 2  # the cluster launch and the single-CTA class launch
     for r, (c, (nv, nh)) in enumerate(zip(cells, comps)):
@@ -79,6 +81,7 @@ def test_bulk_hydride_lattice_on_sixteen_slabs(fk, orc):
     b.set_barriers(0.7, 0.35, 400.0)
     ref = orc.Lattice(cells, nf, nv, nh, seed=0)
     ref.set_rates(0.7, 0.35, 400.0, a_ang=4.01, cap_v=b.info().cap_v, n_tau=0.5, precision=1)
+    assert (b.info().kernel, b.info().ctas) == (2, 16)
     s = b.run(24)
     assert s.launches == 1
     ref.run(24)
