@@ -1192,7 +1192,7 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                 }
                 if (active) {
                     const int a = atomicAdd(&sh.nact, 1);
-                    S.act[a] = lf;
+                    S.act[a] = f0 | (f1 << 10) | (f2 << 20);  // fragment coordinates (< 1024 each)
                     S.act_E[2 * a] = E0;
                     S.act_E[2 * a + 1] = neglog32(blk.x[2]);
                     S.act_xs[2 * a] = blk.x[1];
@@ -1207,10 +1207,9 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                 if (lane == 0) a = atomicAdd(&sh.next_act, 1);
                 a = __shfl_sync(FULL, a, 0);
                 if (a >= nact) break;
-                const int lf = S.act[a];
-                const int fx = lf % D.nf[0];
-                const int fy = (lf / D.nf[0]) % D.nf[1];
-                const int fz = fzb + lf / (D.nf[0] * D.nf[1]);
+                const int fxyz = S.act[a];
+                const int fx = fxyz & 1023, fy = (fxyz >> 10) & 1023, fz = fxyz >> 20;
+                const int lf = ((fz - fzb) * D.nf[1] + fy) * D.nf[0] + fx;
                 const int fid = (fz * D.nf[1] + fy) * D.nf[0] + fx;
                 const int lo0 = frag_start(fx, D.base[0], D.rem[0]), hi0 = frag_start(fx + 1, D.base[0], D.rem[0]);
                 const int lo1 = frag_start(fy, D.base[1], D.rem[1]), hi1 = frag_start(fy + 1, D.base[1], D.rem[1]);
@@ -1249,19 +1248,33 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                 }
                 __syncwarp();
                 const int nch = (n + 3) >> 2;
+                // up to two chunks: each lane keeps its two slots' site keys in registers
+                // (0xffffffff: no slot, or handed off), as in the replica-resident kernel
+                uint32_t kc0 = 0xffffffffu, kc1 = 0xffffffffu;
+                if (nch <= 2) {
+                    const int m0 = lane >> 3, m1 = 4 + (lane >> 3);
+                    if (m0 < n) kc0 = S.key[wslot[m0]];
+                    if (m1 < n) kc1 = S.key[wslot[m1]];
+                }
+                auto type_of = [&](uint32_t k, int q) -> int {
+                    int t, x, y, z;
+                    split32(k, t, x, y, z);
+                    const NbEntry nbe = sh.nb[t][q];
+                    const int code = csite_code(sh, S, geo, me, nbe.t2, wrapc(x + nbe.dc[0], geo.L0),
+                                                wrapc(y + nbe.dc[1], geo.L1), wrapc(z + nbe.dc[2], geo.L2));
+                    return code == SP_V ? -1 : code * 3 + nbe.d[2] + 1;
+                };
                 auto compute_types = [&]() {
-                    for (int c = 0; c < nch; ++c) {
-                        const int e = c * 32 + lane, m = e >> 3;
-                        int ty = -1;
-                        if (m < n && wslot[m] >= 0) {
-                            int t, x, y, z;
-                            split32(S.key[wslot[m]], t, x, y, z);
-                            const NbEntry nbe = sh.nb[t][e & 7];
-                            const int code = csite_code(sh, S, geo, me, nbe.t2, wrapc(x + nbe.dc[0], geo.L0),
-                                                        wrapc(y + nbe.dc[1], geo.L1), wrapc(z + nbe.dc[2], geo.L2));
-                            ty = code == SP_V ? -1 : code * 3 + nbe.d[2] + 1;
+                    if (nch <= 2) {
+                        wtype[lane] = (int8_t)(kc0 != 0xffffffffu ? type_of(kc0, lane & 7) : -1);
+                        if (nch == 2) wtype[32 + lane] = (int8_t)(kc1 != 0xffffffffu ? type_of(kc1, lane & 7) : -1);
+                    } else {
+                        for (int c = 0; c < nch; ++c) {
+                            const int e = c * 32 + lane, m = e >> 3;
+                            int ty = -1;
+                            if (m < n && wslot[m] >= 0) ty = type_of(S.key[wslot[m]], e & 7);
+                            wtype[e] = (int8_t)ty;
                         }
-                        wtype[e] = (int8_t)ty;
                     }
                     __syncwarp();
                 };
@@ -1430,6 +1443,11 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                         }
                     }
                     __syncwarp();
+                    if (nch <= 2) {  // the moved vacancy's lanes follow it (or drop a handed-off slot)
+                        const uint32_t nk = owned ? key32(j.t2, j.jx, j.jy, j.jz) : 0xffffffffu;
+                        if ((lane >> 3) == m) kc0 = nk;
+                        if (4 + (lane >> 3) == m) kc1 = nk;
+                    }
                     // the fragments whose totals changed: owners of the vacancies next to
                     // the two changed sites (lanes 0-7 look around s, 8-15 around j)
                     if (lane < 16) {
