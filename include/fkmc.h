@@ -450,6 +450,40 @@ int kmc_download_state(kmc_batch* b, void* host, size_t bytes);
 int kmc_upload_state(kmc_batch* b, const void* host, size_t bytes);
 
 int kmc_get_replica_info(kmc_batch* b, int32_t r, kmc_replica_info* out);
+
+/* Invariant check of replica r's device state, for debugging and tests.  Every
+ * event of the fragment BKL exchanges a vacancy with a neighbouring ion
+ * (Sec. II.A, Eqs. eventSelection and TimeStep), so the counts of vacancies
+ * and of H- ions never change, and the vacancy records must describe the
+ * occupancy exactly.  Two kernels on the batch's stream measure, without
+ * copying the lattice to the host:
+ *   sites[code]        occupancy census by code (FKMC_O, FKMC_H, FKMC_V; 3 is
+ *                      unused and must be 0);
+ *   records            records over all fragment lists;
+ *   rec_not_vacancy    records whose site does not hold a vacancy;
+ *   rec_wrong_fragment records listed by a fragment that does not own the site;
+ *   rec_outside        records whose site lies outside the lattice;
+ *   frag_bad_count     fragments whose count is below 0 or above cap_v;
+ *   hash_vac_sites, hash_rec_sites  sums (mod 2^64) of a 64-bit mixing
+ *                      function of the linear site index over the vacancy
+ *                      sites and over the record sites: equal sums with equal
+ *                      counts mean one record per vacancy site (up to a 2^-64
+ *                      chance of a collision);
+ *   hash_rec_ids, hash_ids_expected the same sum over the record ids and over
+ *                      0 .. n_vac-1 (each vacancy keeps its id).
+ * ok = 1 when the counts equal the replica's vacancies and H- ions and every
+ * check holds.  Synchronous (waits for the batch's stream); the first call
+ * allocates 96 bytes through the batch's allocator.  Check after every window
+ * by running one window per kmc_run call.  Errors: FKMC_EINVAL for a bad
+ * replica or a NULL output, FKMC_ENOMEM, FKMC_ECUDA. */
+typedef struct {
+    int64_t sites[4];
+    int64_t records, rec_not_vacancy, rec_wrong_fragment, rec_outside, frag_bad_count;
+    uint64_t hash_vac_sites, hash_rec_sites, hash_rec_ids, hash_ids_expected;
+    int32_t ok;
+    int32_t pad;
+} kmc_invariants;
+int kmc_check_invariants(kmc_batch* b, int32_t r, kmc_invariants* out);
 int32_t kmc_num_replicas(const kmc_batch* b);
 
 /* Host-only: the rate table of kmc_set_barriers for one parameter set. */

@@ -9,8 +9,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIB_DIR, "libfkmc.so")
-SOURCES = ["fkmc_kernels.cu", "fkmc_resident.cu", "fkmc_noalloc.cu", "fkmc_null.cu", "fkmc_poisson.cu", "fkmc_api.cu"]
-HEADERS = ["fkmc_device.cuh", "fkmc_kernels.h"]
+SOURCES = ["fkmc_kernels.cu", "fkmc_resident.cu", "fkmc_noalloc.cu", "fkmc_check.cu", "fkmc_null.cu", "fkmc_poisson.cu", "fkmc_api.cu"]
+HEADERS = ["fkmc_device.cuh", "fkmc_kernels.h", "fkmc_check.h"]
 
 NVCC_FLAGS = [
     "-std=c++17", "-O3", "-lineinfo",

@@ -3,6 +3,7 @@
 // rate tables (Eq. RateCnst1 of arXiv:2004.09081 with the ESP shift of
 // Sec. III), the window loop and the read-outs.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -12,7 +13,19 @@
 #include <vector>
 
 #include "fkmc.h"
+#include "fkmc_check.h"
 #include "fkmc_kernels.h"
+
+namespace {
+// NVTX range over one ABI call, named after it (shown by Nsight tools; without
+// a tool attached the header-only NVTX calls do nothing)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
 
 using namespace fkmc;
 
@@ -129,6 +142,7 @@ struct kmc_batch {
     uint32_t* status = nullptr;
     unsigned long long* scratch = nullptr;  // 7 moments
     unsigned long long* scratch_all = nullptr;  // 7 moments per replica
+    unsigned long long* check_buf = nullptr;    // CHECK_WORDS sums of kmc_check_invariants
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<void*> owned;
     // replica-resident kernel: replicas grouped by shared-memory size class
@@ -1072,6 +1086,7 @@ int kmc_set_barriers(kmc_batch* b, const kmc_barrier_table* tables, const double
 
 int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
 {
+    NvtxRange nvtx_range("kmc_run");
     if (!b) return fail(FKMC_EINVAL, "null batch");
     if (!b->rates_set) return fail(FKMC_ESTATE, "kmc_set_barriers must come before kmc_run");
     std::vector<unsigned long long> before = b->stats_host;
@@ -1207,6 +1222,7 @@ int kmc_run(kmc_batch* b, uint64_t windows, kmc_run_stats* stats)
 
 int kmc_run_null(kmc_batch* b, uint64_t steps, int64_t n_frg, kmc_run_stats* stats)
 {
+    NvtxRange nvtx_range("kmc_run_null");
     if (!b) return fail(FKMC_EINVAL, "null batch");
     if (!b->rates_set) return fail(FKMC_ESTATE, "kmc_set_barriers must come before kmc_run_null");
     if (site_path(b)) return fail(FKMC_EINVAL, "the null-event form has no site energies or electrostatics");
@@ -1927,6 +1943,7 @@ int kmc_set_electrostatics(kmc_batch* b, const kmc_electrostatics* e)
 
 int kmc_solve_potential(kmc_batch* b, int32_t r, double* phi, size_t n, double* resid_rel)
 {
+    NvtxRange nvtx_range("kmc_solve_potential");
     if (!valid_replica(b, r) || !phi) return fail(FKMC_EINVAL, "bad replica or output");
     if (!b->elec_on) return fail(FKMC_ESTATE, "electrostatics are off");
     const RepDesc& D = b->desc[r];
@@ -2104,6 +2121,38 @@ int kmc_read_site_field(kmc_batch* b, int32_t r, int32_t* host_field, size_t n)
     CK(cudaMemcpyAsync(host_field, b->field + D.site_off, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, b->st),
        "field copy");
     CK(cudaStreamSynchronize(b->st), "synchronize");
+    return FKMC_OK;
+}
+
+int kmc_check_invariants(kmc_batch* b, int32_t r, kmc_invariants* out)
+{
+    NvtxRange nvtx_range("kmc_check_invariants");
+    if (!valid_replica(b, r) || !out) return fail(FKMC_EINVAL, "bad replica or output");
+    if (!b->check_buf) {
+        b->check_buf = (unsigned long long*)b->dalloc(sizeof(unsigned long long) * CHECK_WORDS);
+        if (!b->check_buf) return fail(FKMC_ENOMEM, "device allocation failed");
+    }
+    CK(launch_check(b->desc[r], b->occ, b->recs, b->counts, b->cap, b->check_buf, b->st), "check kernels");
+    unsigned long long h[CHECK_WORDS];
+    CK(cudaMemcpyAsync(h, b->check_buf, sizeof h, cudaMemcpyDeviceToHost, b->st), "check copy");
+    CK(cudaStreamSynchronize(b->st), "synchronize");
+    std::memset(out, 0, sizeof *out);
+    for (int c = 0; c < 4; ++c) out->sites[c] = (int64_t)h[CHK_SITES + c];
+    out->records = (int64_t)h[CHK_RECORDS];
+    out->rec_not_vacancy = (int64_t)h[CHK_NOT_VAC];
+    out->rec_wrong_fragment = (int64_t)h[CHK_WRONG_FRAG];
+    out->rec_outside = (int64_t)h[CHK_BAD_SITE];
+    out->frag_bad_count = (int64_t)h[CHK_BAD_COUNT];
+    out->hash_vac_sites = h[CHK_HASH_VAC];
+    out->hash_rec_sites = h[CHK_HASH_REC];
+    out->hash_rec_ids = h[CHK_HASH_ID];
+    uint64_t ids = 0;  // every id 0 .. n_vac-1 once
+    for (int64_t i = 0; i < b->n_vac[r]; ++i) ids += check_mix64((uint64_t)i);
+    out->hash_ids_expected = ids;
+    out->ok = out->sites[FKMC_V] == b->n_vac[r] && out->sites[FKMC_H] == b->n_H[r] && out->sites[3] == 0 &&
+              out->records == b->n_vac[r] && out->rec_not_vacancy == 0 && out->rec_wrong_fragment == 0 &&
+              out->rec_outside == 0 && out->frag_bad_count == 0 && out->hash_vac_sites == out->hash_rec_sites &&
+              out->hash_rec_ids == ids;
     return FKMC_OK;
 }
 

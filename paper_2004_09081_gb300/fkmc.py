@@ -85,6 +85,13 @@ class kmc_replica_info(C.Structure):
                 ("kernel", C.c_int32), ("ctas", C.c_int32)]
 
 
+class kmc_invariants(C.Structure):
+    _fields_ = [("sites", C.c_int64 * 4), ("records", C.c_int64), ("rec_not_vacancy", C.c_int64),
+                ("rec_wrong_fragment", C.c_int64), ("rec_outside", C.c_int64), ("frag_bad_count", C.c_int64),
+                ("hash_vac_sites", C.c_uint64), ("hash_rec_sites", C.c_uint64), ("hash_rec_ids", C.c_uint64),
+                ("hash_ids_expected", C.c_uint64), ("ok", C.c_int32), ("pad", C.c_int32)]
+
+
 _P, _I32, _I64, _U64, _SZ, _D = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_size_t, C.c_double
 _SIGNATURES = {
     "kmc_default_opts": (None, [_P]),
@@ -105,6 +112,7 @@ _SIGNATURES = {
     "kmc_download_state": (C.c_int, [_P, _P, _SZ]),
     "kmc_upload_state": (C.c_int, [_P, _P, _SZ]),
     "kmc_get_replica_info": (C.c_int, [_P, _I32, _P]),
+    "kmc_check_invariants": (C.c_int, [_P, _I32, _P]),
     "kmc_num_replicas": (_I32, [_P]),
     "kmc_rate_table": (C.c_int, [_P, _D, _D, _D, _I32, _P, _P, _P, _P]),
     "kmc_neighbour_table": (None, [_P]),
@@ -267,6 +275,12 @@ def kmc_get_replica_info(h, r: int) -> kmc_replica_info:
     info = kmc_replica_info()
     _check(load().kmc_get_replica_info(h, r, C.byref(info)))
     return info
+
+
+def kmc_check_invariants(h, r: int) -> kmc_invariants:
+    inv = kmc_invariants()
+    _check(load().kmc_check_invariants(h, r, C.byref(inv)))
+    return inv
 
 
 def kmc_num_replicas(h) -> int:
@@ -527,6 +541,9 @@ class Batch:
 
     def info(self, r=0):
         return kmc_get_replica_info(self.h, r)
+
+    def check(self, r=0):
+        return kmc_check_invariants(self.h, r)
 
     def set_site_energy(self, vv=(), fe=()):
         kmc_set_site_energy(self.h, vv, fe)
