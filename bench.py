@@ -43,7 +43,7 @@ B_ALG_PER_HOP_ELEC = 160 + 4 * 9
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--windows", type=int, default=0, help="windows per step (0: the workload's default)")

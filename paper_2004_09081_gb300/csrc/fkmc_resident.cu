@@ -528,13 +528,20 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                 }
                 n = __shfl_sync(FULL, n, 0);
                 __syncwarp();
-                if (n <= 32) {  // rank by site (sites are distinct)
+                // a list that received no vacancy since its last visit is still in site order
+                bool ordered = false;
+                uint32_t kk = 0xffffffffu;
+                if (n <= 32) {  // rank by site (sites are distinct), unless already in order
                     const int vk = lane < n ? wslot[lane] : -1;
-                    const uint32_t kk = lane < n ? S.key[vk] : 0xffffffffu;
-                    int rnk = 0;
-                    for (int q = 0; q < n; ++q) rnk += __shfl_sync(FULL, kk, q) < kk ? 1 : 0;
-                    __syncwarp();
-                    if (lane < n) wslot[rnk] = (int16_t)vk;
+                    kk = lane < n ? S.key[vk] : 0xffffffffu;
+                    const uint32_t kprev = __shfl_up_sync(FULL, kk, 1);
+                    ordered = __ballot_sync(FULL, lane > 0 && lane < n && kprev > kk) == 0u;
+                    if (!ordered) {
+                        int rnk = 0;
+                        for (int q = 0; q < n; ++q) rnk += __shfl_sync(FULL, kk, q) < kk ? 1 : 0;
+                        __syncwarp();
+                        if (lane < n) wslot[rnk] = (int16_t)vk;
+                    }
                 } else if (lane == 0) {
                     for (int k = 1; k < n; ++k) {
                         const int v = wslot[k];
@@ -554,8 +561,14 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                 uint32_t kc0 = 0xffffffffu, kc1 = 0xffffffffu;
                 if (nch <= 2) {
                     const int m0 = lane >> 3, m1 = 4 + (lane >> 3);
-                    if (m0 < n) kc0 = S.key[wslot[m0]];
-                    if (m1 < n) kc1 = S.key[wslot[m1]];
+                    if (ordered) {  // lane m holds slot m's key
+                        const uint32_t a0 = __shfl_sync(FULL, kk, m0), a1 = __shfl_sync(FULL, kk, m1);
+                        if (m0 < n) kc0 = a0;
+                        if (m1 < n) kc1 = a1;
+                    } else {
+                        if (m0 < n) kc0 = S.key[wslot[m0]];
+                        if (m1 < n) kc1 = S.key[wslot[m1]];
+                    }
                 }
                 auto type_of = [&](uint32_t k, int q) -> int {
                     int t, x, y, z;
@@ -565,10 +578,11 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                                                wrapc(y + nbe.dc[1], geo.L1), wrapc(z + nbe.dc[2], geo.L2));
                     return code == SP_V ? -1 : code * 3 + nbe.d[2] + 1;
                 };
+                int ty0 = -1, ty1 = -1;  // up to two chunks: rate types of events lane and 32 + lane
                 auto compute_types = [&]() {
                     if (nch <= 2) {
-                        wtype[lane] = (int8_t)(kc0 != 0xffffffffu ? type_of(kc0, lane & 7) : -1);
-                        if (nch == 2) wtype[32 + lane] = (int8_t)(kc1 != 0xffffffffu ? type_of(kc1, lane & 7) : -1);
+                        ty0 = kc0 != 0xffffffffu ? type_of(kc0, lane & 7) : -1;
+                        ty1 = (nch == 2 && kc1 != 0xffffffffu) ? type_of(kc1, lane & 7) : -1;
                     } else {
                         for (int c = 0; c < nch; ++c) {
                             const int e = c * 32 + lane, m = e >> 3;
@@ -592,7 +606,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                     // prefixes the selection needs; beyond that, a reduction now and scans later.
                     unsigned long long inc0 = 0, inc1 = 0;
                     if (nch <= 2) {
-                        const int t0 = wtype[lane];
+                        const int t0 = ty0;
                         inc0 = t0 < 0 ? 0ull : (unsigned long long)D.q[t0];
 #pragma unroll
                         for (int off = 1; off < 32; off <<= 1) {
@@ -601,7 +615,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                         }
                         tot = __shfl_sync(FULL, inc0, 31);
                         if (nch == 2) {
-                            const int t1 = wtype[32 + lane];
+                            const int t1 = ty1;
                             inc1 = t1 < 0 ? 0ull : (unsigned long long)D.q[t1];
 #pragma unroll
                             for (int off = 1; off < 32; off <<= 1) {
@@ -650,10 +664,12 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                     }
                     const float ratio = __fdiv_rn(E, __ull2float_rn(tot));
                     const double nclock = __dadd_rn(clock, scale_pow2((double)ratio, geo.F));
-                    if (nclock > geo.theta) break;
+                    // up to two chunks: the selection (no side effects) before the clock test,
+                    // so that its shuffles overlap the clock's FP64 chain; a break discards it
                     const unsigned long long target = __umul64hi(xs, tot);
-                    // first event whose running sum exceeds the target
                     int e_sel = -1;
+                    uint32_t ksel = 0u;
+                    int tsel = -1;
                     if (nch <= 2) {
                         unsigned bal = __ballot_sync(FULL, inc0 > target);
                         if (bal) {
@@ -662,7 +678,13 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                             bal = __ballot_sync(FULL, inc1 > target);
                             if (bal && nch == 2) e_sel = 32 + __ffs(bal) - 1;
                         }
-                    } else {
+                        const int ms = e_sel >> 3;  // the slot's site key and the event's type
+                        ksel = __shfl_sync(FULL, ms < 4 ? kc0 : kc1, (ms & 3) << 3);
+                        tsel = __shfl_sync(FULL, e_sel < 32 ? ty0 : ty1, e_sel & 31);
+                    }
+                    if (nclock > geo.theta) break;
+                    // first event whose running sum exceeds the target
+                    if (nch > 2) {
                         unsigned long long carry = 0;
                         for (int c = 0; c < nch; ++c) {
                             const int ty = wtype[c * 32 + lane];
@@ -686,15 +708,15 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                         break;
                     }
                     const int m = e_sel >> 3, qd = e_sel & 7;
-                    const int v = wslot[m];
                     int t, x, y, z;
-                    split32(S.key[v], t, x, y, z);
+                    split32(nch <= 2 ? ksel : S.key[wslot[m]], t, x, y, z);
                     const NbEntry nb = sh.nb[t][qd];
                     const NbSite j = nb_site(sh, geo, t, x, y, z, qd);
                     const bool owned = j.jx >= lo0 && j.jx < hi0 && j.jy >= lo1 && j.jy < hi1 && j.jz >= lo2 &&
                                        j.jz < hi2;
                     if (lane == 0) {  // apply the exchange
-                        const uint32_t ion = (uint32_t)(wtype[e_sel] / 3);
+                        const int v = wslot[m];
+                        const uint32_t ion = (uint32_t)((nch <= 2 ? tsel : (int)wtype[e_sel]) / 3);
                         uint32_t* ws = S.occ + ((t * geo.L2 + z) * geo.L1 + y) * geo.RW + (x >> 4);
                         uint32_t* wj = S.occ + ((j.t2 * geo.L2 + j.jz) * geo.L1 + j.jy) * geo.RW + (j.jx >> 4);
                         const uint32_t ms = ((uint32_t)SP_V ^ ion) << occ_shift(x);
@@ -741,33 +763,50 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                         if ((lane >> 3) == m) kc0 = nk;
                         if (4 + (lane >> 3) == m) kc1 = nk;
                     }
-                    // the fragments whose totals changed: owners of the vacancies next
-                    // to the two changed sites (lanes 0-7 look around s, 8-15 around j)
-                    if (lane < 16) {
-                        const int bt = lane < 8 ? t : j.t2;
-                        const int bx = lane < 8 ? x : j.jx, by = lane < 8 ? y : j.jy, bz = lane < 8 ? z : j.jz;
-                        const NbSite c = nb_site(sh, geo, bt, bx, by, bz, lane & 7);
-                        if (site_code(geo, S.occ, c.t2, c.jx, c.jy, c.jz) == SP_V) {
-                            const int g = owner_of(geo, S.frag_of_c, c.jx, c.jy, c.jz);
-                            if (g != fid) {
-                                S.dirty[g] = 1;
-                                if constexpr (CL > 1) st_peer8(peer_addr(S.dirty + g, peer), 1);
-                            }
+                    {
+                        // the fragments whose totals changed: owners of the vacancies next to the
+                        // two changed sites (lanes 0-7 look around s, 8-15 around j; 16-31 repeat
+                        // them without storing, so that no branch splits the warp and the probe's
+                        // loads overlap those of the rate types)
+                        const int pl = lane & 15;
+                        const int bt = pl < 8 ? t : j.t2;
+                        const int bx = pl < 8 ? x : j.jx, by = pl < 8 ? y : j.jy, bz = pl < 8 ? z : j.jz;
+                        const NbSite c = nb_site(sh, geo, bt, bx, by, bz, pl & 7);
+                        const bool vac = site_code(geo, S.occ, c.t2, c.jx, c.jy, c.jz) == SP_V;
+                        const int g = owner_of(geo, S.frag_of_c, c.jx, c.jy, c.jz);
+                        compute_types();
+                        if (lane < 16 && vac && g != fid) {
+                            S.dirty[g] = 1;
+                            if constexpr (CL > 1) st_peer8(peer_addr(S.dirty + g, peer), 1);
                         }
                     }
-                    compute_types();
                     clock = nclock;
                     ++i;
                 }
-                // surviving vacancies stay linked to this fragment, in slot order
+                // surviving vacancies stay linked to this fragment, in slot order (up to 32
+                // slots, each lane links its own slot to the next live one)
+                int head = -1;
+                if (n <= 32) {
+                    const int v = lane < n ? wslot[lane] : -1;
+                    const unsigned live = __ballot_sync(FULL, v >= 0);
+                    const unsigned later = live & ~((2u << lane) - 1u);
+                    const int vn = __shfl_sync(FULL, v, later ? __ffs(later) - 1 : 0);
+                    const int hv = __shfl_sync(FULL, v, live ? __ffs(live) - 1 : 0);
+                    if (v >= 0) {
+                        S.next[v] = (int16_t)(later ? vn : -1);
+                        if constexpr (CL > 1) st_peer16(peer_addr(S.next + v, peer), (int16_t)(later ? vn : -1));
+                    }
+                    head = live ? hv : -1;
+                }
                 if (lane == 0) {
-                    int head = -1;
-                    for (int m = n - 1; m >= 0; --m) {
-                        const int v = wslot[m];
-                        if (v < 0) continue;
-                        S.next[v] = (int16_t)head;
-                        if constexpr (CL > 1) st_peer16(peer_addr(S.next + v, peer), (int16_t)head);
-                        head = v;
+                    if (n > 32) {
+                        for (int m = n - 1; m >= 0; --m) {
+                            const int v = wslot[m];
+                            if (v < 0) continue;
+                            S.next[v] = (int16_t)head;
+                            if constexpr (CL > 1) st_peer16(peer_addr(S.next + v, peer), (int16_t)head);
+                            head = v;
+                        }
                     }
                     S.head[fid] = head;
                     S.S[fid] = tot;
@@ -1227,13 +1266,20 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                 }
                 n = __shfl_sync(FULL, n, 0);
                 __syncwarp();
-                if (n <= 32) {
+                // a list that received no vacancy since its last visit is still in site order
+                bool ordered = false;
+                uint32_t kk = 0xffffffffu;
+                if (n <= 32) {  // rank by site (sites are distinct), unless already in order
                     const int vk = lane < n ? wslot[lane] : -1;
-                    const uint32_t kk = lane < n ? S.key[vk] : 0xffffffffu;
-                    int rnk = 0;
-                    for (int q = 0; q < n; ++q) rnk += __shfl_sync(FULL, kk, q) < kk ? 1 : 0;
-                    __syncwarp();
-                    if (lane < n) wslot[rnk] = (int16_t)vk;
+                    kk = lane < n ? S.key[vk] : 0xffffffffu;
+                    const uint32_t kprev = __shfl_up_sync(FULL, kk, 1);
+                    ordered = __ballot_sync(FULL, lane > 0 && lane < n && kprev > kk) == 0u;
+                    if (!ordered) {
+                        int rnk = 0;
+                        for (int q = 0; q < n; ++q) rnk += __shfl_sync(FULL, kk, q) < kk ? 1 : 0;
+                        __syncwarp();
+                        if (lane < n) wslot[rnk] = (int16_t)vk;
+                    }
                 } else if (lane == 0) {
                     for (int k = 1; k < n; ++k) {
                         const int v = wslot[k];
@@ -1253,8 +1299,14 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                 uint32_t kc0 = 0xffffffffu, kc1 = 0xffffffffu;
                 if (nch <= 2) {
                     const int m0 = lane >> 3, m1 = 4 + (lane >> 3);
-                    if (m0 < n) kc0 = S.key[wslot[m0]];
-                    if (m1 < n) kc1 = S.key[wslot[m1]];
+                    if (ordered) {  // lane m holds slot m's key
+                        const uint32_t a0 = __shfl_sync(FULL, kk, m0), a1 = __shfl_sync(FULL, kk, m1);
+                        if (m0 < n) kc0 = a0;
+                        if (m1 < n) kc1 = a1;
+                    } else {
+                        if (m0 < n) kc0 = S.key[wslot[m0]];
+                        if (m1 < n) kc1 = S.key[wslot[m1]];
+                    }
                 }
                 auto type_of = [&](uint32_t k, int q) -> int {
                     int t, x, y, z;
@@ -1264,10 +1316,11 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                                                 wrapc(y + nbe.dc[1], geo.L1), wrapc(z + nbe.dc[2], geo.L2));
                     return code == SP_V ? -1 : code * 3 + nbe.d[2] + 1;
                 };
+                int ty0 = -1, ty1 = -1;  // up to two chunks: rate types of events lane and 32 + lane
                 auto compute_types = [&]() {
                     if (nch <= 2) {
-                        wtype[lane] = (int8_t)(kc0 != 0xffffffffu ? type_of(kc0, lane & 7) : -1);
-                        if (nch == 2) wtype[32 + lane] = (int8_t)(kc1 != 0xffffffffu ? type_of(kc1, lane & 7) : -1);
+                        ty0 = kc0 != 0xffffffffu ? type_of(kc0, lane & 7) : -1;
+                        ty1 = (nch == 2 && kc1 != 0xffffffffu) ? type_of(kc1, lane & 7) : -1;
                     } else {
                         for (int c = 0; c < nch; ++c) {
                             const int e = c * 32 + lane, m = e >> 3;
@@ -1290,7 +1343,7 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                     // inclusive prefixes the selection needs
                     unsigned long long inc0 = 0, inc1 = 0;
                     if (nch <= 2) {
-                        const int t0 = wtype[lane];
+                        const int t0 = ty0;
                         inc0 = t0 < 0 ? 0ull : (unsigned long long)D.q[t0];
 #pragma unroll
                         for (int off = 1; off < 32; off <<= 1) {
@@ -1299,7 +1352,7 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                         }
                         tot = __shfl_sync(FULL, inc0, 31);
                         if (nch == 2) {
-                            const int t1 = wtype[32 + lane];
+                            const int t1 = ty1;
                             inc1 = t1 < 0 ? 0ull : (unsigned long long)D.q[t1];
 #pragma unroll
                             for (int off = 1; off < 32; off <<= 1) {
@@ -1347,9 +1400,12 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                     }
                     const float ratio = __fdiv_rn(E, __ull2float_rn(tot));
                     const double nclock = __dadd_rn(clock, scale_pow2((double)ratio, geo.F));
-                    if (nclock > geo.theta) break;
+                    // up to two chunks: the selection (no side effects) before the clock test,
+                    // so that its shuffles overlap the clock's FP64 chain; a break discards it
                     const unsigned long long target = __umul64hi(xs, tot);
                     int e_sel = -1;
+                    uint32_t ksel = 0u;
+                    int tsel = -1;
                     if (nch <= 2) {
                         unsigned bal = __ballot_sync(FULL, inc0 > target);
                         if (bal) {
@@ -1358,7 +1414,12 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                             bal = __ballot_sync(FULL, inc1 > target);
                             if (bal && nch == 2) e_sel = 32 + __ffs(bal) - 1;
                         }
-                    } else {
+                        const int ms = e_sel >> 3;  // the slot's site key and the event's type
+                        ksel = __shfl_sync(FULL, ms < 4 ? kc0 : kc1, (ms & 3) << 3);
+                        tsel = __shfl_sync(FULL, e_sel < 32 ? ty0 : ty1, e_sel & 31);
+                    }
+                    if (nclock > geo.theta) break;
+                    if (nch > 2) {
                         unsigned long long carry = 0;
                         for (int c = 0; c < nch; ++c) {
                             const int ty = wtype[c * 32 + lane];
@@ -1382,15 +1443,15 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                         break;
                     }
                     const int m = e_sel >> 3, qd = e_sel & 7;
-                    const int v = wslot[m];
                     int t, x, y, z;
-                    split32(S.key[v], t, x, y, z);
+                    split32(nch <= 2 ? ksel : S.key[wslot[m]], t, x, y, z);
                     const NbEntry nb = sh.nb[t][qd];
                     const NbSite j = cnb_site(sh, geo, t, x, y, z, qd);
                     const bool owned = j.jx >= lo0 && j.jx < hi0 && j.jy >= lo1 && j.jy < hi1 && j.jz >= lo2 &&
                                        j.jz < hi2;
                     if (lane == 0) {  // apply the exchange
-                        const uint32_t ion = (uint32_t)(wtype[e_sel] / 3);
+                        const int v = wslot[m];
+                        const uint32_t ion = (uint32_t)((nch <= 2 ? tsel : (int)wtype[e_sel]) / 3);
                         csite_xor(sh, S, geo, me, t, x, y, z, ((uint32_t)SP_V ^ ion) << occ_shift(x));
                         csite_xor(sh, S, geo, me, j.t2, j.jx, j.jy, j.jz, (ion ^ (uint32_t)SP_V) << occ_shift(j.jx));
                         const int d0 = S.d[3 * v] + nb.d[0], d1 = S.d[3 * v + 1] + nb.d[1],
@@ -1448,16 +1509,20 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                         if ((lane >> 3) == m) kc0 = nk;
                         if (4 + (lane >> 3) == m) kc1 = nk;
                     }
-                    // the fragments whose totals changed: owners of the vacancies next to
-                    // the two changed sites (lanes 0-7 look around s, 8-15 around j)
-                    if (lane < 16) {
-                        const int bt = lane < 8 ? t : j.t2;
-                        const int bx = lane < 8 ? x : j.jx, by = lane < 8 ? y : j.jy, bz = lane < 8 ? z : j.jz;
-                        const NbSite c = cnb_site(sh, geo, bt, bx, by, bz, lane & 7);
-                        if (csite_code(sh, S, geo, me, c.t2, c.jx, c.jy, c.jz) == SP_V) {
-                            uint32_t oc;
-                            int lc;
-                            cowner(sh, S, geo, c.jx, c.jy, c.jz, oc, lc);
+                    {
+                        // the fragments whose totals changed: owners of the vacancies next to the
+                        // two changed sites (lanes 0-7 look around s, 8-15 around j; 16-31 repeat
+                        // them without storing, so that no branch splits the warp)
+                        const int pl = lane & 15;
+                        const int bt = pl < 8 ? t : j.t2;
+                        const int bx = pl < 8 ? x : j.jx, by = pl < 8 ? y : j.jy, bz = pl < 8 ? z : j.jz;
+                        const NbSite c = cnb_site(sh, geo, bt, bx, by, bz, pl & 7);
+                        const bool vac = csite_code(sh, S, geo, me, c.t2, c.jx, c.jy, c.jz) == SP_V;
+                        uint32_t oc;
+                        int lc;
+                        cowner(sh, S, geo, c.jx, c.jy, c.jz, oc, lc);
+                        compute_types();
+                        if (lane < 16 && vac) {
                             if (oc == me) {
                                 if (lc != lf) S.dirty[lc] = 1;
                             } else {
@@ -1465,18 +1530,29 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                             }
                         }
                     }
-                    compute_types();
                     clock = nclock;
                     ++i;
                 }
-                // surviving vacancies stay linked to this fragment, in slot order
+                // surviving vacancies stay linked to this fragment, in slot order (up to 32
+                // slots, each lane links its own slot to the next live one)
+                int head = -1;
+                if (n <= 32) {
+                    const int v = lane < n ? wslot[lane] : -1;
+                    const unsigned live = __ballot_sync(FULL, v >= 0);
+                    const unsigned later = live & ~((2u << lane) - 1u);
+                    const int vn = __shfl_sync(FULL, v, later ? __ffs(later) - 1 : 0);
+                    const int hv = __shfl_sync(FULL, v, live ? __ffs(live) - 1 : 0);
+                    if (v >= 0) S.next[v] = (int16_t)(later ? vn : -1);
+                    head = live ? hv : -1;
+                }
                 if (lane == 0) {
-                    int head = -1;
-                    for (int m = n - 1; m >= 0; --m) {
-                        const int v = wslot[m];
-                        if (v < 0) continue;
-                        S.next[v] = (int16_t)head;
-                        head = v;
+                    if (n > 32) {
+                        for (int m = n - 1; m >= 0; --m) {
+                            const int v = wslot[m];
+                            if (v < 0) continue;
+                            S.next[v] = (int16_t)head;
+                            head = v;
+                        }
                     }
                     S.head[lf] = head;
                     S.S[lf] = tot;
