@@ -275,7 +275,18 @@ struct NbSite {
 struct Geo {
     int L0, L1, L2, RW, nf0, nf1, F;
     double theta;
+    float theta_f;  // the largest float <= theta 2^-F (see window_f)
 };
+
+// The window test of a clock still at zero: 2^F r > theta for the FP32 ratio r
+// (2^F r is an exact double, and 0 + 2^F r is that double) holds exactly when
+// r > theta 2^-F, and for a float r that holds exactly when r exceeds the
+// largest float not above theta 2^-F -- one FP32 compare instead of a
+// conversion, an add and a compare on the FP64 pipe, with the same outcome.
+__device__ __forceinline__ float window_f(double theta, int F)
+{
+    return __double2float_rd(__longlong_as_double(__double_as_longlong(theta) - ((long long)F << 52)));
+}
 
 __device__ __forceinline__ NbSite nb_site(const Shared& sh, const Geo& g, int t, int x, int y, int z, int q)
 {
@@ -444,7 +455,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
     if (sh.abort) return;
 
     const uint64_t hop_k1 = key_word(D.replica, PURPOSE_HOP);
-    const Geo geo{D.L[0], D.L[1], D.L[2], D.row_words, D.nf[0], D.nf[1], D.F, D.theta_tau};
+    const Geo geo{D.L[0], D.L[1], D.L[2], D.row_words, D.nf[0], D.nf[1], D.F, D.theta_tau, window_f(D.theta_tau, D.F)};
     const int lane = tid & 31;
     const int warp = tid >> 5;
     const unsigned FULL = 0xffffffffu;
@@ -489,7 +500,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                 bool active = dirty;
                 if (!active) {
                     const float ratio = __fdiv_rn(E0, __ull2float_rn(tot));
-                    active = !(__dadd_rn(0.0, scale_pow2((double)ratio, geo.F)) > geo.theta);
+                    active = !(ratio > geo.theta_f);  // 0 + 2^F ratio <= theta
                 }
                 if (active) {
                     const int a = atomicAdd(&sh.nact, 1);
@@ -664,6 +675,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                     }
                     const float ratio = __fdiv_rn(E, __ull2float_rn(tot));
                     const double nclock = __dadd_rn(clock, scale_pow2((double)ratio, geo.F));
+                    const bool past = i == 0 ? ratio > geo.theta_f : nclock > geo.theta;  // the first: clock 0
                     // up to two chunks: the selection (no side effects) before the clock test,
                     // so that its shuffles overlap the clock's FP64 chain; a break discards it
                     const unsigned long long target = __umul64hi(xs, tot);
@@ -682,7 +694,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                         ksel = __shfl_sync(FULL, ms < 4 ? kc0 : kc1, (ms & 3) << 3);
                         tsel = __shfl_sync(FULL, e_sel < 32 ? ty0 : ty1, e_sel & 31);
                     }
-                    if (nclock > geo.theta) break;
+                    if (past) break;
                     // first event whose running sum exceeds the target
                     if (nch > 2) {
                         unsigned long long carry = 0;
@@ -933,7 +945,7 @@ struct CLayout {
     int8_t* wtype;
     InboxRec* inbox;     // [2][icap]
     uint16_t* frag_of_c; // cell -> global fragment coordinate: x cells, then y, then z
-    uint8_t* cta_of_fz;  // fragment layer -> CTA
+    uint32_t* zmap;      // z cell -> its CTA | z within that CTA's slab << 8 | fragment layer within it << 18
 };
 
 __host__ __device__ inline size_t cluster_layout_bytes(const RepDesc& D, const ClusterPlan& P, int cap, int nwarps,
@@ -957,7 +969,7 @@ __host__ __device__ inline size_t cluster_layout_bytes(const RepDesc& D, const C
         (size_t)nwarps * cap * 8,           // 13 per-warp event types
         (size_t)2 * P.icap * sizeof(InboxRec),  // 14 inboxes
         (size_t)(D.L[0] + D.L[1] + D.L[2]) * 2, // 15 cell -> fragment tables
-        (size_t)D.nf[2],                    // 16 fragment layer -> CTA
+        (size_t)D.L[2] * 4,                 // 16 z cell -> CTA, slab z, slab fragment layer
     };
     size_t b = 0;
     for (int k = 0; k < 17; ++k) {
@@ -991,7 +1003,7 @@ __device__ __forceinline__ CLayout ccarve(unsigned char* dyn, const RepDesc& D, 
     L.wtype = reinterpret_cast<int8_t*>(dyn + o[13]);
     L.inbox = reinterpret_cast<InboxRec*>(dyn + o[14]);
     L.frag_of_c = reinterpret_cast<uint16_t*>(dyn + o[15]);
-    L.cta_of_fz = reinterpret_cast<uint8_t*>(dyn + o[16]);
+    L.zmap = reinterpret_cast<uint32_t*>(dyn + o[16]);
     return L;
 }
 
@@ -1016,28 +1028,27 @@ struct CWord {
     int idx;
 };
 
-__device__ __forceinline__ CWord cword(const CShared& sh, const CLayout& S, const Geo& g, int t, int x, int y, int z)
+__device__ __forceinline__ CWord cword(const CLayout& S, int zs, const Geo& g, int t, int x, int y, int z)
 {
-    const int fz = S.frag_of_c[g.L0 + g.L1 + z];
-    const uint32_t o = S.cta_of_fz[fz];
+    const uint32_t zm = S.zmap[z];
     CWord w;
-    w.cta = o;
-    w.idx = ((t * sh.P.zs + (z - sh.zbeg[o])) * g.L1 + y) * g.RW + (x >> 4);
+    w.cta = zm & 255u;
+    w.idx = ((t * zs + (int)((zm >> 8) & 1023u)) * g.L1 + y) * g.RW + (x >> 4);
     return w;
 }
 
-__device__ __forceinline__ int csite_code(const CShared& sh, const CLayout& S, const Geo& g, uint32_t me, int t,
-                                          int x, int y, int z)
+__device__ __forceinline__ int csite_code(int zs, const CLayout& S, const Geo& g, uint32_t me, int t, int x, int y,
+                                          int z)
 {
-    const CWord w = cword(sh, S, g, t, x, y, z);
+    const CWord w = cword(S, zs, g, t, x, y, z);
     const uint32_t v = w.cta == me ? S.occ[w.idx] : (uint32_t)ld_peer(peer_addr(S.occ + w.idx, w.cta));
     return (int)((v >> occ_shift(x)) & 3u);
 }
 
-__device__ __forceinline__ void csite_xor(const CShared& sh, const CLayout& S, const Geo& g, uint32_t me, int t, int x,
-                                          int y, int z, uint32_t m)
+__device__ __forceinline__ void csite_xor(int zs, const CLayout& S, const Geo& g, uint32_t me, int t, int x, int y,
+                                          int z, uint32_t m)
 {
-    const CWord w = cword(sh, S, g, t, x, y, z);
+    const CWord w = cword(S, zs, g, t, x, y, z);
     if (w.cta == me) atomicXor(S.occ + w.idx, m);
     else red_peer_xor(peer_addr(S.occ + w.idx, w.cta), m);
 }
@@ -1054,12 +1065,12 @@ __device__ __forceinline__ NbSite cnb_site(const CShared& sh, const Geo& g, int 
 }
 
 // owner of cell (x,y,z): its CTA and that CTA's local fragment index
-__device__ __forceinline__ void cowner(const CShared& sh, const CLayout& S, const Geo& g, int x, int y, int z,
-                                       uint32_t& cta, int& lf)
+__device__ __forceinline__ void cowner(const CLayout& S, const Geo& g, int x, int y, int z, uint32_t& cta, int& lf)
 {
-    const int fx = S.frag_of_c[x], fy = S.frag_of_c[g.L0 + y], fz = S.frag_of_c[g.L0 + g.L1 + z];
-    cta = S.cta_of_fz[fz];
-    lf = ((fz - sh.P.fz0[cta]) * g.nf1 + fy) * g.nf0 + fx;
+    const int fx = S.frag_of_c[x], fy = S.frag_of_c[g.L0 + y];
+    const uint32_t zm = S.zmap[z];
+    cta = zm & 255u;
+    lf = ((int)(zm >> 18) * g.nf1 + fy) * g.nf0 + fx;
 }
 
 }  // namespace
@@ -1093,8 +1104,9 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
     const RepDesc& D = sh.D;
     const ClusterPlan& P = sh.P;
     const CLayout S = ccarve(dyn, D, P, cap, NT / 32);
-    const Geo geo{D.L[0], D.L[1], D.L[2], D.row_words, D.nf[0], D.nf[1], D.F, D.theta_tau};
+    const Geo geo{D.L[0], D.L[1], D.L[2], D.row_words, D.nf[0], D.nf[1], D.F, D.theta_tau, window_f(D.theta_tau, D.F)};
     const int fzb = P.fz0[me], fze = P.fz0[me + 1];
+    const int zs = P.zs;  // cells in z of the common slab layout
     const int zb = sh.zbeg[me], zl = sh.zbeg[me + 1] - zb;
     const int nfl_me = (fze - fzb) * D.nf[0] * D.nf[1];
 
@@ -1110,10 +1122,11 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
         const int c = d == 0 ? k : (d == 1 ? k - D.L[0] : k - D.L[0] - D.L[1]);
         S.frag_of_c[k] = (uint16_t)frag_of(c, D.base[d], D.rem[d]);
     }
-    for (int fz = tid; fz < D.nf[2]; fz += NT) {
+    for (int z = tid; z < D.L[2]; z += NT) {
+        const int fz = frag_of(z, D.base[2], D.rem[2]);
         int c = 0;
         while (c + 1 < P.ncta && P.fz0[c + 1] <= fz) ++c;
-        S.cta_of_fz[fz] = (uint8_t)c;
+        S.zmap[z] = (uint32_t)c | ((uint32_t)(z - sh.zbeg[c]) << 8) | ((uint32_t)(fz - P.fz0[c]) << 18);
     }
     for (int lf = tid; lf < nfl_me; lf += NT) {
         const int fid = (fzb * D.nf[1]) * D.nf[0] + lf;  // layers are contiguous in the global order
@@ -1227,7 +1240,7 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                 bool active = dirty;
                 if (!active) {
                     const float ratio = __fdiv_rn(E0, __ull2float_rn(tot));
-                    active = !(__dadd_rn(0.0, scale_pow2((double)ratio, geo.F)) > geo.theta);
+                    active = !(ratio > geo.theta_f);  // 0 + 2^F ratio <= theta
                 }
                 if (active) {
                     const int a = atomicAdd(&sh.nact, 1);
@@ -1312,7 +1325,7 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                     int t, x, y, z;
                     split32(k, t, x, y, z);
                     const NbEntry nbe = sh.nb[t][q];
-                    const int code = csite_code(sh, S, geo, me, nbe.t2, wrapc(x + nbe.dc[0], geo.L0),
+                    const int code = csite_code(zs, S, geo, me, nbe.t2, wrapc(x + nbe.dc[0], geo.L0),
                                                 wrapc(y + nbe.dc[1], geo.L1), wrapc(z + nbe.dc[2], geo.L2));
                     return code == SP_V ? -1 : code * 3 + nbe.d[2] + 1;
                 };
@@ -1400,6 +1413,7 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                     }
                     const float ratio = __fdiv_rn(E, __ull2float_rn(tot));
                     const double nclock = __dadd_rn(clock, scale_pow2((double)ratio, geo.F));
+                    const bool past = i == 0 ? ratio > geo.theta_f : nclock > geo.theta;  // the first: clock 0
                     // up to two chunks: the selection (no side effects) before the clock test,
                     // so that its shuffles overlap the clock's FP64 chain; a break discards it
                     const unsigned long long target = __umul64hi(xs, tot);
@@ -1418,7 +1432,7 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                         ksel = __shfl_sync(FULL, ms < 4 ? kc0 : kc1, (ms & 3) << 3);
                         tsel = __shfl_sync(FULL, e_sel < 32 ? ty0 : ty1, e_sel & 31);
                     }
-                    if (nclock > geo.theta) break;
+                    if (past) break;
                     if (nch > 2) {
                         unsigned long long carry = 0;
                         for (int c = 0; c < nch; ++c) {
@@ -1452,8 +1466,8 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                     if (lane == 0) {  // apply the exchange
                         const int v = wslot[m];
                         const uint32_t ion = (uint32_t)((nch <= 2 ? tsel : (int)wtype[e_sel]) / 3);
-                        csite_xor(sh, S, geo, me, t, x, y, z, ((uint32_t)SP_V ^ ion) << occ_shift(x));
-                        csite_xor(sh, S, geo, me, j.t2, j.jx, j.jy, j.jz, (ion ^ (uint32_t)SP_V) << occ_shift(j.jx));
+                        csite_xor(zs, S, geo, me, t, x, y, z, ((uint32_t)SP_V ^ ion) << occ_shift(x));
+                        csite_xor(zs, S, geo, me, j.t2, j.jx, j.jy, j.jz, (ion ^ (uint32_t)SP_V) << occ_shift(j.jx));
                         const int d0 = S.d[3 * v] + nb.d[0], d1 = S.d[3 * v + 1] + nb.d[1],
                                   d2 = S.d[3 * v + 2] + nb.d[2];
                         if (tracer) {
@@ -1476,7 +1490,7 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                             wslot[m] = -1;
                             uint32_t o2;
                             int lf2;
-                            cowner(sh, S, geo, j.jx, j.jy, j.jz, o2, lf2);
+                            cowner(S, geo, j.jx, j.jy, j.jz, o2, lf2);
                             if (o2 == me) {  // another fragment of this slab: onto its list
                                 S.d[3 * v] = d0;
                                 S.d[3 * v + 1] = d1;
@@ -1517,10 +1531,10 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                         const int bt = pl < 8 ? t : j.t2;
                         const int bx = pl < 8 ? x : j.jx, by = pl < 8 ? y : j.jy, bz = pl < 8 ? z : j.jz;
                         const NbSite c = cnb_site(sh, geo, bt, bx, by, bz, pl & 7);
-                        const bool vac = csite_code(sh, S, geo, me, c.t2, c.jx, c.jy, c.jz) == SP_V;
+                        const bool vac = csite_code(zs, S, geo, me, c.t2, c.jx, c.jy, c.jz) == SP_V;
                         uint32_t oc;
                         int lc;
-                        cowner(sh, S, geo, c.jx, c.jy, c.jz, oc, lc);
+                        cowner(S, geo, c.jx, c.jy, c.jz, oc, lc);
                         compute_types();
                         if (lane < 16 && vac) {
                             if (oc == me) {
