@@ -1426,8 +1426,8 @@ int kmc_read_state(kmc_batch* b, int32_t r, uint8_t* host_occ, size_t n)
     for (int t = 0; t < 3; ++t)
         for (int z = 0; z < D.L[2]; ++z)
             for (int y = 0; y < D.L[1]; ++y) {
-                const uint32_t* row = w.data() + (((int64_t)t * D.L[2] + z) * D.L[1] + y) * D.row_words;
-                for (int x = 0; x < D.L[0]; ++x) host_occ[s++] = (uint8_t)((row[x >> 4] >> ((x & 15) * 2)) & 3u);
+                for (int x = 0; x < D.L[0]; ++x)
+                    host_occ[s++] = (uint8_t)((w[occ_index(D.row_words, D.L[1], t, x, y, z)] >> ((x & 15) * 2)) & 3u);
             }
     return FKMC_OK;
 }
@@ -1446,11 +1446,10 @@ int kmc_write_state(kmc_batch* b, int32_t r, const uint8_t* host_occ, size_t n)
     for (int t = 0; t < 3; ++t)
         for (int z = 0; z < D.L[2]; ++z)
             for (int y = 0; y < D.L[1]; ++y) {
-                uint32_t* row = w.data() + (((int64_t)t * D.L[2] + z) * D.L[1] + y) * D.row_words;
                 for (int x = 0; x < D.L[0]; ++x, ++s) {
                     const uint8_t c = host_occ[s];
                     if (c > 2) return fail(FKMC_EINVAL, "species codes must be 0, 1 or 2");
-                    row[x >> 4] |= (uint32_t)c << ((x & 15) * 2);
+                    w[occ_index(D.row_words, D.L[1], t, x, y, z)] |= (uint32_t)c << ((x & 15) * 2);
                     if (c == FKMC_H) ++nh;
                     if (c != FKMC_V) continue;
                     int f[3];

@@ -47,12 +47,16 @@ __global__ void k_check_occupancy(RepDesc D, const uint32_t* __restrict__ occ, u
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
          w += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t word = occ[D.occ_word_off + w];
-        const int64_t row = w / D.row_words;  // (t L2 + z) L1 + y
-        const int x0 = (int)(w - row * D.row_words) * 16;
+        const int64_t grp = w / 3;                  // (row, 16-cell block), the types interleaved
+        const int t = (int)(w - grp * 3);
+        const int64_t row = grp / D.row_words;      // z L1 + y
+        const int x0 = (int)(grp - row * D.row_words) * 16;
+        const int64_t z = row / D.L[1], y = row - z * D.L[1];
+        const int64_t lin0 = (((int64_t)t * D.L[2] + z) * D.L[1] + y) * D.L[0] + x0;  // linear site index of x0
         for (int j = 0; j < 16 && x0 + j < D.L[0]; ++j) {
             const int code = (int)((word >> (2 * j)) & 3u);
             v[CHK_SITES + code] += 1ull;
-            if (code == SP_V) v[CHK_HASH_VAC] += check_mix64((uint64_t)(row * D.L[0] + x0 + j));
+            if (code == SP_V) v[CHK_HASH_VAC] += check_mix64((uint64_t)(lin0 + j));
         }
     }
     warp_flush(out, v);

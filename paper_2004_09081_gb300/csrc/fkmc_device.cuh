@@ -284,10 +284,20 @@ __device__ __forceinline__ void split_key(uint64_t k, int& t, int& x, int& y, in
     t = (int)(k >> 48);
 }
 
+// Occupancy layout: 2 bits per site, 16 sites of one row and type per word;
+// the three site types' words of the same 16 cells are adjacent, then the
+// row's next 16 cells, rows ordered (z, y), each row row_words groups long.
+// A vacancy's 8 neighbours (the other two types, in its own row and the
+// adjacent y and z rows) then lie in about three 32-byte sectors.
+__host__ __device__ __forceinline__ int64_t occ_index(int64_t row_words, int L1, int t, int x, int y, int z)
+{
+    return (((int64_t)z * L1 + y) * row_words + (x >> 4)) * 3 + t;
+}
+
 // word index (within the batch occupancy array) and bit shift of a site
 __device__ __forceinline__ int64_t occ_word(const RepDesc& D, int t, int x, int y, int z)
 {
-    return D.occ_word_off + (((int64_t)t * D.L[2] + z) * D.L[1] + y) * D.row_words + (x >> 4);
+    return D.occ_word_off + occ_index(D.row_words, D.L[1], t, x, y, z);
 }
 
 __device__ __forceinline__ int occ_shift(int x) { return (x & 15) * 2; }

@@ -914,16 +914,15 @@ __device__ __forceinline__ uint32_t lane_types(const RepDesc& D, const uint32_t*
     int64_t cells = 0;
     if constexpr (GRAIN) cells = D.site_off / 3;
     if (x >= 1 && x <= L0 - 2 && y >= 1 && y <= L1 - 2 && z >= 1 && z <= L2 - 2) {
-        const int rb = (t * L2 + z) * L1 + y;
-        const int plane = L1 * L2;
+        const int rb = z * L1 + y;
 #pragma unroll
         for (int n = 0; n < 8; ++n) {
             const uint32_t f = (uint32_t)(g8 >> (8 * n));
             const int t2 = (int)(f & 3u);
             const int jx = x + (int)((f >> 2) & 3u) - 1;
             const int dcy = (int)((f >> 4) & 3u) - 1, dcz = (int)((f >> 6) & 3u) - 1;
-            const int row = rb + (t2 - t) * plane + dcz * L1 + dcy;
-            w[n] = __ldcg(occ_r + (int64_t)row * rw + (jx >> 4));
+            const int row = rb + dcz * L1 + dcy;
+            w[n] = __ldcg(occ_r + ((int64_t)row * rw + (jx >> 4)) * 3 + t2);
             xlo |= (uint32_t)(jx & 15) << (4 * n);
             if constexpr (GRAIN)
                 gbit |= (uint32_t)__ldg(gb + cells + ((int64_t)(z + dcz) * L1 + (y + dcy)) * L0 + jx) << n;
@@ -936,7 +935,7 @@ __device__ __forceinline__ uint32_t lane_types(const RepDesc& D, const uint32_t*
             const int jx = wrapc(x + (int)((f >> 2) & 3u) - 1, L0);
             const int jy = wrapc(y + (int)((f >> 4) & 3u) - 1, L1);
             const int jz = wrapc(z + (int)((f >> 6) & 3u) - 1, L2);
-            w[n] = __ldcg(occ_r + ((int64_t)(t2 * L2 + jz) * L1 + jy) * rw + (jx >> 4));
+            w[n] = __ldcg(occ_r + occ_index(rw, L1, t2, jx, jy, jz));
             xlo |= (uint32_t)(jx & 15) << (4 * n);
             if constexpr (GRAIN) gbit |= (uint32_t)__ldg(gb + cells + ((int64_t)jz * L1 + jy) * L0 + jx) << n;
         }

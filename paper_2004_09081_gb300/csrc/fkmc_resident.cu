@@ -301,7 +301,7 @@ __device__ __forceinline__ NbSite nb_site(const Shared& sh, const Geo& g, int t,
 
 __device__ __forceinline__ int site_code(const Geo& g, const uint32_t* occ, int t, int x, int y, int z)
 {
-    const uint32_t w = occ[((t * g.L2 + z) * g.L1 + y) * g.RW + (x >> 4)];
+    const uint32_t w = occ[((z * g.L1 + y) * g.RW + (x >> 4)) * 3 + t];
     return (int)((w >> occ_shift(x)) & 3u);
 }
 
@@ -729,8 +729,8 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                     if (lane == 0) {  // apply the exchange
                         const int v = wslot[m];
                         const uint32_t ion = (uint32_t)((nch <= 2 ? tsel : (int)wtype[e_sel]) / 3);
-                        uint32_t* ws = S.occ + ((t * geo.L2 + z) * geo.L1 + y) * geo.RW + (x >> 4);
-                        uint32_t* wj = S.occ + ((j.t2 * geo.L2 + j.jz) * geo.L1 + j.jy) * geo.RW + (j.jx >> 4);
+                        uint32_t* ws = S.occ + ((z * geo.L1 + y) * geo.RW + (x >> 4)) * 3 + t;
+                        uint32_t* wj = S.occ + ((j.jz * geo.L1 + j.jy) * geo.RW + (j.jx >> 4)) * 3 + j.t2;
                         const uint32_t ms = ((uint32_t)SP_V ^ ion) << occ_shift(x);
                         const uint32_t mj = (ion ^ (uint32_t)SP_V) << occ_shift(j.jx);
                         atomicXor(ws, ms);
@@ -929,7 +929,7 @@ struct CShared {
 };
 
 struct CLayout {
-    uint32_t* occ;       // [3][zs][L1][RW]
+    uint32_t* occ;       // [zs][L1][RW][3], the global layout of the slab's z cells
     uint32_t* key;       // vacancy pool [vcap]
     int32_t* d;
     uint32_t* id;
@@ -1028,27 +1028,26 @@ struct CWord {
     int idx;
 };
 
-__device__ __forceinline__ CWord cword(const CLayout& S, int zs, const Geo& g, int t, int x, int y, int z)
+__device__ __forceinline__ CWord cword(const CLayout& S, const Geo& g, int t, int x, int y, int z)
 {
     const uint32_t zm = S.zmap[z];
     CWord w;
     w.cta = zm & 255u;
-    w.idx = ((t * zs + (int)((zm >> 8) & 1023u)) * g.L1 + y) * g.RW + (x >> 4);
+    w.idx = ((((int)((zm >> 8) & 1023u)) * g.L1 + y) * g.RW + (x >> 4)) * 3 + t;
     return w;
 }
 
-__device__ __forceinline__ int csite_code(int zs, const CLayout& S, const Geo& g, uint32_t me, int t, int x, int y,
-                                          int z)
+__device__ __forceinline__ int csite_code(const CLayout& S, const Geo& g, uint32_t me, int t, int x, int y, int z)
 {
-    const CWord w = cword(S, zs, g, t, x, y, z);
+    const CWord w = cword(S, g, t, x, y, z);
     const uint32_t v = w.cta == me ? S.occ[w.idx] : (uint32_t)ld_peer(peer_addr(S.occ + w.idx, w.cta));
     return (int)((v >> occ_shift(x)) & 3u);
 }
 
-__device__ __forceinline__ void csite_xor(int zs, const CLayout& S, const Geo& g, uint32_t me, int t, int x, int y,
-                                          int z, uint32_t m)
+__device__ __forceinline__ void csite_xor(const CLayout& S, const Geo& g, uint32_t me, int t, int x, int y, int z,
+                                          uint32_t m)
 {
-    const CWord w = cword(S, zs, g, t, x, y, z);
+    const CWord w = cword(S, g, t, x, y, z);
     if (w.cta == me) atomicXor(S.occ + w.idx, m);
     else red_peer_xor(peer_addr(S.occ + w.idx, w.cta), m);
 }
@@ -1106,17 +1105,14 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
     const CLayout S = ccarve(dyn, D, P, cap, NT / 32);
     const Geo geo{D.L[0], D.L[1], D.L[2], D.row_words, D.nf[0], D.nf[1], D.F, D.theta_tau, window_f(D.theta_tau, D.F)};
     const int fzb = P.fz0[me], fze = P.fz0[me + 1];
-    const int zs = P.zs;  // cells in z of the common slab layout
     const int zb = sh.zbeg[me], zl = sh.zbeg[me + 1] - zb;
     const int nfl_me = (fze - fzb) * D.nf[0] * D.nf[1];
 
-    // ---- stage in: this slab's occupancy planes and vacancies, the lookup tables
-    const int plane = zl * D.L[1] * D.row_words;  // words of one site type's slab
-    for (int k = tid; k < 3 * plane; k += NT) {
-        const int t = k / plane, r = k - t * plane;
-        S.occ[t * P.zs * D.L[1] * D.row_words + r] =
-            occ[D.occ_word_off + ((int64_t)t * D.L[2] + zb) * D.L[1] * D.row_words + r];
-    }
+    // ---- stage in: this slab's occupancy (its z cells are contiguous in the
+    // global layout), its vacancies, the lookup tables
+    const int slab_words = zl * D.L[1] * D.row_words * 3;
+    const int64_t slab_off = D.occ_word_off + (int64_t)zb * D.L[1] * D.row_words * 3;
+    for (int k = tid; k < slab_words; k += NT) S.occ[k] = occ[slab_off + k];
     for (int k = tid; k < D.L[0] + D.L[1] + D.L[2]; k += NT) {
         const int d = k < D.L[0] ? 0 : (k < D.L[0] + D.L[1] ? 1 : 2);
         const int c = d == 0 ? k : (d == 1 ? k - D.L[0] : k - D.L[0] - D.L[1]);
@@ -1325,7 +1321,7 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                     int t, x, y, z;
                     split32(k, t, x, y, z);
                     const NbEntry nbe = sh.nb[t][q];
-                    const int code = csite_code(zs, S, geo, me, nbe.t2, wrapc(x + nbe.dc[0], geo.L0),
+                    const int code = csite_code(S, geo, me, nbe.t2, wrapc(x + nbe.dc[0], geo.L0),
                                                 wrapc(y + nbe.dc[1], geo.L1), wrapc(z + nbe.dc[2], geo.L2));
                     return code == SP_V ? -1 : code * 3 + nbe.d[2] + 1;
                 };
@@ -1466,8 +1462,8 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                     if (lane == 0) {  // apply the exchange
                         const int v = wslot[m];
                         const uint32_t ion = (uint32_t)((nch <= 2 ? tsel : (int)wtype[e_sel]) / 3);
-                        csite_xor(zs, S, geo, me, t, x, y, z, ((uint32_t)SP_V ^ ion) << occ_shift(x));
-                        csite_xor(zs, S, geo, me, j.t2, j.jx, j.jy, j.jz, (ion ^ (uint32_t)SP_V) << occ_shift(j.jx));
+                        csite_xor(S, geo, me, t, x, y, z, ((uint32_t)SP_V ^ ion) << occ_shift(x));
+                        csite_xor(S, geo, me, j.t2, j.jx, j.jy, j.jz, (ion ^ (uint32_t)SP_V) << occ_shift(j.jx));
                         const int d0 = S.d[3 * v] + nb.d[0], d1 = S.d[3 * v + 1] + nb.d[1],
                                   d2 = S.d[3 * v + 2] + nb.d[2];
                         if (tracer) {
@@ -1531,7 +1527,7 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                         const int bt = pl < 8 ? t : j.t2;
                         const int bx = pl < 8 ? x : j.jx, by = pl < 8 ? y : j.jy, bz = pl < 8 ? z : j.jz;
                         const NbSite c = cnb_site(sh, geo, bt, bx, by, bz, pl & 7);
-                        const bool vac = csite_code(zs, S, geo, me, c.t2, c.jx, c.jy, c.jz) == SP_V;
+                        const bool vac = csite_code(S, geo, me, c.t2, c.jx, c.jy, c.jz) == SP_V;
                         uint32_t oc;
                         int lc;
                         cowner(S, geo, c.jx, c.jy, c.jz, oc, lc);
@@ -1580,12 +1576,8 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
     }
     if (ph > 0) drain((ph - 1) & 1);
 
-    // ---- stage out: this slab's occupancy planes, its fragments' records
-    for (int k = tid; k < 3 * plane; k += NT) {
-        const int t = k / plane, r = k - t * plane;
-        occ[D.occ_word_off + ((int64_t)t * D.L[2] + zb) * D.L[1] * D.row_words + r] =
-            S.occ[t * P.zs * D.L[1] * D.row_words + r];
-    }
+    // ---- stage out: this slab's occupancy, its fragments' records
+    for (int k = tid; k < slab_words; k += NT) occ[slab_off + k] = S.occ[k];
     for (int lf = tid; lf < nfl_me; lf += NT) {
         const int64_t g = D.frag_base + (int64_t)fzb * D.nf[1] * D.nf[0] + lf;
         int k = 0;

@@ -122,7 +122,7 @@ def test_corrupted_states_are_reported(fk):
     rec0 = g[o_rec + 24 * f0 * cap:o_rec + 24 * (f0 * cap + 1)]
     key = int(rec0[:8].view(np.uint64)[0])
     x, y, z, t = key & 0xFFFF, (key >> 16) & 0xFFFF, (key >> 32) & 0xFFFF, key >> 48
-    word = ((t * cells[2] + z) * cells[1] + y) * rw + (x >> 4)
+    word = ((z * cells[1] + y) * rw + (x >> 4)) * 3 + t  # the three site types interleaved per 16-cell block
 
     def upload_and_check(mutate):
         bad = good.clone().pin_memory()
@@ -136,7 +136,8 @@ def test_corrupted_states_are_reported(fk):
         w[0] &= np.uint32(~(3 << (2 * (x & 15))) & 0xFFFFFFFF)
 
     inv = upload_and_check(clear_vacancy)
-    assert (inv.ok, inv.sites[fk.FKMC_V], inv.sites[fk.FKMC_O], inv.rec_not_vacancy) == (0, nv - 1, 3 * 16 * 12 * 12 - nv - nh + 1, 1)
+    n_o = 3 * 16 * 12 * 12 - nv - nh + 1
+    assert (inv.ok, inv.sites[fk.FKMC_V], inv.sites[fk.FKMC_O], inv.rec_not_vacancy) == (0, nv - 1, n_o, 1)
     assert inv.hash_vac_sites != inv.hash_rec_sites
 
     def change_id(a):
