@@ -1255,6 +1255,22 @@ struct LaneSlots {
     uint32_t ty[LANE_MAX_V][LANE_THREADS];             // packed rate types (lane_types)
 };
 
+// asynchronous copies global -> shared (cp.async, 4 or 8 bytes, both addresses
+// aligned to the size), completed for the issuing thread by cp_async_wait_all
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src)
 {
     const unsigned lo = __shfl_sync(0xffffffffu, (unsigned)v, src);
@@ -1405,18 +1421,23 @@ __global__ void __launch_bounds__(LANE_THREADS) k_run_lane(const RepDesc* __rest
                     atomicOr(status, STATUS_OVERFLOW);
                     nv = cap;
                 }
-                // records to the slots; slot order by ascending site
+                // records to the slots, every copy in flight at once (one memory
+                // latency instead of one per record); slot order by ascending site
+                for (int q = 0; q < nv; ++q) {
+                    const VacRec* src = recs + g * cap + q;
+                    cp_async8(&S.key[q][tid], &src->key);
+                    cp_async4(&S.d[0][q][tid], &src->d[0]);
+                    cp_async4(&S.d[1][q][tid], &src->d[1]);
+                    cp_async4(&S.d[2][q][tid], &src->d[2]);
+                    cp_async4(&S.id[q][tid], &src->id);
+                }
+                cp_async_wait_all();
                 uint32_t rank = 0;  // nibble k: rank of record k
                 for (int q = 0; q < nv; ++q) {
-                    const VacRec r = recs[g * cap + q];
-                    S.key[q][tid] = r.key;
-                    S.d[0][q][tid] = r.d[0];
-                    S.d[1][q][tid] = r.d[1];
-                    S.d[2][q][tid] = r.d[2];
-                    S.id[q][tid] = r.id;
+                    const uint64_t kq = S.key[q][tid];
                     uint32_t rq = 0;
                     for (int j = 0; j < q; ++j) {
-                        const bool less = S.key[j][tid] < r.key;
+                        const bool less = S.key[j][tid] < kq;
                         rq += less;
                         rank += (uint32_t)(!less) << (4 * j);
                     }
