@@ -112,6 +112,17 @@ __device__ __forceinline__ void cluster_sync()
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// the two halves of cluster_sync: work that reads and writes nothing a peer
+// touches may run between them
+__device__ __forceinline__ void cluster_arrive()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait()
+{
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // address in CTA `peer`'s shared memory of the same variable as `p`
 __device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t peer)
 {
@@ -946,13 +957,15 @@ struct CLayout {
     InboxRec* inbox;     // [2][icap]
     uint16_t* frag_of_c; // cell -> global fragment coordinate: x cells, then y, then z
     uint32_t* zmap;      // z cell -> its CTA | z within that CTA's slab << 8 | fragment layer within it << 18
+    uint64_t* pre_xs;    // the next phase's first draws by screen index: selection words of events 0, 1
+    float* pre_E;        // and their exponential variates
 };
 
 __host__ __device__ inline size_t cluster_layout_bytes(const RepDesc& D, const ClusterPlan& P, int cap, int nwarps,
-                                                       size_t* off /* 17 offsets or null */)
+                                                       size_t* off /* 19 offsets or null */)
 {
     const size_t words = (size_t)3 * P.zs * D.L[1] * D.row_words;
-    const size_t sz[17] = {
+    const size_t sz[19] = {
         words * 4,                          // 0 occupancy slab
         (size_t)P.vcap * 4,                 // 1 keys
         (size_t)P.vcap * 12,                // 2 displacements
@@ -970,9 +983,11 @@ __host__ __device__ inline size_t cluster_layout_bytes(const RepDesc& D, const C
         (size_t)2 * P.icap * sizeof(InboxRec),  // 14 inboxes
         (size_t)(D.L[0] + D.L[1] + D.L[2]) * 2, // 15 cell -> fragment tables
         (size_t)D.L[2] * 4,                 // 16 z cell -> CTA, slab z, slab fragment layer
+        (size_t)P.nfl * 16,                 // 17 next phase: selection words of events 0, 1
+        (size_t)P.nfl * 8,                  // 18 next phase: variates
     };
     size_t b = 0;
-    for (int k = 0; k < 17; ++k) {
+    for (int k = 0; k < 19; ++k) {
         if (off) off[k] = b;
         b += (sz[k] + 15) & ~(size_t)15;
     }
@@ -984,7 +999,7 @@ namespace {
 __device__ __forceinline__ CLayout ccarve(unsigned char* dyn, const RepDesc& D, const ClusterPlan& P, int cap,
                                           int nwarps)
 {
-    size_t o[17];
+    size_t o[19];
     cluster_layout_bytes(D, P, cap, nwarps, o);
     CLayout L;
     L.occ = reinterpret_cast<uint32_t*>(dyn + o[0]);
@@ -1004,6 +1019,8 @@ __device__ __forceinline__ CLayout ccarve(unsigned char* dyn, const RepDesc& D, 
     L.inbox = reinterpret_cast<InboxRec*>(dyn + o[14]);
     L.frag_of_c = reinterpret_cast<uint16_t*>(dyn + o[15]);
     L.zmap = reinterpret_cast<uint32_t*>(dyn + o[16]);
+    L.pre_xs = reinterpret_cast<uint64_t*>(dyn + o[17]);
+    L.pre_E = reinterpret_cast<float*>(dyn + o[18]);
     return L;
 }
 
@@ -1194,6 +1211,27 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
         }
     };
 
+    // this slab's fragments of a colour: count per dimension, parity bits, first
+    // fragment layer; and the coordinates of the colour's local fragment l
+    auto colour_geo = [&](int colour, int cnt[2], int bit[3], int& lz0) -> int {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) bit[d] = (colour >> d) & 1;
+#pragma unroll
+        for (int d = 0; d < 2; ++d) cnt[d] = D.nf[d] == 1 ? (bit[d] == 0 ? 1 : 0) : D.nf[d] / 2;
+        lz0 = D.nf[2] == 1 ? 0 : (fzb + ((fzb & 1) != bit[2] ? 1 : 0));
+        const int nlz = D.nf[2] == 1 ? (bit[2] == 0 ? 1 : 0) : (fze > lz0 ? (fze - lz0 + 1) / 2 : 0);
+        return cnt[0] * cnt[1] * nlz;
+    };
+    auto frag_coords = [&](int l, const int cnt[2], const int bit[3], int lz0, int& f0, int& f1, int& f2) {
+        f0 = l % cnt[0];
+        f1 = (l / cnt[0]) % cnt[1];
+        f2 = l / (cnt[0] * cnt[1]);
+        f0 = D.nf[0] == 1 ? 0 : 2 * f0 + bit[0];
+        f1 = D.nf[1] == 1 ? 0 : 2 * f1 + bit[1];
+        f2 = lz0 + 2 * f2;
+    };
+    bool pre_valid = false;  // the phase's first draws were computed at the end of the last one
+
     uint32_t ph = 0;
     for (uint64_t wk = 0; wk < windows; ++wk) {
         const uint64_t w = D.window + wk;
@@ -1205,15 +1243,8 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
         for (int p = 0; p < 8; ++p, ++ph) {
             if (ph > 0) drain((ph - 1) & 1);
             const int colour = (int)((wperm >> (4 * p)) & 15u);
-            int cnt[2], bit[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) bit[d] = (colour >> d) & 1;
-#pragma unroll
-            for (int d = 0; d < 2; ++d) cnt[d] = D.nf[d] == 1 ? (bit[d] == 0 ? 1 : 0) : D.nf[d] / 2;
-            // this slab's layers of the colour's z parity
-            const int lz0 = D.nf[2] == 1 ? 0 : (fzb + ((fzb & 1) != bit[2] ? 1 : 0));
-            const int nlz = D.nf[2] == 1 ? (bit[2] == 0 ? 1 : 0) : (fze > lz0 ? (fze - lz0 + 1) / 2 : 0);
-            const int ncls = cnt[0] * cnt[1] * nlz;
+            int cnt[2], bit[3], lz0;
+            const int ncls = colour_geo(colour, cnt, bit, lz0);
             if (tid == 0) {
                 sh.nact = 0;
                 sh.next_act = 0;
@@ -1221,18 +1252,28 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
             __syncthreads();
             // ---- screen: one thread per local fragment of the colour
             for (int l = tid; l < ncls; l += NT) {
-                int f0 = l % cnt[0], f1 = (l / cnt[0]) % cnt[1], f2 = l / (cnt[0] * cnt[1]);
-                f0 = D.nf[0] == 1 ? 0 : 2 * f0 + bit[0];
-                f1 = D.nf[1] == 1 ? 0 : 2 * f1 + bit[1];
-                f2 = lz0 + 2 * f2;
+                int f0, f1, f2;
+                frag_coords(l, cnt, bit, lz0, f0, f1, f2);
                 const int lf = ((f2 - fzb) * D.nf[1] + f1) * D.nf[0] + f0;
                 const int fid = (f2 * D.nf[1] + f1) * D.nf[0] + f0;
                 if (S.head[lf] < 0) continue;
                 const bool dirty = S.dirty[lf] != 0;
                 const unsigned long long tot = S.S[lf];
                 if (!dirty && tot == 0ull) continue;
-                const U64x4 blk = philox4x64((uint64_t)fid, w, 0, 0, D.seed, hop_k1);
-                const float E0 = neglog32(blk.x[0]);
+                float E0, E1 = 0.f;
+                uint64_t xs0, xs1;
+                U64x4 blk{};
+                if (pre_valid) {
+                    E0 = S.pre_E[2 * l];
+                    E1 = S.pre_E[2 * l + 1];
+                    xs0 = S.pre_xs[2 * l];
+                    xs1 = S.pre_xs[2 * l + 1];
+                } else {
+                    blk = philox4x64((uint64_t)fid, w, 0, 0, D.seed, hop_k1);
+                    E0 = neglog32(blk.x[0]);
+                    xs0 = blk.x[1];
+                    xs1 = blk.x[3];
+                }
                 bool active = dirty;
                 if (!active) {
                     const float ratio = __fdiv_rn(E0, __ull2float_rn(tot));
@@ -1242,9 +1283,9 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                     const int a = atomicAdd(&sh.nact, 1);
                     S.act[a] = f0 | (f1 << 10) | (f2 << 20);  // fragment coordinates (< 1024 each)
                     S.act_E[2 * a] = E0;
-                    S.act_E[2 * a + 1] = neglog32(blk.x[2]);
-                    S.act_xs[2 * a] = blk.x[1];
-                    S.act_xs[2 * a + 1] = blk.x[3];
+                    S.act_E[2 * a + 1] = pre_valid ? E1 : neglog32(blk.x[2]);
+                    S.act_xs[2 * a] = xs0;
+                    S.act_xs[2 * a + 1] = xs1;
                 }
             }
             __syncthreads();
@@ -1571,7 +1612,39 @@ __global__ void __launch_bounds__(NT, 1) k_cluster(const RepDesc* __restrict__ d
                 }
                 __syncwarp();
             }
-            cluster_sync();  // every write of the phase, local and remote, is visible
+            // every write of the phase, local and remote, is visible after the wait.
+            // Between arrival and wait: the next phase's first draws (events 0 and 1
+            // of each of this CTA's fragments of the next colour), which depend on no
+            // fragment's state, so that they overlap the barrier's release
+            cluster_arrive();
+            pre_valid = false;
+            {
+                int ncolour = -1;
+                uint64_t nw = w;
+                if (p < 7) {
+                    ncolour = (int)((wperm >> (4 * (p + 1))) & 15u);
+                } else if (wk + 1 < windows && ((wk + 1) & 63) != 0) {  // the next window's order is known
+                    ncolour = (int)(sh.perms[(wk + 1) & 63] & 15u);
+                    nw = w + 1;
+                }
+                if (ncolour >= 0) {
+                    int ncnt[2], nbit[3], nlz0;
+                    const int nn = colour_geo(ncolour, ncnt, nbit, nlz0);
+                    for (int l = tid; l < nn; l += NT) {
+                        int f0, f1, f2;
+                        frag_coords(l, ncnt, nbit, nlz0, f0, f1, f2);
+                        const int fid = (f2 * D.nf[1] + f1) * D.nf[0] + f0;
+                        const U64x4 blk = philox4x64((uint64_t)fid, nw, 0, 0, D.seed, hop_k1);
+                        S.pre_E[2 * l] = neglog32(blk.x[0]);
+                        S.pre_E[2 * l + 1] = neglog32(blk.x[2]);
+                        S.pre_xs[2 * l] = blk.x[1];
+                        S.pre_xs[2 * l + 1] = blk.x[3];
+                    }
+                    pre_valid = true;
+                }
+            }
+            __syncwarp();
+            cluster_wait();
         }
     }
     if (ph > 0) drain((ph - 1) & 1);
