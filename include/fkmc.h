@@ -184,6 +184,10 @@ typedef struct {
                             kernel (state in one SM's shared memory, or a 2-CTA mirrored pair),
                             2 = cluster-resident kernel (z-slabs in a thread-block cluster) */
     int32_t ctas;        /* CTAs holding the replica (kernels 1 and 2), else 0 */
+    int32_t draw_phases; /* kernel 1: colour phases whose fragments' first random draws the kernel
+                            makes in one batch (8, 4, 2 or 1, as the replica's shared-memory class
+                            leaves room), else 0 */
+    int32_t pad;
 } kmc_replica_info;
 
 typedef struct kmc_batch kmc_batch;

@@ -423,8 +423,19 @@ int plan_residency(kmc_batch* b)
         int c = -1;
         size_t need = 0;
         for (int k = 0; k < 5 && allowed && c < 0; ++k) {
-            need = resident_smem_bytes(b->desc[r], b->n_vac[r], b->cap, threads[k]);
+            need = resident_smem_bytes(b->desc[r], b->n_vac[r], b->cap, threads[k], 1);
             if (need <= bounds[k]) c = k;
+        }
+        // the first draws of as many colour phases per batch as the class's shared
+        // memory allows beside the state (8: one batch per window)
+        b->desc[r].pre_g = 1;
+        for (int g = 8; c >= 0 && g > 1; g >>= 1) {
+            const size_t ng = resident_smem_bytes(b->desc[r], b->n_vac[r], b->cap, threads[c], g);
+            if (ng <= bounds[c]) {
+                b->desc[r].pre_g = g;
+                need = ng;
+                break;
+            }
         }
         // the cluster-resident kernel: a replica too large for one SM (or every
         // replica, with cluster_ctas forced) held by a cluster of CTAs, one z-slab each
@@ -2183,6 +2194,7 @@ int kmc_get_replica_info(kmc_batch* b, int32_t r, kmc_replica_info* out)
     if ((int)b->run_kernel.size() == b->n) {
         out->kernel = b->run_kernel[r];
         out->ctas = b->run_ctas[r];
+        out->draw_phases = b->run_kernel[r] == 1 ? D.pre_g : 0;
     }
     return FKMC_OK;
 }

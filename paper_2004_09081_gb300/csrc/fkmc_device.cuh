@@ -53,7 +53,7 @@ struct RepDesc {
     double theta_tau;      // window length in units of 1/k32max, mixed clock
     double two_pow_F;      // 2^F, exact
     int32_t resident;      // 1: this replica runs in the replica-resident kernel
-    int32_t pad_;
+    int32_t pre_g;         // replica-resident kernel: colour phases whose first draws are made in one batch (1, 2, 4 or 8)
     int64_t btab_off;      // site energies: first Boltzmann-table entry of this replica
     int32_t bhi_mid;       // index of the high-table entry for m1 = 0
     int32_t bhi_len;       // entries of the high table

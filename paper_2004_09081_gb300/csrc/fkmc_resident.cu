@@ -216,8 +216,8 @@ struct Layout {
     unsigned long long* S;
     uint8_t* dirty;
     int32_t* act;          // screened fragments
-    float* act_E;          // their first two exponential variates (events 0, 1)
-    uint64_t* act_xs;      // and selection words
+    float* pre_E;          // first two exponential variates (events 0, 1) of every fragment of the
+    uint64_t* pre_xs;      // batch's phases, and their selection words, by (phase in batch, screen index)
     uint16_t* frag_of_c;   // cell -> fragment index: x cells, then y, then z
     int16_t* wslot;   // per warp: vacancy index of each slot (-1: handed off)
     int8_t* wtype;    // per warp: rate type of each event (-1: none)
@@ -225,7 +225,7 @@ struct Layout {
 
 
 __host__ __device__ inline size_t layout_bytes(int64_t words, int64_t nv, int64_t nfrag, int64_t ncls, int cap,
-                                               int nwarps, int ltot, size_t* off /* 14 offsets or null */)
+                                               int nwarps, int ltot, int pre_g, size_t* off /* 14 offsets or null */)
 {
     // every array starts on a 16-byte boundary, whatever the sizes before it
     const size_t sz[14] = {
@@ -240,8 +240,8 @@ __host__ __device__ inline size_t layout_bytes(int64_t words, int64_t nv, int64_
         (size_t)ncls * 4,          // 8 screened list
         (size_t)nwarps * cap * 2,  // 9 per-warp slots
         (size_t)nwarps * cap * 8,  // 10 per-warp event types
-        (size_t)ncls * 16,         // 11 screened: selection words
-        (size_t)ncls * 8,          // 12 screened: variates
+        (size_t)pre_g * ncls * 16, // 11 first draws of the batch's phases: selection words
+        (size_t)pre_g * ncls * 8,  // 12 and variates
         (size_t)ltot * 2,          // 13 cell -> fragment tables
     };
     size_t b = 0;
@@ -253,10 +253,10 @@ __host__ __device__ inline size_t layout_bytes(int64_t words, int64_t nv, int64_
 }
 
 __device__ __forceinline__ Layout carve(unsigned char* dyn, int64_t words, int64_t nv, int64_t nfrag, int64_t ncls,
-                                        int cap, int nwarps, int ltot)
+                                        int cap, int nwarps, int ltot, int pre_g)
 {
     size_t o[14];
-    layout_bytes(words, nv, nfrag, ncls, cap, nwarps, ltot, o);
+    layout_bytes(words, nv, nfrag, ncls, cap, nwarps, ltot, pre_g, o);
     Layout L;
     L.occ = reinterpret_cast<uint32_t*>(dyn + o[0]);
     L.key = reinterpret_cast<uint32_t*>(dyn + o[1]);
@@ -267,8 +267,8 @@ __device__ __forceinline__ Layout carve(unsigned char* dyn, int64_t words, int64
     L.S = reinterpret_cast<unsigned long long*>(dyn + o[6]);
     L.dirty = reinterpret_cast<uint8_t*>(dyn + o[7]);
     L.act = reinterpret_cast<int32_t*>(dyn + o[8]);
-    L.act_xs = reinterpret_cast<uint64_t*>(dyn + o[11]);
-    L.act_E = reinterpret_cast<float*>(dyn + o[12]);
+    L.pre_xs = reinterpret_cast<uint64_t*>(dyn + o[11]);
+    L.pre_E = reinterpret_cast<float*>(dyn + o[12]);
     L.frag_of_c = reinterpret_cast<uint16_t*>(dyn + o[13]);
     L.wslot = reinterpret_cast<int16_t*>(dyn + o[9]);
     L.wtype = reinterpret_cast<int8_t*>(dyn + o[10]);
@@ -330,14 +330,15 @@ __device__ __forceinline__ double scale_pow2(double d, int F)
 
 }  // namespace
 
-size_t resident_smem_bytes(const RepDesc& D, int64_t n_vac, int cap, int threads)
+size_t resident_smem_bytes(const RepDesc& D, int64_t n_vac, int cap, int threads, int pre_g)
 {
     const int64_t words = 3 * (int64_t)D.L[2] * D.L[1] * D.row_words;
     const int64_t nfrag = (int64_t)D.nf[0] * D.nf[1] * D.nf[2];
     const int64_t ncls = (int64_t)((D.nf[0] + 1) / 2) * ((D.nf[1] + 1) / 2) * ((D.nf[2] + 1) / 2);
     if (D.L[0] > 1024 || D.L[1] > 1024 || D.L[2] > 1024 || n_vac > 32767 || nfrag > 32767)
         return ~(size_t)0;  // compact keys and 16-bit links need these bounds
-    return layout_bytes(words, n_vac, nfrag, ncls, cap, threads / 32, D.L[0] + D.L[1] + D.L[2], nullptr);
+    if (pre_g < 1 || pre_g > 8 || (8 % pre_g) != 0) return ~(size_t)0;
+    return layout_bytes(words, n_vac, nfrag, ncls, cap, threads / 32, D.L[0] + D.L[1] + D.L[2], pre_g, nullptr);
 }
 
 // CL = CTAs per replica (a thread-block cluster).  With CL = 2 both CTAs hold
@@ -376,7 +377,8 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
     const int64_t words = 3 * (int64_t)D.L[2] * D.L[1] * D.row_words;
     const int nfrag = D.nf[0] * D.nf[1] * D.nf[2];
     const int ncls_max = ((D.nf[0] + 1) / 2) * ((D.nf[1] + 1) / 2) * ((D.nf[2] + 1) / 2);
-    const Layout S = carve(dyn, words, n_vac, nfrag, ncls_max, cap, NT / 32, D.L[0] + D.L[1] + D.L[2]);
+    const int pre_g = (D.pre_g == 2 || D.pre_g == 4 || D.pre_g == 8) ? D.pre_g : 1;  // the host sized the layout for it
+    const Layout S = carve(dyn, words, n_vac, nfrag, ncls_max, cap, NT / 32, D.L[0] + D.L[1] + D.L[2], pre_g);
 
     // ---- stage in: occupancy by TMA bulk copies, records by plain loads (the
     // first CTA of a cluster; the second copies its shared memory afterwards)
@@ -454,7 +456,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
             if (!sh.abort) {
                 const uint32_t base = peer_addr(dyn, 0);
                 const size_t bytes = layout_bytes(words, n_vac, nfrag, ncls_max, cap, NT / 32,
-                                                  D.L[0] + D.L[1] + D.L[2], nullptr);
+                                                  D.L[0] + D.L[1] + D.L[2], pre_g, nullptr);
                 for (size_t k = (size_t)tid * 16; k < bytes; k += (size_t)NT * 16) {
                     const uint4 v = ld_peer16(base + (uint32_t)k);
                     *reinterpret_cast<uint4*>(dyn + k) = v;
@@ -490,6 +492,32 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                 cnt[d] = D.nf[d] == 1 ? (bit[d] == 0 ? 1 : 0) : D.nf[d] / 2;
             }
             const int ncls = cnt[0] * cnt[1] * cnt[2];
+            const int pslot = p & (pre_g - 1);  // this phase's rows of the first-draw arrays
+            if (pslot == 0) {
+                // first draws (block 0: events 0 and 1) of every fragment of the next pre_g
+                // phases, one thread each: they depend on no state, and one batch of Philox
+                // blocks here replaces one per phase on the phases' critical paths
+                for (int idx = tid; idx < pre_g * ncls_max; idx += NT) {
+                    const int pp = idx / ncls_max, l = idx - pp * ncls_max;
+                    const int col = (int)((wperm >> (4 * (p + pp))) & 15u);
+                    int c3[3], f3[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+                        c3[d] = D.nf[d] == 1 ? (((col >> d) & 1) == 0 ? 1 : 0) : D.nf[d] / 2;
+                    if (l >= c3[0] * c3[1] * c3[2]) continue;
+                    f3[0] = l % c3[0];
+                    f3[1] = (l / c3[0]) % c3[1];
+                    f3[2] = l / (c3[0] * c3[1]);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) f3[d] = D.nf[d] == 1 ? 0 : 2 * f3[d] + ((col >> d) & 1);
+                    const int fid = (f3[2] * D.nf[1] + f3[1]) * D.nf[0] + f3[0];
+                    const U64x4 blk = philox4x64((uint64_t)fid, w, 0, 0, D.seed, hop_k1);
+                    S.pre_E[2 * idx] = neglog32(blk.x[0]);
+                    S.pre_E[2 * idx + 1] = neglog32(blk.x[2]);
+                    S.pre_xs[2 * idx] = blk.x[1];
+                    S.pre_xs[2 * idx + 1] = blk.x[3];
+                }
+            }
             if (tid == 0) {
                 sh.nact = 0;
                 sh.next_act = 0;
@@ -506,20 +534,15 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                 const bool dirty = S.dirty[fid] != 0;
                 const unsigned long long tot = S.S[fid];
                 if (!dirty && tot == 0ull) continue;
-                const U64x4 blk = philox4x64((uint64_t)fid, w, 0, 0, D.seed, hop_k1);
-                const float E0 = neglog32(blk.x[0]);
                 bool active = dirty;
                 if (!active) {
+                    const float E0 = S.pre_E[2 * (pslot * ncls_max + l)];
                     const float ratio = __fdiv_rn(E0, __ull2float_rn(tot));
                     active = !(ratio > geo.theta_f);  // 0 + 2^F ratio <= theta
                 }
                 if (active) {
                     const int a = atomicAdd(&sh.nact, 1);
                     S.act[a] = f0 | (f1 << 10) | (f2 << 20);  // fragment coordinates (< 1024 each)
-                    S.act_E[2 * a] = E0;
-                    S.act_E[2 * a + 1] = neglog32(blk.x[2]);
-                    S.act_xs[2 * a] = blk.x[1];
-                    S.act_xs[2 * a + 1] = blk.x[3];
                 }
             }
             __syncthreads();
@@ -534,6 +557,10 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                 const int fxyz = S.act[a];
                 const int fx = fxyz & 1023, fy = (fxyz >> 10) & 1023, fz = fxyz >> 20;
                 const int fid = (fz * D.nf[1] + fy) * D.nf[0] + fx;
+                // the fragment's screen index within its colour, and its row of first draws
+                const int ls = ((D.nf[2] == 1 ? 0 : fz >> 1) * cnt[1] + (D.nf[1] == 1 ? 0 : fy >> 1)) * cnt[0] +
+                               (D.nf[0] == 1 ? 0 : fx >> 1);
+                const int prow = pslot * ncls_max + ls;
                 const int lo0 = frag_start(fx, D.base[0], D.rem[0]), hi0 = frag_start(fx + 1, D.base[0], D.rem[0]);
                 const int lo1 = frag_start(fy, D.base[1], D.rem[1]), hi1 = frag_start(fy + 1, D.base[1], D.rem[1]);
                 const int lo2 = frag_start(fz, D.base[2], D.rem[2]), hi2 = frag_start(fz + 1, D.base[2], D.rem[2]);
@@ -664,9 +691,9 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                     }
                     uint64_t xs;
                     float E;
-                    if (i < 2) {  // block 0, drawn by the screen pass
-                        xs = S.act_xs[2 * a + (int)i];
-                        E = S.act_E[2 * a + (int)i];
+                    if (i < 2) {  // block 0, drawn in the batch before the phase
+                        xs = S.pre_xs[2 * prow + (int)i];
+                        E = S.pre_E[2 * prow + (int)i];
                     } else {
                         // events [2 + 64 b, 66 + 64 b) come from blocks 1 + 32 b + lane
                         const uint64_t k = i - 2;

@@ -222,9 +222,15 @@ def test_batched_workload_full_size_sampled(fk, orc):
         m = b.moments(r, 2)
         assert m[0] == reps[r].n_vac
     cap = b.info(0).cap_v
-    # the largest replicas (1024- or 512-thread class) and a spread of others
+    # the largest replicas (1024- or 512-thread class), a spread of others, and
+    # one replica of every batch size of the resident kernel's first draws
     largest = sorted(range(len(reps)), key=lambda r: -reps[r].n_vac)[:3]
-    for r in sorted(set(largest) | {0, 1, 97, 200, 255}):
+    by_draws = {}
+    for r in range(len(reps)):
+        if b.info(r).kernel == 1:
+            by_draws.setdefault(b.info(r).draw_phases, r)
+    assert set(by_draws) <= {1, 2, 4, 8} and 8 in by_draws
+    for r in sorted(set(largest) | {0, 1, 97, 200, 255} | set(by_draws.values())):
         rep = reps[r]
         info = b.info(r)
         ref = orc.Lattice(rep.cells, None, rep.n_vac, rep.n_H, seed=0, replica=r, edge=wl.edge)
