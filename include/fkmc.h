@@ -187,7 +187,8 @@ typedef struct {
     int32_t draw_phases; /* kernel 1: colour phases whose fragments' first random draws the kernel
                             makes in one batch (8, 4, 2 or 1, as the replica's shared-memory class
                             leaves room), else 0 */
-    int32_t pad;
+    int32_t draw_events; /* kernel 1: events per fragment and phase drawn in that batch (4 where
+                            2 or more phases of them fit, else 2), else 0 */
 } kmc_replica_info;
 
 typedef struct kmc_batch kmc_batch;

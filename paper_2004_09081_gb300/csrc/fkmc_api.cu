@@ -423,16 +423,20 @@ int plan_residency(kmc_batch* b)
         int c = -1;
         size_t need = 0;
         for (int k = 0; k < 5 && allowed && c < 0; ++k) {
-            need = resident_smem_bytes(b->desc[r], b->n_vac[r], b->cap, threads[k], 1);
+            need = resident_smem_bytes(b->desc[r], b->n_vac[r], b->cap, threads[k], 1, 2);
             if (need <= bounds[k]) c = k;
         }
         // the first draws of as many colour phases per batch as the class's shared
-        // memory allows beside the state (8: one batch per window)
+        // memory allows beside the state (8: one batch per window): four events per
+        // fragment where 2 or more phases of them fit, else two
         b->desc[r].pre_g = 1;
-        for (int g = 8; c >= 0 && g > 1; g >>= 1) {
-            const size_t ng = resident_smem_bytes(b->desc[r], b->n_vac[r], b->cap, threads[c], g);
+        b->desc[r].pre_ev = 2;
+        static const int pick[6][2] = {{8, 4}, {4, 4}, {2, 4}, {8, 2}, {4, 2}, {2, 2}};  // (phases, events)
+        for (int k = 0; c >= 0 && k < 6; ++k) {
+            const size_t ng = resident_smem_bytes(b->desc[r], b->n_vac[r], b->cap, threads[c], pick[k][0], pick[k][1]);
             if (ng <= bounds[c]) {
-                b->desc[r].pre_g = g;
+                b->desc[r].pre_g = pick[k][0];
+                b->desc[r].pre_ev = pick[k][1];
                 need = ng;
                 break;
             }
@@ -2195,6 +2199,7 @@ int kmc_get_replica_info(kmc_batch* b, int32_t r, kmc_replica_info* out)
         out->kernel = b->run_kernel[r];
         out->ctas = b->run_ctas[r];
         out->draw_phases = b->run_kernel[r] == 1 ? D.pre_g : 0;
+        out->draw_events = b->run_kernel[r] == 1 ? (D.pre_ev == 4 ? 4 : 2) : 0;
     }
     return FKMC_OK;
 }

@@ -69,6 +69,8 @@ struct RepDesc {
     double k64g[6];
     uint64_t qg[6];
     uint64_t qng[6];
+    int32_t pre_ev;        // replica-resident kernel: events per fragment drawn in the batch (2: block 0; 4: blocks 0, 1)
+    int32_t pad_ev_;
 };
 
 // One pick of the null-event form: the vacancy (by id) and its event (-1: null).

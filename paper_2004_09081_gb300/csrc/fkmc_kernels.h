@@ -129,7 +129,7 @@ cudaError_t launch_cluster(const RepDesc* d_descs, const ClusterPlan* d_plans, i
 // replica-resident kernel (fkmc_resident.cu)
 constexpr int RESIDENT_MAX_SLOTS = 64;               // vacancies per fragment a thread can hold
 constexpr size_t RESIDENT_MAX_SMEM = 220 * 1024;     // dynamic shared memory per replica CTA
-size_t resident_smem_bytes(const RepDesc& D, int64_t n_vac, int cap, int threads, int pre_g);
+size_t resident_smem_bytes(const RepDesc& D, int64_t n_vac, int cap, int threads, int pre_g, int pre_ev);
 cudaError_t resident_prepare();
 cudaError_t launch_resident(const RepDesc* d_descs, const int32_t* d_reps, int nreps, const int64_t* d_nvac,
                             size_t smem, int threads, int cluster, uint64_t windows, uint32_t* occ, VacRec* recs,

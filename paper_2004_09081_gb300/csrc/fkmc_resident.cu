@@ -216,8 +216,9 @@ struct Layout {
     unsigned long long* S;
     uint8_t* dirty;
     int32_t* act;          // screened fragments
-    float* pre_E;          // first two exponential variates (events 0, 1) of every fragment of the
-    uint64_t* pre_xs;      // batch's phases, and their selection words, by (phase in batch, screen index)
+    float* pre_E;          // first exponential variates (events 0, 1, and 2, 3 where drawn) of every
+    uint64_t* pre_xs;      // fragment of the batch's phases, and their selection words, by (phase in
+                           // batch, screen index)
     uint16_t* frag_of_c;   // cell -> fragment index: x cells, then y, then z
     int16_t* wslot;   // per warp: vacancy index of each slot (-1: handed off)
     int8_t* wtype;    // per warp: rate type of each event (-1: none)
@@ -225,7 +226,8 @@ struct Layout {
 
 
 __host__ __device__ inline size_t layout_bytes(int64_t words, int64_t nv, int64_t nfrag, int64_t ncls, int cap,
-                                               int nwarps, int ltot, int pre_g, size_t* off /* 14 offsets or null */)
+                                               int nwarps, int ltot, int pre_g, int pre_ev,
+                                               size_t* off /* 14 offsets or null */)
 {
     // every array starts on a 16-byte boundary, whatever the sizes before it
     const size_t sz[14] = {
@@ -240,8 +242,8 @@ __host__ __device__ inline size_t layout_bytes(int64_t words, int64_t nv, int64_
         (size_t)ncls * 4,          // 8 screened list
         (size_t)nwarps * cap * 2,  // 9 per-warp slots
         (size_t)nwarps * cap * 8,  // 10 per-warp event types
-        (size_t)pre_g * ncls * 16, // 11 first draws of the batch's phases: selection words
-        (size_t)pre_g * ncls * 8,  // 12 and variates
+        (size_t)pre_g * pre_ev * ncls * 8,  // 11 first draws of the batch's phases: selection words
+        (size_t)pre_g * pre_ev * ncls * 4,  // 12 and variates
         (size_t)ltot * 2,          // 13 cell -> fragment tables
     };
     size_t b = 0;
@@ -253,10 +255,10 @@ __host__ __device__ inline size_t layout_bytes(int64_t words, int64_t nv, int64_
 }
 
 __device__ __forceinline__ Layout carve(unsigned char* dyn, int64_t words, int64_t nv, int64_t nfrag, int64_t ncls,
-                                        int cap, int nwarps, int ltot, int pre_g)
+                                        int cap, int nwarps, int ltot, int pre_g, int pre_ev)
 {
     size_t o[14];
-    layout_bytes(words, nv, nfrag, ncls, cap, nwarps, ltot, pre_g, o);
+    layout_bytes(words, nv, nfrag, ncls, cap, nwarps, ltot, pre_g, pre_ev, o);
     Layout L;
     L.occ = reinterpret_cast<uint32_t*>(dyn + o[0]);
     L.key = reinterpret_cast<uint32_t*>(dyn + o[1]);
@@ -330,15 +332,16 @@ __device__ __forceinline__ double scale_pow2(double d, int F)
 
 }  // namespace
 
-size_t resident_smem_bytes(const RepDesc& D, int64_t n_vac, int cap, int threads, int pre_g)
+size_t resident_smem_bytes(const RepDesc& D, int64_t n_vac, int cap, int threads, int pre_g, int pre_ev)
 {
     const int64_t words = 3 * (int64_t)D.L[2] * D.L[1] * D.row_words;
     const int64_t nfrag = (int64_t)D.nf[0] * D.nf[1] * D.nf[2];
     const int64_t ncls = (int64_t)((D.nf[0] + 1) / 2) * ((D.nf[1] + 1) / 2) * ((D.nf[2] + 1) / 2);
     if (D.L[0] > 1024 || D.L[1] > 1024 || D.L[2] > 1024 || n_vac > 32767 || nfrag > 32767)
         return ~(size_t)0;  // compact keys and 16-bit links need these bounds
-    if (pre_g < 1 || pre_g > 8 || (8 % pre_g) != 0) return ~(size_t)0;
-    return layout_bytes(words, n_vac, nfrag, ncls, cap, threads / 32, D.L[0] + D.L[1] + D.L[2], pre_g, nullptr);
+    if (pre_g < 1 || pre_g > 8 || (8 % pre_g) != 0 || (pre_ev != 2 && pre_ev != 4)) return ~(size_t)0;
+    return layout_bytes(words, n_vac, nfrag, ncls, cap, threads / 32, D.L[0] + D.L[1] + D.L[2], pre_g, pre_ev,
+                        nullptr);
 }
 
 // CL = CTAs per replica (a thread-block cluster).  With CL = 2 both CTAs hold
@@ -378,7 +381,9 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
     const int nfrag = D.nf[0] * D.nf[1] * D.nf[2];
     const int ncls_max = ((D.nf[0] + 1) / 2) * ((D.nf[1] + 1) / 2) * ((D.nf[2] + 1) / 2);
     const int pre_g = (D.pre_g == 2 || D.pre_g == 4 || D.pre_g == 8) ? D.pre_g : 1;  // the host sized the layout for it
-    const Layout S = carve(dyn, words, n_vac, nfrag, ncls_max, cap, NT / 32, D.L[0] + D.L[1] + D.L[2], pre_g);
+    const int pre_ev = D.pre_ev == 4 ? 4 : 2;  // events per fragment drawn ahead: block 0, or blocks 0 and 1
+    const Layout S =
+        carve(dyn, words, n_vac, nfrag, ncls_max, cap, NT / 32, D.L[0] + D.L[1] + D.L[2], pre_g, pre_ev);
 
     // ---- stage in: occupancy by TMA bulk copies, records by plain loads (the
     // first CTA of a cluster; the second copies its shared memory afterwards)
@@ -456,7 +461,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
             if (!sh.abort) {
                 const uint32_t base = peer_addr(dyn, 0);
                 const size_t bytes = layout_bytes(words, n_vac, nfrag, ncls_max, cap, NT / 32,
-                                                  D.L[0] + D.L[1] + D.L[2], pre_g, nullptr);
+                                                  D.L[0] + D.L[1] + D.L[2], pre_g, pre_ev, nullptr);
                 for (size_t k = (size_t)tid * 16; k < bytes; k += (size_t)NT * 16) {
                     const uint4 v = ld_peer16(base + (uint32_t)k);
                     *reinterpret_cast<uint4*>(dyn + k) = v;
@@ -494,10 +499,13 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
             const int ncls = cnt[0] * cnt[1] * cnt[2];
             const int pslot = p & (pre_g - 1);  // this phase's rows of the first-draw arrays
             if (pslot == 0) {
-                // first draws (block 0: events 0 and 1) of every fragment of the next pre_g
-                // phases, one thread each: they depend on no state, and one batch of Philox
-                // blocks here replaces one per phase on the phases' critical paths
-                for (int idx = tid; idx < pre_g * ncls_max; idx += NT) {
+                // first draws (block 0: events 0 and 1; with pre_ev 4 also block 1: events 2
+                // and 3) of every fragment of the next pre_g phases, one thread per block:
+                // they depend on no state, and one batch of Philox blocks here replaces one
+                // per phase (and one per visit of two events or more) on the critical paths
+                const int nbk = pre_ev >> 1;
+                for (int it = tid; it < pre_g * ncls_max * nbk; it += NT) {
+                    const int idx = nbk == 2 ? it >> 1 : it, bk = it - idx * nbk;
                     const int pp = idx / ncls_max, l = idx - pp * ncls_max;
                     const int col = (int)((wperm >> (4 * (p + pp))) & 15u);
                     int c3[3], f3[3];
@@ -511,11 +519,12 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
 #pragma unroll
                     for (int d = 0; d < 3; ++d) f3[d] = D.nf[d] == 1 ? 0 : 2 * f3[d] + ((col >> d) & 1);
                     const int fid = (f3[2] * D.nf[1] + f3[1]) * D.nf[0] + f3[0];
-                    const U64x4 blk = philox4x64((uint64_t)fid, w, 0, 0, D.seed, hop_k1);
-                    S.pre_E[2 * idx] = neglog32(blk.x[0]);
-                    S.pre_E[2 * idx + 1] = neglog32(blk.x[2]);
-                    S.pre_xs[2 * idx] = blk.x[1];
-                    S.pre_xs[2 * idx + 1] = blk.x[3];
+                    const U64x4 blk = philox4x64((uint64_t)fid, w, (uint64_t)bk, 0, D.seed, hop_k1);
+                    const int o = pre_ev * idx + 2 * bk;
+                    S.pre_E[o] = neglog32(blk.x[0]);
+                    S.pre_E[o + 1] = neglog32(blk.x[2]);
+                    S.pre_xs[o] = blk.x[1];
+                    S.pre_xs[o + 1] = blk.x[3];
                 }
             }
             if (tid == 0) {
@@ -536,7 +545,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                 if (!dirty && tot == 0ull) continue;
                 bool active = dirty;
                 if (!active) {
-                    const float E0 = S.pre_E[2 * (pslot * ncls_max + l)];
+                    const float E0 = S.pre_E[pre_ev * (pslot * ncls_max + l)];
                     const float ratio = __fdiv_rn(E0, __ull2float_rn(tot));
                     active = !(ratio > geo.theta_f);  // 0 + 2^F ratio <= theta
                 }
@@ -691,11 +700,12 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1))) k_r
                     }
                     uint64_t xs;
                     float E;
-                    if (i < 2) {  // block 0, drawn in the batch before the phase
-                        xs = S.pre_xs[2 * prow + (int)i];
-                        E = S.pre_E[2 * prow + (int)i];
+                    if (i < (uint64_t)pre_ev) {  // blocks 0 (and 1), drawn in the batch before the phase
+                        xs = S.pre_xs[pre_ev * prow + (int)i];
+                        E = S.pre_E[pre_ev * prow + (int)i];
                     } else {
-                        // events [2 + 64 b, 66 + 64 b) come from blocks 1 + 32 b + lane
+                        // events [2 + 64 b, 66 + 64 b) come from blocks 1 + 32 b + lane (block 1,
+                        // events 2 and 3, was drawn ahead with pre_ev 4: lane 0 recomputes it unused)
                         const uint64_t k = i - 2;
                         if ((k >> 6) != batch) {
                             batch = k >> 6;

@@ -82,7 +82,7 @@ class kmc_replica_info(C.Structure):
                 ("hops", C.c_uint64), ("handoffs", C.c_uint64), ("nsite", C.c_int64),
                 ("n_vac", C.c_int64), ("n_H", C.c_int64), ("null_steps", C.c_uint64),
                 ("null_theta", C.c_double), ("null_time_s", C.c_double), ("n_Fe", C.c_int64),
-                ("kernel", C.c_int32), ("ctas", C.c_int32), ("draw_phases", C.c_int32), ("pad", C.c_int32)]
+                ("kernel", C.c_int32), ("ctas", C.c_int32), ("draw_phases", C.c_int32), ("draw_events", C.c_int32)]
 
 
 class kmc_invariants(C.Structure):

@@ -223,13 +223,15 @@ def test_batched_workload_full_size_sampled(fk, orc):
         assert m[0] == reps[r].n_vac
     cap = b.info(0).cap_v
     # the largest replicas (1024- or 512-thread class), a spread of others, and
-    # one replica of every batch size of the resident kernel's first draws
+    # one replica of every batch shape (phases, events) of the resident kernel's
+    # first draws
     largest = sorted(range(len(reps)), key=lambda r: -reps[r].n_vac)[:3]
     by_draws = {}
     for r in range(len(reps)):
         if b.info(r).kernel == 1:
-            by_draws.setdefault(b.info(r).draw_phases, r)
-    assert set(by_draws) <= {1, 2, 4, 8} and 8 in by_draws
+            by_draws.setdefault((b.info(r).draw_phases, b.info(r).draw_events), r)
+    assert set(by_draws) <= {(8, 4), (4, 4), (2, 4), (8, 2), (4, 2), (2, 2), (1, 2)}
+    assert (8, 4) in by_draws and any(ev == 2 for _, ev in by_draws)
     for r in sorted(set(largest) | {0, 1, 97, 200, 255} | set(by_draws.values())):
         rep = reps[r]
         info = b.info(r)
