@@ -77,6 +77,72 @@ def test_the_batched_workload_at_the_former_default_fails_the_bound(at):
     assert at.accepted(est, 0.01), (wl.edge, wl.n_tau, est)
 
 
+def test_search_times_only_accepted_candidates_and_keeps_the_fastest(at, monkeypatch):
+    """The search loop (host logic, no GPU): a stand-in for the batch records
+    every candidate it is built with and reports a made-up rate; only the
+    candidates inside the bound are built and timed, each with the same
+    simulated time, and the fastest of them wins."""
+    from paper_2004_09081_gb300 import workloads
+    wl = workloads.batched_batio3(0)
+    cells = [r.cells for r in wl.replicas]
+    built = []
+
+    class Stats:
+        def __init__(self, hops, gpu_ms):
+            self.hops, self.gpu_ms = hops, gpu_ms
+
+    class Info:
+        cap_v = 32
+
+    class FakeBatch:
+        def __init__(self, cells_, comps, seed, precision=None, **kw):
+            self.kw = kw
+            self.windows = []
+            self.closed = False
+            built.append(self)
+
+        def set_barriers(self, *a, **k):
+            pass
+
+        def run(self, windows):
+            self.windows.append(windows)
+            # faster for longer windows and edge 5, slower with cluster pairs
+            rate = self.kw["n_tau"] * (2.0 if self.kw["edge"] == 5 else 1.0) * \
+                (0.5 if self.kw["cluster_top"] != 0 else 1.0)
+            return Stats(hops=int(1e6 * rate), gpu_ms=1.0)
+
+        def info(self, r):
+            return Info()
+
+        def close(self):
+            self.closed = True
+
+    monkeypatch.setattr(at.fkmc, "Batch", FakeBatch)
+    comps = [(r.n_vac, r.n_H) for r in wl.replicas]
+    best, results = at.autotune(cells, comps, 0, 0.7, 0.35, 600.0, warm_windows=2, timed_windows=8)
+    assert len(results) == len(at.EDGES) * len(at.N_TAUS) * len(at.LAUNCH)
+    table = at.deficit_table()
+    for r in results:
+        c = r["candidate"]
+        ok = at.accepted(at.batch_deficit(table, cells, c["edge"], c["n_tau"])[2], 0.01)
+        assert r["accepted"] == ok
+        assert (r["hops_per_s"] is not None) == ok
+    assert len(built) == sum(r["accepted"] for r in results)
+    for b in built:
+        assert b.closed
+        # a warm-up, then the same simulated time at every n_tau
+        assert b.windows == [2, max(1, int(round(8 / b.kw["n_tau"])))]
+    timed = [r for r in results if r["hops_per_s"]]
+    top = max(r["hops_per_s"] for r in timed)
+    assert best in [r["candidate"] for r in timed if r["hops_per_s"] == top]
+    assert best["edge"] == 5 and best["cluster_top"] == 0
+    # the workload's own choice is the fastest accepted n_tau at edge 5
+    assert best["n_tau"] == max(r["candidate"]["n_tau"] for r in timed if r["candidate"]["edge"] == 5)
+    # nothing inside the bound: an error, not a silent default
+    with pytest.raises(RuntimeError):
+        at.autotune(cells, comps, 0, 0.7, 0.35, 600.0, bound=1e-6)
+
+
 def test_table_entry_reproduced_by_the_oracle(orc):
     """One stored per-seed deficit recomputed by the oracle, bit for bit (the
     table was written by oracle/window_deficit.py from the oracle alone)."""
