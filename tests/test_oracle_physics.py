@@ -83,6 +83,56 @@ def test_single_vacancy_D_closed_form(orc):
         assert 0.8 < D / D_exact < 1.25
 
 
+def test_single_vacancy_among_hydride_ions(orc):
+    """The H- exchange rate, apart from the O one.  (1) Every other O site holds
+    H-: all 8 exchanges of the vacancy take the H- barrier, so one fragment
+    gives hop rate 8 k_H and D = (2/3) k_H a^2, whatever the (far higher) O
+    barrier.  (2) A mixture: with equal barriers both ways the configurations
+    of one vacancy among n_H H- and the rest O are equally likely at all
+    times (the placement is uniform and the dynamics reversible with respect
+    to the uniform measure), so the mean hop rate is exactly
+    8 (p k_H + (1 - p) k_O) with p = n_H / (N - 1), N the O-sublattice sites."""
+    T, a = 800.0, 3.905
+    cells = (8, 8, 8)
+    N = 3 * 8 ** 3
+    h = 0.5 * a * 1e-10
+    # (1) all H-
+    Ea_O, Ea_H = 0.9, 0.6
+    kH = k_of(Ea_H, T)
+    disp, hops, t = [], 0, None
+    for s in range(40):
+        L = orc.Lattice(cells, (1, 1, 1), 1, N - 1, seed=s)
+        L.set_rates(Ea_O, Ea_H, T, a_ang=a, n_tau=0.5)
+        L.run(600)
+        disp.append(L.records()[:, 2:5])
+        hops += L.counters()["hops"]
+        t = 600 * L.params()["tau"]
+    expect = 40 * 8 * kH * t
+    assert abs(hops - expect) < 3.5 * math.sqrt(expect), (hops, expect)
+    d = np.concatenate(disp).astype(np.float64)
+    r2 = (d ** 2).sum(1) * h * h / (6 * t)
+    D_exact = 2.0 / 3.0 * kH * (a * 1e-10) ** 2
+    D, se = r2.mean(), r2.std(ddof=1) / math.sqrt(len(r2))
+    assert abs(D - D_exact) < 3 * se, (D / D_exact, se / D_exact)
+    # (2) 30% of the other sites H-
+    Ea_O, Ea_H = 0.6, 0.5
+    kH, kO = k_of(Ea_H, T), k_of(Ea_O, T)
+    nH = round(0.3 * (N - 1))
+    p = nH / (N - 1)
+    rates = []
+    for s in range(48):
+        L = orc.Lattice(cells, (1, 1, 1), 1, nH, seed=100 + s)
+        L.set_rates(Ea_O, Ea_H, T, a_ang=a, n_tau=0.5)
+        L.run(2000)
+        rates.append(L.counters()["hops"] / (2000 * L.params()["tau"]))
+    rates = np.array(rates)
+    expect = 8 * (p * kH + (1 - p) * kO)
+    m, se = rates.mean(), rates.std(ddof=1) / math.sqrt(len(rates))
+    assert abs(m - expect) < 4 * se, (m / expect, se / expect)
+    # the two plausible slips: every exchange at one barrier
+    assert abs(m - 8 * kO) > 10 * se and abs(m - 8 * kH) > 10 * se
+
+
 def test_windowing_error_vanishes_with_tau(orc):
     """Hop-rate deficit of the fragmented scheme is bounded by 4% x n_tau and
     shrinks as the window shortens (4^3 fragments of 4^3 cells)."""
