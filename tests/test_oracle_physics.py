@@ -163,6 +163,30 @@ def test_drift_under_field(orc):
     assert v_exact == 0.0
 
 
+def test_drift_of_a_vacancy_among_hydride_ions(orc):
+    """Every other O site holds H-, so every exchange moves charge +1 (H- <-> V)
+    instead of the vacancy's +2: v_z = (8/3) a k_H sinh(eps_H), eps_H =
+    E a / (4kT) with unit charge.  The field is the one that gives eps = 0.4
+    for O exchanges; charge +2 here would double eps and the drift."""
+    T, a = 800.0, 3.905
+    N = 3 * 8 ** 3
+    h = 0.5 * a * 1e-10
+    Ez = 0.4 * 4 * KB * T / (2.0 * a * 1e-10)
+    eps_H = 1.0 * Ez * a * 1e-10 / (4 * KB * T)
+    v_exact = 8.0 / 3.0 * a * 1e-10 * k_of(0.6, T) * math.sinh(eps_H)
+    vz = []
+    for s in range(300):
+        L = orc.Lattice((8, 8, 8), (1, 1, 1), 1, N - 1, seed=s)
+        L.set_rates(0.9, 0.6, T, Ez=Ez, a_ang=a, n_tau=1.0)
+        L.run(300)
+        vz.append(L.records()[0, 4] * h / (300 * L.params()["tau"]))
+    vz = np.array(vz, np.float64)
+    v, se = vz.mean(), vz.std(ddof=1) / math.sqrt(len(vz))
+    assert abs(v - v_exact) < 3.5 * se, (v / v_exact, se / v_exact)
+    v_q2 = 8.0 / 3.0 * a * 1e-10 * k_of(0.6, T) * math.sinh(2 * eps_H)
+    assert abs(v - v_q2) > 10 * se
+
+
 def test_first_hop_is_uniform(orc):
     """Tiny lattice, one vacancy: the first exchange goes to each of the 8
     neighbours with probability 1/8 (all rates equal)."""
